@@ -1,0 +1,355 @@
+"""Pins of the CPU FP64 oracle against things other than itself.
+
+Each test checks the oracle against a hand derivation, a closed form, an
+independent pure-Python construction, a library routine (numpy) or an
+invariance of the mathematics, chosen so that a plausible slip in the oracle
+(a dropped term, a swapped operand, an off-by-one in the pair decoding, a wrong
+unit rule) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.bruteforce import enumerate_bruteforce
+from oracle.counts import closed_form_sizes, unit_class_counts
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SQUARE, CUBE, INV, SQRT, EXP, LOG, ADD, SUB, MUL, DIV, RDIV, ABSDIFF = range(12)
+
+
+def mask(*c):
+    m = 0
+    for x in c:
+        m |= 1 << x
+    return m
+
+
+def unpruned_space(orc, X, ops, rung, units=None, **kw):
+    kw.setdefault("fmax_max", 1e300)
+    kw.setdefault("fmin_std_rel", -1.0)
+    return orc.Space(X, units, mask(*ops), rung, **kw)
+
+
+# ------------------------------------------------------------------ counts
+
+@pytest.mark.parametrize("ops,rung,n0,N", [
+    ((ADD, MUL, DIV, RDIV, SQUARE, CUBE, EXP), 2, 4, 16),
+    ((ADD, SUB, MUL, SQUARE, CUBE), 2, 5, 12),
+    ((ADD, MUL, DIV, RDIV, SQUARE), 3, 3, 8),
+    ((MUL,), 2, 6, 8),
+    ((SQRT, EXP), 2, 5, 8),
+])
+def test_counts_match_closed_form(orc, ops, rung, n0, N):
+    """No pruning possible (positive data, no domain-restricted op can fail,
+    huge magnitude limit, degeneracy off): every slot is valid, so |Phi_r|
+    must equal the closed form."""
+    rng = np.random.default_rng(7)
+    X = rng.uniform(0.5, 2.0, size=(n0, N))
+    S = unpruned_space(orc, X, ops, rung)
+    nu = sum(1 for o in ops if o <= LOG)
+    nb = len(ops) - nu
+    sizes = closed_form_sizes(n0, nu, nb, rung)
+    total = 0
+    for r in range(rung + 1):
+        slots, rs = S.rung_counts(r)
+        assert rs["valid"] == slots
+        total += slots
+        assert total == sizes[r]
+    assert S.total_candidates == sizes[rung]
+    assert S.n_features == sizes[rung - 1]
+
+
+def test_closed_form_golden_matches_formula():
+    g = json.load(open(os.path.join(GOLDEN, "closed_form_counts.json")))
+    sizes = g["sizes"]
+    assert sizes["tiny: n0=8, 4 unary (sq sqrt exp log), 5 binary slots (+ - * a/b b/a), rung 2"] == [8, 180, 81278]
+    for v in sizes.values():
+        # |new_r| must be exactly reproducible from the previous two sizes
+        for r in range(2, len(v)):
+            assert v[r] > v[r - 1]
+
+
+@pytest.mark.parametrize("explog_dimless", [1, 0])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_counts_match_unit_classes(orc, explog_dimless, seed):
+    """Pruning by units only: the oracle's valid counts per rung equal the
+    class-wise count with Fraction exponents, which never visits a pair."""
+    rng = np.random.default_rng(100 + seed)
+    n0, N = 7, 10
+    X = rng.uniform(0.5, 2.0, size=(n0, N))
+    units = rng.integers(-2, 3, size=(n0, 3)).astype(np.int32)
+    ops = (ADD, MUL, DIV, RDIV, ABSDIFF, SQUARE, CUBE, INV, SQRT, EXP)
+    S = unpruned_space(orc, X, ops, 2, units=units, unit_check_addsub=1, explog_dimensionless=explog_dimless)
+    ref = unit_class_counts(units, ops, 2, unit_check_addsub=True, explog_dimensionless=bool(explog_dimless))
+    for r in (1, 2):
+        slots, rs = S.rung_counts(r)
+        assert (slots, rs["valid"]) == ref[r - 1]
+        assert rs["valid"] + rs["unit"] == slots
+
+
+# -------------------------------------------------------- enumeration order
+
+def _hand_case(orc, case):
+    g = json.load(open(os.path.join(GOLDEN, "tiny_space_2primaries.json")))
+    c = g[case]
+    X = np.array([[0.7, 1.3, 1.9, 0.6], [1.1, 0.8, 1.7, 1.4]])
+    S = unpruned_space(orc, X, (SQUARE, ADD), 2, units=np.array(c["units"], np.int32))
+    return S, c
+
+
+@pytest.mark.parametrize("case", ["dimensionless", "unit_clash"])
+def test_hand_enumerated_space(orc, case):
+    S, c = _hand_case(orc, case)
+    assert S.n_features == len(c["stored"])
+    assert [S.expr(i) for i in range(S.n_features)] == c["stored"]
+    n2 = S.rung_slots(2)
+    assert n2 == len(c["rung2"])
+    got = [S.expr(S.n_features + p) for p in range(n2)]
+    assert got == c["rung2"]
+    valid = [S.candidate(S.n_features + p)[1] == 0 for p in range(n2)]
+    assert valid == c["rung2_unit_valid"]
+    if "rung1_slots" in c:
+        slots, rs = S.rung_counts(1)
+        assert (slots, rs["valid"]) == (c["rung1_slots"], c["rung1_valid"])
+
+
+@pytest.mark.parametrize("n0,rung,ops,dims,seed", [
+    (4, 2, (ADD, SUB, MUL, DIV, RDIV, ABSDIFF, SQUARE, CUBE, INV, SQRT, EXP), 2, 0),
+    (3, 2, (SUB, DIV, SQRT), 1, 1),
+    (4, 2, (RDIV, ABSDIFF, EXP, LOG), 2, 2),
+    (2, 3, (ADD, DIV, SQUARE), 1, 3),
+])
+def test_bruteforce_enumeration(orc, n0, rung, ops, dims, seed):
+    """The oracle's decoding of every flat index (integer bisection on the
+    pair triangle) and its unit rule against explicit expression trees with
+    Fraction exponents.  Data positive and |a-b|, a-b never feed a
+    domain-restricted op at the last rung here unless the op set has none."""
+    rng = np.random.default_rng(seed)
+    N = 6
+    X = rng.uniform(0.5, 2.0, size=(n0, N))
+    units = rng.integers(-1, 2, size=(n0, dims)).astype(np.int32)
+    # keep the unit pruning the only pruning: degeneracy off, huge magnitude,
+    # and domain tests cannot fail for positive data at rung 1; at the last
+    # rung a domain failure is reported as 'domain', which we accept only for
+    # slots the brute force marks unit-valid.
+    S = unpruned_space(orc, X, ops, rung, units=units, unit_check_addsub=1, explog_dimensionless=1)
+    stored, last = enumerate_bruteforce(units, ops, rung, True, True)
+    assert [S.expr(i) for i in range(S.n_features)] == [e.text for e in stored]
+    assert S.rung_slots(rung) == len(last)
+    for p, e in enumerate(last):
+        gid = S.n_features + p
+        assert S.expr(gid) == (e.text if e is not None else S.expr(gid))
+        why = S.candidate(gid)[1]
+        if e is None:
+            assert why == 1, (p, S.expr(gid))
+        else:
+            assert why in (0, 3), (p, e.text, why)
+            assert S.expr(gid) == e.text
+
+
+def test_unit_invalid_strings_still_decode(orc):
+    """Unit-invalid slots decode to the expression the brute force would build
+    without the unit check."""
+    rng = np.random.default_rng(5)
+    units = np.array([[1], [0], [2]], np.int32)
+    X = rng.uniform(0.5, 2.0, size=(3, 5))
+    ops = (ADD, SUB, MUL)
+    S = unpruned_space(orc, X, ops, 2, units=units)
+    stored, last_checked = enumerate_bruteforce(units, ops, 2, True, True)
+    # the unchecked enumeration of the last rung from the same stored set
+    from oracle.bruteforce import _binary
+    begin = [i for i, e in enumerate(stored) if e.rung == 1][0]
+    texts = []
+    for i in range(begin, len(stored)):
+        for j in range(i):
+            for op in ops:
+                texts.append(_binary(op, stored[i], stored[j], False, 2).text)
+    assert [S.expr(S.n_features + p) for p in range(S.rung_slots(2))] == texts
+
+
+# -------------------------------------------------------------------- score
+
+def test_pearson_hand_value(orc):
+    g = json.load(open(os.path.join(GOLDEN, "pearson_hand.json")))
+    X = np.array([g["v"], [0.3, 0.9, 0.1, 0.5]])
+    S = unpruned_space(orc, X, (MUL,), 1)
+    sc, why = S.score_ids(np.array(g["y"]), [0])
+    assert why[0] == 0
+    assert abs(sc[0, 0] - g["score_num"] / math.sqrt(g["score_den_sq"])) < 1e-15
+
+
+def test_score_matches_numpy_corrcoef(orc):
+    rng = np.random.default_rng(11)
+    X = rng.uniform(0.5, 2.0, size=(6, 40))
+    Y = rng.standard_normal((3, 40))
+    S = orc.Space(X, None, mask(ADD, SUB, MUL, DIV, RDIV, SQRT, LOG), 2)
+    ids = rng.choice(S.total_candidates, size=300, replace=False).astype(np.uint64)
+    sc, why = S.score_ids(Y, ids)
+    checked = 0
+    for n, gid in enumerate(ids):
+        v, w = S.candidate(int(gid))
+        assert w == why[n]
+        if w:
+            continue
+        for t in range(3):
+            ref = abs(np.corrcoef(v, Y[t])[0, 1])
+            assert abs(sc[n, t] - ref) <= 1e-12 * max(ref, 1e-3)
+        checked += 1
+    assert checked > 150
+
+
+def test_score_affine_invariance(orc):
+    """score(alpha*y + beta) == score(y), and a primary that is an affine map
+    of another gets the same score as it."""
+    rng = np.random.default_rng(12)
+    X = rng.uniform(0.5, 2.0, size=(5, 64))
+    X = np.vstack([X, -3.5 * X[2] + 7.25])
+    y = rng.standard_normal(64)
+    S = orc.Space(X, None, mask(ADD, MUL, DIV, RDIV, SQUARE), 2)
+    ids = np.arange(0, S.total_candidates, 7, dtype=np.uint64)
+    s1, w1 = S.score_ids(y, ids)
+    s2, w2 = S.score_ids(-0.25 * y + 3.0, ids)
+    ok = w1 == 0
+    assert ok.sum() > 100
+    assert np.all(w1 == w2)
+    # relative to the score, floored at 1e-2: a score near 0 is an absolute
+    # cancellation of size ~1e-16 in the numerator
+    assert np.max(np.abs(s1[ok] - s2[ok]) / np.maximum(s1[ok], 1e-2)) < 1e-12
+    s, _ = S.score_ids(y, [2, 5])
+    assert abs(s[0, 0] - s[1, 0]) < 1e-12
+
+
+def test_aggregated_equals_per_target_for_one_target(orc):
+    rng = np.random.default_rng(13)
+    X = rng.uniform(0.5, 2.0, size=(5, 30))
+    y = rng.standard_normal(30)
+    S = orc.Space(X, None, mask(ADD, SUB, MUL, DIV, RDIV), 2)
+    a_ids, a_sc, _ = S.screen(y, 50, mode="aggregated")
+    p_ids, p_sc, _ = S.screen(y, 50, mode="per_target")
+    assert np.array_equal(a_ids[0], p_ids[0])
+    assert np.allclose(a_sc[0], p_sc[0], rtol=1e-14, atol=0)
+
+
+def test_topk_equals_full_ranking(orc):
+    """The streaming per-thread top-k equals a full ranking of all valid
+    candidates by numpy lexsort on (score desc, id asc)."""
+    rng = np.random.default_rng(14)
+    X = rng.uniform(0.5, 2.0, size=(5, 25))
+    Y = rng.standard_normal((2, 25))
+    S = orc.Space(X, None, mask(ADD, SUB, MUL, DIV, RDIV, SQRT), 2)
+    ids = np.arange(S.total_candidates, dtype=np.uint64)
+    sc, why = S.score_ids(Y, ids)
+    for k in (1, 37, 5000):
+        got_ids, got_sc, cnt = S.screen(Y, k)
+        assert cnt["valid"] == int((why == 0).sum())
+        for t in range(2):
+            v = why == 0
+            order = np.lexsort((ids[v], -sc[v, t]))
+            ref = ids[v][order][:k]
+            assert np.array_equal(got_ids[t], ref)
+            assert np.array_equal(got_sc[t], sc[v, t][order][:k])
+
+
+def test_planted_formula_recovered_noise_free(orc):
+    from paper_2602_06986_gb300 import workloads as W
+
+    w = W.tiny(seed=3, noise=0.0)
+    S = orc.Space(w["X"], w["units"], w["op_mask"], 2, unit_check_addsub=1, explog_dimensionless=0)
+    ids, sc, _ = S.screen(w["Y"], 10)
+    assert 1.0 - sc[0][0] < 1e-14
+    top = [S.expr(int(i)) for i, s in zip(ids[0], sc[0]) if 1.0 - s < 1e-13]
+    assert w["planted"] in top
+    # every member of the top tie group is an algebraic rewrite of 2*x1*x3/x5^2
+    X = w["X"]
+    ref = X[1] * X[3] / X[5] ** 2
+    for i, s in zip(ids[0], sc[0]):
+        if 1.0 - s < 1e-13:
+            v, _ = S.candidate(int(i))
+            c = np.polyfit(ref, v, 1)
+            assert np.allclose(np.polyval(c, ref), v, rtol=1e-12, atol=1e-12)
+
+
+# -------------------------------------------------------------------- masks
+
+def test_domain_magnitude_realised_reasons(orc):
+    N = 8
+    x0 = np.array([-1.0, -0.6, -0.004, 0.2, 0.5, 0.9, 1.2, 1.5])  # crosses zero
+    x1 = np.linspace(0.5, 2.0, N)           # positive
+    x2 = np.linspace(81.0, 90.0, N)         # exp(x2) beyond the domain limit
+    X = np.vstack([x0, x1, x2])
+    S = orc.Space(X, None, mask(SQRT, EXP, LOG, MUL, DIV, RDIV, INV), 1, fmax_max=100.0, fmin_std_rel=1e-8)
+    nf = S.n_features
+    names = {S.expr(nf + p): S.candidate(nf + p)[1] for p in range(S.rung_slots(1))}
+    assert names["log(x0)"] == 3 and names["sqrt(x0)"] == 3
+    assert names["log(x1)"] == 0 and names["sqrt(x1)"] == 0
+    assert names["exp(x2)"] == 3              # max > 80
+    assert names["exp(x1)"] == 0              # e^2 < log(100) bound holds: max 2 <= log(100)
+    assert names["inv(x1)"] == 0
+    # 1/x0: min|x0| = 0.004 > 0, but 1/min|x0| = 250 > 100 -> magnitude
+    assert min(abs(x0)) > 0 and 1.0 / min(abs(x0)) > 100.0
+    assert names["inv(x0)"] == 4
+    # x2*x1 bound = 90*2 = 180 > 100 -> magnitude; x1*x0 bound 3 <= 100
+    assert names["(x2*x1)"] == 4 and names["(x1*x0)"] == 0
+    # (x1/x0): 2/0.004 > 100 -> magnitude; (x0/x1): 1.5/0.5 <= 100
+    assert names["(x1/x0)"] == 4 and names["(x0/x1)"] == 0
+
+
+def test_exact_reciprocal_product_is_degenerate(orc):
+    rng = np.random.default_rng(15)
+    X = rng.uniform(0.5, 2.0, size=(2, 32))
+    S = orc.Space(X, None, mask(MUL, DIV, RDIV), 2, fmin_std_rel=1e-8)
+    nf = S.n_features
+    found = False
+    for p in range(S.rung_slots(2)):
+        e = S.expr(nf + p)
+        if e in ("((x1/x0)*(x0/x1))", "((x0/x1)*(x1/x0))"):
+            assert S.candidate(nf + p)[1] == 5
+            found = True
+    assert found
+
+
+# ------------------------------------------------------------ residual loop
+
+def test_residual_loop_recovers_two_terms(orc):
+    """Noise-free y = c1*fa + c2*fb: D=2 picks columns spanning fa and fb and
+    the RMSE vanishes; the coefficients equal numpy lstsq on those columns."""
+    rng = np.random.default_rng(16)
+    N, n0 = 200, 6
+    X = rng.lognormal(0.0, 0.5, size=(n0, N))
+    fa = X[0] * X[1] / X[2] ** 2
+    fb = (X[3] / X[4]) * np.sqrt(X[5])
+    y = 1.5 * fa - 0.8 * fb + 0.3
+    S = orc.Space(X, None, mask(*range(12)), 2)
+    out = S.residual_loop(y, 3, 200)
+    assert out["rmse"][1] < 1e-10 * y.std()
+    assert out["rmse"][0] > 1e-3
+    cols = [S.candidate(int(i))[0] for i in out["ids"][:2]]
+    A = np.column_stack([np.ones(N)] + cols)
+    beta = np.linalg.lstsq(A, y, rcond=None)[0]
+    assert np.allclose(beta, out["coefs"][1][:3], rtol=1e-8, atol=1e-10)
+    # the chosen two columns reproduce fa and fb up to scale
+    for f in (fa, fb):
+        B = np.column_stack([np.ones(N)] + cols)
+        r = f - B @ np.linalg.lstsq(B, f, rcond=None)[0]
+        assert np.sqrt(np.mean(r ** 2)) < 1e-9 * f.std()
+
+
+def test_residual_loop_first_pick_is_top_sis(orc):
+    rng = np.random.default_rng(17)
+    X = rng.uniform(0.5, 2.0, size=(5, 80))
+    y = X[0] * X[1] + 0.05 * rng.standard_normal(80)
+    S = orc.Space(X, None, mask(ADD, SUB, MUL, DIV, RDIV), 2)
+    out = S.residual_loop(y, 2, 50)
+    ids, sc, _ = S.screen(y, 50)
+    assert np.array_equal(out["sis"][0], ids[0])
+    # the smallest one-feature RMSE belongs to the largest |r|; algebraic
+    # rewrites of the same feature tie to ~1e-16, so any of them may win
+    pick = list(ids[0]).index(out["ids"][0])
+    assert sc[0][0] - sc[0][pick] < 1e-13
+    # one-feature LS RMSE from the correlation: sqrt(Syy (1 - r^2) / N)
+    r = sc[0][pick]
+    yc = y - y.mean()
+    assert abs(out["rmse"][0] - math.sqrt(np.sum(yc ** 2) * (1 - r * r) / 80)) < 1e-12
