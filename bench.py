@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the SIS screening hot path on GB300.
+
+One step = one pass of the whole path over one synthetic workload: build the
+feature space (rungs < k materialised on the device), then the residual loop
+D = 1..3: SIS screen of rung 2 against the current residual (top-1000, exact
+top-k selection with FP64 re-score of the boundary band) and FP64
+least-squares refits of the retained candidates.  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (256 MiB write) between steps.
+
+Metric: SIS-screened candidate features per second (valid candidates scored),
+with evals/s (candidate x sample) and the plain FP64 GPU path on the same
+workload beside it.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dse|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SIS-screened candidate features/sec and evals/sec vs plain FP64 GPU path"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES = 128
+# algorithmic FP32 lane operations per (valid candidate, sample) at one target:
+# evaluation, sum w, sum w^2 (FMA), sum w*y (FMA)
+OPS_PER_EVAL = 4
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            m = json.load(f)
+        mhz = float(m.get("sm_max_mhz", SM_MAX_MHZ))
+        return mhz, "measured max SM clock (MEASURED_PEAKS.json sm_max_mhz)"
+    except Exception:
+        return SM_MAX_MHZ, "nominal max SM clock (fallback)"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(seed):
+    from paper_2602_06986_gb300 import workloads as W
+
+    return W.medium(seed)
+
+
+def count_step_evals(stats_list, N):
+    cands = sum(s["evaluated"] for s in stats_list)
+    return cands, cands * N
+
+
+def run_step_device(torch, dse, w, Xd, yd, k, D, stream, precision, timing=True):
+    """One step with device-resident inputs; returns (stats list, picks)."""
+    sp = dse.Space(Xd, w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                   explog_dimensionless=w["explog_dimensionless"], stream=stream)
+    N = sp.n_samples
+    r = yd
+    fixed, stats = [], []
+    ids = torch.empty(k, dtype=torch.int64, device="cuda")
+    sc = torch.empty(k, dtype=torch.float64, device="cuda")
+    eb = torch.empty(k, dtype=torch.float64, device="cuda")
+    for d in range(D):
+        res = sp.screen(r, k, precision=precision, stream=stream, flags=dse.FLAG_TIMING if timing else 0)
+        n = res.fetch(0, out=(ids, sc, eb))
+        stats.append(res.stats())
+        res.free()
+        nxt = torch.empty(N, dtype=torch.float64, device="cuda")
+        bid, rmse, coefs, _ = sp.ls_refit(yd, np.array(fixed, np.uint64), ids[:n], residual=nxt, stream=stream)
+        fixed.append(bid)
+        r = nxt
+    sp.free()
+    return stats, fixed
+
+
+def run_step_host(dse, w, k, D):
+    """One step through the public API with host buffers (copies inside)."""
+    X = w["X"]
+    y = w["Y"][0]
+    sp = dse.Space(X, w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                   explog_dimensionless=w["explog_dimensionless"])
+    h2d = X.nbytes + w["units"].nbytes
+    d2h = 0
+    r = y
+    fixed, stats = [], []
+    for d in range(D):
+        res = sp.screen(r, k)
+        ids, sc, eb = res.fetch(0)
+        stats.append(res.stats())
+        res.free()
+        h2d += r.nbytes
+        d2h += ids.nbytes + sc.nbytes + eb.nbytes
+        bid, rmse, coefs, resid = sp.ls_refit(y, np.array(fixed, np.uint64), ids)
+        h2d += y.nbytes + ids.nbytes + 8 * len(fixed)
+        d2h += resid.nbytes + 8 * (len(fixed) + 2) + 16
+        fixed.append(bid)
+        r = resid
+    sp.free()
+    return stats, h2d, d2h
+
+
+def cpu_oracle_step(w, k, D):
+    import oracle
+
+    t0 = time.perf_counter()
+    S = oracle.Space(w["X"], w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                     explog_dimensionless=w["explog_dimensionless"])
+    out = S.residual_loop(w["Y"][0], D, k)
+    dt = time.perf_counter() - t0
+    # valid candidates scored by one screen of the full space, per screen
+    slots, rs = S.rung_counts(w["max_rung"])
+    per_screen = S.n_features + rs["valid"]
+    return dt, per_screen * D, out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dse", choices=["dse", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = workload(rank)
+    k, D = w["k"], w["D"]
+    N = w["X"].shape[1]
+    config = {"workload": w["name"], "N": N, "n_primary": int(w["X"].shape[0]), "max_rung": w["max_rung"],
+              "k": k, "D": D, "targets": 1, "l2": "flushed between steps (256 MiB write)",
+              "parallelism": f"replicas x{world} (independent workloads, no collective)"}
+
+    if args.impl == "reference":
+        # the reference arm is the CPU FP64 oracle, timed on the host cores
+        if rank != 0:
+            return
+        import oracle
+
+        oracle.build()
+        for _ in range(args.warmup):
+            cpu_oracle_step(w, k, D)
+        times, cands = [], 0
+        for _ in range(args.steps):
+            dt, c, _ = cpu_oracle_step(w, k, D)
+            times.append(dt)
+            cands += c
+        tot = sum(times)
+        v = cands / tot
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "candidates/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": oracle.num_threads(),
+                                 "kind": "oracle", "sample": "the full workload per step (space build + 3 screens "
+                                                             "+ refits)"},
+                "e2e": {"value": v, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2602_06986_gb300 import _build
+
+    _build.build()
+    from paper_2602_06986_gb300 import dse
+
+    stream = torch.cuda.current_stream().cuda_stream
+    Xd = torch.from_numpy(w["X"]).cuda()
+    yd = torch.from_numpy(w["Y"][0].copy()).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        run_step_device(torch, dse, w, Xd, yd, k, D, stream, dse.PREC_FP32)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    L0 = dse.lib().dse_kernel_launches()
+    step_ms, all_stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats, picks = run_step_device(torch, dse, w, Xd, yd, k, D, stream, dse.PREC_FP32)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        all_stats.append(stats)
+    launches = dse.lib().dse_kernel_launches() - L0
+    barrier()
+    clk = clocks.stop()
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    cands = sum(count_step_evals(s, N)[0] for s in all_stats)
+    value = world * cands / (tot_ms * 1e-3)
+    evals_per_s = value * N
+
+    # dominant kernel: the product/quotient pair kernel (live CUDA-event time)
+    mul_ms = sum(s["kernel_ms"][1] for st in all_stats for s in st)
+    mul_valid = sum(s["valid_by_group"][1] for st in all_stats for s in st)
+    mul_launches = sum(1 for st in all_stats for s in st)
+    mhz, peak_src = peaks()
+    peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12  # T lane-ops/s
+    achieved = mul_valid * N * OPS_PER_EVAL / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
+    group_ms = [sum(s["kernel_ms"][g] for st in all_stats for s in st) for g in range(4)]
+
+    # the plain FP64 GPU path on the same workload (same step, FP64 kernels)
+    fp64_ms, fp64_c = [], 0
+    for _ in range(2):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st64, _ = run_step_device(torch, dse, w, Xd, yd, k, D, stream, dse.PREC_FP64, timing=False)
+        e1.record()
+        torch.cuda.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+        fp64_c += count_step_evals(st64, N)[0]
+    fp64_value = fp64_c / (sum(fp64_ms) * 1e-3)
+
+    # end to end through the public API with host buffers
+    e2e_ms, e2e_c = [], 0
+    for _ in range(3):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        st_h, h2d, d2h = run_step_host(dse, w, k, D)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_c += count_step_evals(st_h, N)[0]
+    e2e_value = e2e_c / (sum(e2e_ms) * 1e-3)
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        dt, c, _ = cpu_oracle_step(w, k, D)
+        cpu = {"value": c / dt, "unit": "candidates/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "one full step of the same workload (space build + 3 screens + refits), "
+                         f"{dt:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "evals_per_s": evals_per_s,
+        "fp64_plain": {"value": fp64_value, "unit": "candidates/s", "ms_per_step": sum(fp64_ms) / len(fp64_ms),
+                       "speedup_of_fp32_path": value / world / fp64_value},
+        "roofline": {"bound": "alu", "kernel": "k_pair<float,MUL,1,2,2> (a*b, a/b, b/a slots)",
+                     "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({peak_src})",
+                     "ops_per_eval": OPS_PER_EVAL, "launch_ms": mul_ms / max(mul_launches, 1),
+                     "share_of_step": mul_ms / tot_ms},
+        "kernel_group_ms_per_step": {"stored_unary": group_ms[0] / args.steps, "pair_mul": group_ms[1] / args.steps,
+                                     "pair_add": group_ms[2] / args.steps, "select": group_ms[3] / args.steps},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * dse.h -- C ABI of the GB300 (sm_103a) descriptor-screening engine.
+ *
+ * The engine implements the data-parallel hot path of SISSO-style symbolic
+ * regression as used by DISCOVER (arXiv 2602.06986): generate rung-k
+ * candidate features from user-provided primary features and an operator
+ * library, drop dimensionally invalid ones, evaluate every candidate on every
+ * sample and keep the top k by Sure Independence Screening (|Pearson|
+ * correlation) against one or many targets or residuals.
+ *
+ * Passages of the paper each call follows:
+ *   dse_build_space     "Software Description": candidates are generated from
+ *                       user features and operator libraries, iteratively;
+ *                       "Physics-Informed Constraints": dimensionally invalid
+ *                       expressions are excluded early; "Design Philosophy
+ *                       and Constraints": restrictions on operators and
+ *                       complexity.
+ *   dse_sis_screen      "Software Description": candidates are evaluated
+ *                       against target data; SIS is the screening of SISSO
+ *                       ("Summary"); the workflow figure places screening
+ *                       between generation and sparse model selection.
+ *   dse_ls_refit        Eq. 1 (L0-constrained least squares, ||beta||_0 <= D)
+ *                       approximated greedily, OMP being one of the strategies
+ *                       named in "Software Description".
+ *
+ * Conventions (all calls):
+ *   - Every entry point returns a dse_status; 0 is success.  No C++ exception
+ *     crosses the ABI.  dse_last_error() gives a message for the last failure
+ *     of the calling thread.
+ *   - Buffers passed in are owned by the caller and are copied (or read in
+ *     place on the device) before the call returns or, for device buffers,
+ *     before the enqueued work completes; they must stay valid until then.
+ *   - Handles (dse_space, dse_result) are owned by the library and released
+ *     with the matching *_free call.
+ *   - Work is enqueued on the stream given in the descriptor (a cudaStream_t,
+ *     NULL for the legacy default stream).  Only dse_topk_fetch,
+ *     dse_result_stats, dse_space_counts and dse_ls_refit wait for the stream.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     computes returns DSE_ECUDA.
+ *
+ * Operator codes are also the slot order of a pair and the bit positions of
+ * op_mask: unary  0 x^2, 1 x^3, 2 x^-1, 3 sqrt, 4 exp, 5 log;
+ *          binary 6 a+b, 7 a-b, 8 a*b, 9 a/b, 10 b/a, 11 |a-b|.
+ * The "/" of the paper's operator lists is the two slots 9 and 10.
+ *
+ * Global candidate ids: ids [0, n_stored) are the stored features of rungs
+ * 0..max_rung-1 (rung by rung, each rung in generation order); id
+ * n_stored + p is flat index p of rung max_rung, whose unary block
+ * (feature-major, op-minor) precedes its binary block (pair (i, j), i from the
+ * newest stored rung, j < i, slot-minor).  Flat indices count every slot,
+ * valid or not.
+ */
+#ifndef DSE_H
+#define DSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dse_status;
+#define DSE_OK 0
+#define DSE_EINVAL (-1)    /* bad argument or descriptor */
+#define DSE_ENOMEM (-2)    /* device or host allocation failed */
+#define DSE_ECUDA (-3)     /* CUDA runtime error or no usable device */
+#define DSE_ERANGE (-4)    /* id or id range outside the candidate space */
+#define DSE_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define DSE_EOVERFLOW (-6) /* space, unit exponent or buffer beyond limits */
+
+enum {
+  DSE_OP_SQUARE = 0, DSE_OP_CUBE = 1, DSE_OP_INV = 2, DSE_OP_SQRT = 3, DSE_OP_EXP = 4,
+  DSE_OP_LOG = 5, DSE_OP_ADD = 6, DSE_OP_SUB = 7, DSE_OP_MUL = 8, DSE_OP_DIV = 9,
+  DSE_OP_RDIV = 10, DSE_OP_ABSDIFF = 11, DSE_OP_PRIMARY = 15
+};
+
+/* Why a candidate is excluded; tests are applied in this order. */
+enum {
+  DSE_VALID = 0,
+  DSE_R_UNIT = 1,       /* unit rule of the op fails                        */
+  DSE_R_COMPLEXITY = 2, /* more operator nodes than max_complexity          */
+  DSE_R_DOMAIN = 3,     /* log/sqrt/inverse/divisor/exp domain from summaries */
+  DSE_R_MAGNITUDE = 4,  /* a-priori bound on max|value| above fmax_max       */
+  DSE_R_REALISED = 5    /* non-finite value or degenerate (std <= f * rms)   */
+};
+
+enum { DSE_MODE_PER_TARGET = 0, DSE_MODE_AGGREGATED = 1 };
+
+enum {
+  DSE_PREC_FP32 = 0,   /* FP32 evaluation and sums with error bounds, FP64
+                          re-score of the top-k boundary                    */
+  DSE_PREC_FP64 = 1,   /* plain FP64 evaluation and sums (the comparator)   */
+  DSE_PREC_BF16X3 = 2, /* FP32 evaluation, BF16x3 tensor-core contraction   */
+  DSE_PREC_AUTO = 3    /* FP32 for few targets, BF16x3 for many             */
+};
+
+typedef struct dse_space dse_space;
+typedef struct dse_result dse_result;
+
+/* Feature space.  X holds n_primary rows of FP64 samples (row stride ld_x
+   elements).  With sample_idx (host array of n_samples column indices,
+   duplicates allowed, e.g. a bootstrap resample) the space is built on those
+   columns; without it on columns [0, n_samples).  units holds n_primary rows
+   of n_dims integer exponents (host).  Rungs 0..max_rung-1 are materialised in
+   FP64 (and FP32) on the device; rung max_rung is never stored. */
+typedef struct {
+  int64_t n_samples;            /* N >= 2                                     */
+  int64_t n_primary;            /* >= 1                                       */
+  int32_t n_dims;               /* unit dimensions, 0..8                      */
+  int32_t max_rung;             /* 1..3                                       */
+  const double *X;              /* [n_primary][ld_x], host or device          */
+  int64_t ld_x;                 /* >= n_samples, or >= max(sample_idx)+1      */
+  int32_t x_on_device;          /* 1: X is a device pointer                   */
+  int32_t reserved0;
+  const int64_t *sample_idx;    /* optional host gather list, NULL = identity */
+  const int32_t *units;         /* host [n_primary][n_dims]; NULL iff n_dims 0 */
+  uint32_t op_mask;             /* bit per op code                            */
+  int32_t max_complexity;       /* <= 0: no cap                               */
+  int32_t unit_check_addsub;    /* + - |a-b| need equal units                 */
+  int32_t explog_dimensionless; /* exp and log need dimensionless operands    */
+  double fmax_max;              /* magnitude limit, finite and > 0 (1e15)     */
+  double fmin_std_rel;          /* degeneracy limit (1e-8); < 0 disables       */
+  void *stream;                 /* cudaStream_t                               */
+} dse_space_desc;
+
+dse_status dse_build_space(const dse_space_desc *desc, dse_space **out);
+void dse_space_free(dse_space *space);
+
+/* Number of stored features (rungs 0..max_rung-1) and of all candidate ids. */
+dse_status dse_space_size(const dse_space *space, int64_t *n_stored, uint64_t *n_total);
+
+/* Per-rung counts.  slots = flat slots of the rung; reasons[6] = counts by
+   reason code (index 0 = valid).  For rungs below max_rung the counts are
+   exact after every test.  For rung max_rung the a-priori tests (unit,
+   complexity, domain, magnitude) are counted by a device pass over all slots;
+   reasons[0] is then the a-priori valid count and reasons[5] is -1 (the
+   realised test needs evaluation: see dse_result_stats). Synchronises. */
+dse_status dse_space_counts(dse_space *space, int32_t rung, uint64_t *slots, int64_t reasons[6]);
+
+/* Expression of a candidate: its rung, op code and operand ids (stored
+   feature ids; for a primary a = primary index, b = -1; for unary ops b = -1). */
+typedef struct {
+  int32_t rung, op;
+  int64_t a, b;
+} dse_expr;
+
+dse_status dse_decode(const dse_space *space, uint64_t id, dse_expr *out);
+/* Canonical text: x<p>, sq(A), cb(A), inv(A), sqrt(A), exp(A), log(A),
+   (A+B), (A-B), (A*B), (A/B), (B/A), |A-B| with A the higher-id operand. */
+dse_status dse_expr_string(const dse_space *space, uint64_t id, char *buf, int64_t len);
+
+/* SIS screen.  Y holds n_targets rows of N FP64 target (or residual) values,
+   row stride ld_y elements.  Candidates with global ids in [id_begin, id_end)
+   are screened (id_end = 0 means all).  PER_TARGET keeps k per target,
+   AGGREGATED keeps k by sqrt(mean_t score_t^2).  The top-k is exact: set and
+   order (score descending, id ascending) equal those of FP64 scores, apart
+   from candidates whose scores differ by less than the reported bounds. */
+typedef struct {
+  const double *Y;       /* [n_targets][ld_y], host or device               */
+  int64_t ld_y;          /* >= N                                            */
+  int32_t y_on_device;
+  int32_t n_targets;     /* >= 1                                            */
+  int64_t k;             /* >= 1                                            */
+  int32_t mode;          /* DSE_MODE_*                                      */
+  int32_t precision;     /* DSE_PREC_*                                      */
+  uint64_t id_begin, id_end;
+  void *stream;          /* cudaStream_t                                    */
+  int32_t flags;         /* DSE_FLAG_* bits                                 */
+  int32_t reserved0;
+} dse_screen_desc;
+
+/* dse_screen_desc.flags: record CUDA events around each kernel group so that
+   dse_result_stats reports their device time (kernel_ms). */
+#define DSE_FLAG_TIMING 1
+
+dse_status dse_sis_screen(dse_space *space, const dse_screen_desc *desc, dse_result **out);
+void dse_result_free(dse_result *result);
+
+/* Copies list `list` (a target index, or 0 in AGGREGATED mode) of a result:
+   up to cap entries of (id, score, err_bound) in rank order, host or device
+   pointers (checked with cudaPointerGetAttributes); n_out gets the list
+   length.  Any of idx/score/err_bound may be NULL.  Synchronises. */
+dse_status dse_topk_fetch(dse_result *result, int32_t list, uint64_t *idx, double *score,
+                          double *err_bound, int64_t cap, int64_t *n_out);
+
+typedef struct {
+  int64_t screened;        /* candidate ids in the screened range            */
+  int64_t reasons[6];      /* over the screened range, by reason code        */
+  int64_t evaluated;       /* candidates whose statistics were accumulated   */
+  int64_t buffered;        /* candidate-target entries that passed threshold */
+  int64_t escalated;       /* FP64 decisions of the realised test            */
+  int64_t rescored;        /* candidate-target pairs re-scored in FP64       */
+  int32_t reruns;          /* screens repeated after a buffer overflow       */
+  int32_t precision_used;  /* DSE_PREC_* actually run                        */
+  double max_err_bound;    /* largest bound among returned scores            */
+  int64_t valid_by_group[3];  /* valid candidates scored by the stored/unary,
+                                 product/quotient and sum/difference kernels */
+  double kernel_ms[4];     /* with DSE_FLAG_TIMING: device time of the
+                              stored/unary, product/quotient, sum/difference
+                              and selection kernel groups; else 0          */
+  int64_t kernel_launches; /* kernels this screen launched                   */
+} dse_stats;
+
+dse_status dse_result_stats(dse_result *result, dse_stats *out);
+
+/* One step of the residual loop: least squares with intercept of y (N FP64
+   values) on the columns of the `n_fixed` candidates `fixed` plus one
+   candidate from `cand` (n_cand ids), for every candidate; picks the one with
+   the smallest RMSE (ties: lower id) and writes its id, RMSE, coefficients
+   (intercept first, n_fixed + 2 values, host) and the residual y - fit
+   (N FP64 values; host or device).  Ids already in `fixed` are skipped.
+   All arithmetic FP64 on the device.  Synchronises. */
+typedef struct {
+  const double *y;        /* N values, host or device                       */
+  int32_t y_on_device;
+  int32_t n_fixed;        /* 0..3                                           */
+  const uint64_t *fixed;  /* host                                           */
+  const uint64_t *cand;   /* host or device (cand_on_device)                */
+  int64_t n_cand;
+  int32_t cand_on_device;
+  int32_t reserved0;
+  void *stream;
+} dse_refit_desc;
+
+dse_status dse_ls_refit(dse_space *space, const dse_refit_desc *desc, uint64_t *best_id,
+                        double *best_rmse, double *coefs, double *residual);
+
+/* Number of kernels the library has launched in this process so far. */
+int64_t dse_kernel_launches(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dse_last_error(void);
+
+/* Library version string. */
+const char *dse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSE_H */

@@ -1,0 +1,714 @@
+// api.cu -- the C ABI: argument checks, handles, and the orchestration of the
+// build, screen and selection kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dse_internal.cuh"
+#include "screen_kernels.cuh"
+#include "util.cuh"
+
+namespace dse {
+const char *last_error();
+dse_status build_space(const dse_space_desc *d, dse_space **out);
+dse_status space_release(dse_space *S);
+dse_status count_last_rung(dse_space *S, cudaStream_t st);
+FeatTable table_of(const dse_space *S);
+RungGeom make_geom(const dse_space *S, int r);
+dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, double *best_rmse, double *coefs,
+                      double *residual);
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+static dse_status check_device() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    set_error("no usable CUDA device (%s)", e != cudaSuccess ? cudaGetErrorString(e) : "0 devices");
+    return DSE_ECUDA;
+  }
+  return DSE_OK;
+}
+
+// ----------------------------------------------------------- tile lists
+
+// Pair tiles over the positions of `rows` grouped in consecutive classes
+// (class c = positions [cb[c], cb[c+1])): for every block of BI positions, the
+// blocks of BJ positions from the start of the first class touching it up to
+// the block itself.  Pairs are taken for position_i > position_j only.
+static void class_tiles(const std::vector<int64_t> &cb, int64_t npos, int BI, int BJ, int64_t i_from,
+                        std::vector<Tile> &out) {
+  // class start of every position
+  std::vector<int64_t> start(npos);
+  for (size_t c = 0; c + 1 < cb.size(); ++c)
+    for (int64_t p = cb[c]; p < cb[c + 1]; ++p) start[p] = cb[c];
+  for (int64_t i0 = i_from; i0 < npos; i0 += BI) {
+    int64_t i1 = std::min(i0 + BI, npos);
+    int64_t jlo = start[i0];
+    int64_t bj0 = jlo / BJ * BJ;
+    for (int64_t j0 = bj0; j0 < i1 - 1; j0 += BJ) {
+      Tile t;
+      t.ibase = (int32_t)i0;
+      t.ni = (int16_t)(i1 - i0);
+      t.jbase = (int32_t)j0;
+      t.nj = (int16_t)std::min<int64_t>(BJ, npos - j0);
+      t.pad = 0;
+      out.push_back(t);
+    }
+  }
+}
+
+// Triangle tiles over ids: i in [ia, ib] (the rows touched by the pair range),
+// j < i.
+static void triangle_tiles(int64_t ia, int64_t ib, int BI, int BJ, std::vector<Tile> &out) {
+  for (int64_t i0 = ia; i0 <= ib; i0 += BI) {
+    int64_t i1 = std::min(i0 + BI, ib + 1);
+    for (int64_t j0 = 0; j0 < i1 - 1; j0 += BJ) {
+      Tile t;
+      t.ibase = (int32_t)i0;
+      t.ni = (int16_t)(i1 - i0);
+      t.jbase = (int32_t)j0;
+      t.nj = (int16_t)std::min<int64_t>(BJ, i1 - 1 - j0);
+      t.pad = 0;
+      out.push_back(t);
+    }
+  }
+}
+
+// ------------------------------------------------------------- screening
+
+struct Scratch {
+  std::vector<std::pair<void **, size_t>> items;
+  template <typename T>
+  void add(T **p, size_t count) {
+    items.push_back({reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(T)});
+  }
+  dse_status alloc(void **base, size_t *bytes) {
+    size_t tot = 0;
+    for (auto &it : items) tot += (it.second + 255) / 256 * 256;
+    DSE_TRY(dmalloc(base, tot, "screen scratch"));
+    *bytes = tot;
+    size_t off = 0;
+    for (auto &it : items) {
+      *it.first = reinterpret_cast<char *>(*base) + off;
+      off += (it.second + 255) / 256 * 256;
+    }
+    return DSE_OK;
+  }
+};
+
+struct ScreenPlan {
+  int prec64, nt, passes;
+  int64_t cap;
+  std::vector<Tile> mul_tiles, add_tiles;
+  uint64_t id0, id1, p0, p1;     // stored ids and unary flat range
+  uint64_t add_total;            // additive slots of the binary block in range
+  float gamma_lane, gamma_pair;
+  int block_len;
+};
+
+static uint64_t count_slots_mod(uint64_t x, int nb, const std::vector<int> &posset) {
+  // number of p' in [0, x) with p' mod nb in posset
+  uint64_t full = x / (uint64_t)nb, rem = x % (uint64_t)nb;
+  uint64_t c = full * posset.size();
+  for (int p : posset)
+    if ((uint64_t)p < rem) ++c;
+  return c;
+}
+
+static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_tiles_mul, void *scr_tiles_add,
+                             ScreenArgs &A, SelectArgs &S, unsigned int *tile_ctr) {
+  dse_space *sp = R->space;
+  cudaStream_t st = R->stream;
+  const int sms = sm_count();
+  const int nl = R->n_lists;
+  DSE_CUDA(cudaMemsetAsync(A.B.count, 0, sizeof(unsigned) * nl, st));
+  DSE_CUDA(cudaMemsetAsync(A.B.hist, 0, sizeof(unsigned) * nl * kNumBins, st));
+  DSE_CUDA(cudaMemsetAsync(A.esc_count, 0, sizeof(unsigned), st));
+  DSE_CUDA(cudaMemsetAsync(A.stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
+  DSE_CUDA(cudaMemsetAsync(S.n_jobs, 0, sizeof(unsigned), st));
+  const int64_t launches0 = launches_so_far();
+  // optional device timing of each kernel group
+  const bool timing = (R->flags & DSE_FLAG_TIMING) != 0;
+  cudaEvent_t ev_open = nullptr;
+  int open_group = -1;
+  auto mark = [&](int group) -> dse_status {
+    if (!timing) return DSE_OK;
+    cudaEvent_t e;
+    DSE_CUDA(cudaEventCreate(&e));
+    DSE_CUDA(cudaEventRecord(e, st));
+    if (ev_open) R->timing.push_back({open_group, {ev_open, e}});
+    if (group >= 0) {
+      DSE_CUDA(cudaEventCreate(&ev_open));
+      DSE_CUDA(cudaEventRecord(ev_open, st));
+    } else {
+      ev_open = nullptr;
+    }
+    open_group = group;
+    return DSE_OK;
+  };
+  for (int pass = 0; pass < plan.passes; ++pass) {
+    A.t0 = pass * plan.nt;
+    A.T = std::min(plan.nt, R->T - A.t0);
+    A.first_pass = pass == 0;
+    DSE_TRY(mark(0));
+    launch_feature(plan.prec64, plan.nt, A, plan.id0, plan.id1, plan.p0, plan.p1, plan.gamma_lane, sms, st);
+    DSE_TRY(mark(1));
+    if (!plan.mul_tiles.empty()) {
+      A.tiles = reinterpret_cast<const Tile *>(scr_tiles_mul);
+      A.n_tiles = (int32_t)plan.mul_tiles.size();
+      A.rowid = sp->rowid_ident;
+      A.tile_counter = tile_ctr;
+      DSE_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(unsigned), st));
+      DSE_TRY(launch_pair(plan.prec64, KIND_MUL, plan.nt, A, plan.block_len, sms, st));
+    }
+    DSE_TRY(mark(2));
+    if (!plan.add_tiles.empty()) {
+      A.tiles = reinterpret_cast<const Tile *>(scr_tiles_add);
+      A.n_tiles = (int32_t)plan.add_tiles.size();
+      A.rowid = sp->class_rows;
+      A.tile_counter = tile_ctr + 1;
+      DSE_CUDA(cudaMemsetAsync(tile_ctr + 1, 0, sizeof(unsigned), st));
+      DSE_TRY(launch_pair(plan.prec64, KIND_ADD, plan.nt, A, plan.block_len, sms, st));
+    }
+  }
+  DSE_TRY(mark(3));
+  ScreenArgs E = A;
+  E.t0 = 0;
+  E.T = R->T;
+  launch_escalate(E, sms, st);
+  DSE_TRY(launch_select(S, E, sms, st));
+  DSE_TRY(mark(-1));
+  DSE_CUDA(cudaGetLastError());
+  R->launches += launches_so_far() - launches0;
+  return DSE_OK;
+}
+
+static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_result **out) {
+  cudaStream_t st = (cudaStream_t)d->stream;
+  const int64_t N = sp->N;
+  const uint64_t total = (uint64_t)sp->n + sp->geom.slots;
+  uint64_t id_begin = d->id_begin, id_end = d->id_end ? d->id_end : total;
+  if (id_begin > id_end || id_end > total) {
+    set_error("id range [%llu, %llu) outside [0, %llu)", (unsigned long long)id_begin,
+              (unsigned long long)id_end, (unsigned long long)total);
+    return DSE_ERANGE;
+  }
+  int prec = d->precision;
+  if (prec == DSE_PREC_AUTO || prec == DSE_PREC_BF16X3) prec = DSE_PREC_FP32;
+  ScreenPlan plan{};
+  plan.prec64 = prec == DSE_PREC_FP64;
+  plan.nt = d->n_targets == 1 ? 1 : 16;
+  plan.passes = (d->n_targets + plan.nt - 1) / plan.nt;
+  if (d->mode == DSE_MODE_AGGREGATED && plan.passes > 1) {
+    set_error("aggregated mode supports at most %d targets", plan.nt);
+    return DSE_EINVAL;
+  }
+  const int n_lists = d->mode == DSE_MODE_AGGREGATED ? 1 : d->n_targets;
+  plan.cap = std::max<int64_t>(8 * d->k, d->k + 131072);
+
+  // ranges of each candidate group
+  const uint64_t ns = (uint64_t)sp->n;
+  const RungGeom &g = sp->geom;
+  plan.id0 = std::min(id_begin, ns);
+  plan.id1 = std::min(id_end, ns);
+  auto clampp = [&](uint64_t id) { return id <= ns ? 0ull : std::min<uint64_t>(id - ns, g.slots); };
+  const uint64_t pb = clampp(id_begin), pe = clampp(id_end);
+  plan.p0 = std::min(pb, g.um);
+  plan.p1 = std::min(pe, g.um);
+  // binary block range in pair space
+  const uint64_t bb = std::max(pb, g.um), be = std::max(pe, g.um);
+  int BI = plan.nt == 1 ? 32 : 16, BJ = BI;
+  std::vector<int> addpos;
+  if (g.nb > 0 && be > bb) {
+    const uint64_t q0 = (bb - g.um) / g.nb, q1 = (be - g.um - 1) / g.nb;
+    uint64_t ia, ja, ib2, jb;
+    pair_from_index(q0 + g.tri_o, &ia, &ja);
+    pair_from_index(q1 + g.tri_o, &ib2, &jb);
+    bool any_mul = false, any_add = false;
+    for (int s = 0; s < g.nb; ++s) {
+      int op = g.bops[s];
+      if (op == DSE_OP_MUL || op == DSE_OP_DIV || op == DSE_OP_RDIV) any_mul = true;
+      else {
+        any_add = true;
+        addpos.push_back(s);
+      }
+    }
+    if (any_mul) triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.mul_tiles);
+    if (any_add) {
+      // positions within class_rows; rows of ids >= o only matter, but classes
+      // interleave old and new ids, so every block is visited.
+      class_tiles(sp->h_class_begin, sp->n, BI, BJ, 0, plan.add_tiles);
+      plan.add_total = count_slots_mod(be - g.um, g.nb, addpos) - count_slots_mod(bb - g.um, g.nb, addpos);
+    }
+  }
+  // accumulation error factors
+  const double u32 = 5.9604644775390625e-8, u64 = 1.1102230246251565e-16;
+  const double u = plan.prec64 ? u64 : u32;
+  int bl = (int)ceil(sqrt((double)N));
+  bl = std::max(16, (bl + 1) / 2 * 2);
+  plan.block_len = bl;
+  const double nlane = ceil((double)N / 32.0);
+  plan.gamma_lane = (float)((16.0 + ceil(nlane / 16.0) + 8.0) * u * 1.05);
+  plan.gamma_pair = plan.prec64 ? (float)((double)(N + 4) * u * 1.05)
+                                : (float)(((double)bl + ceil((double)N / bl) + 4.0) * u * 1.05);
+  if (plan.prec64) plan.gamma_lane = (float)((nlane + 8.0) * u * 1.05);
+
+  dse_result *R = new (std::nothrow) dse_result();
+  if (!R) {
+    set_error("out of host memory");
+    return DSE_ENOMEM;
+  }
+  R->space = sp;
+  R->n_lists = n_lists;
+  R->T = d->n_targets;
+  R->mode = d->mode;
+  R->precision = prec;
+  R->k = d->k;
+  R->id_begin = id_begin;
+  R->id_end = id_end;
+  R->stream = st;
+  R->ldy = (int32_t)sp->ld;
+
+  // one scratch allocation
+  Scratch sc;
+  ScreenArgs A{};
+  SelectArgs S{};
+  double *Yd = nullptr;
+  Tile *tmul = nullptr, *tadd = nullptr;
+  unsigned *tile_ctr = nullptr;
+  const int64_t cap = plan.cap;
+  const int64_t T = d->n_targets;
+  int64_t sort_cap = 1;
+  while (sort_cap < cap) sort_cap <<= 1;
+  if (!d->y_on_device) sc.add(&Yd, (size_t)T * d->ld_y);
+  sc.add(&R->y64, (size_t)T * R->ldy);
+  sc.add(&R->y32, (size_t)T * R->ldy);
+  sc.add(&R->ysum32, (size_t)T);
+  sc.add(&A.B.id, (size_t)n_lists * cap);
+  sc.add(&A.B.score, (size_t)n_lists * cap);
+  sc.add(&A.B.eps, (size_t)n_lists * cap);
+  sc.add(&A.B.count, (size_t)n_lists);
+  sc.add(&A.B.hist, (size_t)n_lists * kNumBins);
+  sc.add(&A.B.theta, (size_t)n_lists);
+  const int64_t esc_cap = 1 << 20;
+  sc.add(&A.esc_id, (size_t)esc_cap);
+  sc.add(&A.esc_count, 1);
+  sc.add(&R->stats, ST_COUNT);
+  sc.add(&R->err, 1);
+  sc.add(&S.r_id, (size_t)n_lists * cap);
+  sc.add(&S.r_s32, (size_t)n_lists * cap);
+  sc.add(&S.r_e32, (size_t)n_lists * cap);
+  sc.add(&S.r_s64, (size_t)n_lists * cap);
+  sc.add(&S.r_e64, (size_t)n_lists * cap);
+  sc.add(&S.r_need, (size_t)n_lists * cap);
+  sc.add(&S.r_count, (size_t)n_lists);
+  sc.add(&R->overflow, (size_t)n_lists);
+  sc.add(&S.job, (size_t)n_lists * cap);
+  sc.add(&S.job_list, (size_t)n_lists * cap);
+  sc.add(&S.n_jobs, 1);
+  sc.add(&R->out_id, (size_t)n_lists * d->k);
+  sc.add(&R->out_score, (size_t)n_lists * d->k);
+  sc.add(&R->out_eps, (size_t)n_lists * d->k);
+  sc.add(&R->out_n, (size_t)n_lists);
+  const bool big_sort = cap > 4096;
+  sc.add(&S.sort_key, big_sort ? (size_t)n_lists * sort_cap : 1);
+  sc.add(&S.sort_id, big_sort ? (size_t)n_lists * sort_cap : 1);
+  sc.add(&tmul, plan.mul_tiles.size());
+  sc.add(&tadd, plan.add_tiles.size());
+  sc.add(&tile_ctr, 2);
+  dse_status s = sc.alloc(&R->scratch, &R->scratch_bytes);
+  if (s != DSE_OK) {
+    delete R;
+    return s;
+  }
+  auto fail = [&](dse_status e) {
+    dfree(R->scratch);
+    delete R;
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  const double *Ysrc = d->Y;
+  if (!d->y_on_device) {
+    e = cudaMemcpyAsync(Yd, d->Y, sizeof(double) * T * d->ld_y, cudaMemcpyHostToDevice, st);
+    Ysrc = Yd;
+  }
+  if (!e && !plan.mul_tiles.empty())
+    e = cudaMemcpyAsync(tmul, plan.mul_tiles.data(), sizeof(Tile) * plan.mul_tiles.size(), cudaMemcpyHostToDevice,
+                        st);
+  if (!e && !plan.add_tiles.empty())
+    e = cudaMemcpyAsync(tadd, plan.add_tiles.data(), sizeof(Tile) * plan.add_tiles.size(), cudaMemcpyHostToDevice,
+                        st);
+  if (!e) e = cudaMemsetAsync(R->err, 0, sizeof(int), st);
+  if (!e) e = cudaMemsetAsync(A.B.theta, 0, sizeof(float) * n_lists, st);
+  if (e) return fail(cuda_status(e, "screen setup"));
+  launch_targets(Ysrc, d->ld_y, (int)T, N, R->ldy, R->y64, R->y32, R->ysum32, R->err, st);
+  R->launches = 1;
+  R->flags = d->flags;
+
+  A.F = table_of(sp);
+  A.G = g;
+  A.n_stored = sp->n;
+  A.id_begin = id_begin;
+  A.id_end = id_end;
+  A.N = (int32_t)N;
+  A.invN = 1.0 / (double)N;
+  A.ldy = R->ldy;
+  A.mode = d->mode;
+  A.n_lists = n_lists;
+  A.y32 = R->y32;
+  A.y64 = R->y64;
+  A.ysum32 = R->ysum32;
+  A.max_complexity = sp->max_complexity;
+  A.fmax64 = sp->fmax_max;
+  {
+    double f = sp->fmax_max;
+    float fd = (float)f, fu = (float)f;
+    if ((double)fd > f) fd = nextafterf(fd, 0.f);
+    if ((double)fu < f) fu = nextafterf(fu, INFINITY);
+    A.fmax32_dn = fd;
+    A.fmax32_up = fu;
+  }
+  A.fmin_std_rel = (float)sp->fmin_std_rel;
+  A.fmin_std_rel64 = sp->fmin_std_rel;
+  A.gamma = plan.gamma_pair;
+  A.u = (float)u;
+  A.k = d->k;
+  A.unit_check_addsub = sp->unit_check_addsub && sp->D > 0;
+  A.explog_dimensionless = sp->explog_dimensionless;
+  A.B.cap = cap;
+  A.esc_cap = esc_cap;
+  A.stats = R->stats;
+  A.err = R->err;
+  for (int c = 0; c < 6; ++c) A.slot_pos[c] = -1;
+  for (int s2 = 0; s2 < g.nb; ++s2) A.slot_pos[g.bops[s2] - 6] = s2;
+
+  S.B = A.B;
+  S.n_lists = n_lists;
+  S.k = d->k;
+  S.all64 = plan.prec64;
+  S.overflow = R->overflow;
+  S.out_id = R->out_id;
+  S.out_score = R->out_score;
+  S.out_eps = R->out_eps;
+  S.out_n = R->out_n;
+  S.sort_cap = big_sort ? sort_cap : 1;
+  S.stats = R->stats;
+
+  s = run_screen(R, plan, tmul, tadd, A, S, tile_ctr);
+  if (s != DSE_OK) return fail(s);
+
+  // keep what a re-run after a buffer overflow needs
+  R->host_stats = dse_stats{};
+  R->host_stats.screened = (int64_t)(id_end - id_begin);
+  R->host_stats.precision_used = prec;
+  struct Keep {
+    ScreenPlan plan;
+    ScreenArgs A;
+    SelectArgs S;
+    Tile *tmul, *tadd;
+    unsigned *tile_ctr;
+  };
+  Keep *keep = new (std::nothrow) Keep{plan, A, S, tmul, tadd, tile_ctr};
+  if (!keep) return fail(DSE_ENOMEM);
+  R->keep = keep;
+  R->keep_free = [](void *p) { delete reinterpret_cast<Keep *>(p); };
+  R->rerun = [](dse_result *r) -> dse_status {
+    Keep *k = reinterpret_cast<Keep *>(r->keep);
+    return run_screen(r, k->plan, k->tmul, k->tadd, k->A, k->S, k->tile_ctr);
+  };
+  R->add_total = plan.add_total;
+  R->buf_count = A.B.count;
+  *out = R;
+  return DSE_OK;
+}
+
+// Wait for a result, re-running the screen while any list overflowed its
+// buffer (the thresholds reached so far stay valid lower bounds).
+static dse_status finish(dse_result *R) {
+  if (R->fetched) return DSE_OK;
+  cudaStream_t st = R->stream;
+  for (int attempt = 0;; ++attempt) {
+    std::vector<unsigned> ov(R->n_lists);
+    unsigned long long hs[ST_COUNT];
+    int herr = 0;
+    DSE_CUDA(cudaMemcpyAsync(ov.data(), R->overflow, sizeof(unsigned) * R->n_lists, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(hs, R->stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(&herr, R->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaStreamSynchronize(st));
+    if (herr) {
+      set_error(herr == DSE_ETIMEOUT ? "a bounded device wait timed out" : "invalid target (zero variance or not finite)");
+      return herr;
+    }
+    if (hs[ST_ESC_OVERFLOW]) {
+      set_error("escalation list overflow");
+      return DSE_EOVERFLOW;
+    }
+    bool any = false;
+    for (unsigned v : ov) any |= v != 0;
+    if (!any || attempt >= 8) {
+      if (any) {
+        set_error("candidate buffer overflow persisted");
+        return DSE_EOVERFLOW;
+      }
+      dse_stats &o = R->host_stats;
+      for (int c = 0; c < 6; ++c) o.reasons[c] = (int64_t)hs[ST_REASON0 + c];
+      o.reasons[DSE_R_UNIT] += (int64_t)R->add_total - (int64_t)hs[ST_ADD_SEEN];
+      o.evaluated = (int64_t)hs[ST_EVALUATED];
+      for (int g = 0; g < 3; ++g) o.valid_by_group[g] = (int64_t)hs[ST_VALID_G0 + g];
+      for (int g = 0; g < 4; ++g) o.kernel_ms[g] = 0.0;
+      for (auto &t : R->timing) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.second.first, t.second.second) == cudaSuccess && t.first >= 0 &&
+            t.first < 4)
+          o.kernel_ms[t.first] += ms;
+      }
+      o.kernel_launches = R->launches;
+      {
+        std::vector<unsigned> bc(R->n_lists);
+        DSE_CUDA(cudaMemcpy(bc.data(), R->buf_count, sizeof(unsigned) * R->n_lists, cudaMemcpyDeviceToHost));
+        o.buffered = 0;
+        for (unsigned v : bc) o.buffered += v;
+      }
+      o.escalated = (int64_t)hs[ST_ESCALATED];
+      o.rescored = (int64_t)hs[ST_RESCORED];
+      o.reruns = R->reruns;
+      std::vector<int64_t> nout(R->n_lists);
+      DSE_CUDA(cudaMemcpy(nout.data(), R->out_n, 8 * R->n_lists, cudaMemcpyDeviceToHost));
+      double mx = 0;
+      for (int l = 0; l < R->n_lists; ++l) {
+        std::vector<double> eps(nout[l]);
+        if (nout[l])
+          DSE_CUDA(cudaMemcpy(eps.data(), R->out_eps + (size_t)l * R->k, 8 * nout[l], cudaMemcpyDeviceToHost));
+        for (double x : eps) mx = std::max(mx, x);
+      }
+      o.max_err_bound = mx;
+      R->fetched = true;
+      return DSE_OK;
+    }
+    ++R->reruns;
+    DSE_TRY(R->rerun(R));
+  }
+}
+
+}  // namespace dse
+
+using namespace dse;
+
+// ================================================================ C ABI
+
+extern "C" {
+
+const char *dse_last_error(void) { return dse::last_error(); }
+const char *dse_version(void) { return "dse 0.1 (sm_103a)"; }
+int64_t dse_kernel_launches(void) { return launches_so_far(); }
+
+dse_status dse_build_space(const dse_space_desc *d, dse_space **out) {
+  clear_error();
+  if (!d || !out) {
+    set_error("null argument");
+    return DSE_EINVAL;
+  }
+  *out = nullptr;
+  if (d->n_samples < 2 || d->n_samples > (1 << 30) || d->n_primary < 1 || d->n_primary > (1 << 24) ||
+      d->n_dims < 0 || d->n_dims > kMaxDims || d->max_rung < 1 || d->max_rung > kMaxRung || !d->X ||
+      (d->n_dims > 0 && !d->units) || (d->op_mask & ~0xFFFu) || d->op_mask == 0 || !(d->fmax_max > 0) ||
+      !isfinite(d->fmax_max) || isnan(d->fmin_std_rel)) {
+    set_error("invalid space descriptor");
+    return DSE_EINVAL;
+  }
+  if (d->sample_idx) {
+    for (int64_t s = 0; s < d->n_samples; ++s)
+      if (d->sample_idx[s] < 0 || d->sample_idx[s] >= d->ld_x) {
+        set_error("sample_idx[%lld] out of range", (long long)s);
+        return DSE_EINVAL;
+      }
+  } else if (d->ld_x < d->n_samples) {
+    set_error("ld_x < n_samples");
+    return DSE_EINVAL;
+  }
+  DSE_TRY(check_device());
+  return build_space(d, out);
+}
+
+void dse_space_free(dse_space *s) { space_release(s); }
+
+dse_status dse_space_size(const dse_space *s, int64_t *n_stored, uint64_t *n_total) {
+  clear_error();
+  if (!s) {
+    set_error("null space");
+    return DSE_EINVAL;
+  }
+  if (n_stored) *n_stored = s->n;
+  if (n_total) *n_total = (uint64_t)s->n + s->geom.slots;
+  return DSE_OK;
+}
+
+dse_status dse_space_counts(dse_space *s, int32_t rung, uint64_t *slots, int64_t reasons[6]) {
+  clear_error();
+  if (!s || rung < 0 || rung > s->max_rung) {
+    set_error("bad space or rung");
+    return DSE_EINVAL;
+  }
+  if (rung == s->max_rung) DSE_TRY(count_last_rung(s, 0));
+  if (slots) *slots = s->slots[rung];
+  if (reasons)
+    for (int c = 0; c < 6; ++c) reasons[c] = s->reasons[rung][c];
+  return DSE_OK;
+}
+
+dse_status dse_decode(const dse_space *s, uint64_t id, dse_expr *out) {
+  clear_error();
+  if (!s || !out) {
+    set_error("null argument");
+    return DSE_EINVAL;
+  }
+  if (id < (uint64_t)s->n) {
+    out->rung = s->h_rung[id];
+    out->op = s->h_op[id];
+    out->a = s->h_ca[id];
+    out->b = s->h_cb[id];
+    return DSE_OK;
+  }
+  int op;
+  int64_t a, b;
+  if (!decode_flat(s->geom, id - (uint64_t)s->n, &op, &a, &b)) {
+    set_error("id %llu outside the space", (unsigned long long)id);
+    return DSE_ERANGE;
+  }
+  out->rung = s->max_rung;
+  out->op = op;
+  out->a = a;
+  out->b = b;
+  return DSE_OK;
+}
+
+static std::string expr_text(const dse_space *s, int op, int64_t a, int64_t b);
+static std::string feat_text(const dse_space *s, int64_t f) {
+  return expr_text(s, s->h_op[f], s->h_ca[f], s->h_cb[f]);
+}
+static std::string expr_text(const dse_space *s, int op, int64_t a, int64_t b) {
+  if (op == DSE_OP_PRIMARY) return "x" + std::to_string(a);
+  std::string A = feat_text(s, a);
+  std::string B = b >= 0 ? feat_text(s, b) : std::string();
+  switch (op) {
+    case DSE_OP_SQUARE: return "sq(" + A + ")";
+    case DSE_OP_CUBE: return "cb(" + A + ")";
+    case DSE_OP_INV: return "inv(" + A + ")";
+    case DSE_OP_SQRT: return "sqrt(" + A + ")";
+    case DSE_OP_EXP: return "exp(" + A + ")";
+    case DSE_OP_LOG: return "log(" + A + ")";
+    case DSE_OP_ADD: return "(" + A + "+" + B + ")";
+    case DSE_OP_SUB: return "(" + A + "-" + B + ")";
+    case DSE_OP_MUL: return "(" + A + "*" + B + ")";
+    case DSE_OP_DIV: return "(" + A + "/" + B + ")";
+    case DSE_OP_RDIV: return "(" + B + "/" + A + ")";
+    case DSE_OP_ABSDIFF: return "|" + A + "-" + B + "|";
+    default: return "?";
+  }
+}
+
+dse_status dse_expr_string(const dse_space *s, uint64_t id, char *buf, int64_t len) {
+  dse_expr e;
+  DSE_TRY(dse_decode(s, id, &e));
+  if (!buf || len < 1) {
+    set_error("null buffer");
+    return DSE_EINVAL;
+  }
+  std::string t = id < (uint64_t)s->n ? feat_text(s, (int64_t)id) : expr_text(s, e.op, e.a, e.b);
+  if ((int64_t)t.size() + 1 > len) {
+    set_error("buffer too small (%zu needed)", t.size() + 1);
+    return DSE_EOVERFLOW;
+  }
+  memcpy(buf, t.c_str(), t.size() + 1);
+  return DSE_OK;
+}
+
+dse_status dse_sis_screen(dse_space *s, const dse_screen_desc *d, dse_result **out) {
+  clear_error();
+  if (!s || !d || !out) {
+    set_error("null argument");
+    return DSE_EINVAL;
+  }
+  *out = nullptr;
+  if (!d->Y || d->n_targets < 1 || d->n_targets > 4096 || d->k < 1 || d->k > (1 << 24) || d->ld_y < s->N ||
+      (d->mode != DSE_MODE_PER_TARGET && d->mode != DSE_MODE_AGGREGATED) || d->precision < 0 ||
+      d->precision > DSE_PREC_AUTO) {
+    set_error("invalid screen descriptor");
+    return DSE_EINVAL;
+  }
+  DSE_TRY(check_device());
+  return screen_impl(s, d, out);
+}
+
+void dse_result_free(dse_result *r) {
+  if (!r) return;
+  if (r->stream) cudaStreamSynchronize(r->stream);
+  else cudaDeviceSynchronize();
+  dfree(r->scratch);
+  if (r->keep && r->keep_free) r->keep_free(r->keep);
+  for (auto &t : r->timing) {
+    cudaEventDestroy(t.second.first);
+    cudaEventDestroy(t.second.second);
+  }
+  delete r;
+}
+
+dse_status dse_topk_fetch(dse_result *r, int32_t list, uint64_t *idx, double *score, double *err_bound, int64_t cap,
+                          int64_t *n_out) {
+  clear_error();
+  if (!r || list < 0 || list >= r->n_lists || cap < 0) {
+    set_error("bad result or list");
+    return DSE_EINVAL;
+  }
+  DSE_TRY(finish(r));
+  int64_t n = 0;
+  DSE_CUDA(cudaMemcpy(&n, r->out_n + list, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  if (n_out) *n_out = n;
+  int64_t m = std::min(n, cap);
+  if (m == 0) return DSE_OK;
+  const size_t off = (size_t)list * r->k;
+  auto cp = [&](void *dst, const void *src, size_t bytes) {
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyDefault);
+  };
+  if (idx) DSE_CUDA(cp(idx, r->out_id + off, 8 * m));
+  if (score) DSE_CUDA(cp(score, r->out_score + off, 8 * m));
+  if (err_bound) DSE_CUDA(cp(err_bound, r->out_eps + off, 8 * m));
+  return DSE_OK;
+}
+
+dse_status dse_result_stats(dse_result *r, dse_stats *out) {
+  clear_error();
+  if (!r || !out) {
+    set_error("null argument");
+    return DSE_EINVAL;
+  }
+  DSE_TRY(finish(r));
+  *out = r->host_stats;
+  return DSE_OK;
+}
+
+dse_status dse_ls_refit(dse_space *s, const dse_refit_desc *d, uint64_t *best_id, double *best_rmse, double *coefs,
+                        double *residual) {
+  clear_error();
+  if (!s || !d || !d->y || d->n_fixed < 0 || d->n_fixed > 3 || (d->n_fixed > 0 && !d->fixed) || !d->cand ||
+      d->n_cand < 1 || !best_id || !best_rmse) {
+    set_error("invalid refit descriptor");
+    return DSE_EINVAL;
+  }
+  DSE_TRY(check_device());
+  return refit_impl(s, d, best_id, best_rmse, coefs, residual);
+}
+
+}  // extern "C"

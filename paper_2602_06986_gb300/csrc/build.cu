@@ -1,0 +1,659 @@
+// build.cu -- dse_build_space: materialise rungs 0..max_rung-1 on the device.
+//
+// Follows the iterative generation of "Software Description" and the early
+// exclusion of dimensionally invalid expressions of "Physics-Informed
+// Constraints": rung r is generated from Phi_{r-1} (unary block over the
+// newest rung, then every pair (i, j) with i in the newest rung and j < i, one
+// slot per enabled binary op), every slot is tested (unit, complexity,
+// domain, magnitude on FP64 summaries, then the realised test on the FP64
+// values) and the valid ones are appended in flat order.  Everything runs in
+// FP64 on the device; the host only sizes arrays between the passes.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+
+#include "dse_internal.cuh"
+#include "eval64.cuh"
+#include "util.cuh"
+
+namespace dse {
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void k_gather_rows(const double *X, int64_t ldx, const int64_t *idx, int64_t n0, int64_t N, int64_t ld,
+                              double *out) {
+  int64_t total = n0 * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t f = e / ld, s = e % ld;
+    double v = 0.0;
+    if (s < N) v = X[f * ldx + (idx ? idx[s] : s)];
+    out[e] = v;
+  }
+}
+
+// Summaries of stored rows [f0, f1): one warp per row.  Also the realised test
+// (finite, std > fmin * rms) into ok[f - f0] when ok != nullptr.
+__global__ void k_summaries(double *v64, int64_t ld, int64_t N, int64_t f0, int64_t f1, double *mean64,
+                            double *rmean64, double *min64, double *max64, double *minabs64, double *maxabs64,
+                            double *minabsnz64, double fmin_std_rel, uint8_t *ok) {
+  int lane = threadIdx.x & 31;
+  int64_t f = f0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (f >= f1) return;
+  const double *x = v64 + f * ld;
+  double mn = INFINITY, mx = -INFINITY, mna = INFINITY, mxa = 0.0, mnz = INFINITY, sum = 0.0;
+  int fin = 1;
+  for (int64_t s = lane; s < N; s += 32) {
+    double v = x[s];
+    if (!isfinite(v)) fin = 0;
+    mn = fmin(mn, v);
+    mx = fmax(mx, v);
+    double a = fabs(v);
+    mna = fmin(mna, a);
+    mxa = fmax(mxa, a);
+    if (a > 0.0) mnz = fmin(mnz, a);
+    sum = __dadd_rn(sum, v);
+  }
+  fin = !__any_sync(0xffffffffu, !fin);
+  mn = warp_min64(mn);
+  mx = warp_max64(mx);
+  mna = warp_min64(mna);
+  mxa = warp_max64(mxa);
+  mnz = warp_min64(mnz);
+  sum = warp_sum64(sum);
+  double mean = sum / (double)N;
+  double sxx = 0.0, s2 = 0.0, rs = 0.0;
+  for (int64_t s = lane; s < N; s += 32) {
+    double v = x[s];
+    double d = __dsub_rn(v, mean);
+    sxx = __fma_rn(d, d, sxx);
+    s2 = __fma_rn(v, v, s2);
+    if (mna > 0.0) rs = __dadd_rn(rs, __drcp_rn(v));
+  }
+  sxx = warp_sum64(sxx);
+  s2 = warp_sum64(s2);
+  rs = warp_sum64(rs);
+  if (lane == 0) {
+    mean64[f] = mean;
+    rmean64[f] = (mna > 0.0) ? rs / (double)N : 0.0;
+    min64[f] = mn;
+    max64[f] = mx;
+    minabs64[f] = mna;
+    maxabs64[f] = mxa;
+    minabsnz64[f] = mnz;
+    if (ok) {
+      int good = fin;
+      if (good && fmin_std_rel >= 0.0) {
+        double sd = __dsqrt_rn(sxx / (double)N), rms = __dsqrt_rn(s2 / (double)N);
+        good = sd > fmin_std_rel * rms;
+      }
+      ok[f - f0] = (uint8_t)(good ? 1 : 0);
+    }
+  }
+}
+
+// A-priori reason of every flat slot of rung r.
+__global__ void k_apriori_rung(FeatTable F, RungGeom g, AprioriParams P, uint8_t *why, int *bad) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.slots;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    int op;
+    int64_t a, b;
+    decode_flat(g, p, &op, &a, &b);
+    int32_t u[kMaxDims], cx;
+    int b_ = 0;
+    int r = apriori64(F, P, op, a, b, u, &cx, &b_);
+    if (b_) atomicOr(bad, b_);
+    why[p] = (uint8_t)r;
+  }
+}
+
+// Realised test of listed slots (FP64 values, not stored): warp per slot.
+__global__ void k_realised_rung(FeatTable F, RungGeom g, const uint64_t *list, uint64_t n_list, double fmin_std_rel,
+                                uint8_t *why) {
+  int lane = threadIdx.x & 31;
+  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (w >= n_list) return;
+  int op;
+  int64_t a, b;
+  decode_flat(g, list[w], &op, &a, &b);
+  const double *xa = F.v64 + a * F.ld;
+  const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
+  const int64_t N = F.N;
+  int fin = 1;
+  double sum = 0.0;
+  for (int64_t s = lane; s < N; s += 32) {
+    double v = eval_op64(op, xa[s], xb[s]);
+    if (!isfinite(v)) fin = 0;
+    sum = __dadd_rn(sum, v);
+  }
+  fin = !__any_sync(0xffffffffu, !fin);
+  sum = warp_sum64(sum);
+  double mean = sum / (double)N, sxx = 0.0, s2 = 0.0;
+  for (int64_t s = lane; s < N; s += 32) {
+    double v = eval_op64(op, xa[s], xb[s]);
+    double d = __dsub_rn(v, mean);
+    sxx = __fma_rn(d, d, sxx);
+    s2 = __fma_rn(v, v, s2);
+  }
+  sxx = warp_sum64(sxx);
+  s2 = warp_sum64(s2);
+  if (lane == 0) {
+    int good = fin;
+    if (good && fmin_std_rel >= 0.0) good = __dsqrt_rn(sxx / (double)N) > fmin_std_rel * __dsqrt_rn(s2 / (double)N);
+    why[w] = (uint8_t)(good ? DSE_VALID : DSE_R_REALISED);
+  }
+}
+
+// Store listed slots as new features [dst0, dst0 + n_list): warp per slot.
+__global__ void k_materialise(FeatTable F, RungGeom g, AprioriParams P, const uint64_t *list, uint64_t n_list,
+                              int64_t dst0, double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
+                              int32_t *cplx_out, int32_t *units_out) {
+  int lane = threadIdx.x & 31;
+  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (w >= n_list) return;
+  int op;
+  int64_t a, b;
+  decode_flat(g, list[w], &op, &a, &b);
+  const double *xa = F.v64 + a * F.ld;
+  const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
+  int64_t f = dst0 + (int64_t)w;
+  double *out = v64 + f * F.ld;
+  for (int64_t s = lane; s < F.ld; s += 32) out[s] = (s < F.N) ? eval_op64(op, xa[s], xb[s]) : 0.0;
+  if (lane == 0) {
+    int32_t u[kMaxDims] = {0, 0, 0, 0, 0, 0, 0, 0}, cx = 0;
+    int bad = 0;
+    apriori64(F, P, op, a, b, u, &cx, &bad);
+    op_out[f] = op;
+    ca_out[f] = a;
+    cb_out[f] = b;
+    cplx_out[f] = cx;
+    for (int d = 0; d < kMaxDims; ++d) units_out[f * kMaxDims + d] = u[d];
+  }
+}
+
+// FP32 rows and per-feature helpers of every stored feature.
+__global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const double *v64, float *v32,
+                            const double *mean64, const double *rmean64, const double *min64, const double *max64,
+                            const double *minabs64, const double *maxabs64, const double *minabsnz64,
+                            const int32_t *units, double exp_arg_max, float4 *fa, float2 *fr, uint32_t *flags,
+                            uint64_t *ukey) {
+  int64_t total = n * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    v32[e] = (e % ld < N) ? __double2float_rn(v64[e]) : 0.0f;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+    double M = maxabs64[f], m = minabs64[f];
+    fa[f] = make_float4(__double2float_rn(mean64[f]), __double2float_rn(rmean64[f]), __double2float_ru(M),
+                        __double2float_rd(M));
+    if (m > 0.0)
+      fr[f] = make_float2(__double2float_ru(__ddiv_ru(1.0, m)), __double2float_rd(__ddiv_rd(1.0, m)));
+    else
+      fr[f] = make_float2(0.0f, 0.0f);
+    uint32_t fl = 0;
+    if (m > 0.0) fl |= F_MINABS_POS;
+    if (min64[f] > 0.0) fl |= F_MIN_POS;
+    if (min64[f] >= 0.0) fl |= F_MIN_NONNEG;
+    if (max64[f] <= 80.0) fl |= F_EXP_DOMAIN;
+    if (max64[f] <= exp_arg_max) fl |= F_EXP_MAG;
+    const double lo = 8.673617379884035e-19, hi = 1.152921504606847e18;  // 2^-60, 2^60
+    double nz = minabsnz64[f];
+    if (M <= hi && (!(nz < INFINITY) || nz >= lo)) fl |= F_FP32_SAFE;
+    uint64_t k0 = 0, k1 = 0;
+    int dimless = 1;
+    for (int d = 0; d < kMaxDims; ++d) {
+      int32_t x = d < D ? units[f * kMaxDims + d] : 0;
+      if (x) dimless = 0;
+      uint64_t bits = (uint64_t)(uint16_t)(int16_t)x;
+      if (d < 4) k0 |= bits << (16 * d);
+      else k1 |= bits << (16 * (d - 4));
+    }
+    if (dimless) fl |= F_DIMLESS;
+    flags[f] = fl;
+    ukey[2 * f] = k0;
+    ukey[2 * f + 1] = k1;
+  }
+}
+
+// ------------------------------------------------------------- host side
+
+static unsigned grid_for(uint64_t work, int threads, unsigned cap = 65535u * 16) {
+  uint64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+struct TableArrays {
+  double *v64 = nullptr, *mean64 = nullptr, *rmean64 = nullptr, *min64 = nullptr, *max64 = nullptr,
+         *minabs64 = nullptr, *maxabs64 = nullptr, *minabsnz64 = nullptr;
+  int32_t *op = nullptr, *cplx = nullptr, *units = nullptr;
+  int64_t *ca = nullptr, *cb = nullptr;
+  int64_t cap = 0;
+  void release() {
+    dfree(v64); dfree(mean64); dfree(rmean64); dfree(min64); dfree(max64); dfree(minabs64); dfree(maxabs64);
+    dfree(minabsnz64); dfree(op); dfree(cplx); dfree(units); dfree(ca); dfree(cb);
+    *this = TableArrays();
+  }
+};
+
+static dse_status table_alloc(TableArrays &t, int64_t cap, int64_t ld) {
+  t.cap = cap;
+  DSE_TRY(dalloc(&t.v64, (size_t)cap * ld, "FP64 feature rows"));
+  DSE_TRY(dalloc(&t.mean64, cap, "summaries"));
+  DSE_TRY(dalloc(&t.rmean64, cap, "summaries"));
+  DSE_TRY(dalloc(&t.min64, cap, "summaries"));
+  DSE_TRY(dalloc(&t.max64, cap, "summaries"));
+  DSE_TRY(dalloc(&t.minabs64, cap, "summaries"));
+  DSE_TRY(dalloc(&t.maxabs64, cap, "summaries"));
+  DSE_TRY(dalloc(&t.minabsnz64, cap, "summaries"));
+  DSE_TRY(dalloc(&t.op, cap, "table"));
+  DSE_TRY(dalloc(&t.cplx, cap, "table"));
+  DSE_TRY(dalloc(&t.units, (size_t)cap * kMaxDims, "table"));
+  DSE_TRY(dalloc(&t.ca, cap, "table"));
+  DSE_TRY(dalloc(&t.cb, cap, "table"));
+  return DSE_OK;
+}
+
+static dse_status table_copy(TableArrays &dst, const TableArrays &src, int64_t n, int64_t ld, cudaStream_t s) {
+  auto cp = [&](void *d, const void *x, size_t bytes) {
+    return cudaMemcpyAsync(d, x, bytes, cudaMemcpyDeviceToDevice, s);
+  };
+  cudaError_t e = cudaSuccess;
+  if (n == 0) return DSE_OK;
+  e = cp(dst.v64, src.v64, sizeof(double) * n * ld);
+  if (!e) e = cp(dst.mean64, src.mean64, 8 * n);
+  if (!e) e = cp(dst.rmean64, src.rmean64, 8 * n);
+  if (!e) e = cp(dst.min64, src.min64, 8 * n);
+  if (!e) e = cp(dst.max64, src.max64, 8 * n);
+  if (!e) e = cp(dst.minabs64, src.minabs64, 8 * n);
+  if (!e) e = cp(dst.maxabs64, src.maxabs64, 8 * n);
+  if (!e) e = cp(dst.minabsnz64, src.minabsnz64, 8 * n);
+  if (!e) e = cp(dst.op, src.op, 4 * n);
+  if (!e) e = cp(dst.cplx, src.cplx, 4 * n);
+  if (!e) e = cp(dst.units, src.units, 4 * n * kMaxDims);
+  if (!e) e = cp(dst.ca, src.ca, 8 * n);
+  if (!e) e = cp(dst.cb, src.cb, 8 * n);
+  if (e) return cuda_status(e, "table copy");
+  return DSE_OK;
+}
+
+static FeatTable view(const TableArrays &t, int64_t n, int64_t N, int64_t ld) {
+  FeatTable F{};
+  F.n = n;
+  F.N = N;
+  F.ld = ld;
+  F.v64 = t.v64;
+  F.mean64 = t.mean64;
+  F.rmean64 = t.rmean64;
+  F.min64 = t.min64;
+  F.max64 = t.max64;
+  F.minabs64 = t.minabs64;
+  F.maxabs64 = t.maxabs64;
+  F.cplx = t.cplx;
+  F.op = t.op;
+  F.ca = t.ca;
+  F.cb = t.cb;
+  F.units = t.units;
+  return F;
+}
+
+RungGeom make_geom(const dse_space *S, int r) {
+  RungGeom g{};
+  g.o = S->rung_begin[r - 1];
+  g.n = S->rung_begin[r];
+  g.nu = g.nb = 0;
+  for (int c = 0; c <= 5; ++c)
+    if (S->op_mask & (1u << c)) g.uops[g.nu++] = c;
+  for (int c = 6; c <= 11; ++c)
+    if (S->op_mask & (1u << c)) g.bops[g.nb++] = c;
+  uint64_t m = (uint64_t)(g.n - g.o), o = (uint64_t)g.o;
+  g.um = (uint64_t)g.nu * m;
+  uint64_t pairs = m ? tri(m) + m * o : 0;
+  g.slots = g.um + (uint64_t)g.nb * pairs;
+  g.tri_o = o ? tri(o) : 0;
+  return g;
+}
+
+dse_status space_release(dse_space *S);
+
+static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
+  cudaStream_t st = (cudaStream_t)d->stream;
+  const int64_t N = d->n_samples, n0 = d->n_primary;
+  const int64_t ld = (N + 3) / 4 * 4;
+  S->N = N;
+  S->ld = ld;
+  S->n_primary = n0;
+  S->D = d->n_dims;
+  S->max_rung = d->max_rung;
+  S->op_mask = d->op_mask;
+  S->max_complexity = d->max_complexity;
+  S->unit_check_addsub = d->unit_check_addsub;
+  S->explog_dimensionless = d->explog_dimensionless;
+  S->fmax_max = d->fmax_max;
+  S->fmin_std_rel = d->fmin_std_rel;
+  S->exp_arg_max = log(d->fmax_max);
+  DSE_CUDA(cudaGetDevice(&S->device));
+
+  AprioriParams P{S->D, S->unit_check_addsub, S->explog_dimensionless, S->max_complexity, S->fmax_max,
+                  S->exp_arg_max};
+
+  // --- rung 0: gather the primaries on the device
+  int64_t ldx = d->ld_x;
+  const double *Xd = d->X;
+  double *Xtmp = nullptr;
+  int64_t *idx_d = nullptr;
+  if (!d->x_on_device) {
+    DSE_TRY(dalloc(&Xtmp, (size_t)n0 * ldx, "primary upload"));
+    DSE_CUDA(cudaMemcpyAsync(Xtmp, d->X, sizeof(double) * n0 * ldx, cudaMemcpyHostToDevice, st));
+    Xd = Xtmp;
+  }
+  if (d->sample_idx) {
+    DSE_TRY(dalloc(&idx_d, N, "sample gather list"));
+    DSE_CUDA(cudaMemcpyAsync(idx_d, d->sample_idx, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
+  }
+  TableArrays T0;
+  DSE_TRY(table_alloc(T0, n0, ld));
+  k_gather_rows<<<grid_for(n0 * ld, 256), 256, 0, st>>>(Xd, ldx, idx_d, n0, N, ld, T0.v64);
+  uint8_t *ok = nullptr;
+  DSE_TRY(dalloc(&ok, n0, "primary flags"));
+  k_summaries<<<grid_for(n0 * 32, 256), 256, 0, st>>>(T0.v64, ld, N, 0, n0, T0.mean64, T0.rmean64, T0.min64,
+                                                       T0.max64, T0.minabs64, T0.maxabs64, T0.minabsnz64,
+                                                       S->fmin_std_rel, ok);
+  std::vector<uint8_t> hok(n0);
+  DSE_CUDA(cudaMemcpyAsync(hok.data(), ok, n0, cudaMemcpyDeviceToHost, st));
+  DSE_CUDA(cudaStreamSynchronize(st));
+  dfree(ok);
+  dfree(Xtmp);
+  dfree(idx_d);
+
+  // keep the primaries that pass the realised test, in input order
+  std::vector<int64_t> keep;
+  for (int64_t p = 0; p < n0; ++p)
+    if (hok[p]) keep.push_back(p);
+  const int64_t nk = (int64_t)keep.size();
+  S->slots[0] = (uint64_t)n0;
+  memset(S->reasons, 0, sizeof(S->reasons));
+  S->reasons[0][DSE_VALID] = nk;
+  S->reasons[0][DSE_R_REALISED] = n0 - nk;
+  S->have_counts[0] = true;
+  if (nk == 0) {
+    T0.release();
+    set_error("no primary feature passes the realised test");
+    return DSE_EINVAL;
+  }
+  TableArrays T;
+  DSE_TRY(table_alloc(T, nk, ld));
+  {
+    // host-assembled metadata of rung 0, rows copied device to device
+    std::vector<int32_t> hop(nk, DSE_OP_PRIMARY), hcx(nk, 0), hun((size_t)nk * kMaxDims, 0);
+    std::vector<int64_t> hca(nk), hcb(nk, -1);
+    const int64_t scale = (int64_t)1 << d->max_rung;
+    for (int64_t f = 0; f < nk; ++f) {
+      int64_t p = keep[f];
+      hca[f] = p;
+      for (int k = 0; k < S->D; ++k) {
+        int64_t u = (int64_t)d->units[p * S->D + k] * scale;
+        if (u > 32767 || u < -32767) {
+          T0.release();
+          T.release();
+          set_error("unit exponent of primary %lld out of range", (long long)p);
+          return DSE_EOVERFLOW;
+        }
+        hun[f * kMaxDims + k] = (int32_t)u;
+      }
+      cudaMemcpyAsync(T.v64 + f * ld, T0.v64 + p * ld, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st);
+#define CP1(field) cudaMemcpyAsync(T.field + f, T0.field + p, sizeof(*T.field), cudaMemcpyDeviceToDevice, st)
+      CP1(mean64); CP1(rmean64); CP1(min64); CP1(max64); CP1(minabs64); CP1(maxabs64); CP1(minabsnz64);
+#undef CP1
+    }
+    DSE_CUDA(cudaMemcpyAsync(T.op, hop.data(), 4 * nk, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(T.cplx, hcx.data(), 4 * nk, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(T.units, hun.data(), 4 * nk * kMaxDims, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(T.ca, hca.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(T.cb, hcb.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaStreamSynchronize(st));
+    T0.release();
+  }
+  int64_t n = nk;
+  S->rung_begin[0] = 0;
+  S->rung_begin[1] = n;
+  S->h_rung.assign(n, 0);
+
+  int *bad = nullptr;
+  DSE_TRY(dalloc(&bad, 1, "flag"));
+  DSE_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  unsigned long long *cnt = nullptr;
+  DSE_TRY(dalloc(&cnt, 6, "counts"));
+
+  // --- rungs 1 .. max_rung-1
+  for (int r = 1; r < d->max_rung; ++r) {
+    RungGeom g = make_geom(S, r);
+    FeatTable F = view(T, n, N, ld);
+    S->slots[r] = g.slots;
+    uint8_t *why = nullptr;
+    uint64_t *list = nullptr;
+    DSE_TRY(dalloc(&why, g.slots, "slot reasons"));
+    k_apriori_rung<<<grid_for(g.slots, 256), 256, 0, st>>>(F, g, P, why, bad);
+    DSE_CUDA(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), st));
+    launch_count_reasons(why, g.slots, cnt, st);
+    unsigned long long hc[6];
+    DSE_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    int hbad = 0;
+    DSE_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaStreamSynchronize(st));
+    if (hbad) {
+      dfree(why);
+      set_error(hbad == 1 ? "odd unit exponent under sqrt" : "unit exponent out of range");
+      return DSE_EOVERFLOW;
+    }
+    uint64_t n_ap = hc[DSE_VALID];
+    DSE_TRY(dalloc(&list, n_ap, "a-priori list"));
+    uint64_t got = 0;
+    DSE_TRY(compact_bytes(why, g.slots, DSE_VALID, list, &got, st));
+    dfree(why);
+    // realised test of the a-priori valid slots
+    uint8_t *rw = nullptr;
+    DSE_TRY(dalloc(&rw, n_ap, "realised flags"));
+    if (n_ap) k_realised_rung<<<grid_for(n_ap * 32, 256), 256, 0, st>>>(F, g, list, n_ap, S->fmin_std_rel, rw);
+    uint64_t *vlist = nullptr;
+    DSE_TRY(dalloc(&vlist, n_ap, "valid list"));
+    uint64_t n_new = 0;
+    DSE_TRY(compact_bytes(rw, n_ap, DSE_VALID, vlist, &n_new, st));
+    dfree(rw);
+    // vlist holds positions into list; map back to flat slots
+    std::vector<uint64_t> hpos(n_new), hlist(n_ap);
+    if (n_new) {
+      DSE_CUDA(cudaMemcpyAsync(hpos.data(), vlist, 8 * n_new, cudaMemcpyDeviceToHost, st));
+      DSE_CUDA(cudaMemcpyAsync(hlist.data(), list, 8 * n_ap, cudaMemcpyDeviceToHost, st));
+      DSE_CUDA(cudaStreamSynchronize(st));
+      for (uint64_t x = 0; x < n_new; ++x) hpos[x] = hlist[hpos[x]];
+      DSE_CUDA(cudaMemcpyAsync(vlist, hpos.data(), 8 * n_new, cudaMemcpyHostToDevice, st));
+    }
+    dfree(list);
+    for (int c = 0; c < 6; ++c) S->reasons[r][c] = (int64_t)hc[c];
+    S->reasons[r][DSE_VALID] = (int64_t)n_new;
+    S->reasons[r][DSE_R_REALISED] = (int64_t)(n_ap - n_new);
+    S->have_counts[r] = true;
+    // grow the table and append
+    TableArrays T2;
+    dse_status s2 = table_alloc(T2, n + (int64_t)n_new, ld);
+    if (s2 != DSE_OK) {
+      dfree(vlist);
+      T.release();
+      return s2;
+    }
+    DSE_TRY(table_copy(T2, T, n, ld, st));
+    FeatTable Fold = view(T, n, N, ld);
+    if (n_new)
+      k_materialise<<<grid_for(n_new * 32, 256), 256, 0, st>>>(Fold, g, P, vlist, n_new, n, T2.v64, T2.op, T2.ca,
+                                                               T2.cb, T2.cplx, T2.units);
+    if (n_new)
+      k_summaries<<<grid_for(n_new * 32, 256), 256, 0, st>>>(T2.v64, ld, N, n, n + (int64_t)n_new, T2.mean64,
+                                                             T2.rmean64, T2.min64, T2.max64, T2.minabs64, T2.maxabs64,
+                                                             T2.minabsnz64, S->fmin_std_rel, nullptr);
+    DSE_CUDA(cudaStreamSynchronize(st));
+    dfree(vlist);
+    T.release();
+    T = T2;
+    n += (int64_t)n_new;
+    S->rung_begin[r + 1] = n;
+    S->h_rung.resize(n, r);
+  }
+  dfree(bad);
+  dfree(cnt);
+
+  // --- FP32 rows and helpers
+  S->n = n;
+  S->v64 = T.v64;
+  S->mean64 = T.mean64;
+  S->rmean64 = T.rmean64;
+  S->min64 = T.min64;
+  S->max64 = T.max64;
+  S->minabs64 = T.minabs64;
+  S->maxabs64 = T.maxabs64;
+  S->op = T.op;
+  S->cplx = T.cplx;
+  S->units = T.units;
+  S->ca = T.ca;
+  S->cb = T.cb;
+  DSE_TRY(dalloc(&S->v32, (size_t)n * ld, "FP32 feature rows"));
+  DSE_TRY(dalloc(&S->fa, n, "helpers"));
+  DSE_TRY(dalloc(&S->fr, n, "helpers"));
+  DSE_TRY(dalloc(&S->flags, n, "flags"));
+  DSE_TRY(dalloc(&S->ukey, 2 * n, "unit keys"));
+  k_fp32_prep<<<grid_for(n * ld, 256), 256, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, T.mean64, T.rmean64, T.min64,
+                                                     T.max64, T.minabs64, T.maxabs64, T.minabsnz64, T.units,
+                                                     S->exp_arg_max, S->fa, S->fr, S->flags, S->ukey);
+  dfree(T.minabsnz64);
+
+  // --- host copies for decoding and the unit classes
+  S->h_op.resize(n);
+  S->h_cplx.resize(n);
+  S->h_ca.resize(n);
+  S->h_cb.resize(n);
+  S->h_ukey.resize(2 * n);
+  DSE_CUDA(cudaMemcpyAsync(S->h_op.data(), S->op, 4 * n, cudaMemcpyDeviceToHost, st));
+  DSE_CUDA(cudaMemcpyAsync(S->h_cplx.data(), S->cplx, 4 * n, cudaMemcpyDeviceToHost, st));
+  DSE_CUDA(cudaMemcpyAsync(S->h_ca.data(), S->ca, 8 * n, cudaMemcpyDeviceToHost, st));
+  DSE_CUDA(cudaMemcpyAsync(S->h_cb.data(), S->cb, 8 * n, cudaMemcpyDeviceToHost, st));
+  DSE_CUDA(cudaMemcpyAsync(S->h_ukey.data(), S->ukey, 16 * n, cudaMemcpyDeviceToHost, st));
+  DSE_CUDA(cudaStreamSynchronize(st));
+
+  std::vector<int32_t> rows(n);
+  std::iota(rows.begin(), rows.end(), 0);
+  const bool one_class = !S->unit_check_addsub || S->D == 0;
+  if (!one_class)
+    std::stable_sort(rows.begin(), rows.end(), [&](int32_t x, int32_t y) {
+      if (S->h_ukey[2 * x + 1] != S->h_ukey[2 * y + 1]) return S->h_ukey[2 * x + 1] < S->h_ukey[2 * y + 1];
+      return S->h_ukey[2 * x] < S->h_ukey[2 * y];
+    });
+  S->h_class_rows = rows;
+  S->h_class_begin.clear();
+  for (int64_t f = 0; f < n; ++f)
+    if (f == 0 || (!one_class && (S->h_ukey[2 * rows[f]] != S->h_ukey[2 * rows[f - 1]] ||
+                                  S->h_ukey[2 * rows[f] + 1] != S->h_ukey[2 * rows[f - 1] + 1])))
+      S->h_class_begin.push_back(f);
+  S->h_class_begin.push_back(n);
+  DSE_TRY(dalloc(&S->class_rows, n, "class rows"));
+  DSE_TRY(dalloc(&S->rowid_ident, n, "row ids"));
+  std::vector<int32_t> ident(n);
+  std::iota(ident.begin(), ident.end(), 0);
+  DSE_CUDA(cudaMemcpyAsync(S->class_rows, rows.data(), 4 * n, cudaMemcpyHostToDevice, st));
+  DSE_CUDA(cudaMemcpyAsync(S->rowid_ident, ident.data(), 4 * n, cudaMemcpyHostToDevice, st));
+  DSE_CUDA(cudaStreamSynchronize(st));
+
+  S->geom = make_geom(S, d->max_rung);
+  S->slots[d->max_rung] = S->geom.slots;
+  return DSE_OK;
+}
+
+dse_status build_space(const dse_space_desc *d, dse_space **out) {
+  dse_space *S = new (std::nothrow) dse_space();
+  if (!S) {
+    set_error("out of host memory");
+    return DSE_ENOMEM;
+  }
+  for (int r = 0; r <= kMaxRung; ++r) S->have_counts[r] = false;
+  dse_status s = build_impl(d, S);
+  if (s != DSE_OK) {
+    space_release(S);
+    return s;
+  }
+  *out = S;
+  return DSE_OK;
+}
+
+dse_status space_release(dse_space *S) {
+  if (!S) return DSE_OK;
+  dfree(S->v64); dfree(S->v32); dfree(S->mean64); dfree(S->rmean64); dfree(S->min64); dfree(S->max64);
+  dfree(S->minabs64); dfree(S->maxabs64); dfree(S->fa); dfree(S->fr); dfree(S->flags); dfree(S->cplx);
+  dfree(S->op); dfree(S->units); dfree(S->ca); dfree(S->cb); dfree(S->ukey); dfree(S->rowid_ident);
+  dfree(S->class_rows);
+  delete S;
+  return DSE_OK;
+}
+
+FeatTable table_of(const dse_space *S) {
+  FeatTable F{};
+  F.n = S->n;
+  F.N = S->N;
+  F.ld = S->ld;
+  F.v64 = S->v64;
+  F.v32 = S->v32;
+  F.mean64 = S->mean64;
+  F.rmean64 = S->rmean64;
+  F.min64 = S->min64;
+  F.max64 = S->max64;
+  F.minabs64 = S->minabs64;
+  F.maxabs64 = S->maxabs64;
+  F.fa = S->fa;
+  F.fr = S->fr;
+  F.flags = S->flags;
+  F.cplx = S->cplx;
+  F.op = S->op;
+  F.ca = S->ca;
+  F.cb = S->cb;
+  F.units = S->units;
+  F.ukey = S->ukey;
+  return F;
+}
+
+// A-priori reason counts of rung max_rung (no evaluation).
+__global__ void k_count_apriori(FeatTable F, RungGeom g, AprioriParams P, unsigned long long *counts) {
+  __shared__ unsigned int c[6];
+  if (threadIdx.x < 6) c[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.slots;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    int op;
+    int64_t a, b;
+    decode_flat(g, p, &op, &a, &b);
+    int32_t u[kMaxDims], cx;
+    int bad = 0;
+    atomicAdd(&c[apriori64(F, P, op, a, b, u, &cx, &bad)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 6 && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)c[threadIdx.x]);
+}
+
+dse_status count_last_rung(dse_space *S, cudaStream_t st) {
+  int r = S->max_rung;
+  if (S->have_counts[r]) return DSE_OK;
+  unsigned long long *cnt = nullptr;
+  DSE_TRY(dalloc(&cnt, 6, "counts"));
+  DSE_CUDA(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), st));
+  AprioriParams P{S->D, S->unit_check_addsub, S->explog_dimensionless, S->max_complexity, S->fmax_max,
+                  S->exp_arg_max};
+  if (S->geom.slots) k_count_apriori<<<grid_for(S->geom.slots, 256, 152 * 32), 256, 0, st>>>(table_of(S), S->geom, P, cnt);
+  unsigned long long hc[6];
+  DSE_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  DSE_CUDA(cudaStreamSynchronize(st));
+  dfree(cnt);
+  for (int c = 0; c < 6; ++c) S->reasons[r][c] = (int64_t)hc[c];
+  S->reasons[r][DSE_R_REALISED] = -1;
+  S->have_counts[r] = true;
+  return DSE_OK;
+}
+
+}  // namespace dse

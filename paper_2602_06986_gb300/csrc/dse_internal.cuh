@@ -1,0 +1,319 @@
+// dse_internal.cuh -- shared definitions of the GB300 descriptor-screening
+// library: device tables, launch arguments, the flat-index codec and the
+// inline-PTX helpers (mbarrier, bulk async copies) used by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dse.h"
+
+namespace dse {
+
+constexpr int kMaxDims = 8;
+constexpr int kMaxRung = 3;
+constexpr int kNumBins = 4096;      // threshold histogram bins over [0, 1]
+constexpr float kTol = 1e-5f;       // relative tolerance of a reported score
+
+// Per-feature flag bits (exact FP64 tests on the feature's summaries).
+enum : uint32_t {
+  F_MINABS_POS = 1u << 0,   // min|x| > 0
+  F_MIN_POS = 1u << 1,      // min x > 0
+  F_MIN_NONNEG = 1u << 2,   // min x >= 0
+  F_EXP_DOMAIN = 1u << 3,   // max x <= 80
+  F_EXP_MAG = 1u << 4,      // max x <= log(fmax_max)
+  F_FP32_SAFE = 1u << 5,    // every nonzero |x| in [2^-60, 2^60]
+  F_DIMLESS = 1u << 6,      // unit vector is zero
+};
+
+// Device view of the stored features Phi_{k-1} (structure of arrays).
+struct FeatTable {
+  int64_t n;        // number of stored features
+  int64_t N;        // samples
+  int64_t ld;       // row stride (elements) of v64 / v32, multiple of 4
+  const double *v64;
+  const float *v32;
+  const double *mean64, *rmean64;            // mean of x, mean of 1/x (0 if min|x| == 0)
+  const double *min64, *max64, *minabs64, *maxabs64;
+  const float4 *fa;                          // {mean32, rmean32, RU(max|x|), RD(max|x|)}
+  const float2 *fr;                          // {RU(1/min|x|), RD(1/min|x|)} (0 if min|x| == 0)
+  const uint32_t *flags;
+  const int32_t *cplx;
+  const int32_t *op;
+  const int64_t *ca, *cb;
+  const int32_t *units;                      // [n][kMaxDims] scaled exponents
+  const uint64_t *ukey;                      // [n][2] packed exponents (16 bits each)
+};
+
+// Rung-k geometry: global id = n_stored + p.
+struct RungGeom {
+  int64_t o;          // first id of the newest stored rung
+  int64_t n;          // stored features
+  int32_t nu, nb;     // enabled unary ops / binary slots
+  int32_t uops[6];    // op codes of the unary ops in order
+  int32_t bops[6];    // op codes of the binary slots in order
+  uint64_t um;        // nu * (n - o): size of the unary block
+  uint64_t slots;     // total flat slots of rung k
+  uint64_t tri_o;     // o(o-1)/2
+};
+
+__host__ __device__ inline uint64_t tri(uint64_t n) { return n * (n - 1) / 2; }
+
+// Pair index qs (>= 0) -> (i, j) with i(i-1)/2 <= qs < i(i+1)/2, j = qs - i(i-1)/2.
+// FP64 square root, then exact integer fix-up.
+__host__ __device__ inline void pair_from_index(uint64_t qs, uint64_t *i, uint64_t *j) {
+  double d = sqrt(8.0 * (double)qs + 1.0);
+  uint64_t r = (uint64_t)((1.0 + d) * 0.5);
+  if (r < 1) r = 1;
+  while (tri(r) > qs) --r;
+  while (tri(r + 1) <= qs) ++r;
+  *i = r;
+  *j = qs - tri(r);
+}
+
+// Flat index p of rung k -> (op, a, b); b = -1 for unary.  Returns false if p
+// is outside the rung.
+__host__ __device__ inline bool decode_flat(const RungGeom &g, uint64_t p, int *op, int64_t *a,
+                                            int64_t *b) {
+  if (p >= g.slots) return false;
+  if (p < g.um) {
+    *a = g.o + (int64_t)(p / (uint64_t)g.nu);
+    *op = g.uops[p % (uint64_t)g.nu];
+    *b = -1;
+    return true;
+  }
+  uint64_t pp = p - g.um;
+  uint64_t q = pp / (uint64_t)g.nb;
+  int slot = (int)(pp % (uint64_t)g.nb);
+  uint64_t i, j;
+  pair_from_index(q + g.tri_o, &i, &j);
+  *op = g.bops[slot];
+  *a = (int64_t)i;
+  *b = (int64_t)j;
+  return true;
+}
+
+__host__ __device__ inline bool is_unary(int op) { return op >= DSE_OP_SQUARE && op <= DSE_OP_LOG; }
+
+// ------------------------------------------------------------------ buffers
+
+// Per-list candidate buffer: entries (global id, FP32 score, error bound).
+struct CandBufs {
+  uint64_t *id;        // [lists][cap]
+  float *score;        // [lists][cap]
+  float *eps;          // [lists][cap]
+  unsigned int *count; // [lists]
+  int64_t cap;
+  unsigned int *hist;  // [lists][kNumBins]
+  float *theta;        // [lists] (as float; raised monotonically with atomicMax on bits)
+};
+
+// Statistics counters on the device (unsigned long long for atomics).
+enum {
+  ST_REASON0 = 0,      // 6 reason counters
+  ST_EVALUATED = 6,
+  ST_BUFFERED = 7,
+  ST_ESCALATED = 8,
+  ST_RESCORED = 9,
+  ST_ESC_OVERFLOW = 10,
+  ST_TIMEOUT = 11,
+  ST_ADD_SEEN = 12,    // additive slots examined by the additive pair kernel
+  ST_VALID_G0 = 13,    // valid candidates scored per kernel group (3)
+  ST_COUNT = 16
+};
+
+// Tile of the pair triangle: rows rowid[ibase .. ibase+ni) x rowid[jbase .. jbase+nj);
+// a pair (x, y) is taken iff position(x) > position(y).
+struct Tile {
+  int32_t ibase, jbase;
+  int16_t ni, nj;
+  int32_t pad;
+};
+
+// Arguments common to the screen kernels.
+struct ScreenArgs {
+  FeatTable F;
+  RungGeom G;
+  int64_t n_stored;
+  uint64_t id_begin, id_end;   // global id range
+  int32_t N;
+  double invN;                 // 1/N (rounded to the evaluation type by each kernel)
+  int32_t ldy;                 // row stride of y32 / y64
+  int32_t T;                   // targets in this pass
+  int32_t t0;                  // first target of this pass (list offset)
+  int32_t mode;                // DSE_MODE_*
+  int32_t n_lists;
+  const float *y32;            // [T][ldy] centred, unit-norm targets (FP32)
+  const double *y64;           // [T][ldy] centred, unit-norm targets (FP64)
+  const float *ysum32;         // [T] sum of the FP32 targets
+  int32_t max_complexity;
+  float fmax32_dn, fmax32_up;  // RD / RU of fmax_max
+  double fmax64;
+  float fmin_std_rel;          // < 0: degeneracy test off
+  double fmin_std_rel64;
+  float gamma;                 // accumulation error factor (FP32 path)
+  float u;                     // unit roundoff of the evaluation type
+  int64_t k;
+  int32_t unit_check_addsub, explog_dimensionless;
+  CandBufs B;
+  uint64_t *esc_id;            // escalation list (global ids)
+  unsigned int *esc_count;
+  int64_t esc_cap;
+  unsigned long long *stats;
+  int *err;                    // device error flag (timeouts)
+  // pair kernels
+  const Tile *tiles;
+  int32_t n_tiles;
+  unsigned int *tile_counter;
+  const int32_t *rowid;
+  int32_t slot_pos[6];         // flat slot position of each binary op code 6..11 (-1 = off)
+  int32_t first_pass;          // count statistics and escalate only in the first target pass
+  int32_t group;               // kernel group for the per-group valid counters
+};
+
+// Launch bookkeeping (process-wide count of the library's kernel launches).
+void note_launches(int64_t n);
+
+// ----------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; returns false (and the caller records a
+// timeout) if the phase did not complete within `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 1-D bulk async copy global -> shared, completing on an mbarrier.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Raise a non-negative float threshold monotonically.
+__device__ __forceinline__ void atomic_max_nonneg(float *addr, float v) {
+  atomicMax(reinterpret_cast<int *>(addr), __float_as_int(v));
+}
+
+__device__ __forceinline__ float ld_relaxed(const float *p) {
+  float v;
+  asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
+}  // namespace dse
+
+// ----------------------------------------------------- host-side handles
+
+struct dse_space {
+  // description
+  int64_t N, ld, n_primary;
+  int32_t D, max_rung;
+  uint32_t op_mask;
+  int32_t max_complexity, unit_check_addsub, explog_dimensionless;
+  double fmax_max, fmin_std_rel, exp_arg_max;
+  int device;
+  // stored features (device)
+  int64_t n;                     // stored
+  int64_t rung_begin[dse::kMaxRung + 2];
+  uint64_t slots[dse::kMaxRung + 1];
+  int64_t reasons[dse::kMaxRung + 1][6];
+  bool have_counts[dse::kMaxRung + 1];
+  double *v64 = nullptr;
+  float *v32 = nullptr;
+  double *mean64 = nullptr, *rmean64 = nullptr, *min64 = nullptr, *max64 = nullptr,
+         *minabs64 = nullptr, *maxabs64 = nullptr;
+  float4 *fa = nullptr;
+  float2 *fr = nullptr;
+  uint32_t *flags = nullptr;
+  int32_t *cplx = nullptr, *op = nullptr, *units = nullptr;
+  int64_t *ca = nullptr, *cb = nullptr;
+  uint64_t *ukey = nullptr;
+  int32_t *rowid_ident = nullptr;   // identity row list [0, n)
+  // host copies for decoding
+  std::vector<int32_t> h_op, h_rung, h_cplx;
+  std::vector<int64_t> h_ca, h_cb;
+  std::vector<uint64_t> h_ukey;     // [n][2]
+  // unit classes for the additive pair kernels
+  std::vector<int32_t> h_class_rows;            // feature ids sorted by (unit key, id)
+  std::vector<int64_t> h_class_begin;           // class boundaries into h_class_rows
+  int32_t *class_rows = nullptr;
+  dse::RungGeom geom;
+  dse::FeatTable table() const;
+};
+
+struct dse_result {
+  dse_space *space;
+  int32_t n_lists, T, mode, precision;
+  int64_t k;
+  uint64_t id_begin, id_end;
+  cudaStream_t stream;
+  // outputs (device)
+  uint64_t *out_id = nullptr;       // [lists][k]
+  double *out_score = nullptr;      // [lists][k]
+  double *out_eps = nullptr;        // [lists][k]
+  int64_t *out_n = nullptr;         // [lists]
+  unsigned long long *stats = nullptr;
+  int *err = nullptr;
+  unsigned int *overflow = nullptr; // [lists]
+  // working state kept for a re-run
+  double *y64 = nullptr;
+  float *y32 = nullptr;
+  float *ysum32 = nullptr;
+  int32_t ldy = 0;
+  int32_t reruns = 0;
+  bool fetched = false;
+  dse_stats host_stats{};
+  void *scratch = nullptr;          // one allocation for buffers
+  size_t scratch_bytes = 0;
+  unsigned int *buf_count = nullptr;
+  uint64_t add_total = 0;           // additive slots of the screened binary range
+  void *keep = nullptr;             // launch state for a re-run
+  void (*keep_free)(void *) = nullptr;
+  dse_status (*rerun)(dse_result *) = nullptr;
+  int32_t flags = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> timing;  // (group, start, stop)
+  int64_t launches = 0;
+};

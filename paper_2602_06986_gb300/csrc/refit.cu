@@ -1,0 +1,281 @@
+// refit.cu -- FP64 least-squares refits of the residual loop.
+//
+// Eq. 1 asks for the best linear model with at most D nonzero coefficients;
+// the greedy loop (OMP is one of the strategies named in "Software
+// Description") keeps the descriptors chosen so far fixed and, for every
+// candidate retained by SIS, fits y on [fixed..., candidate] with an
+// intercept, keeping the candidate with the smallest RMSE.  Each fit is a
+// (D+1)-column problem solved in FP64 on the device: centred normal
+// equations by Cholesky (a column whose Cholesky pivot falls below 1e-12 of
+// its norm is rejected as collinear), the RMSE from the explicit residual.
+#include <math.h>
+
+#include "dse_internal.cuh"
+#include "eval64.cuh"
+#include "util.cuh"
+
+namespace dse {
+
+FeatTable table_of(const dse_space *S);
+
+__device__ __forceinline__ double col_value(const FeatTable &F, const RungGeom &G, int64_t n_stored, int op,
+                                            int64_t a, int64_t b, int64_t s) {
+  (void)G;
+  (void)n_stored;
+  return eval_op64(op, F.v64[a * F.ld + s], b >= 0 ? F.v64[b * F.ld + s] : 0.0);
+}
+
+__device__ __forceinline__ void decode_any(const RungGeom &G, int64_t n_stored, uint64_t gid, int *op, int64_t *a,
+                                           int64_t *b) {
+  if (gid < (uint64_t)n_stored) {
+    *op = DSE_OP_PRIMARY;
+    *a = (int64_t)gid;
+    *b = -1;
+  } else {
+    decode_flat(G, gid - (uint64_t)n_stored, op, a, b);
+  }
+}
+
+// Columns of the given ids into out[c][N] (warp per column).
+__global__ void k_columns(FeatTable F, RungGeom G, int64_t n_stored, const uint64_t *ids, int n, double *out) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n) return;
+  int op;
+  int64_t a, b;
+  decode_any(G, n_stored, ids[w], &op, &a, &b);
+  for (int64_t s = lane; s < F.N; s += 32) out[(int64_t)w * F.N + s] = col_value(F, G, n_stored, op, a, b, s);
+}
+
+constexpr int kMaxP = 4;  // fixed columns + candidate
+
+// One warp per candidate: fit, RMSE and coefficients (intercept first).
+__global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double *y, const double *fixed_cols, int nf,
+                        const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand, double *rmse_out,
+                        double *beta_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_cand) return;
+  const int64_t N = F.N;
+  const int p = nf + 1;
+  const uint64_t gid = cand[w];
+  bool dup = false;
+  for (int j = 0; j < nf; ++j) dup |= fixed_ids[j] == gid;
+  if (dup) {
+    if (lane == 0) rmse_out[w] = INFINITY;
+    return;
+  }
+  int op;
+  int64_t a, b;
+  decode_any(G, n_stored, gid, &op, &a, &b);
+  auto xval = [&](int c, int64_t s) -> double {
+    return c < nf ? fixed_cols[(int64_t)c * N + s] : col_value(F, G, n_stored, op, a, b, s);
+  };
+  // means
+  double m[kMaxP] = {0, 0, 0, 0}, my = 0.0;
+  for (int64_t s = lane; s < N; s += 32) {
+    my += y[s];
+    for (int c = 0; c < p; ++c) m[c] += xval(c, s);
+  }
+  my = warp_sum64(my) / (double)N;
+  for (int c = 0; c < p; ++c) m[c] = warp_sum64(m[c]) / (double)N;
+  // centred Gram, right-hand side and uncentred column norms
+  double Gm[kMaxP][kMaxP] = {}, g[kMaxP] = {}, nrm[kMaxP] = {};
+  for (int64_t s = lane; s < N; s += 32) {
+    double xc[kMaxP];
+    for (int c = 0; c < p; ++c) {
+      double v = xval(c, s);
+      xc[c] = v - m[c];
+      nrm[c] = fma(v, v, nrm[c]);
+    }
+    double yc = y[s] - my;
+    for (int c = 0; c < p; ++c) {
+      g[c] = fma(xc[c], yc, g[c]);
+      for (int d = 0; d <= c; ++d) Gm[c][d] = fma(xc[c], xc[d], Gm[c][d]);
+    }
+  }
+  for (int c = 0; c < p; ++c) {
+    g[c] = warp_sum64(g[c]);
+    nrm[c] = sqrt(warp_sum64(nrm[c]));
+    for (int d = 0; d <= c; ++d) Gm[c][d] = warp_sum64(Gm[c][d]);
+  }
+  // Cholesky G = L L^T (every lane computes the same small factorisation)
+  double L[kMaxP][kMaxP] = {};
+  bool ok = true;
+  for (int c = 0; c < p; ++c) {
+    double dsum = Gm[c][c];
+    for (int k = 0; k < c; ++k) dsum -= L[c][k] * L[c][k];
+    if (!(dsum > 0.0)) {
+      ok = false;
+      break;
+    }
+    L[c][c] = sqrt(dsum);
+    if (!(L[c][c] > 1e-12 * nrm[c])) {
+      ok = false;
+      break;
+    }
+    for (int r = c + 1; r < p; ++r) {
+      double v = Gm[r][c];
+      for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
+      L[r][c] = v / L[c][c];
+    }
+  }
+  double beta[kMaxP + 1] = {};
+  if (ok) {
+    double z[kMaxP];
+    for (int c = 0; c < p; ++c) {
+      double v = g[c];
+      for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
+      z[c] = v / L[c][c];
+    }
+    for (int c = p - 1; c >= 0; --c) {
+      double v = z[c];
+      for (int k = c + 1; k < p; ++k) v -= L[k][c] * beta[k + 1];
+      beta[c + 1] = v / L[c][c];
+    }
+    double b0 = my;
+    for (int c = 0; c < p; ++c) b0 -= beta[c + 1] * m[c];
+    beta[0] = b0;
+  }
+  double rss = 0.0;
+  if (ok) {
+    for (int64_t s = lane; s < N; s += 32) {
+      double f = beta[0];
+      for (int c = 0; c < p; ++c) f = fma(beta[c + 1], xval(c, s), f);
+      double r = y[s] - f;
+      rss = fma(r, r, rss);
+    }
+    rss = warp_sum64(rss);
+  }
+  if (lane == 0) {
+    rmse_out[w] = ok ? sqrt(rss / (double)N) : INFINITY;
+    for (int c = 0; c <= kMaxP; ++c) beta_out[w * (kMaxP + 1) + c] = ok && c <= p ? beta[c] : 0.0;
+  }
+}
+
+// Index of the smallest RMSE (ties: lower id); one block.
+__global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best) {
+  __shared__ double bv[1024];
+  __shared__ uint64_t bid[1024];
+  __shared__ int64_t bix[1024];
+  double v = INFINITY;
+  uint64_t id = ~0ull;
+  int64_t ix = -1;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = rmse[i];
+    if (r < v || (r == v && cand[i] < id)) {
+      v = r;
+      id = cand[i];
+      ix = i;
+    }
+  }
+  bv[threadIdx.x] = v;
+  bid[threadIdx.x] = id;
+  bix[threadIdx.x] = ix;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      double r = bv[threadIdx.x + o];
+      uint64_t i2 = bid[threadIdx.x + o];
+      if (r < bv[threadIdx.x] || (r == bv[threadIdx.x] && i2 < bid[threadIdx.x])) {
+        bv[threadIdx.x] = r;
+        bid[threadIdx.x] = i2;
+        bix[threadIdx.x] = bix[threadIdx.x + o];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *best = bv[0] < INFINITY ? bix[0] : -1;
+}
+
+// Residual y - fit of the chosen candidate.
+__global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const double *y, const double *fixed_cols,
+                           int nf, const uint64_t *cand, const int64_t *best, const double *beta_all, double *res) {
+  const int64_t bi = *best;
+  if (bi < 0) return;
+  const double *beta = beta_all + bi * (kMaxP + 1);
+  int op;
+  int64_t a, b;
+  decode_any(G, n_stored, cand[bi], &op, &a, &b);
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < F.N; s += (int64_t)gridDim.x * blockDim.x) {
+    double f = beta[0];
+    for (int c = 0; c < nf; ++c) f = fma(beta[c + 1], fixed_cols[(int64_t)c * F.N + s], f);
+    f = fma(beta[nf + 1], col_value(F, G, n_stored, op, a, b, s), f);
+    res[s] = y[s] - f;
+  }
+}
+
+dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, double *best_rmse, double *coefs,
+                      double *residual) {
+  cudaStream_t st = (cudaStream_t)d->stream;
+  const int64_t N = S->N, nc = d->n_cand;
+  const int nf = d->n_fixed;
+  const uint64_t total = (uint64_t)S->n + S->geom.slots;
+  for (int j = 0; j < nf; ++j)
+    if (d->fixed[j] >= total) {
+      set_error("fixed id out of range");
+      return DSE_ERANGE;
+    }
+  if (!d->cand_on_device)
+    for (int64_t i = 0; i < nc; ++i)
+      if (d->cand[i] >= total) {
+        set_error("candidate id out of range");
+        return DSE_ERANGE;
+      }
+  // one scratch block: y, fixed ids, fixed columns, candidates, rmse, beta, best, residual
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  size_t o_y = take(8 * N), o_fid = take(8 * 4), o_fc = take(8 * (size_t)N * 4), o_c = take(8 * nc),
+         o_r = take(8 * nc), o_b = take(8 * (size_t)nc * (kMaxP + 1)), o_best = take(8), o_res = take(8 * N);
+  char *base = nullptr;
+  DSE_TRY(dmalloc(reinterpret_cast<void **>(&base), off, "refit scratch"));
+  double *y = reinterpret_cast<double *>(base + o_y);
+  uint64_t *fid = reinterpret_cast<uint64_t *>(base + o_fid);
+  double *fc = reinterpret_cast<double *>(base + o_fc);
+  uint64_t *cand = reinterpret_cast<uint64_t *>(base + o_c);
+  double *rm = reinterpret_cast<double *>(base + o_r);
+  double *beta = reinterpret_cast<double *>(base + o_b);
+  int64_t *best = reinterpret_cast<int64_t *>(base + o_best);
+  double *res = reinterpret_cast<double *>(base + o_res);
+  cudaError_t e = cudaMemcpyAsync(y, d->y, 8 * N, cudaMemcpyDefault, st);
+  if (!e && nf) e = cudaMemcpyAsync(fid, d->fixed, 8 * nf, cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(cand, d->cand, 8 * nc, cudaMemcpyDefault, st);
+  if (e) {
+    dfree(base);
+    return cuda_status(e, "refit upload");
+  }
+  const FeatTable F = table_of(S);
+  note_launches(3 + (nf ? 1 : 0));
+  if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
+  k_refit<<<(unsigned)((nc * 32 + 255) / 256), 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, fid, cand, nc, rm, beta);
+  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best);
+  k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
+  int64_t hb = -1;
+  e = cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) {
+    dfree(base);
+    return cuda_status(e, "refit");
+  }
+  if (hb < 0) {
+    dfree(base);
+    set_error("no candidate gives a full-rank fit");
+    return DSE_EINVAL;
+  }
+  double hb_beta[kMaxP + 1];
+  e = cudaMemcpy(best_rmse, rm + hb, 8, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(best_id, cand + hb, 8, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(hb_beta, beta + hb * (kMaxP + 1), sizeof(hb_beta), cudaMemcpyDeviceToHost);
+  if (!e && residual) e = cudaMemcpy(residual, res, 8 * N, cudaMemcpyDefault);
+  dfree(base);
+  if (e) return cuda_status(e, "refit fetch");
+  if (coefs)
+    for (int c = 0; c < nf + 2; ++c) coefs[c] = hb_beta[c];
+  return DSE_OK;
+}
+
+}  // namespace dse

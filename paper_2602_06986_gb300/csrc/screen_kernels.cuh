@@ -1,0 +1,47 @@
+// screen_kernels.cuh -- launchers of the screening and selection kernels.
+#pragma once
+
+#include "dse_internal.cuh"
+
+namespace dse {
+
+enum { KIND_MUL = 0, KIND_ADD = 1 };
+
+void launch_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,
+                    float *ysum32, int *err, cudaStream_t st);
+void launch_feature(int prec64, int nt, const ScreenArgs &A, uint64_t id0, uint64_t id1, uint64_t p0, uint64_t p1,
+                    float gamma, int sms, cudaStream_t st);
+dse_status launch_pair(int prec64, int kind, int nt, const ScreenArgs &A, int block_len, int sms, cudaStream_t st);
+void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st);
+
+// Selection of the exact top-k of every list from its candidate buffer.
+struct SelectArgs {
+  CandBufs B;
+  int32_t n_lists;
+  int64_t k;
+  int32_t all64;            // re-score every retained entry in FP64
+  // retained set R per list
+  uint64_t *r_id;           // [lists][cap]
+  float *r_s32, *r_e32;     // [lists][cap]
+  double *r_s64, *r_e64;    // [lists][cap]
+  uint8_t *r_need;          // [lists][cap]
+  unsigned int *r_count;    // [lists]
+  unsigned int *overflow;   // [lists]
+  // FP64 re-score jobs
+  uint32_t *job;            // [lists * cap] packed (list << 24 | pos) is not enough: two arrays
+  uint32_t *job_list;
+  unsigned int *n_jobs;
+  // outputs
+  uint64_t *out_id;
+  double *out_score, *out_eps;
+  int64_t *out_n;
+  // sort scratch for large lists [lists][sort_cap]
+  double *sort_key;
+  uint64_t *sort_id;
+  int64_t sort_cap;
+  unsigned long long *stats;
+};
+
+dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cudaStream_t st);
+
+}  // namespace dse

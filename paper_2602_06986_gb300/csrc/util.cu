@@ -1,0 +1,176 @@
+// util.cu -- error state, allocation wrappers and order-preserving compaction.
+#include <stdio.h>
+#include <string.h>
+
+#include "util.cuh"
+
+namespace dse {
+
+static thread_local char g_err[1024] = "";
+static unsigned long long g_launches = 0;
+
+void note_launches(int64_t n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+int64_t launches_so_far() { return (int64_t)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+const char *last_error() { return g_err; }
+
+dse_status cuda_status(cudaError_t e, const char *what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DSE_ENOMEM : DSE_ECUDA;
+}
+
+dse_status dmalloc(void **p, size_t bytes, const char *what) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu) for %s: %s", bytes, what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? DSE_ENOMEM : DSE_ECUDA;
+  }
+  return DSE_OK;
+}
+
+void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+bool is_device_pointer(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------- compaction
+
+constexpr int kCompactThreads = 256;
+constexpr int kCompactPer = 16;  // elements per thread
+constexpr int kCompactTile = kCompactThreads * kCompactPer;
+
+__global__ void k_compact_count(const uint8_t *flags, uint64_t n, uint8_t want, unsigned int *block_counts) {
+  __shared__ unsigned int red[kCompactThreads / 32];
+  uint64_t base = (uint64_t)blockIdx.x * kCompactTile + (uint64_t)threadIdx.x * kCompactPer;
+  unsigned int c = 0;
+  for (int e = 0; e < kCompactPer; ++e) {
+    uint64_t p = base + e;
+    if (p < n && flags[p] == want) ++c;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = 0;
+    for (int w = 0; w < kCompactThreads / 32; ++w) t += red[w];
+    block_counts[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of block counts by one block (loops over chunks).
+__global__ void k_compact_scan(const unsigned int *block_counts, uint64_t nb, unsigned long long *offsets,
+                               unsigned long long *total) {
+  __shared__ unsigned long long part[1024];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint64_t c0 = 0; c0 < nb; c0 += 1024) {
+    uint64_t i = c0 + threadIdx.x;
+    unsigned long long v = i < nb ? block_counts[i] : 0ull;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      unsigned long long t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      part[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) offsets[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_compact_write(const uint8_t *flags, uint64_t n, uint8_t want,
+                                const unsigned long long *offsets, uint64_t *out) {
+  __shared__ unsigned int sc[kCompactThreads];
+  uint64_t base = (uint64_t)blockIdx.x * kCompactTile + (uint64_t)threadIdx.x * kCompactPer;
+  unsigned int c = 0;
+  for (int e = 0; e < kCompactPer; ++e) {
+    uint64_t p = base + e;
+    if (p < n && flags[p] == want) ++c;
+  }
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 1; o < kCompactThreads; o <<= 1) {
+    unsigned int t = threadIdx.x >= (unsigned)o ? sc[threadIdx.x - o] : 0u;
+    __syncthreads();
+    sc[threadIdx.x] += t;
+    __syncthreads();
+  }
+  unsigned long long w = offsets[blockIdx.x] + sc[threadIdx.x] - c;
+  for (int e = 0; e < kCompactPer; ++e) {
+    uint64_t p = base + e;
+    if (p < n && flags[p] == want) out[w++] = p;
+  }
+}
+
+dse_status compact_bytes(const uint8_t *flags, uint64_t n, uint8_t want, uint64_t *out, uint64_t *count_host,
+                         cudaStream_t s) {
+  *count_host = 0;
+  if (n == 0) return DSE_OK;
+  uint64_t nb = (n + kCompactTile - 1) / kCompactTile;
+  unsigned int *bc = nullptr;
+  unsigned long long *off = nullptr;
+  DSE_TRY(dalloc(&bc, nb, "compaction counts"));
+  dse_status st = dalloc(&off, nb + 1, "compaction offsets");
+  if (st != DSE_OK) {
+    dfree(bc);
+    return st;
+  }
+  note_launches(3);
+  k_compact_count<<<(unsigned)nb, kCompactThreads, 0, s>>>(flags, n, want, bc);
+  k_compact_scan<<<1, 1024, 0, s>>>(bc, nb, off, off + nb);
+  k_compact_write<<<(unsigned)nb, kCompactThreads, 0, s>>>(flags, n, want, off, out);
+  unsigned long long tot = 0;
+  cudaError_t e = cudaMemcpyAsync(&tot, off + nb, sizeof(tot), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(bc);
+  dfree(off);
+  if (e != cudaSuccess) return cuda_status(e, "compaction");
+  *count_host = tot;
+  return DSE_OK;
+}
+
+__global__ void k_count_reasons(const uint8_t *flags, uint64_t n, unsigned long long *counts) {
+  __shared__ unsigned int c[6];
+  if (threadIdx.x < 6) c[threadIdx.x] = 0;
+  __syncthreads();
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+    uint8_t f = flags[p];
+    if (f < 6) atomicAdd(&c[f], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 6 && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)c[threadIdx.x]);
+}
+
+void launch_count_reasons(const uint8_t *flags, uint64_t n, unsigned long long *counts, cudaStream_t s) {
+  if (n == 0) return;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  note_launches(1);
+  k_count_reasons<<<(unsigned)blocks, 256, 0, s>>>(flags, n, counts);
+}
+
+}  // namespace dse

@@ -1,0 +1,53 @@
+// util.cuh -- host-side error state and small device utilities (order-preserving
+// compaction, reason counting) shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+
+#include "dse.h"
+
+namespace dse {
+
+void set_error(const char *fmt, ...);
+void clear_error();
+
+// Returns DSE_ECUDA and records the message if `e` is an error.
+dse_status cuda_status(cudaError_t e, const char *what);
+
+#define DSE_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return ::dse::cuda_status(e_, #call); \
+  } while (0)
+
+#define DSE_TRY(call)                  \
+  do {                                 \
+    dse_status s_ = (call);            \
+    if (s_ != DSE_OK) return s_;       \
+  } while (0)
+
+// Device allocation that records DSE_ENOMEM.
+dse_status dmalloc(void **p, size_t bytes, const char *what);
+template <typename T>
+dse_status dalloc(T **p, size_t count, const char *what) {
+  return dmalloc(reinterpret_cast<void **>(p), count * sizeof(T), what);
+}
+void dfree(void *p);
+
+// Order-preserving selection: out[j] = the j-th index p < n with flags[p] == want.
+// Writes the count to *count_host (synchronises the stream).
+dse_status compact_bytes(const uint8_t *flags, uint64_t n, uint8_t want, uint64_t *out,
+                         uint64_t *count_host, cudaStream_t s);
+
+// counts[c] += number of p < n with flags[p] == c, for c < 6 (device counters).
+void launch_count_reasons(const uint8_t *flags, uint64_t n, unsigned long long *counts, cudaStream_t s);
+
+// Process-wide count of kernels the library has launched.
+int64_t launches_so_far();
+
+// Check whether a pointer is device memory.
+bool is_device_pointer(const void *p);
+
+}  // namespace dse

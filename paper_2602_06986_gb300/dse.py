@@ -1,0 +1,261 @@
+"""Python binding of libdse.so: argument marshalling over the C ABI (include/dse.h).
+
+Every computation runs in the CUDA library; this module only packs
+descriptors, passes pointers (numpy arrays for host memory, ``torch`` tensors'
+``data_ptr()`` for device memory) and raises ``DseError`` on a non-zero
+status.  Importing it loads the in-tree library and fails loudly if it is
+missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdse.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ERANGE, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+SQUARE, CUBE, INV, SQRT, EXP, LOG, ADD, SUB, MUL, DIV, RDIV, ABSDIFF = range(12)
+PRIMARY = 15
+MODE_PER_TARGET, MODE_AGGREGATED = 0, 1
+PREC_FP32, PREC_FP64, PREC_BF16X3, PREC_AUTO = 0, 1, 2, 3
+REASONS = ["valid", "unit", "complexity", "domain", "magnitude", "realised"]
+
+
+class DseError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dse status {status}: {msg}")
+        self.status = status
+
+
+class SpaceDesc(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("n_primary", C.c_int64), ("n_dims", C.c_int32),
+                ("max_rung", C.c_int32), ("X", C.c_void_p), ("ld_x", C.c_int64), ("x_on_device", C.c_int32),
+                ("reserved0", C.c_int32), ("sample_idx", C.c_void_p), ("units", C.c_void_p),
+                ("op_mask", C.c_uint32), ("max_complexity", C.c_int32), ("unit_check_addsub", C.c_int32),
+                ("explog_dimensionless", C.c_int32), ("fmax_max", C.c_double), ("fmin_std_rel", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class ScreenDesc(C.Structure):
+    _fields_ = [("Y", C.c_void_p), ("ld_y", C.c_int64), ("y_on_device", C.c_int32), ("n_targets", C.c_int32),
+                ("k", C.c_int64), ("mode", C.c_int32), ("precision", C.c_int32), ("id_begin", C.c_uint64),
+                ("id_end", C.c_uint64), ("stream", C.c_void_p), ("flags", C.c_int32), ("reserved0", C.c_int32)]
+
+
+FLAG_TIMING = 1
+
+
+class Stats(C.Structure):
+    _fields_ = [("screened", C.c_int64), ("reasons", C.c_int64 * 6), ("evaluated", C.c_int64),
+                ("buffered", C.c_int64), ("escalated", C.c_int64), ("rescored", C.c_int64),
+                ("reruns", C.c_int32), ("precision_used", C.c_int32), ("max_err_bound", C.c_double),
+                ("valid_by_group", C.c_int64 * 3), ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64)]
+
+
+class Expr(C.Structure):
+    _fields_ = [("rung", C.c_int32), ("op", C.c_int32), ("a", C.c_int64), ("b", C.c_int64)]
+
+
+class RefitDesc(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("y_on_device", C.c_int32), ("n_fixed", C.c_int32), ("fixed", C.c_void_p),
+                ("cand", C.c_void_p), ("n_cand", C.c_int64), ("cand_on_device", C.c_int32),
+                ("reserved0", C.c_int32), ("stream", C.c_void_p)]
+
+
+EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_counts", "dse_decode",
+           "dse_expr_string", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
+           "dse_ls_refit", "dse_kernel_launches", "dse_last_error", "dse_version"]
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+        L.dse_build_space.argtypes = [C.POINTER(SpaceDesc), C.POINTER(vp)]
+        L.dse_space_free.argtypes = [vp]
+        L.dse_space_free.restype = None
+        L.dse_space_size.argtypes = [vp, C.POINTER(i64), C.POINTER(u64)]
+        L.dse_space_counts.argtypes = [vp, i32, C.POINTER(u64), C.POINTER(i64)]
+        L.dse_decode.argtypes = [vp, u64, C.POINTER(Expr)]
+        L.dse_expr_string.argtypes = [vp, u64, C.c_char_p, i64]
+        L.dse_sis_screen.argtypes = [vp, C.POINTER(ScreenDesc), C.POINTER(vp)]
+        L.dse_result_free.argtypes = [vp]
+        L.dse_result_free.restype = None
+        L.dse_topk_fetch.argtypes = [vp, i32, vp, vp, vp, i64, C.POINTER(i64)]
+        L.dse_result_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
+        L.dse_last_error.restype = C.c_char_p
+        L.dse_version.restype = C.c_char_p
+        L.dse_kernel_launches.restype = i64
+        for name in EXPORTS:
+            if name not in ("dse_space_free", "dse_result_free", "dse_last_error", "dse_version",
+                            "dse_kernel_launches"):
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise DseError(status, lib().dse_last_error().decode())
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError(type(a))
+
+
+def version() -> str:
+    return lib().dse_version().decode()
+
+
+class Result:
+    """A screen's result handle (device resident until fetched)."""
+
+    def __init__(self, handle, n_lists, k):
+        self._h = handle
+        self.n_lists = n_lists
+        self.k = k
+
+    def fetch(self, lst=0, out=None):
+        """(ids uint64, scores float64, err_bounds float64) of list ``lst``.
+        With ``out`` = (ids, scores, bounds) torch CUDA tensors the copy stays on
+        the device and the return value is the list length."""
+        n = C.c_int64()
+        if out is not None:
+            pi, ps, pe = (t.data_ptr() for t in out)
+            _check(lib().dse_topk_fetch(self._h, lst, pi, ps, pe, out[0].numel(), C.byref(n)))
+            return n.value
+        ids = np.zeros(self.k, np.uint64)
+        sc = np.zeros(self.k)
+        eb = np.zeros(self.k)
+        _check(lib().dse_topk_fetch(self._h, lst, ids.ctypes.data, sc.ctypes.data, eb.ctypes.data, self.k,
+                                    C.byref(n)))
+        m = n.value
+        return ids[:m].copy(), sc[:m].copy(), eb[:m].copy()
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().dse_result_stats(self._h, C.byref(s)))
+        return {"screened": s.screened, "reasons": {REASONS[i]: s.reasons[i] for i in range(6)},
+                "evaluated": s.evaluated, "buffered": s.buffered, "escalated": s.escalated,
+                "rescored": s.rescored, "reruns": s.reruns, "precision_used": s.precision_used,
+                "max_err_bound": s.max_err_bound, "valid_by_group": list(s.valid_by_group),
+                "kernel_ms": list(s.kernel_ms), "kernel_launches": s.kernel_launches}
+
+    def free(self):
+        if self._h:
+            lib().dse_result_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Space:
+    """A built feature space (device resident)."""
+
+    def __init__(self, X, units, op_mask, max_rung, max_complexity=0, unit_check_addsub=1, explog_dimensionless=1,
+                 fmax_max=1e15, fmin_std_rel=1e-8, sample_idx=None, stream=None):
+        self._keep = []
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float64)
+        n_primary, ld = X.shape
+        if units is None:
+            units = np.zeros((n_primary, 0), np.int32)
+        units = np.ascontiguousarray(units, dtype=np.int32)
+        n_samples = ld if sample_idx is None else len(sample_idx)
+        if sample_idx is not None:
+            sample_idx = np.ascontiguousarray(sample_idx, dtype=np.int64)
+        self._keep += [X, units, sample_idx]
+        px, xdev = _ptr(X)
+        d = SpaceDesc(n_samples, n_primary, units.shape[1], max_rung, px, ld, xdev, 0,
+                      sample_idx.ctypes.data if sample_idx is not None else None,
+                      units.ctypes.data if units.shape[1] else None, op_mask, max_complexity, unit_check_addsub,
+                      explog_dimensionless, fmax_max, fmin_std_rel, stream)
+        h = C.c_void_p()
+        _check(lib().dse_build_space(C.byref(d), C.byref(h)))
+        self._h = h
+        self.n_samples = n_samples
+        self.max_rung = max_rung
+        ns, nt = C.c_int64(), C.c_uint64()
+        _check(lib().dse_space_size(self._h, C.byref(ns), C.byref(nt)))
+        self.n_stored, self.n_total = ns.value, nt.value
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().dse_space_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def counts(self, rung):
+        slots = C.c_uint64()
+        r = (C.c_int64 * 6)()
+        _check(lib().dse_space_counts(self._h, rung, C.byref(slots), r))
+        return int(slots.value), {REASONS[i]: int(r[i]) for i in range(6)}
+
+    def decode(self, gid):
+        e = Expr()
+        _check(lib().dse_decode(self._h, gid, C.byref(e)))
+        return e.rung, e.op, e.a, e.b
+
+    def expr(self, gid) -> str:
+        buf = C.create_string_buffer(1 << 14)
+        _check(lib().dse_expr_string(self._h, gid, buf, len(buf)))
+        return buf.value.decode()
+
+    def screen(self, Y, k, mode=MODE_PER_TARGET, precision=PREC_FP32, id_begin=0, id_end=0, stream=None,
+               flags=0) -> Result:
+        if isinstance(Y, np.ndarray):
+            Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.float64)
+        elif Y.dim() == 1:
+            Y = Y.reshape(1, -1)
+        T, ldy = Y.shape
+        py, ydev = _ptr(Y)
+        self._ykeep = Y
+        d = ScreenDesc(py, ldy, ydev, T, k, mode, precision, id_begin, id_end, stream, flags, 0)
+        h = C.c_void_p()
+        _check(lib().dse_sis_screen(self._h, C.byref(d), C.byref(h)))
+        return Result(h, 1 if mode == MODE_AGGREGATED else T, k)
+
+    def ls_refit(self, y, fixed, cand, residual=None, stream=None):
+        """Best candidate for the next descriptor slot: (id, rmse, coefs, residual)."""
+        if isinstance(y, np.ndarray):
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        fixed = np.ascontiguousarray(fixed, dtype=np.uint64)
+        if isinstance(cand, np.ndarray):
+            cand = np.ascontiguousarray(cand, dtype=np.uint64)
+        py, ydev = _ptr(y)
+        pc, cdev = _ptr(cand)
+        ncand = len(cand) if isinstance(cand, np.ndarray) else cand.numel()
+        d = RefitDesc(py, ydev, len(fixed), fixed.ctypes.data if len(fixed) else None, pc, ncand, cdev, 0, stream)
+        bid, brm = C.c_uint64(), C.c_double()
+        coefs = np.zeros(len(fixed) + 2)
+        if residual is None:
+            residual = np.zeros(self.n_samples)
+        pr, _ = _ptr(residual)
+        _check(lib().dse_ls_refit(self._h, C.byref(d), C.byref(bid), C.byref(brm), coefs.ctypes.data, pr))
+        return int(bid.value), float(brm.value), coefs, residual

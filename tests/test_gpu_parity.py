@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Bars (scores relative 1e-5 is the stated tolerance of the method's FP32 path):
+  * counts per rung and per reason, stored-feature count, candidate count,
+    expression strings and returned ids: bit-exact;
+  * every returned score within 1e-5 relative of the oracle's FP64 score and
+    within the bound the library reports with it;
+  * top-k sets equal apart from candidates whose oracle score lies within
+    1e-5 * s_k of the k-th oracle score s_k (interchangeable ties).
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__ as ge
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    ge.build()
+    import oracle
+    from paper_2602_06986_gb300 import dse
+    from paper_2602_06986_gb300 import workloads as W
+
+    return torch, oracle, dse, W
+
+
+def spaces(env, w, **extra):
+    torch, oracle, dse, W = env
+    kw = dict(unit_check_addsub=w["unit_check_addsub"], explog_dimensionless=w["explog_dimensionless"])
+    kw.update(extra)
+    sp = dse.Space(torch.from_numpy(w["X"]).cuda(), w["units"], w["op_mask"], w["max_rung"], **kw)
+    orc = oracle.Space(w["X"], w["units"], w["op_mask"], w["max_rung"], **kw)
+    return sp, orc
+
+
+def check_counts(sp, orc, max_rung):
+    assert sp.n_stored == orc.n_features
+    assert sp.n_total == orc.total_candidates
+    for r in range(max_rung):
+        assert sp.counts(r) == orc.rung_counts(r), r
+
+
+def check_list(ids, sc, eb, oids, osc, orc, Y, t):
+    ge._check_topk(ids, sc, eb, oids, osc, orc, Y, t, tol=TOL)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_parity(env, seed):
+    torch, oracle, dse, W = env
+    w = W.tiny(seed)
+    sp, orc = spaces(env, w)
+    check_counts(sp, orc, w["max_rung"])
+    res = sp.screen(torch.from_numpy(w["Y"]).cuda(), w["k"])
+    ids, sc, eb = res.fetch(0)
+    oids, osc, ocnt = orc.screen(w["Y"], w["k"])
+    check_list(ids, sc, eb, oids[0], osc[0], orc, w["Y"], 0)
+    st = res.stats()
+    assert st["reasons"] == ocnt
+    assert [sp.expr(int(i)) for i in ids] == [orc.expr(int(i)) for i in ids]
+    # a-priori counts of the streamed rung
+    slots, rs = sp.counts(w["max_rung"])
+    oslots, ors = orc.rung_counts(w["max_rung"])
+    assert slots == oslots
+    for key in ("unit", "complexity", "domain", "magnitude"):
+        assert rs[key] == ors[key], key
+    assert rs["valid"] == ors["valid"] + ors["realised"]
+
+
+def test_medium_parity(env):
+    torch, oracle, dse, W = env
+    w = W.medium(0)
+    sp, orc = spaces(env, w)
+    check_counts(sp, orc, w["max_rung"])
+    res = sp.screen(torch.from_numpy(w["Y"]).cuda(), w["k"])
+    ids, sc, eb = res.fetch(0)
+    oids, osc, ocnt = orc.screen(w["Y"], w["k"])
+    check_list(ids, sc, eb, oids[0], osc[0], orc, w["Y"], 0)
+    assert res.stats()["reasons"] == ocnt
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_fp64_plain_parity(env, seed):
+    torch, oracle, dse, W = env
+    w = W.tiny(seed)
+    sp, orc = spaces(env, w)
+    res = sp.screen(torch.from_numpy(w["Y"]).cuda(), w["k"], precision=dse.PREC_FP64)
+    ids, sc, eb = res.fetch(0)
+    oids, osc, ocnt = orc.screen(w["Y"], w["k"])
+    check_list(ids, sc, eb, oids[0], osc[0], orc, w["Y"], 0)
+    ref, _ = orc.score_ids(w["Y"], ids)
+    assert np.max(np.abs(sc - ref[:, 0]) / ref[:, 0]) < 1e-12
+    assert res.stats()["reasons"] == ocnt
+
+
+@pytest.mark.parametrize("T,mode", [(3, "per_target"), (5, "aggregated"), (17, "per_target")])
+def test_multi_target(env, T, mode):
+    torch, oracle, dse, W = env
+    w = W.tiny(4)
+    rng = np.random.default_rng(9)
+    X = w["X"]
+    Y = np.stack([X[rng.integers(8)] * X[rng.integers(8)] / X[rng.integers(8)] + 0.05 * rng.standard_normal(100)
+                  for _ in range(T)])
+    sp, orc = spaces(env, w)
+    m = dse.MODE_AGGREGATED if mode == "aggregated" else dse.MODE_PER_TARGET
+    k = 60
+    res = sp.screen(torch.from_numpy(Y).cuda(), k, mode=m)
+    oids, osc, ocnt = orc.screen(Y, k, mode=mode)
+    lists = 1 if mode == "aggregated" else T
+    for l in range(lists):
+        ids, sc, eb = res.fetch(l)
+        if mode == "aggregated":
+            ref, _ = orc.score_ids(Y, ids)
+            agg = np.sqrt(np.mean(ref ** 2, axis=1))
+            assert np.all(np.abs(sc - agg) <= TOL * agg)
+            sk = osc[0][-1]
+            above = {int(i) for i, s in zip(oids[0], osc[0]) if s > sk * (1 + TOL)}
+            assert above <= {int(i) for i in ids}
+        else:
+            check_list(ids, sc, eb, oids[l], osc[l], orc, Y, l)
+    assert res.stats()["reasons"] == ocnt
+
+
+def test_ranges_merge_to_full(env):
+    """Screening disjoint ragged id ranges and merging their top-k equals the
+    full screen (the index-range sharding of the multi-GPU plan)."""
+    torch, oracle, dse, W = env
+    w = W.tiny(5)
+    sp, orc = spaces(env, w)
+    Yd = torch.from_numpy(w["Y"]).cuda()
+    full = sp.screen(Yd, 50).fetch(0)
+    cuts = [0, 37, 1000, 7777, 20011, sp.n_total]
+    parts = []
+    counts = {}
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        r = sp.screen(Yd, 50, id_begin=a, id_end=b)
+        parts.append(r.fetch(0))
+        st = r.stats()
+        assert st["screened"] == b - a
+        for kk, v in st["reasons"].items():
+            counts[kk] = counts.get(kk, 0) + v
+        oi, os_, oc = orc.screen(w["Y"], 50, id_begin=a, id_end=b)
+        assert st["reasons"] == oc
+    ids = np.concatenate([p[0] for p in parts])
+    sc = np.concatenate([p[1] for p in parts])
+    order = np.lexsort((ids, -sc))[:50]
+    assert np.array_equal(ids[order], full[0])
+
+
+def test_edge_cases(env):
+    torch, oracle, dse, W = env
+    w = W.tiny(6)
+    sp, orc = spaces(env, w)
+    Yd = torch.from_numpy(w["Y"]).cuda()
+    # k larger than the number of valid candidates: everything, sorted
+    r = sp.screen(Yd, 10 ** 6, id_begin=0, id_end=300)
+    ids, sc, eb = r.fetch(0)
+    oi, os_, oc = orc.screen(w["Y"], 10 ** 6, id_begin=0, id_end=300)
+    assert len(ids) == oc["valid"] == len(oi[0])
+    check_list(ids, sc, eb, oi[0], os_[0], orc, w["Y"], 0)
+    # k = 1
+    ids, sc, eb = sp.screen(Yd, 1).fetch(0)
+    oi, os_, _ = orc.screen(w["Y"], 1)
+    assert abs(sc[0] - os_[0][0]) <= TOL * os_[0][0]
+    # empty range
+    ids, sc, eb = sp.screen(Yd, 5, id_begin=100, id_end=100).fetch(0)
+    assert len(ids) == 0
+    # range past the end
+    with pytest.raises(dse.DseError) as e:
+        sp.screen(Yd, 5, id_begin=0, id_end=sp.n_total + 1)
+    assert e.value.status == dse.ERANGE
+    # constant target
+    with pytest.raises(dse.DseError) as e:
+        sp.screen(torch.ones(1, 100, dtype=torch.float64, device="cuda"), 5).fetch(0)
+    assert e.value.status == dse.EINVAL
+    # decode past the end
+    with pytest.raises(dse.DseError) as e:
+        sp.decode(sp.n_total)
+    assert e.value.status == dse.ERANGE
+
+
+def test_tiny_samples_and_degenerate_primary(env):
+    """N = 3 samples, a constant primary (dropped by the realised test), ops
+    that trip every domain rule."""
+    torch, oracle, dse, W = env
+    X = np.array([[0.5, 1.5, 2.5], [2.0, 2.0, 2.0], [-1.0, 0.25, 3.0], [1.0, 2.0, 4.0]])
+    units = np.array([[1], [0], [1], [0]], np.int32)
+    y = np.array([1.0, 3.0, 2.0])
+    for ops in (W.OPS_FULL, W.OPS_TINY):
+        sp = dse.Space(torch.from_numpy(X).cuda(), units, ops, 2)
+        orc = oracle.Space(X, units, ops, 2)
+        check_counts(sp, orc, 2)
+        res = sp.screen(torch.from_numpy(y).cuda(), 25)
+        ids, sc, eb = res.fetch(0)
+        oi, os_, oc = orc.screen(y, 25)
+        check_list(ids, sc, eb, oi[0], os_[0], orc, y[None, :], 0)
+        assert res.stats()["reasons"] == oc
+
+
+def test_decode_matches_oracle(env):
+    torch, oracle, dse, W = env
+    w = W.medium(1)
+    sp, orc = spaces(env, w)
+    rng = np.random.default_rng(3)
+    for gid in list(rng.integers(0, sp.n_total, size=300)) + [0, sp.n_stored - 1, sp.n_stored, sp.n_total - 1]:
+        gid = int(gid)
+        assert sp.decode(gid) == orc.decode(gid)
+        assert sp.expr(gid) == orc.expr(gid)
+
+
+def test_determinism(env):
+    torch, oracle, dse, W = env
+    w = W.medium(2)
+    sp, _ = spaces(env, w)
+    Yd = torch.from_numpy(w["Y"]).cuda()
+    a = sp.screen(Yd, w["k"]).fetch(0)
+    b = sp.screen(Yd, w["k"]).fetch(0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_residual_loop_medium(env):
+    """D = 1..3 with FP64 refits of the retained candidates against the
+    oracle's Householder-QR loop."""
+    torch, oracle, dse, W = env
+    w = W.medium(0)
+    sp, orc = spaces(env, w)
+    y = w["Y"][0]
+    ref = orc.residual_loop(y, 3, w["k"])
+    r = y.copy()
+    fixed = []
+    for D in range(1, 4):
+        res = sp.screen(torch.from_numpy(r).cuda(), w["k"])
+        ids, sc, eb = res.fetch(0)
+        bid, rmse, coefs, resid = sp.ls_refit(y, np.array(fixed, np.uint64), ids)
+        # the oracle's pick may be an exact algebraic twin: compare RMSE
+        assert abs(rmse - ref["rmse"][D - 1]) <= 1e-9 * max(ref["rmse"][D - 1], 1e-12) + 1e-13
+        fixed.append(bid)
+        r = resid
+    assert ref["rmse"][2] < ref["rmse"][0]
