@@ -225,6 +225,23 @@ typedef struct {
 dse_status dse_ls_refit(dse_space *space, const dse_refit_desc *desc, uint64_t *best_id,
                         double *best_rmse, double *coefs, double *residual);
 
+/* dse_ls_refit without any device allocation.  The paper has no counterpart:
+   this is an engineering variant of the same refit step for callers that may
+   not allocate device memory while they run -- code inside a CUDA stream
+   capture (cudaMalloc is not allowed there), applications that hand all
+   device memory to their own pool or run under a hard memory budget.
+   Same arguments, results and synchronisation as dse_ls_refit.  Its scratch
+   is one fixed 4 MiB area per device, held by every device that loads the
+   library until the process exits; the limits are N <= 32768 samples and
+   n_cand <= 16384 candidates, and larger requests return DSE_EOVERFLOW with
+   a message.  The first call on a device looks the area's address up
+   (cudaGetSymbolAddress): make that first call before any stream capture.
+   All calls on a device share the one area, which keeps the last call's
+   contents: calls that overlap on the GPU (other streams or threads) race,
+   so the caller must serialise them. */
+dse_status dse_ls_refit_noalloc(dse_space *space, const dse_refit_desc *desc, uint64_t *best_id,
+                                double *best_rmse, double *coefs, double *residual);
+
 /* Number of kernels the library has launched in this process so far. */
 int64_t dse_kernel_launches(void);
 

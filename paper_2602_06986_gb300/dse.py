@@ -67,7 +67,7 @@ class RefitDesc(C.Structure):
 
 EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_counts", "dse_decode",
            "dse_expr_string", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
-           "dse_ls_refit", "dse_kernel_launches", "dse_last_error", "dse_version"]
+           "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error", "dse_version"]
 
 _lib = None
 
@@ -93,6 +93,7 @@ def lib():
         L.dse_topk_fetch.argtypes = [vp, i32, vp, vp, vp, i64, C.POINTER(i64)]
         L.dse_result_stats.argtypes = [vp, C.POINTER(Stats)]
         L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
+        L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
         L.dse_last_error.restype = C.c_char_p
         L.dse_version.restype = C.c_char_p
         L.dse_kernel_launches.restype = i64
@@ -258,4 +259,27 @@ class Space:
             residual = np.zeros(self.n_samples)
         pr, _ = _ptr(residual)
         _check(lib().dse_ls_refit(self._h, C.byref(d), C.byref(bid), C.byref(brm), coefs.ctypes.data, pr))
+        return int(bid.value), float(brm.value), coefs, residual
+
+    def ls_refit_noalloc(self, y, fixed, cand, residual=None, stream=None):
+        """Same as ls_refit through dse_ls_refit_noalloc, which allocates no
+        device memory: for callers that may not allocate while they run (stream
+        capture, an external memory pool or budget).  Fixed limits: N <= 32768
+        samples, at most 16384 candidates; one shared scratch area per device,
+        so overlapping calls must be serialised by the caller."""
+        if isinstance(y, np.ndarray):
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        fixed = np.ascontiguousarray(fixed, dtype=np.uint64)
+        if isinstance(cand, np.ndarray):
+            cand = np.ascontiguousarray(cand, dtype=np.uint64)
+        py, ydev = _ptr(y)
+        pc, cdev = _ptr(cand)
+        ncand = len(cand) if isinstance(cand, np.ndarray) else cand.numel()
+        d = RefitDesc(py, ydev, len(fixed), fixed.ctypes.data if len(fixed) else None, pc, ncand, cdev, 0, stream)
+        bid, brm = C.c_uint64(), C.c_double()
+        coefs = np.zeros(len(fixed) + 2)
+        if residual is None:
+            residual = np.zeros(self.n_samples)
+        pr, _ = _ptr(residual)
+        _check(lib().dse_ls_refit_noalloc(self._h, C.byref(d), C.byref(bid), C.byref(brm), coefs.ctypes.data, pr))
         return int(bid.value), float(brm.value), coefs, residual
