@@ -203,6 +203,62 @@ typedef struct {
 
 dse_status dse_result_stats(dse_result *result, dse_stats *out);
 
+/* Batched SIS screen: many independent problems, each with its own space
+   (its own primaries, or a sample gather list of a shared data set: a
+   cross-validation fold, a bootstrap resample) and its own target, screened
+   together with the same semantics as dse_sis_screen in PER_TARGET mode over
+   the whole space (stored features and rung max_rung), k per problem.  Each
+   kernel group runs once over all problems: work is cut into per-problem
+   jobs (candidate runs, pair tiles, pair-list runs) that warps and CTAs take
+   from device counters, so small and large problems share the GPU.  The
+   paper screens one data set at a time ("Software Description": candidates
+   evaluated against the target); batching independent problems is an
+   engineering form of the same step with no counterpart there.
+
+   dse_sis_screen_batched plans (job and tile lists, per-problem arguments,
+   every buffer, allocated once) and enqueues the first screen on
+   desc->stream.  dse_batch_rescreen screens again with new targets (same
+   problems) without host-side planning or allocation; with DSE_BATCH_GRAPH
+   the whole screen (resets, 9 kernels) is captured once into a CUDA graph
+   and replayed.  Results are read with dse_batch_fetch / dse_batch_stats,
+   which synchronise; if a problem's candidate buffer overflowed, the batch
+   is screened again (eagerly, thresholds kept) before they return.  The
+   spaces must outlive the batch and must not be used concurrently by other
+   calls while it runs.  The target of problem i has the n_samples of its
+   space. */
+typedef struct {
+  dse_space *space;
+  const double *y;        /* n_samples values, host or device              */
+  int32_t y_on_device;
+  int32_t reserved0;
+} dse_batch_item;
+
+typedef struct {
+  int64_t k;              /* per problem, >= 1                              */
+  int32_t precision;      /* DSE_PREC_FP32 / AUTO (FP32) or DSE_PREC_FP64   */
+  int32_t flags;          /* DSE_BATCH_* bits                               */
+  void *stream;           /* cudaStream_t                                   */
+} dse_batch_desc;
+
+/* dse_batch_desc.flags: replay the screen as a CUDA graph in
+   dse_batch_rescreen (captured at its first call). */
+#define DSE_BATCH_GRAPH 1
+
+typedef struct dse_batch dse_batch;
+
+dse_status dse_sis_screen_batched(const dse_batch_item *items, int32_t n_items, const dse_batch_desc *desc,
+                                  dse_batch **out);
+/* Y: the new targets of every problem, concatenated in item order (problem i
+   has its space's n_samples values), host or device.  Enqueued. */
+dse_status dse_batch_rescreen(dse_batch *batch, const double *Y, int32_t y_on_device);
+/* As dse_topk_fetch, for problem `item`. */
+dse_status dse_batch_fetch(dse_batch *batch, int32_t item, uint64_t *idx, double *score, double *err_bound,
+                           int64_t cap, int64_t *n_out);
+/* As dse_result_stats, for problem `item` (kernel_ms: 0; kernel_launches:
+   launches of the whole batch screen). */
+dse_status dse_batch_stats(dse_batch *batch, int32_t item, dse_stats *out);
+void dse_batch_free(dse_batch *batch);
+
 /* One step of the residual loop: least squares with intercept of y (N FP64
    values) on the columns of the `n_fixed` candidates `fixed` plus one
    candidate from `cand` (n_cand ids), for every candidate; picks the one with

@@ -7,9 +7,11 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "dse_internal.cuh"
+#include "plan.cuh"
 #include "screen_kernels.cuh"
 #include "util.cuh"
 
@@ -23,14 +25,29 @@ RungGeom make_geom(const dse_space *S, int r);
 dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, double *best_rmse, double *coefs,
                       double *residual);
 
-static int sm_count() {
+// Blocked-summation error factors of the CUDA-core kernels for N samples:
+// warp-per-candidate kernels (each lane sums its samples in blocks of 16,
+// then a 5-level shuffle tree) and the pair kernel (blocks of block_len
+// samples, about sqrt(N)); FP64 sums are plain.
+void accum_factors(int64_t N, int prec64, float *gamma_lane, float *gamma_pair, int *block_len) {
+  const double u = prec64 ? 1.1102230246251565e-16 : 5.9604644775390625e-8;
+  int bl = (int)ceil(sqrt((double)N));
+  bl = std::max(16, (bl + 1) / 2 * 2);
+  *block_len = bl;
+  const double nlane = ceil((double)N / 32.0);
+  *gamma_lane = prec64 ? (float)((nlane + 8.0) * u * 1.05) : (float)((16.0 + ceil(nlane / 16.0) + 8.0) * u * 1.05);
+  *gamma_pair = prec64 ? (float)((double)(N + 4) * u * 1.05)
+                       : (float)(((double)bl + ceil((double)N / bl) + 4.0) * u * 1.05);
+}
+
+int sm_count() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
   return n > 0 ? n : 1;
 }
 
-static dse_status check_device() {
+dse_status check_device() {
   int n = 0;
   cudaError_t e = cudaGetDeviceCount(&n);
   if (e != cudaSuccess || n == 0) {
@@ -47,7 +64,7 @@ static dse_status check_device() {
 // (class c = positions [cb[c], cb[c+1])): for every block of BI positions, the
 // blocks of BJ positions from the start of the first class touching it up to
 // the block itself.  Pairs are taken for position_i > position_j only.
-static void class_tiles(const std::vector<int64_t> &cb, int64_t npos, int BI, int BJ, int64_t i_from,
+void class_tiles(const std::vector<int64_t> &cb, int64_t npos, int BI, int BJ, int64_t i_from,
                         std::vector<Tile> &out) {
   // class start of every position
   std::vector<int64_t> start(npos);
@@ -63,15 +80,37 @@ static void class_tiles(const std::vector<int64_t> &cb, int64_t npos, int BI, in
       t.ni = (int16_t)(i1 - i0);
       t.jbase = (int32_t)j0;
       t.nj = (int16_t)std::min<int64_t>(BJ, npos - j0);
-      t.pad = 0;
+      t.prob = 0;
       out.push_back(t);
     }
   }
 }
 
+// The pairs (i > j) of equal unit vectors with i in the newest stored rung,
+// built once per space from its unit classes and kept on the device.
+dse_status equal_unit_pairs(dse_space *sp, cudaStream_t st) {
+  if (sp->n_eq_pairs >= 0) return DSE_OK;
+  const int64_t o = sp->geom.o;
+  std::vector<int2> pairs;
+  for (size_t c = 0; c + 1 < sp->h_class_begin.size(); ++c) {
+    const int64_t b = sp->h_class_begin[c], e = sp->h_class_begin[c + 1];
+    for (int64_t x = b + 1; x < e; ++x) {
+      const int32_t i = sp->h_class_rows[x];  // ids ascend within a class
+      if (i < o) continue;
+      for (int64_t y = b; y < x; ++y) pairs.push_back(make_int2(i, sp->h_class_rows[y]));
+    }
+  }
+  DSE_TRY(dalloc(&sp->eq_pairs, pairs.size(), "equal-unit pairs"));
+  if (!pairs.empty())
+    DSE_CUDA(cudaMemcpyAsync(sp->eq_pairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, st));
+  DSE_CUDA(cudaStreamSynchronize(st));
+  sp->n_eq_pairs = (int64_t)pairs.size();
+  return DSE_OK;
+}
+
 // Triangle tiles over ids: i in [ia, ib] (the rows touched by the pair range),
 // j < i.
-static void triangle_tiles(int64_t ia, int64_t ib, int BI, int BJ, std::vector<Tile> &out) {
+void triangle_tiles(int64_t ia, int64_t ib, int BI, int BJ, std::vector<Tile> &out) {
   for (int64_t i0 = ia; i0 <= ib; i0 += BI) {
     int64_t i1 = std::min(i0 + BI, ib + 1);
     for (int64_t j0 = 0; j0 < i1 - 1; j0 += BJ) {
@@ -80,7 +119,7 @@ static void triangle_tiles(int64_t ia, int64_t ib, int BI, int BJ, std::vector<T
       t.ni = (int16_t)(i1 - i0);
       t.jbase = (int32_t)j0;
       t.nj = (int16_t)std::min<int64_t>(BJ, i1 - 1 - j0);
-      t.pad = 0;
+      t.prob = 0;
       out.push_back(t);
     }
   }
@@ -88,37 +127,82 @@ static void triangle_tiles(int64_t ia, int64_t ib, int BI, int BJ, std::vector<T
 
 // ------------------------------------------------------------- screening
 
-struct Scratch {
-  std::vector<std::pair<void **, size_t>> items;
-  template <typename T>
-  void add(T **p, size_t count) {
-    items.push_back({reinterpret_cast<void **>(p), (count ? count : 1) * sizeof(T)});
-  }
-  dse_status alloc(void **base, size_t *bytes) {
-    size_t tot = 0;
-    for (auto &it : items) tot += (it.second + 255) / 256 * 256;
-    DSE_TRY(dmalloc(base, tot, "screen scratch"));
-    *bytes = tot;
-    size_t off = 0;
-    for (auto &it : items) {
-      *it.first = reinterpret_cast<char *>(*base) + off;
-      off += (it.second + 255) / 256 * 256;
-    }
-    return DSE_OK;
-  }
-};
-
 struct ScreenPlan {
   int prec64, nt, passes;
   int64_t cap;
   std::vector<Tile> mul_tiles, add_tiles;
+  bool use_pairlist = false;     // additive slots from the equal-unit pair list
+  bool add_by_id = false;        // additive tiles over ids (one unit class): rows = identity
   uint64_t id0, id1, p0, p1;     // stored ids and unary flat range
   uint64_t add_total;            // additive slots of the binary block in range
   float gamma_lane, gamma_pair;
   int block_len;
+  // tensor-core path (BF16x3 contraction of the binary block)
+  bool use_tc = false;
+  int ntp = 0, tc_passes = 0, gen_blk = 1;
+  int32_t n_seed_tiles = 0;      // leading product/quotient tiles launched first
+  float gamma_gen = 0.f, gamma_num = 0.f;
+  unsigned char *bsplit = nullptr;
 };
 
-static uint64_t count_slots_mod(uint64_t x, int nb, const std::vector<int> &posset) {
+int tc_ntp_for(int T, int N);
+size_t tc_bsplit_bytes(int ntp, int N);
+void launch_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N, int ntp, unsigned char *out,
+                       cudaStream_t st);
+dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, float gamma_gen,
+                          float gamma_num, int gen_blk, int sms, cudaStream_t st);
+
+// The tensor-core pass structure: each pass contracts `ntp` targets; the
+// CUDA-core kernels (stored/unary candidates, sparse additive pairs) cover the
+// same targets in sub-passes of 16.
+static dse_status run_tc_passes(dse_result *R, const ScreenPlan &plan, void *scr_tiles_mul, void *scr_tiles_add,
+                                ScreenArgs &A, int sms, cudaStream_t st,
+                                const std::function<dse_status(int)> &mark) {
+  dse_space *sp = R->space;
+  for (int tp = 0; tp < plan.tc_passes; ++tp) {
+    const int t0 = tp * plan.ntp, tn = std::min(plan.ntp, R->T - t0);
+    launch_tc_targets(R->y32, R->ldy, t0, tn, (int)sp->N, plan.ntp, plan.bsplit, st);
+    DSE_TRY(mark(0));
+    for (int s0 = 0; s0 < tn; s0 += 16) {
+      A.t0 = t0 + s0;
+      A.T = std::min(16, tn - s0);
+      A.first_pass = tp == 0 && s0 == 0;
+      launch_feature(0, 16, A, plan.id0, plan.id1, plan.p0, plan.p1, plan.gamma_lane, sms, st);
+      if (plan.use_pairlist)
+        launch_pairlist(0, 16, A, sp->eq_pairs, sp->n_eq_pairs, plan.gamma_lane, sms, st);
+    }
+    A.t0 = t0;
+    A.T = tn;
+    A.first_pass = tp == 0;
+    DSE_TRY(mark(1));
+    if (!plan.mul_tiles.empty()) {
+      A.rowid = sp->rowid_ident;
+      const Tile *t0p = reinterpret_cast<const Tile *>(scr_tiles_mul);
+      const int32_t nall = (int32_t)plan.mul_tiles.size(), ns = plan.n_seed_tiles;
+      if (ns > 0) {
+        A.tiles = t0p;
+        A.n_tiles = ns;
+        DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, plan.gamma_gen, plan.gamma_num, plan.gen_blk,
+                               sms, st));
+      }
+      A.tiles = t0p + ns;
+      A.n_tiles = nall - ns;
+      DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
+                             st));
+    }
+    DSE_TRY(mark(2));
+    if (!plan.use_pairlist && !plan.add_tiles.empty()) {
+      A.tiles = reinterpret_cast<const Tile *>(scr_tiles_add);
+      A.n_tiles = (int32_t)plan.add_tiles.size();
+      A.rowid = plan.add_by_id ? sp->rowid_ident : sp->class_rows;
+      DSE_TRY(launch_pair_tc(KIND_ADD, plan.ntp, A, plan.bsplit, plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
+                             st));
+    }
+  }
+  return DSE_OK;
+}
+
+uint64_t count_slots_mod(uint64_t x, int nb, const std::vector<int> &posset) {
   // number of p' in [0, x) with p' mod nb in posset
   uint64_t full = x / (uint64_t)nb, rem = x % (uint64_t)nb;
   uint64_t c = full * posset.size();
@@ -135,6 +219,8 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
   const int nl = R->n_lists;
   DSE_CUDA(cudaMemsetAsync(A.B.count, 0, sizeof(unsigned) * nl, st));
   DSE_CUDA(cudaMemsetAsync(A.B.hist, 0, sizeof(unsigned) * nl * kNumBins, st));
+  DSE_CUDA(cudaMemsetAsync(A.B.hist_hi, 0, sizeof(unsigned) * nl * kNumBins, st));
+  DSE_CUDA(cudaMemsetAsync(A.B.hist_c, 0, sizeof(unsigned) * nl * kCoarse, st));
   DSE_CUDA(cudaMemsetAsync(A.esc_count, 0, sizeof(unsigned), st));
   DSE_CUDA(cudaMemsetAsync(A.stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
   DSE_CUDA(cudaMemsetAsync(S.n_jobs, 0, sizeof(unsigned), st));
@@ -158,7 +244,8 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
     open_group = group;
     return DSE_OK;
   };
-  for (int pass = 0; pass < plan.passes; ++pass) {
+  if (plan.use_tc) DSE_TRY(run_tc_passes(R, plan, scr_tiles_mul, scr_tiles_add, A, sms, st, mark));
+  for (int pass = 0; pass < (plan.use_tc ? 0 : plan.passes); ++pass) {
     A.t0 = pass * plan.nt;
     A.T = std::min(plan.nt, R->T - A.t0);
     A.first_pass = pass == 0;
@@ -166,18 +253,28 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
     launch_feature(plan.prec64, plan.nt, A, plan.id0, plan.id1, plan.p0, plan.p1, plan.gamma_lane, sms, st);
     DSE_TRY(mark(1));
     if (!plan.mul_tiles.empty()) {
-      A.tiles = reinterpret_cast<const Tile *>(scr_tiles_mul);
-      A.n_tiles = (int32_t)plan.mul_tiles.size();
       A.rowid = sp->rowid_ident;
       A.tile_counter = tile_ctr;
+      const Tile *t0p = reinterpret_cast<const Tile *>(scr_tiles_mul);
+      const int32_t nall = (int32_t)plan.mul_tiles.size(), ns = plan.n_seed_tiles;
+      if (ns > 0) {
+        A.tiles = t0p;
+        A.n_tiles = ns;
+        DSE_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(unsigned), st));
+        DSE_TRY(launch_pair(plan.prec64, KIND_MUL, plan.nt, A, plan.block_len, sms, st));
+      }
+      A.tiles = t0p + ns;
+      A.n_tiles = nall - ns;
       DSE_CUDA(cudaMemsetAsync(tile_ctr, 0, sizeof(unsigned), st));
       DSE_TRY(launch_pair(plan.prec64, KIND_MUL, plan.nt, A, plan.block_len, sms, st));
     }
     DSE_TRY(mark(2));
-    if (!plan.add_tiles.empty()) {
+    if (plan.use_pairlist) {
+      launch_pairlist(plan.prec64, plan.nt, A, sp->eq_pairs, sp->n_eq_pairs, plan.gamma_lane, sms, st);
+    } else if (!plan.add_tiles.empty()) {
       A.tiles = reinterpret_cast<const Tile *>(scr_tiles_add);
       A.n_tiles = (int32_t)plan.add_tiles.size();
-      A.rowid = sp->class_rows;
+      A.rowid = plan.add_by_id ? sp->rowid_ident : sp->class_rows;
       A.tile_counter = tile_ctr + 1;
       DSE_CUDA(cudaMemsetAsync(tile_ctr + 1, 0, sizeof(unsigned), st));
       DSE_TRY(launch_pair(plan.prec64, KIND_ADD, plan.nt, A, plan.block_len, sms, st));
@@ -206,8 +303,15 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
     return DSE_ERANGE;
   }
   int prec = d->precision;
-  if (prec == DSE_PREC_AUTO || prec == DSE_PREC_BF16X3) prec = DSE_PREC_FP32;
   ScreenPlan plan{};
+  // the tensor-core contraction for many targets (per-target lists only)
+  if (d->mode == DSE_MODE_PER_TARGET &&
+      (prec == DSE_PREC_BF16X3 || (prec == DSE_PREC_AUTO && d->n_targets >= 8))) {
+    plan.use_tc = true;
+    prec = DSE_PREC_BF16X3;
+  } else if (prec == DSE_PREC_AUTO || prec == DSE_PREC_BF16X3) {
+    prec = DSE_PREC_FP32;
+  }
   plan.prec64 = prec == DSE_PREC_FP64;
   plan.nt = d->n_targets == 1 ? 1 : 16;
   plan.passes = (d->n_targets + plan.nt - 1) / plan.nt;
@@ -230,6 +334,10 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   // binary block range in pair space
   const uint64_t bb = std::max(pb, g.um), be = std::max(pe, g.um);
   int BI = plan.nt == 1 ? 32 : 16, BJ = BI;
+  if (plan.use_tc) {
+    BI = 16;  // 128-pair tensor-core tiles
+    BJ = 8;
+  }
   std::vector<int> addpos;
   if (g.nb > 0 && be > bb) {
     const uint64_t q0 = (bb - g.um) / g.nb, q1 = (be - g.um - 1) / g.nb;
@@ -245,25 +353,64 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
         addpos.push_back(s);
       }
     }
-    if (any_mul) triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.mul_tiles);
+    if (any_mul) {
+      triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.mul_tiles);
+      // A large tile list is launched in two parts: every 64th tile first, so
+      // that the thresholds have risen from a spread sample of the space
+      // before the bulk of the candidates is filtered.
+      const size_t nt = plan.mul_tiles.size();
+      if (nt >= 64 * 64) {
+        std::vector<Tile> seed, rest;
+        seed.reserve(nt / 64 + 1);
+        rest.reserve(nt);
+        for (size_t t = 0; t < nt; ++t) (t % 64 == 0 ? seed : rest).push_back(plan.mul_tiles[t]);
+        plan.n_seed_tiles = (int32_t)seed.size();
+        seed.insert(seed.end(), rest.begin(), rest.end());
+        plan.mul_tiles.swap(seed);
+      }
+    }
     if (any_add) {
-      // positions within class_rows; rows of ids >= o only matter, but classes
-      // interleave old and new ids, so every block is visited.
-      class_tiles(sp->h_class_begin, sp->n, BI, BJ, 0, plan.add_tiles);
+      const bool one_class = !(sp->unit_check_addsub && sp->D > 0) || sp->h_class_begin.size() <= 2;
+      if (one_class) {
+        // every pair may be added: the same id triangle as the products,
+        // restricted to the rows of the range
+        triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.add_tiles);
+        plan.add_by_id = true;
+      } else {
+        // sparse equal-unit pairs: an explicit list (built once per space);
+        // dense: tiles over the unit classes (positions within class_rows;
+        // classes interleave old and new ids, so every block is visited)
+        DSE_TRY(equal_unit_pairs(sp, st));
+        const uint64_t mm = (uint64_t)(g.n - g.o), oo = (uint64_t)g.o;
+        const uint64_t all_pairs = mm ? tri(mm) + mm * oo : 0;
+        if ((uint64_t)sp->n_eq_pairs * 4 <= all_pairs)
+          plan.use_pairlist = true;
+        else
+          class_tiles(sp->h_class_begin, sp->n, BI, BJ, 0, plan.add_tiles);
+      }
       plan.add_total = count_slots_mod(be - g.um, g.nb, addpos) - count_slots_mod(bb - g.um, g.nb, addpos);
     }
   }
   // accumulation error factors
   const double u32 = 5.9604644775390625e-8, u64 = 1.1102230246251565e-16;
   const double u = plan.prec64 ? u64 : u32;
-  int bl = (int)ceil(sqrt((double)N));
-  bl = std::max(16, (bl + 1) / 2 * 2);
-  plan.block_len = bl;
-  const double nlane = ceil((double)N / 32.0);
-  plan.gamma_lane = (float)((16.0 + ceil(nlane / 16.0) + 8.0) * u * 1.05);
-  plan.gamma_pair = plan.prec64 ? (float)((double)(N + 4) * u * 1.05)
-                                : (float)(((double)bl + ceil((double)N / bl) + 4.0) * u * 1.05);
-  if (plan.prec64) plan.gamma_lane = (float)((nlane + 8.0) * u * 1.05);
+  accum_factors(N, plan.prec64, &plan.gamma_lane, &plan.gamma_pair, &plan.block_len);
+  if (plan.use_tc) {
+    plan.ntp = tc_ntp_for(d->n_targets, (int)N);
+    plan.tc_passes = (d->n_targets + plan.ntp - 1) / plan.ntp;
+    const int nchunks = (int)((N + 31) / 32);
+    plan.gen_blk = std::max(1, (int)lround(sqrt(nchunks / 16.0)));
+    // generation sums: 16 samples of each chunk per thread, blocks of
+    // gen_blk chunks, the two halves added at the end
+    plan.gamma_gen = (float)((16.0 * plan.gen_blk + ceil((double)nchunks / plan.gen_blk) + 6.0) * u32 * 1.05);
+    // contraction: BF16x3 split (3.01 * 2^-18) plus 2u per tensor-core
+    // accumulation step (3 products x 2 k-steps per chunk, up to 16 chunks per
+    // TMEM block) and the register drain of the blocks, times a safety factor 4
+    const int nblocks = (nchunks + 15) / 16;
+    const double steps = 3.0 * 2.0 * std::min(nchunks, 16);
+    plan.gamma_num = (float)(4.0 * (2.0 * steps + nblocks + 2.0) * u32 + 3.02 * 3.814697265625e-6 +
+                             (double)plan.gamma_gen);
+  }
 
   dse_result *R = new (std::nothrow) dse_result();
   if (!R) {
@@ -301,6 +448,11 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   sc.add(&A.B.eps, (size_t)n_lists * cap);
   sc.add(&A.B.count, (size_t)n_lists);
   sc.add(&A.B.hist, (size_t)n_lists * kNumBins);
+  sc.add(&A.B.hist_hi, (size_t)n_lists * kNumBins);
+  sc.add(&A.B.hist_c, (size_t)n_lists * kCoarse);
+  sc.add(&S.state, (size_t)n_lists);
+  sc.add(&S.colL, (size_t)n_lists * cap);
+  sc.add(&S.colH, (size_t)n_lists * cap);
   sc.add(&A.B.theta, (size_t)n_lists);
   const int64_t esc_cap = 1 << 20;
   sc.add(&A.esc_id, (size_t)esc_cap);
@@ -328,6 +480,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   sc.add(&tmul, plan.mul_tiles.size());
   sc.add(&tadd, plan.add_tiles.size());
   sc.add(&tile_ctr, 2);
+  sc.add(&plan.bsplit, plan.use_tc ? tc_bsplit_bytes(plan.ntp, (int)N) : 1);
   dse_status s = sc.alloc(&R->scratch, &R->scratch_bytes);
   if (s != DSE_OK) {
     delete R;
@@ -539,10 +692,17 @@ dse_status dse_build_space(const dse_space_desc *d, dse_space **out) {
     return DSE_EINVAL;
   }
   DSE_TRY(check_device());
-  return build_space(d, out);
+  AllocStream as((cudaStream_t)d->stream);
+  dse_status st = build_space(d, out);
+  if (st == DSE_OK) (*out)->stream = (cudaStream_t)d->stream;
+  return st;
 }
 
-void dse_space_free(dse_space *s) { space_release(s); }
+void dse_space_free(dse_space *s) {
+  if (!s) return;
+  AllocStream as(s->stream);
+  space_release(s);
+}
 
 dse_status dse_space_size(const dse_space *s, int64_t *n_stored, uint64_t *n_total) {
   clear_error();
@@ -649,13 +809,13 @@ dse_status dse_sis_screen(dse_space *s, const dse_screen_desc *d, dse_result **o
     return DSE_EINVAL;
   }
   DSE_TRY(check_device());
+  AllocStream as((cudaStream_t)d->stream);
   return screen_impl(s, d, out);
 }
 
 void dse_result_free(dse_result *r) {
   if (!r) return;
-  if (r->stream) cudaStreamSynchronize(r->stream);
-  else cudaDeviceSynchronize();
+  AllocStream as(r->stream);  // the free is ordered after the result's work
   dfree(r->scratch);
   if (r->keep && r->keep_free) r->keep_free(r->keep);
   for (auto &t : r->timing) {
@@ -708,6 +868,7 @@ dse_status dse_ls_refit(dse_space *s, const dse_refit_desc *d, uint64_t *best_id
     return DSE_EINVAL;
   }
   DSE_TRY(check_device());
+  AllocStream as((cudaStream_t)d->stream);
   return refit_impl(s, d, best_id, best_rmse, coefs, residual);
 }
 

@@ -178,7 +178,7 @@ __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const doubl
                             const double *mean64, const double *rmean64, const double *min64, const double *max64,
                             const double *minabs64, const double *maxabs64, const double *minabsnz64,
                             const int32_t *units, double exp_arg_max, float4 *fa, float2 *fr, uint32_t *flags,
-                            uint64_t *ukey) {
+                            uint64_t *ukey, float *fnorm) {
   int64_t total = n * ld;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     v32[e] = (e % ld < N) ? __double2float_rn(v64[e]) : 0.0f;
@@ -212,6 +212,9 @@ __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const doubl
     flags[f] = fl;
     ukey[2 * f] = k0;
     ukey[2 * f + 1] = k1;
+    double s2 = 0.0;
+    for (int64_t s = 0; s < N; ++s) s2 = __fma_rn(v64[f * ld + s], v64[f * ld + s], s2);
+    fnorm[f] = __double2float_ru(__dsqrt_ru(s2 * (1.0 + 1e-12)));
   }
 }
 
@@ -520,11 +523,12 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   DSE_TRY(dalloc(&S->v32, (size_t)n * ld, "FP32 feature rows"));
   DSE_TRY(dalloc(&S->fa, n, "helpers"));
   DSE_TRY(dalloc(&S->fr, n, "helpers"));
+  DSE_TRY(dalloc(&S->fnorm, n, "helpers"));
   DSE_TRY(dalloc(&S->flags, n, "flags"));
   DSE_TRY(dalloc(&S->ukey, 2 * n, "unit keys"));
   k_fp32_prep<<<grid_for(n * ld, 256), 256, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, T.mean64, T.rmean64, T.min64,
                                                      T.max64, T.minabs64, T.maxabs64, T.minabsnz64, T.units,
-                                                     S->exp_arg_max, S->fa, S->fr, S->flags, S->ukey);
+                                                     S->exp_arg_max, S->fa, S->fr, S->flags, S->ukey, S->fnorm);
   dfree(T.minabsnz64);
 
   // --- host copies for decoding and the unit classes
@@ -587,9 +591,10 @@ dse_status build_space(const dse_space_desc *d, dse_space **out) {
 dse_status space_release(dse_space *S) {
   if (!S) return DSE_OK;
   dfree(S->v64); dfree(S->v32); dfree(S->mean64); dfree(S->rmean64); dfree(S->min64); dfree(S->max64);
-  dfree(S->minabs64); dfree(S->maxabs64); dfree(S->fa); dfree(S->fr); dfree(S->flags); dfree(S->cplx);
+  dfree(S->minabs64); dfree(S->maxabs64); dfree(S->fa); dfree(S->fr); dfree(S->fnorm); dfree(S->flags); dfree(S->cplx);
   dfree(S->op); dfree(S->units); dfree(S->ca); dfree(S->cb); dfree(S->ukey); dfree(S->rowid_ident);
   dfree(S->class_rows);
+  dfree(S->eq_pairs);
   delete S;
   return DSE_OK;
 }
@@ -616,6 +621,7 @@ FeatTable table_of(const dse_space *S) {
   F.cb = S->cb;
   F.units = S->units;
   F.ukey = S->ukey;
+  F.fnorm = S->fnorm;
   return F;
 }
 

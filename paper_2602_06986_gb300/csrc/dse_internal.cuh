@@ -46,6 +46,7 @@ struct FeatTable {
   const int64_t *ca, *cb;
   const int32_t *units;                      // [n][kMaxDims] scaled exponents
   const uint64_t *ukey;                      // [n][2] packed exponents (16 bits each)
+  const float *fnorm;                        // RU(sqrt(sum_s x_s^2))
 };
 
 // Rung-k geometry: global id = n_stored + p.
@@ -107,9 +108,19 @@ struct CandBufs {
   float *eps;          // [lists][cap]
   unsigned int *count; // [lists]
   int64_t cap;
-  unsigned int *hist;  // [lists][kNumBins]
+  unsigned int *hist;  // [lists][kNumBins]   buffered lower bounds by bin
+  unsigned int *hist_c;// [lists][kCoarse]    the same, kFine bins per coarse bin
+  unsigned int *hist_hi;// [lists][kNumBins]  buffered upper bounds by bin
   float *theta;        // [lists] (as float; raised monotonically with atomicMax on bits)
 };
+
+constexpr int kFine = 64;
+constexpr int kCoarse = kNumBins / kFine;
+
+__host__ __device__ inline int score_bin(float x) {
+  int b = x > 0.f ? (int)(x * (float)kNumBins) : 0;
+  return b > kNumBins - 1 ? kNumBins - 1 : b;
+}
 
 // Statistics counters on the device (unsigned long long for atomics).
 enum {
@@ -130,7 +141,15 @@ enum {
 struct Tile {
   int32_t ibase, jbase;
   int16_t ni, nj;
-  int32_t pad;
+  int32_t prob;  // problem of a batched screen (0 otherwise)
+};
+
+// A run of consecutive work units of one problem of a batched screen
+// (candidates of the stored/unary group, or pairs of the pair list).
+struct Job {
+  int32_t prob;
+  int32_t count;
+  int64_t first;
 };
 
 // Arguments common to the screen kernels.
@@ -172,6 +191,12 @@ struct ScreenArgs {
   int32_t slot_pos[6];         // flat slot position of each binary op code 6..11 (-1 = off)
   int32_t first_pass;          // count statistics and escalate only in the first target pass
   int32_t group;               // kernel group for the per-group valid counters
+  // batched screens: per-problem accumulation factors and the problem index
+  // recorded with each escalated candidate
+  float gamma_lane;            // warp-per-candidate kernels
+  int32_t block_len;           // pair kernel blocking of the FP32 sums
+  int32_t prob;
+  uint32_t *esc_prob;          // escalation list: problem of each entry (batched only)
 };
 
 // Launch bookkeeping (process-wide count of the library's kernel launches).
@@ -267,6 +292,7 @@ struct dse_space {
          *minabs64 = nullptr, *maxabs64 = nullptr;
   float4 *fa = nullptr;
   float2 *fr = nullptr;
+  float *fnorm = nullptr;
   uint32_t *flags = nullptr;
   int32_t *cplx = nullptr, *op = nullptr, *units = nullptr;
   int64_t *ca = nullptr, *cb = nullptr;
@@ -280,7 +306,10 @@ struct dse_space {
   std::vector<int32_t> h_class_rows;            // feature ids sorted by (unit key, id)
   std::vector<int64_t> h_class_begin;           // class boundaries into h_class_rows
   int32_t *class_rows = nullptr;
+  int2 *eq_pairs = nullptr;                     // equal-unit pairs (i > j, i in the newest rung)
+  int64_t n_eq_pairs = -1;                      // -1: not built yet
   dse::RungGeom geom;
+  cudaStream_t stream = nullptr;   // build stream: the space's memory is freed in its order
   dse::FeatTable table() const;
 };
 

@@ -153,6 +153,137 @@ __global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double 
   }
 }
 
+// The same fit with one block of kWide threads per candidate (more warps in
+// flight per SM than a warp per candidate when the candidate list is short).
+constexpr int kWide = 128;
+
+template <int NV>
+__device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum64(v[i]);
+  if (lane == 0)
+    for (int i = 0; i < NV; ++i) sm[w * NV + i] = v[i];
+  __syncthreads();
+  for (int i = 0; i < NV; ++i) {
+    double t = 0.0;
+    for (int ww = 0; ww < kWide / 32; ++ww) t += sm[ww * NV + i];
+    v[i] = t;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, int64_t n_stored, const double *y,
+                                                      const double *fixed_cols, int nf, const uint64_t *fixed_ids,
+                                                      const uint64_t *cand, int64_t n_cand, double *rmse_out,
+                                                      double *beta_out) {
+  __shared__ double sm[(kWide / 32) * 20];
+  const int64_t w = blockIdx.x;
+  if (w >= n_cand) return;
+  const int64_t N = F.N;
+  const int p = nf + 1;
+  const uint64_t gid = cand[w];
+  bool dup = false;
+  for (int j = 0; j < nf; ++j) dup |= fixed_ids[j] == gid;
+  if (dup) {
+    if (threadIdx.x == 0) rmse_out[w] = INFINITY;
+    return;
+  }
+  int op;
+  int64_t a, b;
+  decode_any(G, n_stored, gid, &op, &a, &b);
+  auto xval = [&](int c, int64_t s) -> double {
+    return c < nf ? fixed_cols[(int64_t)c * N + s] : col_value(F, G, n_stored, op, a, b, s);
+  };
+  double mv[kMaxP + 1] = {0, 0, 0, 0, 0};  // column means, then y's
+  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+    for (int c = 0; c < p; ++c) mv[c] += xval(c, s);
+    mv[kMaxP] += y[s];
+  }
+  block_sum_arr<kMaxP + 1>(mv, sm);
+  double m[kMaxP];
+  for (int c = 0; c < kMaxP; ++c) m[c] = mv[c] / (double)N;
+  const double my = mv[kMaxP] / (double)N;
+  // packed: Gram lower triangle (10), g (4), norms (4)
+  double acc[18];
+  for (int i = 0; i < 18; ++i) acc[i] = 0.0;
+  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+    double xc[kMaxP];
+    for (int c = 0; c < p; ++c) {
+      double v = xval(c, s);
+      xc[c] = v - m[c];
+      acc[14 + c] = fma(v, v, acc[14 + c]);
+    }
+    double yc = y[s] - my;
+    int t = 0;
+    for (int c = 0; c < kMaxP; ++c)
+      for (int d = 0; d <= c; ++d, ++t)
+        if (c < p) acc[t] = fma(xc[c], xc[d], acc[t]);
+    for (int c = 0; c < p; ++c) acc[10 + c] = fma(xc[c], yc, acc[10 + c]);
+  }
+  block_sum_arr<18>(acc, sm);
+  double Gm[kMaxP][kMaxP] = {}, g[kMaxP], nrm[kMaxP];
+  {
+    int t = 0;
+    for (int c = 0; c < kMaxP; ++c)
+      for (int d = 0; d <= c; ++d, ++t) Gm[c][d] = acc[t];
+    for (int c = 0; c < kMaxP; ++c) {
+      g[c] = acc[10 + c];
+      nrm[c] = sqrt(acc[14 + c]);
+    }
+  }
+  double L[kMaxP][kMaxP] = {};
+  bool ok = true;
+  for (int c = 0; c < p && ok; ++c) {
+    double dsum = Gm[c][c];
+    for (int k = 0; k < c; ++k) dsum -= L[c][k] * L[c][k];
+    if (!(dsum > 0.0)) {
+      ok = false;
+      break;
+    }
+    L[c][c] = sqrt(dsum);
+    if (!(L[c][c] > 1e-12 * nrm[c])) {
+      ok = false;
+      break;
+    }
+    for (int r = c + 1; r < p; ++r) {
+      double v = Gm[r][c];
+      for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
+      L[r][c] = v / L[c][c];
+    }
+  }
+  double beta[kMaxP + 1] = {};
+  if (ok) {
+    double z[kMaxP];
+    for (int c = 0; c < p; ++c) {
+      double v = g[c];
+      for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
+      z[c] = v / L[c][c];
+    }
+    for (int c = p - 1; c >= 0; --c) {
+      double v = z[c];
+      for (int k = c + 1; k < p; ++k) v -= L[k][c] * beta[k + 1];
+      beta[c + 1] = v / L[c][c];
+    }
+    double b0 = my;
+    for (int c = 0; c < p; ++c) b0 -= beta[c + 1] * m[c];
+    beta[0] = b0;
+  }
+  double rss[1] = {0.0};
+  if (ok) {
+    for (int64_t s = threadIdx.x; s < N; s += kWide) {
+      double f = beta[0];
+      for (int c = 0; c < p; ++c) f = fma(beta[c + 1], xval(c, s), f);
+      double r = y[s] - f;
+      rss[0] = fma(r, r, rss[0]);
+    }
+  }
+  block_sum_arr<1>(rss, sm);
+  if (threadIdx.x == 0) {
+    rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
+    for (int c = 0; c <= kMaxP; ++c) beta_out[w * (kMaxP + 1) + c] = ok && c <= p ? beta[c] : 0.0;
+  }
+}
+
 // Index of the smallest RMSE (ties: lower id); one block.
 __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best) {
   __shared__ double bv[1024];
@@ -251,7 +382,7 @@ dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, 
   const FeatTable F = table_of(S);
   note_launches(3 + (nf ? 1 : 0));
   if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
-  k_refit<<<(unsigned)((nc * 32 + 255) / 256), 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, fid, cand, nc, rm, beta);
+  k_refit_wide<<<(unsigned)nc, kWide, 0, st>>>(F, S->geom, S->n, y, fc, nf, fid, cand, nc, rm, beta);
   k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best);
   k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
   int64_t hb = -1;

@@ -25,6 +25,8 @@
 // the buffered lower bounds (the k-th best lower bound is never below it).
 #include <math.h>
 
+#include <algorithm>
+
 #include "dse_internal.cuh"
 #include "eval64.cuh"
 #include "screen_common.cuh"
@@ -37,13 +39,11 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 
 // ----------------------------------------------------------- target prep
 
-// Centre and normalise each target in FP64 (one block per target).
-__global__ void k_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,
-                          float *ysum32, int *err) {
+// Centre and normalise one target in FP64 (whole block): row y of N values
+// into rows y64 / y32 of ldy (zero beyond N) and the sum of the FP32 row.
+__device__ void target_prep(const double *y, int64_t N, int32_t ldy, double *y64, float *y32, float *ysum32,
+                            int *err) {
   __shared__ double red[32];
-  const int t = blockIdx.x;
-  if (t >= T) return;
-  const double *y = Y + (int64_t)t * ldY;
   auto block_sum = [&](double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -71,65 +71,32 @@ __global__ void k_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_
   for (int64_t i = threadIdx.x; i < ldy; i += blockDim.x) {
     double v = i < N ? (y[i] - mean) * inv : 0.0;
     float f = __double2float_rn(v);
-    y64[(int64_t)t * ldy + i] = v;
-    y32[(int64_t)t * ldy + i] = f;
+    y64[i] = v;
+    y32[i] = f;
     fs += (double)f;
   }
   fs = block_sum(fs);
-  if (threadIdx.x == 0) ysum32[t] = (float)fs;
+  if (threadIdx.x == 0) *ysum32 = (float)fs;
+}
+
+// One block per target.
+__global__ void k_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,
+                          float *ysum32, int *err) {
+  const int t = blockIdx.x;
+  if (t >= T) return;
+  target_prep(Y + (int64_t)t * ldY, N, ldy, y64 + (int64_t)t * ldy, y32 + (int64_t)t * ldy, ysum32 + t, err);
+}
+
+// Batched screens: one block per problem, its target at Y + yoff[p] with the
+// problem's own sample count, into row p.
+__global__ void k_targets_batched(const double *Y, const int64_t *yoff, const ScreenArgs *args, int n,
+                                  int32_t ldy, double *y64, float *y32, float *ysum32, int *err) {
+  const int p = blockIdx.x;
+  if (p >= n) return;
+  target_prep(Y + yoff[p], args[p].N, ldy, y64 + (int64_t)p * ldy, y32 + (int64_t)p * ldy, ysum32 + p, err);
 }
 
 // ------------------------------------------------------ shared epilogue
-
-struct LaneStats {
-  unsigned r[6];
-  unsigned evaluated, escalated, seen;
-  __device__ void zero() {
-    for (int i = 0; i < 6; ++i) r[i] = 0;
-    evaluated = escalated = seen = 0;
-  }
-};
-
-__device__ __forceinline__ void flush_stats(const ScreenArgs &A, LaneStats &ls) {
-  if (!A.first_pass) {
-    ls.zero();
-    return;
-  }
-  {
-    unsigned v = ls.seen;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&A.stats[ST_ADD_SEEN], (unsigned long long)v);
-  }
-  for (int i = 0; i < 6; ++i) {
-    unsigned v = ls.r[i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&A.stats[ST_REASON0 + i], (unsigned long long)v);
-  }
-  {
-    unsigned v = ls.r[DSE_VALID];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&A.stats[ST_VALID_G0 + A.group], (unsigned long long)v);
-  }
-  unsigned e = ls.evaluated, x = ls.escalated;
-  for (int o = 16; o > 0; o >>= 1) {
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-    x += __shfl_xor_sync(0xffffffffu, x, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (e) atomicAdd(&A.stats[ST_EVALUATED], (unsigned long long)e);
-    if (x) atomicAdd(&A.stats[ST_ESCALATED], (unsigned long long)x);
-  }
-  ls.zero();
-}
-
-__device__ __forceinline__ void escalate(const ScreenArgs &A, uint64_t gid) {
-  if (!A.first_pass) return;
-  unsigned pos = atomicAdd(A.esc_count, 1u);
-  if ((int64_t)pos < A.esc_cap)
-    A.esc_id[pos] = gid;
-  else
-    atomicAdd(&A.stats[ST_ESC_OVERFLOW], 1ull);
-}
 
 // Score a candidate's statistics against the pass's targets and push.
 // Warp-cooperative: all lanes call with the same loop structure.
@@ -215,129 +182,174 @@ __device__ __forceinline__ double unary_eval<double>(int op, double a, double c)
   }
 }
 
-// W (per-sample evaluation error / u) of a unary op on feature f with shift c.
-__device__ __forceinline__ double unary_W(const FeatTable &F, int op, int64_t f, double c) {
-  const double M = F.maxabs64[f], m = F.minabs64[f], ac = fabs(c);
+// Evaluation-error coefficients (E = u (kappa ||V|| + lambda)) of a unary op
+// on feature f with shift c: per sample the operand's rounding, the op's own
+// bound (x^2 and x^3: exact products then the FMA; rcp.approx 1 ulp; sqrtf
+// correctly rounded; expf 2 ulp plus the input perturbation |A| u; logf 1 ulp
+// plus an absolute u from the input) and the rounding of the shift.
+template <typename R>
+__device__ __forceinline__ EvalErr<R> unary_err(const FeatTable &F, int op, int64_t f, R c, R sqrtN) {
+  const R ac = c < R(0) ? -c : c;
+  R kappa;
+  R lam = ac * sqrtN;
   switch (op) {
-    case DSE_OP_SQUARE: return 1.01 * (3.0 * M * M + ac);
-    case DSE_OP_CUBE: return 1.01 * (5.0 * M * M * M + ac);
-    case DSE_OP_INV: return 1.01 * (4.0 / m + ac);
-    case DSE_OP_SQRT: return 1.01 * (2.5 * sqrt(M) + ac);
-    case DSE_OP_EXP: {
-      double E = exp(F.max64[f]) * 1.0000001;
-      return 1.01 * ((5.0 + M) * E + ac);
-    }
-    case DSE_OP_LOG: {
-      double L = fmax(fabs(log(F.min64[f])), fabs(log(F.max64[f])));
-      return 1.01 * (3.0 * L + 1.0 + ac);
-    }
-    default: return 1.01 * (2.0 * M + ac);
+    case DSE_OP_SQUARE: kappa = R(3.01); break;
+    case DSE_OP_CUBE: kappa = R(5.01); break;
+    case DSE_OP_INV: kappa = R(4.01); break;
+    case DSE_OP_SQRT: kappa = R(2.51); break;
+    case DSE_OP_EXP: kappa = R(5.01) + (R)F.fa[f].z; break;
+    case DSE_OP_LOG:
+      kappa = R(3.01);
+      lam += R(1.01) * sqrtN;
+      break;
+    default: kappa = R(2.01); break;
   }
+  return EvalErr<R>{kappa, lam};
+}
+
+// One candidate of the stored/unary group (whole warp, lanes over samples):
+// index w < nid is stored id id0 + w, otherwise unary flat index
+// p0 + (w - nid) of rung k.
+template <typename R, int NT>
+__device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, uint64_t id0, uint64_t nid,
+                                             uint64_t p0, R gamma, const R *ysum, LaneStats &ls) {
+  const int lane = threadIdx.x & 31;
+  const R u = sizeof(R) == 4 ? R(5.9604644775390625e-8) : R(1.1102230246251565e-16);
+  const int64_t Ns = A.N;
+  const int T = A.T, t0 = A.t0;
+  const int64_t ldy = A.ldy;
+  const R N = (R)Ns, invN = (R)A.invN, sqrtN = Num<R>::sqrt_(N);
+  const R fmin = (R)A.fmin_std_rel64;
+  const R *Y = sizeof(R) == 4 ? (const R *)A.y32 : (const R *)A.y64;
+  int op;
+  int64_t f;
+  uint64_t gid;
+  int reason = DSE_VALID;
+  if (w < nid) {
+    gid = id0 + w;
+    f = (int64_t)gid;
+    op = DSE_OP_PRIMARY;
+  } else {
+    uint64_t p = p0 + (w - nid);
+    gid = (uint64_t)A.n_stored + p;
+    int64_t b;
+    decode_flat(A.G, p, &op, &f, &b);
+    // unit (exp/log need a dimensionless operand), complexity, domain, magnitude
+    if ((op == DSE_OP_EXP || op == DSE_OP_LOG) && A.explog_dimensionless && !(A.F.flags[f] & F_DIMLESS))
+      reason = DSE_R_UNIT;
+    else if (A.max_complexity > 0 && A.F.cplx[f] + 1 > A.max_complexity)
+      reason = DSE_R_COMPLEXITY;
+    else {
+      double ea = (op == DSE_OP_EXP && (A.F.flags[f] & F_EXP_MAG)) ? INFINITY : -INFINITY;
+      reason = domain_magnitude64(op, A.F.min64[f], A.F.max64[f], A.F.minabs64[f], A.F.maxabs64[f], 0.0, 0.0,
+                                  A.fmax64, ea);
+    }
+  }
+  if (reason != DSE_VALID) {
+    if (lane == 0) ls.r[reason]++;
+    return;
+  }
+  if (sizeof(R) == 4 && !(A.F.flags[f] & F_FP32_SAFE)) {
+    if (lane == 0) {
+      escalate(A, gid);
+      ls.escalated++;
+    }
+    return;
+  }
+  const R *x = sizeof(R) == 4 ? (const R *)(A.F.v32 + f * A.F.ld) : (const R *)(A.F.v64 + f * A.F.ld);
+  const R c = unary_eval<R>(op, x[0], R(0));
+  const EvalErr<R> ee = unary_err<R>(A.F, op, f, c, sqrtN);
+  R S1 = 0, S2 = 0, Sy[NT];
+  R o1 = 0, o2 = 0, oy[NT];
+  for (int t = 0; t < NT; ++t) Sy[t] = oy[t] = 0;
+  int blk = 0;
+  for (int64_t s = lane; s < Ns; s += 32) {
+    R v = unary_eval<R>(op, x[s], c);
+    S1 += v;
+    S2 = Num<R>::fma_(v, v, S2);
+    for (int t = 0; t < NT; ++t)
+      if (t < T) Sy[t] = Num<R>::fma_(v, Y[(int64_t)(t0 + t) * ldy + s], Sy[t]);
+    if (sizeof(R) == 4 && ++blk == 16) {
+      blk = 0;
+      o1 += S1; o2 += S2; S1 = 0; S2 = 0;
+      for (int t = 0; t < NT; ++t) { oy[t] += Sy[t]; Sy[t] = 0; }
+    }
+  }
+  S1 += o1;
+  S2 += o2;
+  for (int t = 0; t < NT; ++t) Sy[t] += oy[t];
+  for (int o = 16; o > 0; o >>= 1) {
+    S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+    for (int t = 0; t < NT; ++t) Sy[t] += __shfl_xor_sync(0xffffffffu, Sy[t], o);
+  }
+  CandInterval<R> ci = cand_interval<R>(S1, S2, N, invN, sqrtN, c, ee, gamma, u, fmin);
+  if (ci.realised == 0) {
+    if (lane == 0) ls.r[DSE_R_REALISED]++;
+    return;
+  }
+  if (ci.realised == 2) {
+    if (lane == 0) {
+      escalate(A, gid);
+      ls.escalated++;
+    }
+    return;
+  }
+  if (lane == 0) {
+    ls.r[DSE_VALID]++;
+    ls.evaluated++;
+  }
+  unsigned pushed = score_and_push<R, NT>(A, lane == 0, gid, ci, S1, Sy, invN, gamma, u, ysum);
+  refresh_pushed<NT>(A, pushed);
+}
+
+template <typename R, int NT>
+__device__ __forceinline__ void load_ysum(const ScreenArgs &A, R (&ysum)[NT]) {
+#pragma unroll
+  for (int t = 0; t < NT; ++t) ysum[t] = (sizeof(R) == 4 && t < A.T) ? (R)A.ysum32[A.t0 + t] : R(0);
 }
 
 // Candidates: stored ids [id0, id1) then unary flat indices [p0, p1).
 template <typename R, int NT>
 __global__ void __launch_bounds__(256) k_feature(const ScreenArgs A, uint64_t id0, uint64_t id1, uint64_t p0,
                                                  uint64_t p1, float gamma_lane) {
-  const int lane = threadIdx.x & 31;
   const uint64_t nid = id1 - id0, ncand = nid + (p1 - p0);
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  const R u = sizeof(R) == 4 ? R(5.9604644775390625e-8) : R(1.1102230246251565e-16);
-  const R gamma = (R)gamma_lane;
-  const R N = (R)A.N, invN = (R)A.invN, sqrtN = Num<R>::sqrt_(N);
-  const R fmin = (R)A.fmin_std_rel64;
-  const R *Y = sizeof(R) == 4 ? (const R *)A.y32 : (const R *)A.y64;
   R ysum[NT];
-  for (int t = 0; t < NT; ++t) ysum[t] = 0;
-  if (sizeof(R) == 4) {
-    for (int t = 0; t < NT; ++t)
-      if (t < A.T) ysum[t] = (R)A.ysum32[A.t0 + t];
-  }
+  load_ysum<R, NT>(A, ysum);
   LaneStats ls;
   ls.zero();
-  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ncand; w += warps) {
-    int op;
-    int64_t f;
-    uint64_t gid;
-    int reason = DSE_VALID;
-    if (w < nid) {
-      gid = id0 + w;
-      f = (int64_t)gid;
-      op = DSE_OP_PRIMARY;
-    } else {
-      uint64_t p = p0 + (w - nid);
-      gid = (uint64_t)A.n_stored + p;
-      int64_t b;
-      decode_flat(A.G, p, &op, &f, &b);
-      // unit (exp/log need a dimensionless operand), complexity, domain, magnitude
-      if ((op == DSE_OP_EXP || op == DSE_OP_LOG) && A.explog_dimensionless && !(A.F.flags[f] & F_DIMLESS))
-        reason = DSE_R_UNIT;
-      else if (A.max_complexity > 0 && A.F.cplx[f] + 1 > A.max_complexity)
-        reason = DSE_R_COMPLEXITY;
-      else {
-        double ea = (op == DSE_OP_EXP && (A.F.flags[f] & F_EXP_MAG)) ? INFINITY : -INFINITY;
-        reason = domain_magnitude64(op, A.F.min64[f], A.F.max64[f], A.F.minabs64[f], A.F.maxabs64[f], 0.0, 0.0,
-                                    A.fmax64, ea);
-      }
-    }
-    if (reason != DSE_VALID) {
-      if (lane == 0) ls.r[reason]++;
-      continue;
-    }
-    if (sizeof(R) == 4 && !(A.F.flags[f] & F_FP32_SAFE)) {
-      if (lane == 0) {
-        escalate(A, gid);
-        ls.escalated++;
-      }
-      continue;
-    }
-    const R *x = sizeof(R) == 4 ? (const R *)(A.F.v32 + f * A.F.ld) : (const R *)(A.F.v64 + f * A.F.ld);
-    const R c = unary_eval<R>(op, x[0], R(0));
-    const R W = (R)unary_W(A.F, op, f, (double)c);
-    R S1 = 0, S2 = 0, Sy[NT];
-    R o1 = 0, o2 = 0, oy[NT];
-    for (int t = 0; t < NT; ++t) Sy[t] = oy[t] = 0;
-    int blk = 0;
-    for (int64_t s = lane; s < A.N; s += 32) {
-      R v = unary_eval<R>(op, x[s], c);
-      S1 += v;
-      S2 = Num<R>::fma_(v, v, S2);
-      for (int t = 0; t < NT; ++t)
-        if (t < A.T) Sy[t] = Num<R>::fma_(v, Y[(int64_t)(A.t0 + t) * A.ldy + s], Sy[t]);
-      if (sizeof(R) == 4 && ++blk == 16) {
-        blk = 0;
-        o1 += S1; o2 += S2; S1 = 0; S2 = 0;
-        for (int t = 0; t < NT; ++t) { oy[t] += Sy[t]; Sy[t] = 0; }
-      }
-    }
-    S1 += o1;
-    S2 += o2;
-    for (int t = 0; t < NT; ++t) Sy[t] += oy[t];
-    for (int o = 16; o > 0; o >>= 1) {
-      S1 += __shfl_xor_sync(0xffffffffu, S1, o);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, o);
-      for (int t = 0; t < NT; ++t) Sy[t] += __shfl_xor_sync(0xffffffffu, Sy[t], o);
-    }
-    CandInterval<R> ci = cand_interval<R>(S1, S2, N, invN, sqrtN, c, W, gamma, u, fmin);
-    if (ci.realised == 0) {
-      if (lane == 0) ls.r[DSE_R_REALISED]++;
-      continue;
-    }
-    if (ci.realised == 2) {
-      if (lane == 0) {
-        escalate(A, gid);
-        ls.escalated++;
-      }
-      continue;
-    }
-    if (lane == 0) {
-      ls.r[DSE_VALID]++;
-      ls.evaluated++;
-    }
-    unsigned pushed = score_and_push<R, NT>(A, lane == 0, gid, ci, S1, Sy, invN, gamma, u, ysum);
-    refresh_pushed<NT>(A, pushed);
-  }
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ncand; w += warps)
+    feature_cand<R, NT>(A, w, id0, nid, p0, (R)gamma_lane, ysum, ls);
   flush_stats(A, ls);
+}
+
+// Batched screens: warps take jobs (runs of one problem's stored/unary
+// candidates, the whole group of every problem) from a shared counter.
+__device__ __forceinline__ bool next_job(unsigned int *counter, int n_jobs, int *j) {
+  unsigned v = 0;
+  if ((threadIdx.x & 31) == 0) v = atomicAdd(counter, 1u);
+  v = __shfl_sync(0xffffffffu, v, 0);
+  *j = (int)v;
+  return (int)v < n_jobs;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_feature_batched(const ScreenArgs *args, const Job *jobs, int n_jobs,
+                                                         unsigned int *counter) {
+  int j;
+  while (next_job(counter, n_jobs, &j)) {
+    const Job jb = jobs[j];
+    const ScreenArgs &A = args[jb.prob];
+    R ysum[1];
+    load_ysum<R, 1>(A, ysum);
+    LaneStats ls;
+    ls.zero();
+    const uint64_t nid = (uint64_t)A.n_stored;
+    for (int64_t w = jb.first; w < jb.first + jb.count; ++w)
+      feature_cand<R, 1>(A, (uint64_t)w, 0, nid, 0, (R)A.gamma_lane, ysum, ls);
+    flush_stats(A, ls, 0);
+  }
 }
 
 // ----------------------------------------------------------- pair kernel
@@ -421,8 +433,60 @@ __device__ __forceinline__ void pair_update(const R (&a)[MI], const R (&b)[MJ], 
   }
 }
 
-template <typename R, int KIND, int NT, int MI, int MJ>
-__global__ void __launch_bounds__(256) k_pair(const ScreenArgs A, int block_len) {
+// One binary candidate (pair ia > ib, op opc) from its accumulated sums:
+// a-priori tests, evaluation-error constant W, score interval, realised
+// decision, escalation and threshold push.  Every lane of the warp calls it
+// (the push is warp-cooperative); only lanes with `active` count and push.
+// kk: the shift constant of the evaluation (a*b, a/b, b/a: the FMA constant;
+// |a-b|: the constant subtracted); mi, mj: the centring means of the two
+// operands in evaluation order (a+b, a-b shift by mi +- mj).
+template <typename R, int NT>
+__device__ __forceinline__ unsigned binary_candidate(const ScreenArgs &A, LaneStats &ls, bool active, bool pv,
+                                                     int64_t ia, int64_t ib, int opc, uint64_t pbase,
+                                                     const float4 &fa_a, const float4 &fa_b, R kk, R mi, R mj,
+                                                     R S1, R S2, const R *Sy, R N, R invN, R sqrtN, R gamma, R u,
+                                                     R fmin, const R *ysum) {
+  const bool additive = opc == DSE_OP_ADD || opc == DSE_OP_SUB || opc == DSE_OP_ABSDIFF;
+  const int pos = A.slot_pos[opc - 6];
+  const uint64_t gid = (uint64_t)A.n_stored + pbase + (uint64_t)(pos < 0 ? 0 : pos);
+  const bool cand = active && pv && pos >= 0 && gid >= A.id_begin && gid < A.id_end;
+  int reason = DSE_VALID;
+  EvalErr<R> ee{R(0), R(0)};
+  if (cand) reason = binary_apriori_W<R>(A, opc, ia, ib, fa_a, fa_b, kk, mi, mj, &ee);
+  if (cand && additive) ls.seen++;
+  if (cand && reason != DSE_VALID) ls.r[reason]++;
+  bool ok = cand && reason == DSE_VALID;
+  if (ok && sizeof(R) == 4 && !((A.F.flags[ia] & A.F.flags[ib]) & F_FP32_SAFE)) {
+    escalate(A, gid);
+    ls.escalated++;
+    ok = false;
+  }
+  CandInterval<R> ci{};
+  if (ok) {
+    // w = V - c: c = kk for the products and |a-b|, mi +- mj for the centred
+    // sum and difference
+    const R cshift = opc == DSE_OP_ADD ? mi + mj : opc == DSE_OP_SUB ? mi - mj : kk;
+    ci = cand_interval<R>(S1, S2, N, invN, sqrtN, cshift, ee, gamma, u, fmin);
+    if (ci.realised == 0) {
+      ls.r[DSE_R_REALISED]++;
+      ok = false;
+    } else if (ci.realised == 2) {
+      escalate(A, gid);
+      ls.escalated++;
+      ok = false;
+    } else {
+      ls.r[DSE_VALID]++;
+      ls.evaluated++;
+    }
+  }
+  return score_and_push<R, NT>(A, ok, gid, ci, S1, Sy, invN, gamma, u, ysum);
+}
+
+// BATCH: the tiles of every problem of a batched screen in one launch; each
+// tile names its problem, whose arguments are read from `batch` (A0 then
+// carries only the tile list, its counter and the error flag).
+template <typename R, int KIND, int NT, int MI, int MJ, bool BATCH>
+__global__ void __launch_bounds__(256) k_pair(const ScreenArgs A0, const ScreenArgs *batch, int block_len0) {
   using C = PairCfg<R, KIND, NT, MI, MJ>;
   using V2 = typename Vec2<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -434,16 +498,7 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A, int block_len)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wi = warp >> 2, wj = warp & 3, li = lane >> 2, lj = lane & 3;
   const R u = sizeof(R) == 4 ? R(5.9604644775390625e-8) : R(1.1102230246251565e-16);
-  const R gamma = (R)A.gamma;
-  const R N = (R)A.N, invN = (R)A.invN, sqrtN = Num<R>::sqrt_(N);
-  const R fmin = (R)A.fmin_std_rel64;
-  const int nchunks = (A.N + C::CH - 1) / C::CH;
-  const int64_t ld = A.F.ld;
-  const R *rows_src = sizeof(R) == 4 ? (const R *)A.F.v32 : (const R *)A.F.v64;
-  const R *y_src = sizeof(R) == 4 ? (const R *)A.y32 : (const R *)A.y64;
-  R ysum[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) ysum[t] = (sizeof(R) == 4 && t < A.T) ? (R)A.ysum32[A.t0 + t] : R(0);
+  constexpr int kGroup = KIND == KIND_MUL ? 1 : 2;
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -455,13 +510,29 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A, int block_len)
   uint32_t gchunk = 0;
   LaneStats ls;
   ls.zero();
+  int cur = BATCH ? -1 : 0;  // problem whose statistics ls holds
 
   for (;;) {
-    if (tid == 0) s_tile = (int)atomicAdd(A.tile_counter, 1u);
+    if (tid == 0) s_tile = (int)atomicAdd(A0.tile_counter, 1u);
     __syncthreads();
     const int tile = s_tile;
-    if (tile >= A.n_tiles || s_abort) break;
-    const Tile tl = A.tiles[tile];
+    if (tile >= A0.n_tiles || s_abort) break;
+    const Tile tl = A0.tiles[tile];
+    if (BATCH && tl.prob != cur) {
+      if (cur >= 0) flush_stats(batch[cur], ls, kGroup);
+      cur = tl.prob;
+    }
+    const ScreenArgs &A = BATCH ? batch[tl.prob] : A0;
+    const int block_len = BATCH ? A.block_len : block_len0;
+    const R gamma = (R)A.gamma;
+    const R N = (R)A.N, invN = (R)A.invN, sqrtN = Num<R>::sqrt_(N);
+    const R fmin = (R)A.fmin_std_rel64;
+    const int nchunks = (A.N + C::CH - 1) / C::CH;
+    const int64_t ld = A.F.ld;
+    const R *rows_src = sizeof(R) == 4 ? (const R *)A.F.v32 : (const R *)A.F.v64;
+    const R *y_src = sizeof(R) == 4 ? (const R *)A.y32 : (const R *)A.y64;
+    R ysum[NT];
+    load_ysum<R, NT>(A, ysum);
     if (tid < C::ROWS) {
       int id = -1;
       if (tid < C::BI) {
@@ -549,7 +620,7 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A, int block_len)
       const uint32_t g = gchunk + ch;
       const int st = g & 1;
       if (!mbar_wait_bounded(&bar[st], (g >> 1) & 1, kWaitLimit)) {
-        atomicExch(A.err, DSE_ETIMEOUT);
+        atomicExch(A0.err, DSE_ETIMEOUT);
         s_abort = 1;
       }
       __syncthreads();
@@ -646,105 +717,133 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A, int block_len)
         for (int k = 0; k < 3; ++k) {
           const int opc = KIND == KIND_MUL ? (k == 0 ? DSE_OP_MUL : k == 1 ? DSE_OP_DIV : DSE_OP_RDIV)
                                            : (k == 0 ? DSE_OP_ADD : k == 1 ? DSE_OP_SUB : DSE_OP_ABSDIFF);
-          const int pos = A.slot_pos[opc - 6];
-          const uint64_t gid = (uint64_t)A.n_stored + pbase + (uint64_t)(pos < 0 ? 0 : pos);
-          bool cand = pv && pos >= 0 && gid >= A.id_begin && gid < A.id_end;
-          int reason = DSE_VALID;
-          R W = 0;
-          if (cand) {
-            // a-priori tests (exact: integer, flags, FP32 directed-rounding
-            // intervals with an FP64 fall-back when the interval straddles)
-            if (KIND == KIND_ADD && A.unit_check_addsub &&
-                (A.F.ukey[2 * ia] != A.F.ukey[2 * ib] || A.F.ukey[2 * ia + 1] != A.F.ukey[2 * ib + 1]))
-              reason = DSE_R_UNIT;
-            else if (A.max_complexity > 0 && A.F.cplx[ia] + A.F.cplx[ib] + 1 > A.max_complexity)
-              reason = DSE_R_COMPLEXITY;
-            else if (opc == DSE_OP_DIV && !(A.F.flags[ib] & F_MINABS_POS))
-              reason = DSE_R_DOMAIN;
-            else if (opc == DSE_OP_RDIV && !(A.F.flags[ia] & F_MINABS_POS))
-              reason = DSE_R_DOMAIN;
-            else {
-              float lo, hi;
-              if (opc == DSE_OP_MUL) {
-                lo = __fmul_rd(fa_a.w, fa_b.w);
-                hi = __fmul_ru(fa_a.z, fa_b.z);
-              } else if (opc == DSE_OP_DIV) {
-                float2 rr = A.F.fr[ib];
-                lo = __fmul_rd(fa_a.w, rr.y);
-                hi = __fmul_ru(fa_a.z, rr.x);
-              } else if (opc == DSE_OP_RDIV) {
-                float2 rr = A.F.fr[ia];
-                lo = __fmul_rd(fa_b.w, rr.y);
-                hi = __fmul_ru(fa_b.z, rr.x);
-              } else {
-                lo = __fadd_rd(fa_a.w, fa_b.w);
-                hi = __fadd_ru(fa_a.z, fa_b.z);
-              }
-              if (hi <= A.fmax32_dn) {
-              } else if (lo > A.fmax32_up) {
-                reason = DSE_R_MAGNITUDE;
-              } else {
-                reason = domain_magnitude64(opc, A.F.min64[ia], A.F.max64[ia], A.F.minabs64[ia], A.F.maxabs64[ia],
-                                            A.F.minabs64[ib], A.F.maxabs64[ib], A.fmax64, 0.0);
-              }
-              // evaluation error constant W (upper bounds of the magnitudes)
-              const R Ma = (R)fa_a.z, Mb = (R)fa_b.z;
-              const R kk = (k == 0 ? k0[r][c] : k == 1 ? k1[r][c] : k2[r][c]);
-              const R akk = kk < R(0) ? -kk : kk;
-              if (opc == DSE_OP_MUL) {
-                W = R(2.01) * Ma * Mb + R(1.01) * (Ma * Mb + akk);
-              } else if (opc == DSE_OP_DIV) {
-                R q = Ma * (R)A.F.fr[ib].x;
-                W = R(4.02) * q + R(1.01) * (q + akk);
-              } else if (opc == DSE_OP_RDIV) {
-                R q = Mb * (R)A.F.fr[ia].x;
-                W = R(4.02) * q + R(1.01) * (q + akk);
-              } else if (opc == DSE_OP_ABSDIFF) {
-                W = R(1.01) * (R(3) * (Ma + Mb) + akk);
-              } else {
-                const R am = mi[r] < R(0) ? -mi[r] : mi[r], bm = mj[c] < R(0) ? -mj[c] : mj[c];
-                W = R(1.01) * (R(3) * (Ma + Mb) + R(2) * (am + bm));
-              }
-            }
-          }
-          if (cand && KIND == KIND_ADD) ls.seen++;
-          if (cand && reason != DSE_VALID) ls.r[reason]++;
-          bool ok = cand && reason == DSE_VALID;
-          if (ok && sizeof(R) == 4 && !((A.F.flags[ia] & A.F.flags[ib]) & F_FP32_SAFE)) {
-            escalate(A, gid);
-            ls.escalated++;
-            ok = false;
-          }
-          const R S1 = tot[r][c][k][0], S2 = tot[r][c][k][1];
-          const R shift = (KIND == KIND_MUL) ? (k == 0 ? k0[r][c] : k == 1 ? k1[r][c] : k2[r][c])
-                                             : (k == 2 ? k2[r][c] : R(0));
-          CandInterval<R> ci{};
-          if (ok) {
-            // w = V - c: c = k0/k1/k2 for the products, mi +- mj for the
-            // centred sum and difference, k2 for |a-b|
-            const R cshift = (KIND == KIND_ADD && k < 2) ? (k == 0 ? mi[r] + mj[c] : mi[r] - mj[c]) : shift;
-            ci = cand_interval<R>(S1, S2, N, invN, sqrtN, cshift, W, gamma, u, fmin);
-            if (ci.realised == 0) {
-              ls.r[DSE_R_REALISED]++;
-              ok = false;
-            } else if (ci.realised == 2) {
-              escalate(A, gid);
-              ls.escalated++;
-              ok = false;
-            } else {
-              ls.r[DSE_VALID]++;
-              ls.evaluated++;
-            }
-          }
+          const R kk = (k == 0 ? k0[r][c] : k == 1 ? k1[r][c] : k2[r][c]);
           R Sy[NT];
 #pragma unroll
           for (int t = 0; t < NT; ++t) Sy[t] = tot[r][c][k][2 + t];
-          pushed |= score_and_push<R, NT>(A, ok, gid, ci, S1, Sy, invN, gamma, u, ysum);
+          pushed |= binary_candidate<R, NT>(A, ls, true, pv, ia, ib, opc, pbase, fa_a, fa_b, kk, mi[r], mj[c],
+                                            tot[r][c][k][0], tot[r][c][k][1], Sy, N, invN, sqrtN, gamma, u, fmin,
+                                            ysum);
         }
       }
     refresh_pushed<NT>(A, pushed);
   }
+  if (cur >= 0) flush_stats(BATCH ? batch[cur] : A0, ls, kGroup);
+}
+
+// ------------------------------------------------ explicit pair lists
+
+// The additive slots (a+b, a-b, |a-b|) of an explicit list of pairs (i > j,
+// equal units): one warp per pair, lanes over samples, warp-shuffle
+// reduction.  Used when equal-unit pairs are a small fraction of all pairs,
+// where tiles over unit classes would be mostly empty.
+template <typename R, int NT>
+__device__ __forceinline__ void pairlist_one(const ScreenArgs &A, int64_t ia, int64_t ib, R gamma, const R *ysum,
+                                             LaneStats &ls) {
+  const int lane = threadIdx.x & 31;
+  const R u = sizeof(R) == 4 ? R(5.9604644775390625e-8) : R(1.1102230246251565e-16);
+  const int64_t Ns = A.N;
+  const int T = A.T, t0 = A.t0;
+  const int64_t ldy = A.ldy;
+  const R N = (R)Ns, invN = (R)A.invN, sqrtN = Num<R>::sqrt_(N);
+  const R fmin = (R)A.fmin_std_rel64;
+  const R *Y = sizeof(R) == 4 ? (const R *)A.y32 : (const R *)A.y64;
+  const R *rows = sizeof(R) == 4 ? (const R *)A.F.v32 : (const R *)A.F.v64;
+  const uint64_t pbase = A.G.um + (tri((uint64_t)ia) + (uint64_t)ib - A.G.tri_o) * (uint64_t)A.G.nb;
+  const float4 fa_a = A.F.fa[ia], fa_b = A.F.fa[ib];
+  const R mi = sizeof(R) == 4 ? (R)fa_a.x : (R)A.F.mean64[ia];
+  const R mj = sizeof(R) == 4 ? (R)fa_b.x : (R)A.F.mean64[ib];
+  const R cabs = mi - mj < R(0) ? mj - mi : mi - mj;
+  const R *xa = rows + ia * A.F.ld, *xb = rows + ib * A.F.ld;
+  R acc[3][2 + NT], tot[3][2 + NT];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int e = 0; e < 2 + NT; ++e) acc[k][e] = tot[k][e] = R(0);
+  int blk = 0;
+  for (int64_t s = lane; s < Ns; s += 32) {
+    const R a = xa[s], b = xb[s];
+    const R ac = a - mi, bc = b - mj, d = a - b;
+    R w3[3];
+    w3[0] = ac + bc;
+    w3[1] = ac - bc;
+    w3[2] = (d < R(0) ? -d : d) - cabs;
+    R y[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) y[t] = t < T ? Y[(int64_t)(t0 + t) * ldy + s] : R(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc[k][0] += w3[k];
+      acc[k][1] = Num<R>::fma_(w3[k], w3[k], acc[k][1]);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) acc[k][2 + t] = Num<R>::fma_(w3[k], y[t], acc[k][2 + t]);
+    }
+    if (sizeof(R) == 4 && ++blk == 16) {
+      blk = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int e = 0; e < 2 + NT; ++e) {
+          tot[k][e] += acc[k][e];
+          acc[k][e] = R(0);
+        }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int e = 0; e < 2 + NT; ++e) {
+      R v = tot[k][e] + acc[k][e];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      tot[k][e] = v;
+    }
+  unsigned pushed = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int opc = k == 0 ? DSE_OP_ADD : k == 1 ? DSE_OP_SUB : DSE_OP_ABSDIFF;
+    R Sy[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Sy[t] = tot[k][2 + t];
+    pushed |= binary_candidate<R, NT>(A, ls, lane == 0, true, ia, ib, opc, pbase, fa_a, fa_b, cabs, mi, mj,
+                                      tot[k][0], tot[k][1], Sy, N, invN, sqrtN, gamma, u, fmin, ysum);
+  }
+  refresh_pushed<NT>(A, pushed);
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(256) k_pairlist(const ScreenArgs A, const int2 *pairs, int64_t n_pairs,
+                                                  float gamma_lane) {
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  R ysum[NT];
+  load_ysum<R, NT>(A, ysum);
+  LaneStats ls;
+  ls.zero();
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (uint64_t)n_pairs; w += warps) {
+    const int2 pr = pairs[w];
+    pairlist_one<R, NT>(A, pr.x, pr.y, (R)gamma_lane, ysum, ls);
+  }
   flush_stats(A, ls);
+}
+
+// Batched screens: the equal-unit pair lists of every problem, concatenated;
+// warps take jobs (runs of one problem's pairs) from a shared counter.
+template <typename R>
+__global__ void __launch_bounds__(256) k_pairlist_batched(const ScreenArgs *args, const int2 *pairs,
+                                                          const Job *jobs, int n_jobs, unsigned int *counter) {
+  int j;
+  while (next_job(counter, n_jobs, &j)) {
+    const Job jb = jobs[j];
+    const ScreenArgs &A = args[jb.prob];
+    R ysum[1];
+    load_ysum<R, 1>(A, ysum);
+    LaneStats ls;
+    ls.zero();
+    for (int64_t w = jb.first; w < jb.first + jb.count; ++w) {
+      const int2 pr = pairs[w];
+      pairlist_one<R, 1>(A, pr.x, pr.y, (R)A.gamma_lane, ysum, ls);
+    }
+    flush_stats(A, ls, 2);
+  }
 }
 
 // --------------------------------------------------- FP64 escalation
@@ -772,67 +871,94 @@ __device__ __forceinline__ void decode_gid(const ScreenArgs &A, uint64_t gid, in
 }
 
 // Escalated candidates: decide the realised test in FP64 and, if valid,
-// push FP64 scores for every target.  One warp per candidate.
-__global__ void k_escalate(const ScreenArgs A) {
-  const int lane = threadIdx.x & 31;
-  const unsigned n = min(*A.esc_count, (unsigned)A.esc_cap);
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += warps) {
-    const uint64_t gid = A.esc_id[w];
+// push FP64 scores for every target.  One block of kEsc threads per
+// candidate; one pass for the statistics (sums shifted by the first value, so
+// Sxx = S2 - S1^2/N keeps FP64 accuracy even for a near-constant candidate),
+// then one pass per group of 16 targets.
+constexpr int kEsc = 128;
+
+template <int NV>
+__device__ __forceinline__ void block_sum64(double (&v)[NV], double *sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum64(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[w * NV + i] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = 0.0;
+    for (int ww = 0; ww < kEsc / 32; ++ww) t += sm[ww * NV + i];
+    v[i] = t;
+  }
+  __syncthreads();
+}
+
+// batch != nullptr: entries of a batched screen, each with its problem.
+__global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const ScreenArgs *batch) {
+  __shared__ double sm[(kEsc / 32) * 16];
+  const unsigned n = min(*A0.esc_count, (unsigned)A0.esc_cap);
+  for (unsigned w = blockIdx.x; w < n; w += gridDim.x) {
+    const ScreenArgs &A = batch ? batch[A0.esc_prob[w]] : A0;
+    const int64_t N = A.N;
+    const uint64_t gid = A0.esc_id[w];
     int op;
     int64_t a, b;
     decode_gid(A, gid, &op, &a, &b);
-    const int64_t N = A.N;
-    double sum = 0.0;
-    int fin = 1;
-    for (int64_t s = lane; s < N; s += 32) {
-      double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
-      if (!isfinite(v)) fin = 0;
-      sum += v;
+    const double c = cand_value64(A.F, A.G, A.n_stored, gid, 0, op, a, b);
+    // sum (v-c), sum (v-c)^2, sum v^2, number of non-finite values
+    double st[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t s = threadIdx.x; s < N; s += kEsc) {
+      const double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
+      if (!isfinite(v)) st[3] += 1.0;
+      const double d = v - c;
+      st[0] += d;
+      st[1] = fma(d, d, st[1]);
+      st[2] = fma(v, v, st[2]);
     }
-    fin = !__any_sync(0xffffffffu, !fin);
-    sum = warp_sum64(sum);
-    const double mean = sum / (double)N;
-    double sxx = 0.0, s2 = 0.0;
-    for (int64_t s = lane; s < N; s += 32) {
-      double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
-      double d = v - mean;
-      sxx = fma(d, d, sxx);
-      s2 = fma(v, v, s2);
-    }
-    sxx = warp_sum64(sxx);
-    s2 = warp_sum64(s2);
-    int good = fin;
+    block_sum64<4>(st, sm);
+    const double sxx = st[1] - st[0] * (st[0] / (double)N);
+    int good = st[3] == 0.0 && isfinite(sxx);
     if (good && A.fmin_std_rel64 >= 0.0)
-      good = __dsqrt_rn(sxx / (double)N) > A.fmin_std_rel64 * __dsqrt_rn(s2 / (double)N);
-    if (lane == 0) atomicAdd(&A.stats[good ? ST_REASON0 + DSE_VALID : ST_REASON0 + DSE_R_REALISED], 1ull);
-    if (!good) continue;
-    if (lane == 0) atomicAdd(&A.stats[ST_EVALUATED], 1ull);
-    // scores against every target of the screen (FP64 two-pass)
-    const double err = (double)(N / 32 + 40) * 1.1102230246251565e-16 * 8.0;
+      good = __dsqrt_rn(fmax(sxx, 0.0) / (double)N) > A.fmin_std_rel64 * __dsqrt_rn(st[2] / (double)N);
+    if (threadIdx.x == 0) {
+      atomicAdd(&A.stats[good ? ST_REASON0 + DSE_VALID : ST_REASON0 + DSE_R_REALISED], 1ull);
+      if (good) atomicAdd(&A.stats[ST_EVALUATED], 1ull);
+    }
+    if (!good || !(sxx > 0.0)) continue;
+    const double err = (double)(N / kEsc + 64) * 1.1102230246251565e-16 * 16.0;
+    const double dm = st[0] / (double)N;  // vbar - c
     double agg = 0.0;
-    for (int t = 0; t < A.T; ++t) {
-      const double *y = A.y64 + (int64_t)t * A.ldy;
-      double sxy = 0.0;
-      for (int64_t s = lane; s < N; s += 32) {
-        double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
-        sxy = fma(v - mean, y[s], sxy);
+    for (int t0 = 0; t0 < A.T; t0 += 16) {
+      double sy[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) sy[t] = 0.0;
+      for (int64_t s = threadIdx.x; s < N; s += kEsc) {
+        const double d = (cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b) - c) - dm;
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t0 + t < A.T) sy[t] = fma(d, A.y64[(int64_t)(A.t0 + t0 + t) * A.ldy + s], sy[t]);
       }
-      sxy = warp_sum64(sxy);
-      double sc = fabs(sxy) / sqrt(sxx);
-      if (A.mode == DSE_MODE_AGGREGATED) {
-        agg += sc * sc;
-      } else if (lane == 0) {
-        float sf = (float)sc;
-        float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
-        push_one(A.B, t, gid, sf, ef);
+      block_sum64<16>(sy, sm);
+      if (threadIdx.x == 0) {
+        for (int t = 0; t < 16 && t0 + t < A.T; ++t) {
+          const double sc = fabs(sy[t]) / sqrt(sxx);
+          if (A.mode == DSE_MODE_AGGREGATED) {
+            agg += sc * sc;
+          } else {
+            const float sf = (float)sc;
+            const float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+            push_one(A.B, A.t0 + t0 + t, gid, sf, ef);
+          }
+        }
       }
     }
-    if (A.mode == DSE_MODE_AGGREGATED && lane == 0) {
-      double sc = sqrt(agg / (double)A.T);
-      float sf = (float)sc;
-      float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
-      push_one(A.B, 0, gid, sf, ef);
+    if (A.mode == DSE_MODE_AGGREGATED && threadIdx.x == 0) {
+      const double sc = sqrt(agg / (double)A.T);
+      const float sf = (float)sc;
+      const float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+      push_one(A.B, A.t0, gid, sf, ef);
     }
   }
 }
@@ -853,27 +979,30 @@ void launch_feature_t(const ScreenArgs &A, uint64_t id0, uint64_t id1, uint64_t 
   k_feature<R, NT><<<(unsigned)blocks, 256, 0, st>>>(B, id0, id1, p0, p1, gamma);
 }
 
-template <typename R, int KIND, int NT, int MI, int MJ>
-dse_status launch_pair_t(const ScreenArgs &A, int block_len, int sms, cudaStream_t st) {
+template <typename R, int KIND, int NT, int MI, int MJ, bool BATCH = false>
+dse_status launch_pair_t(const ScreenArgs &A, int block_len, int sms, cudaStream_t st,
+                         const ScreenArgs *batch = nullptr) {
   using C = PairCfg<R, KIND, NT, MI, MJ>;
   if (A.n_tiles <= 0) return DSE_OK;
   static bool attr_set[64] = {false};
+  static int per_sm_of[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (!attr_set[dev & 63]) {
-    DSE_CUDA(cudaFuncSetAttribute(k_pair<R, KIND, NT, MI, MJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    DSE_CUDA(cudaFuncSetAttribute(k_pair<R, KIND, NT, MI, MJ, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)C::SMEM));
+    int per_sm = 0;
+    DSE_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R, KIND, NT, MI, MJ, BATCH>, 256, C::SMEM));
+    per_sm_of[dev & 63] = per_sm < 1 ? 1 : per_sm;
     attr_set[dev & 63] = true;
   }
-  int per_sm = 0;
-  DSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<R, KIND, NT, MI, MJ>, 256, C::SMEM));
-  if (per_sm < 1) per_sm = 1;
-  int grid = sms * per_sm;
+  int grid = sms * per_sm_of[dev & 63];
   if (grid > A.n_tiles) grid = A.n_tiles;
   note_launches(1);
   ScreenArgs B = A;
   B.group = KIND == KIND_MUL ? 1 : 2;
-  k_pair<R, KIND, NT, MI, MJ><<<grid, 256, C::SMEM, st>>>(B, block_len);
+  k_pair<R, KIND, NT, MI, MJ, BATCH><<<grid, 256, C::SMEM, st>>>(B, batch, block_len);
   return DSE_OK;
 }
 
@@ -903,9 +1032,62 @@ dse_status launch_pair(int prec64, int kind, int nt, const ScreenArgs &A, int bl
                           : launch_pair_t<float, KIND_ADD, 16, 1, 1>(A, block_len, sms, st);
 }
 
-void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st) {
+void launch_pairlist(int prec64, int nt, const ScreenArgs &A, const int2 *pairs, int64_t n_pairs, float gamma,
+                     int sms, cudaStream_t st) {
+  if (n_pairs <= 0) return;
+  uint64_t blocks = ((uint64_t)n_pairs + 7) / 8;
+  if (blocks > (uint64_t)sms * 16) blocks = (uint64_t)sms * 16;
   note_launches(1);
-  k_escalate<<<sms * 4, 256, 0, st>>>(A);
+  ScreenArgs B = A;
+  B.group = 2;
+  if (prec64) {
+    if (nt == 1) k_pairlist<double, 1><<<(unsigned)blocks, 256, 0, st>>>(B, pairs, n_pairs, gamma);
+    else k_pairlist<double, 16><<<(unsigned)blocks, 256, 0, st>>>(B, pairs, n_pairs, gamma);
+  } else {
+    if (nt == 1) k_pairlist<float, 1><<<(unsigned)blocks, 256, 0, st>>>(B, pairs, n_pairs, gamma);
+    else k_pairlist<float, 16><<<(unsigned)blocks, 256, 0, st>>>(B, pairs, n_pairs, gamma);
+  }
+}
+
+// ---------------------------------------------------- batched launchers
+
+void launch_targets_batched(const double *Y, const int64_t *yoff, const ScreenArgs *args, int n, int32_t ldy,
+                            double *y64, float *y32, float *ysum32, int *err, cudaStream_t st) {
+  if (n <= 0) return;
+  note_launches(1);
+  k_targets_batched<<<n, 256, 0, st>>>(Y, yoff, args, n, ldy, y64, y32, ysum32, err);
+}
+
+void launch_feature_batched(int prec64, const ScreenArgs *args, const Job *jobs, int n_jobs, unsigned int *counter,
+                            int sms, cudaStream_t st) {
+  if (n_jobs <= 0) return;
+  const int blocks = std::min(sms * 8, (n_jobs + 7) / 8);
+  note_launches(1);
+  if (prec64) k_feature_batched<double><<<blocks, 256, 0, st>>>(args, jobs, n_jobs, counter);
+  else k_feature_batched<float><<<blocks, 256, 0, st>>>(args, jobs, n_jobs, counter);
+}
+
+dse_status launch_pair_batched(int prec64, int kind, const ScreenArgs &A0, const ScreenArgs *args, int sms,
+                               cudaStream_t st) {
+  if (prec64)
+    return kind == KIND_MUL ? launch_pair_t<double, KIND_MUL, 1, 2, 2, true>(A0, 0, sms, st, args)
+                            : launch_pair_t<double, KIND_ADD, 1, 2, 2, true>(A0, 0, sms, st, args);
+  return kind == KIND_MUL ? launch_pair_t<float, KIND_MUL, 1, 2, 2, true>(A0, 0, sms, st, args)
+                          : launch_pair_t<float, KIND_ADD, 1, 2, 2, true>(A0, 0, sms, st, args);
+}
+
+void launch_pairlist_batched(int prec64, const ScreenArgs *args, const int2 *pairs, const Job *jobs, int n_jobs,
+                             unsigned int *counter, int sms, cudaStream_t st) {
+  if (n_jobs <= 0) return;
+  const int blocks = std::min(sms * 8, (n_jobs + 7) / 8);
+  note_launches(1);
+  if (prec64) k_pairlist_batched<double><<<blocks, 256, 0, st>>>(args, pairs, jobs, n_jobs, counter);
+  else k_pairlist_batched<float><<<blocks, 256, 0, st>>>(args, pairs, jobs, n_jobs, counter);
+}
+
+void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st, const ScreenArgs *batch) {
+  note_launches(1);
+  k_escalate<<<sms * 8, kEsc, 0, st>>>(A, batch);
 }
 
 void launch_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,

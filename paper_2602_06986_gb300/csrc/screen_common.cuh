@@ -10,10 +10,14 @@
 //
 // Error bound (float path).  With u the unit roundoff of R:
 //   * evaluation: every sample's w differs from the exact op(A, B) - c (A, B
-//     the FP64 operands) by at most u*W, W a per-candidate constant from the
-//     operand magnitude bounds; the centred norm of the error vector is then
-//     at most E = sqrt(N) u W, which bounds the error of sqrt(Sxx) directly
-//     (triangle inequality) and of the numerator (Cauchy-Schwarz).
+//     the FP64 operands) by at most u * (kappa |V_s| + lambda_s), where kappa
+//     counts the roundings of the operation (operand rounding, the op's own
+//     documented ulp bound, the shifted FMA) and lambda_s collects the shift
+//     and, for sums and differences, the operands' magnitudes; by Minkowski
+//     the 2-norm of the error vector is at most E = u (kappa ||V|| + Lambda)
+//     with ||V|| from the accumulated sums and Lambda from per-feature norms,
+//     which bounds the error of sqrt(Sxx) directly (triangle inequality) and
+//     of the numerator (Cauchy-Schwarz).
 //   * accumulation: each sum is a sum of n terms in a fixed order with at most
 //     `gamma` relative error on the sum of absolute terms (blocked summation,
 //     gamma from the block structure); sum |w| <= sqrt(N S2), sum |w y| <=
@@ -25,6 +29,7 @@
 #pragma once
 
 #include "dse_internal.cuh"
+#include "eval64.cuh"
 
 namespace dse {
 
@@ -47,24 +52,35 @@ struct CandInterval {
   R q;        // computed sqrt(Sxx)
   R q_lo, q_hi;
   R sqS2;     // sqrt(S2)
-  R E;        // sqrt(N) u W
+  R E;        // bound of the evaluation error vector's 2-norm
   int realised;  // 1 valid, 0 degenerate, 2 undecided
 };
 
+// Per-candidate evaluation-error coefficients: E = u (kappa ||V|| + lambda).
 template <typename R>
-__device__ __forceinline__ CandInterval<R> cand_interval(R S1, R S2, R N, R invN, R sqrtN, R c, R W, R gamma, R u,
-                                                         R fmin) {
+struct EvalErr {
+  R kappa, lambda;
+};
+
+template <typename R>
+__device__ __forceinline__ CandInterval<R> cand_interval(R S1, R S2, R N, R invN, R sqrtN, R c, EvalErr<R> ee,
+                                                         R gamma, R u, R fmin) {
   CandInterval<R> o;
   const R mean = S1 * invN;
   const R Sxx = Num<R>::fma_(-S1, mean, S2);
   const R dSxx = (R(3) * gamma + R(6) * u) * S2 * R(1.01);
-  o.E = sqrtN * u * W * R(1.01);
+  o.sqS2 = Num<R>::sqrt_(S2);
+  // ||V||^2 = sum (w + c)^2 = S2 + 2 c S1 + N c^2 (of the computed values)
+  const R ac = c < R(0) ? -c : c;
+  const R Z = S2 + R(2) * c * S1 + N * c * c;
+  const R dZ = (gamma + R(8) * u) * (S2 + R(2) * ac * sqrtN * o.sqS2 + N * c * c) * R(1.01);
+  const R Vc_hi = Num<R>::sqrt_(Z + dZ) * (R(1) + R(4) * u);
+  o.E = u * (ee.kappa * Vc_hi + ee.lambda) * R(1.02);
   o.q = Num<R>::sqrt_(Sxx > R(0) ? Sxx : R(0));
   const R lo2 = Sxx - dSxx;
   o.q_lo = Num<R>::sqrt_(lo2 > R(0) ? lo2 : R(0)) * (R(1) - R(4) * u) - o.E;
   o.q_hi = Num<R>::sqrt_(Sxx + dSxx) * (R(1) + R(4) * u) + o.E;
-  o.sqS2 = Num<R>::sqrt_(S2);
-  bool finite = isfinite(S1) && isfinite(S2) && isfinite(W);
+  bool finite = isfinite(S1) && isfinite(S2) && isfinite(o.E);
   if (!finite) {
     o.realised = 2;
     return o;
@@ -73,13 +89,9 @@ __device__ __forceinline__ CandInterval<R> cand_interval(R S1, R S2, R N, R invN
     o.realised = 1;
     return o;
   }
-  // ||V||^2 = sum (w + c)^2 = S2 + 2 c S1 + N c^2
-  const R ac = c < R(0) ? -c : c;
-  const R Z = S2 + R(2) * c * S1 + N * c * c;
-  const R dZ = (gamma + R(8) * u) * (S2 + R(2) * ac * sqrtN * o.sqS2 + N * c * c) * R(1.01);
   const R vlo2 = Z - dZ;
   const R V_lo = Num<R>::sqrt_(vlo2 > R(0) ? vlo2 : R(0)) * (R(1) - R(4) * u) - o.E;
-  const R V_hi = Num<R>::sqrt_(Z + dZ) * (R(1) + R(4) * u) + o.E;
+  const R V_hi = Vc_hi + o.E;
   if (o.q_lo > fmin * V_hi * (R(1) + R(8) * u))
     o.realised = 1;
   else if (o.q_hi < fmin * (V_lo > R(0) ? V_lo : R(0)) * (R(1) - R(8) * u))
@@ -120,12 +132,184 @@ __device__ __forceinline__ void cand_score(const CandInterval<R> &ci, R S1, R Sy
   *eps_out = eps;
 }
 
+// Score interval against one target with a separate relative error factor
+// for the numerator accumulation (the tensor-core path's contraction error);
+// otherwise as cand_score.
+template <typename R>
+__device__ __forceinline__ void cand_score_num(const CandInterval<R> &ci, R S1, R Sy, R invN, R ysum, R gamma,
+                                               R gamma_num, R u, R *s_out, R *eps_out) {
+  const R P = Num<R>::fma_(-S1, ysum * invN, Sy);
+  const R aP = P < R(0) ? -P : P;
+  const R aS1 = S1 < R(0) ? -S1 : S1;
+  const R ays = ysum < R(0) ? -ysum : ysum;
+  const R dP = (gamma_num * ci.sqS2 * (R(1) + R(2) * u) + aS1 * invN * ays * (gamma + R(4) * u) + u * aP +
+                ci.E * (R(1) + R(2) * u) + R(2) * u * ci.q_hi) *
+               R(1.01);
+  R s, eps;
+  if (!(ci.q > R(0))) {
+    s = R(0);
+    eps = R(1);
+  } else {
+    s = aP / ci.q;
+    R rlo = (aP - dP) / ci.q_hi;
+    if (!(rlo > R(0))) rlo = R(0);
+    R rhi = ci.q_lo > R(0) ? (aP + dP) / ci.q_lo : R(1);
+    if (!(rhi < R(1))) rhi = R(1);
+    if (s > R(1)) s = R(1);
+    R e1 = s - rlo, e2 = rhi - s;
+    eps = (e1 > e2 ? e1 : e2) * (R(1) + R(16) * u) + R(4e-12) * s;
+    if (!(eps >= R(0))) eps = R(1);
+  }
+  *s_out = s;
+  *eps_out = eps;
+}
+
+// ----------------------------------------------------- per-lane statistics
+
+struct LaneStats {
+  unsigned r[6];
+  unsigned evaluated, escalated, seen;
+  __device__ void zero() {
+    for (int i = 0; i < 6; ++i) r[i] = 0;
+    evaluated = escalated = seen = 0;
+  }
+};
+
+// Warp-reduce the lane counters into the screen's statistics (whole warp).
+__device__ __forceinline__ void flush_stats(const ScreenArgs &A, LaneStats &ls, int group = -1) {
+  if (group < 0) group = A.group;
+  if (!A.first_pass) {
+    ls.zero();
+    return;
+  }
+  {
+    unsigned v = ls.seen;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&A.stats[ST_ADD_SEEN], (unsigned long long)v);
+  }
+  for (int i = 0; i < 6; ++i) {
+    unsigned v = ls.r[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&A.stats[ST_REASON0 + i], (unsigned long long)v);
+  }
+  {
+    unsigned v = ls.r[DSE_VALID];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&A.stats[ST_VALID_G0 + group], (unsigned long long)v);
+  }
+  unsigned e = ls.evaluated, x = ls.escalated;
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (e) atomicAdd(&A.stats[ST_EVALUATED], (unsigned long long)e);
+    if (x) atomicAdd(&A.stats[ST_ESCALATED], (unsigned long long)x);
+  }
+  ls.zero();
+}
+
+// Queue a candidate for the FP64 decision of its realised test.
+__device__ __forceinline__ void escalate(const ScreenArgs &A, uint64_t gid) {
+  if (!A.first_pass) return;
+  unsigned pos = atomicAdd(A.esc_count, 1u);
+  if ((int64_t)pos < A.esc_cap) {
+    A.esc_id[pos] = gid;
+    if (A.esc_prob) A.esc_prob[pos] = (uint32_t)A.prob;
+  } else
+    atomicAdd(&A.stats[ST_ESC_OVERFLOW], 1ull);
+}
+
+// A-priori tests (unit, complexity, domain, magnitude) of the binary
+// candidate op(ia, ib), exact: integer keys, flags, FP32 directed-rounding
+// intervals with an FP64 fall-back when the interval straddles the limit.
+// Also the evaluation-error coefficients of the evaluation with shift kk
+// (a*b, a/b, b/a: the FMA constant; |a-b|: the subtracted constant) or, for
+// a+b and a-b, centring means mi, mj:
+//   a*b   fma(a, b, -c): operands rounded (2u |V|) and one rounding of the
+//         shifted result (u (|V| + |c|))                 kappa 3, lambda |c| sqrt(N)
+//   a/b   fma(a, rcp(b), -c): operands (2u), rcp.approx (2u), FMA rounding
+//                                                         kappa 5, lambda |c| sqrt(N)
+//   |a-b| rounded operands and difference (3u (|A|+|B|)), shift rounding
+//                                                         kappa 0, lambda 3(||A||+||B||) + |c| sqrt(N)
+//   a+-b  centred operands (2u|A| + u|mean|, likewise B) and the sum
+//                                                         kappa 0, lambda 3(||A||+||B||) + 2(|mi|+|mj|) sqrt(N)
+template <typename R>
+__device__ __forceinline__ int binary_apriori_W(const ScreenArgs &A, int opc, int64_t ia, int64_t ib,
+                                                const float4 &fa_a, const float4 &fa_b, R kk, R mi, R mj,
+                                                EvalErr<R> *err_out) {
+  const bool additive = opc == DSE_OP_ADD || opc == DSE_OP_SUB || opc == DSE_OP_ABSDIFF;
+  int reason = DSE_VALID;
+  EvalErr<R> ee{R(0), R(0)};
+  if (additive && A.unit_check_addsub &&
+      (A.F.ukey[2 * ia] != A.F.ukey[2 * ib] || A.F.ukey[2 * ia + 1] != A.F.ukey[2 * ib + 1]))
+    reason = DSE_R_UNIT;
+  else if (A.max_complexity > 0 && A.F.cplx[ia] + A.F.cplx[ib] + 1 > A.max_complexity)
+    reason = DSE_R_COMPLEXITY;
+  else if (opc == DSE_OP_DIV && !(A.F.flags[ib] & F_MINABS_POS))
+    reason = DSE_R_DOMAIN;
+  else if (opc == DSE_OP_RDIV && !(A.F.flags[ia] & F_MINABS_POS))
+    reason = DSE_R_DOMAIN;
+  else {
+    float lo, hi;
+    if (opc == DSE_OP_MUL) {
+      lo = __fmul_rd(fa_a.w, fa_b.w);
+      hi = __fmul_ru(fa_a.z, fa_b.z);
+    } else if (opc == DSE_OP_DIV) {
+      float2 rr = A.F.fr[ib];
+      lo = __fmul_rd(fa_a.w, rr.y);
+      hi = __fmul_ru(fa_a.z, rr.x);
+    } else if (opc == DSE_OP_RDIV) {
+      float2 rr = A.F.fr[ia];
+      lo = __fmul_rd(fa_b.w, rr.y);
+      hi = __fmul_ru(fa_b.z, rr.x);
+    } else {
+      lo = __fadd_rd(fa_a.w, fa_b.w);
+      hi = __fadd_ru(fa_a.z, fa_b.z);
+    }
+    if (hi <= A.fmax32_dn) {
+    } else if (lo > A.fmax32_up) {
+      reason = DSE_R_MAGNITUDE;
+    } else {
+      reason = domain_magnitude64(opc, A.F.min64[ia], A.F.max64[ia], A.F.minabs64[ia], A.F.maxabs64[ia],
+                                  A.F.minabs64[ib], A.F.maxabs64[ib], A.fmax64, 0.0);
+    }
+    const R akk = kk < R(0) ? -kk : kk;
+    const R sqrtN = Num<R>::sqrt_((R)A.N);
+    const R na = (R)A.F.fnorm[ia], nb = (R)A.F.fnorm[ib];
+    if (opc == DSE_OP_MUL) {
+      ee.kappa = R(3.01);
+      ee.lambda = akk * sqrtN;
+    } else if (opc == DSE_OP_DIV || opc == DSE_OP_RDIV) {
+      ee.kappa = R(5.01);
+      ee.lambda = akk * sqrtN;
+    } else if (opc == DSE_OP_ABSDIFF) {
+      ee.kappa = R(0);
+      ee.lambda = R(3.01) * (na + nb) + akk * sqrtN;
+    } else {
+      const R am = mi < R(0) ? -mi : mi, bm = mj < R(0) ? -mj : mj;
+      ee.kappa = R(0);
+      ee.lambda = R(3.01) * (na + nb) + R(2.01) * (am + bm) * sqrtN;
+    }
+  }
+  *err_out = ee;
+  return reason;
+}
+
 // ------------------------------------------------------ threshold filter
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
+}
+
+// Histogram counts of a buffered entry's lower and upper bounds.
+__device__ __forceinline__ void count_bounds(const CandBufs &B, int l, float s, float eps) {
+  const int bl = score_bin(s - eps), bh = score_bin(s + eps);
+  atomicAdd(&B.hist[(size_t)l * kNumBins + bl], 1u);
+  atomicAdd(&B.hist_c[(size_t)l * kCoarse + bl / kFine], 1u);
+  atomicAdd(&B.hist_hi[(size_t)l * kNumBins + bh], 1u);
 }
 
 // Push (id, s, eps) into list `l` if s + eps reaches its threshold; warp-
@@ -149,10 +333,7 @@ __device__ __forceinline__ bool push_warp(const CandBufs &B, int l, bool want, u
       B.score[e] = s;
       B.eps[e] = eps;
     }
-    float lo = s - eps;
-    int bin = lo > 0.f ? (int)(lo * (float)kNumBins) : 0;
-    if (bin > kNumBins - 1) bin = kNumBins - 1;
-    atomicAdd(&B.hist[(size_t)l * kNumBins + bin], 1u);
+    count_bounds(B, l, s, eps);
   }
   return p;
 }
@@ -168,38 +349,47 @@ __device__ __forceinline__ bool push_one(const CandBufs &B, int l, uint64_t id, 
     B.score[e] = s;
     B.eps[e] = eps;
   }
-  float lo = s - eps;
-  int bin = lo > 0.f ? (int)(lo * (float)kNumBins) : 0;
-  if (bin > kNumBins - 1) bin = kNumBins - 1;
-  atomicAdd(&B.hist[(size_t)l * kNumBins + bin], 1u);
+  count_bounds(B, l, s, eps);
   return true;
 }
 
-// Raise list l's threshold to the lower edge of the highest bin b such that at
-// least k entries have lower bound >= b / kNumBins.  Whole warp calls.
-__device__ __forceinline__ void refresh_theta(const CandBufs &B, int l, int64_t k) {
+// Warp-wide scan of `n` (multiple of 32) counters from the top: the highest
+// index b with cum + sum(h[b..n)) >= k, or -1; *cum_out gets the sum above b.
+__device__ __forceinline__ int scan_top(const unsigned *h, int n, unsigned long long cum, unsigned long long k,
+                                        unsigned long long *cum_out) {
   const int lane = threadIdx.x & 31;
-  const unsigned *h = B.hist + (size_t)l * kNumBins;
-  unsigned long long cum = 0;
-  for (int top = kNumBins - 1; top >= 0; top -= 32) {
-    int b = top - lane;
-    unsigned v = b >= 0 ? ld_relaxed_u32(h + b) : 0u;
+  for (int top = n - 1; top >= 0; top -= 32) {
+    const int b = top - lane;
+    const unsigned v = b >= 0 ? ld_relaxed_u32(h + b) : 0u;
     unsigned long long x = v;
     for (int o = 1; o < 32; o <<= 1) {
       unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    unsigned ok = __ballot_sync(0xffffffffu, b >= 0 && cum + x >= (unsigned long long)k);
+    const unsigned ok = __ballot_sync(0xffffffffu, b >= 0 && cum + x >= k);
     if (ok) {
-      int first = __ffs(ok) - 1;
-      if (lane == 0) {
-        int bb = top - first;
-        if (bb > 0) atomic_max_nonneg(&B.theta[l], (float)bb / (float)kNumBins);
-      }
-      return;
+      const int first = __ffs(ok) - 1;
+      const unsigned long long before = __shfl_sync(0xffffffffu, x - v, first);
+      *cum_out = cum + before;
+      return top - first;
     }
     cum += __shfl_sync(0xffffffffu, x, 31);
   }
+  *cum_out = cum;
+  return -1;
+}
+
+// Raise list l's threshold to the lower edge of the highest bin b such that at
+// least k entries have lower bound >= b / kNumBins (coarse bins first, then
+// the fine bins of the crossing coarse bin).  Whole warp calls.
+__device__ __forceinline__ void refresh_theta(const CandBufs &B, int l, int64_t k) {
+  unsigned long long above = 0, above2 = 0;
+  const int c = scan_top(B.hist_c + (size_t)l * kCoarse, kCoarse, 0ull, (unsigned long long)k, &above);
+  if (c < 0) return;
+  const int f = scan_top(B.hist + (size_t)l * kNumBins + c * kFine, kFine, above, (unsigned long long)k, &above2);
+  if (f < 0) return;
+  const int bb = c * kFine + f;
+  if ((threadIdx.x & 31) == 0 && bb > 0) atomic_max_nonneg(&B.theta[l], (float)bb / (float)kNumBins);
 }
 
 }  // namespace dse

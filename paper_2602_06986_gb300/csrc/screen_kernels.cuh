@@ -12,10 +12,35 @@ void launch_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy,
 void launch_feature(int prec64, int nt, const ScreenArgs &A, uint64_t id0, uint64_t id1, uint64_t p0, uint64_t p1,
                     float gamma, int sms, cudaStream_t st);
 dse_status launch_pair(int prec64, int kind, int nt, const ScreenArgs &A, int block_len, int sms, cudaStream_t st);
-void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st);
+void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st, const ScreenArgs *batch = nullptr);
+void launch_pairlist(int prec64, int nt, const ScreenArgs &A, const int2 *pairs, int64_t n_pairs, float gamma,
+                     int sms, cudaStream_t st);
+
+// Batched screens (one problem per list; problem arguments in device array
+// `args`; work in jobs taken from a device counter).
+void launch_targets_batched(const double *Y, const int64_t *yoff, const ScreenArgs *args, int n, int32_t ldy,
+                            double *y64, float *y32, float *ysum32, int *err, cudaStream_t st);
+void launch_feature_batched(int prec64, const ScreenArgs *args, const Job *jobs, int n_jobs, unsigned int *counter,
+                            int sms, cudaStream_t st);
+dse_status launch_pair_batched(int prec64, int kind, const ScreenArgs &A0, const ScreenArgs *args, int sms,
+                               cudaStream_t st);
+void launch_pairlist_batched(int prec64, const ScreenArgs *args, const int2 *pairs, const Job *jobs, int n_jobs,
+                             unsigned int *counter, int sms, cudaStream_t st);
+
+// Per-list selection state.
+struct SelState {
+  unsigned n;               // buffered entries (capped)
+  int all_in;               // n <= k: every entry is retained
+  int binL, binH;           // bins holding L and H
+  unsigned rankL, rankH;    // their ranks within those bins
+  unsigned nL, nH;          // entries collected from those bins
+  float L, H;
+};
 
 // Selection of the exact top-k of every list from its candidate buffer.
 struct SelectArgs {
+  SelState *state;          // [lists]
+  float *colL, *colH;       // [lists][cap] bounds collected from the L / H bins
   CandBufs B;
   int32_t n_lists;
   int64_t k;
@@ -42,6 +67,7 @@ struct SelectArgs {
   unsigned long long *stats;
 };
 
-dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cudaStream_t st);
+dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cudaStream_t st,
+                         const ScreenArgs *batch = nullptr);
 
 }  // namespace dse

@@ -1,0 +1,646 @@
+// screen_tc.cu -- the multi-target screen on the 5th-generation tensor cores.
+//
+// With T targets (residuals or tasks) screened at once, the numerators
+// sum_s w_s y_{t,s} of every candidate are a dense contraction
+// D[m][t] = sum_s A[m][s] B[t][s] between the candidate values A (generated on
+// the fly, never written to HBM) and the targets B.  This kernel evaluates the
+// binary block of rung k tile by tile (128 pairs per tile, the three slots of
+// one kind) and contracts on tcgen05 in BF16x3: A = Ah + Al, B = Bh + Bl (BF16
+// splits of the FP32 values), D += Ah Bh + Ah Bl + Al Bh with FP32
+// accumulation in TMEM.  S1 = sum w and S2 = sum w^2 stay on the CUDA cores in
+// FP32.
+//
+// Warp roles (one CTA per SM, persistent over a static tile stride):
+//   warp 0        producer: 1-D bulk async copies of the tile's 24 operand
+//                 rows and the pre-split target block of each 32-sample chunk
+//                 into a 3-stage ring (mbarrier expect-tx);
+//   warp 1        TMEM allocation and the MMA issuer (one elected thread):
+//                 3 slots x 2 k-steps x 3 products per chunk; tcgen05.commit to
+//                 the stage's "empty" barrier and, after the last chunk of an
+//                 accumulation block, to the accumulator's "full" barrier;
+//   warps 2-9     generation: row m (a pair) x one half of each chunk's
+//                 samples: candidate values, FP32 S1/S2, BF16 hi/lo split,
+//                 16-byte stores into the canonical K-major layout (8x8 core
+//                 matrices, no swizzle), proxy fence, arrive;
+//   warps 10-13   epilogue: tcgen05.ld of TMEM lane quadrant (warp % 4),
+//                 block accumulation, scores, error bounds, threshold pushes.
+// Accumulators are double-buffered in TMEM by accumulation block (up to 16
+// chunks = 512 samples), so the epilogue of one block overlaps the MMAs of
+// the next; longer sample ranges drain each block into FP32 registers.
+//
+// Error model of the contraction (used for the reported bound, and the
+// reason reported TC scores above the 1e-5 tolerance are re-scored in FP64):
+// the BF16x3 split drops Al Bl and the splits' residuals, at most
+// 3.01 * 2^-18 of sum |w y|; each tensor-core accumulation step is modelled
+// with a relative error of 2u on the running sum of |terms|, with a safety
+// factor of 4.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "dse_internal.cuh"
+#include "eval64.cuh"
+#include "screen_common.cuh"
+#include "screen_kernels.cuh"
+#include "util.cuh"
+
+namespace dse {
+
+namespace tc {
+
+constexpr int M = 128;  // pairs per tile
+constexpr int BI = 16, BJ = 8, ROWS = BI + BJ;
+constexpr int KC = 32;    // samples per chunk (stage)
+constexpr int NS = 3;     // stages
+constexpr int KB = 16;    // chunks per accumulation block (512 samples)
+constexpr int NGEN = 8;   // generation warps
+constexpr int WARPS = 2 + NGEN + 4;
+constexpr int THREADS = WARPS * 32;
+constexpr uint32_t kWait = 1u << 22;
+
+constexpr uint32_t ROWS_BYTES = ROWS * KC * 4;  // 3072
+constexpr uint32_t A_TILE = M * KC * 2;         // 8192 per slot per hi/lo
+constexpr uint32_t A_OFF = ROWS_BYTES;
+constexpr uint32_t B_OFF = A_OFF + 6 * A_TILE;  // 52224
+__host__ __device__ constexpr uint32_t b_bytes(int ntp) { return 2u * (uint32_t)ntp * KC * 2; }
+__host__ __device__ constexpr uint32_t stage_bytes(int ntp) { return B_OFF + b_bytes(ntp); }
+
+// K-major tile of KC columns as 8x8 (16-byte-row) core matrices: core matrix
+// (row/8, k/8) at (row/8)*SBO + (k/8)*LBO; LBO = 128 (K direction), SBO =
+// KC/8*128 (row direction).
+constexpr uint32_t LBO = 128, SBO = (KC / 8) * 128;
+__host__ __device__ inline uint32_t core_off(int row, int k) {
+  return (uint32_t)(row >> 3) * SBO + (uint32_t)(k >> 3) * LBO + (uint32_t)(row & 7) * 16 + (uint32_t)(k & 7) * 2;
+}
+
+// Shared-memory matrix descriptor (no swizzle): start address >> 4, LBO >> 4
+// at bit 16, SBO >> 4 at bit 32, fixed 0b001 at bits 46-48.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+         (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: F32 accumulator (bit 4), BF16 A (bits
+// 7-9 = 1) and B (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at
+// bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+struct Shared {
+  uint64_t full_rows[NS], full_a[NS], empty[NS];
+  uint64_t acc_full[2], acc_empty[2], gen_done[2], epi_free[2];
+  uint64_t drain;  // last tcgen05.commit of the MMA issuer, before TMEM is freed
+  uint32_t tmem_base;
+  int abort;
+  float hand[2][2][M][6];  // [tile parity][sample half][row][S1, S2 per slot]
+};
+
+constexpr size_t shared_bytes() { return (sizeof(Shared) + 1023) / 1024 * 1024; }
+
+}  // namespace tc
+
+// Pre-split targets: for chunk c, {hi, lo} x ntp x KC BF16 in the core-matrix
+// layout (targets beyond T and samples beyond N are zero).
+__global__ void k_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N, int ntp, int nchunks,
+                             unsigned char *out) {
+  const int64_t total = (int64_t)nchunks * ntp * tc::KC;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ((int64_t)ntp * tc::KC));
+    const int rem = (int)(e % ((int64_t)ntp * tc::KC));
+    const int t = rem / tc::KC, k = rem % tc::KC;
+    const int s = c * tc::KC + k;
+    const float v = (t < T && s < N) ? y32[(int64_t)(t0 + t) * ldy + s] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    unsigned char *base = out + (size_t)c * tc::b_bytes(ntp);
+    *reinterpret_cast<__nv_bfloat16 *>(base + tc::core_off(t, k)) = h;
+    *reinterpret_cast<__nv_bfloat16 *>(base + (size_t)ntp * tc::KC * 2 + tc::core_off(t, k)) = l;
+  }
+}
+
+// Epilogue of one candidate (row m, slot k) with its NTP numerators.
+template <int NTP>
+__device__ __forceinline__ uint64_t tc_candidate(const ScreenArgs &A, LaneStats &ls, bool pv, int64_t ia, int64_t ib,
+                                                 int opc, uint64_t pbase, const float4 &fa_a, const float4 &fa_b,
+                                                 float kk, float mi, float mj, float S1, float S2, const float *Sy,
+                                                 float gamma_gen, float gamma_num, const float *ysum) {
+  const bool additive = opc == DSE_OP_ADD || opc == DSE_OP_SUB || opc == DSE_OP_ABSDIFF;
+  const int pos = A.slot_pos[opc - 6];
+  const uint64_t gid = (uint64_t)A.n_stored + pbase + (uint64_t)(pos < 0 ? 0 : pos);
+  const bool cand = pv && pos >= 0 && gid >= A.id_begin && gid < A.id_end;
+  if (!cand) return 0;
+  if (additive) ls.seen++;
+  EvalErr<float> ee{0.f, 0.f};
+  const int reason = binary_apriori_W<float>(A, opc, ia, ib, fa_a, fa_b, kk, mi, mj, &ee);
+  if (reason != DSE_VALID) {
+    ls.r[reason]++;
+    return 0;
+  }
+  if (!((A.F.flags[ia] & A.F.flags[ib]) & F_FP32_SAFE)) {
+    escalate(A, gid);
+    ls.escalated++;
+    return 0;
+  }
+  const float u = 5.9604644775390625e-8f;
+  const float N = (float)A.N, invN = (float)A.invN, sqrtN = sqrtf(N);
+  const float cshift = opc == DSE_OP_ADD ? mi + mj : opc == DSE_OP_SUB ? mi - mj : kk;
+  const CandInterval<float> ci =
+      cand_interval<float>(S1, S2, N, invN, sqrtN, cshift, ee, gamma_gen, u, (float)A.fmin_std_rel64);
+  if (ci.realised == 0) {
+    ls.r[DSE_R_REALISED]++;
+    return 0;
+  }
+  if (ci.realised == 2) {
+    escalate(A, gid);
+    ls.escalated++;
+    return 0;
+  }
+  ls.r[DSE_VALID]++;
+  ls.evaluated++;
+  uint64_t pushed = 0;
+  for (int t = 0; t < NTP; ++t) {
+    if (t >= A.T) break;
+    // cheap upper bound first: s + eps <= (|P| + dP) / q_lo
+    const float th = ld_relaxed(&A.B.theta[A.t0 + t]);
+    float s, e;
+    cand_score_num<float>(ci, S1, Sy[t], invN, ysum[t], gamma_gen, gamma_num, u, &s, &e);
+    if (s + e < th) continue;
+    if (push_one(A.B, A.t0 + t, gid, s, e * (1.0f + 2.4e-7f))) pushed |= 1ull << t;
+  }
+  return pushed;
+}
+
+template <int KIND, int NTP>
+__global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, const unsigned char *bsplit,
+                                                             float gamma_gen, float gamma_num, int gen_blk) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  Shared &sh = *reinterpret_cast<Shared *>(smem);
+  unsigned char *stages = smem + shared_bytes();
+  constexpr uint32_t SB = stage_bytes(NTP);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (A.N + KC - 1) / KC;
+  const int nblocks = (nchunks + KB - 1) / KB;
+  constexpr int TMEM_COLS = (6 * NTP <= 32)    ? 32
+                            : (6 * NTP <= 64)  ? 64
+                            : (6 * NTP <= 128) ? 128
+                            : (6 * NTP <= 256) ? 256
+                                               : 512;
+  static_assert(6 * NTP <= 512, "too many targets for the TMEM accumulators");
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&sh.full_rows[s], 1);
+      mbar_init(&sh.full_a[s], NGEN);
+      mbar_init(&sh.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.acc_full[b], 1);
+      mbar_init(&sh.acc_empty[b], 4);
+      mbar_init(&sh.gen_done[b], NGEN);
+      mbar_init(&sh.epi_free[b], 4);
+    }
+    mbar_init(&sh.drain, 1);
+    sh.abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                 "r"((uint32_t)TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sh.tmem_base;
+
+  // Every wait is bounded: on expiry the kernel records DSE_ETIMEOUT, raises
+  // the CTA's abort flag and every role leaves its loop.  wait() is for the
+  // single-thread roles, wait_warp() for whole warps (warp-uniform result).
+  volatile int *abort_flag = &sh.abort;
+  auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+    if (mbar_wait_bounded(bar, parity, kWait)) return true;
+    atomicExch(A.err, DSE_ETIMEOUT);
+    *abort_flag = 1;
+    return false;
+  };
+  auto wait_warp = [&](uint64_t *bar, uint32_t parity) -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, kWait));
+    if (!ok && lane == 0) {
+      atomicExch(A.err, DSE_ETIMEOUT);
+      *abort_flag = 1;
+    }
+    return ok;
+  };
+  auto aborted_warp = [&]() -> bool { return __any_sync(0xffffffffu, *abort_flag != 0); };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int lt = 0;
+      uint32_t issued = 0;  // chunks whose copies were issued
+      for (int tile = blockIdx.x; tile < A.n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
+        const Tile tl = A.tiles[tile];
+        int32_t ids[ROWS];
+        for (int r = 0; r < ROWS; ++r) {
+          int id = -1;
+          if (r < BI) {
+            if (r < tl.ni) id = A.rowid[tl.ibase + r];
+          } else if (r - BI < tl.nj) {
+            id = A.rowid[tl.jbase + r - BI];
+          }
+          ids[r] = id;
+        }
+        for (int c = 0; c < nchunks; ++c) {
+          const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
+          if (u >= 1 && !wait(&sh.empty[st], (u - 1) & 1)) break;
+          unsigned char *S = stages + (size_t)st * SB;
+          const int64_t s0 = (int64_t)c * KC;
+          int64_t cnt = A.F.ld - s0;
+          if (cnt > KC) cnt = KC;
+          const uint32_t rb = (uint32_t)cnt * 4u;
+          uint32_t bytes = b_bytes(NTP);
+          for (int r = 0; r < ROWS; ++r)
+            if (ids[r] >= 0) bytes += rb;
+          mbar_arrive_expect_tx(&sh.full_rows[st], bytes);
+          for (int r = 0; r < ROWS; ++r)
+            if (ids[r] >= 0) bulk_g2s(S + r * KC * 4, A.F.v32 + (int64_t)ids[r] * A.F.ld + s0, rb, &sh.full_rows[st]);
+          bulk_g2s(S + B_OFF, bsplit + (size_t)c * b_bytes(NTP), b_bytes(NTP), &sh.full_rows[st]);
+          issued = gc + 1;
+        }
+      }
+      // no copy may still be landing when the CTA exits (normally these
+      // phases completed long ago and the waits return at once)
+      for (uint32_t st = 0; st < (uint32_t)NS && st < issued; ++st) {
+        const uint32_t last = (issued - 1 - st) / NS * NS + st;  // last use of stage st
+        mbar_wait_bounded(&sh.full_rows[st], (last / NS) & 1, kWait);
+      }
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0) {
+      constexpr uint32_t IDESC = idesc_bf16(M, NTP);
+      int lt = 0;
+      for (int tile = blockIdx.x; tile < A.n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
+        for (int b = 0; b < nblocks && !*abort_flag; ++b) {
+          const uint32_t gb = (uint32_t)lt * nblocks + b, buf = gb & 1, ub = gb >> 1;
+          if (ub >= 1 && !wait(&sh.acc_empty[buf], (ub - 1) & 1)) break;
+          fence_after();
+          const int c_end = min(nchunks, (b + 1) * KB);
+          for (int c = b * KB; c < c_end; ++c) {
+            const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
+            if (!wait(&sh.full_rows[st], u & 1) || !wait(&sh.full_a[st], u & 1)) break;
+            fence_after();
+            const uint32_t sbase = smem_u32(stages + (size_t)st * SB);
+            const uint32_t bh = sbase + B_OFF, bl = bh + (uint32_t)NTP * KC * 2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const uint32_t d = tmem + (buf * 3 + k) * NTP;
+              const uint32_t ah = sbase + A_OFF + (2 * k) * A_TILE, al = ah + A_TILE;
+#pragma unroll
+              for (int kk = 0; kk < KC / 16; ++kk) {
+                const uint32_t koff = kk * 2 * LBO;
+                const uint32_t acc = (c == b * KB && kk == 0) ? 0u : 1u;
+                mma_bf16(d, smem_desc(ah + koff), smem_desc(bh + koff), IDESC, acc);
+                mma_bf16(d, smem_desc(ah + koff), smem_desc(bl + koff), IDESC, 1u);
+                mma_bf16(d, smem_desc(al + koff), smem_desc(bh + koff), IDESC, 1u);
+              }
+            }
+            mma_commit(&sh.empty[st]);
+            if (c == c_end - 1) mma_commit(&sh.acc_full[buf]);
+          }
+        }
+      }
+      // every MMA this thread issued has completed before TMEM is freed
+      mma_commit(&sh.drain);
+      mbar_wait_bounded(&sh.drain, 0, kWait);
+    }
+  } else if (warp < 2 + NGEN) {
+    // ---------------------------------------------------------- generation
+    const int gw = warp - 2;
+    const int m = (gw & 3) * 32 + lane;  // row = pair
+    const int half = gw >> 2;            // which 16 samples of a chunk
+    const int ti = m >> 3, tj = m & 7;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < A.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
+      const Tile tl = A.tiles[tile];
+      const int fi = ti < tl.ni ? A.rowid[tl.ibase + ti] : -1;
+      const int fj = tj < tl.nj ? A.rowid[tl.jbase + tj] : -1;
+      const float4 fa_i = fi >= 0 ? A.F.fa[fi] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 fa_j = fj >= 0 ? A.F.fa[fj] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float mi = fa_i.x, mj = fa_j.x;
+      float c0, c1, c2;
+      if (KIND == KIND_MUL) {
+        c0 = mi * mj;
+        c1 = mi * fa_j.y;
+        c2 = mj * fa_i.y;
+      } else {
+        c0 = c1 = 0.f;
+        c2 = fabsf(mi - mj);
+      }
+      float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, t1[3] = {0.f, 0.f, 0.f}, t2[3] = {0.f, 0.f, 0.f};
+      int blk = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c) {
+        const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
+        if (!wait_warp(&sh.full_rows[st], u & 1)) {
+          ok = false;
+          break;
+        }
+        unsigned char *S = stages + (size_t)st * SB;
+        const float *ra = reinterpret_cast<const float *>(S) + ti * KC;
+        const float *rb = reinterpret_cast<const float *>(S) + (BI + tj) * KC;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const int k0s = half * 16 + g * 8;
+          uint32_t hi[3][4], lo[3][4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            float wv[2][3];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int kk = k0s + e + q;
+              if (c * KC + kk < A.N) {
+                const float a = ra[kk], b = rb[kk];
+                if (KIND == KIND_MUL) {
+                  wv[q][0] = fmaf(a, b, -c0);
+                  wv[q][1] = fmaf(a, rcp_approx(b), -c1);
+                  wv[q][2] = fmaf(b, rcp_approx(a), -c2);
+                } else {
+                  const float ac = a - mi, bc = b - mj, d = a - b;
+                  wv[q][0] = ac + bc;
+                  wv[q][1] = ac - bc;
+                  wv[q][2] = fabsf(d) - c2;
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                  t1[k] += wv[q][k];
+                  t2[k] = fmaf(wv[q][k], wv[q][k], t2[k]);
+                }
+              } else {
+                wv[q][0] = wv[q][1] = wv[q][2] = 0.f;
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(wv[0][k]), h1 = __float2bfloat16_rn(wv[1][k]);
+              const __nv_bfloat16 l0 = __float2bfloat16_rn(wv[0][k] - __bfloat162float(h0));
+              const __nv_bfloat16 l1 = __float2bfloat16_rn(wv[1][k] - __bfloat162float(h1));
+              hi[k][e >> 1] = pack_bf16(h0, h1);
+              lo[k][e >> 1] = pack_bf16(l0, l1);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            *reinterpret_cast<uint4 *>(S + A_OFF + (2 * k) * A_TILE + core_off(m, k0s)) =
+                make_uint4(hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
+            *reinterpret_cast<uint4 *>(S + A_OFF + (2 * k + 1) * A_TILE + core_off(m, k0s)) =
+                make_uint4(lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
+          }
+        }
+        if (++blk == gen_blk) {
+          blk = 0;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            s1[k] += t1[k];
+            s2[k] += t2[k];
+            t1[k] = t2[k] = 0.f;
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.full_a[st]);
+      }
+      if (!ok) break;
+      // hand this half's S1/S2 of the row to the epilogue warps
+      const int p = lt & 1;
+      if (lt >= 2 && !wait_warp(&sh.epi_free[p], ((lt >> 1) - 1) & 1)) break;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sh.hand[p][half][m][2 * k] = s1[k] + t1[k];
+        sh.hand[p][half][m][2 * k + 1] = s2[k] + t2[k];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.gen_done[p]);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;
+    const int m = q * 32 + lane;
+    const int ti = m >> 3, tj = m & 7;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const float *ysum = A.ysum32 + A.t0;  // read per target (L1-resident)
+    LaneStats ls;
+    ls.zero();
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < A.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
+      const Tile tl = A.tiles[tile];
+      const int64_t x = ti < tl.ni ? A.rowid[tl.ibase + ti] : -1;
+      const int64_t y = tj < tl.nj ? A.rowid[tl.jbase + tj] : -1;
+      bool pv = x >= 0 && y >= 0 && (tl.ibase + ti) > (tl.jbase + tj);
+      const int64_t ia = x > y ? x : y, ib = x > y ? y : x;
+      pv = pv && ia >= A.G.o;
+      uint64_t pbase = 0;
+      if (pv) pbase = A.G.um + (tri((uint64_t)ia) + (uint64_t)ib - A.G.tri_o) * (uint64_t)A.G.nb;
+      const float4 fa_x = x >= 0 ? A.F.fa[x] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 fa_y = y >= 0 ? A.F.fa[y] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 fa_a = x > y ? fa_x : fa_y, fa_b = x > y ? fa_y : fa_x;
+      const float mi = fa_x.x, mj = fa_y.x;  // evaluation order: row i, row j
+      float kks[3];
+      if (KIND == KIND_MUL) {
+        kks[0] = mi * mj;
+        kks[1] = mi * fa_y.y;
+        kks[2] = mj * fa_x.y;
+      } else {
+        kks[0] = kks[1] = 0.f;
+        kks[2] = fabsf(mi - mj);
+      }
+      // numerators: one block stays in TMEM until the end; longer sample
+      // ranges are drained block by block into registers
+      float acc[3][NTP <= 32 ? NTP : 1];
+      if (nblocks > 1) {
+        if (NTP <= 32) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int t = 0; t < (NTP <= 32 ? NTP : 1); ++t) acc[k][t] = 0.f;
+          for (int b = 0; b < nblocks; ++b) {
+            const uint32_t gb = (uint32_t)lt * nblocks + b, buf = gb & 1, ub = gb >> 1;
+            if (!wait_warp(&sh.acc_full[buf], ub & 1)) break;
+            fence_after();
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+              for (int c16 = 0; c16 < (NTP <= 32 ? NTP : 16); c16 += 16) {
+                float v[16];
+                tmem_ld16(tmem + lane_base + (buf * 3 + k) * NTP + c16, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                  if (c16 + i < (NTP <= 32 ? NTP : 1)) acc[k][c16 + i] += v[i];
+              }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
+          }
+        }
+      }
+      const uint32_t gb_last = (uint32_t)lt * nblocks + (nblocks - 1), buf_last = gb_last & 1;
+      if (nblocks == 1 && !wait_warp(&sh.acc_full[buf_last], (gb_last >> 1) & 1)) break;
+      if (aborted_warp()) break;
+      fence_after();
+      const int p = lt & 1;
+      if (!wait_warp(&sh.gen_done[p], (lt >> 1) & 1)) break;
+      float st12[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) st12[i] = sh.hand[p][0][m][i] + sh.hand[p][1][m][i];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.epi_free[p]);
+      uint64_t pushed = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int opc = KIND == KIND_MUL ? (k == 0 ? DSE_OP_MUL : k == 1 ? DSE_OP_DIV : DSE_OP_RDIV)
+                                         : (k == 0 ? DSE_OP_ADD : k == 1 ? DSE_OP_SUB : DSE_OP_ABSDIFF);
+        float Sy[NTP];
+        if (nblocks == 1) {
+#pragma unroll
+          for (int c16 = 0; c16 < NTP; c16 += 16) tmem_ld16(tmem + lane_base + (buf_last * 3 + k) * NTP + c16, Sy + c16);
+        } else {
+#pragma unroll
+          for (int t = 0; t < NTP; ++t) Sy[t] = NTP <= 32 ? acc[k][t < (NTP <= 32 ? NTP : 1) ? t : 0] : 0.f;
+        }
+        pushed |= tc_candidate<NTP>(A, ls, pv, ia, ib, opc, pbase, fa_a, fa_b, kks[k], mi, mj, st12[2 * k],
+                                    st12[2 * k + 1], Sy, gamma_gen, gamma_num, ysum);
+      }
+      if (nblocks == 1) {
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.acc_empty[buf_last]);
+      }
+      // raise the thresholds of the lists this warp pushed to
+      unsigned lo = (unsigned)pushed, hi = (unsigned)(pushed >> 32);
+      lo = __reduce_or_sync(0xffffffffu, lo);
+      hi = __reduce_or_sync(0xffffffffu, hi);
+      const uint64_t all = (uint64_t)lo | ((uint64_t)hi << 32);
+      for (int t = 0; t < NTP && t < 64; ++t)
+        if (all & (1ull << t)) refresh_theta(A.B, A.t0 + t, A.k);
+    }
+    flush_stats(A, ls);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  __syncwarp();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TMEM_COLS)
+                 : "memory");
+}
+
+// --------------------------------------------------------------- launcher
+
+template <int KIND, int NTP>
+static dse_status launch_tc_t(const ScreenArgs &A, const unsigned char *bsplit, float gamma_gen, float gamma_num,
+                              int gen_blk, int sms, cudaStream_t st) {
+  const size_t smem = tc::shared_bytes() + (size_t)tc::NS * tc::stage_bytes(NTP);
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!attr[dev & 63]) {
+    DSE_CUDA(cudaFuncSetAttribute(k_pair_tc<KIND, NTP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[dev & 63] = true;
+  }
+  int grid = sms < A.n_tiles ? sms : A.n_tiles;
+  if (grid < 1) return DSE_OK;
+  note_launches(1);
+  ScreenArgs B = A;
+  B.group = KIND == KIND_MUL ? 1 : 2;
+  k_pair_tc<KIND, NTP><<<grid, tc::THREADS, smem, st>>>(B, bsplit, gamma_gen, gamma_num, gen_blk);
+  return DSE_OK;
+}
+
+int tc_ntp_for(int T, int N) {
+  // one accumulation block keeps every target in TMEM; longer sample ranges
+  // drain blocks into registers, which bounds the targets per pass at 32
+  const int nchunks = (N + tc::KC - 1) / tc::KC;
+  const int cap = nchunks > tc::KB ? 32 : 64;
+  int t = T < cap ? T : cap;
+  return t <= 16 ? 16 : t <= 32 ? 32 : t <= 48 ? 48 : 64;
+}
+
+size_t tc_bsplit_bytes(int ntp, int N) {
+  const int nchunks = (N + tc::KC - 1) / tc::KC;
+  return (size_t)nchunks * tc::b_bytes(ntp);
+}
+
+void launch_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N, int ntp, unsigned char *out,
+                       cudaStream_t st) {
+  const int nchunks = (N + tc::KC - 1) / tc::KC;
+  const int64_t total = (int64_t)nchunks * ntp * tc::KC;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  note_launches(1);
+  k_tc_targets<<<(unsigned)blocks, 256, 0, st>>>(y32, ldy, t0, T, N, ntp, nchunks, out);
+}
+
+dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, float gamma_gen,
+                          float gamma_num, int gen_blk, int sms, cudaStream_t st) {
+  if (A.n_tiles <= 0) return DSE_OK;
+  if (ntp > 32 && (A.N + tc::KC - 1) / tc::KC > tc::KB) {
+    set_error("target block %d needs N <= %d samples", ntp, tc::KB * tc::KC);
+    return DSE_EINVAL;
+  }
+#define DSE_TC_CASE(NTPV)                                                                                   \
+  case NTPV:                                                                                                \
+    return kind == KIND_MUL ? launch_tc_t<KIND_MUL, NTPV>(A, bsplit, gamma_gen, gamma_num, gen_blk, sms, st) \
+                            : launch_tc_t<KIND_ADD, NTPV>(A, bsplit, gamma_gen, gamma_num, gen_blk, sms, st);
+  switch (ntp) {
+    DSE_TC_CASE(16)
+    DSE_TC_CASE(32)
+    DSE_TC_CASE(48)
+    DSE_TC_CASE(64)
+    default:
+      set_error("unsupported target block %d", ntp);
+      return DSE_EINVAL;
+  }
+#undef DSE_TC_CASE
+}
+
+}  // namespace dse

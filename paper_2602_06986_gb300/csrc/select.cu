@@ -9,8 +9,15 @@
 //   otherwise       it is undecided and re-scored in FP64.
 // The retained set (certain + undecided) is ordered by score (FP64 where
 // re-scored), then id, and its first k entries are the result: order by score
-// descending, then global id ascending (the SIS top-k, SISSO screening).
+// descending, then global id ascending (the SIS top-k of SISSO screening).
+//
+// L and H come from the bound histograms the screen kept while buffering:
+// the bin holding the k-th lower bound (resp. (k+1)-th upper bound) is found
+// from the counts, and only the entries of that one bin are ranked exactly.
+// Every pass over the buffers is spread over the whole GPU.
 #include <math.h>
+
+#include <algorithm>
 
 #include "dse_internal.cuh"
 #include "eval64.cuh"
@@ -20,39 +27,111 @@
 
 namespace dse {
 
-__device__ __forceinline__ uint32_t key_lo(float s, float e) {
+__device__ __forceinline__ float lo_of(float s, float e) {
   float lo = s - e;
-  if (!(lo > 0.f)) lo = 0.f;
-  return __float_as_uint(lo);
+  return lo > 0.f ? lo : 0.f;
 }
-__device__ __forceinline__ uint32_t key_hi(float s, float e) {
+__device__ __forceinline__ float hi_of(float s, float e) {
   float hi = s + e;
-  if (!(hi > 0.f)) hi = 0.f;
-  return __float_as_uint(hi);
+  return hi > 0.f ? hi : 0.f;
 }
 
-// k-th largest key (1-based) among n entries; block-wide radix select.
-template <bool HI>
-__device__ uint32_t kth_largest(const float *s, const float *e, int64_t n, int64_t k, unsigned *hist) {
+// Highest bin b of h[0..kNumBins) whose suffix count reaches k; *rank = k minus
+// the count above b.  One block of 1024 threads.
+__device__ int suffix_bin(const unsigned *h, unsigned long long k, unsigned long long *rank,
+                          unsigned long long *suf) {
+  for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) suf[b] = h[b];
+  __syncthreads();
+  // suffix sums (Hillis-Steele from the top)
+  for (int o = 1; o < kNumBins; o <<= 1) {
+    unsigned long long v[kNumBins / 1024];
+    for (int r = 0; r < kNumBins / 1024; ++r) {
+      int b = threadIdx.x + r * 1024;
+      v[r] = (b + o < kNumBins) ? suf[b + o] : 0ull;
+    }
+    __syncthreads();
+    for (int r = 0; r < kNumBins / 1024; ++r) suf[threadIdx.x + r * 1024] += v[r];
+    __syncthreads();
+  }
+  __shared__ int found;
+  if (threadIdx.x == 0) found = -1;
+  __syncthreads();
+  for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) {
+    unsigned long long above = b + 1 < kNumBins ? suf[b + 1] : 0ull;
+    if (suf[b] >= k && above < k) {
+      found = b;
+      *rank = k - above;
+    }
+  }
+  __syncthreads();
+  return found;
+}
+
+// 1) per list: entry count, overflow flag, bins and in-bin ranks of L and H.
+__global__ void __launch_bounds__(1024) k_sel_bins(const SelectArgs S) {
+  __shared__ unsigned long long suf[kNumBins];
+  __shared__ unsigned long long rankL, rankH;
+  const int l = blockIdx.x;
+  const unsigned cnt = S.B.count[l];
+  const int64_t n = (int64_t)cnt < S.B.cap ? (int64_t)cnt : S.B.cap;
+  SelState st{};
+  st.n = (unsigned)n;
+  if (n <= S.k) {
+    st.all_in = 1;
+    st.binL = st.binH = -1;
+  } else {
+    st.binL = suffix_bin(S.B.hist + (size_t)l * kNumBins, (unsigned long long)S.k, &rankL, suf);
+    st.binH = suffix_bin(S.B.hist_hi + (size_t)l * kNumBins, (unsigned long long)S.k + 1ull, &rankH, suf);
+    st.rankL = (unsigned)rankL;
+    st.rankH = (unsigned)rankH;
+  }
+  if (threadIdx.x == 0) {
+    S.overflow[l] = (int64_t)cnt > S.B.cap ? 1u : 0u;
+    S.state[l] = st;
+    S.r_count[l] = 0;
+  }
+}
+
+// 2) entries of the L bin and of the H bin, per list (all blocks, 2-D grid).
+__global__ void k_sel_collect(const SelectArgs S) {
+  const int l = blockIdx.y;
+  const SelState st = S.state[l];
+  if (st.all_in) return;
+  const size_t base = (size_t)l * S.B.cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float s = S.B.score[base + i], e = S.B.eps[base + i];
+    if (score_bin(s - e) == st.binL) {
+      unsigned p = atomicAdd(&S.state[l].nL, 1u);
+      S.colL[base + p] = lo_of(s, e);
+    }
+    if (score_bin(s + e) == st.binH) {
+      unsigned p = atomicAdd(&S.state[l].nH, 1u);
+      S.colH[base + p] = hi_of(s, e);
+    }
+  }
+}
+
+// r-th largest (1-based) of n non-negative floats; block-wide radix select.
+__device__ float kth_largest(const float *v, unsigned n, unsigned r, unsigned *hist) {
   __shared__ uint32_t sh_prefix, sh_mask;
-  __shared__ unsigned long long sh_rem;
+  __shared__ unsigned sh_rem;
   if (threadIdx.x == 0) {
     sh_prefix = 0;
     sh_mask = 0;
-    sh_rem = (unsigned long long)k;
+    sh_rem = r;
   }
   __syncthreads();
   for (int shift = 24; shift >= 0; shift -= 8) {
     for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     const uint32_t prefix = sh_prefix, mask = sh_mask;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      uint32_t key = HI ? key_hi(s[i], e[i]) : key_lo(s[i], e[i]);
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+      uint32_t key = __float_as_uint(v[i]);
       if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned long long cum = 0, rem = sh_rem;
+      unsigned cum = 0, rem = sh_rem;
       int d = 255;
       for (; d > 0; --d) {
         if (cum + hist[d] >= rem) break;
@@ -64,35 +143,35 @@ __device__ uint32_t kth_largest(const float *s, const float *e, int64_t n, int64
     }
     __syncthreads();
   }
-  return sh_prefix;
+  return __uint_as_float(sh_prefix);
 }
 
-// One block per list: thresholds, classification, retained set, FP64 jobs.
-__global__ void __launch_bounds__(1024) k_classify(const SelectArgs S) {
+// 3) exact L and H from their bins (one block per list).
+__global__ void __launch_bounds__(1024) k_sel_exact(const SelectArgs S) {
   __shared__ unsigned hist[256];
-  __shared__ unsigned sh_rn;
   const int l = blockIdx.x;
-  const unsigned cnt = S.B.count[l];
-  const int64_t n = (int64_t)cnt < S.B.cap ? (int64_t)cnt : S.B.cap;
-  if (threadIdx.x == 0) {
-    S.overflow[l] = (int64_t)cnt > S.B.cap ? 1u : 0u;
-    sh_rn = 0;
-  }
+  SelState st = S.state[l];
+  if (st.all_in) return;
   const size_t base = (size_t)l * S.B.cap;
-  const float *sc = S.B.score + base, *ep = S.B.eps + base;
-  float L = -1.f, H = -1.f;
-  if (n > S.k) {
-    L = __uint_as_float(kth_largest<false>(sc, ep, n, S.k, hist));
-    H = __uint_as_float(kth_largest<true>(sc, ep, n, S.k + 1, hist));
+  const float L = kth_largest(S.colL + base, st.nL, st.rankL, hist);
+  const float H = kth_largest(S.colH + base, st.nH, st.rankH, hist);
+  if (threadIdx.x == 0) {
+    S.state[l].L = L;
+    S.state[l].H = H;
   }
-  __syncthreads();
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const float s = sc[i], e = ep[i];
-    const float lo = __uint_as_float(key_lo(s, e)), hi = __uint_as_float(key_hi(s, e));
-    const bool in = n <= S.k || lo > H;
-    const bool und = !in && hi >= L;
+}
+
+// 4) classification into the retained set and the FP64 job list (all blocks).
+__global__ void k_sel_classify(const SelectArgs S) {
+  const int l = blockIdx.y;
+  const SelState st = S.state[l];
+  const size_t base = (size_t)l * S.B.cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float s = S.B.score[base + i], e = S.B.eps[base + i];
+    const bool in = st.all_in || lo_of(s, e) > st.H;
+    const bool und = !in && hi_of(s, e) >= st.L;
     if (!(in || und)) continue;
-    const unsigned pos = atomicAdd(&sh_rn, 1u);
+    const unsigned pos = atomicAdd(&S.r_count[l], 1u);
     const size_t r = base + pos;
     S.r_id[r] = S.B.id[base + i];
     S.r_s32[r] = s;
@@ -105,18 +184,23 @@ __global__ void __launch_bounds__(1024) k_classify(const SelectArgs S) {
       S.job_list[j] = (uint32_t)l;
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) S.r_count[l] = sh_rn;
 }
 
-// FP64 re-score: one warp per job.
-__global__ void k_rescore(const SelectArgs S, const ScreenArgs A) {
-  const int lane = threadIdx.x & 31;
+// 5) FP64 re-score: one block of kRes threads per job, one pass over the
+// samples with sums shifted by the candidate's first value (so Sxx = S2 - S1^2/N
+// keeps FP64 accuracy), targets of the list (all targets in aggregated mode,
+// at most 16 there).
+constexpr int kRes = 128;
+
+// batch != nullptr: list l is problem l of a batched screen.
+__global__ void __launch_bounds__(kRes) k_rescore(const SelectArgs S, const ScreenArgs A0, const ScreenArgs *batch) {
+  __shared__ double red[kRes / 32][18];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned nj = *S.n_jobs;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t N = A.N;
-  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nj; w += warps) {
+  for (unsigned w = blockIdx.x; w < nj; w += gridDim.x) {
     const unsigned pos = S.job[w], l = S.job_list[w];
+    const ScreenArgs &A = batch ? batch[l] : A0;
+    const int64_t N = A.N;
     const size_t r = (size_t)l * S.B.cap + pos;
     const uint64_t gid = S.r_id[r];
     int op;
@@ -130,33 +214,44 @@ __global__ void k_rescore(const SelectArgs S, const ScreenArgs A) {
     }
     const double *xa = A.F.v64 + a * A.F.ld;
     const double *xb = A.F.v64 + (b >= 0 ? b : a) * A.F.ld;
-    double sum = 0.0;
-    for (int64_t s = lane; s < N; s += 32) sum += eval_op64(op, xa[s], xb[s]);
-    sum = warp_sum64(sum);
-    const double mean = sum / (double)N;
-    double sxx = 0.0;
-    for (int64_t s = lane; s < N; s += 32) {
-      double d = eval_op64(op, xa[s], xb[s]) - mean;
-      sxx = fma(d, d, sxx);
-    }
-    sxx = warp_sum64(sxx);
     const int t_begin = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
-    const int t_end = A.mode == DSE_MODE_AGGREGATED ? A.T : (int)l + 1;
-    double agg = 0.0;
-    for (int t = t_begin; t < t_end; ++t) {
-      const double *y = A.y64 + (int64_t)t * A.ldy;
-      double sxy = 0.0;
-      for (int64_t s = lane; s < N; s += 32) sxy = fma(eval_op64(op, xa[s], xb[s]) - mean, y[s], sxy);
-      sxy = warp_sum64(sxy);
-      double sc = fabs(sxy) / sqrt(sxx);
-      agg += sc * sc;
+    const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < 16 ? A.T : 16) : 1;
+    const double c = eval_op64(op, xa[0], xb[0]);
+    double acc[18];
+    for (int i = 0; i < 18; ++i) acc[i] = 0.0;
+    for (int64_t s = threadIdx.x; s < N; s += kRes) {
+      const double v = eval_op64(op, xa[s], xb[s]) - c;
+      acc[0] += v;
+      acc[1] = fma(v, v, acc[1]);
+      for (int t = 0; t < nt; ++t) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
     }
-    double sc = A.mode == DSE_MODE_AGGREGATED ? sqrt(agg / (double)A.T) : sqrt(agg);
-    if (lane == 0) {
+    for (int i = 0; i < 2 + nt; ++i) {
+      double v = warp_sum64(acc[i]);
+      if (lane == 0) red[wid][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t1 = 0, t2 = 0;
+      for (int q = 0; q < kRes / 32; ++q) {
+        t1 += red[q][0];
+        t2 += red[q][1];
+      }
+      const double mean = t1 / (double)N;
+      const double sxx = t2 - t1 * mean;
+      double agg = 0.0;
+      for (int t = 0; t < nt; ++t) {
+        double sy = 0;
+        for (int q = 0; q < kRes / 32; ++q) sy += red[q][2 + t];
+        // the targets are centred: sum (v - vbar) y = sum (v - c) y - (vbar - c) sum y, sum y = 0 up to rounding
+        const double sc = fabs(sy) / sqrt(sxx);
+        agg += sc * sc;
+      }
+      const double sc = A.mode == DSE_MODE_AGGREGATED ? sqrt(agg / (double)nt) : sqrt(agg);
       S.r_s64[r] = sc;
-      S.r_e64[r] = (double)(N / 32 + 40) * 1.1102230246251565e-16 * 8.0 * (sc + 1e-3);
+      S.r_e64[r] = (double)(N / kRes + 64) * 1.1102230246251565e-16 * 16.0 * (sc + 1e-3);
       atomicAdd(&A.stats[ST_RESCORED], 1ull);
     }
+    __syncthreads();
   }
 }
 
@@ -190,7 +285,7 @@ __device__ void bitonic(double *key, uint64_t *id, int64_t M) {
 
 constexpr int64_t kSmemSort = 4096;
 
-// One block per list: order the retained set and write the first k.
+// 6) one block per list: order the retained set and write the first k.
 __global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int l = blockIdx.x;
@@ -207,8 +302,6 @@ __global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
     key = S.sort_key + (size_t)l * S.sort_cap;
     id = S.sort_id + (size_t)l * S.sort_cap;
   }
-  // id slot holds the retained position; ties are resolved on the real ids
-  // below, so sort on (key, global id) pairs directly.
   for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
     if (i < rn) {
       const size_t r = base + i;
@@ -221,16 +314,14 @@ __global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
   }
   __syncthreads();
   bitonic(key, id, M);
-  // look up each output's bound by searching the retained set (rn small
-  // relative to the work above; entries are unique by id)
   const int64_t nout = rn < S.k ? rn : S.k;
   for (int64_t i = threadIdx.x; i < nout; i += blockDim.x) {
     S.out_id[(size_t)l * S.k + i] = id[i];
     S.out_score[(size_t)l * S.k + i] = key[i];
   }
   __syncthreads();
+  // each retained entry finds its rank by binary search and writes its bound
   for (int64_t i = threadIdx.x; i < rn; i += blockDim.x) {
-    // position of entry i in the sorted order: binary search on (key, id)
     const size_t r = base + i;
     const double k0 = S.r_need[r] ? S.r_s64[r] : (double)S.r_s32[r];
     const uint64_t i0 = S.r_id[r];
@@ -245,10 +336,16 @@ __global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
   if (threadIdx.x == 0) S.out_n[l] = nout;
 }
 
-dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cudaStream_t st) {
-  note_launches(3);
-  k_classify<<<S.n_lists, 1024, 0, st>>>(S);
-  k_rescore<<<sms * 4, 256, 0, st>>>(S, A);
+dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cudaStream_t st,
+                         const ScreenArgs *batch) {
+  note_launches(6);
+  k_sel_bins<<<S.n_lists, 1024, 0, st>>>(S);
+  const unsigned bx = (unsigned)std::max(1, std::min(256, (sms * 4 + S.n_lists - 1) / S.n_lists));
+  dim3 g(bx, S.n_lists);
+  k_sel_collect<<<g, 256, 0, st>>>(S);
+  k_sel_exact<<<S.n_lists, 1024, 0, st>>>(S);
+  k_sel_classify<<<g, 256, 0, st>>>(S);
+  k_rescore<<<sms * 8, kRes, 0, st>>>(S, A, batch);
   static bool attr = false;
   if (!attr) {
     DSE_CUDA(cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -26,20 +26,50 @@ dse_status cuda_status(cudaError_t e, const char *what) {
   return e == cudaErrorMemoryAllocation ? DSE_ENOMEM : DSE_ECUDA;
 }
 
+// The stream that dmalloc / dfree order their pool operations on (set by each
+// entry point for the duration of the call).
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+
+AllocStream::AllocStream(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+AllocStream::~AllocStream() { g_alloc_stream = prev; }
+
 dse_status dmalloc(void **p, size_t bytes, const char *what) {
+  return dmalloc_async(p, bytes, g_alloc_stream, what);
+}
+
+void dfree(void *p) { dfree_async(p, g_alloc_stream); }
+
+// Stream-ordered allocation from the device's default memory pool.  The
+// pool's release threshold is raised once per device for this process, so
+// freed blocks stay cached and a later allocation of a similar size costs no
+// driver round trip and no device-wide synchronisation.
+static bool g_pool_ready[64] = {false};
+
+dse_status dmalloc_async(void **p, size_t bytes, cudaStream_t s, const char *what) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !g_pool_ready[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    g_pool_ready[dev] = true;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error("cudaMalloc(%zu) for %s: %s", bytes, what, cudaGetErrorString(e));
+    set_error("cudaMallocAsync(%zu) for %s: %s", bytes, what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? DSE_ENOMEM : DSE_ECUDA;
   }
   return DSE_OK;
 }
 
-void dfree(void *p) {
-  if (p) cudaFree(p);
+void dfree_async(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
 }
 
 bool is_device_pointer(const void *p) {

@@ -28,13 +28,23 @@ dse_status cuda_status(cudaError_t e, const char *what);
     if (s_ != DSE_OK) return s_;       \
   } while (0)
 
-// Device allocation that records DSE_ENOMEM.
+// Device allocation that records DSE_ENOMEM.  Allocations are stream-ordered
+// on the stream installed by the innermost AllocStream guard (each entry point
+// installs its descriptor's stream), from the device's cached memory pool.
+struct AllocStream {
+  explicit AllocStream(cudaStream_t s);
+  ~AllocStream();
+  cudaStream_t prev;
+};
 dse_status dmalloc(void **p, size_t bytes, const char *what);
 template <typename T>
 dse_status dalloc(T **p, size_t count, const char *what) {
   return dmalloc(reinterpret_cast<void **>(p), count * sizeof(T), what);
 }
 void dfree(void *p);
+// Stream-ordered, pool-cached allocation (cudaMallocAsync / cudaFreeAsync).
+dse_status dmalloc_async(void **p, size_t bytes, cudaStream_t s, const char *what);
+void dfree_async(void *p, cudaStream_t s);
 
 // Order-preserving selection: out[j] = the j-th index p < n with flags[p] == want.
 // Writes the count to *count_host (synchronises the stream).

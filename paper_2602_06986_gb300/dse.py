@@ -65,8 +65,19 @@ class RefitDesc(C.Structure):
                 ("reserved0", C.c_int32), ("stream", C.c_void_p)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("space", C.c_void_p), ("y", C.c_void_p), ("y_on_device", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("k", C.c_int64), ("precision", C.c_int32), ("flags", C.c_int32), ("stream", C.c_void_p)]
+
+
+BATCH_GRAPH = 1
+
 EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_counts", "dse_decode",
            "dse_expr_string", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
+           "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
            "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error", "dse_version"]
 
 _lib = None
@@ -92,14 +103,20 @@ def lib():
         L.dse_result_free.restype = None
         L.dse_topk_fetch.argtypes = [vp, i32, vp, vp, vp, i64, C.POINTER(i64)]
         L.dse_result_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.dse_sis_screen_batched.argtypes = [C.POINTER(BatchItem), i32, C.POINTER(BatchDesc), C.POINTER(vp)]
+        L.dse_batch_rescreen.argtypes = [vp, vp, i32]
+        L.dse_batch_fetch.argtypes = [vp, i32, vp, vp, vp, i64, C.POINTER(i64)]
+        L.dse_batch_stats.argtypes = [vp, i32, C.POINTER(Stats)]
+        L.dse_batch_free.argtypes = [vp]
+        L.dse_batch_free.restype = None
         L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
         L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
         L.dse_last_error.restype = C.c_char_p
         L.dse_version.restype = C.c_char_p
         L.dse_kernel_launches.restype = i64
         for name in EXPORTS:
-            if name not in ("dse_space_free", "dse_result_free", "dse_last_error", "dse_version",
-                            "dse_kernel_launches"):
+            if name not in ("dse_space_free", "dse_result_free", "dse_batch_free", "dse_last_error",
+                            "dse_version", "dse_kernel_launches"):
                 getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -153,15 +170,79 @@ class Result:
     def stats(self) -> dict:
         s = Stats()
         _check(lib().dse_result_stats(self._h, C.byref(s)))
-        return {"screened": s.screened, "reasons": {REASONS[i]: s.reasons[i] for i in range(6)},
-                "evaluated": s.evaluated, "buffered": s.buffered, "escalated": s.escalated,
-                "rescored": s.rescored, "reruns": s.reruns, "precision_used": s.precision_used,
-                "max_err_bound": s.max_err_bound, "valid_by_group": list(s.valid_by_group),
-                "kernel_ms": list(s.kernel_ms), "kernel_launches": s.kernel_launches}
+        return _stats_dict(s)
 
     def free(self):
         if self._h:
             lib().dse_result_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _stats_dict(s) -> dict:
+    return {"screened": s.screened, "reasons": {REASONS[i]: s.reasons[i] for i in range(6)},
+                "evaluated": s.evaluated, "buffered": s.buffered, "escalated": s.escalated,
+                "rescored": s.rescored, "reruns": s.reruns, "precision_used": s.precision_used,
+                "max_err_bound": s.max_err_bound, "valid_by_group": list(s.valid_by_group),
+            "kernel_ms": list(s.kernel_ms), "kernel_launches": s.kernel_launches}
+
+
+class Batch:
+    """A batched screen over many (space, target) problems (dse_sis_screen_batched).
+
+    ``spaces``: Space objects (kept alive by the batch); ``targets``: one
+    target per space (numpy arrays or torch CUDA tensors of that space's
+    n_samples values).  The first screen is enqueued at construction;
+    ``rescreen`` screens again with new targets (replaying a CUDA graph with
+    ``graph=True``)."""
+
+    def __init__(self, spaces, targets, k, precision=PREC_FP32, graph=False, stream=None):
+        self.spaces = list(spaces)
+        self.k = k
+        self._keep = []
+        items = (BatchItem * len(self.spaces))()
+        for i, (sp, y) in enumerate(zip(self.spaces, targets)):
+            if isinstance(y, np.ndarray):
+                y = np.ascontiguousarray(y, dtype=np.float64)
+            self._keep.append(y)
+            py, ydev = _ptr(y)
+            items[i] = BatchItem(sp._h.value, py, ydev, 0)
+        d = BatchDesc(k, precision, BATCH_GRAPH if graph else 0, stream)
+        h = C.c_void_p()
+        _check(lib().dse_sis_screen_batched(items, len(self.spaces), C.byref(d), C.byref(h)))
+        self._h = h
+
+    def rescreen(self, Ycat):
+        """New targets, concatenated in problem order."""
+        if isinstance(Ycat, np.ndarray):
+            Ycat = np.ascontiguousarray(Ycat, dtype=np.float64)
+        self._ycat = Ycat
+        py, ydev = _ptr(Ycat)
+        _check(lib().dse_batch_rescreen(self._h, py, ydev))
+
+    def fetch(self, item):
+        n = C.c_int64()
+        ids = np.zeros(self.k, np.uint64)
+        sc = np.zeros(self.k)
+        eb = np.zeros(self.k)
+        _check(lib().dse_batch_fetch(self._h, item, ids.ctypes.data, sc.ctypes.data, eb.ctypes.data, self.k,
+                                     C.byref(n)))
+        m = n.value
+        return ids[:m].copy(), sc[:m].copy(), eb[:m].copy()
+
+    def stats(self, item) -> dict:
+        s = Stats()
+        _check(lib().dse_batch_stats(self._h, item, C.byref(s)))
+        return _stats_dict(s)
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().dse_batch_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -124,22 +124,25 @@ def large(seed: int = 0, n_targets: int = 16):
                 max_rung=2, unit_check_addsub=1, explog_dimensionless=1, k=10000)
 
 
-def batched(seed: int = 0, n_base: int = 32, n_folds: int = 5, n_boot: int = 3):
+def batched(seed: int = 0, n_base: int = 32, n_folds: int = 5, n_boot: int = 3, n_hi: int = 5000,
+            p_hi: int = 30):
     """256 problems = 32 base datasets x (5 CV-fold training sets + 3 bootstrap
     resamples).  Base sizes N_b are log-uniform so that problem sample counts
     span [50, 5000]; each base has 10-30 primaries U[0.5,5] (FP32) with units
     over 3 dims, the full op library, rung 2 and a planted target; top-200 per
-    problem.  Each problem is (base index, sample gather list)."""
+    problem.  Each problem is (base index, sample gather list).  n_hi / p_hi
+    shrink the largest base and primary count for cases the oracle screens
+    in full."""
     rng = np.random.Generator(np.random.PCG64(4000 + seed))
     bases, problems = [], []
-    lo, hi = np.log(50 / 0.8), np.log(5000)
+    lo, hi = np.log(50 / 0.8), np.log(n_hi)
     for b in range(n_base):
         Nb = int(round(np.exp(rng.uniform(lo, hi))))
         if b == 0:
             Nb = int(np.ceil(50 / 0.8))
         if b == 1:
-            Nb = 5000
-        n0 = int(rng.integers(10, 31))
+            Nb = n_hi
+        n0 = int(rng.integers(10, p_hi + 1))
         X = _f32(rng.uniform(0.5, 5.0, size=(n0, Nb)))
         units = _units(rng, n0, 3)
         a, c, d = rng.choice(n0, size=3, replace=False)

@@ -45,6 +45,8 @@ def test_struct_layouts_match_header(dse):
     assert C.sizeof(dse.Stats) == 8 + 8 * 6 + 8 * 4 + 4 * 2 + 8 + 8 * 3 + 8 * 4 + 8
     assert C.sizeof(dse.Expr) == 4 * 2 + 8 * 2
     assert C.sizeof(dse.RefitDesc) == 8 + 4 * 2 + 8 + 8 + 8 + 4 * 2 + 8
+    assert C.sizeof(dse.BatchItem) == 8 + 8 + 4 * 2
+    assert C.sizeof(dse.BatchDesc) == 8 + 4 * 2 + 8
 
 
 def test_version_and_null_arguments(dse):
@@ -54,6 +56,11 @@ def test_version_and_null_arguments(dse):
     assert b"null" in L.dse_last_error()
     assert L.dse_sis_screen(None, None, None) == dse.EINVAL
     assert L.dse_topk_fetch(None, 0, None, None, None, 0, None) == dse.EINVAL
+    assert L.dse_sis_screen_batched(None, 0, None, None) == dse.EINVAL
+    assert L.dse_batch_rescreen(None, None, 0) == dse.EINVAL
+    assert L.dse_batch_fetch(None, 0, None, None, None, 0, None) == dse.EINVAL
+    assert L.dse_batch_stats(None, 0, None) == dse.EINVAL
+    L.dse_batch_free(None)
 
 
 def test_invalid_descriptor_rejected_before_device(dse):

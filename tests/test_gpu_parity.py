@@ -127,6 +127,29 @@ def test_multi_target(env, T, mode):
     assert res.stats()["reasons"] == ocnt
 
 
+@pytest.mark.parametrize("wname,T", [("tiny", 17), ("tiny", 40), ("medium", 8), ("medium", 33)])
+def test_tensor_core_multi_target(env, wname, T):
+    """BF16x3 tcgen05 contraction (one TMEM block at N=100, drained blocks at
+    N=1000) against the oracle, per target."""
+    torch, oracle, dse, W = env
+    w = getattr(W, wname)(7)
+    X = w["X"]
+    rng = np.random.default_rng(T)
+    N = X.shape[1]
+    Y = np.stack([X[rng.integers(len(X))] * X[rng.integers(len(X))] / X[rng.integers(len(X))]
+                  + 0.05 * rng.standard_normal(N) for _ in range(T)])
+    sp, orc = spaces(env, w)
+    k = 50
+    res = sp.screen(torch.from_numpy(Y).cuda(), k, precision=dse.PREC_BF16X3)
+    st = res.stats()
+    assert st["precision_used"] == dse.PREC_BF16X3
+    oids, osc, ocnt = orc.screen(Y, k)
+    assert st["reasons"] == ocnt
+    for l in range(T):
+        ids, sc, eb = res.fetch(l)
+        check_list(ids, sc, eb, oids[l], osc[l], orc, Y, l)
+
+
 def test_ranges_merge_to_full(env):
     """Screening disjoint ragged id ranges and merging their top-k equals the
     full screen (the index-range sharding of the multi-GPU plan)."""
