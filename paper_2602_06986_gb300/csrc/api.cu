@@ -403,12 +403,14 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
     // generation sums: 16 samples of each chunk per thread, blocks of
     // gen_blk chunks, the two halves added at the end
     plan.gamma_gen = (float)((16.0 * plan.gen_blk + ceil((double)nchunks / plan.gen_blk) + 6.0) * u32 * 1.05);
-    // contraction: BF16x3 split (3.01 * 2^-18) plus 2u per tensor-core
+    // contraction: BF16x3 split (w = wh + wl + ew with |ew| <= 2^-16 |w|, the
+    // same for y; dropping wl*yl, ew*y and w*ey leaves at most 3.01 * 2^-16
+    // of sum |w y|) plus 2u per tensor-core
     // accumulation step (3 products x 2 k-steps per chunk, up to 16 chunks per
     // TMEM block) and the register drain of the blocks, times a safety factor 4
     const int nblocks = (nchunks + 15) / 16;
     const double steps = 3.0 * 2.0 * std::min(nchunks, 16);
-    plan.gamma_num = (float)(4.0 * (2.0 * steps + nblocks + 2.0) * u32 + 3.02 * 3.814697265625e-6 +
+    plan.gamma_num = (float)(4.0 * (2.0 * steps + nblocks + 2.0) * u32 + 3.02 * 1.52587890625e-5 +
                              (double)plan.gamma_gen);
   }
 
@@ -474,6 +476,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   sc.add(&R->out_score, (size_t)n_lists * d->k);
   sc.add(&R->out_eps, (size_t)n_lists * d->k);
   sc.add(&R->out_n, (size_t)n_lists);
+  sc.add(&S.max_eps, (size_t)n_lists);
   const bool big_sort = cap > 4096;
   sc.add(&S.sort_key, big_sort ? (size_t)n_lists * sort_cap : 1);
   sc.add(&S.sort_id, big_sort ? (size_t)n_lists * sort_cap : 1);
@@ -556,6 +559,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   S.out_score = R->out_score;
   S.out_eps = R->out_eps;
   S.out_n = R->out_n;
+  R->max_eps = S.max_eps;
   S.sort_cap = big_sort ? sort_cap : 1;
   S.stats = R->stats;
 
@@ -588,18 +592,29 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
 }
 
 // Wait for a result, re-running the screen while any list overflowed its
-// buffer (the thresholds reached so far stay valid lower bounds).
+// buffer (the thresholds reached so far stay valid lower bounds).  Every
+// small device result is copied asynchronously into the thread's pinned
+// staging area, so each attempt costs one stream synchronisation.
 static dse_status finish(dse_result *R) {
   if (R->fetched) return DSE_OK;
   cudaStream_t st = R->stream;
+  const int nl = R->n_lists;
+  // staging layout: stats | out_n | max_eps | overflow | buf_count | err
+  const size_t o_stats = 0, o_n = o_stats + 8 * ST_COUNT, o_eps = o_n + 8 * (size_t)nl,
+               o_ov = o_eps + 8 * (size_t)nl, o_bc = o_ov + 4 * (size_t)nl, o_err = o_bc + 4 * (size_t)nl,
+               bytes = o_err + 8;
   for (int attempt = 0;; ++attempt) {
-    std::vector<unsigned> ov(R->n_lists);
-    unsigned long long hs[ST_COUNT];
-    int herr = 0;
-    DSE_CUDA(cudaMemcpyAsync(ov.data(), R->overflow, sizeof(unsigned) * R->n_lists, cudaMemcpyDeviceToHost, st));
-    DSE_CUDA(cudaMemcpyAsync(hs, R->stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-    DSE_CUDA(cudaMemcpyAsync(&herr, R->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    char *h = static_cast<char *>(pinned_staging(bytes));
+    if (!h) return DSE_ENOMEM;
+    DSE_CUDA(cudaMemcpyAsync(h + o_stats, R->stats, 8 * ST_COUNT, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(h + o_n, R->out_n, 8 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(h + o_eps, R->max_eps, 8 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(h + o_ov, R->overflow, 4 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(h + o_bc, R->buf_count, 4 * (size_t)nl, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(h + o_err, R->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     DSE_CUDA(cudaStreamSynchronize(st));
+    const unsigned long long *hs = reinterpret_cast<const unsigned long long *>(h + o_stats);
+    const int herr = *reinterpret_cast<const int *>(h + o_err);
     if (herr) {
       set_error(herr == DSE_ETIMEOUT ? "a bounded device wait timed out" : "invalid target (zero variance or not finite)");
       return herr;
@@ -608,50 +623,45 @@ static dse_status finish(dse_result *R) {
       set_error("escalation list overflow");
       return DSE_EOVERFLOW;
     }
+    const unsigned *ov = reinterpret_cast<const unsigned *>(h + o_ov);
     bool any = false;
-    for (unsigned v : ov) any |= v != 0;
-    if (!any || attempt >= 8) {
-      if (any) {
-        set_error("candidate buffer overflow persisted");
-        return DSE_EOVERFLOW;
-      }
-      dse_stats &o = R->host_stats;
-      for (int c = 0; c < 6; ++c) o.reasons[c] = (int64_t)hs[ST_REASON0 + c];
-      o.reasons[DSE_R_UNIT] += (int64_t)R->add_total - (int64_t)hs[ST_ADD_SEEN];
-      o.evaluated = (int64_t)hs[ST_EVALUATED];
-      for (int g = 0; g < 3; ++g) o.valid_by_group[g] = (int64_t)hs[ST_VALID_G0 + g];
-      for (int g = 0; g < 4; ++g) o.kernel_ms[g] = 0.0;
-      for (auto &t : R->timing) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, t.second.first, t.second.second) == cudaSuccess && t.first >= 0 &&
-            t.first < 4)
-          o.kernel_ms[t.first] += ms;
-      }
-      o.kernel_launches = R->launches;
-      {
-        std::vector<unsigned> bc(R->n_lists);
-        DSE_CUDA(cudaMemcpy(bc.data(), R->buf_count, sizeof(unsigned) * R->n_lists, cudaMemcpyDeviceToHost));
-        o.buffered = 0;
-        for (unsigned v : bc) o.buffered += v;
-      }
-      o.escalated = (int64_t)hs[ST_ESCALATED];
-      o.rescored = (int64_t)hs[ST_RESCORED];
-      o.reruns = R->reruns;
-      std::vector<int64_t> nout(R->n_lists);
-      DSE_CUDA(cudaMemcpy(nout.data(), R->out_n, 8 * R->n_lists, cudaMemcpyDeviceToHost));
-      double mx = 0;
-      for (int l = 0; l < R->n_lists; ++l) {
-        std::vector<double> eps(nout[l]);
-        if (nout[l])
-          DSE_CUDA(cudaMemcpy(eps.data(), R->out_eps + (size_t)l * R->k, 8 * nout[l], cudaMemcpyDeviceToHost));
-        for (double x : eps) mx = std::max(mx, x);
-      }
-      o.max_err_bound = mx;
-      R->fetched = true;
-      return DSE_OK;
+    for (int l = 0; l < nl; ++l) any |= ov[l] != 0;
+    if (any && attempt < 8) {
+      ++R->reruns;
+      DSE_TRY(R->rerun(R));
+      continue;
     }
-    ++R->reruns;
-    DSE_TRY(R->rerun(R));
+    if (any) {
+      set_error("candidate buffer overflow persisted");
+      return DSE_EOVERFLOW;
+    }
+    dse_stats &o = R->host_stats;
+    for (int c = 0; c < 6; ++c) o.reasons[c] = (int64_t)hs[ST_REASON0 + c];
+    o.reasons[DSE_R_UNIT] += (int64_t)R->add_total - (int64_t)hs[ST_ADD_SEEN];
+    o.evaluated = (int64_t)hs[ST_EVALUATED];
+    for (int g = 0; g < 3; ++g) o.valid_by_group[g] = (int64_t)hs[ST_VALID_G0 + g];
+    for (int g = 0; g < 4; ++g) o.kernel_ms[g] = 0.0;
+    for (auto &t : R->timing) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.second.first, t.second.second) == cudaSuccess && t.first >= 0 && t.first < 4)
+        o.kernel_ms[t.first] += ms;
+    }
+    o.kernel_launches = R->launches;
+    const unsigned *bc = reinterpret_cast<const unsigned *>(h + o_bc);
+    o.buffered = 0;
+    for (int l = 0; l < nl; ++l) o.buffered += bc[l];
+    o.escalated = (int64_t)hs[ST_ESCALATED];
+    o.rescored = (int64_t)hs[ST_RESCORED];
+    o.reruns = R->reruns;
+    const int64_t *nout = reinterpret_cast<const int64_t *>(h + o_n);
+    const double *mx = reinterpret_cast<const double *>(h + o_eps);
+    R->h_out_n.assign(nout, nout + nl);
+    double m = 0.0;
+    for (int l = 0; l < nl; ++l)
+      if (nout[l] > 0) m = std::max(m, mx[l]);
+    o.max_err_bound = m;
+    R->fetched = true;
+    return DSE_OK;
   }
 }
 
@@ -833,18 +843,21 @@ dse_status dse_topk_fetch(dse_result *r, int32_t list, uint64_t *idx, double *sc
     return DSE_EINVAL;
   }
   DSE_TRY(finish(r));
-  int64_t n = 0;
-  DSE_CUDA(cudaMemcpy(&n, r->out_n + list, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  const int64_t n = r->h_out_n[list];
   if (n_out) *n_out = n;
   int64_t m = std::min(n, cap);
   if (m == 0) return DSE_OK;
   const size_t off = (size_t)list * r->k;
+  // copies on the result's stream; wait only when one lands in host memory
+  bool host = false;
   auto cp = [&](void *dst, const void *src, size_t bytes) {
-    return cudaMemcpy(dst, src, bytes, cudaMemcpyDefault);
+    host |= !is_device_pointer(dst);
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, r->stream);
   };
   if (idx) DSE_CUDA(cp(idx, r->out_id + off, 8 * m));
   if (score) DSE_CUDA(cp(score, r->out_score + off, 8 * m));
   if (err_bound) DSE_CUDA(cp(err_bound, r->out_eps + off, 8 * m));
+  if (host) DSE_CUDA(cudaStreamSynchronize(r->stream));
   return DSE_OK;
 }
 

@@ -75,6 +75,7 @@ struct dse_batch {
   int32_t reruns = 0;
   int64_t launches = 0;
   std::vector<dse_stats> host_stats;
+  std::vector<int64_t> h_out_n;
 };
 
 namespace {
@@ -188,9 +189,10 @@ dse_status finish(dse_batch *b) {
       return DSE_EOVERFLOW;
     }
     std::vector<int64_t> nout(n);
-    std::vector<double> eps((size_t)n * b->k);
+    std::vector<double> mxe(n);
     DSE_CUDA(cudaMemcpy(nout.data(), b->out_n, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
-    DSE_CUDA(cudaMemcpy(eps.data(), b->out_eps, sizeof(double) * eps.size(), cudaMemcpyDeviceToHost));
+    DSE_CUDA(cudaMemcpy(mxe.data(), b->S.max_eps, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    b->h_out_n = nout;
     b->host_stats.assign(n, dse_stats{});
     for (int p = 0; p < n; ++p) {
       const unsigned long long *h = hs.data() + (size_t)p * ST_COUNT;
@@ -206,9 +208,7 @@ dse_status finish(dse_batch *b) {
       o.precision_used = b->prec64 ? DSE_PREC_FP64 : DSE_PREC_FP32;
       for (int g = 0; g < 3; ++g) o.valid_by_group[g] = (int64_t)h[ST_VALID_G0 + g];
       o.kernel_launches = b->launches;
-      double mx = 0.0;
-      for (int64_t i = 0; i < nout[p]; ++i) mx = std::max(mx, eps[(size_t)p * b->k + i]);
-      o.max_err_bound = mx;
+      o.max_err_bound = nout[p] > 0 ? mxe[p] : 0.0;
     }
     b->fetched = true;
     return DSE_OK;
@@ -371,6 +371,7 @@ dse_status plan(const dse_batch_item *items, int32_t n, const dse_batch_desc *d,
   sc.add(&b->out_score, (size_t)n * k);
   sc.add(&b->out_eps, (size_t)n * k);
   sc.add(&b->out_n, (size_t)n);
+  sc.add(&S.max_eps, (size_t)n);
   sc.add(&S.sort_key, big_sort ? (size_t)n * sort_cap : 1);
   sc.add(&S.sort_id, big_sort ? (size_t)n * sort_cap : 1);
   DSE_TRY(sc.alloc(&b->scratch, &b->scratch_bytes));
@@ -549,8 +550,7 @@ dse_status dse_batch_fetch(dse_batch *b, int32_t item, uint64_t *idx, double *sc
   }
   AllocStream as(b->stream);
   DSE_TRY(finish(b));
-  int64_t n = 0;
-  DSE_CUDA(cudaMemcpy(&n, b->out_n + item, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  const int64_t n = b->h_out_n[item];
   if (n_out) *n_out = n;
   const int64_t m = std::min(n, cap);
   if (m == 0) return DSE_OK;

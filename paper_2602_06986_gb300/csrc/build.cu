@@ -34,14 +34,10 @@ __global__ void k_gather_rows(const double *X, int64_t ldx, const int64_t *idx, 
   }
 }
 
-// Summaries of stored rows [f0, f1): one warp per row.  Also the realised test
-// (finite, std > fmin * rms) into ok[f - f0] when ok != nullptr.
-__global__ void k_summaries(double *v64, int64_t ld, int64_t N, int64_t f0, int64_t f1, double *mean64,
-                            double *rmean64, double *min64, double *max64, double *minabs64, double *maxabs64,
-                            double *minabsnz64, double fmin_std_rel, uint8_t *ok) {
-  int lane = threadIdx.x & 31;
-  int64_t f = f0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  if (f >= f1) return;
+__device__ __forceinline__ void summary_one(double *v64, int64_t ld, int64_t N, int64_t f, int64_t f0,
+                                            double *mean64, double *rmean64, double *min64, double *max64,
+                                            double *minabs64, double *maxabs64, double *minabsnz64,
+                                            double fmin_std_rel, uint8_t *ok, int lane) {
   const double *x = v64 + f * ld;
   double mn = INFINITY, mx = -INFINITY, mna = INFINITY, mxa = 0.0, mnz = INFINITY, sum = 0.0;
   int fin = 1;
@@ -94,6 +90,18 @@ __global__ void k_summaries(double *v64, int64_t ld, int64_t N, int64_t f0, int6
   }
 }
 
+// Summaries of stored rows [f0, f1): one warp per row.  Also the realised test
+// (finite, std > fmin * rms) into ok[f - f0] when ok != nullptr.
+__global__ void k_summaries(double *v64, int64_t ld, int64_t N, int64_t f0, int64_t f1, double *mean64,
+                            double *rmean64, double *min64, double *max64, double *minabs64, double *maxabs64,
+                            double *minabsnz64, double fmin_std_rel, uint8_t *ok) {
+  int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
+  for (int64_t f = f0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; f < f1; f += warps)
+    summary_one(v64, ld, N, f, f0, mean64, rmean64, min64, max64, minabs64, maxabs64, minabsnz64, fmin_std_rel, ok,
+                lane);
+}
+
 // A-priori reason of every flat slot of rung r.
 __global__ void k_apriori_rung(FeatTable F, RungGeom g, AprioriParams P, uint8_t *why, int *bad) {
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < g.slots;
@@ -109,15 +117,11 @@ __global__ void k_apriori_rung(FeatTable F, RungGeom g, AprioriParams P, uint8_t
   }
 }
 
-// Realised test of listed slots (FP64 values, not stored): warp per slot.
-__global__ void k_realised_rung(FeatTable F, RungGeom g, const uint64_t *list, uint64_t n_list, double fmin_std_rel,
-                                uint8_t *why) {
-  int lane = threadIdx.x & 31;
-  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  if (w >= n_list) return;
+__device__ __forceinline__ void realised_one(FeatTable F, RungGeom g, uint64_t slot, double fmin_std_rel,
+                                             uint8_t *why, int lane) {
   int op;
   int64_t a, b;
-  decode_flat(g, list[w], &op, &a, &b);
+  decode_flat(g, slot, &op, &a, &b);
   const double *xa = F.v64 + a * F.ld;
   const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
   const int64_t N = F.N;
@@ -142,23 +146,59 @@ __global__ void k_realised_rung(FeatTable F, RungGeom g, const uint64_t *list, u
   if (lane == 0) {
     int good = fin;
     if (good && fmin_std_rel >= 0.0) good = __dsqrt_rn(sxx / (double)N) > fmin_std_rel * __dsqrt_rn(s2 / (double)N);
-    why[w] = (uint8_t)(good ? DSE_VALID : DSE_R_REALISED);
+    *why = (uint8_t)(good ? DSE_VALID : DSE_R_REALISED);
   }
 }
 
-// Store listed slots as new features [dst0, dst0 + n_list): warp per slot.
-__global__ void k_materialise(FeatTable F, RungGeom g, AprioriParams P, const uint64_t *list, uint64_t n_list,
-                              int64_t dst0, double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
-                              int32_t *cplx_out, int32_t *units_out) {
+// Realised test of listed slots (FP64 values, not stored): warp per slot;
+// the list length is *n_dev (at most n_cap).
+__global__ void k_realised_rung(FeatTable F, RungGeom g, const uint64_t *list, uint64_t n_cap,
+                                const unsigned long long *n_dev, double fmin_std_rel, uint8_t *why) {
   int lane = threadIdx.x & 31;
-  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  if (w >= n_list) return;
+  const uint64_t n_list = min((uint64_t)*n_dev, n_cap);
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) / 32;
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_list; w += warps)
+    realised_one(F, g, list[w], fmin_std_rel, why + w, lane);
+}
+
+// Rows keep[0..nk) of a table into rows 0..nk of another (values and
+// summaries): one block per kept row.
+__global__ void k_take_rows(const int64_t *keep, int64_t nk, int64_t ld, const double *v64, const double *mean64,
+                            const double *rmean64, const double *min64, const double *max64, const double *minabs64,
+                            const double *maxabs64, const double *minabsnz64, double *o_v64, double *o_mean64,
+                            double *o_rmean64, double *o_min64, double *o_max64, double *o_minabs64,
+                            double *o_maxabs64, double *o_minabsnz64) {
+  const int64_t f = blockIdx.x;
+  if (f >= nk) return;
+  const int64_t p = keep[f];
+  for (int64_t s = threadIdx.x; s < ld; s += blockDim.x) o_v64[f * ld + s] = v64[p * ld + s];
+  if (threadIdx.x == 0) {
+    o_mean64[f] = mean64[p];
+    o_rmean64[f] = rmean64[p];
+    o_min64[f] = min64[p];
+    o_max64[f] = max64[p];
+    o_minabs64[f] = minabs64[p];
+    o_maxabs64[f] = maxabs64[p];
+    o_minabsnz64[f] = minabsnz64[p];
+  }
+}
+
+// pos[x] = list[pos[x]] for x < *n_dev (at most n_cap): positions of the
+// second compaction back to flat slots.
+__global__ void k_map_positions(uint64_t *pos, const uint64_t *list, uint64_t n_cap, const unsigned long long *n_dev) {
+  const uint64_t n = min((uint64_t)*n_dev, n_cap);
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+    pos[x] = list[pos[x]];
+}
+
+__device__ __forceinline__ void materialise_one(FeatTable F, RungGeom g, AprioriParams P, uint64_t slot, int64_t f,
+                                                double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
+                                                int32_t *cplx_out, int32_t *units_out, int lane) {
   int op;
   int64_t a, b;
-  decode_flat(g, list[w], &op, &a, &b);
+  decode_flat(g, slot, &op, &a, &b);
   const double *xa = F.v64 + a * F.ld;
   const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
-  int64_t f = dst0 + (int64_t)w;
   double *out = v64 + f * F.ld;
   for (int64_t s = lane; s < F.ld; s += 32) out[s] = (s < F.N) ? eval_op64(op, xa[s], xb[s]) : 0.0;
   if (lane == 0) {
@@ -173,16 +213,35 @@ __global__ void k_materialise(FeatTable F, RungGeom g, AprioriParams P, const ui
   }
 }
 
+// Store listed slots as new features [dst0, dst0 + n_list): warp per slot.
+__global__ void k_materialise(FeatTable F, RungGeom g, AprioriParams P, const uint64_t *list, uint64_t n_list,
+                              int64_t dst0, double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
+                              int32_t *cplx_out, int32_t *units_out) {
+  int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) / 32;
+  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_list; w += warps)
+    materialise_one(F, g, P, list[w], dst0 + (int64_t)w, v64, op_out, ca_out, cb_out, cplx_out, units_out, lane);
+}
+
 // FP32 rows and per-feature helpers of every stored feature.
+// FP32 rows and per-feature helpers: one warp per feature (row conversion
+// and the FP64 sum of squares for the norm bound are coalesced over lanes).
 __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const double *v64, float *v32,
                             const double *mean64, const double *rmean64, const double *min64, const double *max64,
                             const double *minabs64, const double *maxabs64, const double *minabsnz64,
                             const int32_t *units, double exp_arg_max, float4 *fa, float2 *fr, uint32_t *flags,
                             uint64_t *ukey, float *fnorm) {
-  int64_t total = n * ld;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    v32[e] = (e % ld < N) ? __double2float_rn(v64[e]) : 0.0f;
-  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
+  for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; f < n; f += warps) {
+    double s2 = 0.0;
+    for (int64_t s = lane; s < ld; s += 32) {
+      const double v = s < N ? v64[f * ld + s] : 0.0;
+      v32[f * ld + s] = __double2float_rn(v);
+      s2 = __fma_rn(v, v, s2);
+    }
+    s2 = warp_sum64(s2);
+    if (lane) continue;
     double M = maxabs64[f], m = minabs64[f];
     fa[f] = make_float4(__double2float_rn(mean64[f]), __double2float_rn(rmean64[f]), __double2float_ru(M),
                         __double2float_rd(M));
@@ -212,9 +271,10 @@ __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const doubl
     flags[f] = fl;
     ukey[2 * f] = k0;
     ukey[2 * f + 1] = k1;
-    double s2 = 0.0;
-    for (int64_t s = 0; s < N; ++s) s2 = __fma_rn(v64[f * ld + s], v64[f * ld + s], s2);
-    fnorm[f] = __double2float_ru(__dsqrt_ru(s2 * (1.0 + 1e-12)));
+    // sum of non-negative terms: each lane's running sum of about N/32 FMAs
+    // then a 5-level tree, relative error below (N/32 + 8) u
+    const double margin = 1.0 + ((double)(N / 32) + 8.0) * 2.3e-16;
+    fnorm[f] = __double2float_ru(__dsqrt_ru(__dmul_ru(s2, margin)));
   }
 }
 
@@ -405,17 +465,22 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
         }
         hun[f * kMaxDims + k] = (int32_t)u;
       }
-      cudaMemcpyAsync(T.v64 + f * ld, T0.v64 + p * ld, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st);
-#define CP1(field) cudaMemcpyAsync(T.field + f, T0.field + p, sizeof(*T.field), cudaMemcpyDeviceToDevice, st)
-      CP1(mean64); CP1(rmean64); CP1(min64); CP1(max64); CP1(minabs64); CP1(maxabs64); CP1(minabsnz64);
-#undef CP1
     }
+    // (host-to-device copies from pageable memory are staged before the
+    // calls return, so the host vectors may go out of scope)
+    int64_t *keep_d = nullptr;
+    DSE_TRY(dalloc(&keep_d, nk, "kept primaries"));
+    DSE_CUDA(cudaMemcpyAsync(keep_d, keep.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+    note_launches(1);
+    k_take_rows<<<(unsigned)nk, 128, 0, st>>>(keep_d, nk, ld, T0.v64, T0.mean64, T0.rmean64, T0.min64, T0.max64,
+                                              T0.minabs64, T0.maxabs64, T0.minabsnz64, T.v64, T.mean64, T.rmean64,
+                                              T.min64, T.max64, T.minabs64, T.maxabs64, T.minabsnz64);
+    dfree(keep_d);
     DSE_CUDA(cudaMemcpyAsync(T.op, hop.data(), 4 * nk, cudaMemcpyHostToDevice, st));
     DSE_CUDA(cudaMemcpyAsync(T.cplx, hcx.data(), 4 * nk, cudaMemcpyHostToDevice, st));
     DSE_CUDA(cudaMemcpyAsync(T.units, hun.data(), 4 * nk * kMaxDims, cudaMemcpyHostToDevice, st));
     DSE_CUDA(cudaMemcpyAsync(T.ca, hca.data(), 8 * nk, cudaMemcpyHostToDevice, st));
     DSE_CUDA(cudaMemcpyAsync(T.cb, hcb.data(), 8 * nk, cudaMemcpyHostToDevice, st));
-    DSE_CUDA(cudaStreamSynchronize(st));
     T0.release();
   }
   int64_t n = nk;
@@ -423,58 +488,58 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   S->rung_begin[1] = n;
   S->h_rung.assign(n, 0);
 
-  int *bad = nullptr;
-  DSE_TRY(dalloc(&bad, 1, "flag"));
-  DSE_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
-  unsigned long long *cnt = nullptr;
-  DSE_TRY(dalloc(&cnt, 6, "counts"));
+  // per-rung counters on the device: 6 reason counts, a-priori valid count,
+  // realised count, error flag -- read back with one copy and one sync
+  unsigned long long *meta = nullptr;
+  DSE_TRY(dalloc(&meta, 10, "rung counters"));
+  unsigned long long *hmeta = static_cast<unsigned long long *>(pinned_staging(10 * sizeof(unsigned long long)));
+  if (!hmeta) {
+    dfree(meta);
+    T.release();
+    return DSE_ENOMEM;
+  }
 
   // --- rungs 1 .. max_rung-1
   for (int r = 1; r < d->max_rung; ++r) {
     RungGeom g = make_geom(S, r);
     FeatTable F = view(T, n, N, ld);
     S->slots[r] = g.slots;
-    uint8_t *why = nullptr;
-    uint64_t *list = nullptr;
+    uint8_t *why = nullptr, *rw = nullptr;
+    uint64_t *list = nullptr, *vlist = nullptr;
+    // capacities: every slot (the counts are known only on the device)
     DSE_TRY(dalloc(&why, g.slots, "slot reasons"));
-    k_apriori_rung<<<grid_for(g.slots, 256), 256, 0, st>>>(F, g, P, why, bad);
-    DSE_CUDA(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), st));
-    launch_count_reasons(why, g.slots, cnt, st);
-    unsigned long long hc[6];
-    DSE_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    int hbad = 0;
-    DSE_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSE_TRY(dalloc(&list, g.slots, "a-priori list"));
+    DSE_TRY(dalloc(&rw, g.slots, "realised flags"));
+    DSE_TRY(dalloc(&vlist, g.slots, "valid list"));
+    DSE_CUDA(cudaMemsetAsync(meta, 0, 10 * sizeof(unsigned long long), st));
+    note_launches(3);
+    if (g.slots) k_apriori_rung<<<grid_for(g.slots, 256), 256, 0, st>>>(F, g, P, why, (int *)(meta + 8));
+    launch_count_reasons(why, g.slots, meta, st);
+    DSE_TRY(compact_bytes_dev(why, g.slots, DSE_VALID, list, meta + 6, st));
+    dfree(why);
+    // realised test of the a-priori valid slots (flags past the count stay
+    // "not valid")
+    DSE_CUDA(cudaMemsetAsync(rw, 0xFF, g.slots, st));
+    if (g.slots)
+      k_realised_rung<<<grid_for(g.slots * 32, 256), 256, 0, st>>>(F, g, list, g.slots, meta + 6, S->fmin_std_rel,
+                                                                   rw);
+    DSE_TRY(compact_bytes_dev(rw, g.slots, DSE_VALID, vlist, meta + 7, st));
+    dfree(rw);
+    // vlist holds positions into list; map back to flat slots
+    if (g.slots) k_map_positions<<<grid_for(g.slots, 256, 1024), 256, 0, st>>>(vlist, list, g.slots, meta + 7);
+    dfree(list);
+    DSE_CUDA(cudaMemcpyAsync(hmeta, meta, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     DSE_CUDA(cudaStreamSynchronize(st));
+    const int hbad = (int)(hmeta[8] & 0xFFFFFFFFull);
     if (hbad) {
-      dfree(why);
+      dfree(vlist);
+      dfree(meta);
+      T.release();
       set_error(hbad == 1 ? "odd unit exponent under sqrt" : "unit exponent out of range");
       return DSE_EOVERFLOW;
     }
-    uint64_t n_ap = hc[DSE_VALID];
-    DSE_TRY(dalloc(&list, n_ap, "a-priori list"));
-    uint64_t got = 0;
-    DSE_TRY(compact_bytes(why, g.slots, DSE_VALID, list, &got, st));
-    dfree(why);
-    // realised test of the a-priori valid slots
-    uint8_t *rw = nullptr;
-    DSE_TRY(dalloc(&rw, n_ap, "realised flags"));
-    if (n_ap) k_realised_rung<<<grid_for(n_ap * 32, 256), 256, 0, st>>>(F, g, list, n_ap, S->fmin_std_rel, rw);
-    uint64_t *vlist = nullptr;
-    DSE_TRY(dalloc(&vlist, n_ap, "valid list"));
-    uint64_t n_new = 0;
-    DSE_TRY(compact_bytes(rw, n_ap, DSE_VALID, vlist, &n_new, st));
-    dfree(rw);
-    // vlist holds positions into list; map back to flat slots
-    std::vector<uint64_t> hpos(n_new), hlist(n_ap);
-    if (n_new) {
-      DSE_CUDA(cudaMemcpyAsync(hpos.data(), vlist, 8 * n_new, cudaMemcpyDeviceToHost, st));
-      DSE_CUDA(cudaMemcpyAsync(hlist.data(), list, 8 * n_ap, cudaMemcpyDeviceToHost, st));
-      DSE_CUDA(cudaStreamSynchronize(st));
-      for (uint64_t x = 0; x < n_new; ++x) hpos[x] = hlist[hpos[x]];
-      DSE_CUDA(cudaMemcpyAsync(vlist, hpos.data(), 8 * n_new, cudaMemcpyHostToDevice, st));
-    }
-    dfree(list);
-    for (int c = 0; c < 6; ++c) S->reasons[r][c] = (int64_t)hc[c];
+    const uint64_t n_ap = hmeta[6], n_new = hmeta[7];
+    for (int c = 0; c < 6; ++c) S->reasons[r][c] = (int64_t)hmeta[c];
     S->reasons[r][DSE_VALID] = (int64_t)n_new;
     S->reasons[r][DSE_R_REALISED] = (int64_t)(n_ap - n_new);
     S->have_counts[r] = true;
@@ -483,6 +548,7 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     dse_status s2 = table_alloc(T2, n + (int64_t)n_new, ld);
     if (s2 != DSE_OK) {
       dfree(vlist);
+      dfree(meta);
       T.release();
       return s2;
     }
@@ -495,7 +561,8 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
       k_summaries<<<grid_for(n_new * 32, 256), 256, 0, st>>>(T2.v64, ld, N, n, n + (int64_t)n_new, T2.mean64,
                                                              T2.rmean64, T2.min64, T2.max64, T2.minabs64, T2.maxabs64,
                                                              T2.minabsnz64, S->fmin_std_rel, nullptr);
-    DSE_CUDA(cudaStreamSynchronize(st));
+    // stream-ordered frees: the old table and the list stay valid for the
+    // kernels above
     dfree(vlist);
     T.release();
     T = T2;
@@ -503,8 +570,7 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     S->rung_begin[r + 1] = n;
     S->h_rung.resize(n, r);
   }
-  dfree(bad);
-  dfree(cnt);
+  dfree(meta);
 
   // --- FP32 rows and helpers
   S->n = n;
@@ -526,7 +592,7 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   DSE_TRY(dalloc(&S->fnorm, n, "helpers"));
   DSE_TRY(dalloc(&S->flags, n, "flags"));
   DSE_TRY(dalloc(&S->ukey, 2 * n, "unit keys"));
-  k_fp32_prep<<<grid_for(n * ld, 256), 256, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, T.mean64, T.rmean64, T.min64,
+  k_fp32_prep<<<grid_for(n * 32, 256), 256, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, T.mean64, T.rmean64, T.min64,
                                                      T.max64, T.minabs64, T.maxabs64, T.minabsnz64, T.units,
                                                      S->exp_arg_max, S->fa, S->fr, S->flags, S->ukey, S->fnorm);
   dfree(T.minabsnz64);
@@ -537,12 +603,22 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   S->h_ca.resize(n);
   S->h_cb.resize(n);
   S->h_ukey.resize(2 * n);
-  DSE_CUDA(cudaMemcpyAsync(S->h_op.data(), S->op, 4 * n, cudaMemcpyDeviceToHost, st));
-  DSE_CUDA(cudaMemcpyAsync(S->h_cplx.data(), S->cplx, 4 * n, cudaMemcpyDeviceToHost, st));
-  DSE_CUDA(cudaMemcpyAsync(S->h_ca.data(), S->ca, 8 * n, cudaMemcpyDeviceToHost, st));
-  DSE_CUDA(cudaMemcpyAsync(S->h_cb.data(), S->cb, 8 * n, cudaMemcpyDeviceToHost, st));
-  DSE_CUDA(cudaMemcpyAsync(S->h_ukey.data(), S->ukey, 16 * n, cudaMemcpyDeviceToHost, st));
-  DSE_CUDA(cudaStreamSynchronize(st));
+  {
+    // one pinned staging area, five asynchronous copies, one sync
+    char *hs = static_cast<char *>(pinned_staging((size_t)40 * n));
+    if (!hs) return DSE_ENOMEM;
+    DSE_CUDA(cudaMemcpyAsync(hs, S->op, 4 * n, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(hs + 4 * n, S->cplx, 4 * n, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(hs + 8 * n, S->ca, 8 * n, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(hs + 16 * n, S->cb, 8 * n, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(hs + 24 * n, S->ukey, 16 * n, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaStreamSynchronize(st));
+    memcpy(S->h_op.data(), hs, 4 * n);
+    memcpy(S->h_cplx.data(), hs + 4 * n, 4 * n);
+    memcpy(S->h_ca.data(), hs + 8 * n, 8 * n);
+    memcpy(S->h_cb.data(), hs + 16 * n, 8 * n);
+    memcpy(S->h_ukey.data(), hs + 24 * n, 16 * n);
+  }
 
   std::vector<int32_t> rows(n);
   std::iota(rows.begin(), rows.end(), 0);
@@ -565,7 +641,6 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   std::iota(ident.begin(), ident.end(), 0);
   DSE_CUDA(cudaMemcpyAsync(S->class_rows, rows.data(), 4 * n, cudaMemcpyHostToDevice, st));
   DSE_CUDA(cudaMemcpyAsync(S->rowid_ident, ident.data(), 4 * n, cudaMemcpyHostToDevice, st));
-  DSE_CUDA(cudaStreamSynchronize(st));
 
   S->geom = make_geom(S, d->max_rung);
   S->slots[d->max_rung] = S->geom.slots;

@@ -324,6 +324,8 @@ struct dse_result {
   double *out_score = nullptr;      // [lists][k]
   double *out_eps = nullptr;        // [lists][k]
   int64_t *out_n = nullptr;         // [lists]
+  double *max_eps = nullptr;        // [lists] largest returned bound
+  std::vector<int64_t> h_out_n;     // list lengths (host, after the wait)
   unsigned long long *stats = nullptr;
   int *err = nullptr;
   unsigned int *overflow = nullptr; // [lists]

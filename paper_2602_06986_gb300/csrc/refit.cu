@@ -9,6 +9,7 @@
 // equations by Cholesky (a column whose Cholesky pivot falls below 1e-12 of
 // its norm is rejected as collinear), the RMSE from the explicit residual.
 #include <math.h>
+#include <string.h>
 
 #include "dse_internal.cuh"
 #include "eval64.cuh"
@@ -172,11 +173,71 @@ __device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, int64_t n_stored, const double *y,
-                                                      const double *fixed_cols, int nf, const uint64_t *fixed_ids,
-                                                      const uint64_t *cand, int64_t n_cand, double *rmse_out,
-                                                      double *beta_out) {
+// Statistics of the fixed columns and the target, shared by every
+// candidate's fit (one block): means, centred copies, their centred Gram
+// matrix and products with the centred target, and the raw column norms
+// (for the collinearity test).  pre layout: [0..kMaxP) means of the fixed
+// columns, kMaxP: mean of y, then Gram lower triangle (kMaxP*kMaxP), then
+// products with y (kMaxP), then raw norms (kMaxP).
+constexpr int kPreMean = 0, kPreMy = kMaxP, kPreGram = kMaxP + 1, kPreG = kPreGram + kMaxP * kMaxP,
+              kPreNorm = kPreG + kMaxP, kPreSize = kPreNorm + kMaxP;
+
+__global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const double *fixed_cols, int nf, int64_t N,
+                                                      double *fcc, double *ycc, double *pre) {
+  __shared__ double sm[(kWide / 32) * (kMaxP * kMaxP + 2 * kMaxP)];
+  double mv[kMaxP + 1] = {0, 0, 0, 0, 0};
+  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+    for (int c = 0; c < nf; ++c) mv[c] += fixed_cols[(int64_t)c * N + s];
+    mv[kMaxP] += y[s];
+  }
+  block_sum_arr<kMaxP + 1>(mv, sm);
+  double m[kMaxP];
+  for (int c = 0; c < kMaxP; ++c) m[c] = mv[c] / (double)N;
+  const double my = mv[kMaxP] / (double)N;
+  double acc[kMaxP * kMaxP + 2 * kMaxP];
+  for (int i = 0; i < kMaxP * kMaxP + 2 * kMaxP; ++i) acc[i] = 0.0;
+  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+    double xc[kMaxP] = {0, 0, 0, 0};
+    for (int c = 0; c < nf; ++c) {
+      const double v = fixed_cols[(int64_t)c * N + s];
+      xc[c] = v - m[c];
+      fcc[(int64_t)c * N + s] = xc[c];
+      acc[kMaxP * kMaxP + kMaxP + c] = fma(v, v, acc[kMaxP * kMaxP + kMaxP + c]);
+    }
+    const double yc = y[s] - my;
+    ycc[s] = yc;
+    for (int c = 0; c < nf; ++c) {
+      for (int d = 0; d <= c; ++d) acc[c * kMaxP + d] = fma(xc[c], xc[d], acc[c * kMaxP + d]);
+      acc[kMaxP * kMaxP + c] = fma(xc[c], yc, acc[kMaxP * kMaxP + c]);
+    }
+  }
+  block_sum_arr<kMaxP * kMaxP + 2 * kMaxP>(acc, sm);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < kMaxP; ++c) pre[kPreMean + c] = m[c];
+    pre[kPreMy] = my;
+    for (int i = 0; i < kMaxP * kMaxP; ++i) pre[kPreGram + i] = acc[i];
+    for (int c = 0; c < kMaxP; ++c) pre[kPreG + c] = acc[kMaxP * kMaxP + c];
+    for (int c = 0; c < kMaxP; ++c) pre[kPreNorm + c] = sqrt(acc[kMaxP * kMaxP + kMaxP + c]);
+  }
+}
+
+// One block of kWide threads per candidate v: the fit of the centred target
+// on the centred [fixed..., v] (Cholesky of the centred normal equations,
+// collinearity test on the pivots against the raw column norms), then the
+// residual sum of squares explicitly.  Per sample and candidate only the
+// terms that involve v are accumulated: Σv, Σv², then Σd², Σd·f_j, Σd·y with
+// d = v - mean(v), then the residual.  CACHE: v is evaluated once into
+// shared memory (N doubles); FP64 arithmetic is the cost on this part.
+constexpr int64_t kRefitCacheMax = 6144;  // samples (48 KiB)
+
+template <bool CACHE>
+__global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, int64_t n_stored, const double *fcc,
+                                                      const double *ycc, const double *pre, int nf,
+                                                      const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand,
+                                                      double *rmse_out, double *beta_out) {
   __shared__ double sm[(kWide / 32) * 20];
+  __shared__ double s_bc[kMaxP + 2];
+  extern __shared__ double col[];
   const int64_t w = blockIdx.x;
   if (w >= n_cand) return;
   const int64_t N = F.N;
@@ -191,101 +252,99 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   int op;
   int64_t a, b;
   decode_any(G, n_stored, gid, &op, &a, &b);
-  auto xval = [&](int c, int64_t s) -> double {
-    return c < nf ? fixed_cols[(int64_t)c * N + s] : col_value(F, G, n_stored, op, a, b, s);
-  };
-  double mv[kMaxP + 1] = {0, 0, 0, 0, 0};  // column means, then y's
+  auto vval = [&](int64_t s) -> double { return CACHE ? col[s] : col_value(F, G, n_stored, op, a, b, s); };
+  double s1[2] = {0.0, 0.0};  // sum v, sum v^2
   for (int64_t s = threadIdx.x; s < N; s += kWide) {
-    for (int c = 0; c < p; ++c) mv[c] += xval(c, s);
-    mv[kMaxP] += y[s];
+    const double v = col_value(F, G, n_stored, op, a, b, s);
+    if (CACHE) col[s] = v;
+    s1[0] += v;
+    s1[1] = fma(v, v, s1[1]);
   }
-  block_sum_arr<kMaxP + 1>(mv, sm);
-  double m[kMaxP];
-  for (int c = 0; c < kMaxP; ++c) m[c] = mv[c] / (double)N;
-  const double my = mv[kMaxP] / (double)N;
-  // packed: Gram lower triangle (10), g (4), norms (4)
-  double acc[18];
-  for (int i = 0; i < 18; ++i) acc[i] = 0.0;
+  block_sum_arr<2>(s1, sm);
+  const double mvv = s1[0] / (double)N;
+  double s2[kMaxP + 2] = {0, 0, 0, 0, 0, 0};  // sum d f_j (j < nf), sum d^2, sum d y
   for (int64_t s = threadIdx.x; s < N; s += kWide) {
-    double xc[kMaxP];
-    for (int c = 0; c < p; ++c) {
-      double v = xval(c, s);
-      xc[c] = v - m[c];
-      acc[14 + c] = fma(v, v, acc[14 + c]);
-    }
-    double yc = y[s] - my;
-    int t = 0;
-    for (int c = 0; c < kMaxP; ++c)
-      for (int d = 0; d <= c; ++d, ++t)
-        if (c < p) acc[t] = fma(xc[c], xc[d], acc[t]);
-    for (int c = 0; c < p; ++c) acc[10 + c] = fma(xc[c], yc, acc[10 + c]);
+    const double dv = vval(s) - mvv;
+    for (int c = 0; c < nf; ++c) s2[c] = fma(dv, fcc[(int64_t)c * N + s], s2[c]);
+    s2[kMaxP] = fma(dv, dv, s2[kMaxP]);
+    s2[kMaxP + 1] = fma(dv, ycc[s], s2[kMaxP + 1]);
   }
-  block_sum_arr<18>(acc, sm);
-  double Gm[kMaxP][kMaxP] = {}, g[kMaxP], nrm[kMaxP];
-  {
-    int t = 0;
-    for (int c = 0; c < kMaxP; ++c)
-      for (int d = 0; d <= c; ++d, ++t) Gm[c][d] = acc[t];
-    for (int c = 0; c < kMaxP; ++c) {
-      g[c] = acc[10 + c];
-      nrm[c] = sqrt(acc[14 + c]);
+  block_sum_arr<kMaxP + 2>(s2, sm);
+  if (threadIdx.x == 0) {
+    double Gm[kMaxP][kMaxP] = {}, g[kMaxP] = {}, nrm[kMaxP] = {};
+    for (int c = 0; c < nf; ++c) {
+      for (int d = 0; d <= c; ++d) Gm[c][d] = pre[kPreGram + c * kMaxP + d];
+      g[c] = pre[kPreG + c];
+      nrm[c] = pre[kPreNorm + c];
+      Gm[nf][c] = s2[c];
     }
+    Gm[nf][nf] = s2[kMaxP];
+    g[nf] = s2[kMaxP + 1];
+    nrm[nf] = sqrt(s1[1]);
+    double L[kMaxP][kMaxP] = {};
+    bool ok = true;
+    for (int c = 0; c < p && ok; ++c) {
+      double dsum = Gm[c][c];
+      for (int k = 0; k < c; ++k) dsum -= L[c][k] * L[c][k];
+      if (!(dsum > 0.0)) {
+        ok = false;
+        break;
+      }
+      L[c][c] = sqrt(dsum);
+      if (!(L[c][c] > 1e-12 * nrm[c])) {
+        ok = false;
+        break;
+      }
+      for (int r = c + 1; r < p; ++r) {
+        double v = Gm[r][c];
+        for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
+        L[r][c] = v / L[c][c];
+      }
+    }
+    double beta[kMaxP + 1] = {};
+    if (ok) {
+      double z[kMaxP];
+      for (int c = 0; c < p; ++c) {
+        double v = g[c];
+        for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
+        z[c] = v / L[c][c];
+      }
+      for (int c = p - 1; c >= 0; --c) {
+        double v = z[c];
+        for (int k = c + 1; k < p; ++k) v -= L[k][c] * beta[k + 1];
+        beta[c + 1] = v / L[c][c];
+      }
+      double b0 = pre[kPreMy];
+      for (int c = 0; c < nf; ++c) b0 -= beta[c + 1] * pre[kPreMean + c];
+      b0 -= beta[p] * mvv;
+      beta[0] = b0;
+    }
+    for (int c = 0; c <= kMaxP; ++c) beta_out[w * (kMaxP + 1) + c] = ok && c <= p ? beta[c] : 0.0;
+    for (int c = 0; c < p; ++c) s_bc[c] = beta[c + 1];
+    s_bc[kMaxP + 1] = ok ? 1.0 : 0.0;
   }
-  double L[kMaxP][kMaxP] = {};
-  bool ok = true;
-  for (int c = 0; c < p && ok; ++c) {
-    double dsum = Gm[c][c];
-    for (int k = 0; k < c; ++k) dsum -= L[c][k] * L[c][k];
-    if (!(dsum > 0.0)) {
-      ok = false;
-      break;
-    }
-    L[c][c] = sqrt(dsum);
-    if (!(L[c][c] > 1e-12 * nrm[c])) {
-      ok = false;
-      break;
-    }
-    for (int r = c + 1; r < p; ++r) {
-      double v = Gm[r][c];
-      for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
-      L[r][c] = v / L[c][c];
-    }
-  }
-  double beta[kMaxP + 1] = {};
-  if (ok) {
-    double z[kMaxP];
-    for (int c = 0; c < p; ++c) {
-      double v = g[c];
-      for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
-      z[c] = v / L[c][c];
-    }
-    for (int c = p - 1; c >= 0; --c) {
-      double v = z[c];
-      for (int k = c + 1; k < p; ++k) v -= L[k][c] * beta[k + 1];
-      beta[c + 1] = v / L[c][c];
-    }
-    double b0 = my;
-    for (int c = 0; c < p; ++c) b0 -= beta[c + 1] * m[c];
-    beta[0] = b0;
-  }
+  __syncthreads();
+  const bool ok = s_bc[kMaxP + 1] != 0.0;
   double rss[1] = {0.0};
   if (ok) {
+    double bc[kMaxP];
+    for (int c = 0; c < p; ++c) bc[c] = s_bc[c];
     for (int64_t s = threadIdx.x; s < N; s += kWide) {
-      double f = beta[0];
-      for (int c = 0; c < p; ++c) f = fma(beta[c + 1], xval(c, s), f);
-      double r = y[s] - f;
+      double r = ycc[s];
+      for (int c = 0; c < nf; ++c) r = fma(-bc[c], fcc[(int64_t)c * N + s], r);
+      r = fma(-bc[nf], vval(s) - mvv, r);
       rss[0] = fma(r, r, rss[0]);
     }
   }
   block_sum_arr<1>(rss, sm);
-  if (threadIdx.x == 0) {
-    rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
-    for (int c = 0; c <= kMaxP; ++c) beta_out[w * (kMaxP + 1) + c] = ok && c <= p ? beta[c] : 0.0;
-  }
+  if (threadIdx.x == 0) rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
 }
 
-// Index of the smallest RMSE (ties: lower id); one block.
-__global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best) {
+// Index of the smallest RMSE (ties: lower id); one block.  report (when not
+// null) gets {index, id, rmse, beta[kMaxP + 1]} of the winner as doubles /
+// bit patterns, for one small copy to the host.
+__global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
+                         double *report) {
   __shared__ double bv[1024];
   __shared__ uint64_t bid[1024];
   __shared__ int64_t bix[1024];
@@ -316,7 +375,16 @@ __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, in
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *best = bv[0] < INFINITY ? bix[0] : -1;
+  if (threadIdx.x == 0) {
+    const int64_t b = bv[0] < INFINITY ? bix[0] : -1;
+    *best = b;
+    if (report) {
+      report[0] = __longlong_as_double(b);
+      report[1] = __longlong_as_double(b >= 0 ? (long long)cand[b] : -1ll);
+      report[2] = b >= 0 ? rmse[b] : INFINITY;
+      for (int c = 0; c <= kMaxP; ++c) report[3 + c] = b >= 0 ? beta[b * (kMaxP + 1) + c] : 0.0;
+    }
+  }
 }
 
 // Residual y - fit of the chosen candidate.
@@ -334,6 +402,12 @@ __global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const doub
     f = fma(beta[nf + 1], col_value(F, G, n_stored, op, a, b, s), f);
     res[s] = y[s] - f;
   }
+}
+
+static inline long long __double_as_longlong_host(double x) {
+  long long v;
+  memcpy(&v, &x, sizeof(v));
+  return v;
 }
 
 dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, double *best_rmse, double *coefs,
@@ -360,52 +434,69 @@ dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, 
     off += (bytes + 255) / 256 * 256;
     return o;
   };
-  size_t o_y = take(8 * N), o_fid = take(8 * 4), o_fc = take(8 * (size_t)N * 4), o_c = take(8 * nc),
-         o_r = take(8 * nc), o_b = take(8 * (size_t)nc * (kMaxP + 1)), o_best = take(8), o_res = take(8 * N);
+  // inputs already on the device are read in place; a device residual
+  // buffer is written in place (the call waits before it returns)
+  const bool res_dev = residual && is_device_pointer(residual);
+  size_t o_y = take(d->y_on_device ? 0 : 8 * N), o_fid = take(8 * 4), o_fc = take(8 * (size_t)N * 4),
+         o_c = take(d->cand_on_device ? 0 : 8 * nc), o_r = take(8 * nc), o_b = take(8 * (size_t)nc * (kMaxP + 1)),
+         o_best = take(8), o_rep = take(8 * (kMaxP + 4)), o_res = take(res_dev ? 0 : 8 * N),
+         o_fcc = take(8 * (size_t)N * kMaxP), o_ycc = take(8 * N), o_pre = take(8 * kPreSize);
   char *base = nullptr;
   DSE_TRY(dmalloc(reinterpret_cast<void **>(&base), off, "refit scratch"));
-  double *y = reinterpret_cast<double *>(base + o_y);
+  const double *y = d->y_on_device ? d->y : reinterpret_cast<double *>(base + o_y);
   uint64_t *fid = reinterpret_cast<uint64_t *>(base + o_fid);
   double *fc = reinterpret_cast<double *>(base + o_fc);
-  uint64_t *cand = reinterpret_cast<uint64_t *>(base + o_c);
+  const uint64_t *cand = d->cand_on_device ? d->cand : reinterpret_cast<uint64_t *>(base + o_c);
   double *rm = reinterpret_cast<double *>(base + o_r);
   double *beta = reinterpret_cast<double *>(base + o_b);
   int64_t *best = reinterpret_cast<int64_t *>(base + o_best);
-  double *res = reinterpret_cast<double *>(base + o_res);
-  cudaError_t e = cudaMemcpyAsync(y, d->y, 8 * N, cudaMemcpyDefault, st);
+  double *rep = reinterpret_cast<double *>(base + o_rep);
+  double *res = res_dev ? residual : reinterpret_cast<double *>(base + o_res);
+  double *fcc = reinterpret_cast<double *>(base + o_fcc);
+  double *ycc = reinterpret_cast<double *>(base + o_ycc);
+  double *pre = reinterpret_cast<double *>(base + o_pre);
+  cudaError_t e = cudaSuccess;
+  if (!d->y_on_device)
+    e = cudaMemcpyAsync(const_cast<double *>(y), d->y, 8 * N, cudaMemcpyHostToDevice, st);
   if (!e && nf) e = cudaMemcpyAsync(fid, d->fixed, 8 * nf, cudaMemcpyHostToDevice, st);
-  if (!e) e = cudaMemcpyAsync(cand, d->cand, 8 * nc, cudaMemcpyDefault, st);
+  if (!e && !d->cand_on_device)
+    e = cudaMemcpyAsync(const_cast<uint64_t *>(cand), d->cand, 8 * nc, cudaMemcpyHostToDevice, st);
   if (e) {
     dfree(base);
     return cuda_status(e, "refit upload");
   }
   const FeatTable F = table_of(S);
-  note_launches(3 + (nf ? 1 : 0));
+  note_launches(4 + (nf ? 1 : 0));
   if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
-  k_refit_wide<<<(unsigned)nc, kWide, 0, st>>>(F, S->geom, S->n, y, fc, nf, fid, cand, nc, rm, beta);
-  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best);
+  k_refit_prep<<<1, kWide, 0, st>>>(y, fc, nf, N, fcc, ycc, pre);
+  if (N <= kRefitCacheMax)
+    k_refit_wide<true><<<(unsigned)nc, kWide, (size_t)N * sizeof(double), st>>>(F, S->geom, S->n, fcc, ycc, pre,
+                                                                              nf, fid, cand, nc, rm, beta);
+  else
+    k_refit_wide<false><<<(unsigned)nc, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, nf, fid, cand, nc, rm,
+                                                         beta);
+  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, rep);
   k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
-  int64_t hb = -1;
-  e = cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st);
-  if (!e) e = cudaStreamSynchronize(st);
-  if (e) {
+  // one asynchronous copy of the winner's report (and of a host residual), one sync
+  double *h = static_cast<double *>(pinned_staging(8 * (kMaxP + 4)));
+  if (!h) {
     dfree(base);
-    return cuda_status(e, "refit");
+    return DSE_ENOMEM;
   }
+  e = cudaMemcpyAsync(h, rep, 8 * (kMaxP + 4), cudaMemcpyDeviceToHost, st);
+  if (!e && residual && !res_dev) e = cudaMemcpyAsync(residual, res, 8 * N, cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(base);
+  if (e) return cuda_status(e, "refit");
+  const int64_t hb = (int64_t)__double_as_longlong_host(h[0]);
   if (hb < 0) {
-    dfree(base);
     set_error("no candidate gives a full-rank fit");
     return DSE_EINVAL;
   }
-  double hb_beta[kMaxP + 1];
-  e = cudaMemcpy(best_rmse, rm + hb, 8, cudaMemcpyDeviceToHost);
-  if (!e) e = cudaMemcpy(best_id, cand + hb, 8, cudaMemcpyDeviceToHost);
-  if (!e) e = cudaMemcpy(hb_beta, beta + hb * (kMaxP + 1), sizeof(hb_beta), cudaMemcpyDeviceToHost);
-  if (!e && residual) e = cudaMemcpy(residual, res, 8 * N, cudaMemcpyDefault);
-  dfree(base);
-  if (e) return cuda_status(e, "refit fetch");
+  *best_id = (uint64_t)__double_as_longlong_host(h[1]);
+  *best_rmse = h[2];
   if (coefs)
-    for (int c = 0; c < nf + 2; ++c) coefs[c] = hb_beta[c];
+    for (int c = 0; c < nf + 2; ++c) coefs[c] = h[3 + c];
   return DSE_OK;
 }
 

@@ -360,7 +360,8 @@ struct PairCfg {
   static constexpr int CH = sizeof(R) == 4 ? 128 : 64;
   static constexpr int STR = CH + (sizeof(R) == 4 ? 4 : 2);
   static constexpr int STAGE = ROWS * STR + NT * CH;  // elements
-  static constexpr size_t SMEM = 2 * (size_t)STAGE * sizeof(R) + 64;
+  static constexpr int NS = 3;                        // ring stages
+  static constexpr size_t SMEM = NS * (size_t)STAGE * sizeof(R) + 128;
 };
 
 template <typename R>
@@ -482,41 +483,131 @@ __device__ __forceinline__ unsigned binary_candidate(const ScreenArgs &A, LaneSt
   return score_and_push<R, NT>(A, ok, gid, ci, S1, Sy, invN, gamma, u, ysum);
 }
 
+// Shared-memory ring of the pair kernel (after its stage buffers): a stage
+// is refilled by the last warp to finish with it (no block-wide barrier), in
+// the CTA's chunk order kept by the issue cursor.
+struct PairRing {
+  uint64_t full[4];    // stage holds its chunk (one arrival + transaction bytes)
+  unsigned done[4];    // warps finished with the stage's current chunk
+  unsigned issued[4];  // chunks issued into the stage
+  int cur_i, cur_c;    // next chunk to issue: chunk cur_c of the CTA's cur_i-th tile
+  int pad[2];
+};
+
+// A CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (a static
+// schedule, so that any warp can name the tile of any later chunk).  Each of
+// its 8 warps owns a 2-D slice of the tile's pairs and runs through the
+// tile's sample chunks on its own; the chunks stream through NS stages.
 // BATCH: the tiles of every problem of a batched screen in one launch; each
 // tile names its problem, whose arguments are read from `batch` (A0 then
-// carries only the tile list, its counter and the error flag).
+// carries only the tile list and the error flag).
 template <typename R, int KIND, int NT, int MI, int MJ, bool BATCH>
-__global__ void __launch_bounds__(256) k_pair(const ScreenArgs A0, const ScreenArgs *batch, int block_len0) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && NT == 1) ? 2 : 1)
+    k_pair(const ScreenArgs A0, const ScreenArgs *batch, int block_len0) {
   using C = PairCfg<R, KIND, NT, MI, MJ>;
   using V2 = typename Vec2<R>::T;
+  constexpr int NS = C::NS, WARPS = 8;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   R *stage_base = reinterpret_cast<R *>(smem_raw);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * (size_t)C::STAGE * sizeof(R));
-  __shared__ int s_tile, s_abort;
-  __shared__ int32_t s_row[C::ROWS];
+  PairRing *ring = reinterpret_cast<PairRing *>(smem_raw + (size_t)NS * C::STAGE * sizeof(R));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wi = warp >> 2, wj = warp & 3, li = lane >> 2, lj = lane & 3;
   const R u = sizeof(R) == 4 ? R(5.9604644775390625e-8) : R(1.1102230246251565e-16);
   constexpr int kGroup = KIND == KIND_MUL ? 1 : 2;
+  const int n_tiles = A0.n_tiles;
 
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_fence_init();
-    s_abort = 0;
+  auto tile_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
+  auto row_id = [&](const ScreenArgs &A, const Tile &tl, int r) -> int {
+    if (r < C::BI) return r < tl.ni ? A.rowid[tl.ibase + r] : -1;
+    return (r - C::BI) < tl.nj ? A.rowid[tl.jbase + r - C::BI] : -1;
+  };
+  // whole warp: the bulk copies of chunk c of tile t into stage st
+  auto issue = [&](int t, int c, int st) {
+    const Tile tl = A0.tiles[t];
+    const ScreenArgs &A = BATCH ? batch[tl.prob] : A0;
+    const int64_t ld = A.F.ld;
+    const R *rows_src = sizeof(R) == 4 ? (const R *)A.F.v32 : (const R *)A.F.v64;
+    const R *y_src = sizeof(R) == 4 ? (const R *)A.y32 : (const R *)A.y64;
+    const int64_t s0 = (int64_t)c * C::CH;
+    int64_t cnt = ld - s0;
+    if (cnt > C::CH) cnt = C::CH;
+    const uint32_t rb = (uint32_t)(cnt * sizeof(R));
+    int64_t ycnt = (int64_t)A.ldy - s0;
+    if (ycnt > C::CH) ycnt = C::CH;
+    const uint32_t yb = (uint32_t)(ycnt * sizeof(R));
+    constexpr int RPL = (C::ROWS + 31) / 32;  // rows per lane
+    int ids[RPL];
+    unsigned mine = 0;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = lane + 32 * q;
+      ids[q] = r < C::ROWS ? row_id(A, tl, r) : -1;
+      if (ids[q] >= 0) mine += rb;
+    }
+    const bool ylane = lane < NT && lane < A.T;
+    if (ylane) mine += yb;
+    const unsigned bytes = __reduce_add_sync(0xffffffffu, mine);
+    R *dst = stage_base + (size_t)st * C::STAGE;
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&ring->full[st], bytes);
+      ring->issued[st] += 1;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < RPL; ++q)
+      if (ids[q] >= 0)
+        bulk_g2s(dst + (lane + 32 * q) * C::STR, rows_src + (int64_t)ids[q] * ld + s0, rb, &ring->full[st]);
+    if (ylane)
+      bulk_g2s(dst + C::ROWS * C::STR + lane * C::CH, y_src + (int64_t)(A.t0 + lane) * A.ldy + s0, yb,
+               &ring->full[st]);
+  };
+  // whole warp: issue the chunk the cursor names (if any) into stage st
+  auto issue_next = [&](int st) {
+    int i = ring->cur_i, c = ring->cur_c;
+    const int t = tile_of(i);
+    if (t < n_tiles) {
+      issue(t, c, st);
+      const Tile tl = A0.tiles[t];
+      const int nch = ((BATCH ? batch[tl.prob].N : A0.N) + C::CH - 1) / C::CH;
+      if (++c == nch) {
+        c = 0;
+        ++i;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      ring->cur_i = i;
+      ring->cur_c = c;
+    }
+    __syncwarp();
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int st = 0; st < NS; ++st) {
+        mbar_init(&ring->full[st], 1);
+        ring->done[st] = 0;
+        ring->issued[st] = 0;
+      }
+      ring->cur_i = 0;
+      ring->cur_c = 0;
+      mbar_fence_init();
+    }
+    __syncwarp();
+    for (int st = 0; st < NS; ++st) issue_next(st);
   }
   __syncthreads();
-  uint32_t gchunk = 0;
+
+  uint32_t g = 0;  // the CTA's chunk counter (same sequence in every warp)
+  bool aborted = false;
   LaneStats ls;
   ls.zero();
   int cur = BATCH ? -1 : 0;  // problem whose statistics ls holds
 
-  for (;;) {
-    if (tid == 0) s_tile = (int)atomicAdd(A0.tile_counter, 1u);
-    __syncthreads();
-    const int tile = s_tile;
-    if (tile >= A0.n_tiles || s_abort) break;
+  for (int ti = 0;; ++ti) {
+    const int tile = tile_of(ti);
+    if (tile >= n_tiles) break;
     const Tile tl = A0.tiles[tile];
     if (BATCH && tl.prob != cur) {
       if (cur >= 0) flush_stats(batch[cur], ls, kGroup);
@@ -528,33 +619,20 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A0, const ScreenA
     const R N = (R)A.N, invN = (R)A.invN, sqrtN = Num<R>::sqrt_(N);
     const R fmin = (R)A.fmin_std_rel64;
     const int nchunks = (A.N + C::CH - 1) / C::CH;
-    const int64_t ld = A.F.ld;
-    const R *rows_src = sizeof(R) == 4 ? (const R *)A.F.v32 : (const R *)A.F.v64;
-    const R *y_src = sizeof(R) == 4 ? (const R *)A.y32 : (const R *)A.y64;
     R ysum[NT];
     load_ysum<R, NT>(A, ysum);
-    if (tid < C::ROWS) {
-      int id = -1;
-      if (tid < C::BI) {
-        if (tid < tl.ni) id = A.rowid[tl.ibase + tid];
-      } else if (tid - C::BI < tl.nj) {
-        id = A.rowid[tl.jbase + tid - C::BI];
-      }
-      s_row[tid] = id;
-    }
-    __syncthreads();
 
     int ri[MI], rj[MJ];
     int64_t fi[MI], fj[MJ];
 #pragma unroll
     for (int r = 0; r < MI; ++r) {
       ri[r] = wi * 8 * MI + li + 8 * r;
-      fi[r] = s_row[ri[r]];
+      fi[r] = row_id(A, tl, ri[r]);
     }
 #pragma unroll
     for (int c = 0; c < MJ; ++c) {
       rj[c] = wj * 4 * MJ + lj + 4 * c;
-      fj[c] = s_row[C::BI + rj[c]];
+      fj[c] = row_id(A, tl, C::BI + rj[c]);
     }
     // per-pair shift constants and per-operand centring
     R k0[MI][MJ], k1[MI][MJ], k2[MI][MJ], mi[MI], mj[MJ];
@@ -590,41 +668,14 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A0, const ScreenA
 #pragma unroll
           for (int e = 0; e < 2 + NT; ++e) acc[r][c][k][e] = tot[r][c][k][e] = R(0);
 
-    auto issue = [&](int chunk) {
-      const int st = (gchunk + chunk) & 1;
-      R *dst = stage_base + (size_t)st * C::STAGE;
-      const int64_t s0 = (int64_t)chunk * C::CH;
-      int64_t cnt = ld - s0;
-      if (cnt > C::CH) cnt = C::CH;
-      const uint32_t rb = (uint32_t)(cnt * sizeof(R));
-      uint32_t bytes = 0;
-      for (int r = 0; r < C::ROWS; ++r)
-        if (s_row[r] >= 0) bytes += rb;
-      int64_t ycnt = (int64_t)A.ldy - s0;
-      if (ycnt > C::CH) ycnt = C::CH;
-      const uint32_t yb = (uint32_t)(ycnt * sizeof(R));
-      for (int t = 0; t < NT; ++t)
-        if (t < A.T) bytes += yb;
-      mbar_arrive_expect_tx(&bar[st], bytes);
-      for (int r = 0; r < C::ROWS; ++r)
-        if (s_row[r] >= 0) bulk_g2s(dst + r * C::STR, rows_src + (int64_t)s_row[r] * ld + s0, rb, &bar[st]);
-      for (int t = 0; t < NT; ++t)
-        if (t < A.T)
-          bulk_g2s(dst + C::ROWS * C::STR + t * C::CH, y_src + (int64_t)(A.t0 + t) * A.ldy + s0, yb, &bar[st]);
-    };
-
-    if (tid == 0) issue(0);
     int blk = 0;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      if (tid == 0 && ch + 1 < nchunks) issue(ch + 1);
-      const uint32_t g = gchunk + ch;
-      const int st = g & 1;
-      if (!mbar_wait_bounded(&bar[st], (g >> 1) & 1, kWaitLimit)) {
-        atomicExch(A0.err, DSE_ETIMEOUT);
-        s_abort = 1;
+    for (int ch = 0; ch < nchunks; ++ch, ++g) {
+      const int st = (int)(g % NS);
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&ring->full[st], (g / NS) & 1u, kWaitLimit))) {
+        if (lane == 0) atomicExch(A0.err, DSE_ETIMEOUT);
+        aborted = true;
+        break;
       }
-      __syncthreads();
-      if (s_abort) break;
       const R *S = stage_base + (size_t)st * C::STAGE;
       const R *Si = S, *Sj = S + C::BI * C::STR, *Sy = S + C::ROWS * C::STR;
       int ns = A.N - ch * C::CH;
@@ -686,10 +737,21 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A0, const ScreenA
         for (int t = 0; t < NT; ++t) y[t] = Sy[t * C::CH + s];
         pair_update<R, KIND, NT, MI, MJ>(a, b, y, k0, k1, k2, mi, mj, acc);
       }
-      __syncthreads();
+      // release the stage; the last warp to do so refills it
+      __syncwarp();
+      unsigned last = 0;
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&ring->done[st], 1u) == WARPS - 1 ? 1u : 0u;
+        if (last) ring->done[st] = 0;
+        __threadfence_block();
+      }
+      if (__shfl_sync(0xffffffffu, last, 0)) {
+        __syncwarp();  // the cursor lane 0 acquired is visible to every lane
+        issue_next(st);
+      }
     }
-    gchunk += nchunks;
-    if (s_abort) break;
+    if (aborted) break;
 #pragma unroll
     for (int r = 0; r < MI; ++r)
 #pragma unroll
@@ -727,6 +789,15 @@ __global__ void __launch_bounds__(256) k_pair(const ScreenArgs A0, const ScreenA
         }
       }
     refresh_pushed<NT>(A, pushed);
+  }
+  if (aborted) {
+    // no copy may still be landing when the CTA exits
+    if (lane == 0)
+      for (int st = 0; st < NS; ++st) {
+        const unsigned n = ((volatile unsigned *)ring->issued)[st];
+        if (n) mbar_wait_bounded(&ring->full[st], (n - 1) & 1u, kWaitLimit);
+      }
+    return;
   }
   if (cur >= 0) flush_stats(BATCH ? batch[cur] : A0, ls, kGroup);
 }

@@ -60,6 +60,7 @@ struct SelectArgs {
   uint64_t *out_id;
   double *out_score, *out_eps;
   int64_t *out_n;
+  double *max_eps;          // [lists] largest returned bound
   // sort scratch for large lists [lists][sort_cap]
   double *sort_key;
   uint64_t *sort_id;

@@ -30,10 +30,12 @@
 //
 // Error model of the contraction (used for the reported bound, and the
 // reason reported TC scores above the 1e-5 tolerance are re-scored in FP64):
-// the BF16x3 split drops Al Bl and the splits' residuals, at most
-// 3.01 * 2^-18 of sum |w y|; each tensor-core accumulation step is modelled
-// with a relative error of 2u on the running sum of |terms|, with a safety
-// factor of 4.
+// the BF16x3 split drops Al Bl and the splits' residuals (BF16 rounds to
+// 8 significant bits, so each two-term split leaves at most 2^-16 of the
+// value), at most 3.01 * 2^-16 of sum |w y|; each tensor-core accumulation
+// step is modelled with a relative error of 2u on the running sum of
+// |terms|, with a safety factor of 4 (the accumulation order and rounding
+// inside an MMA are not documented, so this part is a model, not a proof).
 #include <cuda_bf16.h>
 #include <math.h>
 

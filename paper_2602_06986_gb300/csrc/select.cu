@@ -125,21 +125,50 @@ __device__ float kth_largest(const float *v, unsigned n, unsigned r, unsigned *h
     for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     const uint32_t prefix = sh_prefix, mask = sh_mask;
-    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-      uint32_t key = __float_as_uint(v[i]);
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    // the collected values share one score bin, so most digits coincide:
+    // lanes with equal digits add once per group (warp-aggregated atomics)
+    const unsigned n_up = (n + 31u) & ~31u;
+    for (unsigned i = threadIdx.x; i < n_up; i += blockDim.x) {
+      int digit = -1;
+      if (i < n) {
+        const uint32_t key = __float_as_uint(v[i]);
+        if ((key & mask) == prefix) digit = (int)((key >> shift) & 255u);
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, digit);
+      if (digit >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+        atomicAdd(&hist[digit], (unsigned)__popc(peers));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned cum = 0, rem = sh_rem;
-      int d = 255;
-      for (; d > 0; --d) {
-        if (cum + hist[d] >= rem) break;
-        cum += hist[d];
+    // warp 0: the digit d holding the rem-th largest, by a suffix scan of the
+    // 256 counts (lane j owns digits 255-8j .. 248-8j, highest first)
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const unsigned rem = sh_rem;
+      unsigned c[8], tot = 0;
+      for (int q = 0; q < 8; ++q) {
+        c[q] = hist[255 - 8 * lane - q];
+        tot += c[q];
       }
-      sh_rem = rem - cum;
-      sh_prefix = prefix | ((uint32_t)d << shift);
-      sh_mask = mask | (255u << shift);
+      unsigned incl = tot;  // inclusive prefix over lanes (higher digits first)
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const unsigned excl = incl - tot;
+      // the first lane whose inclusive count reaches rem holds the digit
+      const unsigned hit = __ballot_sync(0xffffffffu, incl >= rem);
+      const int owner = hit ? __ffs(hit) - 1 : 31;
+      if (lane == owner) {
+        unsigned cum = excl;
+        int d = 255 - 8 * lane;
+        for (int q = 0; q < 8; ++q, --d) {
+          if (cum + c[q] >= rem || d == 0) break;
+          cum += c[q];
+        }
+        sh_rem = rem - cum;
+        sh_prefix = prefix | ((uint32_t)d << shift);
+        sh_mask = mask | (255u << shift);
+      }
     }
     __syncthreads();
   }
@@ -255,19 +284,24 @@ __global__ void __launch_bounds__(kRes) k_rescore(const SelectArgs S, const Scre
   }
 }
 
-__device__ __forceinline__ bool before(double ka, uint64_t ia, double kb, uint64_t ib) {
+// Scores are non-negative, so the bit patterns of their doubles order like
+// the values: the sort compares 64-bit integers (integer ALU), not doubles
+// (FP64 compares are slow on this part).  Padding: key 0, id 2^64-1.
+__device__ __forceinline__ uint64_t score_key(double s) { return (uint64_t)__double_as_longlong(s); }
+
+__device__ __forceinline__ bool before(uint64_t ka, uint64_t ia, uint64_t kb, uint64_t ib) {
   return ka > kb || (ka == kb && ia < ib);
 }
 
 // Bitonic sort (descending key, ascending id) of M (power of two) entries.
-__device__ void bitonic(double *key, uint64_t *id, int64_t M) {
+__device__ void bitonic(uint64_t *key, uint64_t *id, int64_t M) {
   for (int64_t size = 2; size <= M; size <<= 1) {
     for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
       for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
         int64_t j = i ^ stride;
         if (j > i) {
           bool up = (i & size) == 0;
-          double ki = key[i], kj = key[j];
+          uint64_t ki = key[i], kj = key[j];
           uint64_t ii = id[i], ij = id[j];
           bool sw = up ? before(kj, ij, ki, ii) : before(ki, ii, kj, ij);
           if (sw) {
@@ -293,22 +327,22 @@ __global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
   const size_t base = (size_t)l * S.B.cap;
   int64_t M = 1;
   while (M < rn) M <<= 1;
-  double *key;
+  uint64_t *key;
   uint64_t *id;
   if (M <= kSmemSort) {
-    key = reinterpret_cast<double *>(sm);
-    id = reinterpret_cast<uint64_t *>(sm + kSmemSort * sizeof(double));
+    key = reinterpret_cast<uint64_t *>(sm);
+    id = reinterpret_cast<uint64_t *>(sm + kSmemSort * sizeof(uint64_t));
   } else {
-    key = S.sort_key + (size_t)l * S.sort_cap;
+    key = reinterpret_cast<uint64_t *>(S.sort_key) + (size_t)l * S.sort_cap;
     id = S.sort_id + (size_t)l * S.sort_cap;
   }
   for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
     if (i < rn) {
       const size_t r = base + i;
-      key[i] = S.r_need[r] ? S.r_s64[r] : (double)S.r_s32[r];
+      key[i] = score_key(S.r_need[r] ? S.r_s64[r] : (double)S.r_s32[r]);
       id[i] = S.r_id[r];
     } else {
-      key[i] = -INFINITY;
+      key[i] = 0ull;
       id[i] = ~0ull;
     }
   }
@@ -317,13 +351,16 @@ __global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
   const int64_t nout = rn < S.k ? rn : S.k;
   for (int64_t i = threadIdx.x; i < nout; i += blockDim.x) {
     S.out_id[(size_t)l * S.k + i] = id[i];
-    S.out_score[(size_t)l * S.k + i] = key[i];
+    S.out_score[(size_t)l * S.k + i] = __longlong_as_double((long long)key[i]);
   }
   __syncthreads();
-  // each retained entry finds its rank by binary search and writes its bound
+  // each retained entry finds its rank by binary search and writes its bound;
+  // the list's largest returned bound is reduced on the way
+  __shared__ double s_mx[32];
+  double mx = 0.0;
   for (int64_t i = threadIdx.x; i < rn; i += blockDim.x) {
     const size_t r = base + i;
-    const double k0 = S.r_need[r] ? S.r_s64[r] : (double)S.r_s32[r];
+    const uint64_t k0 = score_key(S.r_need[r] ? S.r_s64[r] : (double)S.r_s32[r]);
     const uint64_t i0 = S.r_id[r];
     int64_t lo = 0, hi = M;
     while (lo < hi) {
@@ -331,9 +368,20 @@ __global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
       if (before(key[mid], id[mid], k0, i0)) lo = mid + 1;
       else hi = mid;
     }
-    if (lo < nout) S.out_eps[(size_t)l * S.k + lo] = S.r_need[r] ? S.r_e64[r] : (double)S.r_e32[r];
+    if (lo < nout) {
+      const double e = S.r_need[r] ? S.r_e64[r] : (double)S.r_e32[r];
+      S.out_eps[(size_t)l * S.k + lo] = e;
+      mx = fmax(mx, e);
+    }
   }
-  if (threadIdx.x == 0) S.out_n[l] = nout;
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_mx[w]);
+    S.out_n[l] = nout;
+    S.max_eps[l] = fmax(mx, s_mx[0]);
+  }
 }
 
 dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cudaStream_t st,

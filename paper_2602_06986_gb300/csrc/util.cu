@@ -72,6 +72,37 @@ void dfree_async(void *p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
+// The calling thread's pinned staging area (grown on demand, never shrunk,
+// held until the thread exits).
+namespace {
+struct Pinned {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local Pinned g_pinned;
+}  // namespace
+
+void *pinned_staging(size_t bytes) {
+  if (bytes > g_pinned.bytes) {
+    size_t want = 4096;
+    while (want < bytes) want <<= 1;
+    if (g_pinned.p) cudaFreeHost(g_pinned.p);
+    g_pinned.p = nullptr;
+    g_pinned.bytes = 0;
+    if (cudaMallocHost(&g_pinned.p, want) != cudaSuccess) {
+      cudaGetLastError();
+      g_pinned.p = nullptr;
+      set_error("cudaMallocHost(%zu) for staging failed", want);
+      return nullptr;
+    }
+    g_pinned.bytes = want;
+  }
+  return g_pinned.p;
+}
+
 bool is_device_pointer(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -154,6 +185,31 @@ __global__ void k_compact_write(const uint8_t *flags, uint64_t n, uint8_t want,
     uint64_t p = base + e;
     if (p < n && flags[p] == want) out[w++] = p;
   }
+}
+
+dse_status compact_bytes_dev(const uint8_t *flags, uint64_t n, uint8_t want, uint64_t *out,
+                             unsigned long long *count_dev, cudaStream_t s) {
+  if (n == 0) {
+    DSE_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long), s));
+    return DSE_OK;
+  }
+  uint64_t nb = (n + kCompactTile - 1) / kCompactTile;
+  unsigned int *bc = nullptr;
+  unsigned long long *off = nullptr;
+  DSE_TRY(dalloc(&bc, nb, "compaction counts"));
+  dse_status st = dalloc(&off, nb, "compaction offsets");
+  if (st != DSE_OK) {
+    dfree(bc);
+    return st;
+  }
+  note_launches(3);
+  k_compact_count<<<(unsigned)nb, kCompactThreads, 0, s>>>(flags, n, want, bc);
+  k_compact_scan<<<1, 1024, 0, s>>>(bc, nb, off, count_dev);
+  k_compact_write<<<(unsigned)nb, kCompactThreads, 0, s>>>(flags, n, want, off, out);
+  dfree(bc);
+  dfree(off);
+  DSE_CUDA(cudaGetLastError());
+  return DSE_OK;
 }
 
 dse_status compact_bytes(const uint8_t *flags, uint64_t n, uint8_t want, uint64_t *out, uint64_t *count_host,

@@ -51,6 +51,16 @@ void dfree_async(void *p, cudaStream_t s);
 dse_status compact_bytes(const uint8_t *flags, uint64_t n, uint8_t want, uint64_t *out,
                          uint64_t *count_host, cudaStream_t s);
 
+// Same with the count left on the device (*count_dev); no synchronisation.
+dse_status compact_bytes_dev(const uint8_t *flags, uint64_t n, uint8_t want, uint64_t *out,
+                             unsigned long long *count_dev, cudaStream_t s);
+
+// The calling thread's pinned host staging area of at least `bytes` bytes
+// (nullptr and an error message if it cannot be allocated).  Small results
+// are copied there asynchronously so that one stream synchronisation covers
+// several copies; its contents are valid until the thread's next call.
+void *pinned_staging(size_t bytes);
+
 // counts[c] += number of p < n with flags[p] == c, for c < 6 (device counters).
 void launch_count_reasons(const uint8_t *flags, uint64_t n, unsigned long long *counts, cudaStream_t s);
 
