@@ -3,9 +3,10 @@
 
 One step = one pass of the whole path over one synthetic workload: build the
 feature space (rungs < k materialised on the device), then the residual loop
-D = 1..3: SIS screen of rung 2 against the current residual (top-1000, exact
-top-k selection with FP64 re-score of the boundary band) and FP64
-least-squares refits of the retained candidates.  Inputs are resident in HBM
+D = 1..3 (one dse_residual_loop call, iterations chained on the device): SIS
+screen of rung 2 against the current residual (top-1000, exact top-k
+selection with FP64 re-score of the boundary band) and FP64 least-squares
+refits of the retained candidates.  Inputs are resident in HBM
 when the timed region starts; L2 is flushed (256 MiB write) between steps.
 
 Metric: SIS-screened candidate features per second (valid candidates scored),
@@ -103,6 +104,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def profiled_traffic(name="k_pair_mul_medium.txt"):
+    """DRAM bytes (read + write) per launch of the dominant kernel from the
+    committed ncu summary of the same kernel and workload, or None."""
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    try:
+        tot = 0.0
+        found = 0
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 4 and parts[0] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                    tot += float(parts[2]) * scale[parts[3]]
+                    found += 1
+        return tot if found == 2 else None
+    except Exception:
+        return None
+
+
 def workload(seed):
     from paper_2602_06986_gb300 import workloads as W
 
@@ -115,52 +134,37 @@ def count_step_evals(stats_list, N):
 
 
 def run_step_device(torch, dse, w, Xd, yd, k, D, stream, precision, timing=True):
-    """One step with device-resident inputs; returns (stats list, picks)."""
+    """One step with device-resident inputs: space build, then the residual
+    loop D = 1..3 on the device (dse_residual_loop).  Returns (per-screen
+    stats, chosen ids)."""
     sp = dse.Space(Xd, w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
                    explog_dimensionless=w["explog_dimensionless"], stream=stream)
-    N = sp.n_samples
-    r = yd
-    fixed, stats = [], []
-    ids = torch.empty(k, dtype=torch.int64, device="cuda")
-    sc = torch.empty(k, dtype=torch.float64, device="cuda")
-    eb = torch.empty(k, dtype=torch.float64, device="cuda")
-    for d in range(D):
-        res = sp.screen(r, k, precision=precision, stream=stream, flags=dse.FLAG_TIMING if timing else 0)
-        n = res.fetch(0, out=(ids, sc, eb))
-        stats.append(res.stats())
-        res.free()
-        nxt = torch.empty(N, dtype=torch.float64, device="cuda")
-        bid, rmse, coefs, _ = sp.ls_refit(yd, np.array(fixed, np.uint64), ids[:n], residual=nxt, stream=stream)
-        fixed.append(bid)
-        r = nxt
+    out = sp.residual_loop(yd, D, k, precision=precision, stream=stream, flags=dse.FLAG_TIMING if timing else 0)
     sp.free()
-    return stats, fixed
+    return out["stats"], out["chosen"]
 
 
 def run_step_host(dse, w, k, D):
-    """One step through the public API with host buffers (copies inside)."""
+    """One step through the public API with host buffers: the primaries and
+    the target are copied to the device inside the step, the SIS subspaces,
+    the final residual and the picks come back to host memory."""
     X = w["X"]
-    y = w["Y"][0]
+    y = np.ascontiguousarray(w["Y"][0])
     sp = dse.Space(X, w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
                    explog_dimensionless=w["explog_dimensionless"])
-    h2d = X.nbytes + w["units"].nbytes
-    d2h = 0
-    r = y
-    fixed, stats = [], []
-    for d in range(D):
-        res = sp.screen(r, k)
-        ids, sc, eb = res.fetch(0)
-        stats.append(res.stats())
-        res.free()
-        h2d += r.nbytes
-        d2h += ids.nbytes + sc.nbytes + eb.nbytes
-        bid, rmse, coefs, resid = sp.ls_refit(y, np.array(fixed, np.uint64), ids)
-        h2d += y.nbytes + ids.nbytes + 8 * len(fixed)
-        d2h += resid.nbytes + 8 * (len(fixed) + 2) + 16
-        fixed.append(bid)
-        r = resid
+    sis = np.zeros((D, k), np.uint64)
+    resid = np.zeros(len(y))
+    out = sp.residual_loop(y, D, k, sis_ids=sis, residual=resid)
     sp.free()
-    return stats, h2d, d2h
+    h2d = X.nbytes + w["units"].nbytes + y.nbytes
+    d2h = sis.nbytes + resid.nbytes + ctypes_sizeof_loop_result(dse)
+    return out["stats"], h2d, d2h
+
+
+def ctypes_sizeof_loop_result(dse):
+    import ctypes
+
+    return ctypes.sizeof(dse.LoopResult)
 
 
 def cpu_oracle_step(w, k, D):
@@ -394,7 +398,9 @@ def main():
                        "speedup_of_fp32_path": value / world / fp64_value},
         "roofline": {"bound": "alu", "kernel": "k_pair<float,MUL,1,2,2> (a*b, a/b, b/a slots)",
                      "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                       "(profiles/k_pair_mul_medium.txt)",
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({peak_src})",
                      "ops_per_eval": OPS_PER_EVAL, "launch_ms": mul_ms / max(mul_launches, 1),
                      "share_of_step": mul_ms / tot_ms},

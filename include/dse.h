@@ -22,6 +22,10 @@
  *   dse_ls_refit        Eq. 1 (L0-constrained least squares, ||beta||_0 <= D)
  *                       approximated greedily, OMP being one of the strategies
  *                       named in "Software Description".
+ *   dse_residual_loop   the two above chained on the device for D = 1..n_iter
+ *                       (screen the residual, refit, new residual).
+ *   dse_sis_screen_batched  dse_sis_screen over many independent data sets at
+ *                       once (no counterpart in the paper: an engineering form).
  *
  * Conventions (all calls):
  *   - Every entry point returns a dse_status; 0 is success.  No C++ exception
@@ -33,8 +37,9 @@
  *   - Handles (dse_space, dse_result) are owned by the library and released
  *     with the matching *_free call.
  *   - Work is enqueued on the stream given in the descriptor (a cudaStream_t,
- *     NULL for the legacy default stream).  Only dse_topk_fetch,
- *     dse_result_stats, dse_space_counts and dse_ls_refit wait for the stream.
+ *     NULL for the legacy default stream).  dse_build_space,
+ *     dse_topk_fetch, dse_result_stats, dse_space_counts, dse_ls_refit,
+ *     dse_residual_loop, dse_batch_fetch and dse_batch_stats wait for it.
  *   - There is no CPU fallback: without a usable CUDA device every call that
  *     computes returns DSE_ECUDA.
  *
@@ -280,6 +285,42 @@ typedef struct {
 
 dse_status dse_ls_refit(dse_space *space, const dse_refit_desc *desc, uint64_t *best_id,
                         double *best_rmse, double *coefs, double *residual);
+
+/* The whole residual loop on the device ("Software Description": SIS to
+   retain candidates, then a sparsifying step, OMP being one of the named
+   strategies; Eq. 1 approximated greedily): r_0 = y; for D = 1..n_iter the
+   SIS screen of r_{D-1} over the whole space (top k, same semantics as
+   dse_sis_screen in PER_TARGET mode), then the least-squares refits of
+   every retained candidate with the D-1 descriptors chosen so far (as
+   dse_ls_refit), the pick of the smallest RMSE and the new residual
+   r_D = y - fit.  The screen is planned once and every iteration is
+   enqueued back to back with no host round trip; the call waits once at
+   the end (and re-runs an iteration on the host-driven path if its
+   candidate buffer overflowed).  Synchronises.  Errors: DSE_EINVAL when an
+   iteration finds no full-rank fit, DSE_EOVERFLOW on a persistent overflow,
+   the codes of dse_sis_screen otherwise. */
+typedef struct {
+  const double *y;        /* N values, host or device                       */
+  int32_t y_on_device;
+  int32_t n_iter;         /* 1..4                                           */
+  int64_t k;              /* retained candidates per iteration, >= 1        */
+  int32_t precision;      /* DSE_PREC_FP32 / AUTO (FP32) or DSE_PREC_FP64   */
+  int32_t flags;          /* DSE_FLAG_TIMING: kernel_ms of each screen      */
+  void *stream;           /* cudaStream_t                                   */
+} dse_loop_desc;
+
+typedef struct {
+  uint64_t chosen[4];     /* descriptor ids d_1..d_n_iter                   */
+  double rmse[4];         /* RMSE of the fit after each iteration           */
+  double coefs[4][5];     /* per iteration: intercept, then D coefficients  */
+  dse_stats stats[4];     /* statistics of each iteration's screen          */
+} dse_loop_result;
+
+/* sis_ids: optional [n_iter][k] (host or device) -- each iteration's SIS
+   subspace in rank order, 2^64-1 past its length; residual: optional final
+   residual r_n_iter (N values, host or device). */
+dse_status dse_residual_loop(dse_space *space, const dse_loop_desc *desc, dse_loop_result *out,
+                             uint64_t *sis_ids, double *residual);
 
 /* dse_ls_refit without any device allocation.  The paper has no counterpart:
    this is an engineering variant of the same refit step for callers that may

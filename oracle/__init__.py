@@ -93,6 +93,8 @@ def lib():
             L.orc_residual_loop.argtypes = [vp, dp, C.c_int, i64, C.POINTER(u64), dp, dp,
                                             C.POINTER(u64), C.POINTER(i64), dp]
             L.orc_num_threads.restype = C.c_int
+            L.orc_margins.argtypes = [vp, C.c_int, u64, u64, dp]
+            L.orc_margins.restype = C.c_int
             _lib = L
     return _lib
 
@@ -226,6 +228,16 @@ class Space:
                                _dptr(sc), why.ctypes.data_as(C.POINTER(C.c_int32))):
             raise ValueError("orc_score_ids failed")
         return sc, why
+
+    def margins(self, rung: int, p_begin: int = 0, p_end=None):
+        """Smallest relative margins of the magnitude, exp-domain and realised
+        tests over flat slots [p_begin, p_end) of ``rung`` (and the slot count)."""
+        out = np.zeros(4)
+        if p_end is None:
+            p_end = np.iinfo(np.uint64).max
+        if lib().orc_margins(self._h, rung, p_begin, p_end, _dptr(out)):
+            raise ValueError("orc_margins failed")
+        return {"magnitude": out[0], "exp_domain": out[1], "realised": out[2], "slots": int(out[3])}
 
     def residual_loop(self, y, Dmax: int, k: int):
         y = np.ascontiguousarray(y, dtype=np.float64)

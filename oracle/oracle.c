@@ -872,6 +872,84 @@ int orc_residual_loop(const orc_space *S, const double *y, int Dmax, int64_t k, 
   return rc;
 }
 
+/* Margins of the threshold tests (R5-R7) over flat slots [p0, p1) of rung r:
+   how close any decision came to flipping, as relative distances, so that a
+   1-ulp difference in an FP64 library function (exp, log) between two
+   implementations cannot change a mask when every margin is well above the
+   rounding level.  out[0] magnitude: |B - fmax_max| / fmax_max over slots
+   reaching the magnitude test (exp: |max - log(fmax_max)| / log(fmax_max));
+   out[1] exp domain: |max - 80| / 80; out[2] realised: |sd - f*rms| / (f*rms)
+   over slots reaching the realised test with finite values; out[3] the
+   number of slots whose tests were examined.  Minima start at +inf. */
+int orc_margins(const orc_space *S, int r, uint64_t p0, uint64_t p1, double *out) {
+  if (r < 1 || r > S->P.max_rung) return -1;
+  const uint64_t slots = rung_slots(S, r);
+  if (p1 > slots) p1 = slots;
+  double m_mag = INFINITY, m_exp = INFINITY, m_real = INFINITY, n_seen = 0;
+  const int64_t N = S->N;
+#pragma omp parallel reduction(min : m_mag, m_exp, m_real) reduction(+ : n_seen)
+  {
+    double *v = (double *)malloc(sizeof(double) * (size_t)N);
+#pragma omp for schedule(dynamic, 256)
+    for (int64_t pi = (int64_t)p0; pi < (int64_t)p1; ++pi) {
+      int op; int64_t a, b;
+      int64_t u[ORC_MAX_DIMS]; int32_t cx;
+      if (decode_flat(S, r, (uint64_t)pi, &op, &a, &b) != 0) continue;
+      n_seen += 1;
+      const int why = apriori(S, op, a, b, u, &cx);
+      if (why == ORC_R_UNIT || why == ORC_R_COMPLEXITY) continue;
+      if (op == ORC_EXP) {
+        const double d = fabs(S->vmax[a] - 80.0) / 80.0;
+        if (d < m_exp) m_exp = d;
+        if (why == ORC_R_DOMAIN) continue;
+        const double e = fabs(S->vmax[a] - S->exp_arg_max) / fabs(S->exp_arg_max);
+        if (e < m_mag) m_mag = e;
+      } else if (why != ORC_R_DOMAIN && op != ORC_LOG) {
+        const double mna = S->vminabs[a], mxa = S->vmaxabs[a];
+        double B = 0;
+        switch (op) {
+        case ORC_SQUARE: B = mxa * mxa; break;
+        case ORC_CUBE: B = (mxa * mxa) * mxa; break;
+        case ORC_INV: B = 1.0 / mna; break;
+        case ORC_SQRT: B = sqrt(mxa); break;
+        case ORC_ADD: case ORC_SUB: case ORC_ABSDIFF: B = mxa + S->vmaxabs[b]; break;
+        case ORC_MUL: B = mxa * S->vmaxabs[b]; break;
+        case ORC_DIV: B = mxa / S->vminabs[b]; break;
+        case ORC_RDIV: B = S->vmaxabs[b] / mna; break;
+        default: break;
+        }
+        const double d = fabs(B - S->P.fmax_max) / S->P.fmax_max;
+        if (d < m_mag) m_mag = d;
+      }
+      if (why != ORC_VALID || S->P.fmin_std_rel < 0) continue;
+      evaluate(S, op, a, b, v);
+      int fin = 1;
+      for (int64_t t = 0; t < N; ++t) fin &= isfinite(v[t]) != 0;
+      if (!fin) continue;
+      nsum q0 = {0, 0};
+      for (int64_t t = 0; t < N; ++t) nadd(&q0, v[t]);
+      const double mean = nval(&q0) / (double)N;
+      nsum q = {0, 0}, rr = {0, 0};
+      for (int64_t t = 0; t < N; ++t) {
+        const double d = v[t] - mean;
+        nadd(&q, d * d);
+        nadd(&rr, v[t] * v[t]);
+      }
+      const double sd = sqrt(nval(&q) / (double)N), lim = S->P.fmin_std_rel * sqrt(nval(&rr) / (double)N);
+      if (lim > 0) {
+        const double d = fabs(sd - lim) / lim;
+        if (d < m_real) m_real = d;
+      }
+    }
+    free(v);
+  }
+  out[0] = m_mag;
+  out[1] = m_exp;
+  out[2] = m_real;
+  out[3] = n_seen;
+  return 0;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

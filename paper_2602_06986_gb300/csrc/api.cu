@@ -292,7 +292,19 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
   return DSE_OK;
 }
 
-static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_result **out) {
+// What a re-run of a screen needs (launch arguments, plan, tile lists).
+struct Keep {
+  ScreenPlan plan;
+  ScreenArgs A;
+  SelectArgs S;
+  Tile *tmul, *tadd;
+  unsigned *tile_ctr;
+};
+
+// Plan a screen and allocate everything; with launch, also upload the
+// targets and enqueue it (otherwise d->Y is ignored and the screen is run
+// later by screen_enqueue_target).
+static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_result **out, bool launch = true) {
   cudaStream_t st = (cudaStream_t)d->stream;
   const int64_t N = sp->N;
   const uint64_t total = (uint64_t)sp->n + sp->geom.slots;
@@ -441,7 +453,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   const int64_t T = d->n_targets;
   int64_t sort_cap = 1;
   while (sort_cap < cap) sort_cap <<= 1;
-  if (!d->y_on_device) sc.add(&Yd, (size_t)T * d->ld_y);
+  if (launch && !d->y_on_device) sc.add(&Yd, (size_t)T * d->ld_y);
   sc.add(&R->y64, (size_t)T * R->ldy);
   sc.add(&R->y32, (size_t)T * R->ldy);
   sc.add(&R->ysum32, (size_t)T);
@@ -496,7 +508,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   };
   cudaError_t e = cudaSuccess;
   const double *Ysrc = d->Y;
-  if (!d->y_on_device) {
+  if (launch && !d->y_on_device) {
     e = cudaMemcpyAsync(Yd, d->Y, sizeof(double) * T * d->ld_y, cudaMemcpyHostToDevice, st);
     Ysrc = Yd;
   }
@@ -509,8 +521,8 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   if (!e) e = cudaMemsetAsync(R->err, 0, sizeof(int), st);
   if (!e) e = cudaMemsetAsync(A.B.theta, 0, sizeof(float) * n_lists, st);
   if (e) return fail(cuda_status(e, "screen setup"));
-  launch_targets(Ysrc, d->ld_y, (int)T, N, R->ldy, R->y64, R->y32, R->ysum32, R->err, st);
-  R->launches = 1;
+  if (launch) launch_targets(Ysrc, d->ld_y, (int)T, N, R->ldy, R->y64, R->y32, R->ysum32, R->err, st);
+  R->launches = launch ? 1 : 0;
   R->flags = d->flags;
 
   A.F = table_of(sp);
@@ -563,20 +575,15 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   S.sort_cap = big_sort ? sort_cap : 1;
   S.stats = R->stats;
 
-  s = run_screen(R, plan, tmul, tadd, A, S, tile_ctr);
-  if (s != DSE_OK) return fail(s);
+  if (launch) {
+    s = run_screen(R, plan, tmul, tadd, A, S, tile_ctr);
+    if (s != DSE_OK) return fail(s);
+  }
 
   // keep what a re-run after a buffer overflow needs
   R->host_stats = dse_stats{};
   R->host_stats.screened = (int64_t)(id_end - id_begin);
   R->host_stats.precision_used = prec;
-  struct Keep {
-    ScreenPlan plan;
-    ScreenArgs A;
-    SelectArgs S;
-    Tile *tmul, *tadd;
-    unsigned *tile_ctr;
-  };
   Keep *keep = new (std::nothrow) Keep{plan, A, S, tmul, tadd, tile_ctr};
   if (!keep) return fail(DSE_ENOMEM);
   R->keep = keep;
@@ -589,6 +596,40 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   R->buf_count = A.B.count;
   *out = R;
   return DSE_OK;
+}
+
+// Screen a prepared result (screen_impl without launch) against new targets
+// already on the device (T rows of stride ld_y): thresholds start from zero.
+static dse_status screen_enqueue_target(dse_result *R, const double *Y, int64_t ld_y) {
+  cudaStream_t st = R->stream;
+  Keep *k = reinterpret_cast<Keep *>(R->keep);
+  DSE_CUDA(cudaMemsetAsync(R->err, 0, sizeof(int), st));
+  DSE_CUDA(cudaMemsetAsync(k->A.B.theta, 0, sizeof(float) * R->n_lists, st));
+  launch_targets(Y, ld_y, R->T, R->space->N, R->ldy, R->y64, R->y32, R->ysum32, R->err, st);
+  R->launches = 1;
+  R->fetched = false;
+  R->reruns = 0;
+  return run_screen(R, k->plan, k->tmul, k->tadd, k->A, k->S, k->tile_ctr);
+}
+
+// The statistics of a finished screen from its device counters (stats,
+// per-list buffered counts, list lengths and largest bounds).
+static void stats_from_counters(const dse_result *R, const unsigned long long *hs, const unsigned *bc,
+                                const int64_t *nout, const double *mx, dse_stats &o) {
+  for (int c = 0; c < 6; ++c) o.reasons[c] = (int64_t)hs[ST_REASON0 + c];
+  o.reasons[DSE_R_UNIT] += (int64_t)R->add_total - (int64_t)hs[ST_ADD_SEEN];
+  o.evaluated = (int64_t)hs[ST_EVALUATED];
+  for (int g = 0; g < 3; ++g) o.valid_by_group[g] = (int64_t)hs[ST_VALID_G0 + g];
+  o.kernel_launches = R->launches;
+  o.buffered = 0;
+  for (int l = 0; l < R->n_lists; ++l) o.buffered += bc[l];
+  o.escalated = (int64_t)hs[ST_ESCALATED];
+  o.rescored = (int64_t)hs[ST_RESCORED];
+  o.reruns = R->reruns;
+  double m = 0.0;
+  for (int l = 0; l < R->n_lists; ++l)
+    if (nout[l] > 0) m = std::max(m, mx[l]);
+  o.max_err_bound = m;
 }
 
 // Wait for a result, re-running the screen while any list overflowed its
@@ -636,33 +677,203 @@ static dse_status finish(dse_result *R) {
       return DSE_EOVERFLOW;
     }
     dse_stats &o = R->host_stats;
-    for (int c = 0; c < 6; ++c) o.reasons[c] = (int64_t)hs[ST_REASON0 + c];
-    o.reasons[DSE_R_UNIT] += (int64_t)R->add_total - (int64_t)hs[ST_ADD_SEEN];
-    o.evaluated = (int64_t)hs[ST_EVALUATED];
-    for (int g = 0; g < 3; ++g) o.valid_by_group[g] = (int64_t)hs[ST_VALID_G0 + g];
+    stats_from_counters(R, hs, reinterpret_cast<const unsigned *>(h + o_bc),
+                        reinterpret_cast<const int64_t *>(h + o_n), reinterpret_cast<const double *>(h + o_eps), o);
     for (int g = 0; g < 4; ++g) o.kernel_ms[g] = 0.0;
     for (auto &t : R->timing) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, t.second.first, t.second.second) == cudaSuccess && t.first >= 0 && t.first < 4)
         o.kernel_ms[t.first] += ms;
     }
-    o.kernel_launches = R->launches;
-    const unsigned *bc = reinterpret_cast<const unsigned *>(h + o_bc);
-    o.buffered = 0;
-    for (int l = 0; l < nl; ++l) o.buffered += bc[l];
-    o.escalated = (int64_t)hs[ST_ESCALATED];
-    o.rescored = (int64_t)hs[ST_RESCORED];
-    o.reruns = R->reruns;
     const int64_t *nout = reinterpret_cast<const int64_t *>(h + o_n);
-    const double *mx = reinterpret_cast<const double *>(h + o_eps);
     R->h_out_n.assign(nout, nout + nl);
-    double m = 0.0;
-    for (int l = 0; l < nl; ++l)
-      if (nout[l] > 0) m = std::max(m, mx[l]);
-    o.max_err_bound = m;
     R->fetched = true;
     return DSE_OK;
   }
+}
+
+
+// ------------------------------------------------------ residual loop
+
+size_t refit_chain_bytes(int64_t N, int64_t cap);
+void refit_chain(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
+                 const int64_t *n_dev, void *scratch, double *res, double *report, uint64_t *chosen,
+                 cudaStream_t st);
+
+constexpr int kLoopMax = 4;  // descriptors (the refit fits up to 4 columns)
+constexpr int kReport = 8;   // winner's index, id, rmse, intercept + 4 coefficients
+constexpr int kSmall = ST_COUNT + 5;  // per iteration: counters, overflow, buffered, list length, max bound, error
+
+// The residual loop with every iteration enqueued back to back: screen of
+// the current residual (one plan, reused), then the refits of its top k
+// against the descriptors chosen so far, all on the device; the host reads
+// the reports once at the end.  An iteration whose candidate buffer
+// overflowed is repeated, with the rest of the loop, on the host-driven
+// path (wait, re-run from the thresholds reached, refit).
+static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_loop_result *out, uint64_t *sis_ids,
+                                     double *residual) {
+  cudaStream_t st = (cudaStream_t)d->stream;
+  const int D = d->n_iter;
+  const int64_t N = sp->N, k = d->k;
+  dse_screen_desc sd{};
+  sd.ld_y = N;
+  sd.n_targets = 1;
+  sd.k = k;
+  sd.mode = DSE_MODE_PER_TARGET;
+  sd.precision = d->precision == DSE_PREC_FP64 ? DSE_PREC_FP64 : DSE_PREC_FP32;
+  sd.stream = d->stream;
+  sd.flags = d->flags & DSE_FLAG_TIMING;
+  dse_result *R = nullptr;
+  DSE_TRY(screen_impl(sp, &sd, &R, false));
+  struct Owner {
+    dse_result *R;
+    void *scratch = nullptr;
+    ~Owner() {
+      dfree(scratch);
+      dse_result_free(R);
+    }
+  } own{R};
+
+  double *ydev = nullptr, *r = nullptr, *rep = nullptr;
+  uint64_t *fid = nullptr, *ids = nullptr;
+  unsigned long long *small = nullptr;
+  unsigned char *rscr = nullptr;
+  Scratch sc;
+  if (!d->y_on_device) sc.add(&ydev, (size_t)N);
+  sc.add(&r, (size_t)D * N);
+  sc.add(&fid, kLoopMax);
+  sc.add(&rep, (size_t)D * kReport);
+  sc.add(&small, (size_t)D * kSmall);
+  sc.add(&ids, (size_t)D * k);
+  sc.add(&rscr, refit_chain_bytes(N, k));
+  size_t bytes = 0;
+  DSE_TRY(sc.alloc(&own.scratch, &bytes));
+  const double *y = d->y;
+  if (!d->y_on_device) {
+    DSE_CUDA(cudaMemcpyAsync(ydev, d->y, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    y = ydev;
+  }
+  DSE_CUDA(cudaMemsetAsync(fid, 0xFF, sizeof(uint64_t) * kLoopMax, st));
+  DSE_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * D * N, st));
+  DSE_CUDA(cudaMemsetAsync(small, 0, sizeof(unsigned long long) * D * kSmall, st));
+  DSE_CUDA(cudaMemsetAsync(ids, 0xFF, sizeof(uint64_t) * D * k, st));
+
+  auto snapshot = [&](int it) -> dse_status {
+    unsigned long long *sm = small + (size_t)it * kSmall;
+    DSE_CUDA(cudaMemcpyAsync(sm, R->stats, 8 * ST_COUNT, cudaMemcpyDeviceToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT, R->overflow, 4, cudaMemcpyDeviceToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 1, R->buf_count, 4, cudaMemcpyDeviceToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 2, R->out_n, 8, cudaMemcpyDeviceToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 3, R->max_eps, 8, cudaMemcpyDeviceToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 4, R->err, 4, cudaMemcpyDeviceToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(ids + (size_t)it * k, R->out_id, 8 * k, cudaMemcpyDeviceToDevice, st));
+    return DSE_OK;
+  };
+  auto step = [&](int it) -> dse_status {
+    const double *src = it == 0 ? y : r + (size_t)(it - 1) * N;
+    DSE_TRY(screen_enqueue_target(R, src, N));
+    DSE_TRY(snapshot(it));
+    refit_chain(sp, y, fid, it, R->out_id, k, R->out_n, rscr, r + (size_t)it * N, rep + (size_t)it * kReport,
+                fid + it, st);
+    DSE_CUDA(cudaGetLastError());
+    return DSE_OK;
+  };
+  const size_t hbytes = sizeof(unsigned long long) * D * kSmall + sizeof(double) * D * kReport;
+  auto read_back = [&](unsigned long long **hs, double **hr) -> dse_status {
+    char *h = static_cast<char *>(pinned_staging(hbytes));
+    if (!h) return DSE_ENOMEM;
+    DSE_CUDA(cudaMemcpyAsync(h, small, sizeof(unsigned long long) * D * kSmall, cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaMemcpyAsync(h + sizeof(unsigned long long) * D * kSmall, rep, sizeof(double) * D * kReport,
+                             cudaMemcpyDeviceToHost, st));
+    DSE_CUDA(cudaStreamSynchronize(st));
+    *hs = reinterpret_cast<unsigned long long *>(h);
+    *hr = reinterpret_cast<double *>(h + sizeof(unsigned long long) * D * kSmall);
+    return DSE_OK;
+  };
+
+  // all iterations back to back, one wait
+  size_t tmark[kLoopMax + 1];  // each iteration's range of timing events
+  for (int it = 0; it < D; ++it) {
+    tmark[it] = R->timing.size();
+    DSE_TRY(step(it));
+  }
+  tmark[D] = R->timing.size();
+  unsigned long long *hs = nullptr;
+  double *hr = nullptr;
+  DSE_TRY(read_back(&hs, &hr));
+  int first_bad = D;
+  for (int it = 0; it < D && first_bad == D; ++it) {
+    const unsigned long long *sm = hs + (size_t)it * kSmall;
+    if ((unsigned)sm[ST_COUNT] != 0u) first_bad = it;  // buffer overflow
+  }
+  if (first_bad < D) {
+    // repeat from the overflowed iteration with the host-driven path
+    for (int it = first_bad; it < D; ++it) {
+      const double *src = it == 0 ? y : r + (size_t)(it - 1) * N;
+      tmark[it] = R->timing.size();
+      DSE_TRY(screen_enqueue_target(R, src, N));
+      DSE_TRY(finish(R));
+      DSE_TRY(snapshot(it));
+      refit_chain(sp, y, fid, it, R->out_id, k, R->out_n, rscr, r + (size_t)it * N, rep + (size_t)it * kReport,
+                  fid + it, st);
+      DSE_CUDA(cudaGetLastError());
+      out->stats[it] = R->host_stats;
+      tmark[it + 1] = R->timing.size();
+    }
+    DSE_TRY(read_back(&hs, &hr));
+  }
+  for (int it = 0; it < D; ++it) {
+    const unsigned long long *sm = hs + (size_t)it * kSmall;
+    const int herr = (int)(unsigned)sm[ST_COUNT + 4];
+    if (herr) {
+      set_error(herr == DSE_ETIMEOUT ? "a bounded device wait timed out"
+                                     : "invalid target or residual (zero variance or not finite)");
+      return herr;
+    }
+    if (sm[ST_ESC_OVERFLOW]) {
+      set_error("escalation list overflow");
+      return DSE_EOVERFLOW;
+    }
+    const double *rr = hr + (size_t)it * kReport;
+    long long bi, bid;
+    memcpy(&bi, &rr[0], 8);
+    memcpy(&bid, &rr[1], 8);
+    if (bi < 0) {
+      set_error("iteration %d: no candidate gives a full-rank fit", it + 1);
+      return DSE_EINVAL;
+    }
+    out->chosen[it] = (uint64_t)bid;
+    out->rmse[it] = rr[2];
+    for (int c = 0; c < 5; ++c) out->coefs[it][c] = c < it + 2 ? rr[3 + c] : 0.0;
+    if (it < first_bad) {
+      const unsigned bc = (unsigned)sm[ST_COUNT + 1];
+      const int64_t nout = (int64_t)sm[ST_COUNT + 2];
+      double mx;
+      memcpy(&mx, &sm[ST_COUNT + 3], 8);
+      dse_stats &o = out->stats[it];
+      o = dse_stats{};
+      o.screened = R->host_stats.screened;
+      o.precision_used = R->host_stats.precision_used;
+      R->reruns = 0;
+      stats_from_counters(R, sm, &bc, &nout, &mx, o);
+    }
+    // device time of the kernel groups of this iteration's screen
+    dse_stats &o = out->stats[it];
+    for (int g = 0; g < 4; ++g) o.kernel_ms[g] = 0.0;
+    for (size_t e = tmark[it]; e < tmark[it + 1] && e < R->timing.size(); ++e) {
+      float ms = 0.f;
+      const auto &t = R->timing[e];
+      if (cudaEventElapsedTime(&ms, t.second.first, t.second.second) == cudaSuccess && t.first >= 0 && t.first < 4)
+        o.kernel_ms[t.first] += ms;
+    }
+  }
+  // outputs
+  if (sis_ids) {
+    DSE_CUDA(cudaMemcpyAsync(sis_ids, ids, sizeof(uint64_t) * D * k, cudaMemcpyDefault, st));
+  }
+  if (residual) DSE_CUDA(cudaMemcpyAsync(residual, r + (size_t)(D - 1) * N, sizeof(double) * N, cudaMemcpyDefault, st));
+  DSE_CUDA(cudaStreamSynchronize(st));
+  return DSE_OK;
 }
 
 }  // namespace dse
@@ -870,6 +1081,20 @@ dse_status dse_result_stats(dse_result *r, dse_stats *out) {
   DSE_TRY(finish(r));
   *out = r->host_stats;
   return DSE_OK;
+}
+
+dse_status dse_residual_loop(dse_space *s, const dse_loop_desc *d, dse_loop_result *out, uint64_t *sis_ids,
+                             double *residual) {
+  clear_error();
+  if (!s || !d || !out || !d->y || d->n_iter < 1 || d->n_iter > kLoopMax || d->k < 1 || d->k > (1 << 20) ||
+      d->precision < 0 || d->precision > DSE_PREC_AUTO) {
+    set_error("invalid loop descriptor");
+    return DSE_EINVAL;
+  }
+  *out = dse_loop_result{};
+  DSE_TRY(check_device());
+  AllocStream as((cudaStream_t)d->stream);
+  return residual_loop_impl(s, d, out, sis_ids, residual);
 }
 
 dse_status dse_ls_refit(dse_space *s, const dse_refit_desc *d, uint64_t *best_id, double *best_rmse, double *coefs,

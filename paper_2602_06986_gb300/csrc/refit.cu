@@ -42,6 +42,10 @@ __global__ void k_columns(FeatTable F, RungGeom G, int64_t n_stored, const uint6
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n) return;
+  if (ids[w] >= (uint64_t)n_stored + G.slots) {  // no such candidate (a failed step of a chained loop)
+    for (int64_t s = lane; s < F.N; s += 32) out[(int64_t)w * F.N + s] = 0.0;
+    return;
+  }
   int op;
   int64_t a, b;
   decode_any(G, n_stored, ids[w], &op, &a, &b);
@@ -234,12 +238,12 @@ template <bool CACHE>
 __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, int64_t n_stored, const double *fcc,
                                                       const double *ycc, const double *pre, int nf,
                                                       const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand,
-                                                      double *rmse_out, double *beta_out) {
+                                                      const int64_t *n_dev, double *rmse_out, double *beta_out) {
   __shared__ double sm[(kWide / 32) * 20];
   __shared__ double s_bc[kMaxP + 2];
   extern __shared__ double col[];
   const int64_t w = blockIdx.x;
-  if (w >= n_cand) return;
+  if (w >= n_cand || (n_dev && w >= *n_dev)) return;
   const int64_t N = F.N;
   const int p = nf + 1;
   const uint64_t gid = cand[w];
@@ -343,8 +347,11 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
 // Index of the smallest RMSE (ties: lower id); one block.  report (when not
 // null) gets {index, id, rmse, beta[kMaxP + 1]} of the winner as doubles /
 // bit patterns, for one small copy to the host.
+// n_dev (when not null) caps n with a count on the device; chosen (when not
+// null) gets the winner's id (2^64-1 if none), for fits chained on the device.
 __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
-                         double *report) {
+                         double *report, const int64_t *n_dev, uint64_t *chosen) {
+  if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ double bv[1024];
   __shared__ uint64_t bid[1024];
   __shared__ int64_t bix[1024];
@@ -378,6 +385,7 @@ __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, in
   if (threadIdx.x == 0) {
     const int64_t b = bv[0] < INFINITY ? bix[0] : -1;
     *best = b;
+    if (chosen) *chosen = b >= 0 ? cand[b] : ~0ull;
     if (report) {
       report[0] = __longlong_as_double(b);
       report[1] = __longlong_as_double(b >= 0 ? (long long)cand[b] : -1ll);
@@ -402,6 +410,51 @@ __global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const doub
     f = fma(beta[nf + 1], col_value(F, G, n_stored, op, a, b, s), f);
     res[s] = y[s] - f;
   }
+}
+
+// ------------------------------------------------ refits chained on the device
+
+size_t refit_chain_bytes(int64_t N, int64_t cap) {
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  return r(8 * (size_t)N * kMaxP) * 2 + r(8 * N) + r(8 * kPreSize) + r(8 * cap) + r(8 * (size_t)cap * (kMaxP + 1)) +
+         r(8);
+}
+
+// One refit step with everything on the device: candidates cand[0..*n_dev)
+// (at most cap), fixed ids fid[0..nf) (device), the chosen id written to
+// *chosen, the residual y - fit to res, the winner's report (index, id,
+// rmse, coefficients) to report.  scratch: refit_chain_bytes(N, cap) bytes.
+void refit_chain(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
+                 const int64_t *n_dev, void *scratch, double *res, double *report, uint64_t *chosen,
+                 cudaStream_t st) {
+  const int64_t N = S->N;
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  char *base = static_cast<char *>(scratch);
+  double *fc = reinterpret_cast<double *>(base);
+  base += r(8 * (size_t)N * kMaxP);
+  double *fcc = reinterpret_cast<double *>(base);
+  base += r(8 * (size_t)N * kMaxP);
+  double *ycc = reinterpret_cast<double *>(base);
+  base += r(8 * N);
+  double *pre = reinterpret_cast<double *>(base);
+  base += r(8 * kPreSize);
+  double *rm = reinterpret_cast<double *>(base);
+  base += r(8 * cap);
+  double *beta = reinterpret_cast<double *>(base);
+  base += r(8 * (size_t)cap * (kMaxP + 1));
+  int64_t *best = reinterpret_cast<int64_t *>(base);
+  const FeatTable F = table_of(S);
+  note_launches(4 + (nf ? 1 : 0));
+  if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
+  k_refit_prep<<<1, kWide, 0, st>>>(y, fc, nf, N, fcc, ycc, pre);
+  if (N <= kRefitCacheMax)
+    k_refit_wide<true><<<(unsigned)cap, kWide, (size_t)N * sizeof(double), st>>>(F, S->geom, S->n, fcc, ycc, pre,
+                                                                               nf, fid, cand, cap, n_dev, rm, beta);
+  else
+    k_refit_wide<false><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, nf, fid, cand, cap, n_dev,
+                                                          rm, beta);
+  k_argmin<<<1, 1024, 0, st>>>(rm, cand, cap, best, beta, report, n_dev, chosen);
+  k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
 }
 
 static inline long long __double_as_longlong_host(double x) {
@@ -471,11 +524,11 @@ dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, 
   k_refit_prep<<<1, kWide, 0, st>>>(y, fc, nf, N, fcc, ycc, pre);
   if (N <= kRefitCacheMax)
     k_refit_wide<true><<<(unsigned)nc, kWide, (size_t)N * sizeof(double), st>>>(F, S->geom, S->n, fcc, ycc, pre,
-                                                                              nf, fid, cand, nc, rm, beta);
+                                                                              nf, fid, cand, nc, nullptr, rm, beta);
   else
-    k_refit_wide<false><<<(unsigned)nc, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, nf, fid, cand, nc, rm,
-                                                         beta);
-  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, rep);
+    k_refit_wide<false><<<(unsigned)nc, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, nf, fid, cand, nc, nullptr,
+                                                         rm, beta);
+  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, rep, nullptr, nullptr);
   k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
   // one asynchronous copy of the winner's report (and of a host residual), one sync
   double *h = static_cast<double *>(pinned_staging(8 * (kMaxP + 4)));

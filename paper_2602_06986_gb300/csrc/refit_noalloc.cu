@@ -24,7 +24,7 @@ __global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double 
                         const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand, double *rmse_out,
                         double *beta_out);
 __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
-                         double *report);
+                         double *report, const int64_t *n_dev, uint64_t *chosen);
 __global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const double *y, const double *fixed_cols,
                            int nf, const uint64_t *cand, const int64_t *best, const double *beta_all, double *res);
 
@@ -131,7 +131,7 @@ dse_status refit_noalloc_impl(dse_space *S, const dse_refit_desc *d, uint64_t *b
   note_launches(3 + (nf ? 1 : 0));
   if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
   k_refit<<<(unsigned)((nc * 32 + 255) / 256), 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, fid, cand, nc, rm, beta);
-  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, nullptr);
+  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, nullptr, nullptr, nullptr);
   k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
   int64_t hb = -1;
   e = cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st);

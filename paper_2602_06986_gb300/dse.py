@@ -75,10 +75,21 @@ class BatchDesc(C.Structure):
 
 BATCH_GRAPH = 1
 
+
+class LoopDesc(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("y_on_device", C.c_int32), ("n_iter", C.c_int32), ("k", C.c_int64),
+                ("precision", C.c_int32), ("flags", C.c_int32), ("stream", C.c_void_p)]
+
+
+class LoopResult(C.Structure):
+    _fields_ = [("chosen", C.c_uint64 * 4), ("rmse", C.c_double * 4), ("coefs", (C.c_double * 5) * 4),
+                ("stats", Stats * 4)]
+
 EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_counts", "dse_decode",
            "dse_expr_string", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
            "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
-           "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error", "dse_version"]
+           "dse_residual_loop", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error",
+           "dse_version"]
 
 _lib = None
 
@@ -109,6 +120,7 @@ def lib():
         L.dse_batch_stats.argtypes = [vp, i32, C.POINTER(Stats)]
         L.dse_batch_free.argtypes = [vp]
         L.dse_batch_free.restype = None
+        L.dse_residual_loop.argtypes = [vp, C.POINTER(LoopDesc), C.POINTER(LoopResult), vp, vp]
         L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
         L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
         L.dse_last_error.restype = C.c_char_p
@@ -322,6 +334,24 @@ class Space:
         h = C.c_void_p()
         _check(lib().dse_sis_screen(self._h, C.byref(d), C.byref(h)))
         return Result(h, 1 if mode == MODE_AGGREGATED else T, k)
+
+    def residual_loop(self, y, n_iter, k, precision=PREC_FP32, sis_ids=None, residual=None, stream=None, flags=0):
+        """The residual loop on the device (dse_residual_loop): returns a dict
+        with the chosen ids, RMSEs, coefficients and per-iteration screen
+        statistics.  ``sis_ids`` / ``residual``: optional output buffers
+        (numpy or torch CUDA) of n_iter*k ids and N values."""
+        if isinstance(y, np.ndarray):
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        py, ydev = _ptr(y)
+        d = LoopDesc(py, ydev, n_iter, k, precision, flags, stream)
+        out = LoopResult()
+        pi, _ = _ptr(sis_ids)
+        pr, _ = _ptr(residual)
+        _check(lib().dse_residual_loop(self._h, C.byref(d), C.byref(out), pi, pr))
+        return {"chosen": [int(out.chosen[i]) for i in range(n_iter)],
+                "rmse": [float(out.rmse[i]) for i in range(n_iter)],
+                "coefs": [[float(out.coefs[i][c]) for c in range(i + 2)] for i in range(n_iter)],
+                "stats": [_stats_dict(out.stats[i]) for i in range(n_iter)]}
 
     def ls_refit(self, y, fixed, cand, residual=None, stream=None):
         """Best candidate for the next descriptor slot: (id, rmse, coefs, residual)."""

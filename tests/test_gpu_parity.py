@@ -267,3 +267,49 @@ def test_residual_loop_medium(env):
         fixed.append(bid)
         r = resid
     assert ref["rmse"][2] < ref["rmse"][0]
+
+
+@pytest.mark.parametrize("wname,D,prec", [("medium", 3, "fp32"), ("tiny", 2, "fp32"), ("medium", 2, "fp64")])
+def test_residual_loop_on_device(env, wname, D, prec):
+    """dse_residual_loop (screen, refit and residual chained on the device)
+    against the oracle's loop (RMSE per iteration; the pick may be an exact
+    algebraic twin) and against the host-driven sequence of the same calls
+    (identical picks, RMSEs and SIS subspaces)."""
+    torch, oracle, dse, W = env
+    w = getattr(W, wname)(0)
+    sp, orc = spaces(env, w)
+    y = w["Y"][0]
+    k = w["k"]
+    p = dse.PREC_FP64 if prec == "fp64" else dse.PREC_FP32
+    ref = orc.residual_loop(y, D, k)
+    ids = np.zeros((D, k), np.uint64)
+    resid = np.zeros(len(y))
+    out = sp.residual_loop(y, D, k, precision=p, sis_ids=ids, residual=resid)
+    for d in range(D):
+        assert abs(out["rmse"][d] - ref["rmse"][d]) <= 1e-9 * max(ref["rmse"][d], 1e-12) + 1e-13, d
+        assert out["stats"][d]["screened"] == sp.n_total
+        assert sum(out["stats"][d]["reasons"].values()) == sp.n_total
+    # the first subspace is the oracle's screen of y (same top-k set up to ties)
+    n1 = int(np.sum(ids[0] != np.iinfo(np.uint64).max))
+    assert n1 == k
+    oids, osc, _ = orc.screen(y, k)
+    sc1, why = orc.score_ids(y[None, :], ids[0][:n1])
+    assert np.all(why == 0)
+    sk = osc[0][-1]
+    assert np.all(sc1[:, 0] >= sk * (1 - 1e-5))
+    above = {int(i) for i, s_ in zip(oids[0], osc[0]) if s_ > sk * (1 + 1e-5)}
+    assert above <= {int(i) for i in ids[0][:n1]}
+    # the host-driven sequence of the same calls gives the same loop
+    r = y.copy()
+    fixed = []
+    for d in range(D):
+        res = sp.screen(r, k, precision=p)
+        hids, hsc, heb = res.fetch(0)
+        np.testing.assert_array_equal(hids, ids[d][:len(hids)])
+        bid, rmse, coefs, resid_h = sp.ls_refit(y, np.array(fixed, np.uint64), hids)
+        assert bid == out["chosen"][d]
+        assert rmse == out["rmse"][d]
+        np.testing.assert_array_equal(coefs, np.array(out["coefs"][d]))
+        fixed.append(bid)
+        r = resid_h
+    np.testing.assert_array_equal(resid, r)

@@ -353,3 +353,40 @@ def test_residual_loop_first_pick_is_top_sis(orc):
     r = sc[0][pick]
     yc = y - y.mean()
     assert abs(out["rmse"][0] - math.sqrt(np.sum(yc ** 2) * (1 - r * r) / 80)) < 1e-12
+
+
+def test_threshold_margin_report_pin():
+    """The margin report measures the distance to the threshold: a square
+    whose a-priori bound sits 1e-6 (relative) under fmax_max."""
+    import oracle
+
+    X = np.array([[1.0, -2.0, 1.5, 0.5], [1.0, 2.0, 3.0, 4.0]])
+    fmax = 4.0 * (1 + 1e-6)
+    S = oracle.Space(X, None, oracle.op_mask(oracle.SQUARE), 1, fmax_max=fmax)
+    m = S.margins(1)
+    assert m["slots"] == 2
+    # square of row 1 has bound 16 > fmax (decided, margin 3); row 0's bound 4
+    assert abs(m["magnitude"] - (fmax - 4.0) / fmax) < 1e-15
+
+
+@pytest.mark.parametrize("name,seed,samples", [("tiny", 0, None), ("tiny", 1, None), ("tiny", 2, None),
+                                               ("medium", 0, 300000), ("precision", 0, 200000),
+                                               ("large", 0, 200000)])
+def test_threshold_margins_of_committed_seeds(name, seed, samples):
+    """Every magnitude, exp-domain and realised decision of the committed
+    seeds (all build rungs, and the screened rung in full or on its first
+    slots) is at least 1e-9 (relative) away from its threshold, so FP64
+    library differences of an ulp cannot flip a mask between the oracle and
+    the CUDA path."""
+    import oracle
+    from paper_2602_06986_gb300 import workloads as W
+
+    w = getattr(W, name)(seed)
+    S = oracle.Space(w["X"], w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                     explog_dimensionless=w["explog_dimensionless"])
+    for r in range(1, w["max_rung"] + 1):
+        end = None if (samples is None or r < w["max_rung"]) else samples
+        m = S.margins(r, 0, end) if end is not None else S.margins(r)
+        assert m["slots"] > 0
+        for key in ("magnitude", "exp_domain", "realised"):
+            assert m[key] > 1e-9, (name, seed, r, key, m[key])
