@@ -238,6 +238,85 @@ def bench_batched(args):
     print(json.dumps(line))
 
 
+def bench_multi_target(args, which):
+    """Multi-target screens on the tensor-core path (BF16x3 tcgen05): the
+    precision workload (N=500, rung 3, one 2^30-id block, 64 targets,
+    top-1000 each) or the large one (N=20000, rung 2, 16 targets, top-10000
+    each).  The space is built once (untimed); a step is one screen, targets
+    resident; L2 flushed between steps."""
+    import torch
+
+    from paper_2602_06986_gb300 import _build
+    from paper_2602_06986_gb300 import workloads as W
+
+    _build.build()
+    from paper_2602_06986_gb300 import dse
+
+    w = W.precision(0, n_targets=64) if which == "precision" else W.large(0, n_targets=16)
+    sp = dse.Space(torch.from_numpy(w["X"]).cuda(), w["units"], w["op_mask"], w["max_rung"],
+                   unit_check_addsub=w["unit_check_addsub"], explog_dimensionless=w["explog_dimensionless"])
+    Yd = torch.from_numpy(w["Y"]).cuda()
+    T, N = w["Y"].shape
+    if which == "precision":
+        b0 = sp.n_stored + 6 * sp.n_stored + w["block_seed"]
+        b1 = min(b0 + w["block_len"], sp.n_total)
+    else:
+        b0, b1 = 0, 0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        r = sp.screen(Yd, w["k"], id_begin=b0, id_end=b1, precision=dse.PREC_AUTO, flags=dse.FLAG_TIMING)
+        r.stats()
+        r.free()
+    ms, stats = [], []
+    clocks = Clocks(0)
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = sp.screen(Yd, w["k"], id_begin=b0, id_end=b1, precision=dse.PREC_AUTO, flags=dse.FLAG_TIMING)
+        st = r.stats()
+        e1.record()
+        torch.cuda.synchronize()
+        r.free()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    clk = clocks.stop()
+    tot = sum(ms)
+    cands = sum(s["evaluated"] for s in stats)
+    tc_ms = sum(s["kernel_ms"][1] + s["kernel_ms"][2] for s in stats)
+    tc_valid = sum(s["valid_by_group"][1] + s["valid_by_group"][2] for s in stats)
+    flops = 6.0 * T * N * tc_valid  # BF16x3: three products of 2 flops per candidate, sample, target
+    achieved = flops / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    peak, peak_src = 1688.5, "bf16_tflops_sustained (MEASURED_PEAKS.json)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        peak, peak_src = 1700.0, "fallback sustained bf16"
+    mhz, _ = peaks()
+    alu_peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
+    alu = 6.0 * N * tc_valid / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    line = {"metric": f"{which}: SIS-screened candidate features/sec (multi-target, tensor cores)",
+            "value": cands / (tot * 1e-3), "unit": "candidates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "dtype": "f32+bf16x3",
+            "data": "synthetic", "config": {"workload": w["name"], "targets": T, "N": N, "k": w["k"],
+                                            "screened_ids": stats[0]["screened"], "l2": "flushed between steps"},
+            "evals_per_s": cands * N / (tot * 1e-3), "precision_used": stats[0]["precision_used"],
+            "roofline": {"bound": "tensor", "kernel": "k_pair_tc (BF16x3 tcgen05)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                         "traffic": None, "peak_source": peak_src, "flops_per_candidate_sample": 6 * T,
+                         "launch_ms_total_per_step": tc_ms / args.steps,
+                         "alu_lane_ops_tps": alu, "alu_frac": alu / alu_peak if alu else None},
+            "per_screen": {k2: sum(s[k2] for s in stats) / len(stats)
+                           for k2 in ("evaluated", "buffered", "escalated", "rescored", "reruns")},
+            "kernel_group_ms_per_step": [sum(s["kernel_ms"][g] for s in stats) / len(stats) for g in range(4)],
+            "clocks": clk}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,10 +324,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dse", choices=["dse", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched"])
+    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "precision", "large"])
     args = ap.parse_args()
     if args.workload == "batched":
         return bench_batched(args)
+    if args.workload in ("precision", "large"):
+        return bench_multi_target(args, args.workload)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
