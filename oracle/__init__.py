@@ -95,6 +95,9 @@ def lib():
             L.orc_num_threads.restype = C.c_int
             L.orc_margins.argtypes = [vp, C.c_int, u64, u64, dp]
             L.orc_margins.restype = C.c_int
+            L.orc_l0_search.argtypes = [vp, dp, C.POINTER(u64), i64, C.c_int, i64, C.POINTER(i64), dp,
+                                        C.POINTER(i64)]
+            L.orc_l0_search.restype = C.c_int
             _lib = L
     return _lib
 
@@ -228,6 +231,20 @@ class Space:
                                _dptr(sc), why.ctypes.data_as(C.POINTER(C.c_int32))):
             raise ValueError("orc_score_ids failed")
         return sc, why
+
+    def l0_search(self, y, ids, D: int, m_top: int = 16):
+        """Exhaustive search of the best D-subsets of the listed candidates
+        (Eq. 1 over a subspace): (positions int64[m, D], RMSE[m]) in the order
+        (RMSE ascending, positions lexicographically ascending)."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        pos = np.zeros((m_top, D), np.int64)
+        rm = np.zeros(m_top)
+        nf = C.c_int64()
+        if lib().orc_l0_search(self._h, _dptr(y), ids.ctypes.data_as(C.POINTER(C.c_uint64)), len(ids), D, m_top,
+                               pos.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(rm), C.byref(nf)):
+            raise ValueError("orc_l0_search failed")
+        return pos[:nf.value].copy(), rm[:nf.value].copy()
 
     def margins(self, rung: int, p_begin: int = 0, p_end=None):
         """Smallest relative margins of the magnitude, exp-domain and realised

@@ -872,6 +872,109 @@ int orc_residual_loop(const orc_space *S, const double *y, int Dmax, int64_t k, 
   return rc;
 }
 
+/* ------------------------------------------------------ exhaustive L0 */
+
+typedef struct { double rmse; int64_t pos[4]; } l0_hit;
+
+/* (rmse ascending, positions lexicographically ascending) */
+static int l0_before(const l0_hit *a, const l0_hit *b, int D) {
+  if (a->rmse != b->rmse) return a->rmse < b->rmse;
+  for (int c = 0; c < D; ++c)
+    if (a->pos[c] != b->pos[c]) return a->pos[c] < b->pos[c];
+  return 0;
+}
+
+static void l0_insert(l0_hit *top, int64_t *n, int64_t m, const l0_hit *h, int D) {
+  if (*n == m && !l0_before(h, &top[m - 1], D)) return;
+  int64_t i = *n < m ? (*n)++ : m - 1;
+  while (i > 0 && l0_before(h, &top[i - 1], D)) { top[i] = top[i - 1]; --i; }
+  top[i] = *h;
+}
+
+/* Eq. 1 solved exhaustively over a listed subspace (the sparsifying step of
+   SISSO that follows SIS): among all D-subsets {p_0 < .. < p_{D-1}} of the
+   positions of ids[0..n), the least-squares fit with intercept of y on the
+   candidates' columns (ls_qr: Householder QR, rank rule of R11) with the
+   smallest RMSE.  Keeps the m_top best full-rank subsets in the order
+   (RMSE ascending, positions lexicographically ascending); best_pos[m_top][D],
+   best_rmse[m_top]; *n_found = how many were kept. */
+int orc_l0_search(const orc_space *S, const double *y, const uint64_t *ids, int64_t n, int D, int64_t m_top,
+                  int64_t *best_pos, double *best_rmse, int64_t *n_found) {
+  const int64_t N = S->N;
+  if (D < 1 || D > 4 || n < D || m_top < 1) return -1;
+  double *cols = (double *)malloc(sizeof(double) * (size_t)n * (size_t)N);
+  if (!cols) return -1;
+  int err = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t why = 0;
+    if (ids[i] >= orc_total_candidates(S) || orc_candidate(S, ids[i], cols + i * N, &why) || why) err = 1;
+  }
+  if (err) { free(cols); return -1; }
+  l0_hit *all = NULL;
+  int64_t n_all = 0;
+#pragma omp parallel
+  {
+    l0_hit *top = (l0_hit *)malloc(sizeof(l0_hit) * (size_t)m_top);
+    int64_t nt = 0;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t p0 = 0; p0 < n; ++p0) {
+      int64_t p[4] = {p0, 0, 0, 0};
+      /* the remaining positions in lexicographic order */
+      int c = 1;
+      if (D > 1) p[1] = p0;
+      for (;;) {
+        if (c == D) {
+          const double *C[4];
+          double beta[5];
+          for (int q = 0; q < D; ++q) C[q] = cols + p[q] * N;
+          l0_hit h;
+          h.rmse = ls_qr(C, D, y, N, beta);
+          for (int q = 0; q < 4; ++q) h.pos[q] = q < D ? p[q] : 0;
+          if (h.rmse < INFINITY) l0_insert(top, &nt, m_top, &h, D);
+          --c;
+          if (c < 1) break;
+          continue;
+        }
+        /* advance position c (c >= 1) */
+        ++p[c];
+        if (p[c] > n - (D - c)) {  /* no room for the later positions */
+          --c;
+          if (c < 1) break;
+          continue;
+        }
+        ++c;
+        if (c < D) p[c] = p[c - 1];
+      }
+    }
+#pragma omp critical
+    {
+      l0_hit *grown = (l0_hit *)realloc(all, sizeof(l0_hit) * (size_t)(n_all + nt));
+      if (grown) {
+        all = grown;
+        memcpy(all + n_all, top, sizeof(l0_hit) * (size_t)nt);
+        n_all += nt;
+      } else {
+        err = 1;
+      }
+    }
+    free(top);
+  }
+  int64_t nf = 0;
+  if (!err) {
+    l0_hit *top = (l0_hit *)malloc(sizeof(l0_hit) * (size_t)m_top);
+    for (int64_t i = 0; i < n_all; ++i) l0_insert(top, &nf, m_top, &all[i], D);
+    for (int64_t i = 0; i < nf; ++i) {
+      best_rmse[i] = top[i].rmse;
+      for (int q = 0; q < D; ++q) best_pos[i * D + q] = top[i].pos[q];
+    }
+    free(top);
+  }
+  *n_found = nf;
+  free(all);
+  free(cols);
+  return err ? -1 : 0;
+}
+
 /* Margins of the threshold tests (R5-R7) over flat slots [p0, p1) of rung r:
    how close any decision came to flipping, as relative distances, so that a
    1-ulp difference in an FP64 library function (exp, log) between two

@@ -390,3 +390,72 @@ def test_threshold_margins_of_committed_seeds(name, seed, samples):
         assert m["slots"] > 0
         for key in ("magnitude", "exp_domain", "realised"):
             assert m[key] > 1e-9, (name, seed, r, key, m[key])
+
+
+def _l0_space():
+    import oracle
+    from paper_2602_06986_gb300 import workloads as W
+
+    w = W.tiny(0)
+    S = oracle.Space(w["X"], w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                     explog_dimensionless=w["explog_dimensionless"])
+    return S, w
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_l0_search_brute_force_lstsq(D):
+    """The exhaustive L0 search against numpy.linalg.lstsq over every
+    D-subset of a small subspace (independent arithmetic)."""
+    import itertools
+
+    S, w = _l0_space()
+    rng = np.random.default_rng(D)
+    y = w["Y"][0] + 0.3 * rng.standard_normal(w["X"].shape[1])
+    ids = np.sort(rng.choice(S.total_candidates, size=40, replace=False)).astype(np.uint64)
+    vals = []
+    for g in ids:
+        v, why = S.candidate(int(g))
+        vals.append(v if why == 0 else None)
+    keep = [i for i, v in enumerate(vals) if v is not None][:11]
+    ids = ids[keep]
+    cols = np.stack([vals[i] for i in keep])
+    ref = []
+    for tup in itertools.combinations(range(len(ids)), D):
+        A = np.column_stack([np.ones(cols.shape[1])] + [cols[t] for t in tup])
+        beta, *_ = np.linalg.lstsq(A, y, rcond=None)
+        if np.linalg.matrix_rank(A) < A.shape[1]:
+            continue
+        ref.append((float(np.sqrt(np.mean((y - A @ beta) ** 2))), tup))
+    ref.sort()
+    pos, rm = S.l0_search(y, ids, D, 10)
+    assert len(pos) == 10
+    for i in range(10):
+        assert abs(rm[i] - ref[i][0]) <= 1e-12 * ref[i][0] + 1e-15
+    # same subsets apart from RMSE ties
+    got = {tuple(p) for p, r in zip(pos.tolist(), rm) if r < ref[9][0] * (1 - 1e-9)}
+    want = {t for r, t in ref[:10] if r < ref[9][0] * (1 - 1e-9)}
+    assert got == want
+
+
+def test_l0_search_special_cases():
+    """D = 1 is the largest |Pearson| (RMSE = std(y) sqrt(1 - r^2)); a
+    noise-free two-term model is recovered with RMSE ~ 0; the best RMSE does
+    not grow with D."""
+    S, w = _l0_space()
+    y0 = w["Y"][0]
+    ids, sc, _ = S.screen(y0, 30)
+    ids = np.sort(ids[0])
+    cols = np.stack([S.candidate(int(g))[0] for g in ids])
+    r = np.array([np.corrcoef(c, y0)[0, 1] for c in cols])
+    pos, rm = S.l0_search(y0, ids, 1, 3)
+    best = int(np.argmax(np.abs(r)))
+    assert abs(abs(r[pos[0][0]]) - abs(r[best])) <= 1e-12
+    assert abs(rm[0] - np.std(y0) * np.sqrt(1 - r[best] ** 2)) <= 1e-10 * np.std(y0)
+    # planted: y = 1.5 + 2 c_a - 0.7 c_b
+    a, b = 3, 17
+    yp = 1.5 + 2.0 * cols[a] - 0.7 * cols[b]
+    pos2, rm2 = S.l0_search(yp, ids, 2, 4)
+    assert rm2[0] <= 1e-10 * np.std(yp)
+    assert tuple(pos2[0]) == (a, b) or rm2[0] <= 1e-12 * np.std(yp)
+    best = [S.l0_search(y0, ids, D, 1)[1][0] for D in (1, 2, 3)]
+    assert best[2] <= best[1] <= best[0]
