@@ -947,7 +947,7 @@ int orc_l0_search(const orc_space *S, const double *y, const uint64_t *ids, int6
       }
     }
 #pragma omp critical
-    {
+    if (nt > 0) {  /* (realloc to zero bytes may return NULL) */
       l0_hit *grown = (l0_hit *)realloc(all, sizeof(l0_hit) * (size_t)(n_all + nt));
       if (grown) {
         all = grown;
