@@ -317,6 +317,71 @@ def bench_multi_target(args, which):
     print(json.dumps(line))
 
 
+def bench_l0(args):
+    """Exhaustive L0 search over the union of the SIS subspaces of the medium
+    workload's residual loop (3 x top-1000): every pair (D = 2) and every
+    triple (D = 3) of the union, FP64 on the device.  The subspace is found
+    once (untimed); a step is one search per dimension."""
+    import math
+
+    import torch
+
+    from paper_2602_06986_gb300 import _build
+    from paper_2602_06986_gb300 import workloads as W
+
+    _build.build()
+    from paper_2602_06986_gb300 import dse
+
+    w = W.medium(0)
+    sp = dse.Space(torch.from_numpy(w["X"]).cuda(), w["units"], w["op_mask"], w["max_rung"],
+                   unit_check_addsub=w["unit_check_addsub"], explog_dimensionless=w["explog_dimensionless"])
+    y = np.ascontiguousarray(w["Y"][0])
+    D, k = w["D"], w["k"]
+    sis = np.zeros((D, k), np.uint64)
+    sp.residual_loop(y, D, k, sis_ids=sis)
+    ids = np.unique(sis[sis != np.iinfo(np.uint64).max])
+    n = len(ids)
+    yd = torch.from_numpy(y).cuda()
+    idd = torch.from_numpy(ids.astype(np.int64)).cuda()
+    res = {}
+    for dim in (2, 3):
+        for _ in range(args.warmup):
+            sp.l0_search(yd, idd, dim, n_top=8)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pos, rm, cf = sp.l0_search(yd, idd, dim, n_top=8)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = sum(ms) / len(ms)
+        subsets = math.comb(n, dim)
+        res[f"D{dim}"] = {"ms": t, "subsets": subsets, "subsets_per_s": subsets / (t * 1e-3),
+                          "best_rmse": float(rm[0]), "best_ids": [int(ids[p]) for p in pos[0]]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        orc = oracle.Space(w["X"], w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                           explog_dimensionless=w["explog_dimensionless"])
+        sub = ids[:400]
+        t0 = time.perf_counter()
+        orc.l0_search(y, sub, 2, 8)
+        dt = time.perf_counter() - t0
+        cpu = {"value": math.comb(len(sub), 2) / dt, "unit": "subsets/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"D=2 over the first {len(sub)} ids of the union ({dt:.1f} s)"}
+    line = {"metric": "exhaustive L0 search: least-squares subsets evaluated per second",
+            "value": res["D3"]["subsets_per_s"], "unit": "subsets/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["D3"]["ms"], "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "medium_n1000 SIS-subspace union", "n_ids": n,
+                                            "dims": [2, 3]},
+            "per_dim": res, "cpu_baseline": cpu}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,12 +389,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dse", choices=["dse", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "precision", "large"])
+    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "precision", "large", "l0"])
     args = ap.parse_args()
     if args.workload == "batched":
         return bench_batched(args)
     if args.workload in ("precision", "large"):
         return bench_multi_target(args, args.workload)
+    if args.workload == "l0":
+        return bench_l0(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -322,6 +322,34 @@ typedef struct {
 dse_status dse_residual_loop(dse_space *space, const dse_loop_desc *desc, dse_loop_result *out,
                              uint64_t *sis_ids, double *residual);
 
+/* Exhaustive L0 search over a listed subspace: Eq. 1 (least squares with
+   intercept, ||beta||_0 <= D) solved exactly over the n_ids listed candidates
+   (typically the union of the SIS subspaces of dse_residual_loop) -- every
+   D-subset, the sparsifying step SISSO applies after SIS ("Summary";
+   exhaustive search over the subspace rather than the greedy loop).  On the
+   device: centred columns, their FP64 Gram matrix, a scan of every subset by
+   an incremental Cholesky step (rank rule of dse_ls_refit, pivots in position
+   order), the 32 best by explained variance, each refit explicitly in FP64.
+   Returns the n_top best subsets by (RMSE ascending, positions ascending):
+   top_pos[n_top][dim] positions into ids (ascending within a subset),
+   top_rmse[n_top], top_coefs[n_top][dim+1] (intercept first; may be NULL),
+   host arrays; n_found = how many (fewer if fewer subsets have full rank).
+   Limits: dim 1..3, n_ids <= 65536 (the Gram matrix takes 8 n_ids^2 bytes),
+   n_top <= 32.  Synchronises. */
+typedef struct {
+  const double *y;        /* N values, host or device                       */
+  int32_t y_on_device;
+  int32_t dim;            /* D: 1..3                                        */
+  const uint64_t *ids;    /* n_ids candidate ids, host or device            */
+  int64_t n_ids;
+  int32_t ids_on_device;
+  int32_t n_top;          /* 1..32                                          */
+  void *stream;           /* cudaStream_t                                   */
+} dse_l0_desc;
+
+dse_status dse_l0_search(dse_space *space, const dse_l0_desc *desc, int64_t *top_pos, double *top_rmse,
+                         double *top_coefs, int32_t *n_found);
+
 /* dse_ls_refit without any device allocation.  The paper has no counterpart:
    this is an engineering variant of the same refit step for callers that may
    not allocate device memory while they run -- code inside a CUDA stream

@@ -46,6 +46,9 @@ void triangle_tiles(int64_t ia, int64_t ib, int BI, int BJ, std::vector<Tile> &o
 dse_status equal_unit_pairs(dse_space *sp, cudaStream_t st);
 // Number of p' in [0, x) with p' mod nb in posset.
 uint64_t count_slots_mod(uint64_t x, int nb, const std::vector<int> &posset);
+// Exhaustive L0 search (l0.cu).
+dse_status l0_search_impl(dse_space *sp, const dse_l0_desc *d, int64_t *top_pos, double *top_rmse, double *top_coefs,
+                          int32_t *n_found);
 // Accumulation error factors of the CUDA-core kernels for N samples.
 void accum_factors(int64_t N, int prec64, float *gamma_lane, float *gamma_pair, int *block_len);
 

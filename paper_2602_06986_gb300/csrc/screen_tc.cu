@@ -59,10 +59,14 @@ constexpr int WARPS = 2 + NGEN + 4;
 constexpr int THREADS = WARPS * 32;
 constexpr uint32_t kWait = 1u << 22;
 
-constexpr uint32_t ROWS_BYTES = ROWS * KC * 4;  // 3072
+// operand rows in shared memory are RSTR floats apart (16 bytes of padding
+// per 32-sample row, so that the 8 j-rows a warp reads start in different
+// bank groups)
+constexpr int RSTR = KC + 4;
+constexpr uint32_t ROWS_BYTES = ROWS * RSTR * 4;  // 3456
 constexpr uint32_t A_TILE = M * KC * 2;         // 8192 per slot per hi/lo
 constexpr uint32_t A_OFF = ROWS_BYTES;
-constexpr uint32_t B_OFF = A_OFF + 6 * A_TILE;  // 52224
+constexpr uint32_t B_OFF = A_OFF + 6 * A_TILE;  // 52608
 __host__ __device__ constexpr uint32_t b_bytes(int ntp) { return 2u * (uint32_t)ntp * KC * 2; }
 __host__ __device__ constexpr uint32_t stage_bytes(int ntp) { return B_OFF + b_bytes(ntp); }
 
@@ -130,9 +134,14 @@ struct Shared {
   uint64_t full_rows[NS], full_a[NS], empty[NS];
   uint64_t acc_full[2], acc_empty[2], gen_done[2], epi_free[2];
   uint64_t drain;  // last tcgen05.commit of the MMA issuer, before TMEM is freed
+  uint64_t rcp_ready[NS];  // every generation warp wrote its share of the stage's reciprocals
   uint32_t tmem_base;
   int abort;
   float hand[2][2][M][6];  // [tile parity][sample half][row][S1, S2 per slot]
+  __align__(16) float rcp[NS][ROWS * RSTR];  // reciprocals of each stage's operand rows (products/quotients)
+  float theta[4][64];        // each epilogue warp's copy of the pass's list thresholds
+  float ysum[4][64];         // and of the targets' sums
+  float sy[4][16][32];       // each epilogue warp's spill of 16 numerators for its rare full scores
 };
 
 constexpr size_t shared_bytes() { return (sizeof(Shared) + 1023) / 1024 * 1024; }
@@ -158,54 +167,102 @@ __global__ void k_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N
   }
 }
 
-// Epilogue of one candidate (row m, slot k) with its NTP numerators.
-template <int NTP>
-__device__ __forceinline__ uint64_t tc_candidate(const ScreenArgs &A, LaneStats &ls, bool pv, int64_t ia, int64_t ib,
-                                                 int opc, uint64_t pbase, const float4 &fa_a, const float4 &fa_b,
-                                                 float kk, float mi, float mj, float S1, float S2, const float *Sy,
-                                                 float gamma_gen, float gamma_num, const float *ysum) {
+// Epilogue of one candidate (row m, slot k), in two parts: the tests that
+// do not depend on the target (a-priori, realised; escalation) and the
+// target-independent terms of the score bound, then the targets 16 at a
+// time straight from the tensor memory (no per-thread array of NTP values).
+struct TcCand {
+  bool ok;
+  uint64_t gid;
+  CandInterval<float> ci;
+  float S1, a0, a1, a2, qlo;
+};
+
+__device__ __forceinline__ TcCand tc_prepare(const ScreenArgs &A, LaneStats &ls, bool pv, int64_t ia, int64_t ib,
+                                             int opc, uint64_t pbase, const float4 &fa_a, const float4 &fa_b,
+                                             float kk, float mi, float mj, float S1, float S2, float gamma_gen,
+                                             float gamma_num) {
+  TcCand o;
+  o.ok = false;
   const bool additive = opc == DSE_OP_ADD || opc == DSE_OP_SUB || opc == DSE_OP_ABSDIFF;
   const int pos = A.slot_pos[opc - 6];
-  const uint64_t gid = (uint64_t)A.n_stored + pbase + (uint64_t)(pos < 0 ? 0 : pos);
-  const bool cand = pv && pos >= 0 && gid >= A.id_begin && gid < A.id_end;
-  if (!cand) return 0;
+  o.gid = (uint64_t)A.n_stored + pbase + (uint64_t)(pos < 0 ? 0 : pos);
+  const bool cand = pv && pos >= 0 && o.gid >= A.id_begin && o.gid < A.id_end;
+  if (!cand) return o;
   if (additive) ls.seen++;
   EvalErr<float> ee{0.f, 0.f};
   const int reason = binary_apriori_W<float>(A, opc, ia, ib, fa_a, fa_b, kk, mi, mj, &ee);
   if (reason != DSE_VALID) {
     ls.r[reason]++;
-    return 0;
+    return o;
   }
   if (!((A.F.flags[ia] & A.F.flags[ib]) & F_FP32_SAFE)) {
-    escalate(A, gid);
+    escalate(A, o.gid);
     ls.escalated++;
-    return 0;
+    return o;
   }
   const float u = 5.9604644775390625e-8f;
   const float N = (float)A.N, invN = (float)A.invN, sqrtN = sqrtf(N);
   const float cshift = opc == DSE_OP_ADD ? mi + mj : opc == DSE_OP_SUB ? mi - mj : kk;
-  const CandInterval<float> ci =
-      cand_interval<float>(S1, S2, N, invN, sqrtN, cshift, ee, gamma_gen, u, (float)A.fmin_std_rel64);
-  if (ci.realised == 0) {
+  o.ci = cand_interval<float>(S1, S2, N, invN, sqrtN, cshift, ee, gamma_gen, u, (float)A.fmin_std_rel64);
+  if (o.ci.realised == 0) {
     ls.r[DSE_R_REALISED]++;
-    return 0;
+    return o;
   }
-  if (ci.realised == 2) {
-    escalate(A, gid);
+  if (o.ci.realised == 2) {
+    escalate(A, o.gid);
     ls.escalated++;
-    return 0;
+    return o;
   }
   ls.r[DSE_VALID]++;
   ls.evaluated++;
+  // The largest score the interval of target t can reach is
+  // rhi = (|P_t| a2 + a0 + a1 |ysum_t|) / q_lo (the terms of cand_score_num's
+  // numerator bound, split into what depends on the target and what does
+  // not); a candidate whose rhi is below the list's threshold (a lower bound
+  // of the final k-th lower bound) cannot be in the top k.
+  o.S1 = S1;
+  o.a0 = (gamma_num * o.ci.sqS2 * (1.0f + 2.0f * u) + o.ci.E * (1.0f + 2.0f * u) + 2.0f * u * o.ci.q_hi) * 1.01f;
+  o.a1 = fabsf(S1) * invN * (gamma_gen + 4.0f * u) * 1.01f;
+  o.a2 = 1.0f + u * 1.01f;
+  o.qlo = o.ci.q_lo * (1.0f - 8.0f * u);
+  o.ok = true;
+  return o;
+}
+
+// Targets t0 .. t0+15 of a prepared candidate; returns the lists pushed to.
+// The cheap bound is evaluated for all 16 without branches (independent
+// chains); the few survivors are scored in full from a per-lane copy of
+// their numerators in shared memory (sy: [16][32] of this warp).
+__device__ __forceinline__ uint64_t tc_targets16(const ScreenArgs &A, const TcCand &c, const float (&Sy)[16], int t0,
+                                                 float gamma_gen, float gamma_num, const float *ysum,
+                                                 const float *theta, float (*sy)[32]) {
+  const float u = 5.9604644775390625e-8f;
+  const float invN = (float)A.invN;
+  const int lane = threadIdx.x & 31;
+  unsigned mask = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int t = t0 + i;
+    const float ys = ysum[t];
+    const float aP = fabsf(fmaf(-c.S1, ys * invN, Sy[i]));
+    const float num = fmaf(aP, c.a2, fmaf(c.a1, fabsf(ys), c.a0)) * (1.0f + 8.0f * u);
+    const bool pass = t < A.T && !(c.qlo > 0.0f && num < theta[t] * c.qlo);
+    mask |= pass ? 1u << i : 0u;
+  }
+  if (!mask) return 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) sy[i][lane] = Sy[i];
   uint64_t pushed = 0;
-  for (int t = 0; t < NTP; ++t) {
-    if (t >= A.T) break;
-    // cheap upper bound first: s + eps <= (|P| + dP) / q_lo
-    const float th = ld_relaxed(&A.B.theta[A.t0 + t]);
+  while (mask) {
+    const int i = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const int t = t0 + i;
+    const float v = sy[i][lane];
     float s, e;
-    cand_score_num<float>(ci, S1, Sy[t], invN, ysum[t], gamma_gen, gamma_num, u, &s, &e);
-    if (s + e < th) continue;
-    if (push_one(A.B, A.t0 + t, gid, s, e * (1.0f + 2.4e-7f))) pushed |= 1ull << t;
+    cand_score_num<float>(c.ci, c.S1, v, invN, ysum[t], gamma_gen, gamma_num, u, &s, &e);
+    if (s + e < theta[t]) continue;
+    if (push_one(A.B, A.t0 + t, c.gid, s, e * (1.0f + 2.4e-7f))) pushed |= 1ull << t;
   }
   return pushed;
 }
@@ -241,6 +298,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       mbar_init(&sh.epi_free[b], 4);
     }
     mbar_init(&sh.drain, 1);
+    for (int s = 0; s < NS; ++s) mbar_init(&sh.rcp_ready[s], NGEN);
     sh.abort = 0;
     mbar_fence_init();
   }
@@ -277,46 +335,45 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      int lt = 0;
-      uint32_t issued = 0;  // chunks whose copies were issued
-      for (int tile = blockIdx.x; tile < A.n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
-        const Tile tl = A.tiles[tile];
-        int32_t ids[ROWS];
-        for (int r = 0; r < ROWS; ++r) {
-          int id = -1;
-          if (r < BI) {
-            if (r < tl.ni) id = A.rowid[tl.ibase + r];
-          } else if (r - BI < tl.nj) {
-            id = A.rowid[tl.jbase + r - BI];
-          }
-          ids[r] = id;
-        }
-        for (int c = 0; c < nchunks; ++c) {
-          const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
-          if (u >= 1 && !wait(&sh.empty[st], (u - 1) & 1)) break;
-          unsigned char *S = stages + (size_t)st * SB;
-          const int64_t s0 = (int64_t)c * KC;
-          int64_t cnt = A.F.ld - s0;
-          if (cnt > KC) cnt = KC;
-          const uint32_t rb = (uint32_t)cnt * 4u;
-          uint32_t bytes = b_bytes(NTP);
-          for (int r = 0; r < ROWS; ++r)
-            if (ids[r] >= 0) bytes += rb;
-          mbar_arrive_expect_tx(&sh.full_rows[st], bytes);
-          for (int r = 0; r < ROWS; ++r)
-            if (ids[r] >= 0) bulk_g2s(S + r * KC * 4, A.F.v32 + (int64_t)ids[r] * A.F.ld + s0, rb, &sh.full_rows[st]);
-          bulk_g2s(S + B_OFF, bsplit + (size_t)c * b_bytes(NTP), b_bytes(NTP), &sh.full_rows[st]);
-          issued = gc + 1;
-        }
+    // whole warp: lane r < 24 copies operand row r, lane 24 the target block
+    int lt = 0;
+    uint32_t issued = 0;  // chunks whose copies were issued
+    for (int tile = blockIdx.x; tile < A.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
+      const Tile tl = A.tiles[tile];
+      int id = -1;
+      if (lane < BI) {
+        if (lane < tl.ni) id = A.rowid[tl.ibase + lane];
+      } else if (lane < ROWS && lane - BI < tl.nj) {
+        id = A.rowid[tl.jbase + lane - BI];
       }
-      // no copy may still be landing when the CTA exits (normally these
-      // phases completed long ago and the waits return at once)
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c) {
+        const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
+        if (u >= 1 && !wait_warp(&sh.empty[st], (u - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        unsigned char *S = stages + (size_t)st * SB;
+        const int64_t s0 = (int64_t)c * KC;
+        int64_t cnt = A.F.ld - s0;
+        if (cnt > KC) cnt = KC;
+        const uint32_t rb = (uint32_t)cnt * 4u;
+        const unsigned bytes = __reduce_add_sync(0xffffffffu, id >= 0 ? rb : 0u) + b_bytes(NTP);
+        if (lane == 0) mbar_arrive_expect_tx(&sh.full_rows[st], bytes);
+        __syncwarp();
+        if (id >= 0) bulk_g2s(S + lane * RSTR * 4, A.F.v32 + (int64_t)id * A.F.ld + s0, rb, &sh.full_rows[st]);
+        if (lane == ROWS) bulk_g2s(S + B_OFF, bsplit + (size_t)c * b_bytes(NTP), b_bytes(NTP), &sh.full_rows[st]);
+        issued = gc + 1;
+      }
+      if (!ok) break;
+    }
+    // no copy may still be landing when the CTA exits (normally these
+    // phases completed long ago and the waits return at once)
+    if (lane == 0)
       for (uint32_t st = 0; st < (uint32_t)NS && st < issued; ++st) {
         const uint32_t last = (issued - 1 - st) / NS * NS + st;  // last use of stage st
         mbar_wait_bounded(&sh.full_rows[st], (last / NS) & 1, kWait);
       }
-    }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
     if (lane == 0) {
@@ -389,54 +446,79 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
           break;
         }
         unsigned char *S = stages + (size_t)st * SB;
-        const float *ra = reinterpret_cast<const float *>(S) + ti * KC;
-        const float *rb = reinterpret_cast<const float *>(S) + (BI + tj) * KC;
+        const float *rows = reinterpret_cast<const float *>(S);
+        if (KIND == KIND_MUL) {
+          // the reciprocals of the stage's 24 operand rows, computed once
+          // (each generation thread takes 3 of the 768) and shared by the
+          // 128 pairs; a bounded mbarrier wait orders them before use
+          float *rc = sh.rcp[st];
+          for (int e = gw * 32 + lane; e < ROWS * KC; e += NGEN * 32) {
+            const int r = e / KC, k = e % KC;
+            rc[r * RSTR + k] = rcp_approx(rows[r * RSTR + k]);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.rcp_ready[st]);
+          if (!wait_warp(&sh.rcp_ready[st], u & 1)) {
+            ok = false;
+            break;
+          }
+        }
+        const float *ra = rows + ti * RSTR, *rb = rows + (BI + tj) * RSTR;
+        const float *ria = sh.rcp[st] + ti * RSTR, *rib = sh.rcp[st] + (BI + tj) * RSTR;
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
           const int k0s = half * 16 + g * 8;
-          uint32_t hi[3][4], lo[3][4];
+          float av[8], bv[8], iav[8], ibv[8];
+          *reinterpret_cast<float4 *>(av) = *reinterpret_cast<const float4 *>(ra + k0s);
+          *reinterpret_cast<float4 *>(av + 4) = *reinterpret_cast<const float4 *>(ra + k0s + 4);
+          *reinterpret_cast<float4 *>(bv) = *reinterpret_cast<const float4 *>(rb + k0s);
+          *reinterpret_cast<float4 *>(bv + 4) = *reinterpret_cast<const float4 *>(rb + k0s + 4);
+          if (KIND == KIND_MUL) {
+            *reinterpret_cast<float4 *>(iav) = *reinterpret_cast<const float4 *>(ria + k0s);
+            *reinterpret_cast<float4 *>(iav + 4) = *reinterpret_cast<const float4 *>(ria + k0s + 4);
+            *reinterpret_cast<float4 *>(ibv) = *reinterpret_cast<const float4 *>(rib + k0s);
+            *reinterpret_cast<float4 *>(ibv + 4) = *reinterpret_cast<const float4 *>(rib + k0s + 4);
+          }
+          float wv[3][8];
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            float wv[2][3];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const int kk = k0s + e + q;
-              if (c * KC + kk < A.N) {
-                const float a = ra[kk], b = rb[kk];
-                if (KIND == KIND_MUL) {
-                  wv[q][0] = fmaf(a, b, -c0);
-                  wv[q][1] = fmaf(a, rcp_approx(b), -c1);
-                  wv[q][2] = fmaf(b, rcp_approx(a), -c2);
-                } else {
-                  const float ac = a - mi, bc = b - mj, d = a - b;
-                  wv[q][0] = ac + bc;
-                  wv[q][1] = ac - bc;
-                  wv[q][2] = fabsf(d) - c2;
-                }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                  t1[k] += wv[q][k];
-                  t2[k] = fmaf(wv[q][k], wv[q][k], t2[k]);
-                }
+          for (int e = 0; e < 8; ++e) {
+            if (c * KC + k0s + e < A.N) {
+              const float a = av[e], b = bv[e];
+              if (KIND == KIND_MUL) {
+                wv[0][e] = fmaf(a, b, -c0);
+                wv[1][e] = fmaf(a, ibv[e], -c1);
+                wv[2][e] = fmaf(b, iav[e], -c2);
               } else {
-                wv[q][0] = wv[q][1] = wv[q][2] = 0.f;
+                const float ac = a - mi, bc = b - mj, d = a - b;
+                wv[0][e] = ac + bc;
+                wv[1][e] = ac - bc;
+                wv[2][e] = fabsf(d) - c2;
               }
-            }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(wv[0][k]), h1 = __float2bfloat16_rn(wv[1][k]);
-              const __nv_bfloat16 l0 = __float2bfloat16_rn(wv[0][k] - __bfloat162float(h0));
-              const __nv_bfloat16 l1 = __float2bfloat16_rn(wv[1][k] - __bfloat162float(h1));
-              hi[k][e >> 1] = pack_bf16(h0, h1);
-              lo[k][e >> 1] = pack_bf16(l0, l1);
+              for (int k = 0; k < 3; ++k) {
+                t1[k] += wv[k][e];
+                t2[k] = fmaf(wv[k][e], wv[k][e], t2[k]);
+              }
+            } else {
+              wv[0][e] = wv[1][e] = wv[2][e] = 0.f;
             }
           }
+          // BF16 hi/lo splits of two values per conversion instruction
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(wv[k][e], wv[k][e + 1]);
+              const __nv_bfloat162 l =
+                  __floats2bfloat162_rn(wv[k][e] - __low2float(h), wv[k][e + 1] - __high2float(h));
+              hi[e >> 1] = *reinterpret_cast<const uint32_t *>(&h);
+              lo[e >> 1] = *reinterpret_cast<const uint32_t *>(&l);
+            }
             *reinterpret_cast<uint4 *>(S + A_OFF + (2 * k) * A_TILE + core_off(m, k0s)) =
-                make_uint4(hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
+                make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4 *>(S + A_OFF + (2 * k + 1) * A_TILE + core_off(m, k0s)) =
-                make_uint4(lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
+                make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
         }
         if (++blk == gen_blk) {
@@ -470,7 +552,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
     const int m = q * 32 + lane;
     const int ti = m >> 3, tj = m & 7;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const float *ysum = A.ysum32 + A.t0;  // read per target (L1-resident)
     LaneStats ls;
     ls.zero();
     int lt = 0;
@@ -531,6 +612,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       fence_after();
       const int p = lt & 1;
       if (!wait_warp(&sh.gen_done[p], (lt >> 1) & 1)) break;
+      // this warp's copy of the list thresholds (they only rise, so an older
+      // copy is still a valid lower bound)
+      for (int t = lane; t < NTP; t += 32) {
+        sh.theta[q][t] = t < A.T ? ld_relaxed(&A.B.theta[A.t0 + t]) : 0.f;
+        sh.ysum[q][t] = t < A.T ? A.ysum32[A.t0 + t] : 0.f;
+      }
+      __syncwarp();
       float st12[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) st12[i] = sh.hand[p][0][m][i] + sh.hand[p][1][m][i];
@@ -541,16 +629,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       for (int k = 0; k < 3; ++k) {
         const int opc = KIND == KIND_MUL ? (k == 0 ? DSE_OP_MUL : k == 1 ? DSE_OP_DIV : DSE_OP_RDIV)
                                          : (k == 0 ? DSE_OP_ADD : k == 1 ? DSE_OP_SUB : DSE_OP_ABSDIFF);
-        float Sy[NTP];
-        if (nblocks == 1) {
+        const TcCand tcc = tc_prepare(A, ls, pv, ia, ib, opc, pbase, fa_a, fa_b, kks[k], mi, mj, st12[2 * k],
+                                      st12[2 * k + 1], gamma_gen, gamma_num);
+#pragma unroll(NTP <= 32 ? 2 : 1)
+        for (int c16 = 0; c16 < NTP; c16 += 16) {
+          float v[16];
+          if (nblocks == 1) {
+            tmem_ld16(tmem + lane_base + (buf_last * 3 + k) * NTP + c16, v);  // whole warp
+          } else {
 #pragma unroll
-          for (int c16 = 0; c16 < NTP; c16 += 16) tmem_ld16(tmem + lane_base + (buf_last * 3 + k) * NTP + c16, Sy + c16);
-        } else {
-#pragma unroll
-          for (int t = 0; t < NTP; ++t) Sy[t] = NTP <= 32 ? acc[k][t < (NTP <= 32 ? NTP : 1) ? t : 0] : 0.f;
+            for (int i = 0; i < 16; ++i) v[i] = NTP <= 32 ? acc[k][(c16 + i) % (NTP <= 32 ? NTP : 1)] : 0.f;
+          }
+          if (tcc.ok) pushed |= tc_targets16(A, tcc, v, c16, gamma_gen, gamma_num, sh.ysum[q], sh.theta[q], sh.sy[q]);
         }
-        pushed |= tc_candidate<NTP>(A, ls, pv, ia, ib, opc, pbase, fa_a, fa_b, kks[k], mi, mj, st12[2 * k],
-                                    st12[2 * k + 1], Sy, gamma_gen, gamma_num, ysum);
       }
       if (nblocks == 1) {
         fence_before();

@@ -289,6 +289,60 @@ __global__ void __launch_bounds__(kRes) k_rescore(const SelectArgs S, const Scre
 // (FP64 compares are slow on this part).  Padding: key 0, id 2^64-1.
 __device__ __forceinline__ uint64_t score_key(double s) { return (uint64_t)__double_as_longlong(s); }
 
+// The same re-score with one warp per job (lanes over samples, shuffle
+// reductions, no block barriers): for short sample ranges, where a block per
+// job would spend its time in barriers and reductions.
+__global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const ScreenArgs A) {
+  const int lane = threadIdx.x & 31;
+  const unsigned nj = *S.n_jobs;
+  const unsigned warps = (gridDim.x * blockDim.x) >> 5;
+  const int64_t N = A.N;
+  for (unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nj; w += warps) {
+    const unsigned pos = S.job[w], l = S.job_list[w];
+    const size_t r = (size_t)l * S.B.cap + pos;
+    const uint64_t gid = S.r_id[r];
+    int op;
+    int64_t a, b;
+    if (gid < (uint64_t)A.n_stored) {
+      op = DSE_OP_PRIMARY;
+      a = (int64_t)gid;
+      b = -1;
+    } else {
+      decode_flat(A.G, gid - (uint64_t)A.n_stored, &op, &a, &b);
+    }
+    const double *xa = A.F.v64 + a * A.F.ld;
+    const double *xb = A.F.v64 + (b >= 0 ? b : a) * A.F.ld;
+    const int t_begin = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
+    const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < 16 ? A.T : 16) : 1;
+    const double c = eval_op64(op, xa[0], xb[0]);
+    double acc[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) acc[i] = 0.0;
+    for (int64_t s = lane; s < N; s += 32) {
+      const double v = eval_op64(op, xa[s], xb[s]) - c;
+      acc[0] += v;
+      acc[1] = fma(v, v, acc[1]);
+      for (int t = 0; t < nt; ++t) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
+    }
+    acc[0] = warp_sum64(acc[0]);
+    acc[1] = warp_sum64(acc[1]);
+    for (int t = 0; t < nt; ++t) acc[2 + t] = warp_sum64(acc[2 + t]);
+    if (lane == 0) {
+      const double mean = acc[0] / (double)N;
+      const double sxx = acc[1] - acc[0] * mean;
+      double agg = 0.0;
+      for (int t = 0; t < nt; ++t) {
+        const double sc = fabs(acc[2 + t]) / sqrt(sxx);
+        agg += sc * sc;
+      }
+      const double sc = A.mode == DSE_MODE_AGGREGATED ? sqrt(agg / (double)nt) : sqrt(agg);
+      S.r_s64[r] = sc;
+      S.r_e64[r] = (double)(N / 32 + 64) * 1.1102230246251565e-16 * 16.0 * (sc + 1e-3);
+      atomicAdd(&A.stats[ST_RESCORED], 1ull);
+    }
+  }
+}
+
 __device__ __forceinline__ bool before(uint64_t ka, uint64_t ia, uint64_t kb, uint64_t ib) {
   return ka > kb || (ka == kb && ia < ib);
 }
@@ -393,7 +447,10 @@ dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cuda
   k_sel_collect<<<g, 256, 0, st>>>(S);
   k_sel_exact<<<S.n_lists, 1024, 0, st>>>(S);
   k_sel_classify<<<g, 256, 0, st>>>(S);
-  k_rescore<<<sms * 8, kRes, 0, st>>>(S, A, batch);
+  if (!batch && A.N <= 4096)
+    k_rescore_warp<<<sms * 8, 256, 0, st>>>(S, A);
+  else
+    k_rescore<<<sms * 8, kRes, 0, st>>>(S, A, batch);
   static bool attr = false;
   if (!attr) {
     DSE_CUDA(cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -81,6 +81,11 @@ class LoopDesc(C.Structure):
                 ("precision", C.c_int32), ("flags", C.c_int32), ("stream", C.c_void_p)]
 
 
+class L0Desc(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("y_on_device", C.c_int32), ("dim", C.c_int32), ("ids", C.c_void_p),
+                ("n_ids", C.c_int64), ("ids_on_device", C.c_int32), ("n_top", C.c_int32), ("stream", C.c_void_p)]
+
+
 class LoopResult(C.Structure):
     _fields_ = [("chosen", C.c_uint64 * 4), ("rmse", C.c_double * 4), ("coefs", (C.c_double * 5) * 4),
                 ("stats", Stats * 4)]
@@ -88,7 +93,7 @@ class LoopResult(C.Structure):
 EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_counts", "dse_decode",
            "dse_expr_string", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
            "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
-           "dse_residual_loop", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error",
+           "dse_residual_loop", "dse_l0_search", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error",
            "dse_version"]
 
 _lib = None
@@ -121,6 +126,7 @@ def lib():
         L.dse_batch_free.argtypes = [vp]
         L.dse_batch_free.restype = None
         L.dse_residual_loop.argtypes = [vp, C.POINTER(LoopDesc), C.POINTER(LoopResult), vp, vp]
+        L.dse_l0_search.argtypes = [vp, C.POINTER(L0Desc), vp, vp, vp, C.POINTER(i32)]
         L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
         L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
         L.dse_last_error.restype = C.c_char_p
@@ -352,6 +358,27 @@ class Space:
                 "rmse": [float(out.rmse[i]) for i in range(n_iter)],
                 "coefs": [[float(out.coefs[i][c]) for c in range(i + 2)] for i in range(n_iter)],
                 "stats": [_stats_dict(out.stats[i]) for i in range(n_iter)]}
+
+    def l0_search(self, y, ids, dim, n_top=16, stream=None):
+        """Exhaustive L0 search over the listed candidates (dse_l0_search):
+        (positions int64[m, dim], RMSE[m], coefficients[m, dim+1]) of the m
+        best subsets by (RMSE, positions)."""
+        if isinstance(y, np.ndarray):
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        if isinstance(ids, np.ndarray):
+            ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        py, ydev = _ptr(y)
+        pi, idev = _ptr(ids)
+        n = len(ids) if isinstance(ids, np.ndarray) else ids.numel()
+        d = L0Desc(py, ydev, dim, pi, n, idev, n_top, stream)
+        pos = np.zeros((n_top, dim), np.int64)
+        rm = np.zeros(n_top)
+        cf = np.zeros((n_top, dim + 1))
+        nf = C.c_int32()
+        _check(lib().dse_l0_search(self._h, C.byref(d), pos.ctypes.data, rm.ctypes.data, cf.ctypes.data,
+                                   C.byref(nf)))
+        m = nf.value
+        return pos[:m].copy(), rm[:m].copy(), cf[:m].copy()
 
     def ls_refit(self, y, fixed, cand, residual=None, stream=None):
         """Best candidate for the next descriptor slot: (id, rmse, coefs, residual)."""

@@ -48,6 +48,7 @@ def test_struct_layouts_match_header(dse):
     assert C.sizeof(dse.BatchItem) == 8 + 8 + 4 * 2
     assert C.sizeof(dse.BatchDesc) == 8 + 4 * 2 + 8
     assert C.sizeof(dse.LoopDesc) == 8 + 4 * 2 + 8 + 4 * 2 + 8
+    assert C.sizeof(dse.L0Desc) == 8 + 4 * 2 + 8 + 8 + 4 * 2 + 8
     assert C.sizeof(dse.LoopResult) == 8 * 4 + 8 * 4 + 8 * 20 + 4 * C.sizeof(dse.Stats)
 
 
@@ -64,6 +65,7 @@ def test_version_and_null_arguments(dse):
     assert L.dse_batch_stats(None, 0, None) == dse.EINVAL
     L.dse_batch_free(None)
     assert L.dse_residual_loop(None, None, None, None, None) == dse.EINVAL
+    assert L.dse_l0_search(None, None, None, None, None, None) == dse.EINVAL
 
 
 def test_invalid_descriptor_rejected_before_device(dse):
