@@ -252,7 +252,9 @@ def bench_multi_target(args, which):
     _build.build()
     from paper_2602_06986_gb300 import dse
 
-    w = W.precision(0, n_targets=64) if which == "precision" else W.large(0, n_targets=16)
+    w = W.precision(0, n_targets=64) if which in ("precision", "tc_small") else W.large(0, n_targets=16)
+    if which == "tc_small":  # the precision primaries at rung 2: a small case of the same kernels
+        w = dict(w, max_rung=2, name="precision_primaries_rung2_T64_top1000")
     sp = dse.Space(torch.from_numpy(w["X"]).cuda(), w["units"], w["op_mask"], w["max_rung"],
                    unit_check_addsub=w["unit_check_addsub"], explog_dimensionless=w["explog_dimensionless"])
     Yd = torch.from_numpy(w["Y"]).cuda()
@@ -389,11 +391,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dse", choices=["dse", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "precision", "large", "l0"])
+    ap.add_argument("--workload", default="medium",
+                    choices=["medium", "batched", "precision", "large", "tc_small", "l0"])
     args = ap.parse_args()
     if args.workload == "batched":
         return bench_batched(args)
-    if args.workload in ("precision", "large"):
+    if args.workload in ("precision", "large", "tc_small"):
         return bench_multi_target(args, args.workload)
     if args.workload == "l0":
         return bench_l0(args)
