@@ -31,6 +31,8 @@ SQUARE, CUBE, INV, SQRT, EXP, LOG, ADD, SUB, MUL, DIV, RDIV, ABSDIFF = range(12)
 PRIMARY = 15
 OP_NAMES = ["sq", "cb", "inv", "sqrt", "exp", "log", "+", "-", "*", "a/b", "b/a", "|a-b|"]
 REASONS = ["valid", "unit", "complexity", "domain", "magnitude", "realised"]
+# reason 2 also counts candidates failing a variable-combination or
+# functional-form rule (the "form" reason: complexity cap or rule)
 
 
 def op_mask(*codes):
@@ -61,6 +63,7 @@ class _Params(C.Structure):
         ("op_mask", C.c_uint32), ("max_complexity", C.c_int32),
         ("unit_check_addsub", C.c_int32), ("explog_dimensionless", C.c_int32),
         ("fmax_max", C.c_double), ("fmin_std_rel", C.c_double),
+        ("pair_deny", C.POINTER(C.c_uint64)), ("op_deny", C.POINTER(C.c_uint64)),
     ]
 
 
@@ -98,6 +101,9 @@ def lib():
             L.orc_l0_search.argtypes = [vp, dp, C.POINTER(u64), i64, C.c_int, i64, C.POINTER(i64), dp,
                                         C.POINTER(i64)]
             L.orc_l0_search.restype = C.c_int
+            L.orc_screen_dedup.argtypes = [vp, dp, C.c_int, i64, C.c_int, C.c_double, u64, u64, C.POINTER(u64),
+                                           dp, C.POINTER(i64), C.POINTER(i64), dp]
+            L.orc_screen_dedup.restype = C.c_int
             _lib = L
     return _lib
 
@@ -120,16 +126,26 @@ class Space:
     """
 
     def __init__(self, X, units, op_mask, max_rung, max_complexity=0, unit_check_addsub=1,
-                 explog_dimensionless=1, fmax_max=1e15, fmin_std_rel=1e-8):
+                 explog_dimensionless=1, fmax_max=1e15, fmin_std_rel=1e-8, pair_deny=None, op_deny=None):
+        """``pair_deny`` (uint64 [n_primary]: bit q of row p forbids primaries
+        p and q in one expression) and ``op_deny`` (uint64 [12]: bit p of row o
+        forbids primary p below op o) are the optional user rules of R15."""
         L = lib()
         self.X = np.ascontiguousarray(X, dtype=np.float64)
         n_primary, n_samples = self.X.shape
         units = np.zeros((n_primary, 0), np.int32) if units is None else units
         self.units = np.ascontiguousarray(units, dtype=np.int32)
         assert self.units.shape[0] == n_primary
+        u64p = C.POINTER(C.c_uint64)
+        self._pd = None if pair_deny is None else np.ascontiguousarray(pair_deny, dtype=np.uint64)
+        self._od = None if op_deny is None else np.ascontiguousarray(op_deny, dtype=np.uint64)
+        assert self._pd is None or self._pd.shape == (n_primary,)
+        assert self._od is None or self._od.shape == (12,)
         p = _Params(n_samples, n_primary, self.units.shape[1], max_rung, _dptr(self.X),
                     self.units.ctypes.data_as(C.POINTER(C.c_int32)), op_mask, max_complexity,
-                    unit_check_addsub, explog_dimensionless, fmax_max, fmin_std_rel)
+                    unit_check_addsub, explog_dimensionless, fmax_max, fmin_std_rel,
+                    None if self._pd is None else self._pd.ctypes.data_as(u64p),
+                    None if self._od is None else self._od.ctypes.data_as(u64p))
         h = C.c_void_p()
         rc = L.orc_space_build(C.byref(p), C.byref(h))
         if rc != 0:
@@ -219,6 +235,31 @@ class Space:
             raise ValueError(f"orc_screen failed: {rc}")
         return ([ids[l, : n[l]].copy() for l in range(Lc)], [sc[l, : n[l]].copy() for l in range(Lc)],
                 {REASONS[i]: int(cnt[i]) for i in range(6)})
+
+    def screen_dedup(self, Y, k: int, tau: float = 1e-10, mode: str = "per_target", id_begin: int = 0,
+                     id_end=None):
+        """Top-k of the non-redundant candidates (R16).  Returns (ids per list,
+        scores per list, redundant entries passed over per list, smallest
+        correlation margin | (1 - |rho|) - tau |)."""
+        Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.float64)
+        T = Y.shape[0]
+        m = {"per_target": 0, "aggregated": 1}[mode]
+        Lc = T if m == 0 else 1
+        if id_end is None:
+            id_end = self.total_candidates
+        ids = np.zeros((Lc, k), np.uint64)
+        sc = np.zeros((Lc, k))
+        n = np.zeros(Lc, np.int64)
+        red = np.zeros(Lc, np.int64)
+        mg = C.c_double()
+        rc = lib().orc_screen_dedup(self._h, _dptr(Y), T, k, m, tau, id_begin, id_end,
+                                    ids.ctypes.data_as(C.POINTER(C.c_uint64)), _dptr(sc),
+                                    n.ctypes.data_as(C.POINTER(C.c_int64)), red.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    C.byref(mg))
+        if rc:
+            raise ValueError(f"orc_screen_dedup failed: {rc}")
+        return ([ids[l, : n[l]].copy() for l in range(Lc)], [sc[l, : n[l]].copy() for l in range(Lc)],
+                red.copy(), mg.value)
 
     def score_ids(self, Y, ids):
         """(scores [n, T] with NaN for invalid ids, reason codes [n])."""

@@ -64,6 +64,21 @@
  *       r_{D-1}; for each s in S_D not already chosen, least squares with
  *       intercept of y on [d_1..d_{D-1}, s] (Householder QR); d_D = the s with
  *       the smallest RMSE (ties: lower id); r_D = y - fit.
+ *   R15 User rules on variable combinations and functional forms ("Design
+ *       Philosophy and Constraints"), optional, for at most 64 primaries:
+ *       pair_deny[p] bit q (made symmetric) forbids primaries p and q in one
+ *       expression (p = q: p may occur as a leaf at most once); op_deny[o]
+ *       bit p forbids primary p anywhere below an application of op o.  A
+ *       failing candidate takes reason 2 (the "form" reason: complexity cap
+ *       or rule), tested after the complexity cap.  Primaries are named by
+ *       their input index.
+ *   R16 Redundancy: two valid candidates are equivalent when the FP64
+ *       Pearson correlation of their values has |rho| >= 1 - tau; a candidate
+ *       is redundant when an equivalent valid candidate with a smaller global
+ *       id exists.  The deduplicated SIS list is the top-k (R10) of the
+ *       non-redundant candidates.  Equivalent candidates' scores differ by at
+ *       most sqrt(2 tau) (unit vectors at distance sqrt(2(1-|rho|))), so the
+ *       search for an equivalent partner is confined to that score window.
  *
  * All arithmetic is IEEE FP64; compile with -ffp-contract=off so that no
  * multiply-add is fused.
@@ -101,6 +116,8 @@ typedef struct {
   int32_t explog_dimensionless;
   double fmax_max;
   double fmin_std_rel; /* < 0 disables the degeneracy test */
+  const uint64_t *pair_deny; /* R15, NULL or [n_primary] rows; n_primary <= 64 */
+  const uint64_t *op_deny;   /* R15, NULL or [12] rows */
 } orc_params;
 
 typedef struct {
@@ -120,6 +137,10 @@ typedef struct {
   int uops[6], nu;
   int bops[6], nb;
   double exp_arg_max;
+  int rules;          /* R15 active */
+  uint64_t deny[64];  /* symmetric pair rule, by primary input index */
+  uint64_t opdeny[12];
+  uint64_t *leaves;   /* [nfeat] set of primary input indices among the leaves */
 } orc_space;
 
 /* ---------------------------------------------------------------- sums */
@@ -172,6 +193,23 @@ static int realised_ok(const orc_space *S, const double *v) {
 
 static int is_unary(int op) { return op >= ORC_SQUARE && op <= ORC_LOG; }
 
+/* R15.  The operands satisfy the rules themselves (every stored feature
+   passed this test when it was generated), so only what the new node adds is
+   checked: a forbidden pair with one leaf in each operand (a leaf shared by
+   both operands occurs twice), and a forbidden leaf below op. */
+static int rule_fails(const orc_space *S, int op, int64_t a, int64_t b) {
+  const uint64_t la = S->leaves[a], lb = is_unary(op) ? 0 : S->leaves[b];
+  for (int p = 0; p < 64; ++p) {
+    if (!((la >> p) & 1)) continue;
+    for (int q = 0; q < 64; ++q)
+      if (((lb >> q) & 1) && ((S->deny[p] >> q) & 1)) return 1;
+  }
+  const uint64_t all = la | lb;
+  for (int p = 0; p < 64; ++p)
+    if (((all >> p) & 1) && ((S->opdeny[op] >> p) & 1)) return 1;
+  return 0;
+}
+
 /* R3-R6: a-priori tests of op(a[, b]).  Returns the reason code (0 = pass)
    and writes the result's unit vector and complexity. */
 static int apriori(const orc_space *S, int op, int64_t a, int64_t b, int64_t *u, int32_t *cx) {
@@ -212,6 +250,7 @@ static int apriori(const orc_space *S, int op, int64_t a, int64_t b, int64_t *u,
   int32_t c = S->cplx[a] + 1 + (is_unary(op) ? 0 : S->cplx[b]);
   *cx = c;
   if (S->P.max_complexity > 0 && c > S->P.max_complexity) return ORC_R_COMPLEXITY;
+  if (S->rules && rule_fails(S, op, a, b)) return ORC_R_COMPLEXITY;
 
   const double mna = S->vminabs[a], mxa = S->vmaxabs[a];
   switch (op) {
@@ -327,7 +366,7 @@ static int grow(orc_space *S, int64_t n) {
     S->ptr = (type *)q;                                                                 \
   } while (0)
   GROW(op, int32_t, 1); GROW(rung, int32_t, 1); GROW(cplx, int32_t, 1);
-  GROW(ca, int64_t, 1); GROW(cb, int64_t, 1);
+  GROW(ca, int64_t, 1); GROW(cb, int64_t, 1); GROW(leaves, uint64_t, 1);
   GROW(unit, int64_t, D);
   GROW(val, double, N);
   GROW(vmin, double, 1); GROW(vmax, double, 1); GROW(vminabs, double, 1); GROW(vmaxabs, double, 1);
@@ -343,7 +382,7 @@ static void set_summary(orc_space *S, int64_t f) {
 
 void orc_space_free(orc_space *S) {
   if (!S) return;
-  free(S->op); free(S->rung); free(S->cplx); free(S->ca); free(S->cb); free(S->unit);
+  free(S->op); free(S->rung); free(S->cplx); free(S->ca); free(S->cb); free(S->unit); free(S->leaves);
   free(S->val); free(S->vmin); free(S->vmax); free(S->vminabs); free(S->vmaxabs);
   free(S);
 }
@@ -356,7 +395,16 @@ int orc_space_build(const orc_params *P, orc_space **out) {
   orc_space *S = (orc_space *)calloc(1, sizeof(orc_space));
   if (!S) return -2;
   S->P = *P;
-  S->P.X = NULL; S->P.units = NULL;
+  S->P.X = NULL; S->P.units = NULL; S->P.pair_deny = NULL; S->P.op_deny = NULL;
+  if (P->pair_deny || P->op_deny) {
+    if (P->n_primary > 64) { free(S); return -1; }
+    S->rules = 1;
+    for (int64_t p = 0; p < P->n_primary; ++p)
+      for (int64_t q = 0; q < P->n_primary; ++q)
+        if (P->pair_deny && (((P->pair_deny[p] >> q) & 1) || ((P->pair_deny[q] >> p) & 1)))
+          S->deny[p] |= (uint64_t)1 << q;
+    for (int o = 0; o < 12; ++o) S->opdeny[o] = P->op_deny ? P->op_deny[o] : 0;
+  }
   S->N = P->n_samples;
   S->D = P->n_dims;
   S->exp_arg_max = log(P->fmax_max);
@@ -377,6 +425,7 @@ int orc_space_build(const orc_params *P, orc_space **out) {
     memcpy(S->val + nf * N, x, (size_t)N * sizeof(double));
     S->op[nf] = ORC_PRIMARY; S->rung[nf] = 0; S->cplx[nf] = 0;
     S->ca[nf] = p; S->cb[nf] = -1;
+    S->leaves[nf] = S->rules ? (uint64_t)1 << p : 0;
     for (int k = 0; k < S->D; ++k) S->unit[nf * S->D + k] = (int64_t)P->units[p * S->D + k] * scale;
     set_summary(S, nf);
     S->reasons[0][ORC_VALID]++;
@@ -416,6 +465,7 @@ int orc_space_build(const orc_params *P, orc_space **out) {
       const int64_t f = S->nfeat++;
       evaluate(S, op, a, b, S->val + f * N);
       S->op[f] = op; S->rung[f] = r; S->cplx[f] = cx; S->ca[f] = a; S->cb[f] = b;
+      S->leaves[f] = S->leaves[a] | (is_unary(op) ? 0 : S->leaves[b]);
       for (int k = 0; k < S->D; ++k) S->unit[f * S->D + k] = u[k];
       set_summary(S, f);
     }
@@ -739,6 +789,88 @@ int orc_score_ids(const orc_space *S, const double *Y, int T, const uint64_t *id
   }
   targets_free(&G);
   return err ? -1 : 0;
+}
+
+/* ------------------------------------------------- redundancy (R16) */
+
+/* FP64 Pearson correlation of two value vectors, two-pass with
+   Neumaier-compensated sums. */
+static double pearson(const double *a, const double *b, int64_t N) {
+  nsum sa = {0, 0}, sb = {0, 0};
+  for (int64_t s = 0; s < N; ++s) { nadd(&sa, a[s]); nadd(&sb, b[s]); }
+  const double ma = nval(&sa) / (double)N, mb = nval(&sb) / (double)N;
+  nsum qa = {0, 0}, qb = {0, 0}, c = {0, 0};
+  for (int64_t s = 0; s < N; ++s) {
+    const double da = a[s] - ma, db = b[s] - mb;
+    nadd(&qa, da * da);
+    nadd(&qb, db * db);
+    nadd(&c, da * db);
+  }
+  return nval(&c) / sqrt(nval(&qa) * nval(&qb));
+}
+
+/* R16.  orc_screen (mode 0 or 1) followed by redundancy removal: each list
+   holds the top-k of the non-redundant candidates of the screened range
+   (partners are sought in the same range).  The lists are screened with a
+   larger length kk and walked in rank order; an entry is decided only when
+   every candidate within sqrt(2 tau) of its score is in the list, else kk
+   doubles.  n_redundant (optional, per list) counts the redundant entries
+   passed over; margin (optional) gets min | (1 - |rho|) - tau | over the
+   correlations computed. */
+int orc_screen_dedup(const orc_space *S, const double *Y, int T, int64_t k, int mode, double tau,
+                     uint64_t id_begin, uint64_t id_end, uint64_t *out_ids, double *out_scores, int64_t *n_out,
+                     int64_t *n_redundant, double *margin) {
+  if (!(tau > 0) || !(tau < 1) || k < 1 || T < 1 || (mode != 0 && mode != 1) || id_begin > id_end) return -1;
+  const int L = mode == 0 ? T : 1;
+  const int64_t N = S->N;
+  const double w = sqrt(2.0 * tau) * (1.0 + 1e-9) + 1e-13;
+  const int64_t range = (int64_t)(id_end - id_begin);
+  int64_t kk = 4 * k;
+  double mg = INFINITY;
+  double *va = (double *)malloc((size_t)N * sizeof(double));
+  double *vb = (double *)malloc((size_t)N * sizeof(double));
+  int rc = 0;
+  for (;;) {
+    if (kk > range) kk = range > 0 ? range : 1;
+    uint64_t *ids = (uint64_t *)malloc((size_t)L * (size_t)kk * sizeof(uint64_t));
+    double *sc = (double *)malloc((size_t)L * (size_t)kk * sizeof(double));
+    int64_t *nl = (int64_t *)malloc((size_t)L * sizeof(int64_t));
+    rc = orc_screen(S, Y, T, kk, mode, id_begin, id_end, ids, sc, nl, NULL);
+    int undecided = 0;
+    for (int l = 0; l < L && rc == 0 && !undecided; ++l) {
+      const uint64_t *li = ids + (int64_t)l * kk;
+      const double *ls = sc + (int64_t)l * kk;
+      const int64_t n = nl[l];
+      const int full = (n == kk) && (kk < range);
+      int64_t kept = 0, red = 0;
+      for (int64_t i = 0; i < n && kept < k; ++i) {
+        if (full && !(ls[i] - w > ls[n - 1])) { undecided = 1; break; }
+        int redundant = 0;
+        for (int dir = -1; dir <= 1 && !redundant; dir += 2)
+          for (int64_t j = i + dir; j >= 0 && j < n && fabs(ls[j] - ls[i]) <= w; j += dir) {
+            if (li[j] >= li[i]) continue;
+            int32_t r1, r2;
+            if (orc_candidate(S, li[i], va, &r1) || orc_candidate(S, li[j], vb, &r2)) { rc = -3; break; }
+            const double rho = fabs(pearson(va, vb, N));
+            const double d = fabs((1.0 - rho) - tau);
+            if (d < mg) mg = d;
+            if (rho >= 1.0 - tau) { redundant = 1; break; }
+          }
+        if (redundant) { ++red; continue; }
+        out_ids[(int64_t)l * k + kept] = li[i];
+        out_scores[(int64_t)l * k + kept] = ls[i];
+        ++kept;
+      }
+      n_out[l] = kept;
+      if (n_redundant) n_redundant[l] = red;
+    }
+    free(ids); free(sc); free(nl);
+    if (rc || !undecided || kk >= range) break;
+    kk *= 2;
+  }
+  free(va); free(vb);
+  if (margin) *margin = mg;
+  return rc;
 }
 
 /* ------------------------------------------------------- residual loop */

@@ -459,3 +459,184 @@ def test_l0_search_special_cases():
     assert tuple(pos2[0]) == (a, b) or rm2[0] <= 1e-12 * np.std(yp)
     best = [S.l0_search(y0, ids, D, 1)[1][0] for D in (1, 2, 3)]
     assert best[2] <= best[1] <= best[0]
+
+
+# --------------------------------------------- user rules (variable combinations)
+
+def _rule_rows(n0, pairs, op_sets):
+    """uint64 rule rows; each pair is set in one direction only (the oracle
+    makes the relation symmetric)."""
+    pd = np.zeros(n0, np.uint64)
+    for pq in pairs:
+        p, q = (pq[0], pq[0]) if len(pq) == 1 else pq
+        pd[p] |= np.uint64(1 << q)
+    od = np.zeros(12, np.uint64)
+    for o, ps in op_sets.items():
+        for p in ps:
+            od[o] |= np.uint64(1 << p)
+    return pd, od
+
+
+@pytest.mark.parametrize("n0,rung,ops,dims,seed,pairs,op_sets", [
+    (4, 2, (ADD, SUB, MUL, DIV, SQUARE, SQRT, EXP), 1, 0, [(0, 1), (2,)], {EXP: {3}, MUL: {0}}),
+    (3, 3, (ADD, DIV, SQUARE), 1, 1, [(2, 0)], {SQUARE: {1}}),
+    (5, 2, (MUL, RDIV, ABSDIFF, INV, LOG), 2, 2, [(1,), (3,), (4, 0)], {ABSDIFF: {2}}),
+    (4, 2, (ADD, MUL, DIV, RDIV, CUBE), 0, 3, [(0,), (1,), (2,), (3,)], {}),
+])
+def test_rules_bruteforce(orc, n0, rung, ops, dims, seed, pairs, op_sets):
+    """Rule masks against explicit expression trees: every leaf and every
+    operator node of the whole tree is inspected (no incremental shortcut),
+    stored features and last-rung reasons must match."""
+    from oracle.bruteforce import RULE
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.5, 2.0, size=(n0, 6))
+    units = rng.integers(-1, 2, size=(n0, dims)).astype(np.int32) if dims else None
+    pd, od = _rule_rows(n0, pairs, op_sets)
+    S = unpruned_space(orc, X, ops, rung, units=units, unit_check_addsub=1, explog_dimensionless=1,
+                       pair_deny=pd, op_deny=od)
+    stored, last = enumerate_bruteforce(units if dims else np.zeros((n0, 0), np.int32), ops, rung, True, True,
+                                        pair_deny={frozenset(x) for x in pairs}, op_deny=op_sets)
+    assert [S.expr(i) for i in range(S.n_features)] == [e.text for e in stored]
+    n_rule = 0
+    for p, e in enumerate(last):
+        gid = S.n_features + p
+        why = S.candidate(gid)[1]
+        if e is None:
+            assert why == 1, (p, S.expr(gid))
+        elif e is RULE:
+            n_rule += 1
+            assert why == 2, (p, S.expr(gid), why)
+        else:
+            assert why in (0, 3), (p, e.text, why)
+            assert S.expr(gid) == e.text
+    assert n_rule > 0
+
+
+def test_rules_special_cases(orc):
+    """Closed forms: with every pair and every repeat forbidden no binary
+    candidate survives (rung 1: all nb*T(n0) binary slots fail the rule, the
+    unary ones all pass); forbidding every primary below sq removes exactly
+    the sq slots; no rule at all leaves the counts unchanged."""
+    rng = np.random.default_rng(7)
+    n0, N = 6, 10
+    X = rng.uniform(0.5, 2.0, size=(n0, N))
+    ops = (ADD, SUB, MUL, DIV, RDIV, SQUARE, SQRT)
+    allp = [(p, q) for p in range(n0) for q in range(p + 1)]
+    pd, od = _rule_rows(n0, allp, {})
+    S = unpruned_space(orc, X, ops, 1, pair_deny=pd, op_deny=od)
+    slots, r = S.rung_counts(1)
+    assert slots == 2 * n0 + 5 * n0 * (n0 - 1) // 2
+    assert r["complexity"] == 5 * n0 * (n0 - 1) // 2 and r["valid"] == 2 * n0
+    pd, od = _rule_rows(n0, [], {SQUARE: set(range(n0))})
+    S2 = unpruned_space(orc, X, ops, 2, pair_deny=pd, op_deny=od)
+    S0 = unpruned_space(orc, X, ops, 2)
+    s2, r2 = S2.rung_counts(1)
+    s0, r0 = S0.rung_counts(1)
+    assert s2 == s0 and r2["complexity"] == n0 and r2["valid"] == r0["valid"] - n0
+    pd, od = _rule_rows(n0, [], {})
+    S3 = unpruned_space(orc, X, ops, 2, pair_deny=pd, op_deny=od)
+    assert S3.rung_counts(2) == S0.rung_counts(2)
+
+
+# ------------------------------------------------ redundancy removal (R16)
+
+def _dedup_brute(orc_space, Y, tau):
+    """Every valid candidate, all pairwise correlations by one numpy matrix
+    product of centred unit vectors (no score window): (ids, scores,
+    redundant flags, smallest | (1 - |rho|) - tau |)."""
+    ids, vals = [], []
+    for g in range(orc_space.total_candidates):
+        v, why = orc_space.candidate(g)
+        if why == 0:
+            ids.append(g)
+            vals.append(v)
+    V = np.array(vals)
+    Z = V - V.mean(axis=1, keepdims=True)
+    Z /= np.linalg.norm(Z, axis=1, keepdims=True)
+    y = Y - Y.mean()
+    y /= np.linalg.norm(y)
+    scores = np.abs(Z @ y)
+    R = np.abs(Z @ Z.T)
+    low = np.tril(np.ones_like(R, dtype=bool), -1)  # d < c in id order
+    red = ((R >= 1.0 - tau) & low).any(axis=1)
+    margin = np.abs((1.0 - R[low]) - tau).min()
+    return np.array(ids, np.uint64), scores, red, margin
+
+
+@pytest.mark.parametrize("k", [10, 60, 5000])
+def test_dedup_brute_force(orc, k):
+    """The windowed, list-doubling redundancy removal equals the plain
+    definition evaluated over all pairs of valid candidates."""
+    rng = np.random.default_rng(11)
+    X = rng.uniform(0.5, 2.0, size=(3, 20))
+    y = X[0] * X[1] / X[2] + 0.3 * X[2] + rng.normal(0, 0.05, 20)
+    S = unpruned_space(orc, X, (ADD, SUB, MUL, DIV, RDIV, SQUARE, SQRT), 2)
+    tau = 1e-10
+    ids, scores, red, margin = _dedup_brute(S, y, tau)
+    assert margin > 1e-13
+    assert red.sum() > 50  # the op set makes many algebraic duplicates
+    keep = np.flatnonzero(~red)
+    order = sorted(keep, key=lambda i: (-scores[i], int(ids[i])))[:k]
+    want = ids[order]
+    got, gsc, nred, mg = S.screen_dedup(y, k, tau)
+    got = got[0]
+    assert len(got) == len(want) == min(k, len(keep))
+    sk = scores[order[-1]]
+    sure = [int(i) for i, s in zip(want, scores[order]) if s > sk + 1e-9]
+    assert [int(i) for i in got[: len(sure)]] == sure
+    assert set(map(int, got)) - set(map(int, want)) <= {int(i) for i, s in zip(ids, scores) if abs(s - sk) <= 1e-9}
+    np.testing.assert_allclose(gsc[0], scores[order], rtol=0, atol=1e-12)
+    assert mg > 1e-13
+
+
+def test_dedup_affine_primary_and_identity_group(orc):
+    """A primary that is an affine image of an earlier one (x1 = 3 x0 + 1) is
+    redundant, and so is x1 - x0 = 2 x0 + 1; the equivalent forms of a planted
+    rung-2 product collapse onto the smallest id among them."""
+    rng = np.random.default_rng(3)
+    x0 = rng.uniform(0.5, 2.0, 30)
+    X = np.stack([x0, 3 * x0 + 1, rng.uniform(0.5, 2.0, 30), rng.uniform(0.5, 2.0, 30)])
+    S = unpruned_space(orc, X, (ADD, SUB, MUL, DIV), 1)
+    y = x0 + rng.normal(0, 0.01, 30)
+    got = [S.expr(int(i)) for i in S.screen_dedup(y, 5)[0][0]]
+    assert got[0] == "x0" and "x1" not in got and "(x1-x0)" not in got
+    plain = [S.expr(int(i)) for i in S.screen(y, 5)[0][0]]
+    assert {"x0", "x1", "(x1-x0)"} <= set(plain)
+
+    Xb = rng.uniform(0.5, 2.0, size=(3, 25))
+    S2 = unpruned_space(orc, Xb, (MUL, DIV, RDIV), 2)
+    yb = Xb[0] * Xb[1] / Xb[2]
+    ids, sc, _ = S2.screen(yb, 40)
+    group = [int(i) for i, s in zip(ids[0], sc[0]) if s > 1 - 1e-12]
+    assert len(group) >= 3
+    d_ids, d_sc, nred, _ = S2.screen_dedup(yb, 5)
+    assert int(d_ids[0][0]) == min(group) and d_sc[0][1] < 1 - 1e-6
+    assert nred[0] >= len(group) - 1
+
+
+def test_dedup_near_equivalent_pair_uses_full_window(orc):
+    """A primary built at correlation 1 - 0.3 tau with an earlier one, against
+    a target that separates their scores by about sqrt(tau): redundant by the
+    definition, found only if the score window is as wide as sqrt(2 tau)."""
+    rng = np.random.default_rng(5)
+    N, tau = 40, 1e-10
+    x0 = rng.uniform(0.5, 2.0, N)
+    c0 = x0 - x0.mean()
+    u0 = c0 / np.linalg.norm(c0)
+    z = rng.normal(size=N)
+    z -= z.mean()
+    z -= (z @ u0) * u0
+    z /= np.linalg.norm(z)
+    eta = math.sqrt(2 * 0.3 * tau)
+    x1 = x0.mean() + np.linalg.norm(c0) * (u0 + eta * z)
+    X = np.stack([x0, rng.uniform(0.5, 2.0, N), x1])
+    y = 2.0 * c0 / np.linalg.norm(c0) + 1.5 * z + 0.2 * rng.normal(size=N)
+    S = unpruned_space(orc, X, (MUL,), 1)
+    ids, scores, red, margin = _dedup_brute(S, y, tau)
+    s0, s1 = scores[list(ids).index(0)], scores[list(ids).index(2)]
+    assert abs(s0 - s1) > 1e-7  # outside any narrow tie window
+    assert red[list(ids).index(2)] and margin > 1e-13
+    got = [int(i) for i in S.screen_dedup(y, 3, tau)[0][0]]
+    keep = np.flatnonzero(~red)
+    want = [int(ids[i]) for i in sorted(keep, key=lambda i: (-scores[i], int(ids[i])))[:3]]
+    assert got == want and 2 not in got
