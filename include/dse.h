@@ -83,7 +83,8 @@ enum {
 enum {
   DSE_VALID = 0,
   DSE_R_UNIT = 1,       /* unit rule of the op fails                        */
-  DSE_R_COMPLEXITY = 2, /* more operator nodes than max_complexity          */
+  DSE_R_COMPLEXITY = 2, /* form: more operator nodes than max_complexity, or
+                           a user rule (pair_deny / op_deny) fails          */
   DSE_R_DOMAIN = 3,     /* log/sqrt/inverse/divisor/exp domain from summaries */
   DSE_R_MAGNITUDE = 4,  /* a-priori bound on max|value| above fmax_max       */
   DSE_R_REALISED = 5    /* non-finite value or degenerate (std <= f * rms)   */
@@ -126,6 +127,18 @@ typedef struct {
   double fmax_max;              /* magnitude limit, finite and > 0 (1e15)     */
   double fmin_std_rel;          /* degeneracy limit (1e-8); < 0 disables       */
   void *stream;                 /* cudaStream_t                               */
+  /* Optional user rules on variable combinations and functional forms
+     ("Design Philosophy and Constraints"); either may be NULL; non-NULL
+     needs n_primary <= 64.  Primaries are named by their input index.
+     pair_deny: host [n_primary] rows; bit q of row p (or of row q, bit p)
+       forbids primaries p and q in one expression; bit p of row p lets p
+       occur as a leaf at most once.
+     op_deny: host [12] rows by op code; bit p of row o forbids primary p
+       anywhere below an application of op o.
+     A candidate failing a rule gets reason DSE_R_COMPLEXITY, tested after
+     the complexity cap; rung-0 primaries are never excluded by a rule. */
+  const uint64_t *pair_deny;
+  const uint64_t *op_deny;
 } dse_space_desc;
 
 dse_status dse_build_space(const dse_space_desc *desc, dse_space **out);
@@ -172,11 +185,26 @@ typedef struct {
   void *stream;          /* cudaStream_t                                    */
   int32_t flags;         /* DSE_FLAG_* bits                                 */
   int32_t reserved0;
+  double dedup_tau;      /* with DSE_FLAG_DEDUP: 0 < tau < 0.5 (0: 1e-10)   */
 } dse_screen_desc;
 
 /* dse_screen_desc.flags: record CUDA events around each kernel group so that
    dse_result_stats reports their device time (kernel_ms). */
 #define DSE_FLAG_TIMING 1
+/* Score-based redundancy removal ("Design Philosophy and Constraints": the
+   search space is reduced by rules; SISSO's convention of keeping one of
+   several interchangeable features).  Two valid candidates are equivalent
+   when the FP64 Pearson correlation of their values has |rho| >= 1 - tau
+   (then they are interchangeable in any linear model with intercept); a
+   candidate is redundant when an equivalent candidate of the screened range
+   has a smaller id.  Each list then holds the top-k of the non-redundant
+   candidates.  Equivalent candidates' scores differ by at most sqrt(2 tau),
+   so partners are sought only within that score window of a longer list
+   (4k entries, doubled until every decision is covered); an entry is
+   decided only when the list holds every candidate of its window.  The
+   call synchronises the stream (it reads the list state between rounds).
+   Not available in dse_residual_loop or the batched screens. */
+#define DSE_FLAG_DEDUP 2
 
 dse_status dse_sis_screen(dse_space *space, const dse_screen_desc *desc, dse_result **out);
 void dse_result_free(dse_result *result);
@@ -204,6 +232,10 @@ typedef struct {
                               stored/unary, product/quotient, sum/difference
                               and selection kernel groups; else 0          */
   int64_t kernel_launches; /* kernels this screen launched                   */
+  int64_t redundant;       /* DSE_FLAG_DEDUP: redundant entries passed over
+                              while filling the lists (all lists)           */
+  int32_t dedup_rounds;    /* DSE_FLAG_DEDUP: list lengths tried (0: off)    */
+  int32_t reserved1;
 } dse_stats;
 
 dse_status dse_result_stats(dse_result *result, dse_stats *out);

@@ -693,6 +693,51 @@ static dse_status finish(dse_result *R) {
 }
 
 
+// ------------------------------------------------- redundancy removal
+
+dse_status dedup_result(dse_result *R, int64_t k, double tau, bool full, bool *undecided, int64_t *n_redundant);
+
+// DSE_FLAG_DEDUP: screen for lists of kk = 4k entries, remove redundant
+// entries within the score window, and double kk while an entry's window
+// may reach past the end of its list.
+static dse_status dedup_screen(dse_space *sp, const dse_screen_desc *d, dse_result **out) {
+  const double tau = d->dedup_tau > 0.0 ? d->dedup_tau : 1e-10;
+  const uint64_t total = (uint64_t)sp->n + sp->geom.slots;
+  const uint64_t id_end = d->id_end ? d->id_end : total;
+  const uint64_t range = id_end > d->id_begin ? id_end - d->id_begin : 0;
+  const int64_t kmax = (int64_t)1 << 24;
+  int64_t kk = std::min<int64_t>(4 * d->k, kmax);
+  dse_screen_desc d2 = *d;
+  d2.flags &= ~DSE_FLAG_DEDUP;
+  for (int round = 1;; ++round) {
+    if ((uint64_t)kk > range) kk = (int64_t)std::max<uint64_t>(range, 1);
+    d2.k = kk;
+    dse_result *R = nullptr;
+    DSE_TRY(screen_impl(sp, &d2, &R));
+    dse_status s = finish(R);
+    bool undecided = false;
+    int64_t nred = 0;
+    const bool full = (uint64_t)kk < range;
+    if (s == DSE_OK) s = dedup_result(R, d->k, tau, full, &undecided, &nred);
+    if (s != DSE_OK) {
+      dse_result_free(R);
+      return s;
+    }
+    if (!undecided) {
+      R->host_stats.redundant = nred;
+      R->host_stats.dedup_rounds = round;
+      *out = R;
+      return DSE_OK;
+    }
+    dse_result_free(R);
+    if (kk >= kmax) {
+      set_error("redundancy removal needs lists longer than %lld", (long long)kmax);
+      return DSE_EOVERFLOW;
+    }
+    kk = std::min<int64_t>(2 * kk, kmax);
+  }
+}
+
 // ------------------------------------------------------ residual loop
 
 size_t refit_chain_bytes(int64_t N, int64_t cap);
@@ -902,6 +947,10 @@ dse_status dse_build_space(const dse_space_desc *d, dse_space **out) {
     set_error("invalid space descriptor");
     return DSE_EINVAL;
   }
+  if ((d->pair_deny || d->op_deny) && d->n_primary > 64) {
+    set_error("user rules need n_primary <= 64");
+    return DSE_EINVAL;
+  }
   if (d->sample_idx) {
     for (int64_t s = 0; s < d->n_samples; ++s)
       if (d->sample_idx[s] < 0 || d->sample_idx[s] >= d->ld_x) {
@@ -1029,8 +1078,13 @@ dse_status dse_sis_screen(dse_space *s, const dse_screen_desc *d, dse_result **o
     set_error("invalid screen descriptor");
     return DSE_EINVAL;
   }
+  if ((d->flags & DSE_FLAG_DEDUP) && !(d->dedup_tau == 0.0 || (d->dedup_tau > 0.0 && d->dedup_tau < 0.5))) {
+    set_error("dedup_tau outside (0, 0.5)");
+    return DSE_EINVAL;
+  }
   DSE_TRY(check_device());
   AllocStream as((cudaStream_t)d->stream);
+  if (d->flags & DSE_FLAG_DEDUP) return dedup_screen(s, d, out);
   return screen_impl(s, d, out);
 }
 
@@ -1038,6 +1092,7 @@ void dse_result_free(dse_result *r) {
   if (!r) return;
   AllocStream as(r->stream);  // the free is ordered after the result's work
   dfree(r->scratch);
+  dfree(r->extra);
   if (r->keep && r->keep_free) r->keep_free(r->keep);
   for (auto &t : r->timing) {
     cudaEventDestroy(t.second.first);

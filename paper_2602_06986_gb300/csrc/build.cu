@@ -193,7 +193,8 @@ __global__ void k_map_positions(uint64_t *pos, const uint64_t *list, uint64_t n_
 
 __device__ __forceinline__ void materialise_one(FeatTable F, RungGeom g, AprioriParams P, uint64_t slot, int64_t f,
                                                 double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
-                                                int32_t *cplx_out, int32_t *units_out, int lane) {
+                                                int32_t *cplx_out, int32_t *units_out, uint64_t *used_out,
+                                                uint64_t *dmask_out, int lane) {
   int op;
   int64_t a, b;
   decode_flat(g, slot, &op, &a, &b);
@@ -210,17 +211,22 @@ __device__ __forceinline__ void materialise_one(FeatTable F, RungGeom g, Apriori
     cb_out[f] = b;
     cplx_out[f] = cx;
     for (int d = 0; d < kMaxDims; ++d) units_out[f * kMaxDims + d] = u[d];
+    if (F.used) {
+      used_out[f] = F.used[a] | (b >= 0 ? F.used[b] : 0ull);
+      dmask_out[f] = F.dmask[a] | (b >= 0 ? F.dmask[b] : 0ull);
+    }
   }
 }
 
 // Store listed slots as new features [dst0, dst0 + n_list): warp per slot.
 __global__ void k_materialise(FeatTable F, RungGeom g, AprioriParams P, const uint64_t *list, uint64_t n_list,
                               int64_t dst0, double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
-                              int32_t *cplx_out, int32_t *units_out) {
+                              int32_t *cplx_out, int32_t *units_out, uint64_t *used_out, uint64_t *dmask_out) {
   int lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) / 32;
   for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_list; w += warps)
-    materialise_one(F, g, P, list[w], dst0 + (int64_t)w, v64, op_out, ca_out, cb_out, cplx_out, units_out, lane);
+    materialise_one(F, g, P, list[w], dst0 + (int64_t)w, v64, op_out, ca_out, cb_out, cplx_out, units_out, used_out,
+                    dmask_out, lane);
 }
 
 // FP32 rows and per-feature helpers of every stored feature.
@@ -292,15 +298,16 @@ struct TableArrays {
          *minabs64 = nullptr, *maxabs64 = nullptr, *minabsnz64 = nullptr;
   int32_t *op = nullptr, *cplx = nullptr, *units = nullptr;
   int64_t *ca = nullptr, *cb = nullptr;
+  uint64_t *used = nullptr, *dmask = nullptr;  // only with user rules
   int64_t cap = 0;
   void release() {
     dfree(v64); dfree(mean64); dfree(rmean64); dfree(min64); dfree(max64); dfree(minabs64); dfree(maxabs64);
-    dfree(minabsnz64); dfree(op); dfree(cplx); dfree(units); dfree(ca); dfree(cb);
+    dfree(minabsnz64); dfree(op); dfree(cplx); dfree(units); dfree(ca); dfree(cb); dfree(used); dfree(dmask);
     *this = TableArrays();
   }
 };
 
-static dse_status table_alloc(TableArrays &t, int64_t cap, int64_t ld) {
+static dse_status table_alloc(TableArrays &t, int64_t cap, int64_t ld, bool rules) {
   t.cap = cap;
   DSE_TRY(dalloc(&t.v64, (size_t)cap * ld, "FP64 feature rows"));
   DSE_TRY(dalloc(&t.mean64, cap, "summaries"));
@@ -315,6 +322,10 @@ static dse_status table_alloc(TableArrays &t, int64_t cap, int64_t ld) {
   DSE_TRY(dalloc(&t.units, (size_t)cap * kMaxDims, "table"));
   DSE_TRY(dalloc(&t.ca, cap, "table"));
   DSE_TRY(dalloc(&t.cb, cap, "table"));
+  if (rules) {
+    DSE_TRY(dalloc(&t.used, cap, "rule masks"));
+    DSE_TRY(dalloc(&t.dmask, cap, "rule masks"));
+  }
   return DSE_OK;
 }
 
@@ -337,12 +348,19 @@ static dse_status table_copy(TableArrays &dst, const TableArrays &src, int64_t n
   if (!e) e = cp(dst.units, src.units, 4 * n * kMaxDims);
   if (!e) e = cp(dst.ca, src.ca, 8 * n);
   if (!e) e = cp(dst.cb, src.cb, 8 * n);
+  if (!e && src.used) e = cp(dst.used, src.used, 8 * n);
+  if (!e && src.dmask) e = cp(dst.dmask, src.dmask, 8 * n);
   if (e) return cuda_status(e, "table copy");
   return DSE_OK;
 }
 
-static FeatTable view(const TableArrays &t, int64_t n, int64_t N, int64_t ld) {
+static FeatTable view(const TableArrays &t, int64_t n, int64_t N, int64_t ld, const uint64_t *op_deny) {
   FeatTable F{};
+  if (t.used) {
+    F.used = t.used;
+    F.dmask = t.dmask;
+    F.op_deny = op_deny;
+  }
   F.n = n;
   F.N = N;
   F.ld = ld;
@@ -398,6 +416,21 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   S->exp_arg_max = log(d->fmax_max);
   DSE_CUDA(cudaGetDevice(&S->device));
 
+  // user rules: the symmetric pair relation by primary, the op rows on the
+  // device (the space keeps them for the screens)
+  const bool rules = d->pair_deny || d->op_deny;
+  std::vector<uint64_t> deny_sym(rules ? n0 : 0, 0ull);
+  if (rules) {
+    for (int64_t p = 0; p < n0; ++p)
+      for (int64_t q = 0; q < n0; ++q)
+        if (d->pair_deny && (((d->pair_deny[p] >> q) & 1ull) || ((d->pair_deny[q] >> p) & 1ull)))
+          deny_sym[p] |= 1ull << q;
+    uint64_t od[12];
+    for (int o = 0; o < 12; ++o) od[o] = d->op_deny ? d->op_deny[o] : 0ull;
+    DSE_TRY(dalloc(&S->op_deny, 12, "op rules"));
+    DSE_CUDA(cudaMemcpyAsync(S->op_deny, od, sizeof(od), cudaMemcpyHostToDevice, st));
+  }
+
   AprioriParams P{S->D, S->unit_check_addsub, S->explog_dimensionless, S->max_complexity, S->fmax_max,
                   S->exp_arg_max};
 
@@ -416,7 +449,7 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     DSE_CUDA(cudaMemcpyAsync(idx_d, d->sample_idx, sizeof(int64_t) * N, cudaMemcpyHostToDevice, st));
   }
   TableArrays T0;
-  DSE_TRY(table_alloc(T0, n0, ld));
+  DSE_TRY(table_alloc(T0, n0, ld, false));
   k_gather_rows<<<grid_for(n0 * ld, 256), 256, 0, st>>>(Xd, ldx, idx_d, n0, N, ld, T0.v64);
   uint8_t *ok = nullptr;
   DSE_TRY(dalloc(&ok, n0, "primary flags"));
@@ -446,15 +479,20 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     return DSE_EINVAL;
   }
   TableArrays T;
-  DSE_TRY(table_alloc(T, nk, ld));
+  DSE_TRY(table_alloc(T, nk, ld, rules));
   {
     // host-assembled metadata of rung 0, rows copied device to device
     std::vector<int32_t> hop(nk, DSE_OP_PRIMARY), hcx(nk, 0), hun((size_t)nk * kMaxDims, 0);
     std::vector<int64_t> hca(nk), hcb(nk, -1);
+    std::vector<uint64_t> hused(rules ? nk : 0), hdmask(rules ? nk : 0);
     const int64_t scale = (int64_t)1 << d->max_rung;
     for (int64_t f = 0; f < nk; ++f) {
       int64_t p = keep[f];
       hca[f] = p;
+      if (rules) {
+        hused[f] = 1ull << p;
+        hdmask[f] = deny_sym[p];
+      }
       for (int k = 0; k < S->D; ++k) {
         int64_t u = (int64_t)d->units[p * S->D + k] * scale;
         if (u > 32767 || u < -32767) {
@@ -481,6 +519,10 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     DSE_CUDA(cudaMemcpyAsync(T.units, hun.data(), 4 * nk * kMaxDims, cudaMemcpyHostToDevice, st));
     DSE_CUDA(cudaMemcpyAsync(T.ca, hca.data(), 8 * nk, cudaMemcpyHostToDevice, st));
     DSE_CUDA(cudaMemcpyAsync(T.cb, hcb.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+    if (rules) {
+      DSE_CUDA(cudaMemcpyAsync(T.used, hused.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+      DSE_CUDA(cudaMemcpyAsync(T.dmask, hdmask.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+    }
     T0.release();
   }
   int64_t n = nk;
@@ -502,7 +544,7 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   // --- rungs 1 .. max_rung-1
   for (int r = 1; r < d->max_rung; ++r) {
     RungGeom g = make_geom(S, r);
-    FeatTable F = view(T, n, N, ld);
+    FeatTable F = view(T, n, N, ld, S->op_deny);
     S->slots[r] = g.slots;
     uint8_t *why = nullptr, *rw = nullptr;
     uint64_t *list = nullptr, *vlist = nullptr;
@@ -545,7 +587,7 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     S->have_counts[r] = true;
     // grow the table and append
     TableArrays T2;
-    dse_status s2 = table_alloc(T2, n + (int64_t)n_new, ld);
+    dse_status s2 = table_alloc(T2, n + (int64_t)n_new, ld, rules);
     if (s2 != DSE_OK) {
       dfree(vlist);
       dfree(meta);
@@ -553,10 +595,10 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
       return s2;
     }
     DSE_TRY(table_copy(T2, T, n, ld, st));
-    FeatTable Fold = view(T, n, N, ld);
+    FeatTable Fold = view(T, n, N, ld, S->op_deny);
     if (n_new)
       k_materialise<<<grid_for(n_new * 32, 256), 256, 0, st>>>(Fold, g, P, vlist, n_new, n, T2.v64, T2.op, T2.ca,
-                                                               T2.cb, T2.cplx, T2.units);
+                                                               T2.cb, T2.cplx, T2.units, T2.used, T2.dmask);
     if (n_new)
       k_summaries<<<grid_for(n_new * 32, 256), 256, 0, st>>>(T2.v64, ld, N, n, n + (int64_t)n_new, T2.mean64,
                                                              T2.rmean64, T2.min64, T2.max64, T2.minabs64, T2.maxabs64,
@@ -586,6 +628,8 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   S->units = T.units;
   S->ca = T.ca;
   S->cb = T.cb;
+  S->used = T.used;
+  S->dmask = T.dmask;
   DSE_TRY(dalloc(&S->v32, (size_t)n * ld, "FP32 feature rows"));
   DSE_TRY(dalloc(&S->fa, n, "helpers"));
   DSE_TRY(dalloc(&S->fr, n, "helpers"));
@@ -668,6 +712,7 @@ dse_status space_release(dse_space *S) {
   dfree(S->v64); dfree(S->v32); dfree(S->mean64); dfree(S->rmean64); dfree(S->min64); dfree(S->max64);
   dfree(S->minabs64); dfree(S->maxabs64); dfree(S->fa); dfree(S->fr); dfree(S->fnorm); dfree(S->flags); dfree(S->cplx);
   dfree(S->op); dfree(S->units); dfree(S->ca); dfree(S->cb); dfree(S->ukey); dfree(S->rowid_ident);
+  dfree(S->used); dfree(S->dmask); dfree(S->op_deny);
   dfree(S->class_rows);
   dfree(S->eq_pairs);
   delete S;
@@ -697,6 +742,11 @@ FeatTable table_of(const dse_space *S) {
   F.units = S->units;
   F.ukey = S->ukey;
   F.fnorm = S->fnorm;
+  if (S->used) {
+    F.used = S->used;
+    F.dmask = S->dmask;
+    F.op_deny = S->op_deny;
+  }
   return F;
 }
 

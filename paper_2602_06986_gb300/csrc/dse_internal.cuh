@@ -47,6 +47,10 @@ struct FeatTable {
   const int32_t *units;                      // [n][kMaxDims] scaled exponents
   const uint64_t *ukey;                      // [n][2] packed exponents (16 bits each)
   const float *fnorm;                        // RU(sqrt(sum_s x_s^2))
+  // user rules (all three nullptr when the space has none): used[f] = the
+  // primaries among f's leaves; dmask[f] = the primaries that may not meet
+  // any of them; op_deny[o] = the primaries forbidden below op o
+  const uint64_t *used, *dmask, *op_deny;
 };
 
 // Rung-k geometry: global id = n_stored + p.
@@ -297,6 +301,7 @@ struct dse_space {
   int32_t *cplx = nullptr, *op = nullptr, *units = nullptr;
   int64_t *ca = nullptr, *cb = nullptr;
   uint64_t *ukey = nullptr;
+  uint64_t *used = nullptr, *dmask = nullptr, *op_deny = nullptr;  // user rules (nullptr: none)
   int32_t *rowid_ident = nullptr;   // identity row list [0, n)
   // host copies for decoding
   std::vector<int32_t> h_op, h_rung, h_cplx;
@@ -338,6 +343,7 @@ struct dse_result {
   bool fetched = false;
   dse_stats host_stats{};
   void *scratch = nullptr;          // one allocation for buffers
+  void *extra = nullptr;            // deduplicated lists (out_* point into it)
   size_t scratch_bytes = 0;
   unsigned int *buf_count = nullptr;
   uint64_t add_total = 0;           // additive slots of the screened binary range

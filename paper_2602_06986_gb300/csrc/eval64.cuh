@@ -99,6 +99,38 @@ __device__ __forceinline__ int domain_magnitude64(int op, double mina, double ma
   return (B <= fmax) ? DSE_VALID : DSE_R_MAGNITUDE;
 }
 
+// FP64 value at sample s of the candidate with global id gid (a stored
+// feature for gid < n_stored, else flat slot gid - n_stored of the last rung).
+__device__ __forceinline__ double candidate_value64(const FeatTable &F, const RungGeom &G, int64_t n_stored,
+                                                   uint64_t gid, int64_t s) {
+  int op;
+  int64_t a, b;
+  if (gid < (uint64_t)n_stored) {
+    op = DSE_OP_PRIMARY;
+    a = (int64_t)gid;
+    b = -1;
+  } else {
+    decode_flat(G, gid - (uint64_t)n_stored, &op, &a, &b);
+  }
+  return eval_op64(op, F.v64[a * F.ld + s], b >= 0 ? F.v64[b * F.ld + s] : 0.0);
+}
+
+// User rules on the candidate op(a[, b]) (b < 0 for a unary op).  Both
+// operands satisfy the rules already, so only the new node is checked: a
+// forbidden pair with a leaf in each operand (dmask[a] is symmetric in the
+// relation) and a forbidden primary below op.
+__device__ __forceinline__ bool rule_fails(const FeatTable &F, int op, int64_t a, int64_t b) {
+  if (!F.used) return false;
+  uint64_t u = F.used[a];
+  bool bad = false;
+  if (b >= 0) {
+    const uint64_t ub = F.used[b];
+    bad = (F.dmask[a] & ub) != 0;
+    u |= ub;
+  }
+  return bad || (u & F.op_deny[op]) != 0;
+}
+
 // Full a-priori test of op(a[, b]) against the stored table.
 struct AprioriParams {
   int D, check_addsub, explog_dimless, max_complexity;
@@ -113,6 +145,7 @@ __device__ __forceinline__ int apriori64(const FeatTable &F, const AprioriParams
   int32_t c = F.cplx[a] + 1 + (b >= 0 ? F.cplx[b] : 0);
   *cx = c;
   if (P.max_complexity > 0 && c > P.max_complexity) return DSE_R_COMPLEXITY;
+  if (rule_fails(F, op, a, b)) return DSE_R_COMPLEXITY;
   return domain_magnitude64(op, F.min64[a], F.max64[a], F.minabs64[a], F.maxabs64[a],
                             b >= 0 ? F.minabs64[b] : 0.0, b >= 0 ? F.maxabs64[b] : 0.0, P.fmax, P.exp_arg_max);
 }

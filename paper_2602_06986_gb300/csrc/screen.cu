@@ -239,6 +239,8 @@ __device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, ui
       reason = DSE_R_UNIT;
     else if (A.max_complexity > 0 && A.F.cplx[f] + 1 > A.max_complexity)
       reason = DSE_R_COMPLEXITY;
+    else if (rule_fails(A.F, op, f, -1))
+      reason = DSE_R_COMPLEXITY;
     else {
       double ea = (op == DSE_OP_EXP && (A.F.flags[f] & F_EXP_MAG)) ? INFINITY : -INFINITY;
       reason = domain_magnitude64(op, A.F.min64[f], A.F.max64[f], A.F.minabs64[f], A.F.maxabs64[f], 0.0, 0.0,

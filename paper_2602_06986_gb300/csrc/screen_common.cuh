@@ -246,6 +246,8 @@ __device__ __forceinline__ int binary_apriori_W(const ScreenArgs &A, int opc, in
     reason = DSE_R_UNIT;
   else if (A.max_complexity > 0 && A.F.cplx[ia] + A.F.cplx[ib] + 1 > A.max_complexity)
     reason = DSE_R_COMPLEXITY;
+  else if (rule_fails(A.F, opc, ia, ib))
+    reason = DSE_R_COMPLEXITY;
   else if (opc == DSE_OP_DIV && !(A.F.flags[ib] & F_MINABS_POS))
     reason = DSE_R_DOMAIN;
   else if (opc == DSE_OP_RDIV && !(A.F.flags[ia] & F_MINABS_POS))

@@ -36,23 +36,26 @@ class SpaceDesc(C.Structure):
                 ("reserved0", C.c_int32), ("sample_idx", C.c_void_p), ("units", C.c_void_p),
                 ("op_mask", C.c_uint32), ("max_complexity", C.c_int32), ("unit_check_addsub", C.c_int32),
                 ("explog_dimensionless", C.c_int32), ("fmax_max", C.c_double), ("fmin_std_rel", C.c_double),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("pair_deny", C.c_void_p), ("op_deny", C.c_void_p)]
 
 
 class ScreenDesc(C.Structure):
     _fields_ = [("Y", C.c_void_p), ("ld_y", C.c_int64), ("y_on_device", C.c_int32), ("n_targets", C.c_int32),
                 ("k", C.c_int64), ("mode", C.c_int32), ("precision", C.c_int32), ("id_begin", C.c_uint64),
-                ("id_end", C.c_uint64), ("stream", C.c_void_p), ("flags", C.c_int32), ("reserved0", C.c_int32)]
+                ("id_end", C.c_uint64), ("stream", C.c_void_p), ("flags", C.c_int32), ("reserved0", C.c_int32),
+                ("dedup_tau", C.c_double)]
 
 
 FLAG_TIMING = 1
+FLAG_DEDUP = 2
 
 
 class Stats(C.Structure):
     _fields_ = [("screened", C.c_int64), ("reasons", C.c_int64 * 6), ("evaluated", C.c_int64),
                 ("buffered", C.c_int64), ("escalated", C.c_int64), ("rescored", C.c_int64),
                 ("reruns", C.c_int32), ("precision_used", C.c_int32), ("max_err_bound", C.c_double),
-                ("valid_by_group", C.c_int64 * 3), ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64)]
+                ("valid_by_group", C.c_int64 * 3), ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64),
+                ("redundant", C.c_int64), ("dedup_rounds", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class Expr(C.Structure):
@@ -207,7 +210,8 @@ def _stats_dict(s) -> dict:
                 "evaluated": s.evaluated, "buffered": s.buffered, "escalated": s.escalated,
                 "rescored": s.rescored, "reruns": s.reruns, "precision_used": s.precision_used,
                 "max_err_bound": s.max_err_bound, "valid_by_group": list(s.valid_by_group),
-            "kernel_ms": list(s.kernel_ms), "kernel_launches": s.kernel_launches}
+            "kernel_ms": list(s.kernel_ms), "kernel_launches": s.kernel_launches,
+            "redundant": s.redundant, "dedup_rounds": s.dedup_rounds}
 
 
 class Batch:
@@ -274,8 +278,20 @@ class Space:
     """A built feature space (device resident)."""
 
     def __init__(self, X, units, op_mask, max_rung, max_complexity=0, unit_check_addsub=1, explog_dimensionless=1,
-                 fmax_max=1e15, fmin_std_rel=1e-8, sample_idx=None, stream=None):
+                 fmax_max=1e15, fmin_std_rel=1e-8, sample_idx=None, stream=None, pair_deny=None, op_deny=None):
+        """pair_deny: uint64 [n_primary] rows (bit q of row p: primaries p and q
+        never in one expression; bit p of row p: p at most once); op_deny:
+        uint64 [12] rows by op code (bit p: primary p never below that op)."""
         self._keep = []
+        if pair_deny is not None:
+            pair_deny = np.ascontiguousarray(pair_deny, dtype=np.uint64)
+            if pair_deny.shape != (X.shape[0],):
+                raise ValueError("pair_deny must have one uint64 row per primary")
+        if op_deny is not None:
+            op_deny = np.ascontiguousarray(op_deny, dtype=np.uint64)
+            if op_deny.shape != (12,):
+                raise ValueError("op_deny must have 12 uint64 rows")
+        self._keep += [pair_deny, op_deny]
         if isinstance(X, np.ndarray):
             X = np.ascontiguousarray(X, dtype=np.float64)
         n_primary, ld = X.shape
@@ -290,7 +306,9 @@ class Space:
         d = SpaceDesc(n_samples, n_primary, units.shape[1], max_rung, px, ld, xdev, 0,
                       sample_idx.ctypes.data if sample_idx is not None else None,
                       units.ctypes.data if units.shape[1] else None, op_mask, max_complexity, unit_check_addsub,
-                      explog_dimensionless, fmax_max, fmin_std_rel, stream)
+                      explog_dimensionless, fmax_max, fmin_std_rel, stream,
+                      pair_deny.ctypes.data if pair_deny is not None else None,
+                      op_deny.ctypes.data if op_deny is not None else None)
         h = C.c_void_p()
         _check(lib().dse_build_space(C.byref(d), C.byref(h)))
         self._h = h
@@ -328,7 +346,11 @@ class Space:
         return buf.value.decode()
 
     def screen(self, Y, k, mode=MODE_PER_TARGET, precision=PREC_FP32, id_begin=0, id_end=0, stream=None,
-               flags=0) -> Result:
+               flags=0, dedup_tau=None) -> Result:
+        """SIS screen (dse_sis_screen).  With ``dedup_tau`` (0 < tau < 0.5) the
+        lists hold the top-k of the non-redundant candidates (DSE_FLAG_DEDUP)."""
+        if dedup_tau is not None:
+            flags |= FLAG_DEDUP
         if isinstance(Y, np.ndarray):
             Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.float64)
         elif Y.dim() == 1:
@@ -336,7 +358,8 @@ class Space:
         T, ldy = Y.shape
         py, ydev = _ptr(Y)
         self._ykeep = Y
-        d = ScreenDesc(py, ldy, ydev, T, k, mode, precision, id_begin, id_end, stream, flags, 0)
+        d = ScreenDesc(py, ldy, ydev, T, k, mode, precision, id_begin, id_end, stream, flags, 0,
+                       dedup_tau if dedup_tau is not None else 0.0)
         h = C.c_void_p()
         _check(lib().dse_sis_screen(self._h, C.byref(d), C.byref(h)))
         return Result(h, 1 if mode == MODE_AGGREGATED else T, k)
