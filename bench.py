@@ -185,7 +185,7 @@ def bench_batched(args):
     """The batched workload: 256 problems (32 base data sets x 5 CV folds + 3
     bootstrap resamples, N in [50, 5000], 10-30 primaries, rung 2, top-200
     each).  Spaces are built once (untimed); a step is one screen of every
-    problem with fresh targets: eager (plan reused, 9 kernels) and CUDA-graph
+    problem with fresh targets: eager (plan reused) and CUDA-graph
     replay, targets device resident."""
     import torch
 

@@ -256,7 +256,7 @@ dse_status dse_result_stats(dse_result *result, dse_stats *out);
    every buffer, allocated once) and enqueues the first screen on
    desc->stream.  dse_batch_rescreen screens again with new targets (same
    problems) without host-side planning or allocation; with DSE_BATCH_GRAPH
-   the whole screen (resets, 9 kernels) is captured once into a CUDA graph
+   the whole screen (resets and kernels) is captured once into a CUDA graph
    and replayed.  Results are read with dse_batch_fetch / dse_batch_stats,
    which synchronise; if a problem's candidate buffer overflowed, the batch
    is screened again (eagerly, thresholds kept) before they return.  The

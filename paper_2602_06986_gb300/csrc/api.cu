@@ -451,8 +451,6 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   unsigned *tile_ctr = nullptr;
   const int64_t cap = plan.cap;
   const int64_t T = d->n_targets;
-  int64_t sort_cap = 1;
-  while (sort_cap < cap) sort_cap <<= 1;
   if (launch && !d->y_on_device) sc.add(&Yd, (size_t)T * d->ld_y);
   sc.add(&R->y64, (size_t)T * R->ldy);
   sc.add(&R->y32, (size_t)T * R->ldy);
@@ -489,9 +487,8 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   sc.add(&R->out_eps, (size_t)n_lists * d->k);
   sc.add(&R->out_n, (size_t)n_lists);
   sc.add(&S.max_eps, (size_t)n_lists);
-  const bool big_sort = cap > 4096;
-  sc.add(&S.sort_key, big_sort ? (size_t)n_lists * sort_cap : 1);
-  sc.add(&S.sort_id, big_sort ? (size_t)n_lists * sort_cap : 1);
+  sc.add(&S.r_rank, (size_t)n_lists * cap);
+  sc.add(&S.r_key, (size_t)n_lists * cap);
   sc.add(&tmul, plan.mul_tiles.size());
   sc.add(&tadd, plan.add_tiles.size());
   sc.add(&tile_ctr, 2);
@@ -572,7 +569,6 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   S.out_eps = R->out_eps;
   S.out_n = R->out_n;
   R->max_eps = S.max_eps;
-  S.sort_cap = big_sort ? sort_cap : 1;
   S.stats = R->stats;
 
   if (launch) {

@@ -11,7 +11,7 @@
 // problem each -- runs of stored/unary candidates, pair tiles, runs of the
 // concatenated equal-unit pair lists -- whose sizes follow the problem's
 // sample count, and warps/CTAs take them from device counters.  A re-screen
-// with new targets is a fixed sequence of resets and 9 kernels with no host
+// with new targets is a fixed sequence of resets and kernels with no host
 // work, which the library can capture once into a CUDA graph and replay.
 #include <math.h>
 #include <string.h>
@@ -317,9 +317,6 @@ dse_status plan(const dse_batch_item *items, int32_t n, const dse_batch_desc *d,
 
   // buffers
   const int64_t cap = std::max<int64_t>(8 * k, k + 32768);
-  int64_t sort_cap = 1;
-  while (sort_cap < cap) sort_cap <<= 1;
-  const bool big_sort = cap > 4096;
   const int64_t esc_cap = 1 << 20;
   SelectArgs &S = b->S;
   CandBufs &B = b->B;
@@ -372,8 +369,8 @@ dse_status plan(const dse_batch_item *items, int32_t n, const dse_batch_desc *d,
   sc.add(&b->out_eps, (size_t)n * k);
   sc.add(&b->out_n, (size_t)n);
   sc.add(&S.max_eps, (size_t)n);
-  sc.add(&S.sort_key, big_sort ? (size_t)n * sort_cap : 1);
-  sc.add(&S.sort_id, big_sort ? (size_t)n * sort_cap : 1);
+  sc.add(&S.r_rank, (size_t)n * cap);
+  sc.add(&S.r_key, (size_t)n * cap);
   DSE_TRY(sc.alloc(&b->scratch, &b->scratch_bytes));
   B.cap = cap;
 
@@ -461,7 +458,6 @@ dse_status plan(const dse_batch_item *items, int32_t n, const dse_batch_desc *d,
   S.out_score = b->out_score;
   S.out_eps = b->out_eps;
   S.out_n = b->out_n;
-  S.sort_cap = big_sort ? sort_cap : 1;
   S.stats = b->stats;
 
   // uploads (pageable host memory: the copies complete before the call returns)

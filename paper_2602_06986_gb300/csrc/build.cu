@@ -34,51 +34,114 @@ __global__ void k_gather_rows(const double *X, int64_t ldx, const int64_t *idx, 
   }
 }
 
-__device__ __forceinline__ void summary_one(double *v64, int64_t ld, int64_t N, int64_t f, int64_t f0,
-                                            double *mean64, double *rmean64, double *min64, double *max64,
-                                            double *minabs64, double *maxabs64, double *minabsnz64,
-                                            double fmin_std_rel, uint8_t *ok, int lane) {
+// Order-preserving integer images of doubles (not NaN): signed for values,
+// unsigned magnitude bits for absolute values.  Minima and maxima are taken
+// on the integer pipe: on this part FP64 instructions issue at a small
+// fraction of the integer rate, and the results are the same doubles.
+__device__ __forceinline__ long long ord_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double ord_val(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFll));
+}
+
+constexpr int kSumThreads = 128;
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce_sum(T v, T *sm, Op op) {
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  T t = sm[0];
+  for (int i = 1; i < kSumThreads / 32; ++i) t = op(t, sm[i]);
+  return t;
+}
+
+// Summaries of stored rows [f0, f1) (only the first *n_dev of them when n_dev
+// is given): one block of kSumThreads per row.
+// min, max, min|x|, max|x| and the smallest non-zero |x| on integer images;
+// the FP64 sum for the mean, then the centred sum of squares and the sum of
+// squares for the realised test (finite, std > fmin * rms) into ok[f - f0]
+// when ok != nullptr.  rmean (the mean of 1/x, 0 if min|x| == 0) is only a
+// shift constant of the quotient kernels, so it is accumulated in FP32
+// (FP64 when a reciprocal leaves the FP32 range).
+__global__ void __launch_bounds__(kSumThreads) k_summaries(double *v64, int64_t ld, int64_t N, int64_t f0,
+                                                           int64_t f1, double *mean64, double *rmean64, double *min64,
+                                                           double *max64, double *minabs64, double *maxabs64,
+                                                           double *minabsnz64, double fmin_std_rel, uint8_t *ok,
+                                                           const unsigned long long *n_dev) {
+  __shared__ long long smi[kSumThreads / 32];
+  __shared__ double smd[kSumThreads / 32];
+  const int64_t f = f0 + blockIdx.x;
+  if (f >= f1 || (n_dev && (unsigned long long)(f - f0) >= *n_dev)) return;
   const double *x = v64 + f * ld;
-  double mn = INFINITY, mx = -INFINITY, mna = INFINITY, mxa = 0.0, mnz = INFINITY, sum = 0.0;
+  long long kmn = 0x7FFFFFFFFFFFFFFFll, kmx = (long long)0x8000000000000000ull;
+  unsigned long long amn = ~0ull, amx = 0ull, anz = ~0ull;
   int fin = 1;
-  for (int64_t s = lane; s < N; s += 32) {
-    double v = x[s];
-    if (!isfinite(v)) fin = 0;
-    mn = fmin(mn, v);
-    mx = fmax(mx, v);
-    double a = fabs(v);
-    mna = fmin(mna, a);
-    mxa = fmax(mxa, a);
-    if (a > 0.0) mnz = fmin(mnz, a);
+  double sum = 0.0;
+  for (int64_t s = threadIdx.x; s < N; s += kSumThreads) {
+    const double v = x[s];
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+    fin &= a < 0x7FF0000000000000ull;
+    const long long k = ord_key(v);
+    kmn = k < kmn ? k : kmn;
+    kmx = k > kmx ? k : kmx;
+    amn = a < amn ? a : amn;
+    amx = a > amx ? a : amx;
+    if (a != 0ull) anz = a < anz ? a : anz;
     sum = __dadd_rn(sum, v);
   }
-  fin = !__any_sync(0xffffffffu, !fin);
-  mn = warp_min64(mn);
-  mx = warp_max64(mx);
-  mna = warp_min64(mna);
-  mxa = warp_max64(mxa);
-  mnz = warp_min64(mnz);
-  sum = warp_sum64(sum);
-  double mean = sum / (double)N;
-  double sxx = 0.0, s2 = 0.0, rs = 0.0;
-  for (int64_t s = lane; s < N; s += 32) {
-    double v = x[s];
-    double d = __dsub_rn(v, mean);
+  auto mn_ll = [](long long p, long long q) { return p < q ? p : q; };
+  auto mx_ll = [](long long p, long long q) { return p > q ? p : q; };
+  kmn = block_reduce_sum(kmn, smi, mn_ll);
+  kmx = block_reduce_sum(kmx, smi, mx_ll);
+  amn = (unsigned long long)block_reduce_sum((long long)amn, smi,
+                                             [](long long p, long long q) {
+                                               return (unsigned long long)p < (unsigned long long)q ? p : q;
+                                             });
+  amx = (unsigned long long)block_reduce_sum((long long)amx, smi, mx_ll);
+  anz = (unsigned long long)block_reduce_sum((long long)anz, smi,
+                                             [](long long p, long long q) {
+                                               return (unsigned long long)p < (unsigned long long)q ? p : q;
+                                             });
+  fin = __syncthreads_and(fin);
+  sum = block_reduce_sum(sum, smd, [](double p, double q) { return p + q; });
+  const double mean = sum / (double)N;
+  const double mna = __longlong_as_double((long long)amn);
+  double sxx = 0.0, s2 = 0.0;
+  float rs = 0.f;
+  for (int64_t s = threadIdx.x; s < N; s += kSumThreads) {
+    const double v = x[s];
+    const double d = __dsub_rn(v, mean);
     sxx = __fma_rn(d, d, sxx);
     s2 = __fma_rn(v, v, s2);
-    if (mna > 0.0) rs = __dadd_rn(rs, __drcp_rn(v));
+    if (mna > 0.0) rs += __frcp_rn(__double2float_rn(v));
   }
-  sxx = warp_sum64(sxx);
-  s2 = warp_sum64(s2);
-  rs = warp_sum64(rs);
-  if (lane == 0) {
+  sxx = block_reduce_sum(sxx, smd, [](double p, double q) { return p + q; });
+  s2 = block_reduce_sum(s2, smd, [](double p, double q) { return p + q; });
+  rs = block_reduce_sum(rs, reinterpret_cast<float *>(smd), [](float p, float q) { return p + q; });
+  double rmean = 0.0;
+  if (mna > 0.0) {
+    rmean = (double)rs / (double)N;
+    if (!isfinite(rmean)) {
+      // a reciprocal outside the FP32 range: the FP64 mean of 1/x
+      double r64 = 0.0;
+      for (int64_t s = threadIdx.x; s < N; s += kSumThreads) r64 = __dadd_rn(r64, __drcp_rn(x[s]));
+      rmean = block_reduce_sum(r64, smd, [](double p, double q) { return p + q; }) / (double)N;
+    }
+  }
+  if (threadIdx.x == 0) {
     mean64[f] = mean;
-    rmean64[f] = (mna > 0.0) ? rs / (double)N : 0.0;
-    min64[f] = mn;
-    max64[f] = mx;
+    rmean64[f] = rmean;
+    min64[f] = ord_val(kmn);
+    max64[f] = ord_val(kmx);
     minabs64[f] = mna;
-    maxabs64[f] = mxa;
-    minabsnz64[f] = mnz;
+    maxabs64[f] = __longlong_as_double((long long)amx);
+    minabsnz64[f] = anz == ~0ull ? INFINITY : __longlong_as_double((long long)anz);
     if (ok) {
       int good = fin;
       if (good && fmin_std_rel >= 0.0) {
@@ -90,16 +153,65 @@ __device__ __forceinline__ void summary_one(double *v64, int64_t ld, int64_t N, 
   }
 }
 
-// Summaries of stored rows [f0, f1): one warp per row.  Also the realised test
-// (finite, std > fmin * rms) into ok[f - f0] when ok != nullptr.
-__global__ void k_summaries(double *v64, int64_t ld, int64_t N, int64_t f0, int64_t f1, double *mean64,
-                            double *rmean64, double *min64, double *max64, double *minabs64, double *maxabs64,
-                            double *minabsnz64, double fmin_std_rel, uint8_t *ok) {
-  int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
-  for (int64_t f = f0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; f < f1; f += warps)
-    summary_one(v64, ld, N, f, f0, mean64, rmean64, min64, max64, minabs64, maxabs64, minabsnz64, fmin_std_rel, ok,
-                lane);
+// FP64 values of the listed slots (the first *n_dev of at most cap) into
+// scratch rows: one block per slot, one evaluation per sample.
+__global__ void __launch_bounds__(kSumThreads) k_eval_rows(FeatTable F, RungGeom g, const uint64_t *list, uint64_t cap,
+                                                           const unsigned long long *n_dev, double *rows) {
+  const uint64_t w = blockIdx.x;
+  if (w >= cap || w >= *n_dev) return;
+  int op;
+  int64_t a, b;
+  decode_flat(g, list[w], &op, &a, &b);
+  const double *xa = F.v64 + a * F.ld;
+  const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
+  double *out = rows + w * F.ld;
+  for (int64_t s = threadIdx.x; s < F.ld; s += kSumThreads) out[s] = s < F.N ? eval_op64(op, xa[s], xb[s]) : 0.0;
+}
+
+// Scratch summaries of one evaluated rung (per scratch row).
+struct RowSummaries {
+  double *mean64, *rmean64, *min64, *max64, *minabs64, *maxabs64, *minabsnz64;
+};
+
+// Kept rows: scratch row pos[w] (slot list[pos[w]]) becomes stored feature
+// dst0 + w: values, summaries and the metadata of its expression (op,
+// operands, complexity, units, rule masks).  One block per kept row.
+__global__ void __launch_bounds__(kSumThreads) k_take_eval(FeatTable F, RungGeom g, AprioriParams P,
+                                                           const uint64_t *list, const uint64_t *pos, uint64_t n_keep,
+                                                           int64_t dst0, const double *rows, RowSummaries src,
+                                                           double *v64, RowSummaries dst, int32_t *op_out,
+                                                           int64_t *ca_out, int64_t *cb_out, int32_t *cplx_out,
+                                                           int32_t *units_out, uint64_t *used_out,
+                                                           uint64_t *dmask_out) {
+  const uint64_t w = blockIdx.x;
+  if (w >= n_keep) return;
+  const uint64_t p = pos[w];
+  const int64_t f = dst0 + (int64_t)w;
+  for (int64_t s = threadIdx.x; s < F.ld; s += kSumThreads) v64[f * F.ld + s] = rows[p * F.ld + s];
+  if (threadIdx.x == 0) {
+    dst.mean64[f] = src.mean64[p];
+    dst.rmean64[f] = src.rmean64[p];
+    dst.min64[f] = src.min64[p];
+    dst.max64[f] = src.max64[p];
+    dst.minabs64[f] = src.minabs64[p];
+    dst.maxabs64[f] = src.maxabs64[p];
+    dst.minabsnz64[f] = src.minabsnz64[p];
+    int op;
+    int64_t a, b;
+    decode_flat(g, list[p], &op, &a, &b);
+    int32_t u[kMaxDims] = {0, 0, 0, 0, 0, 0, 0, 0}, cx = 0;
+    int bad = 0;
+    apriori64(F, P, op, a, b, u, &cx, &bad);
+    op_out[f] = op;
+    ca_out[f] = a;
+    cb_out[f] = b;
+    cplx_out[f] = cx;
+    for (int d = 0; d < kMaxDims; ++d) units_out[f * kMaxDims + d] = u[d];
+    if (F.used) {
+      used_out[f] = F.used[a] | (b >= 0 ? F.used[b] : 0ull);
+      dmask_out[f] = F.dmask[a] | (b >= 0 ? F.dmask[b] : 0ull);
+    }
+  }
 }
 
 // A-priori reason of every flat slot of rung r.
@@ -115,50 +227,6 @@ __global__ void k_apriori_rung(FeatTable F, RungGeom g, AprioriParams P, uint8_t
     if (b_) atomicOr(bad, b_);
     why[p] = (uint8_t)r;
   }
-}
-
-__device__ __forceinline__ void realised_one(FeatTable F, RungGeom g, uint64_t slot, double fmin_std_rel,
-                                             uint8_t *why, int lane) {
-  int op;
-  int64_t a, b;
-  decode_flat(g, slot, &op, &a, &b);
-  const double *xa = F.v64 + a * F.ld;
-  const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
-  const int64_t N = F.N;
-  int fin = 1;
-  double sum = 0.0;
-  for (int64_t s = lane; s < N; s += 32) {
-    double v = eval_op64(op, xa[s], xb[s]);
-    if (!isfinite(v)) fin = 0;
-    sum = __dadd_rn(sum, v);
-  }
-  fin = !__any_sync(0xffffffffu, !fin);
-  sum = warp_sum64(sum);
-  double mean = sum / (double)N, sxx = 0.0, s2 = 0.0;
-  for (int64_t s = lane; s < N; s += 32) {
-    double v = eval_op64(op, xa[s], xb[s]);
-    double d = __dsub_rn(v, mean);
-    sxx = __fma_rn(d, d, sxx);
-    s2 = __fma_rn(v, v, s2);
-  }
-  sxx = warp_sum64(sxx);
-  s2 = warp_sum64(s2);
-  if (lane == 0) {
-    int good = fin;
-    if (good && fmin_std_rel >= 0.0) good = __dsqrt_rn(sxx / (double)N) > fmin_std_rel * __dsqrt_rn(s2 / (double)N);
-    *why = (uint8_t)(good ? DSE_VALID : DSE_R_REALISED);
-  }
-}
-
-// Realised test of listed slots (FP64 values, not stored): warp per slot;
-// the list length is *n_dev (at most n_cap).
-__global__ void k_realised_rung(FeatTable F, RungGeom g, const uint64_t *list, uint64_t n_cap,
-                                const unsigned long long *n_dev, double fmin_std_rel, uint8_t *why) {
-  int lane = threadIdx.x & 31;
-  const uint64_t n_list = min((uint64_t)*n_dev, n_cap);
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) / 32;
-  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_list; w += warps)
-    realised_one(F, g, list[w], fmin_std_rel, why + w, lane);
 }
 
 // Rows keep[0..nk) of a table into rows 0..nk of another (values and
@@ -183,53 +251,6 @@ __global__ void k_take_rows(const int64_t *keep, int64_t nk, int64_t ld, const d
   }
 }
 
-// pos[x] = list[pos[x]] for x < *n_dev (at most n_cap): positions of the
-// second compaction back to flat slots.
-__global__ void k_map_positions(uint64_t *pos, const uint64_t *list, uint64_t n_cap, const unsigned long long *n_dev) {
-  const uint64_t n = min((uint64_t)*n_dev, n_cap);
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
-    pos[x] = list[pos[x]];
-}
-
-__device__ __forceinline__ void materialise_one(FeatTable F, RungGeom g, AprioriParams P, uint64_t slot, int64_t f,
-                                                double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
-                                                int32_t *cplx_out, int32_t *units_out, uint64_t *used_out,
-                                                uint64_t *dmask_out, int lane) {
-  int op;
-  int64_t a, b;
-  decode_flat(g, slot, &op, &a, &b);
-  const double *xa = F.v64 + a * F.ld;
-  const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
-  double *out = v64 + f * F.ld;
-  for (int64_t s = lane; s < F.ld; s += 32) out[s] = (s < F.N) ? eval_op64(op, xa[s], xb[s]) : 0.0;
-  if (lane == 0) {
-    int32_t u[kMaxDims] = {0, 0, 0, 0, 0, 0, 0, 0}, cx = 0;
-    int bad = 0;
-    apriori64(F, P, op, a, b, u, &cx, &bad);
-    op_out[f] = op;
-    ca_out[f] = a;
-    cb_out[f] = b;
-    cplx_out[f] = cx;
-    for (int d = 0; d < kMaxDims; ++d) units_out[f * kMaxDims + d] = u[d];
-    if (F.used) {
-      used_out[f] = F.used[a] | (b >= 0 ? F.used[b] : 0ull);
-      dmask_out[f] = F.dmask[a] | (b >= 0 ? F.dmask[b] : 0ull);
-    }
-  }
-}
-
-// Store listed slots as new features [dst0, dst0 + n_list): warp per slot.
-__global__ void k_materialise(FeatTable F, RungGeom g, AprioriParams P, const uint64_t *list, uint64_t n_list,
-                              int64_t dst0, double *v64, int32_t *op_out, int64_t *ca_out, int64_t *cb_out,
-                              int32_t *cplx_out, int32_t *units_out, uint64_t *used_out, uint64_t *dmask_out) {
-  int lane = threadIdx.x & 31;
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) / 32;
-  for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_list; w += warps)
-    materialise_one(F, g, P, list[w], dst0 + (int64_t)w, v64, op_out, ca_out, cb_out, cplx_out, units_out, used_out,
-                    dmask_out, lane);
-}
-
-// FP32 rows and per-feature helpers of every stored feature.
 // FP32 rows and per-feature helpers: one warp per feature (row conversion
 // and the FP64 sum of squares for the norm bound are coalesced over lanes).
 __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const double *v64, float *v32,
@@ -453,9 +474,9 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   k_gather_rows<<<grid_for(n0 * ld, 256), 256, 0, st>>>(Xd, ldx, idx_d, n0, N, ld, T0.v64);
   uint8_t *ok = nullptr;
   DSE_TRY(dalloc(&ok, n0, "primary flags"));
-  k_summaries<<<grid_for(n0 * 32, 256), 256, 0, st>>>(T0.v64, ld, N, 0, n0, T0.mean64, T0.rmean64, T0.min64,
+  k_summaries<<<(unsigned)n0, kSumThreads, 0, st>>>(T0.v64, ld, N, 0, n0, T0.mean64, T0.rmean64, T0.min64,
                                                        T0.max64, T0.minabs64, T0.maxabs64, T0.minabsnz64,
-                                                       S->fmin_std_rel, ok);
+                                                       S->fmin_std_rel, ok, nullptr);
   std::vector<uint8_t> hok(n0);
   DSE_CUDA(cudaMemcpyAsync(hok.data(), ok, n0, cudaMemcpyDeviceToHost, st));
   DSE_CUDA(cudaStreamSynchronize(st));
@@ -554,27 +575,50 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     DSE_TRY(dalloc(&rw, g.slots, "realised flags"));
     DSE_TRY(dalloc(&vlist, g.slots, "valid list"));
     DSE_CUDA(cudaMemsetAsync(meta, 0, 10 * sizeof(unsigned long long), st));
-    note_launches(3);
+    note_launches(1);
     if (g.slots) k_apriori_rung<<<grid_for(g.slots, 256), 256, 0, st>>>(F, g, P, why, (int *)(meta + 8));
     launch_count_reasons(why, g.slots, meta, st);
     DSE_TRY(compact_bytes_dev(why, g.slots, DSE_VALID, list, meta + 6, st));
     dfree(why);
-    // realised test of the a-priori valid slots (flags past the count stay
-    // "not valid")
-    DSE_CUDA(cudaMemsetAsync(rw, 0xFF, g.slots, st));
-    if (g.slots)
-      k_realised_rung<<<grid_for(g.slots * 32, 256), 256, 0, st>>>(F, g, list, g.slots, meta + 6, S->fmin_std_rel,
-                                                                   rw);
-    DSE_TRY(compact_bytes_dev(rw, g.slots, DSE_VALID, vlist, meta + 7, st));
+    // every a-priori valid slot evaluated once into scratch rows and
+    // summarised there (the summary carries the realised test); the kept
+    // rows are then copied into the grown table.  The scratch has a row per
+    // slot unless that passes 4 GiB, in which case the a-priori count is
+    // read first.
+    uint64_t cap_rows = g.slots;
+    if ((double)g.slots * (double)ld * 8.0 > 4.0 * (double)(1ull << 30)) {
+      DSE_CUDA(cudaMemcpyAsync(hmeta, meta + 6, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+      DSE_CUDA(cudaStreamSynchronize(st));
+      cap_rows = hmeta[0];
+    }
+    double *rows = nullptr;
+    RowSummaries rsum{};
+    DSE_TRY(dalloc(&rows, (size_t)std::max<uint64_t>(cap_rows, 1) * ld, "rung scratch rows"));
+    double **rs_arr[7] = {&rsum.mean64, &rsum.rmean64, &rsum.min64, &rsum.max64, &rsum.minabs64, &rsum.maxabs64,
+                          &rsum.minabsnz64};
+    for (double **q : rs_arr) DSE_TRY(dalloc(q, std::max<uint64_t>(cap_rows, 1), "rung scratch summaries"));
+    DSE_CUDA(cudaMemsetAsync(rw, 0, g.slots, st));
+    note_launches(2);
+    if (cap_rows) {
+      k_eval_rows<<<(unsigned)cap_rows, kSumThreads, 0, st>>>(F, g, list, cap_rows, meta + 6, rows);
+      k_summaries<<<(unsigned)cap_rows, kSumThreads, 0, st>>>(rows, ld, N, 0, (int64_t)cap_rows, rsum.mean64,
+                                                             rsum.rmean64, rsum.min64, rsum.max64, rsum.minabs64,
+                                                             rsum.maxabs64, rsum.minabsnz64, S->fmin_std_rel, rw,
+                                                             meta + 6);
+    }
+    DSE_TRY(compact_bytes_dev(rw, cap_rows, 1, vlist, meta + 7, st));
     dfree(rw);
-    // vlist holds positions into list; map back to flat slots
-    if (g.slots) k_map_positions<<<grid_for(g.slots, 256, 1024), 256, 0, st>>>(vlist, list, g.slots, meta + 7);
-    dfree(list);
     DSE_CUDA(cudaMemcpyAsync(hmeta, meta, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     DSE_CUDA(cudaStreamSynchronize(st));
     const int hbad = (int)(hmeta[8] & 0xFFFFFFFFull);
-    if (hbad) {
+    auto drop_scratch = [&]() {
+      dfree(rows);
+      for (double **q : rs_arr) dfree(*q);
+      dfree(list);
       dfree(vlist);
+    };
+    if (hbad) {
+      drop_scratch();
       dfree(meta);
       T.release();
       set_error(hbad == 1 ? "odd unit exponent under sqrt" : "unit exponent out of range");
@@ -589,23 +633,21 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     TableArrays T2;
     dse_status s2 = table_alloc(T2, n + (int64_t)n_new, ld, rules);
     if (s2 != DSE_OK) {
-      dfree(vlist);
+      drop_scratch();
       dfree(meta);
       T.release();
       return s2;
     }
     DSE_TRY(table_copy(T2, T, n, ld, st));
     FeatTable Fold = view(T, n, N, ld, S->op_deny);
+    RowSummaries dsum{T2.mean64, T2.rmean64, T2.min64, T2.max64, T2.minabs64, T2.maxabs64, T2.minabsnz64};
+    note_launches(1);
     if (n_new)
-      k_materialise<<<grid_for(n_new * 32, 256), 256, 0, st>>>(Fold, g, P, vlist, n_new, n, T2.v64, T2.op, T2.ca,
-                                                               T2.cb, T2.cplx, T2.units, T2.used, T2.dmask);
-    if (n_new)
-      k_summaries<<<grid_for(n_new * 32, 256), 256, 0, st>>>(T2.v64, ld, N, n, n + (int64_t)n_new, T2.mean64,
-                                                             T2.rmean64, T2.min64, T2.max64, T2.minabs64, T2.maxabs64,
-                                                             T2.minabsnz64, S->fmin_std_rel, nullptr);
-    // stream-ordered frees: the old table and the list stay valid for the
-    // kernels above
-    dfree(vlist);
+      k_take_eval<<<(unsigned)n_new, kSumThreads, 0, st>>>(Fold, g, P, list, vlist, n_new, n, rows, rsum, T2.v64, dsum,
+                                                           T2.op, T2.ca, T2.cb, T2.cplx, T2.units, T2.used, T2.dmask);
+    drop_scratch();
+    // stream-ordered frees: the old table and the scratch stay valid for
+    // the kernels above
     T.release();
     T = T2;
     n += (int64_t)n_new;

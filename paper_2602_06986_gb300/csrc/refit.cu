@@ -37,19 +37,20 @@ __device__ __forceinline__ void decode_any(const RungGeom &G, int64_t n_stored, 
   }
 }
 
-// Columns of the given ids into out[c][N] (warp per column).
+// Columns of the given ids into out[c][N]: block c (any block size),
+// threads over samples, so that the FP64 evaluations of a column overlap.
 __global__ void k_columns(FeatTable F, RungGeom G, int64_t n_stored, const uint64_t *ids, int n, double *out) {
-  const int lane = threadIdx.x & 31;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int w = blockIdx.x;
   if (w >= n) return;
   if (ids[w] >= (uint64_t)n_stored + G.slots) {  // no such candidate (a failed step of a chained loop)
-    for (int64_t s = lane; s < F.N; s += 32) out[(int64_t)w * F.N + s] = 0.0;
+    for (int64_t s = threadIdx.x; s < F.N; s += blockDim.x) out[(int64_t)w * F.N + s] = 0.0;
     return;
   }
   int op;
   int64_t a, b;
   decode_any(G, n_stored, ids[w], &op, &a, &b);
-  for (int64_t s = lane; s < F.N; s += 32) out[(int64_t)w * F.N + s] = col_value(F, G, n_stored, op, a, b, s);
+  for (int64_t s = threadIdx.x; s < F.N; s += blockDim.x)
+    out[(int64_t)w * F.N + s] = col_value(F, G, n_stored, op, a, b, s);
 }
 
 constexpr int kMaxP = 4;  // fixed columns + candidate
@@ -165,12 +166,16 @@ constexpr int kWide = 128;
 template <int NV>
 __device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = warp_sum64(v[i]);
   if (lane == 0)
+#pragma unroll
     for (int i = 0; i < NV; ++i) sm[w * NV + i] = v[i];
   __syncthreads();
+#pragma unroll
   for (int i = 0; i < NV; ++i) {
     double t = 0.0;
+#pragma unroll
     for (int ww = 0; ww < kWide / 32; ++ww) t += sm[ww * NV + i];
     v[i] = t;
   }
@@ -186,22 +191,30 @@ __device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
 constexpr int kPreMean = 0, kPreMy = kMaxP, kPreGram = kMaxP + 1, kPreG = kPreGram + kMaxP * kMaxP,
               kPreNorm = kPreG + kMaxP, kPreSize = kPreNorm + kMaxP;
 
-__global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const double *fixed_cols, int nf, int64_t N,
+// NF (the number of fixed columns) is a template argument so that every
+// per-column array stays in registers.
+template <int NF>
+__global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const double *fixed_cols, int64_t N,
                                                       double *fcc, double *ycc, double *pre) {
+  constexpr int nf = NF;
   __shared__ double sm[(kWide / 32) * (kMaxP * kMaxP + 2 * kMaxP)];
   double mv[kMaxP + 1] = {0, 0, 0, 0, 0};
   for (int64_t s = threadIdx.x; s < N; s += kWide) {
+#pragma unroll
     for (int c = 0; c < nf; ++c) mv[c] += fixed_cols[(int64_t)c * N + s];
     mv[kMaxP] += y[s];
   }
   block_sum_arr<kMaxP + 1>(mv, sm);
   double m[kMaxP];
+#pragma unroll
   for (int c = 0; c < kMaxP; ++c) m[c] = mv[c] / (double)N;
   const double my = mv[kMaxP] / (double)N;
   double acc[kMaxP * kMaxP + 2 * kMaxP];
+#pragma unroll
   for (int i = 0; i < kMaxP * kMaxP + 2 * kMaxP; ++i) acc[i] = 0.0;
   for (int64_t s = threadIdx.x; s < N; s += kWide) {
     double xc[kMaxP] = {0, 0, 0, 0};
+#pragma unroll
     for (int c = 0; c < nf; ++c) {
       const double v = fixed_cols[(int64_t)c * N + s];
       xc[c] = v - m[c];
@@ -210,17 +223,23 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
     }
     const double yc = y[s] - my;
     ycc[s] = yc;
+#pragma unroll
     for (int c = 0; c < nf; ++c) {
+#pragma unroll
       for (int d = 0; d <= c; ++d) acc[c * kMaxP + d] = fma(xc[c], xc[d], acc[c * kMaxP + d]);
       acc[kMaxP * kMaxP + c] = fma(xc[c], yc, acc[kMaxP * kMaxP + c]);
     }
   }
   block_sum_arr<kMaxP * kMaxP + 2 * kMaxP>(acc, sm);
   if (threadIdx.x == 0) {
+#pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreMean + c] = m[c];
     pre[kPreMy] = my;
+#pragma unroll
     for (int i = 0; i < kMaxP * kMaxP; ++i) pre[kPreGram + i] = acc[i];
+#pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreG + c] = acc[kMaxP * kMaxP + c];
+#pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreNorm + c] = sqrt(acc[kMaxP * kMaxP + kMaxP + c]);
   }
 }
@@ -234,18 +253,19 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
 // shared memory (N doubles); FP64 arithmetic is the cost on this part.
 constexpr int64_t kRefitCacheMax = 6144;  // samples (48 KiB)
 
-template <bool CACHE>
+template <bool CACHE, int NF>
 __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, int64_t n_stored, const double *fcc,
-                                                      const double *ycc, const double *pre, int nf,
+                                                      const double *ycc, const double *pre,
                                                       const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand,
                                                       const int64_t *n_dev, double *rmse_out, double *beta_out) {
+  constexpr int nf = NF;
   __shared__ double sm[(kWide / 32) * 20];
   __shared__ double s_bc[kMaxP + 2];
   extern __shared__ double col[];
   const int64_t w = blockIdx.x;
   if (w >= n_cand || (n_dev && w >= *n_dev)) return;
   const int64_t N = F.N;
-  const int p = nf + 1;
+  constexpr int p = nf + 1;
   const uint64_t gid = cand[w];
   bool dup = false;
   for (int j = 0; j < nf; ++j) dup |= fixed_ids[j] == gid;
@@ -269,6 +289,7 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   double s2[kMaxP + 2] = {0, 0, 0, 0, 0, 0};  // sum d f_j (j < nf), sum d^2, sum d y
   for (int64_t s = threadIdx.x; s < N; s += kWide) {
     const double dv = vval(s) - mvv;
+#pragma unroll
     for (int c = 0; c < nf; ++c) s2[c] = fma(dv, fcc[(int64_t)c * N + s], s2[c]);
     s2[kMaxP] = fma(dv, dv, s2[kMaxP]);
     s2[kMaxP + 1] = fma(dv, ycc[s], s2[kMaxP + 1]);
@@ -276,7 +297,9 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   block_sum_arr<kMaxP + 2>(s2, sm);
   if (threadIdx.x == 0) {
     double Gm[kMaxP][kMaxP] = {}, g[kMaxP] = {}, nrm[kMaxP] = {};
+#pragma unroll
     for (int c = 0; c < nf; ++c) {
+#pragma unroll
       for (int d = 0; d <= c; ++d) Gm[c][d] = pre[kPreGram + c * kMaxP + d];
       g[c] = pre[kPreG + c];
       nrm[c] = pre[kPreNorm + c];
@@ -287,20 +310,21 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
     nrm[nf] = sqrt(s1[1]);
     double L[kMaxP][kMaxP] = {};
     bool ok = true;
-    for (int c = 0; c < p && ok; ++c) {
+#pragma unroll
+    for (int c = 0; c < p; ++c) {
       double dsum = Gm[c][c];
+#pragma unroll
       for (int k = 0; k < c; ++k) dsum -= L[c][k] * L[c][k];
-      if (!(dsum > 0.0)) {
-        ok = false;
-        break;
-      }
-      L[c][c] = sqrt(dsum);
-      if (!(L[c][c] > 1e-12 * nrm[c])) {
-        ok = false;
-        break;
-      }
+      // a non-positive or tiny pivot (collinear column) rejects the fit; the
+      // remaining steps run on a harmless pivot so that the loops stay
+      // branch-free and fully unrolled
+      const double piv = dsum > 0.0 ? sqrt(dsum) : 0.0;
+      ok = ok && dsum > 0.0 && piv > 1e-12 * nrm[c];
+      L[c][c] = ok ? piv : 1.0;
+#pragma unroll
       for (int r = c + 1; r < p; ++r) {
         double v = Gm[r][c];
+#pragma unroll
         for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
         L[r][c] = v / L[c][c];
       }
@@ -308,22 +332,29 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
     double beta[kMaxP + 1] = {};
     if (ok) {
       double z[kMaxP];
+#pragma unroll
       for (int c = 0; c < p; ++c) {
         double v = g[c];
+#pragma unroll
         for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
         z[c] = v / L[c][c];
       }
+#pragma unroll
       for (int c = p - 1; c >= 0; --c) {
         double v = z[c];
+#pragma unroll
         for (int k = c + 1; k < p; ++k) v -= L[k][c] * beta[k + 1];
         beta[c + 1] = v / L[c][c];
       }
       double b0 = pre[kPreMy];
+#pragma unroll
       for (int c = 0; c < nf; ++c) b0 -= beta[c + 1] * pre[kPreMean + c];
       b0 -= beta[p] * mvv;
       beta[0] = b0;
     }
+#pragma unroll
     for (int c = 0; c <= kMaxP; ++c) beta_out[w * (kMaxP + 1) + c] = ok && c <= p ? beta[c] : 0.0;
+#pragma unroll
     for (int c = 0; c < p; ++c) s_bc[c] = beta[c + 1];
     s_bc[kMaxP + 1] = ok ? 1.0 : 0.0;
   }
@@ -332,9 +363,11 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   double rss[1] = {0.0};
   if (ok) {
     double bc[kMaxP];
+#pragma unroll
     for (int c = 0; c < p; ++c) bc[c] = s_bc[c];
     for (int64_t s = threadIdx.x; s < N; s += kWide) {
       double r = ycc[s];
+#pragma unroll
       for (int c = 0; c < nf; ++c) r = fma(-bc[c], fcc[(int64_t)c * N + s], r);
       r = fma(-bc[nf], vval(s) - mvv, r);
       rss[0] = fma(r, r, rss[0]);
@@ -342,6 +375,33 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   }
   block_sum_arr<1>(rss, sm);
   if (threadIdx.x == 0) rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
+}
+
+// The per-candidate fits (prep of the fixed columns, then one block per
+// candidate) with the fixed-column count as a compile-time argument.
+template <int NF>
+static void launch_fits_nf(const FeatTable &F, const dse_space *S, const double *y, const double *fc,
+                           const uint64_t *fid, const uint64_t *cand, int64_t cap, const int64_t *n_dev, double *fcc,
+                           double *ycc, double *pre, double *rm, double *beta, cudaStream_t st) {
+  const int64_t N = S->N;
+  k_refit_prep<NF><<<1, kWide, 0, st>>>(y, fc, N, fcc, ycc, pre);
+  if (N <= kRefitCacheMax)
+    k_refit_wide<true, NF><<<(unsigned)cap, kWide, (size_t)N * sizeof(double), st>>>(F, S->geom, S->n, fcc, ycc, pre,
+                                                                                   fid, cand, cap, n_dev, rm, beta);
+  else
+    k_refit_wide<false, NF><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, fid, cand, cap, n_dev,
+                                                              rm, beta);
+}
+
+static void launch_fits(const FeatTable &F, const dse_space *S, int nf, const double *y, const double *fc,
+                        const uint64_t *fid, const uint64_t *cand, int64_t cap, const int64_t *n_dev, double *fcc,
+                        double *ycc, double *pre, double *rm, double *beta, cudaStream_t st) {
+  switch (nf) {
+    case 0: launch_fits_nf<0>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
+    case 1: launch_fits_nf<1>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
+    case 2: launch_fits_nf<2>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
+    default: launch_fits_nf<3>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
+  }
 }
 
 // Index of the smallest RMSE (ties: lower id); one block.  report (when not
@@ -445,14 +505,8 @@ void refit_chain(dse_space *S, const double *y, const uint64_t *fid, int nf, con
   int64_t *best = reinterpret_cast<int64_t *>(base);
   const FeatTable F = table_of(S);
   note_launches(4 + (nf ? 1 : 0));
-  if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
-  k_refit_prep<<<1, kWide, 0, st>>>(y, fc, nf, N, fcc, ycc, pre);
-  if (N <= kRefitCacheMax)
-    k_refit_wide<true><<<(unsigned)cap, kWide, (size_t)N * sizeof(double), st>>>(F, S->geom, S->n, fcc, ycc, pre,
-                                                                               nf, fid, cand, cap, n_dev, rm, beta);
-  else
-    k_refit_wide<false><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, nf, fid, cand, cap, n_dev,
-                                                          rm, beta);
+  if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
+  launch_fits(F, S, nf, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st);
   k_argmin<<<1, 1024, 0, st>>>(rm, cand, cap, best, beta, report, n_dev, chosen);
   k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
 }
@@ -520,14 +574,8 @@ dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, 
   }
   const FeatTable F = table_of(S);
   note_launches(4 + (nf ? 1 : 0));
-  if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
-  k_refit_prep<<<1, kWide, 0, st>>>(y, fc, nf, N, fcc, ycc, pre);
-  if (N <= kRefitCacheMax)
-    k_refit_wide<true><<<(unsigned)nc, kWide, (size_t)N * sizeof(double), st>>>(F, S->geom, S->n, fcc, ycc, pre,
-                                                                              nf, fid, cand, nc, nullptr, rm, beta);
-  else
-    k_refit_wide<false><<<(unsigned)nc, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, nf, fid, cand, nc, nullptr,
-                                                         rm, beta);
+  if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
+  launch_fits(F, S, nf, y, fc, fid, cand, nc, nullptr, fcc, ycc, pre, rm, beta, st);
   k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, rep, nullptr, nullptr);
   k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
   // one asynchronous copy of the winner's report (and of a host residual), one sync

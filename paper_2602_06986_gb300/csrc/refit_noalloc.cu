@@ -129,7 +129,7 @@ dse_status refit_noalloc_impl(dse_space *S, const dse_refit_desc *d, uint64_t *b
   if (e) return cuda_status(e, "no-alloc refit upload");
   const FeatTable F = table_of(S);
   note_launches(3 + (nf ? 1 : 0));
-  if (nf) k_columns<<<(nf * 32 + 255) / 256, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
+  if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
   k_refit<<<(unsigned)((nc * 32 + 255) / 256), 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, fid, cand, nc, rm, beta);
   k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, nullptr, nullptr, nullptr);
   k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);

@@ -49,6 +49,7 @@ struct SelectArgs {
   uint64_t *r_id;           // [lists][cap]
   float *r_s32, *r_e32;     // [lists][cap]
   double *r_s64, *r_e64;    // [lists][cap]
+  uint64_t *r_key;          // [lists][cap] ordering key of the final score
   uint8_t *r_need;          // [lists][cap]
   unsigned int *r_count;    // [lists]
   unsigned int *overflow;   // [lists]
@@ -61,10 +62,7 @@ struct SelectArgs {
   double *out_score, *out_eps;
   int64_t *out_n;
   double *max_eps;          // [lists] largest returned bound
-  // sort scratch for large lists [lists][sort_cap]
-  double *sort_key;
-  uint64_t *sort_id;
-  int64_t sort_cap;
+  unsigned int *r_rank;     // [lists][cap] rank of each retained entry
   unsigned long long *stats;
 };
 

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(1024) k_sel_bins(const SelectArgs S) {
     S.overflow[l] = (int64_t)cnt > S.B.cap ? 1u : 0u;
     S.state[l] = st;
     S.r_count[l] = 0;
+    S.max_eps[l] = 0.0;
   }
 }
 
@@ -190,6 +191,11 @@ __global__ void __launch_bounds__(1024) k_sel_exact(const SelectArgs S) {
   }
 }
 
+// Scores are non-negative, so the bit patterns of their doubles order like
+// the values: ranks compare 64-bit integers (integer ALU), not doubles (FP64
+// compares are slow on this part).
+__device__ __forceinline__ uint64_t score_key(double s) { return (uint64_t)__double_as_longlong(s); }
+
 // 4) classification into the retained set and the FP64 job list (all blocks).
 __global__ void k_sel_classify(const SelectArgs S) {
   const int l = blockIdx.y;
@@ -202,11 +208,13 @@ __global__ void k_sel_classify(const SelectArgs S) {
     if (!(in || und)) continue;
     const unsigned pos = atomicAdd(&S.r_count[l], 1u);
     const size_t r = base + pos;
+    S.r_rank[r] = 0u;
     S.r_id[r] = S.B.id[base + i];
     S.r_s32[r] = s;
     S.r_e32[r] = e;
     const bool need = S.all64 || und || e > kTol * s;
     S.r_need[r] = need ? 1 : 0;
+    if (!need) S.r_key[r] = score_key((double)s);
     if (need) {
       unsigned j = atomicAdd(S.n_jobs, 1u);
       S.job[j] = pos;
@@ -221,9 +229,12 @@ __global__ void k_sel_classify(const SelectArgs S) {
 // at most 16 there).
 constexpr int kRes = 128;
 
-// batch != nullptr: list l is problem l of a batched screen.
+// batch != nullptr: list l is problem l of a batched screen.  NT: 1 for
+// per-target lists, 16 (the first nt used) for aggregated lists; a
+// compile-time count keeps the accumulators in registers.
+template <int NT>
 __global__ void __launch_bounds__(kRes) k_rescore(const SelectArgs S, const ScreenArgs A0, const ScreenArgs *batch) {
-  __shared__ double red[kRes / 32][18];
+  __shared__ double red[kRes / 32][2 + NT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned nj = *S.n_jobs;
   for (unsigned w = blockIdx.x; w < nj; w += gridDim.x) {
@@ -244,17 +255,21 @@ __global__ void __launch_bounds__(kRes) k_rescore(const SelectArgs S, const Scre
     const double *xa = A.F.v64 + a * A.F.ld;
     const double *xb = A.F.v64 + (b >= 0 ? b : a) * A.F.ld;
     const int t_begin = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
-    const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < 16 ? A.T : 16) : 1;
+    const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < NT ? A.T : NT) : 1;
     const double c = eval_op64(op, xa[0], xb[0]);
-    double acc[18];
-    for (int i = 0; i < 18; ++i) acc[i] = 0.0;
+    double acc[2 + NT];
+#pragma unroll
+    for (int i = 0; i < 2 + NT; ++i) acc[i] = 0.0;
     for (int64_t s = threadIdx.x; s < N; s += kRes) {
       const double v = eval_op64(op, xa[s], xb[s]) - c;
       acc[0] += v;
       acc[1] = fma(v, v, acc[1]);
-      for (int t = 0; t < nt; ++t) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (t < nt) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
     }
-    for (int i = 0; i < 2 + nt; ++i) {
+#pragma unroll
+    for (int i = 0; i < 2 + NT; ++i) {
       double v = warp_sum64(acc[i]);
       if (lane == 0) red[wid][i] = v;
     }
@@ -278,20 +293,17 @@ __global__ void __launch_bounds__(kRes) k_rescore(const SelectArgs S, const Scre
       const double sc = A.mode == DSE_MODE_AGGREGATED ? sqrt(agg / (double)nt) : sqrt(agg);
       S.r_s64[r] = sc;
       S.r_e64[r] = (double)(N / kRes + 64) * 1.1102230246251565e-16 * 16.0 * (sc + 1e-3);
+      S.r_key[r] = score_key(sc);
       atomicAdd(&A.stats[ST_RESCORED], 1ull);
     }
     __syncthreads();
   }
 }
 
-// Scores are non-negative, so the bit patterns of their doubles order like
-// the values: the sort compares 64-bit integers (integer ALU), not doubles
-// (FP64 compares are slow on this part).  Padding: key 0, id 2^64-1.
-__device__ __forceinline__ uint64_t score_key(double s) { return (uint64_t)__double_as_longlong(s); }
-
 // The same re-score with one warp per job (lanes over samples, shuffle
 // reductions, no block barriers): for short sample ranges, where a block per
 // job would spend its time in barriers and reductions.
+template <int NT>
 __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const ScreenArgs A) {
   const int lane = threadIdx.x & 31;
   const unsigned nj = *S.n_jobs;
@@ -313,31 +325,35 @@ __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const 
     const double *xa = A.F.v64 + a * A.F.ld;
     const double *xb = A.F.v64 + (b >= 0 ? b : a) * A.F.ld;
     const int t_begin = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
-    const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < 16 ? A.T : 16) : 1;
+    const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < NT ? A.T : NT) : 1;
     const double c = eval_op64(op, xa[0], xb[0]);
-    double acc[18];
+    double acc[2 + NT];
 #pragma unroll
-    for (int i = 0; i < 18; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 2 + NT; ++i) acc[i] = 0.0;
     for (int64_t s = lane; s < N; s += 32) {
       const double v = eval_op64(op, xa[s], xb[s]) - c;
       acc[0] += v;
       acc[1] = fma(v, v, acc[1]);
-      for (int t = 0; t < nt; ++t) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (t < nt) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
     }
-    acc[0] = warp_sum64(acc[0]);
-    acc[1] = warp_sum64(acc[1]);
-    for (int t = 0; t < nt; ++t) acc[2 + t] = warp_sum64(acc[2 + t]);
+#pragma unroll
+    for (int i = 0; i < 2 + NT; ++i) acc[i] = warp_sum64(acc[i]);
     if (lane == 0) {
       const double mean = acc[0] / (double)N;
       const double sxx = acc[1] - acc[0] * mean;
       double agg = 0.0;
-      for (int t = 0; t < nt; ++t) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (t >= nt) break;
         const double sc = fabs(acc[2 + t]) / sqrt(sxx);
         agg += sc * sc;
       }
       const double sc = A.mode == DSE_MODE_AGGREGATED ? sqrt(agg / (double)nt) : sqrt(agg);
       S.r_s64[r] = sc;
       S.r_e64[r] = (double)(N / 32 + 64) * 1.1102230246251565e-16 * 16.0 * (sc + 1e-3);
+      S.r_key[r] = score_key(sc);
       atomicAdd(&A.stats[ST_RESCORED], 1ull);
     }
   }
@@ -347,117 +363,99 @@ __device__ __forceinline__ bool before(uint64_t ka, uint64_t ia, uint64_t kb, ui
   return ka > kb || (ka == kb && ia < ib);
 }
 
-// Bitonic sort (descending key, ascending id) of M (power of two) entries.
-__device__ void bitonic(uint64_t *key, uint64_t *id, int64_t M) {
-  for (int64_t size = 2; size <= M; size <<= 1) {
-    for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
-        int64_t j = i ^ stride;
-        if (j > i) {
-          bool up = (i & size) == 0;
-          uint64_t ki = key[i], kj = key[j];
-          uint64_t ii = id[i], ij = id[j];
-          bool sw = up ? before(kj, ij, ki, ii) : before(ki, ii, kj, ij);
-          if (sw) {
-            key[i] = kj;
-            key[j] = ki;
-            id[i] = ij;
-            id[j] = ii;
-          }
-        }
+__device__ __forceinline__ uint64_t retained_key(const SelectArgs &S, size_t r) { return S.r_key[r]; }
+
+// 6) order of the retained set (score descending, id ascending) by counting:
+// the rank of an entry is the number of entries ordered before it (ids are
+// unique within a list, so the ranks are a permutation).  Work items are
+// (8 entries, a tile of kRankTile keys); a block stages the tile's keys in
+// shared memory and each warp counts for one entry, lanes over the tile;
+// partial counts meet in r_rank by atomic adds.  Spread over all blocks, so
+// a list of a thousand entries costs a few microseconds instead of a
+// single-block sort.
+constexpr int kRankTile = 2048, kRankGroup = 8;
+
+__global__ void __launch_bounds__(256) k_rank(const SelectArgs S) {
+  __shared__ uint64_t tk[kRankTile], ti[kRankTile];
+  const int l = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t rn = S.r_count[l];
+  const size_t base = (size_t)l * S.B.cap;
+  const int64_t n_groups = (rn + kRankGroup - 1) / kRankGroup, n_tiles = (rn + kRankTile - 1) / kRankTile;
+  int64_t loaded = -1;
+  for (int64_t item = blockIdx.x; item < n_groups * n_tiles; item += gridDim.x) {
+    const int64_t g = item / n_tiles, t = item % n_tiles;
+    const int64_t t0 = t * kRankTile;
+    const int nt = (int)(rn - t0 < kRankTile ? rn - t0 : kRankTile);
+    if (t != loaded) {
+      __syncthreads();
+      for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+        tk[j] = retained_key(S, base + t0 + j);
+        ti[j] = S.r_id[base + t0 + j];
       }
       __syncthreads();
+      loaded = t;
+    }
+    for (int e = 0; e < kRankGroup / 8; ++e) {
+      const int64_t i = g * kRankGroup + warp * (kRankGroup / 8) + e;
+      if (i >= rn) break;
+      const uint64_t ki = retained_key(S, base + i), ii = S.r_id[base + i];
+      unsigned c = 0;
+      for (int j = lane; j < nt; j += 32) c += before(tk[j], ti[j], ki, ii) ? 1u : 0u;
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (lane == 0 && c) atomicAdd(&S.r_rank[base + i], c);
     }
   }
 }
 
-constexpr int64_t kSmemSort = 4096;
-
-// 6) one block per list: order the retained set and write the first k.
-__global__ void __launch_bounds__(1024) k_final(const SelectArgs S) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  const int l = blockIdx.x;
+// 7) entries of rank < k to their output slots; the list's length and its
+// largest returned bound (bounds are non-negative: their bit patterns order
+// like the values).
+__global__ void k_rank_write(const SelectArgs S) {
+  const int l = blockIdx.y;
   const int64_t rn = S.r_count[l];
   const size_t base = (size_t)l * S.B.cap;
-  int64_t M = 1;
-  while (M < rn) M <<= 1;
-  uint64_t *key;
-  uint64_t *id;
-  if (M <= kSmemSort) {
-    key = reinterpret_cast<uint64_t *>(sm);
-    id = reinterpret_cast<uint64_t *>(sm + kSmemSort * sizeof(uint64_t));
-  } else {
-    key = reinterpret_cast<uint64_t *>(S.sort_key) + (size_t)l * S.sort_cap;
-    id = S.sort_id + (size_t)l * S.sort_cap;
-  }
-  for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
-    if (i < rn) {
-      const size_t r = base + i;
-      key[i] = score_key(S.r_need[r] ? S.r_s64[r] : (double)S.r_s32[r]);
-      id[i] = S.r_id[r];
-    } else {
-      key[i] = 0ull;
-      id[i] = ~0ull;
-    }
-  }
-  __syncthreads();
-  bitonic(key, id, M);
   const int64_t nout = rn < S.k ? rn : S.k;
-  for (int64_t i = threadIdx.x; i < nout; i += blockDim.x) {
-    S.out_id[(size_t)l * S.k + i] = id[i];
-    S.out_score[(size_t)l * S.k + i] = __longlong_as_double((long long)key[i]);
-  }
-  __syncthreads();
-  // each retained entry finds its rank by binary search and writes its bound;
-  // the list's largest returned bound is reduced on the way
-  __shared__ double s_mx[32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) S.out_n[l] = nout;
   double mx = 0.0;
-  for (int64_t i = threadIdx.x; i < rn; i += blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rn; i += (int64_t)gridDim.x * blockDim.x) {
     const size_t r = base + i;
-    const uint64_t k0 = score_key(S.r_need[r] ? S.r_s64[r] : (double)S.r_s32[r]);
-    const uint64_t i0 = S.r_id[r];
-    int64_t lo = 0, hi = M;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if (before(key[mid], id[mid], k0, i0)) lo = mid + 1;
-      else hi = mid;
-    }
-    if (lo < nout) {
-      const double e = S.r_need[r] ? S.r_e64[r] : (double)S.r_e32[r];
-      S.out_eps[(size_t)l * S.k + lo] = e;
-      mx = fmax(mx, e);
-    }
+    const unsigned rank = S.r_rank[r];
+    if (rank >= nout) continue;
+    const bool n64 = S.r_need[r] != 0;
+    const size_t o = (size_t)l * S.k + rank;
+    S.out_id[o] = S.r_id[r];
+    S.out_score[o] = n64 ? S.r_s64[r] : (double)S.r_s32[r];
+    const double e = n64 ? S.r_e64[r] : (double)S.r_e32[r];
+    S.out_eps[o] = e;
+    mx = fmax(mx, e);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, s_mx[w]);
-    S.out_n[l] = nout;
-    S.max_eps[l] = fmax(mx, s_mx[0]);
-  }
+  mx = warp_max64(mx);
+  if ((threadIdx.x & 31) == 0 && mx > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long *>(&S.max_eps[l]), (unsigned long long)__double_as_longlong(mx));
 }
 
 dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cudaStream_t st,
                          const ScreenArgs *batch) {
-  note_launches(6);
+  note_launches(7);
   k_sel_bins<<<S.n_lists, 1024, 0, st>>>(S);
   const unsigned bx = (unsigned)std::max(1, std::min(256, (sms * 4 + S.n_lists - 1) / S.n_lists));
   dim3 g(bx, S.n_lists);
   k_sel_collect<<<g, 256, 0, st>>>(S);
   k_sel_exact<<<S.n_lists, 1024, 0, st>>>(S);
   k_sel_classify<<<g, 256, 0, st>>>(S);
-  if (!batch && A.N <= 4096)
-    k_rescore_warp<<<sms * 8, 256, 0, st>>>(S, A);
-  else
-    k_rescore<<<sms * 8, kRes, 0, st>>>(S, A, batch);
-  static bool attr = false;
-  if (!attr) {
-    DSE_CUDA(cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(kSmemSort * (sizeof(double) + sizeof(uint64_t)))));
-    attr = true;
+  const bool one = batch || A.mode != DSE_MODE_AGGREGATED || A.T == 1;
+  if (!batch && A.N <= 4096) {
+    if (one) k_rescore_warp<1><<<sms * 8, 256, 0, st>>>(S, A);
+    else k_rescore_warp<16><<<sms * 8, 256, 0, st>>>(S, A);
+  } else {
+    if (one) k_rescore<1><<<sms * 8, kRes, 0, st>>>(S, A, batch);
+    else k_rescore<16><<<sms * 8, kRes, 0, st>>>(S, A, batch);
   }
-  k_final<<<S.n_lists, 1024, kSmemSort * (sizeof(double) + sizeof(uint64_t)), st>>>(S);
+  const dim3 gr((unsigned)std::max(1, std::min(1024, (sms * 2 + S.n_lists - 1) / S.n_lists)), S.n_lists);
+  k_rank<<<gr, 256, 0, st>>>(S);
+  const dim3 gw((unsigned)std::max(1, std::min(64, (sms + S.n_lists - 1) / S.n_lists)), S.n_lists);
+  k_rank_write<<<gw, 256, 0, st>>>(S);
   return DSE_OK;
 }
 
