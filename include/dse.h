@@ -205,6 +205,11 @@ typedef struct {
    call synchronises the stream (it reads the list state between rounds).
    Not available in dse_residual_loop or the batched screens. */
 #define DSE_FLAG_DEDUP 2
+/* Evaluate the product and quotient slots sample by sample.  Without it a
+   single-target FP32 screen with 16 <= N <= 2048 takes their statistics from
+   Gram contractions on the tensor cores (same results: the same bounds
+   contract, the same FP64 re-score of the list). */
+#define DSE_FLAG_DIRECT 4
 
 dse_status dse_sis_screen(dse_space *space, const dse_screen_desc *desc, dse_result **out);
 void dse_result_free(dse_result *result);

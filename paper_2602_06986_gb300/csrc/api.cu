@@ -143,7 +143,20 @@ struct ScreenPlan {
   int32_t n_seed_tiles = 0;      // leading product/quotient tiles launched first
   float gamma_gen = 0.f, gamma_num = 0.f;
   unsigned char *bsplit = nullptr;
+  // Gram path of the product/quotient slots (single-target FP32 screens)
+  bool use_gram = false;
+  std::vector<int2> gram_tiles;
+  int2 *gram_tiles_dev = nullptr;
+  void *gram_scr = nullptr;
 };
+
+bool gram_eligible(int64_t N);
+size_t gram_space_bytes(int64_t n, int64_t N);
+size_t gram_screen_bytes(int64_t n, int64_t N);
+void gram_build_space(const FeatTable &F, void *buf, cudaStream_t st);
+void gram_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::vector<int2> &out);
+dse_status launch_pair_gram(const ScreenArgs &A, const void *space_buf, void *scr, const int2 *tiles, int n_tiles,
+                            int sms, cudaStream_t st);
 
 int tc_ntp_for(int T, int N);
 size_t tc_bsplit_bytes(int ntp, int N);
@@ -252,7 +265,14 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
     DSE_TRY(mark(0));
     launch_feature(plan.prec64, plan.nt, A, plan.id0, plan.id1, plan.p0, plan.p1, plan.gamma_lane, sms, st);
     DSE_TRY(mark(1));
-    if (!plan.mul_tiles.empty()) {
+    if (plan.use_gram) {
+      if (!sp->gram_buf) {
+        DSE_TRY(dmalloc(&sp->gram_buf, gram_space_bytes(sp->n, sp->N), "product Gram images"));
+        gram_build_space(table_of(sp), sp->gram_buf, st);
+      }
+      DSE_TRY(launch_pair_gram(A, sp->gram_buf, plan.gram_scr, plan.gram_tiles_dev, (int)plan.gram_tiles.size(), sms,
+                               st));
+    } else if (!plan.mul_tiles.empty()) {
       A.rowid = sp->rowid_ident;
       A.tile_counter = tile_ctr;
       const Tile *t0p = reinterpret_cast<const Tile *>(scr_tiles_mul);
@@ -365,7 +385,11 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
         addpos.push_back(s);
       }
     }
-    if (any_mul) {
+    plan.use_gram = any_mul && !plan.prec64 && !plan.use_tc && d->n_targets == 1 && gram_eligible(N) &&
+                    !(d->flags & DSE_FLAG_DIRECT);
+    if (plan.use_gram) {
+      gram_tiles(sp, id_begin, id_end, plan.gram_tiles);
+    } else if (any_mul) {
       triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.mul_tiles);
       // A large tile list is launched in two parts: every 64th tile first, so
       // that the thresholds have risen from a spread sample of the space
@@ -493,7 +517,11 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   sc.add(&tadd, plan.add_tiles.size());
   sc.add(&tile_ctr, 2);
   sc.add(&plan.bsplit, plan.use_tc ? tc_bsplit_bytes(plan.ntp, (int)N) : 1);
+  unsigned char *gram_scr = nullptr;
+  sc.add(&plan.gram_tiles_dev, plan.gram_tiles.size());
+  sc.add(&gram_scr, plan.use_gram ? gram_screen_bytes(sp->n, N) : 1);
   dse_status s = sc.alloc(&R->scratch, &R->scratch_bytes);
+  plan.gram_scr = gram_scr;
   if (s != DSE_OK) {
     delete R;
     return s;
@@ -515,6 +543,9 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   if (!e && !plan.add_tiles.empty())
     e = cudaMemcpyAsync(tadd, plan.add_tiles.data(), sizeof(Tile) * plan.add_tiles.size(), cudaMemcpyHostToDevice,
                         st);
+  if (!e && !plan.gram_tiles.empty())
+    e = cudaMemcpyAsync(plan.gram_tiles_dev, plan.gram_tiles.data(), sizeof(int2) * plan.gram_tiles.size(),
+                        cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemsetAsync(R->err, 0, sizeof(int), st);
   if (!e) e = cudaMemsetAsync(A.B.theta, 0, sizeof(float) * n_lists, st);
   if (e) return fail(cuda_status(e, "screen setup"));

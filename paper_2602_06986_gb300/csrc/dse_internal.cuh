@@ -303,6 +303,7 @@ struct dse_space {
   uint64_t *ukey = nullptr;
   uint64_t *used = nullptr, *dmask = nullptr, *op_deny = nullptr;  // user rules (nullptr: none)
   int32_t *rowid_ident = nullptr;   // identity row list [0, n)
+  void *gram_buf = nullptr;         // product Gram images and sums (built at the first use)
   // host copies for decoding
   std::vector<int32_t> h_op, h_rung, h_cplx;
   std::vector<int64_t> h_ca, h_cb;

@@ -43,6 +43,7 @@
 #include "eval64.cuh"
 #include "screen_common.cuh"
 #include "screen_kernels.cuh"
+#include "tcgen05.cuh"
 #include "util.cuh"
 
 namespace dse {
@@ -51,7 +52,6 @@ namespace tc {
 
 constexpr int M = 128;  // pairs per tile
 constexpr int BI = 16, BJ = 8, ROWS = BI + BJ;
-constexpr int KC = 32;    // samples per chunk (stage)
 constexpr int NS = 3;     // stages
 constexpr int KB = 16;    // chunks per accumulation block (512 samples)
 constexpr int NGEN = 8;   // generation warps
@@ -69,66 +69,6 @@ constexpr uint32_t A_OFF = ROWS_BYTES;
 constexpr uint32_t B_OFF = A_OFF + 6 * A_TILE;  // 52608
 __host__ __device__ constexpr uint32_t b_bytes(int ntp) { return 2u * (uint32_t)ntp * KC * 2; }
 __host__ __device__ constexpr uint32_t stage_bytes(int ntp) { return B_OFF + b_bytes(ntp); }
-
-// K-major tile of KC columns as 8x8 (16-byte-row) core matrices: core matrix
-// (row/8, k/8) at (row/8)*SBO + (k/8)*LBO; LBO = 128 (K direction), SBO =
-// KC/8*128 (row direction).
-constexpr uint32_t LBO = 128, SBO = (KC / 8) * 128;
-__host__ __device__ inline uint32_t core_off(int row, int k) {
-  return (uint32_t)(row >> 3) * SBO + (uint32_t)(k >> 3) * LBO + (uint32_t)(row & 7) * 16 + (uint32_t)(k & 7) * 2;
-}
-
-// Shared-memory matrix descriptor (no swizzle): start address >> 4, LBO >> 4
-// at bit 16, SBO >> 4 at bit 32, fixed 0b001 at bits 46-48.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
-         (1ull << 46);
-}
-
-// kind::f16 instruction descriptor: F32 accumulator (bit 4), BF16 A (bits
-// 7-9 = 1) and B (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at
-// bit 24.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
 
 struct Shared {
   uint64_t full_rows[NS], full_a[NS], empty[NS];

@@ -48,6 +48,7 @@ class ScreenDesc(C.Structure):
 
 FLAG_TIMING = 1
 FLAG_DEDUP = 2
+FLAG_DIRECT = 4
 
 
 class Stats(C.Structure):

@@ -73,16 +73,21 @@ def test_tiny_parity(env, seed):
     assert rs["valid"] == ors["valid"] + ors["realised"]
 
 
-def test_medium_parity(env):
+@pytest.mark.parametrize("direct", [False, True])
+def test_medium_parity(env, direct):
+    """Products and quotients from the tensor-core Gram contraction (default
+    for one FP32 target) and sample by sample (DSE_FLAG_DIRECT)."""
     torch, oracle, dse, W = env
     w = W.medium(0)
     sp, orc = spaces(env, w)
     check_counts(sp, orc, w["max_rung"])
-    res = sp.screen(torch.from_numpy(w["Y"]).cuda(), w["k"])
+    res = sp.screen(torch.from_numpy(w["Y"]).cuda(), w["k"], flags=dse.FLAG_DIRECT if direct else 0)
     ids, sc, eb = res.fetch(0)
     oids, osc, ocnt = orc.screen(w["Y"], w["k"])
     check_list(ids, sc, eb, oids[0], osc[0], orc, w["Y"], 0)
-    assert res.stats()["reasons"] == ocnt
+    st = res.stats()
+    assert st["reasons"] == ocnt
+    assert st["valid_by_group"][1] > 0
 
 
 @pytest.mark.parametrize("seed", [0, 3])
