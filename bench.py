@@ -39,6 +39,10 @@ FP32_LANES = 128
 # algorithmic FP32 lane operations per (valid candidate, sample) at one target:
 # evaluation, sum w, sum w^2 (FMA), sum w*y (FMA)
 OPS_PER_EVAL = 4
+# Gram path of the product/quotient slots (one FP32 target, 16 <= N <= 2048):
+# per pair and sample, 5 contraction entries x 3 slots x 3 BF16 products x 2
+# flops of tensor work
+GRAM_FLOPS_PER_PAIR_SAMPLE = 5 * 3 * 3 * 2
 
 
 def peaks():
@@ -102,6 +106,16 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measured_bf16(key):
+    """A bf16 tensor peak (TFLOP/s) from MEASURED_PEAKS.json, else the
+    recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), f"{key} (MEASURED_PEAKS.json)"
+    except Exception:
+        return (1900.0 if key == "bf16_tflops" else 1700.0), f"fallback {key}"
 
 
 def profiled_traffic(name="k_pair_mul_medium.txt"):
@@ -498,9 +512,37 @@ def main():
     mul_valid = sum(s["valid_by_group"][1] for st in all_stats for s in st)
     mul_launches = sum(1 for st in all_stats for s in st)
     mhz, peak_src = peaks()
-    peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12  # T lane-ops/s
-    achieved = mul_valid * N * OPS_PER_EVAL / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
     group_ms = [sum(s["kernel_ms"][g] for st in all_stats for s in st) for g in range(4)]
+    launch_ms = mul_ms / max(mul_launches, 1)
+    if 16 <= N <= 2048:
+        # the Gram contraction on the tensor cores: every pair of the binary
+        # block (i in the newest stored rung, j < i) is contracted
+        sp = dse.Space(Xd, w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                       explog_dimensionless=w["explog_dimensionless"])
+        o = sp.counts(0)[1]["valid"]
+        m = sp.n_stored - o
+        pairs = m * (m - 1) // 2 + m * o
+        sp.free()
+        flops = GRAM_FLOPS_PER_PAIR_SAMPLE * pairs * N
+        peak, tc_src = measured_bf16("bf16_tflops")
+        achieved = flops / (launch_ms * 1e-3) / 1e12 if launch_ms > 0 else None
+        roofline = {"bound": "tensor", "kernel": "k_pair_gram (BF16x3 tcgen05 Gram contraction: a*b, a/b, b/a)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (achieved / peak) if achieved else None,
+                    "traffic": profiled_traffic("k_pair_gram_medium.txt"),
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                      "(profiles/k_pair_gram_medium.txt)",
+                    "peak_source": tc_src + " (of measured, burst: the kernel runs ~0.1 ms inside a short step)",
+                    "flops_per_launch": flops, "flops_per_pair_sample": GRAM_FLOPS_PER_PAIR_SAMPLE,
+                    "pairs": pairs, "launch_ms": launch_ms, "share_of_step": mul_ms / tot_ms}
+    else:
+        peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12  # T lane-ops/s
+        achieved = mul_valid * N * OPS_PER_EVAL / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
+        roofline = {"bound": "alu", "kernel": "k_pair<float,MUL,1,2,2> (a*b, a/b, b/a slots)",
+                    "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
+                    "frac": (achieved / peak) if achieved else None, "traffic": None,
+                    "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({peak_src})",
+                    "ops_per_eval": OPS_PER_EVAL, "launch_ms": launch_ms, "share_of_step": mul_ms / tot_ms}
 
     # the plain FP64 GPU path on the same workload (same step, FP64 kernels)
     fp64_ms, fp64_c = [], 0
@@ -547,14 +589,7 @@ def main():
         "evals_per_s": evals_per_s,
         "fp64_plain": {"value": fp64_value, "unit": "candidates/s", "ms_per_step": sum(fp64_ms) / len(fp64_ms),
                        "speedup_of_fp32_path": value / world / fp64_value},
-        "roofline": {"bound": "alu", "kernel": "k_pair<float,MUL,1,2,2> (a*b, a/b, b/a slots)",
-                     "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(),
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
-                                       "(profiles/k_pair_mul_medium.txt)",
-                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({peak_src})",
-                     "ops_per_eval": OPS_PER_EVAL, "launch_ms": mul_ms / max(mul_launches, 1),
-                     "share_of_step": mul_ms / tot_ms},
+        "roofline": roofline,
         "kernel_group_ms_per_step": {"stored_unary": group_ms[0] / args.steps, "pair_mul": group_ms[1] / args.steps,
                                      "pair_add": group_ms[2] / args.steps, "select": group_ms[3] / args.steps},
         "per_screen": {key: sum(s[key] for st in all_stats for s in st) / max(1, sum(len(st) for st in all_stats))

@@ -234,8 +234,10 @@ typedef struct {
   int64_t valid_by_group[3];  /* valid candidates scored by the stored/unary,
                                  product/quotient and sum/difference kernels */
   double kernel_ms[4];     /* with DSE_FLAG_TIMING: device time of the
-                              stored/unary, product/quotient, sum/difference
-                              and selection kernel groups; else 0          */
+                              stored/unary kernel (with the Gram operand
+                              images when the products take that path), the
+                              product/quotient kernel, the sum/difference
+                              kernel and the selection kernels; else 0     */
   int64_t kernel_launches; /* kernels this screen launched                   */
   int64_t redundant;       /* DSE_FLAG_DEDUP: redundant entries passed over
                               while filling the lists (all lists)           */
@@ -393,7 +395,7 @@ dse_status dse_l0_search(dse_space *space, const dse_l0_desc *desc, int64_t *top
    capture (cudaMalloc is not allowed there), applications that hand all
    device memory to their own pool or run under a hard memory budget.
    Same arguments, results and synchronisation as dse_ls_refit.  Its scratch
-   is one fixed 4 MiB area per device, held by every device that loads the
+   is one fixed 8 MiB area per device, held by every device that loads the
    library until the process exits; the limits are N <= 32768 samples and
    n_cand <= 16384 candidates, and larger requests return DSE_EOVERFLOW with
    a message.  The first call on a device looks the area's address up

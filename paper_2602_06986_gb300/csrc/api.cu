@@ -155,6 +155,7 @@ size_t gram_space_bytes(int64_t n, int64_t N);
 size_t gram_screen_bytes(int64_t n, int64_t N);
 void gram_build_space(const FeatTable &F, void *buf, cudaStream_t st);
 void gram_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::vector<int2> &out);
+void launch_gram_arows(const ScreenArgs &A, const void *space_buf, void *scr, cudaStream_t st);
 dse_status launch_pair_gram(const ScreenArgs &A, const void *space_buf, void *scr, const int2 *tiles, int n_tiles,
                             int sms, cudaStream_t st);
 
@@ -264,12 +265,16 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
     A.first_pass = pass == 0;
     DSE_TRY(mark(0));
     launch_feature(plan.prec64, plan.nt, A, plan.id0, plan.id1, plan.p0, plan.p1, plan.gamma_lane, sms, st);
-    DSE_TRY(mark(1));
     if (plan.use_gram) {
+      // the operand images (timed with the stored/unary group)
       if (!sp->gram_buf) {
         DSE_TRY(dmalloc(&sp->gram_buf, gram_space_bytes(sp->n, sp->N), "product Gram images"));
         gram_build_space(table_of(sp), sp->gram_buf, st);
       }
+      launch_gram_arows(A, sp->gram_buf, plan.gram_scr, st);
+    }
+    DSE_TRY(mark(1));
+    if (plan.use_gram) {
       DSE_TRY(launch_pair_gram(A, sp->gram_buf, plan.gram_scr, plan.gram_tiles_dev, (int)plan.gram_tiles.size(), sms,
                                st));
     } else if (!plan.mul_tiles.empty()) {
@@ -768,9 +773,12 @@ static dse_status dedup_screen(dse_space *sp, const dse_screen_desc *d, dse_resu
 // ------------------------------------------------------ residual loop
 
 size_t refit_chain_bytes(int64_t N, int64_t cap);
-void refit_chain(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
-                 const int64_t *n_dev, void *scratch, double *res, double *report, uint64_t *chosen,
-                 cudaStream_t st);
+void refit_chain_prep(dse_space *S, const double *y, const uint64_t *fid, int nf, void *scratch, int64_t cap,
+                      cudaStream_t st);
+void refit_chain_vectors(void *scratch, int64_t N, int64_t cap, const double **vec, double **outx);
+void refit_chain_fit(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
+                     const int64_t *n_dev, void *scratch, bool have_sums, double *res, double *report,
+                     uint64_t *chosen, cudaStream_t st);
 
 constexpr int kLoopMax = 4;  // descriptors (the refit fits up to 4 columns)
 constexpr int kReport = 8;   // winner's index, id, rmse, intercept + 4 coefficients
@@ -810,6 +818,11 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   uint64_t *fid = nullptr, *ids = nullptr;
   unsigned long long *small = nullptr;
   unsigned char *rscr = nullptr;
+  double *rx = nullptr;
+  Keep *kp = reinterpret_cast<Keep *>(R->keep);
+  // the re-score takes the refit sums alongside (one warp per candidate:
+  // N <= 4096); rx holds them per retained entry
+  const bool fused = N <= 4096;
   Scratch sc;
   if (!d->y_on_device) sc.add(&ydev, (size_t)N);
   sc.add(&r, (size_t)D * N);
@@ -818,6 +831,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   sc.add(&small, (size_t)D * kSmall);
   sc.add(&ids, (size_t)D * k);
   sc.add(&rscr, refit_chain_bytes(N, k));
+  sc.add(&rx, fused ? (size_t)R->n_lists * kp->plan.cap * 8 : 1);
   size_t bytes = 0;
   DSE_TRY(sc.alloc(&own.scratch, &bytes));
   const double *y = d->y;
@@ -841,12 +855,30 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
     DSE_CUDA(cudaMemcpyAsync(ids + (size_t)it * k, R->out_id, 8 * k, cudaMemcpyDeviceToDevice, st));
     return DSE_OK;
   };
+  // before iteration it's screen: the fixed columns' fit, and the vectors
+  // the re-score takes the candidates' sums against
+  auto prepare = [&](int it) {
+    refit_chain_prep(sp, y, fid, it, rscr, k, st);
+    if (fused) {
+      const double *vec[4];
+      double *outx = nullptr;
+      refit_chain_vectors(rscr, N, k, vec, &outx);
+      for (int m = 0; m < 4; ++m) kp->S.xv[m] = vec[m];
+      kp->S.nx = 1 + it;
+      kp->S.r_x = rx;
+      kp->S.out_x = outx;
+    }
+  };
+  auto fit = [&](int it) {
+    refit_chain_fit(sp, y, fid, it, R->out_id, k, R->out_n, rscr, fused, r + (size_t)it * N,
+                    rep + (size_t)it * kReport, fid + it, st);
+  };
   auto step = [&](int it) -> dse_status {
     const double *src = it == 0 ? y : r + (size_t)(it - 1) * N;
+    prepare(it);
     DSE_TRY(screen_enqueue_target(R, src, N));
     DSE_TRY(snapshot(it));
-    refit_chain(sp, y, fid, it, R->out_id, k, R->out_n, rscr, r + (size_t)it * N, rep + (size_t)it * kReport,
-                fid + it, st);
+    fit(it);
     DSE_CUDA(cudaGetLastError());
     return DSE_OK;
   };
@@ -883,11 +915,11 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
     for (int it = first_bad; it < D; ++it) {
       const double *src = it == 0 ? y : r + (size_t)(it - 1) * N;
       tmark[it] = R->timing.size();
+      prepare(it);
       DSE_TRY(screen_enqueue_target(R, src, N));
       DSE_TRY(finish(R));
       DSE_TRY(snapshot(it));
-      refit_chain(sp, y, fid, it, R->out_id, k, R->out_n, rscr, r + (size_t)it * N, rep + (size_t)it * kReport,
-                  fid + it, st);
+      fit(it);
       DSE_CUDA(cudaGetLastError());
       out->stats[it] = R->host_stats;
       tmark[it + 1] = R->timing.size();

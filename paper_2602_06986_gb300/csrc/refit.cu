@@ -189,15 +189,22 @@ __device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
 // columns, kMaxP: mean of y, then Gram lower triangle (kMaxP*kMaxP), then
 // products with y (kMaxP), then raw norms (kMaxP).
 constexpr int kPreMean = 0, kPreMy = kMaxP, kPreGram = kMaxP + 1, kPreG = kPreGram + kMaxP * kMaxP,
-              kPreNorm = kPreG + kMaxP, kPreSize = kPreNorm + kMaxP;
+              kPreNorm = kPreG + kMaxP, kPreSize0 = kPreNorm + kMaxP;
+// then the fit of y on the fixed columns alone (the Frisch-Waugh-Lovell
+// form of every candidate's fit): Cholesky factor of the centred Gram
+// matrix, coefficients, RSS of the explicit residual r = yc - Fc beta, sum r,
+// sums of the centred fixed columns, and whether the fixed fit is full rank
+constexpr int kPreL = kPreSize0, kPreBf = kPreL + kMaxP * kMaxP, kPreRss = kPreBf + kMaxP, kPreSr = kPreRss + 1,
+              kPreSf = kPreSr + 1, kPreOk = kPreSf + kMaxP, kPreSize = kPreOk + 1;
 
 // NF (the number of fixed columns) is a template argument so that every
 // per-column array stays in registers.
 template <int NF>
 __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const double *fixed_cols, int64_t N,
-                                                      double *fcc, double *ycc, double *pre) {
+                                                      double *fcc, double *ycc, double *rc, double *pre) {
   constexpr int nf = NF;
-  __shared__ double sm[(kWide / 32) * (kMaxP * kMaxP + 2 * kMaxP)];
+  __shared__ double sm[(kWide / 32) * (kMaxP * kMaxP + 3 * kMaxP)];
+  __shared__ double s_beta[kMaxP + 1];
   double mv[kMaxP + 1] = {0, 0, 0, 0, 0};
   for (int64_t s = threadIdx.x; s < N; s += kWide) {
 #pragma unroll
@@ -209,9 +216,9 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
 #pragma unroll
   for (int c = 0; c < kMaxP; ++c) m[c] = mv[c] / (double)N;
   const double my = mv[kMaxP] / (double)N;
-  double acc[kMaxP * kMaxP + 2 * kMaxP];
+  double acc[kMaxP * kMaxP + 3 * kMaxP];
 #pragma unroll
-  for (int i = 0; i < kMaxP * kMaxP + 2 * kMaxP; ++i) acc[i] = 0.0;
+  for (int i = 0; i < kMaxP * kMaxP + 3 * kMaxP; ++i) acc[i] = 0.0;
   for (int64_t s = threadIdx.x; s < N; s += kWide) {
     double xc[kMaxP] = {0, 0, 0, 0};
 #pragma unroll
@@ -220,6 +227,7 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
       xc[c] = v - m[c];
       fcc[(int64_t)c * N + s] = xc[c];
       acc[kMaxP * kMaxP + kMaxP + c] = fma(v, v, acc[kMaxP * kMaxP + kMaxP + c]);
+      acc[kMaxP * kMaxP + 2 * kMaxP + c] += xc[c];
     }
     const double yc = y[s] - my;
     ycc[s] = yc;
@@ -230,7 +238,7 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
       acc[kMaxP * kMaxP + c] = fma(xc[c], yc, acc[kMaxP * kMaxP + c]);
     }
   }
-  block_sum_arr<kMaxP * kMaxP + 2 * kMaxP>(acc, sm);
+  block_sum_arr<kMaxP * kMaxP + 3 * kMaxP>(acc, sm);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreMean + c] = m[c];
@@ -241,6 +249,184 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
     for (int c = 0; c < kMaxP; ++c) pre[kPreG + c] = acc[kMaxP * kMaxP + c];
 #pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreNorm + c] = sqrt(acc[kMaxP * kMaxP + kMaxP + c]);
+    // the fixed-only fit: Cholesky with the collinearity test on the pivots
+    double L[kMaxP][kMaxP] = {}, z[kMaxP] = {}, bf[kMaxP] = {};
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < nf; ++c) {
+      double dsum = acc[c * kMaxP + c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) dsum -= L[c][k] * L[c][k];
+      const double piv = dsum > 0.0 ? sqrt(dsum) : 0.0;
+      ok = ok && dsum > 0.0 && piv > 1e-12 * sqrt(acc[kMaxP * kMaxP + kMaxP + c]);
+      L[c][c] = ok ? piv : 1.0;
+#pragma unroll
+      for (int r = c + 1; r < nf; ++r) {
+        double v = acc[r * kMaxP + c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
+        L[r][c] = v / L[c][c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < nf; ++c) {
+      double v = acc[kMaxP * kMaxP + c];
+#pragma unroll
+      for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
+      z[c] = v / L[c][c];
+    }
+#pragma unroll
+    for (int c = nf - 1; c >= 0; --c) {
+      double v = z[c];
+#pragma unroll
+      for (int k = c + 1; k < nf; ++k) v -= L[k][c] * bf[k];
+      bf[c] = v / L[c][c];
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxP * kMaxP; ++i) pre[kPreL + i] = L[i / kMaxP][i % kMaxP];
+#pragma unroll
+    for (int c = 0; c < kMaxP; ++c) {
+      pre[kPreBf + c] = ok ? bf[c] : 0.0;
+      s_beta[c] = ok ? bf[c] : 0.0;
+      pre[kPreSf + c] = acc[kMaxP * kMaxP + 2 * kMaxP + c];
+    }
+    pre[kPreOk] = ok ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // the explicit residual of the fixed-only fit
+  double bfr[kMaxP];
+#pragma unroll
+  for (int c = 0; c < kMaxP; ++c) bfr[c] = s_beta[c];
+  double q[2] = {0.0, 0.0};
+  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+    double r = ycc[s];
+#pragma unroll
+    for (int c = 0; c < nf; ++c) r = fma(-bfr[c], fcc[(int64_t)c * N + s], r);
+    rc[s] = r;
+    q[0] = fma(r, r, q[0]);
+    q[1] += r;
+  }
+  block_sum_arr<2>(q, sm);
+  if (threadIdx.x == 0) {
+    pre[kPreRss] = q[0];
+    pre[kPreSr] = q[1];
+  }
+}
+
+// Column sums of the candidates whose record the re-score did not fill
+// (out_x[w][7] == 0), one warp per candidate, with the same function and
+// vector order as the re-score: {rc, fcc_0 ..}.
+template <int NF>
+__global__ void __launch_bounds__(256) k_refit_fill(FeatTable F, RungGeom G, int64_t n_stored, const uint64_t *cand,
+                                                    int64_t n_cand, const int64_t *n_dev, const double *rc,
+                                                    const double *fcc, double *out_x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_cand || (n_dev && w >= *n_dev)) return;
+  double *x = out_x + w * 8;
+  if (x[7] != 0.0) return;
+  const int64_t N = F.N;
+  const uint64_t gid = cand[w];
+  if (gid >= (uint64_t)n_stored + G.slots) return;
+  int op;
+  int64_t a, b;
+  decode_any(G, n_stored, gid, &op, &a, &b);
+  const double c = col_value(F, G, n_stored, op, a, b, 0);
+  const double *vec[kColVec] = {rc, fcc, fcc + N, fcc + 2 * N, fcc + 3 * N};
+  double acc[2 + kColVec];
+  col_sums_warp(F, op, a, b, N, c, vec, 1 + NF, acc, lane);
+  if (lane == 0) {
+    x[0] = c;
+    x[1] = acc[0];
+    x[2] = acc[1];
+    for (int m = 0; m < 4; ++m) x[3 + m] = m < 1 + NF ? acc[2 + m] : 0.0;
+    x[7] = 1.0;
+  }
+}
+
+// Every candidate's fit from its column sums (thread per candidate), in the
+// Frisch-Waugh-Lovell form: with d the centred candidate column, e_j =
+// sum d f_j, w = G^-1 e (G the centred Gram matrix of the fixed columns),
+// |d_perp|^2 = sum d^2 - e.w and sum d_perp r = sum d r (r, the fixed-only
+// residual, is orthogonal to the fixed columns), the candidate's coefficient
+// is (sum d r) / |d_perp|^2 and RSS = RSS_fixed - (sum d r)^2 / |d_perp|^2.
+// The pivot test is the full fit's (|d_perp| > 1e-12 |v|).  A fit that leaves
+// less than 1e-6 of RSS_fixed (where the subtraction loses digits) is flagged
+// for the explicit residual pass.
+template <int NF>
+__global__ void k_refit_solve(const double *out_x, const uint64_t *cand, int64_t n_cand, const int64_t *n_dev,
+                              const uint64_t *fixed_ids, const double *pre, int64_t N, double *rmse_out,
+                              double *beta_out, uint8_t *explicit_flag) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_cand || (n_dev && w >= *n_dev)) return;
+  constexpr int nf = NF;
+  const uint64_t gid = cand[w];
+  bool dup = false;
+#pragma unroll
+  for (int j = 0; j < nf; ++j) dup |= fixed_ids[j] == gid;
+  explicit_flag[w] = 0;
+  const double *x = out_x + w * 8;
+  if (dup || x[7] == 0.0 || pre[kPreOk] == 0.0) {
+    rmse_out[w] = INFINITY;
+#pragma unroll
+    for (int c = 0; c <= kMaxP; ++c) beta_out[w * (kMaxP + 1) + c] = 0.0;
+    return;
+  }
+  const double Nd = (double)N;
+  const double c0 = x[0], S1 = x[1], S2 = x[2];
+  const double mS = S1 / Nd;  // vbar - c
+  const double Sdd = S2 - S1 * mS;
+  const double Sdr = x[3] - mS * pre[kPreSr];
+  double e[kMaxP] = {}, z[kMaxP] = {}, wv[kMaxP] = {};
+#pragma unroll
+  for (int j = 0; j < nf; ++j) e[j] = x[4 + j] - mS * pre[kPreSf + j];
+  // w = G^-1 e with G = L L^T
+#pragma unroll
+  for (int c = 0; c < nf; ++c) {
+    double v = e[c];
+#pragma unroll
+    for (int k = 0; k < c; ++k) v -= pre[kPreL + c * kMaxP + k] * z[k];
+    z[c] = v / pre[kPreL + c * kMaxP + c];
+  }
+#pragma unroll
+  for (int c = nf - 1; c >= 0; --c) {
+    double v = z[c];
+#pragma unroll
+    for (int k = c + 1; k < nf; ++k) v -= pre[kPreL + k * kMaxP + c] * wv[k];
+    wv[c] = v / pre[kPreL + c * kMaxP + c];
+  }
+  double ew = 0.0;
+#pragma unroll
+  for (int j = 0; j < nf; ++j) ew += e[j] * wv[j];
+  const double den = Sdd - ew;
+  const double raw2 = S2 + 2.0 * c0 * S1 + Nd * c0 * c0;  // sum v^2
+  const bool ok = den > 0.0 && sqrt(den) > 1e-12 * sqrt(raw2 > 0.0 ? raw2 : 0.0);
+  double *bo = beta_out + w * (kMaxP + 1);
+  if (!ok) {
+    rmse_out[w] = INFINITY;
+#pragma unroll
+    for (int c = 0; c <= kMaxP; ++c) bo[c] = 0.0;
+    return;
+  }
+  const double bc = Sdr / den;
+  const double rss_f = pre[kPreRss];
+  const double rss = rss_f - Sdr * bc;
+  double b0 = pre[kPreMy] - bc * (c0 + mS);
+#pragma unroll
+  for (int j = 0; j < nf; ++j) {
+    const double bj = pre[kPreBf + j] - wv[j] * bc;
+    bo[j + 1] = bj;
+    b0 -= bj * pre[kPreMean + j];
+  }
+  bo[0] = b0;
+  bo[nf + 1] = bc;
+#pragma unroll
+  for (int c = nf + 2; c <= kMaxP; ++c) bo[c] = 0.0;
+  if (rss < 1e-6 * rss_f) {
+    explicit_flag[w] = 1;
+    rmse_out[w] = INFINITY;
+  } else {
+    rmse_out[w] = sqrt(rss / Nd);
   }
 }
 
@@ -257,13 +443,15 @@ template <bool CACHE, int NF>
 __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, int64_t n_stored, const double *fcc,
                                                       const double *ycc, const double *pre,
                                                       const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand,
-                                                      const int64_t *n_dev, double *rmse_out, double *beta_out) {
+                                                      const int64_t *n_dev, double *rmse_out, double *beta_out,
+                                                      const uint8_t *only) {
   constexpr int nf = NF;
   __shared__ double sm[(kWide / 32) * 20];
   __shared__ double s_bc[kMaxP + 2];
   extern __shared__ double col[];
   const int64_t w = blockIdx.x;
   if (w >= n_cand || (n_dev && w >= *n_dev)) return;
+  if (only && !only[w]) return;
   const int64_t N = F.N;
   constexpr int p = nf + 1;
   const uint64_t gid = cand[w];
@@ -377,31 +565,115 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   if (threadIdx.x == 0) rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
 }
 
-// The per-candidate fits (prep of the fixed columns, then one block per
-// candidate) with the fixed-column count as a compile-time argument.
-template <int NF>
-static void launch_fits_nf(const FeatTable &F, const dse_space *S, const double *y, const double *fc,
-                           const uint64_t *fid, const uint64_t *cand, int64_t cap, const int64_t *n_dev, double *fcc,
-                           double *ycc, double *pre, double *rm, double *beta, cudaStream_t st) {
-  const int64_t N = S->N;
-  k_refit_prep<NF><<<1, kWide, 0, st>>>(y, fc, N, fcc, ycc, pre);
-  if (N <= kRefitCacheMax)
-    k_refit_wide<true, NF><<<(unsigned)cap, kWide, (size_t)N * sizeof(double), st>>>(F, S->geom, S->n, fcc, ycc, pre,
-                                                                                   fid, cand, cap, n_dev, rm, beta);
-  else
-    k_refit_wide<false, NF><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, fcc, ycc, pre, fid, cand, cap, n_dev,
-                                                              rm, beta);
+__global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
+                         double *report, const int64_t *n_dev, uint64_t *chosen);
+__global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const double *y, const double *fixed_cols,
+                           int nf, const uint64_t *cand, const int64_t *best, const double *beta_all, double *res);
+
+// Buffers of one refit step, carved from one scratch block: fixed columns,
+// their centred copies, centred y, the fixed-only residual, the shared
+// statistics, and per candidate its column sums, RMSE, coefficients and the
+// explicit-pass flag.
+struct RefitBufs {
+  double *fc, *fcc, *ycc, *rc, *pre, *outx, *rm, *beta;
+  uint8_t *flag;
+  int64_t *best;
+};
+
+static size_t rnd256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t refit_chain_bytes(int64_t N, int64_t cap) {
+  return rnd256(8 * (size_t)N * kMaxP) * 2 + rnd256(8 * N) * 2 + rnd256(8 * kPreSize) + rnd256(64 * (size_t)cap) +
+         rnd256(8 * cap) + rnd256(8 * (size_t)cap * (kMaxP + 1)) + rnd256(cap) + rnd256(8);
 }
 
-static void launch_fits(const FeatTable &F, const dse_space *S, int nf, const double *y, const double *fc,
-                        const uint64_t *fid, const uint64_t *cand, int64_t cap, const int64_t *n_dev, double *fcc,
-                        double *ycc, double *pre, double *rm, double *beta, cudaStream_t st) {
+static RefitBufs carve(void *scratch, int64_t N, int64_t cap) {
+  char *p = static_cast<char *>(scratch);
+  RefitBufs b;
+  auto take = [&](size_t bytes) {
+    char *q = p;
+    p += rnd256(bytes);
+    return q;
+  };
+  b.fc = reinterpret_cast<double *>(take(8 * (size_t)N * kMaxP));
+  b.fcc = reinterpret_cast<double *>(take(8 * (size_t)N * kMaxP));
+  b.ycc = reinterpret_cast<double *>(take(8 * N));
+  b.rc = reinterpret_cast<double *>(take(8 * N));
+  b.pre = reinterpret_cast<double *>(take(8 * kPreSize));
+  b.outx = reinterpret_cast<double *>(take(64 * (size_t)cap));
+  b.rm = reinterpret_cast<double *>(take(8 * cap));
+  b.beta = reinterpret_cast<double *>(take(8 * (size_t)cap * (kMaxP + 1)));
+  b.flag = reinterpret_cast<uint8_t *>(take(cap));
+  b.best = reinterpret_cast<int64_t *>(take(8));
+  return b;
+}
+
+template <int NF>
+static void prep_nf(const dse_space *S, const double *y, const RefitBufs &b, cudaStream_t st) {
+  k_refit_prep<NF><<<1, kWide, 0, st>>>(y, b.fc, S->N, b.fcc, b.ycc, b.rc, b.pre);
+}
+
+// Fill the missing column sums, solve every fit, redo the flagged ones
+// explicitly (one block per flagged candidate).
+template <int NF>
+static void fit_nf(const FeatTable &F, const dse_space *S, const uint64_t *fid, const uint64_t *cand, int64_t cap,
+                   const int64_t *n_dev, const RefitBufs &b, cudaStream_t st) {
+  const int64_t N = S->N;
+  k_refit_fill<NF><<<(unsigned)((cap * 32 + 255) / 256), 256, 0, st>>>(F, S->geom, S->n, cand, cap, n_dev, b.rc,
+                                                                        b.fcc, b.outx);
+  k_refit_solve<NF><<<(unsigned)((cap + 127) / 128), 128, 0, st>>>(b.outx, cand, cap, n_dev, fid, b.pre, N, b.rm,
+                                                                    b.beta, b.flag);
+  if (N <= kRefitCacheMax)
+    k_refit_wide<true, NF><<<(unsigned)cap, kWide, (size_t)N * sizeof(double), st>>>(
+        F, S->geom, S->n, b.fcc, b.ycc, b.pre, fid, cand, cap, n_dev, b.rm, b.beta, b.flag);
+  else
+    k_refit_wide<false, NF><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, b.fcc, b.ycc, b.pre, fid, cand, cap,
+                                                              n_dev, b.rm, b.beta, b.flag);
+}
+
+// The fixed columns' statistics and residual (before the screen whose
+// re-score takes the candidates' sums against them).
+void refit_chain_prep(dse_space *S, const double *y, const uint64_t *fid, int nf, void *scratch, int64_t cap,
+                      cudaStream_t st) {
+  const RefitBufs b = carve(scratch, S->N, cap);
+  const FeatTable F = table_of(S);
+  note_launches(1 + (nf ? 1 : 0));
+  if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, b.fc);
   switch (nf) {
-    case 0: launch_fits_nf<0>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
-    case 1: launch_fits_nf<1>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
-    case 2: launch_fits_nf<2>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
-    default: launch_fits_nf<3>(F, S, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st); break;
+    case 0: prep_nf<0>(S, y, b, st); break;
+    case 1: prep_nf<1>(S, y, b, st); break;
+    case 2: prep_nf<2>(S, y, b, st); break;
+    default: prep_nf<3>(S, y, b, st); break;
   }
+}
+
+// What a re-score needs to take the refit sums: the vectors {rc, fcc_0 ..}
+// (1 + nf of them) and the per-candidate record array.
+void refit_chain_vectors(void *scratch, int64_t N, int64_t cap, const double **vec, double **outx) {
+  const RefitBufs b = carve(scratch, N, cap);
+  vec[0] = b.rc;
+  for (int j = 0; j < 3; ++j) vec[1 + j] = b.fcc + (size_t)j * N;
+  *outx = b.outx;
+}
+
+// The fits of candidates cand[0..*n_dev) (at most cap) after refit_chain_prep;
+// have_sums: the re-score filled the records (else every record is taken
+// here).  Writes the winner's report, its id to *chosen and the residual.
+void refit_chain_fit(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
+                     const int64_t *n_dev, void *scratch, bool have_sums, double *res, double *report,
+                     uint64_t *chosen, cudaStream_t st) {
+  const RefitBufs b = carve(scratch, S->N, cap);
+  const FeatTable F = table_of(S);
+  if (!have_sums) cudaMemsetAsync(b.outx, 0, 64 * (size_t)cap, st);
+  note_launches(5);
+  switch (nf) {
+    case 0: fit_nf<0>(F, S, fid, cand, cap, n_dev, b, st); break;
+    case 1: fit_nf<1>(F, S, fid, cand, cap, n_dev, b, st); break;
+    case 2: fit_nf<2>(F, S, fid, cand, cap, n_dev, b, st); break;
+    default: fit_nf<3>(F, S, fid, cand, cap, n_dev, b, st); break;
+  }
+  k_argmin<<<1, 1024, 0, st>>>(b.rm, cand, cap, b.best, b.beta, report, n_dev, chosen);
+  k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, b.fc, nf, cand, b.best, b.beta, res);
 }
 
 // Index of the smallest RMSE (ties: lower id); one block.  report (when not
@@ -473,43 +745,7 @@ __global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const doub
 }
 
 // ------------------------------------------------ refits chained on the device
-
-size_t refit_chain_bytes(int64_t N, int64_t cap) {
-  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
-  return r(8 * (size_t)N * kMaxP) * 2 + r(8 * N) + r(8 * kPreSize) + r(8 * cap) + r(8 * (size_t)cap * (kMaxP + 1)) +
-         r(8);
-}
-
-// One refit step with everything on the device: candidates cand[0..*n_dev)
-// (at most cap), fixed ids fid[0..nf) (device), the chosen id written to
-// *chosen, the residual y - fit to res, the winner's report (index, id,
-// rmse, coefficients) to report.  scratch: refit_chain_bytes(N, cap) bytes.
-void refit_chain(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
-                 const int64_t *n_dev, void *scratch, double *res, double *report, uint64_t *chosen,
-                 cudaStream_t st) {
-  const int64_t N = S->N;
-  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
-  char *base = static_cast<char *>(scratch);
-  double *fc = reinterpret_cast<double *>(base);
-  base += r(8 * (size_t)N * kMaxP);
-  double *fcc = reinterpret_cast<double *>(base);
-  base += r(8 * (size_t)N * kMaxP);
-  double *ycc = reinterpret_cast<double *>(base);
-  base += r(8 * N);
-  double *pre = reinterpret_cast<double *>(base);
-  base += r(8 * kPreSize);
-  double *rm = reinterpret_cast<double *>(base);
-  base += r(8 * cap);
-  double *beta = reinterpret_cast<double *>(base);
-  base += r(8 * (size_t)cap * (kMaxP + 1));
-  int64_t *best = reinterpret_cast<int64_t *>(base);
-  const FeatTable F = table_of(S);
-  note_launches(4 + (nf ? 1 : 0));
-  if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
-  launch_fits(F, S, nf, y, fc, fid, cand, cap, n_dev, fcc, ycc, pre, rm, beta, st);
-  k_argmin<<<1, 1024, 0, st>>>(rm, cand, cap, best, beta, report, n_dev, chosen);
-  k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
-}
+// (refit_chain_prep / refit_chain_fit above)
 
 static inline long long __double_as_longlong_host(double x) {
   long long v;
@@ -534,7 +770,8 @@ dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, 
         set_error("candidate id out of range");
         return DSE_ERANGE;
       }
-  // one scratch block: y, fixed ids, fixed columns, candidates, rmse, beta, best, residual
+  // one scratch block: the refit step's buffers, then y, fixed ids,
+  // candidates, the report and the residual
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -544,24 +781,17 @@ dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, 
   // inputs already on the device are read in place; a device residual
   // buffer is written in place (the call waits before it returns)
   const bool res_dev = residual && is_device_pointer(residual);
-  size_t o_y = take(d->y_on_device ? 0 : 8 * N), o_fid = take(8 * 4), o_fc = take(8 * (size_t)N * 4),
-         o_c = take(d->cand_on_device ? 0 : 8 * nc), o_r = take(8 * nc), o_b = take(8 * (size_t)nc * (kMaxP + 1)),
-         o_best = take(8), o_rep = take(8 * (kMaxP + 4)), o_res = take(res_dev ? 0 : 8 * N),
-         o_fcc = take(8 * (size_t)N * kMaxP), o_ycc = take(8 * N), o_pre = take(8 * kPreSize);
+  const int64_t cap = nc > 0 ? nc : 1;
+  size_t o_chain = take(refit_chain_bytes(N, cap)), o_y = take(d->y_on_device ? 0 : 8 * N), o_fid = take(8 * 4),
+         o_c = take(d->cand_on_device ? 0 : 8 * nc), o_rep = take(8 * (kMaxP + 4)),
+         o_res = take(res_dev ? 0 : 8 * N);
   char *base = nullptr;
   DSE_TRY(dmalloc(reinterpret_cast<void **>(&base), off, "refit scratch"));
   const double *y = d->y_on_device ? d->y : reinterpret_cast<double *>(base + o_y);
   uint64_t *fid = reinterpret_cast<uint64_t *>(base + o_fid);
-  double *fc = reinterpret_cast<double *>(base + o_fc);
   const uint64_t *cand = d->cand_on_device ? d->cand : reinterpret_cast<uint64_t *>(base + o_c);
-  double *rm = reinterpret_cast<double *>(base + o_r);
-  double *beta = reinterpret_cast<double *>(base + o_b);
-  int64_t *best = reinterpret_cast<int64_t *>(base + o_best);
   double *rep = reinterpret_cast<double *>(base + o_rep);
   double *res = res_dev ? residual : reinterpret_cast<double *>(base + o_res);
-  double *fcc = reinterpret_cast<double *>(base + o_fcc);
-  double *ycc = reinterpret_cast<double *>(base + o_ycc);
-  double *pre = reinterpret_cast<double *>(base + o_pre);
   cudaError_t e = cudaSuccess;
   if (!d->y_on_device)
     e = cudaMemcpyAsync(const_cast<double *>(y), d->y, 8 * N, cudaMemcpyHostToDevice, st);
@@ -572,12 +802,8 @@ dse_status refit_impl(dse_space *S, const dse_refit_desc *d, uint64_t *best_id, 
     dfree(base);
     return cuda_status(e, "refit upload");
   }
-  const FeatTable F = table_of(S);
-  note_launches(4 + (nf ? 1 : 0));
-  if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
-  launch_fits(F, S, nf, y, fc, fid, cand, nc, nullptr, fcc, ycc, pre, rm, beta, st);
-  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, rep, nullptr, nullptr);
-  k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
+  refit_chain_prep(S, y, fid, nf, base + o_chain, cap, st);
+  refit_chain_fit(S, y, fid, nf, cand, nc, nullptr, base + o_chain, false, res, rep, nullptr, st);
   // one asynchronous copy of the winner's report (and of a host residual), one sync
   double *h = static_cast<double *>(pinned_staging(8 * (kMaxP + 4)));
   if (!h) {

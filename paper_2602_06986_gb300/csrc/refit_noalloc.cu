@@ -8,6 +8,8 @@
 // owned by their own pool or accounted against a hard budget, and paths that
 // run after the caller has reserved the whole device.  The price is a fixed
 // ceiling on the problem size and one shared scratch area per device.
+#include <string.h>
+
 #include <mutex>
 
 #include "dse_internal.cuh"
@@ -17,21 +19,19 @@ namespace dse {
 
 FeatTable table_of(const dse_space *S);
 
-// The refit kernels of refit.cu (same definitions, launched here on the
-// static scratch).
-__global__ void k_columns(FeatTable F, RungGeom G, int64_t n_stored, const uint64_t *ids, int n, double *out);
-__global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double *y, const double *fixed_cols, int nf,
-                        const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand, double *rmse_out,
-                        double *beta_out);
-__global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
-                         double *report, const int64_t *n_dev, uint64_t *chosen);
-__global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const double *y, const double *fixed_cols,
-                           int nf, const uint64_t *cand, const int64_t *best, const double *beta_all, double *res);
+// The refit steps of refit.cu (the same kernels as dse_ls_refit, so the two
+// agree to the bit), launched here on the static scratch.
+size_t refit_chain_bytes(int64_t N, int64_t cap);
+void refit_chain_prep(dse_space *S, const double *y, const uint64_t *fid, int nf, void *scratch, int64_t cap,
+                      cudaStream_t st);
+void refit_chain_fit(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
+                     const int64_t *n_dev, void *scratch, bool have_sums, double *res, double *report,
+                     uint64_t *chosen, cudaStream_t st);
 
 namespace {
 
 constexpr int kCoef = 5;                       // intercept + up to 4 columns
-constexpr size_t kScratchBytes = 4u << 20;     // 4 MiB per device
+constexpr size_t kScratchBytes = 8u << 20;     // 8 MiB per device
 constexpr int64_t kMaxSamples = 32768;
 constexpr int64_t kMaxCand = 16384;
 constexpr int kMaxDevices = 64;
@@ -94,15 +94,16 @@ dse_status refit_noalloc_impl(dse_space *S, const dse_refit_desc *d, uint64_t *b
         set_error("candidate id out of range");
         return DSE_ERANGE;
       }
-  // layout: y, fixed ids, fixed columns, candidates, rmse, beta, best, residual
+  // layout: the refit step's buffers, then y, fixed ids, candidates, the
+  // winner's report and the residual
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off += round256(bytes);
     return o;
   };
-  const size_t o_y = take(8 * N), o_fid = take(8 * 4), o_fc = take(8 * (size_t)N * 4), o_c = take(8 * nc),
-               o_r = take(8 * nc), o_b = take(8 * (size_t)nc * kCoef), o_best = take(8), o_res = take(8 * N);
+  const size_t o_chain = take(refit_chain_bytes(N, nc)), o_y = take(8 * N), o_fid = take(8 * 4), o_c = take(8 * nc),
+               o_rep = take(8 * (kCoef + 3)), o_res = take(8 * N);
   if (off > kScratchBytes) {
     set_error("no-alloc refit needs %zu bytes of scratch, the fixed area holds %zu", off, kScratchBytes);
     return DSE_EOVERFLOW;
@@ -112,43 +113,38 @@ dse_status refit_noalloc_impl(dse_space *S, const dse_refit_desc *d, uint64_t *b
   char *base = static_cast<char *>(vbase);
   double *y = reinterpret_cast<double *>(base + o_y);
   uint64_t *fid = reinterpret_cast<uint64_t *>(base + o_fid);
-  double *fc = reinterpret_cast<double *>(base + o_fc);
   uint64_t *cand = reinterpret_cast<uint64_t *>(base + o_c);
-  double *rm = reinterpret_cast<double *>(base + o_r);
-  double *beta = reinterpret_cast<double *>(base + o_b);
-  int64_t *best = reinterpret_cast<int64_t *>(base + o_best);
+  double *rep = reinterpret_cast<double *>(base + o_rep);
   double *res = reinterpret_cast<double *>(base + o_res);
-  // Every kernel below writes all it later reads (columns, one RMSE and one
-  // coefficient row per candidate, the argmin slot, the residual), so nothing
-  // left by an earlier call is read; the argmin slot is still cleared so that
-  // a failed launch cannot report an earlier call's pick.
-  cudaError_t e = cudaMemsetAsync(best, 0xff, 8, st);
+  // Every kernel writes all it later reads, so nothing left by an earlier
+  // call is read; the report is still cleared so that a failed launch cannot
+  // return an earlier call's pick.
+  cudaError_t e = cudaMemsetAsync(rep, 0xff, 8 * (kCoef + 3), st);
   if (!e) e = cudaMemcpyAsync(y, d->y, 8 * N, cudaMemcpyDefault, st);
   if (!e && nf) e = cudaMemcpyAsync(fid, d->fixed, 8 * nf, cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemcpyAsync(cand, d->cand, 8 * nc, cudaMemcpyDefault, st);
   if (e) return cuda_status(e, "no-alloc refit upload");
-  const FeatTable F = table_of(S);
-  note_launches(3 + (nf ? 1 : 0));
-  if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, fc);
-  k_refit<<<(unsigned)((nc * 32 + 255) / 256), 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, fid, cand, nc, rm, beta);
-  k_argmin<<<1, 1024, 0, st>>>(rm, cand, nc, best, beta, nullptr, nullptr, nullptr);
-  k_residual<<<64, 256, 0, st>>>(F, S->geom, S->n, y, fc, nf, cand, best, beta, res);
-  int64_t hb = -1;
-  e = cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st);
+  refit_chain_prep(S, y, fid, nf, base + o_chain, nc, st);
+  refit_chain_fit(S, y, fid, nf, cand, nc, nullptr, base + o_chain, false, res, rep, nullptr, st);
+  double h[kCoef + 3];
+  e = cudaMemcpyAsync(h, rep, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (!e) e = cudaStreamSynchronize(st);
   if (e) return cuda_status(e, "no-alloc refit");
+  long long hb, hid;
+  memcpy(&hb, &h[0], 8);
+  memcpy(&hid, &h[1], 8);
   if (hb < 0) {
     set_error("no candidate gives a full-rank fit");
     return DSE_EINVAL;
   }
-  double hb_beta[kCoef];
-  e = cudaMemcpy(best_rmse, rm + hb, 8, cudaMemcpyDeviceToHost);
-  if (!e) e = cudaMemcpy(best_id, cand + hb, 8, cudaMemcpyDeviceToHost);
-  if (!e) e = cudaMemcpy(hb_beta, beta + hb * kCoef, sizeof(hb_beta), cudaMemcpyDeviceToHost);
-  if (!e && residual) e = cudaMemcpy(residual, res, 8 * N, cudaMemcpyDefault);
-  if (e) return cuda_status(e, "no-alloc refit fetch");
+  *best_id = (uint64_t)hid;
+  *best_rmse = h[2];
+  if (residual) {
+    e = cudaMemcpy(residual, res, 8 * N, cudaMemcpyDefault);
+    if (e) return cuda_status(e, "no-alloc refit fetch");
+  }
   if (coefs)
-    for (int c = 0; c < nf + 2; ++c) coefs[c] = hb_beta[c];
+    for (int c = 0; c < nf + 2; ++c) coefs[c] = h[3 + c];
   return DSE_OK;
 }
 

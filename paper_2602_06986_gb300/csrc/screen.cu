@@ -1036,6 +1036,55 @@ __global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const Sc
   }
 }
 
+// The same decision and score for screens with one target (every problem of
+// a batched screen too), in one pass over the samples: the centred numerator
+// follows from the shifted sums, sum (v - vbar) y = sum (v - c) y -
+// (vbar - c) sum y, with sum y accumulated alongside.
+__global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const ScreenArgs *batch) {
+  __shared__ double sm[(kEsc / 32) * 6];
+  const unsigned n = min(*A0.esc_count, (unsigned)A0.esc_cap);
+  for (unsigned w = blockIdx.x; w < n; w += gridDim.x) {
+    const ScreenArgs &A = batch ? batch[A0.esc_prob[w]] : A0;
+    const int64_t N = A.N;
+    const uint64_t gid = A0.esc_id[w];
+    int op;
+    int64_t a, b;
+    decode_gid(A, gid, &op, &a, &b);
+    const double c = cand_value64(A.F, A.G, A.n_stored, gid, 0, op, a, b);
+    const double *y = A.y64 + (int64_t)A.t0 * A.ldy;
+    // sum (v-c), sum (v-c)^2, sum v^2, non-finite count, sum (v-c) y, sum y
+    double st[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t s = threadIdx.x; s < N; s += kEsc) {
+      const double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
+      if (!isfinite(v)) st[3] += 1.0;
+      const double d = v - c;
+      st[0] += d;
+      st[1] = fma(d, d, st[1]);
+      st[2] = fma(v, v, st[2]);
+      st[4] = fma(d, y[s], st[4]);
+      st[5] += y[s];
+    }
+    block_sum64<6>(st, sm);
+    const double sxx = st[1] - st[0] * (st[0] / (double)N);
+    int good = st[3] == 0.0 && isfinite(sxx);
+    if (good && A.fmin_std_rel64 >= 0.0)
+      good = __dsqrt_rn(fmax(sxx, 0.0) / (double)N) > A.fmin_std_rel64 * __dsqrt_rn(st[2] / (double)N);
+    if (threadIdx.x == 0) {
+      atomicAdd(&A.stats[good ? ST_REASON0 + DSE_VALID : ST_REASON0 + DSE_R_REALISED], 1ull);
+      if (good) atomicAdd(&A.stats[ST_EVALUATED], 1ull);
+      if (good && sxx > 0.0) {
+        const double err = (double)(N / kEsc + 64) * 1.1102230246251565e-16 * 16.0;
+        const double dm = st[0] / (double)N;  // vbar - c
+        const double sc = fabs(st[4] - dm * st[5]) / sqrt(sxx);
+        const float sf = (float)sc;
+        const float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+        push_one(A.B, A.t0, gid, sf, ef);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ launchers
 
 template <typename R, int NT>
@@ -1160,7 +1209,10 @@ void launch_pairlist_batched(int prec64, const ScreenArgs *args, const int2 *pai
 
 void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st, const ScreenArgs *batch) {
   note_launches(1);
-  k_escalate<<<sms * 8, kEsc, 0, st>>>(A, batch);
+  if (batch || A.T == 1)
+    k_escalate1<<<sms * 8, kEsc, 0, st>>>(A, batch);
+  else
+    k_escalate<<<sms * 8, kEsc, 0, st>>>(A, batch);
 }
 
 void launch_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,

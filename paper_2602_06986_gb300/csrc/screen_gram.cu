@@ -44,10 +44,12 @@
 //               K-major core-matrix layout), 4-stage ring;
 //   warp 1      TMEM allocation (512 columns: two 256-column accumulators)
 //               and the MMA issuer: 2 k-steps x 3 products per chunk;
-//   warps 2-5   epilogue: warp w reads the TMEM lanes of quadrant w % 4,
+//   warps 2-9   epilogue: warp w reads the TMEM lanes of quadrant w % 4,
 //               which hold its five a-features' rows, 32 columns at a time
-//               through a private shared-memory patch, and scores the 120
-//               candidates (5 a x 8 b x 3 slots) of each patch.
+//               (every other patch: two warps per quadrant) through a private
+//               shared-memory patch, and scores the 120 candidates (5 a x 8 b
+//               x 3 slots) of each patch from a private copy of the 37
+//               features' records (loaded while the tile's MMAs run).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -69,12 +71,13 @@ constexpr int FA = 20;  // a-features per tile
 constexpr int FB = 64;  // b-features per tile
 constexpr int FW = 5;   // a-features per epilogue warp (6 rows each)
 constexpr int M = 128, NCOL = 256;
-constexpr int NS = 4;
+constexpr int NS = 3;
 constexpr uint32_t A_HALF = M * tc::KC * 2;     // hi or lo part of an a-image chunk
 constexpr uint32_t B_HALF = NCOL * tc::KC * 2;  // hi or lo part of a b-image chunk
 constexpr uint32_t A_IMG = 2 * A_HALF, B_IMG = 2 * B_HALF;
 constexpr uint32_t STAGE = A_IMG + B_IMG;
-constexpr int THREADS = 6 * 32;
+constexpr int EPI = 8;  // epilogue warps: two per TMEM lane quadrant
+constexpr int THREADS = (2 + EPI) * 32;
 constexpr uint32_t kWait = 1u << 22;
 constexpr int EC = 32;  // TMEM columns per epilogue patch (8 b-features)
 
@@ -84,13 +87,26 @@ __host__ __device__ inline int arow(int f, int t) { return 32 * (f / FW) + 6 * (
 // Column of b-feature g (0..63), type t (0..3: q, q^2 of x, then of 1/x).
 __host__ __device__ inline int bcol(int g, int t) { return 4 * g + t; }
 
+// What the epilogue reads of a feature, copied once per tile into the warp's
+// own shared-memory cache (5 a-features + the 32 b-features of its patches).
+struct EpiFeat {
+  float4 fa;     // {mean, mean of 1/x, RU max|x|, RD max|x|}
+  float2 fr;     // {RU 1/min|x|, RD 1/min|x|}
+  uint32_t flags;
+  int32_t cplx;
+  float c[2], s1[2], s2[2], n1[2], n2[2], nu[2];  // GramFeat
+  float sy[2], ny[2];                             // GramTgt
+};
+constexpr int NCACHE = FW + 32;
+
 struct Shared {
   uint64_t full[NS], empty[NS];
   uint64_t acc_full[2], acc_empty[2];
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
-  float E[4][32][EC + 1];  // each epilogue warp's patch: its 32 lanes x 32 columns
+  float E[EPI][32][EC + 1];        // each epilogue warp's patch: its 32 lanes x 32 columns
+  EpiFeat cache[EPI][NCACHE];      // each epilogue warp's feature records
 };
 
 constexpr size_t shared_bytes() { return (sizeof(Shared) + 1023) / 1024 * 1024; }
@@ -147,6 +163,19 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Compensated FP32 accumulation (TwoSum: s + c carries the exact sum of
+// the terms to a few units in the last place of the result).
+struct Comp32 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 template <int NV>
 __device__ __forceinline__ void gram_block_sum(double (&v)[NV], double *sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -180,7 +209,10 @@ __global__ void __launch_bounds__(128) k_gram_space(FeatTable F, int nchunks, un
   const bool ok[2] = {okx, okr};
   const int64_t gb = f / gram::FB;
   const int g = (int)(f % gram::FB);
-  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // per family: s1, s2, s4, su2 (uncentred), +1 spare
+  // per family: sum p and sum p^2 (compensated), sum p^4 and sum (c + p)^2
+  // (plain FP32: they only bound norms, with a margin for their rounding)
+  Comp32 cs1[2], cs2[2];
+  float s4[2] = {0.f, 0.f}, su2[2] = {0.f, 0.f};
   const int64_t groups = (int64_t)nchunks * (tc::KC / 8);
   for (int64_t gi = threadIdx.x; gi < groups; gi += blockDim.x) {
     const int64_t s0 = gi * 8;
@@ -193,12 +225,11 @@ __global__ void __launch_bounds__(128) k_gram_space(FeatTable F, int nchunks, un
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         p2[e] = p[e] * p[e];
-        const double pd = (double)p[e];
-        acc[5 * fam + 0] += pd;
-        acc[5 * fam + 1] = fma(pd, pd, acc[5 * fam + 1]);
-        acc[5 * fam + 2] = fma((double)p2[e], (double)p2[e], acc[5 * fam + 2]);
-        const double ud = (double)p[e] + (double)c[fam] * (ok[fam] && s0 + e < F.N ? 1.0 : 0.0);
-        acc[5 * fam + 3] = fma(ud, ud, acc[5 * fam + 3]);
+        cs1[fam].add(p[e]);
+        cs2[fam].add(p2[e]);
+        s4[fam] = fmaf(p2[e], p2[e], s4[fam]);
+        const float uv = (ok[fam] && s0 + e < F.N) ? p[e] + c[fam] : 0.f;
+        su2[fam] = fmaf(uv, uv, su2[fam]);
       }
       uint4 h, l;
       split8(p, h, l);
@@ -211,6 +242,8 @@ __global__ void __launch_bounds__(128) k_gram_space(FeatTable F, int nchunks, un
       *reinterpret_cast<uint4 *>(base + gram::B_HALF + o2) = l;
     }
   }
+  double acc[10] = {cs1[0].value(), cs2[0].value(), (double)s4[0], (double)su2[0], 0.0,
+                    cs1[1].value(), cs2[1].value(), (double)s4[1], (double)su2[1], 0.0};
   gram_block_sum<10>(acc, sm);
   if (threadIdx.x == 0) {
     GramFeat o{};
@@ -218,9 +251,12 @@ __global__ void __launch_bounds__(128) k_gram_space(FeatTable F, int nchunks, un
       o.c[fam] = c[fam];
       o.s1[fam] = (float)acc[5 * fam + 0];
       o.s2[fam] = (float)acc[5 * fam + 1];
-      o.n1[fam] = __double2float_ru(sqrt(acc[5 * fam + 1]) * (1.0 + 1e-15));
-      o.n2[fam] = __double2float_ru(sqrt(acc[5 * fam + 2]) * (1.0 + 1e-15));
-      o.nu[fam] = __double2float_ru(sqrt(acc[5 * fam + 3]) * (1.0 + 1e-15));
+      // the FP32 partial sums of squares are low by at most (terms per
+      // thread + 2) u of themselves
+      const double marg = 1.0 + ((double)groups * 8.0 / blockDim.x + 10.0) * 5.9604644775390625e-8;
+      o.n1[fam] = __double2float_ru(sqrt(acc[5 * fam + 1] * marg) * (1.0 + 1e-15));
+      o.n2[fam] = __double2float_ru(sqrt(acc[5 * fam + 2] * marg) * (1.0 + 1e-15));
+      o.nu[fam] = __double2float_ru(sqrt(acc[5 * fam + 3] * marg) * (1.0 + 1e-15));
       o.ok[fam] = ok[fam] ? 1 : 0;
     }
     gf[f] = o;
@@ -237,7 +273,9 @@ __global__ void __launch_bounds__(128) k_gram_arows(FeatTable F, int nchunks, co
   const GramFeat G = gf[f];
   const int64_t ab = f / gram::FA;
   const int fa = (int)(f % gram::FA);
-  double acc[4] = {0, 0, 0, 0};  // per family: sum p y, sum (p y)^2
+  // per family: sum p y (compensated) and sum (p y)^2 (plain FP32, a norm)
+  Comp32 csy[2];
+  float sq[2] = {0.f, 0.f};
   const int64_t groups = (int64_t)nchunks * (tc::KC / 8);
   for (int64_t gi = threadIdx.x; gi < groups; gi += blockDim.x) {
     const int64_t s0 = gi * 8;
@@ -254,8 +292,8 @@ __global__ void __launch_bounds__(128) k_gram_arows(FeatTable F, int nchunks, co
       for (int e = 0; e < 8; ++e) {
         p2[e] = p[e] * p[e];
         py[e] = p[e] * y[e];
-        acc[2 * fam + 0] = fma((double)p[e], (double)y[e], acc[2 * fam + 0]);
-        acc[2 * fam + 1] = fma((double)py[e], (double)py[e], acc[2 * fam + 1]);
+        csy[fam].add(py[e]);
+        sq[fam] = fmaf(py[e], py[e], sq[fam]);
       }
       uint4 h, l;
       const float *rows[3] = {p, p2, py};
@@ -271,12 +309,14 @@ __global__ void __launch_bounds__(128) k_gram_arows(FeatTable F, int nchunks, co
       }
     }
   }
+  double acc[4] = {csy[0].value(), (double)sq[0], csy[1].value(), (double)sq[1]};
   gram_block_sum<4>(acc, sm);
   if (threadIdx.x == 0) {
     GramTgt o;
     for (int fam = 0; fam < 2; ++fam) {
+      const double marg = 1.0 + ((double)groups * 8.0 / blockDim.x + 10.0) * 5.9604644775390625e-8;
       o.sy[fam] = (float)acc[2 * fam];
-      o.ny[fam] = __double2float_ru(sqrt(acc[2 * fam + 1]) * (1.0 + 1e-15));
+      o.ny[fam] = __double2float_ru(sqrt(acc[2 * fam + 1] * marg) * (1.0 + 1e-15));
     }
     gt[f] = o;
   }
@@ -292,17 +332,16 @@ struct GramCand {
 // Score interval of v = u w from the contraction entries (G11, G22, G12,
 // G21, H) and the two features' sums; family fu of the a-feature, fw of the
 // b-feature; kappa of the evaluation error.
-// (The feature records are read in place: a run-time family index into a
+// (The cached records are read in place: a run-time family index into a
 // register copy would live in local memory.)
-__device__ __forceinline__ GramCand gram_score(const GramFeat *Fa, const GramTgt *Ta, int fu, const GramFeat *Fb,
-                                               const GramTgt *Tb, int fw, float G11, float G22, float G12, float G21,
-                                               float H, float kappa, float delta, float N, float invN, float ysum,
-                                               float fmin) {
+__device__ __forceinline__ GramCand gram_score(const gram::EpiFeat *Fa, int fu, const gram::EpiFeat *Fb, int fw,
+                                               float G11, float G22, float G12, float G21, float H, float kappa,
+                                               float delta, float N, float invN, float ysum, float fmin) {
   const float u = 5.9604644775390625e-8f;
   GramCand o;
   const float cu = Fa->c[fu], cw = Fb->c[fw];
-  const float P1 = Fa->s1[fu], P2 = Fa->s2[fu], PY = Ta->sy[fu];
-  const float Q1 = Fb->s1[fw], Q2 = Fb->s2[fw], QY = Tb->sy[fw];
+  const float P1 = Fa->s1[fu], P2 = Fa->s2[fu], PY = Fa->sy[fu];
+  const float Q1 = Fb->s1[fw], Q2 = Fb->s2[fw], QY = Fb->sy[fw];
   // statistics of v - k, k = cu cw
   const float t1a = cu * Q1, t1b = cw * P1;
   const float S1 = t1a + t1b + G11;
@@ -316,12 +355,15 @@ __device__ __forceinline__ GramCand gram_score(const GramFeat *Fa, const GramTgt
   const float acu = fabsf(cu), acw = fabsf(cw);
   const float dG11 = delta * Fa->n1[fu] * Fb->n1[fw], dG22 = delta * Fa->n2[fu] * Fb->n2[fw];
   const float dG12 = delta * Fa->n1[fu] * Fb->n2[fw], dG21 = delta * Fa->n2[fu] * Fb->n1[fw];
-  const float dH = delta * Ta->ny[fu] * Fb->n1[fw];
+  const float dH = delta * Fa->ny[fu] * Fb->n1[fw];
   const float dS1 = (dG11 + 10.f * u * (fabsf(t1a) + fabsf(t1b) + fabsf(G11))) * 1.01f;
   const float dS2 = (dG22 + 2.f * acu * acw * dG11 + 2.f * acu * dG12 + 2.f * acw * dG21 +
                      12.f * u * (t2a + t2b + fabsf(G22) + fabsf(t2c) + fabsf(t2d) + fabsf(t2e))) *
                     1.01f;
-  const float dSy = (dH + 10.f * u * (fabsf(tya) + fabsf(tyb) + fabsf(H))) * 1.01f;
+  // (the target sums come from the rounded products p y: u |p|_2 each)
+  const float dSy =
+      (dH + 10.f * u * (fabsf(tya) + fabsf(tyb) + fabsf(H)) + 1.01f * u * (acu * Fb->n1[fw] + acw * Fa->n1[fu])) *
+      1.01f;
   // centred sum of squares and its interval
   const float mean = S1 * invN;
   const float Sxx = fmaf(-S1, mean, S2);
@@ -382,6 +424,33 @@ __device__ __forceinline__ GramCand gram_score(const GramFeat *Fa, const GramTgt
   return o;
 }
 
+// A-priori tests of op(ia, ib) for a*b, a/b, b/a from the cached records:
+// the same tests, in the same order and arithmetic, as binary_apriori_W
+// (complexity, user rules, divisor domain, FP32 directed-rounding magnitude
+// interval with the exact FP64 test when it straddles the limit).
+__device__ __forceinline__ int gram_apriori(const ScreenArgs &A, int opc, int64_t ia, int64_t ib,
+                                            const gram::EpiFeat &a, const gram::EpiFeat &b) {
+  if (A.max_complexity > 0 && a.cplx + b.cplx + 1 > A.max_complexity) return DSE_R_COMPLEXITY;
+  if (rule_fails(A.F, opc, ia, ib)) return DSE_R_COMPLEXITY;
+  if (opc == DSE_OP_DIV && !(b.flags & F_MINABS_POS)) return DSE_R_DOMAIN;
+  if (opc == DSE_OP_RDIV && !(a.flags & F_MINABS_POS)) return DSE_R_DOMAIN;
+  float lo, hi;
+  if (opc == DSE_OP_MUL) {
+    lo = __fmul_rd(a.fa.w, b.fa.w);
+    hi = __fmul_ru(a.fa.z, b.fa.z);
+  } else if (opc == DSE_OP_DIV) {
+    lo = __fmul_rd(a.fa.w, b.fr.y);
+    hi = __fmul_ru(a.fa.z, b.fr.x);
+  } else {
+    lo = __fmul_rd(b.fa.w, a.fr.y);
+    hi = __fmul_ru(b.fa.z, a.fr.x);
+  }
+  if (hi <= A.fmax32_dn) return DSE_VALID;
+  if (lo > A.fmax32_up) return DSE_R_MAGNITUDE;
+  return domain_magnitude64(opc, A.F.min64[ia], A.F.max64[ia], A.F.minabs64[ia], A.F.maxabs64[ia],
+                            A.F.minabs64[ib], A.F.maxabs64[ib], A.fmax64, 0.0);
+}
+
 // ------------------------------------------------------------------ kernel
 
 struct GramArgs {
@@ -410,7 +479,7 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.acc_full[b], 1);
-      mbar_init(&sh.acc_empty[b], 4);
+      mbar_init(&sh.acc_empty[b], EPI);
     }
     mbar_init(&sh.drain, 1);
     sh.abort = 0;
@@ -511,9 +580,12 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lane quadrant = a-features 5q .. 5q+4
+    const int ew = warp - 2;         // 0 .. EPI-1
+    const int q = warp & 3;          // TMEM lane quadrant = a-features 5q .. 5q+4
+    const int h = ew >> 2;           // patches h, h+2, h+4, h+6
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    float(*E)[EC + 1] = sh.E[q];
+    float(*E)[EC + 1] = sh.E[ew];
+    EpiFeat *cache = sh.cache[ew];
     LaneStats ls;
     ls.zero();
     const float N = (float)A.N, invN = (float)A.invN;
@@ -523,11 +595,45 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
     int lt = 0;
     for (int tile = blockIdx.x; tile < GA.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
       const int2 tl = GA.tiles[tile];
+      // this warp's feature records: a-features 0..4, then the b-features of
+      // its four patches (8 each), while the tile's MMAs run
+      for (int e = lane; e < NCACHE; e += 32) {
+        int64_t f;
+        if (e < FW) {
+          f = (int64_t)tl.x * FA + q * FW + e;
+        } else {
+          const int k = e - FW;
+          f = (int64_t)tl.y * FB + (2 * (k >> 3) + h) * (EC / 4) + (k & 7);
+        }
+        if (f < n) {
+          EpiFeat c;
+          c.fa = A.F.fa[f];
+          c.fr = A.F.fr[f];
+          c.flags = A.F.flags[f];
+          c.cplx = A.F.cplx[f];
+          const GramFeat g = GA.gf[f];
+          const GramTgt t = GA.gt[f];
+#pragma unroll
+          for (int m = 0; m < 2; ++m) {
+            c.c[m] = g.c[m];
+            c.s1[m] = g.s1[m];
+            c.s2[m] = g.s2[m];
+            c.n1[m] = g.n1[m];
+            c.n2[m] = g.n2[m];
+            c.nu[m] = g.nu[m];
+            c.sy[m] = t.sy[m];
+            c.ny[m] = t.ny[m];
+          }
+          cache[e] = c;
+        }
+      }
+      __syncwarp();
       const uint32_t buf = lt & 1, ub = lt >> 1;
       if (!wait_warp(&sh.acc_full[buf], ub & 1)) break;
       fence_after();
       bool pushed_any = false;
-      for (int pc = 0; pc < NCOL / EC; ++pc) {
+      for (int pcl = 0; pcl < 4; ++pcl) {
+        const int pc = 2 * pcl + h;
         float v[EC];
         tmem_ld32(tmem + lane_base + buf * NCOL + pc * EC, v);
 #pragma unroll
@@ -549,19 +655,18 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
             const uint64_t pbase = A.G.um + (tri((uint64_t)i) + (uint64_t)j - A.G.tri_o) * (uint64_t)A.G.nb;
             gid = (uint64_t)A.n_stored + pbase + (uint64_t)pos;
             if (gid >= A.id_begin && gid < A.id_end) {
-              const float4 fa_a = A.F.fa[i], fa_b = A.F.fa[j];
-              EvalErr<float> ee{0.f, 0.f};
-              const int reason = binary_apriori_W<float>(A, opc, i, j, fa_a, fa_b, 0.f, 0.f, 0.f, &ee);
+              const EpiFeat &ca = cache[fi], &cb = cache[FW + pcl * 8 + gj];
+              const int reason = gram_apriori(A, opc, i, j, ca, cb);
               if (reason != DSE_VALID) {
                 ls.r[reason]++;
-              } else if (!((A.F.flags[i] & A.F.flags[j]) & F_FP32_SAFE)) {
+              } else if (!((ca.flags & cb.flags) & F_FP32_SAFE)) {
                 escalate(A, gid);
                 ls.escalated++;
               } else {
                 const int fu = slot == 2 ? 1 : 0, fw = slot == 1 ? 1 : 0;
-                const int ra = 6 * fi + 3 * fu, cb = 4 * gj + 2 * fw;
-                const GramCand gc = gram_score(GA.gf + i, GA.gt + i, fu, GA.gf + j, GA.gt + j, fw, E[ra][cb], E[ra + 1][cb + 1], E[ra][cb + 1],
-                                               E[ra + 1][cb], E[ra + 2][cb], slot == 0 ? 4.01f : 5.01f, GA.delta, N,
+                const int ra = 6 * fi + 3 * fu, cl = 4 * gj + 2 * fw;
+                const GramCand gc = gram_score(&ca, fu, &cb, fw, E[ra][cl], E[ra + 1][cl + 1], E[ra][cl + 1],
+                                               E[ra + 1][cl], E[ra + 2][cl], slot == 0 ? 4.01f : 5.01f, GA.delta, N,
                                                invN, ysum, fmin);
                 if (gc.realised == 0) {
                   ls.r[DSE_R_REALISED]++;
@@ -661,8 +766,23 @@ float gram_delta(int64_t N) {
   return (float)(4.0 * (2.0 * steps + 2.0) * u32 + 3.02 * 1.52587890625e-5 + 4.0 * u32);
 }
 
-// One screen's product/quotient slots: a-rows of the target into `scr`
-// (gram_screen_bytes), then the kernel over `tiles` (device, n_tiles).
+// One screen's a-images and target sums into `scr` (gram_screen_bytes).
+void launch_gram_arows(const ScreenArgs &A, const void *space_buf, void *scr, cudaStream_t st) {
+  const int64_t n = A.F.n, N = A.N;
+  const int nchunks = (int)((N + tc::KC - 1) / tc::KC);
+  const int64_t na = (n + gram::FA - 1) / gram::FA, nb = (n + gram::FB - 1) / gram::FB;
+  const unsigned char *bimg = static_cast<const unsigned char *>(space_buf);
+  const GramFeat *gf = reinterpret_cast<const GramFeat *>(bimg + (size_t)nb * nchunks * gram::B_IMG);
+  unsigned char *aimg = static_cast<unsigned char *>(scr);
+  GramTgt *gt = reinterpret_cast<GramTgt *>(aimg + (size_t)na * nchunks * gram::A_IMG);
+  // (every row the epilogue reads is written for every chunk; the unused
+  // rows only feed TMEM lanes that are never read)
+  note_launches(1);
+  k_gram_arows<<<(unsigned)n, 128, 0, st>>>(A.F, nchunks, A.y32 + (int64_t)A.t0 * A.ldy, gf, aimg, gt);
+}
+
+// One screen's product/quotient slots: the kernel over `tiles` (device,
+// n_tiles) after launch_gram_arows.
 dse_status launch_pair_gram(const ScreenArgs &A, const void *space_buf, void *scr, const int2 *tiles, int n_tiles,
                             int sms, cudaStream_t st) {
   if (n_tiles <= 0) return DSE_OK;
@@ -673,10 +793,7 @@ dse_status launch_pair_gram(const ScreenArgs &A, const void *space_buf, void *sc
   const GramFeat *gf = reinterpret_cast<const GramFeat *>(bimg + (size_t)nb * nchunks * gram::B_IMG);
   unsigned char *aimg = static_cast<unsigned char *>(scr);
   GramTgt *gt = reinterpret_cast<GramTgt *>(aimg + (size_t)na * nchunks * gram::A_IMG);
-  // (every row the epilogue reads is written for every chunk; the unused
-  // rows only feed TMEM lanes that are never read)
-  note_launches(2);
-  k_gram_arows<<<(unsigned)n, 128, 0, st>>>(A.F, nchunks, A.y32 + (int64_t)A.t0 * A.ldy, gf, aimg, gt);
+  note_launches(1);
   static bool attr[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);

@@ -63,6 +63,14 @@ struct SelectArgs {
   int64_t *out_n;
   double *max_eps;          // [lists] largest returned bound
   unsigned int *r_rank;     // [lists][cap] rank of each retained entry
+  // optional column sums for refits that follow the screen (one target,
+  // N <= 4096): the re-score of each entry also accumulates its shifted
+  // column against nx vectors; r_x [lists][cap][8] = {c, S1, S2, E_0.., 1},
+  // out_x [lists][k][8] the same in rank order (last field 0 when the entry
+  // was not re-scored)
+  const double *xv[4];
+  int32_t nx;
+  double *r_x, *out_x;
   unsigned long long *stats;
 };
 

@@ -215,7 +215,11 @@ __global__ void k_sel_classify(const SelectArgs S) {
     const bool need = S.all64 || und || e > kTol * s;
     S.r_need[r] = need ? 1 : 0;
     if (!need) S.r_key[r] = score_key((double)s);
-    if (need) {
+    // with refit sums requested every retained entry is a job (the entries
+    // that need no re-score keep their score and key: only their sums are
+    // taken)
+    if (S.r_x) S.r_x[r * 8 + 7] = 0.0;
+    if (need || S.r_x) {
       unsigned j = atomicAdd(S.n_jobs, 1u);
       S.job[j] = pos;
       S.job_list[j] = (uint32_t)l;
@@ -327,20 +331,39 @@ __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const 
     const int t_begin = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
     const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < NT ? A.T : NT) : 1;
     const double c = eval_op64(op, xa[0], xb[0]);
-    double acc[2 + NT];
+    double acc[NT == 1 ? 2 + kColVec : 2 + NT];
+    if (NT == 1) {
+      // the list's target, then the refit vectors (if any)
+      const double *vec[kColVec] = {A.y64 + (int64_t)t_begin * A.ldy, S.xv[0], S.xv[1], S.xv[2], S.xv[3]};
+      double a7[2 + kColVec];
+      col_sums_warp(A.F, op, a, b, N, c, vec, 1 + S.nx, a7, lane);
 #pragma unroll
-    for (int i = 0; i < 2 + NT; ++i) acc[i] = 0.0;
-    for (int64_t s = lane; s < N; s += 32) {
-      const double v = eval_op64(op, xa[s], xb[s]) - c;
-      acc[0] += v;
-      acc[1] = fma(v, v, acc[1]);
+      for (int i = 0; i < (NT == 1 ? 2 + kColVec : 2 + NT); ++i) acc[i] = a7[i];
+    } else {
 #pragma unroll
-      for (int t = 0; t < NT; ++t)
-        if (t < nt) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
+      for (int i = 0; i < 2 + NT; ++i) acc[i] = 0.0;
+      for (int64_t s = lane; s < N; s += 32) {
+        const double v = eval_op64(op, xa[s], xb[s]) - c;
+        acc[0] += v;
+        acc[1] = fma(v, v, acc[1]);
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+          if (t < nt) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2 + NT; ++i) acc[i] = warp_sum64(acc[i]);
     }
-#pragma unroll
-    for (int i = 0; i < 2 + NT; ++i) acc[i] = warp_sum64(acc[i]);
     if (lane == 0) {
+      if (NT == 1 && S.r_x) {
+        double *x = S.r_x + r * 8;
+        x[0] = c;
+        x[1] = acc[0];
+        x[2] = acc[1];
+        for (int m = 0; m < 4; ++m) x[3 + m] = m < S.nx ? acc[3 + m] : 0.0;
+        x[7] = 1.0;
+      }
+    }
+    if (lane == 0 && S.r_need[r]) {
       const double mean = acc[0] / (double)N;
       const double sxx = acc[1] - acc[0] * mean;
       double agg = 0.0;
@@ -424,6 +447,10 @@ __global__ void k_rank_write(const SelectArgs S) {
     if (rank >= nout) continue;
     const bool n64 = S.r_need[r] != 0;
     const size_t o = (size_t)l * S.k + rank;
+    if (S.out_x) {
+      const bool has = S.r_x[r * 8 + 7] != 0.0;
+      for (int m = 0; m < 8; ++m) S.out_x[o * 8 + m] = has ? S.r_x[r * 8 + m] : 0.0;
+    }
     S.out_id[o] = S.r_id[r];
     S.out_score[o] = n64 ? S.r_s64[r] : (double)S.r_s32[r];
     const double e = n64 ? S.r_e64[r] : (double)S.r_e32[r];
