@@ -225,20 +225,35 @@ uint64_t count_slots_mod(uint64_t x, int nb, const std::vector<int> &posset) {
   return c;
 }
 
+// Zero a screen's buffer counts, bound histograms, escalation count,
+// statistics and re-score job count.
+__global__ void k_screen_reset(unsigned *count, unsigned *hist, unsigned *hist_hi, unsigned *hist_c, int nl,
+                               unsigned *esc_count, unsigned long long *stats, unsigned *n_jobs) {
+  const int64_t nh = (int64_t)nl * kNumBins, nc = (int64_t)nl * kCoarse;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nh; e += (int64_t)gridDim.x * blockDim.x) {
+    hist[e] = 0u;
+    hist_hi[e] = 0u;
+    if (e < nc) hist_c[e] = 0u;
+    if (e < nl) count[e] = 0u;
+    if (e < ST_COUNT) stats[e] = 0ull;
+    if (e == 0) {
+      *esc_count = 0u;
+      *n_jobs = 0u;
+    }
+  }
+}
+
 static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_tiles_mul, void *scr_tiles_add,
                              ScreenArgs &A, SelectArgs &S, unsigned int *tile_ctr) {
   dse_space *sp = R->space;
   cudaStream_t st = R->stream;
   const int sms = sm_count();
   const int nl = R->n_lists;
-  DSE_CUDA(cudaMemsetAsync(A.B.count, 0, sizeof(unsigned) * nl, st));
-  DSE_CUDA(cudaMemsetAsync(A.B.hist, 0, sizeof(unsigned) * nl * kNumBins, st));
-  DSE_CUDA(cudaMemsetAsync(A.B.hist_hi, 0, sizeof(unsigned) * nl * kNumBins, st));
-  DSE_CUDA(cudaMemsetAsync(A.B.hist_c, 0, sizeof(unsigned) * nl * kCoarse, st));
-  DSE_CUDA(cudaMemsetAsync(A.esc_count, 0, sizeof(unsigned), st));
-  DSE_CUDA(cudaMemsetAsync(A.stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
-  DSE_CUDA(cudaMemsetAsync(S.n_jobs, 0, sizeof(unsigned), st));
   const int64_t launches0 = launches_so_far();
+  // the screen's counters and histograms, zeroed by one kernel
+  note_launches(1);
+  k_screen_reset<<<std::max(1, std::min(sms, (int)((nl * kNumBins + 255) / 256))), 256, 0, st>>>(
+      A.B.count, A.B.hist, A.B.hist_hi, A.B.hist_c, nl, A.esc_count, A.stats, S.n_jobs);
   // optional device timing of each kernel group
   const bool timing = (R->flags & DSE_FLAG_TIMING) != 0;
   cudaEvent_t ev_open = nullptr;
@@ -790,6 +805,24 @@ constexpr int kSmall = ST_COUNT + 5;  // per iteration: counters, overflow, buff
 // the reports once at the end.  An iteration whose candidate buffer
 // overflowed is repeated, with the rest of the loop, on the host-driven
 // path (wait, re-run from the thresholds reached, refit).
+// One iteration's small results into the loop's report rows (counters,
+// overflow flag, buffered count, list length, largest bound, error flag as
+// 64-bit words) and its list of ids, in one launch.
+__global__ void k_loop_snapshot(const unsigned long long *stats, const unsigned *overflow, const unsigned *buf_count,
+                                const int64_t *out_n, const double *max_eps, const int *err, const uint64_t *out_id,
+                                int64_t k, unsigned long long *small, uint64_t *ids) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ST_COUNT) small[t] = stats[t];
+  if (t == 0) {
+    small[ST_COUNT] = *overflow;
+    small[ST_COUNT + 1] = *buf_count;
+    small[ST_COUNT + 2] = (unsigned long long)*out_n;
+    small[ST_COUNT + 3] = (unsigned long long)__double_as_longlong(*max_eps);
+    small[ST_COUNT + 4] = (unsigned long long)(unsigned)*err;
+  }
+  for (int64_t i = t; i < k; i += (int64_t)gridDim.x * blockDim.x) ids[i] = out_id[i];
+}
+
 static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_loop_result *out, uint64_t *sis_ids,
                                      double *residual) {
   cudaStream_t st = (cudaStream_t)d->stream;
@@ -845,14 +878,10 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   DSE_CUDA(cudaMemsetAsync(ids, 0xFF, sizeof(uint64_t) * D * k, st));
 
   auto snapshot = [&](int it) -> dse_status {
-    unsigned long long *sm = small + (size_t)it * kSmall;
-    DSE_CUDA(cudaMemcpyAsync(sm, R->stats, 8 * ST_COUNT, cudaMemcpyDeviceToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT, R->overflow, 4, cudaMemcpyDeviceToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 1, R->buf_count, 4, cudaMemcpyDeviceToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 2, R->out_n, 8, cudaMemcpyDeviceToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 3, R->max_eps, 8, cudaMemcpyDeviceToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(sm + ST_COUNT + 4, R->err, 4, cudaMemcpyDeviceToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(ids + (size_t)it * k, R->out_id, 8 * k, cudaMemcpyDeviceToDevice, st));
+    note_launches(1);
+    k_loop_snapshot<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (k + 255) / 256)), 256, 0, st>>>(
+        R->stats, R->overflow, R->buf_count, R->out_n, R->max_eps, R->err, R->out_id, k,
+        small + (size_t)it * kSmall, ids + (size_t)it * k);
     return DSE_OK;
   };
   // before iteration it's screen: the fixed columns' fit, and the vectors

@@ -163,7 +163,7 @@ __global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double 
 // flight per SM than a warp per candidate when the candidate list is short).
 constexpr int kWide = 128;
 
-template <int NV>
+template <int NV, int THREADS = kWide>
 __device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -176,7 +176,7 @@ __device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
   for (int i = 0; i < NV; ++i) {
     double t = 0.0;
 #pragma unroll
-    for (int ww = 0; ww < kWide / 32; ++ww) t += sm[ww * NV + i];
+    for (int ww = 0; ww < THREADS / 32; ++ww) t += sm[ww * NV + i];
     v[i] = t;
   }
   __syncthreads();
@@ -199,19 +199,21 @@ constexpr int kPreL = kPreSize0, kPreBf = kPreL + kMaxP * kMaxP, kPreRss = kPreB
 
 // NF (the number of fixed columns) is a template argument so that every
 // per-column array stays in registers.
+constexpr int kPrep = kWide;  // threads of the (one-block) prep
+
 template <int NF>
-__global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const double *fixed_cols, int64_t N,
+__global__ void __launch_bounds__(kPrep) k_refit_prep(const double *y, const double *fixed_cols, int64_t N,
                                                       double *fcc, double *ycc, double *rc, double *pre) {
   constexpr int nf = NF;
-  __shared__ double sm[(kWide / 32) * (kMaxP * kMaxP + 3 * kMaxP)];
+  __shared__ double sm[(kPrep / 32) * (kMaxP * kMaxP + 3 * kMaxP)];
   __shared__ double s_beta[kMaxP + 1];
   double mv[kMaxP + 1] = {0, 0, 0, 0, 0};
-  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+  for (int64_t s = threadIdx.x; s < N; s += kPrep) {
 #pragma unroll
     for (int c = 0; c < nf; ++c) mv[c] += fixed_cols[(int64_t)c * N + s];
     mv[kMaxP] += y[s];
   }
-  block_sum_arr<kMaxP + 1>(mv, sm);
+  block_sum_arr<kMaxP + 1, kPrep>(mv, sm);
   double m[kMaxP];
 #pragma unroll
   for (int c = 0; c < kMaxP; ++c) m[c] = mv[c] / (double)N;
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
   double acc[kMaxP * kMaxP + 3 * kMaxP];
 #pragma unroll
   for (int i = 0; i < kMaxP * kMaxP + 3 * kMaxP; ++i) acc[i] = 0.0;
-  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+  for (int64_t s = threadIdx.x; s < N; s += kPrep) {
     double xc[kMaxP] = {0, 0, 0, 0};
 #pragma unroll
     for (int c = 0; c < nf; ++c) {
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
       acc[kMaxP * kMaxP + c] = fma(xc[c], yc, acc[kMaxP * kMaxP + c]);
     }
   }
-  block_sum_arr<kMaxP * kMaxP + 3 * kMaxP>(acc, sm);
+  block_sum_arr<kMaxP * kMaxP + 3 * kMaxP, kPrep>(acc, sm);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreMean + c] = m[c];
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
 #pragma unroll
   for (int c = 0; c < kMaxP; ++c) bfr[c] = s_beta[c];
   double q[2] = {0.0, 0.0};
-  for (int64_t s = threadIdx.x; s < N; s += kWide) {
+  for (int64_t s = threadIdx.x; s < N; s += kPrep) {
     double r = ycc[s];
 #pragma unroll
     for (int c = 0; c < nf; ++c) r = fma(-bfr[c], fcc[(int64_t)c * N + s], r);
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(kWide) k_refit_prep(const double *y, const dou
     q[0] = fma(r, r, q[0]);
     q[1] += r;
   }
-  block_sum_arr<2>(q, sm);
+  block_sum_arr<2, kPrep>(q, sm);
   if (threadIdx.x == 0) {
     pre[kPreRss] = q[0];
     pre[kPreSr] = q[1];
@@ -610,7 +612,7 @@ static RefitBufs carve(void *scratch, int64_t N, int64_t cap) {
 
 template <int NF>
 static void prep_nf(const dse_space *S, const double *y, const RefitBufs &b, cudaStream_t st) {
-  k_refit_prep<NF><<<1, kWide, 0, st>>>(y, b.fc, S->N, b.fcc, b.ycc, b.rc, b.pre);
+  k_refit_prep<NF><<<1, kPrep, 0, st>>>(y, b.fc, S->N, b.fcc, b.ycc, b.rc, b.pre);
 }
 
 // Fill the missing column sums, solve every fit, redo the flagged ones

@@ -37,31 +37,42 @@ __device__ __forceinline__ float hi_of(float s, float e) {
 }
 
 // Highest bin b of h[0..kNumBins) whose suffix count reaches k; *rank = k minus
-// the count above b.  One block of 1024 threads.
-__device__ int suffix_bin(const unsigned *h, unsigned long long k, unsigned long long *rank,
-                          unsigned long long *suf) {
-  for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) suf[b] = h[b];
-  __syncthreads();
-  // suffix sums (Hillis-Steele from the top)
-  for (int o = 1; o < kNumBins; o <<= 1) {
-    unsigned long long v[kNumBins / 1024];
-    for (int r = 0; r < kNumBins / 1024; ++r) {
-      int b = threadIdx.x + r * 1024;
-      v[r] = (b + o < kNumBins) ? suf[b + o] : 0ull;
-    }
-    __syncthreads();
-    for (int r = 0; r < kNumBins / 1024; ++r) suf[threadIdx.x + r * 1024] += v[r];
-    __syncthreads();
+// the count above b.  One block of 1024 threads: thread t owns kNumBins/1024
+// consecutive bins; the suffix sums over threads come from warp shuffles and
+// one pass over the 32 warp totals.
+__device__ int suffix_bin(const unsigned *h, unsigned long long k, unsigned long long *rank) {
+  constexpr int PER = kNumBins / 1024;
+  __syncthreads();  // a previous call's result has been read by every thread
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  unsigned long long c[PER], tot = 0;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    c[i] = h[t * PER + i];
+    tot += c[i];
   }
+  // suffix within the warp (lanes >= this one)
+  unsigned long long x = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o < 32) x += v;
+  }
+  __shared__ unsigned long long wsum[32];
   __shared__ int found;
-  if (threadIdx.x == 0) found = -1;
+  if (lane == 0) wsum[w] = x;
+  if (t == 0) found = -1;
   __syncthreads();
-  for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) {
-    unsigned long long above = b + 1 < kNumBins ? suf[b + 1] : 0ull;
-    if (suf[b] >= k && above < k) {
-      found = b;
-      *rank = k - above;
+  unsigned long long above_w = 0;  // all bins of the warps above this one
+  for (int q = w + 1; q < 32; ++q) above_w += wsum[q];
+  // count above this thread's highest bin, then walk its bins downwards
+  unsigned long long cum = above_w + (x - tot);
+#pragma unroll
+  for (int i = PER - 1; i >= 0; --i) {
+    if (cum < k && cum + c[i] >= k) {
+      found = t * PER + i;
+      *rank = k - cum;
     }
+    cum += c[i];
   }
   __syncthreads();
   return found;
@@ -69,7 +80,6 @@ __device__ int suffix_bin(const unsigned *h, unsigned long long k, unsigned long
 
 // 1) per list: entry count, overflow flag, bins and in-bin ranks of L and H.
 __global__ void __launch_bounds__(1024) k_sel_bins(const SelectArgs S) {
-  __shared__ unsigned long long suf[kNumBins];
   __shared__ unsigned long long rankL, rankH;
   const int l = blockIdx.x;
   const unsigned cnt = S.B.count[l];
@@ -80,8 +90,8 @@ __global__ void __launch_bounds__(1024) k_sel_bins(const SelectArgs S) {
     st.all_in = 1;
     st.binL = st.binH = -1;
   } else {
-    st.binL = suffix_bin(S.B.hist + (size_t)l * kNumBins, (unsigned long long)S.k, &rankL, suf);
-    st.binH = suffix_bin(S.B.hist_hi + (size_t)l * kNumBins, (unsigned long long)S.k + 1ull, &rankH, suf);
+    st.binL = suffix_bin(S.B.hist + (size_t)l * kNumBins, (unsigned long long)S.k, &rankL);
+    st.binH = suffix_bin(S.B.hist_hi + (size_t)l * kNumBins, (unsigned long long)S.k + 1ull, &rankH);
     st.rankL = (unsigned)rankL;
     st.rankH = (unsigned)rankH;
   }
