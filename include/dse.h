@@ -210,6 +210,10 @@ typedef struct {
    Gram contractions on the tensor cores (same results: the same bounds
    contract, the same FP64 re-score of the list). */
 #define DSE_FLAG_DIRECT 4
+/* Time only the product/quotient kernel group (kernel_ms[1]; the other
+   entries 0): two events per screen instead of five, for timing that kernel
+   inside a longer measured region.  DSE_FLAG_TIMING takes precedence. */
+#define DSE_FLAG_TIMING_MAIN 8
 
 dse_status dse_sis_screen(dse_space *space, const dse_screen_desc *desc, dse_result **out);
 void dse_result_free(dse_result *result);
@@ -233,7 +237,8 @@ typedef struct {
   double max_err_bound;    /* largest bound among returned scores            */
   int64_t valid_by_group[3];  /* valid candidates scored by the stored/unary,
                                  product/quotient and sum/difference kernels */
-  double kernel_ms[4];     /* with DSE_FLAG_TIMING: device time of the
+  double kernel_ms[4];     /* with DSE_FLAG_TIMING (DSE_FLAG_TIMING_MAIN:
+                              the second entry only): device time of the
                               stored/unary kernel (with the Gram operand
                               images when the products take that path), the
                               product/quotient kernel, the sum/difference
@@ -344,7 +349,8 @@ typedef struct {
   int32_t n_iter;         /* 1..4                                           */
   int64_t k;              /* retained candidates per iteration, >= 1        */
   int32_t precision;      /* DSE_PREC_FP32 / AUTO (FP32) or DSE_PREC_FP64   */
-  int32_t flags;          /* DSE_FLAG_TIMING: kernel_ms of each screen      */
+  int32_t flags;          /* DSE_FLAG_TIMING / _TIMING_MAIN: kernel_ms of
+                             each screen                                     */
   void *stream;           /* cudaStream_t                                   */
 } dse_loop_desc;
 

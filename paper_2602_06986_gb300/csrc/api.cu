@@ -255,24 +255,29 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
   k_screen_reset<<<std::max(1, std::min(sms, (int)((nl * kNumBins + 255) / 256))), 256, 0, st>>>(
       A.B.count, A.B.hist, A.B.hist_hi, A.B.hist_c, nl, A.esc_count, A.stats, S.n_jobs);
   // optional device timing of each kernel group
-  const bool timing = (R->flags & DSE_FLAG_TIMING) != 0;
+  const bool timing = (R->flags & (DSE_FLAG_TIMING | DSE_FLAG_TIMING_MAIN)) != 0;
+  const bool main_only = !(R->flags & DSE_FLAG_TIMING);
   cudaEvent_t ev_open = nullptr;
   int open_group = -1;
+  // one event per group boundary: it closes the open group and opens the
+  // next (main_only: events around group 1 only)
   auto mark = [&](int group) -> dse_status {
     if (!timing) return DSE_OK;
+    const bool need = !main_only || group == 1 || open_group == 1;
+    if (!need) {
+      open_group = group;
+      return DSE_OK;
+    }
     cudaEvent_t e;
     DSE_CUDA(cudaEventCreate(&e));
+    R->events.push_back(e);
     DSE_CUDA(cudaEventRecord(e, st));
     if (ev_open) R->timing.push_back({open_group, {ev_open, e}});
-    if (group >= 0) {
-      DSE_CUDA(cudaEventCreate(&ev_open));
-      DSE_CUDA(cudaEventRecord(ev_open, st));
-    } else {
-      ev_open = nullptr;
-    }
+    ev_open = group >= 0 && (!main_only || group == 1) ? e : nullptr;
     open_group = group;
     return DSE_OK;
   };
+
   if (plan.use_tc) DSE_TRY(run_tc_passes(R, plan, scr_tiles_mul, scr_tiles_add, A, sms, st, mark));
   for (int pass = 0; pass < (plan.use_tc ? 0 : plan.passes); ++pass) {
     A.t0 = pass * plan.nt;
@@ -498,6 +503,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   if (launch && !d->y_on_device) sc.add(&Yd, (size_t)T * d->ld_y);
   sc.add(&R->y64, (size_t)T * R->ldy);
   sc.add(&R->y32, (size_t)T * R->ldy);
+  sc.add(&R->ydf, (size_t)T * R->ldy);
   sc.add(&R->ysum32, (size_t)T);
   sc.add(&A.B.id, (size_t)n_lists * cap);
   sc.add(&A.B.score, (size_t)n_lists * cap);
@@ -569,7 +575,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   if (!e) e = cudaMemsetAsync(R->err, 0, sizeof(int), st);
   if (!e) e = cudaMemsetAsync(A.B.theta, 0, sizeof(float) * n_lists, st);
   if (e) return fail(cuda_status(e, "screen setup"));
-  if (launch) launch_targets(Ysrc, d->ld_y, (int)T, N, R->ldy, R->y64, R->y32, R->ysum32, R->err, st);
+  if (launch) launch_targets(Ysrc, d->ld_y, (int)T, N, R->ldy, R->y64, R->y32, R->ydf, R->ysum32, R->err, st);
   R->launches = launch ? 1 : 0;
   R->flags = d->flags;
 
@@ -584,6 +590,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   A.mode = d->mode;
   A.n_lists = n_lists;
   A.y32 = R->y32;
+  A.ydf = R->ydf;
   A.y64 = R->y64;
   A.ysum32 = R->ysum32;
   A.max_complexity = sp->max_complexity;
@@ -652,7 +659,7 @@ static dse_status screen_enqueue_target(dse_result *R, const double *Y, int64_t 
   Keep *k = reinterpret_cast<Keep *>(R->keep);
   DSE_CUDA(cudaMemsetAsync(R->err, 0, sizeof(int), st));
   DSE_CUDA(cudaMemsetAsync(k->A.B.theta, 0, sizeof(float) * R->n_lists, st));
-  launch_targets(Y, ld_y, R->T, R->space->N, R->ldy, R->y64, R->y32, R->ysum32, R->err, st);
+  launch_targets(Y, ld_y, R->T, R->space->N, R->ldy, R->y64, R->y32, R->ydf, R->ysum32, R->err, st);
   R->launches = 1;
   R->fetched = false;
   R->reruns = 0;
@@ -790,7 +797,8 @@ static dse_status dedup_screen(dse_space *sp, const dse_screen_desc *d, dse_resu
 size_t refit_chain_bytes(int64_t N, int64_t cap);
 void refit_chain_prep(dse_space *S, const double *y, const uint64_t *fid, int nf, void *scratch, int64_t cap,
                       cudaStream_t st);
-void refit_chain_vectors(void *scratch, int64_t N, int64_t cap, const double **vec, double **outx);
+void refit_chain_vectors(void *scratch, int64_t N, int64_t cap, const double **vec, const float2 **vdf,
+                         const int **vexp, double **outx);
 void refit_chain_fit(dse_space *S, const double *y, const uint64_t *fid, int nf, const uint64_t *cand, int64_t cap,
                      const int64_t *n_dev, void *scratch, bool have_sums, double *res, double *report,
                      uint64_t *chosen, cudaStream_t st);
@@ -835,7 +843,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   sd.mode = DSE_MODE_PER_TARGET;
   sd.precision = d->precision == DSE_PREC_FP64 ? DSE_PREC_FP64 : DSE_PREC_FP32;
   sd.stream = d->stream;
-  sd.flags = d->flags & DSE_FLAG_TIMING;
+  sd.flags = d->flags & (DSE_FLAG_TIMING | DSE_FLAG_TIMING_MAIN);
   dse_result *R = nullptr;
   DSE_TRY(screen_impl(sp, &sd, &R, false));
   struct Owner {
@@ -890,9 +898,15 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
     refit_chain_prep(sp, y, fid, it, rscr, k, st);
     if (fused) {
       const double *vec[4];
+      const float2 *vdf[4];
+      const int *vexp = nullptr;
       double *outx = nullptr;
-      refit_chain_vectors(rscr, N, k, vec, &outx);
-      for (int m = 0; m < 4; ++m) kp->S.xv[m] = vec[m];
+      refit_chain_vectors(rscr, N, k, vec, vdf, &vexp, &outx);
+      for (int m = 0; m < 4; ++m) {
+        kp->S.xv[m] = vec[m];
+        kp->S.xdf[m] = vdf[m];
+      }
+      kp->S.xexp = vexp;
       kp->S.nx = 1 + it;
       kp->S.r_x = rx;
       kp->S.out_x = outx;
@@ -1182,10 +1196,7 @@ void dse_result_free(dse_result *r) {
   dfree(r->scratch);
   dfree(r->extra);
   if (r->keep && r->keep_free) r->keep_free(r->keep);
-  for (auto &t : r->timing) {
-    cudaEventDestroy(t.second.first);
-    cudaEventDestroy(t.second.second);
-  }
+  for (cudaEvent_t e : r->events) cudaEventDestroy(e);
   delete r;
 }
 

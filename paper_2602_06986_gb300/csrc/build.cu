@@ -254,7 +254,7 @@ __global__ void k_take_rows(const int64_t *keep, int64_t nk, int64_t ld, const d
 // FP32 rows and per-feature helpers: one warp per feature (row conversion
 // and the FP64 sum of squares for the norm bound are coalesced over lanes).
 __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const double *v64, float *v32,
-                            const double *mean64, const double *rmean64, const double *min64, const double *max64,
+                            float *v32lo, const double *mean64, const double *rmean64, const double *min64, const double *max64,
                             const double *minabs64, const double *maxabs64, const double *minabsnz64,
                             const int32_t *units, double exp_arg_max, float4 *fa, float2 *fr, uint32_t *flags,
                             uint64_t *ukey, float *fnorm) {
@@ -264,7 +264,9 @@ __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const doubl
     double s2 = 0.0;
     for (int64_t s = lane; s < ld; s += 32) {
       const double v = s < N ? v64[f * ld + s] : 0.0;
-      v32[f * ld + s] = __double2float_rn(v);
+      const float h = __double2float_rn(v);
+      v32[f * ld + s] = h;
+      v32lo[f * ld + s] = __double2float_rn(__dsub_rn(v, (double)h));
       s2 = __fma_rn(v, v, s2);
     }
     s2 = warp_sum64(s2);
@@ -673,12 +675,13 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   S->used = T.used;
   S->dmask = T.dmask;
   DSE_TRY(dalloc(&S->v32, (size_t)n * ld, "FP32 feature rows"));
+  DSE_TRY(dalloc(&S->v32lo, (size_t)n * ld, "FP32 remainder rows"));
   DSE_TRY(dalloc(&S->fa, n, "helpers"));
   DSE_TRY(dalloc(&S->fr, n, "helpers"));
   DSE_TRY(dalloc(&S->fnorm, n, "helpers"));
   DSE_TRY(dalloc(&S->flags, n, "flags"));
   DSE_TRY(dalloc(&S->ukey, 2 * n, "unit keys"));
-  k_fp32_prep<<<grid_for(n * 32, 256), 256, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, T.mean64, T.rmean64, T.min64,
+  k_fp32_prep<<<grid_for(n * 32, 256), 256, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, S->v32lo, T.mean64, T.rmean64, T.min64,
                                                      T.max64, T.minabs64, T.maxabs64, T.minabsnz64, T.units,
                                                      S->exp_arg_max, S->fa, S->fr, S->flags, S->ukey, S->fnorm);
   dfree(T.minabsnz64);
@@ -751,7 +754,7 @@ dse_status build_space(const dse_space_desc *d, dse_space **out) {
 
 dse_status space_release(dse_space *S) {
   if (!S) return DSE_OK;
-  dfree(S->v64); dfree(S->v32); dfree(S->mean64); dfree(S->rmean64); dfree(S->min64); dfree(S->max64);
+  dfree(S->v64); dfree(S->v32); dfree(S->v32lo); dfree(S->mean64); dfree(S->rmean64); dfree(S->min64); dfree(S->max64);
   dfree(S->minabs64); dfree(S->maxabs64); dfree(S->fa); dfree(S->fr); dfree(S->fnorm); dfree(S->flags); dfree(S->cplx);
   dfree(S->op); dfree(S->units); dfree(S->ca); dfree(S->cb); dfree(S->ukey); dfree(S->rowid_ident);
   dfree(S->used); dfree(S->dmask); dfree(S->op_deny); dfree(S->gram_buf);
@@ -768,6 +771,7 @@ FeatTable table_of(const dse_space *S) {
   F.ld = S->ld;
   F.v64 = S->v64;
   F.v32 = S->v32;
+  F.v32lo = S->v32lo;
   F.mean64 = S->mean64;
   F.rmean64 = S->rmean64;
   F.min64 = S->min64;

@@ -35,7 +35,9 @@ struct FeatTable {
   int64_t N;        // samples
   int64_t ld;       // row stride (elements) of v64 / v32, multiple of 4
   const double *v64;
-  const float *v32;
+  const float *v32;                          // RN(v64)
+  const float *v32lo;                        // RN(v64 - v32): v64 = v32 + v32lo to 2^-48 relative
+                                             // for F_FP32_SAFE features (nullptr while building)
   const double *mean64, *rmean64;            // mean of x, mean of 1/x (0 if min|x| == 0)
   const double *min64, *max64, *minabs64, *maxabs64;
   const float4 *fa;                          // {mean32, rmean32, RU(max|x|), RD(max|x|)}
@@ -68,10 +70,18 @@ struct RungGeom {
 __host__ __device__ inline uint64_t tri(uint64_t n) { return n * (n - 1) / 2; }
 
 // Pair index qs (>= 0) -> (i, j) with i(i-1)/2 <= qs < i(i+1)/2, j = qs - i(i-1)/2.
-// FP64 square root, then exact integer fix-up.
+// A square root estimate, then an exact integer fix-up.
 __host__ __device__ inline void pair_from_index(uint64_t qs, uint64_t *i, uint64_t *j) {
+#ifdef __CUDA_ARCH__
+  // on the device an FP32 root (the FP64 pipe is slow on this part): within
+  // one unit of the row for qs < 2^44 (2^22 stored features); the loops
+  // below correct whatever is left
+  const float d = sqrtf(8.0f * (float)qs + 1.0f);
+  uint64_t r = (uint64_t)((1.0f + d) * 0.5f);
+#else
   double d = sqrt(8.0 * (double)qs + 1.0);
   uint64_t r = (uint64_t)((1.0 + d) * 0.5);
+#endif
   if (r < 1) r = 1;
   while (tri(r) > qs) --r;
   while (tri(r + 1) <= qs) ++r;
@@ -170,6 +180,7 @@ struct ScreenArgs {
   int32_t mode;                // DSE_MODE_*
   int32_t n_lists;
   const float *y32;            // [T][ldy] centred, unit-norm targets (FP32)
+  const float2 *ydf;           // [T][ldy] the same as pairs (hi, lo) = (y32, RN(y64 - y32)), or nullptr
   const double *y64;           // [T][ldy] centred, unit-norm targets (FP64)
   const float *ysum32;         // [T] sum of the FP32 targets
   int32_t max_complexity;
@@ -291,7 +302,7 @@ struct dse_space {
   int64_t reasons[dse::kMaxRung + 1][6];
   bool have_counts[dse::kMaxRung + 1];
   double *v64 = nullptr;
-  float *v32 = nullptr;
+  float *v32 = nullptr, *v32lo = nullptr;
   double *mean64 = nullptr, *rmean64 = nullptr, *min64 = nullptr, *max64 = nullptr,
          *minabs64 = nullptr, *maxabs64 = nullptr;
   float4 *fa = nullptr;
@@ -338,6 +349,7 @@ struct dse_result {
   // working state kept for a re-run
   double *y64 = nullptr;
   float *y32 = nullptr;
+  float2 *ydf = nullptr;
   float *ysum32 = nullptr;
   int32_t ldy = 0;
   int32_t reruns = 0;
@@ -353,5 +365,6 @@ struct dse_result {
   dse_status (*rerun)(dse_result *) = nullptr;
   int32_t flags = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> timing;  // (group, start, stop)
+  std::vector<cudaEvent_t> events;  // every event of timing (one may close a group and open the next)
   int64_t launches = 0;
 };

@@ -167,32 +167,8 @@ __device__ __forceinline__ int warp_or(int v) {
   return __any_sync(0xffffffffu, v) ? 1 : 0;
 }
 
-// Shifted FP64 sums of one candidate column over N samples, one warp (lanes
-// over samples, shuffle reduction; every lane gets the results):
-//   acc[0] = sum (v - c), acc[1] = sum (v - c)^2, acc[2 + m] = sum (v - c) x_m
-// for the vectors x_m, m < nv <= kColVec, with c = v at sample 0.  Each sum
-// is the same sequence of operations wherever this is called, so the sums a
-// re-score takes alongside its own and the sums a refit takes later agree to
-// the bit.
+// Vectors a candidate column is summed against (the target and up to four
+// refit vectors).
 constexpr int kColVec = 5;
-
-__device__ __forceinline__ void col_sums_warp(const FeatTable &F, int op, int64_t a, int64_t b, int64_t N, double c,
-                                              const double *const *vec, int nv, double (&acc)[2 + kColVec],
-                                              int lane) {
-  const double *xa = F.v64 + a * F.ld;
-  const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
-#pragma unroll
-  for (int i = 0; i < 2 + kColVec; ++i) acc[i] = 0.0;
-  for (int64_t s = lane; s < N; s += 32) {
-    const double v = eval_op64(op, xa[s], xb[s]) - c;
-    acc[0] += v;
-    acc[1] = fma(v, v, acc[1]);
-#pragma unroll
-    for (int m = 0; m < kColVec; ++m)
-      if (m < nv) acc[2 + m] = fma(v, vec[m][s], acc[2 + m]);
-  }
-#pragma unroll
-  for (int i = 0; i < 2 + kColVec; ++i) acc[i] = warp_sum64(acc[i]);
-}
 
 }  // namespace dse

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include "dse_internal.cuh"
+#include "df32.cuh"
 #include "eval64.cuh"
 #include "util.cuh"
 
@@ -317,13 +318,19 @@ __global__ void __launch_bounds__(kPrep) k_refit_prep(const double *y, const dou
 
 // Column sums of the candidates whose record the re-score did not fill
 // (out_x[w][7] == 0), one warp per candidate, with the same function and
-// vector order as the re-score: {rc, fcc_0 ..}.
+// vectors as the re-score: {rc, fcc_0 ..} and their pair images xdf with
+// scale exponents xexp.  A record is {c, sum (v - c), sum (v - c)^2,
+// sum (v - c) rc, sum (v - c) fcc_j .., eps}, eps > 0 the relative error
+// scale of its sums (pair or FP64 arithmetic).
 template <int NF>
-__global__ void __launch_bounds__(256) k_refit_fill(FeatTable F, RungGeom G, int64_t n_stored, const uint64_t *cand,
-                                                    int64_t n_cand, const int64_t *n_dev, const double *rc,
-                                                    const double *fcc, double *out_x) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(kColThreads) k_refit_fill(FeatTable F, RungGeom G, int64_t n_stored,
+                                                            const uint64_t *cand, int64_t n_cand,
+                                                            const int64_t *n_dev, const double *rc,
+                                                            const double *fcc, const float2 *xdf, const int *xexp,
+                                                            double *out_x, unsigned long long *minkey) {
+  __shared__ ColShared sh;
+  const int64_t w = blockIdx.x;
+  if (w == 0 && threadIdx.x == 0) *minkey = ~0ull;  // the smallest RSS + err of this fit (below)
   if (w >= n_cand || (n_dev && w >= *n_dev)) return;
   double *x = out_x + w * 8;
   if (x[7] != 0.0) return;
@@ -333,17 +340,49 @@ __global__ void __launch_bounds__(256) k_refit_fill(FeatTable F, RungGeom G, int
   int op;
   int64_t a, b;
   decode_any(G, n_stored, gid, &op, &a, &b);
-  const double c = col_value(F, G, n_stored, op, a, b, 0);
-  const double *vec[kColVec] = {rc, fcc, fcc + N, fcc + 2 * N, fcc + 3 * N};
-  double acc[2 + kColVec];
-  col_sums_warp(F, op, a, b, N, c, vec, 1 + NF, acc, lane);
-  if (lane == 0) {
-    x[0] = c;
-    x[1] = acc[0];
-    x[2] = acc[1];
-    for (int m = 0; m < 4; ++m) x[3 + m] = m < 1 + NF ? acc[2 + m] : 0.0;
-    x[7] = 1.0;
+  ColVecs V;
+  V.nv = 1 + NF;
+#pragma unroll
+  for (int m = 0; m < kColVec; ++m) {
+    V.v64[m] = m == 0 ? rc : m <= NF ? fcc + (int64_t)(m - 1) * N : nullptr;
+    V.vdf[m] = m <= NF ? xdf + (int64_t)m * N : nullptr;
+    V.e[m] = m <= NF ? xexp[m] : 0;
   }
+  ColSums cs;
+  col_sums(F, op, a, b, N, V, cs, sh);
+  if (threadIdx.x == 0) {
+    x[0] = cs.c;
+    x[1] = cs.acc[0];
+    x[2] = cs.acc[1];
+    for (int m = 0; m < 4; ++m) x[3 + m] = m < 1 + NF ? cs.acc[2 + m] : 0.0;
+    x[7] = col_err_scale(cs, N);
+  }
+}
+
+// The pair images of the refit vectors {rc, fcc_0 .. fcc_{NF-1}}: x 2^-e
+// split into (RN(x 2^-e), RN(x 2^-e - hi)), e the scale exponent of the
+// vector's 2-norm (RSS of the fixed-only fit, diagonal of the centred Gram
+// matrix), so that every image has norm in [1/2, 1); xexp[m] = e.
+template <int NF>
+__global__ void k_refit_split(const double *rc, const double *fcc, const double *pre, int64_t N, float2 *xdf,
+                              int *xexp) {
+  const int64_t total = (int64_t)(1 + NF) * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / N);
+    const int64_t s = i - (int64_t)m * N;
+    const double n2 = m == 0 ? pre[kPreRss] : pre[kPreGram + (m - 1) * kMaxP + (m - 1)];
+    const int e = df::scale_exp(sqrt(n2 > 0.0 ? n2 : 0.0));
+    const double x = __dmul_rn(m == 0 ? rc[s] : fcc[(int64_t)(m - 1) * N + s], df::pow2d(-e));
+    const float h = __double2float_rn(x);
+    xdf[i] = make_float2(h, __double2float_rn(__dsub_rn(x, (double)h)));
+    if (s == 0) xexp[m] = e;
+  }
+}
+
+// Order-preserving key of a double (unsigned comparison = numeric order).
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
 // Every candidate's fit from its column sums (thread per candidate), in the
@@ -354,11 +393,17 @@ __global__ void __launch_bounds__(256) k_refit_fill(FeatTable F, RungGeom G, int
 // is (sum d r) / |d_perp|^2 and RSS = RSS_fixed - (sum d r)^2 / |d_perp|^2.
 // The pivot test is the full fit's (|d_perp| > 1e-12 |v|).  A fit that leaves
 // less than 1e-6 of RSS_fixed (where the subtraction loses digits) is flagged
-// for the explicit residual pass.
+// for the explicit residual pass.  err_out gets a bound on the RSS error from
+// the record's error scale eps: with the sums' errors at most eps sqrt(Sdd)
+// |x|, (sum d r)^2 / |d_perp|^2 moves by at most 5 eps RSS_fixed Sdd /
+// |d_perp|^2 (by Cauchy-Schwarz, (sum d r)^2 <= RSS_fixed |d_perp|^2); it is
+// taken with a factor 8, and the smallest RSS + err of the fit is kept in
+// *minkey (order key) for the near-best pass of k_refit_wide.
 template <int NF>
 __global__ void k_refit_solve(const double *out_x, const uint64_t *cand, int64_t n_cand, const int64_t *n_dev,
                               const uint64_t *fixed_ids, const double *pre, int64_t N, double *rmse_out,
-                              double *beta_out, uint8_t *explicit_flag) {
+                              double *beta_out, uint8_t *explicit_flag, double *err_out,
+                              unsigned long long *minkey) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= n_cand || (n_dev && w >= *n_dev)) return;
   constexpr int nf = NF;
@@ -367,6 +412,7 @@ __global__ void k_refit_solve(const double *out_x, const uint64_t *cand, int64_t
 #pragma unroll
   for (int j = 0; j < nf; ++j) dup |= fixed_ids[j] == gid;
   explicit_flag[w] = 0;
+  err_out[w] = 0.0;
   const double *x = out_x + w * 8;
   if (dup || x[7] == 0.0 || pre[kPreOk] == 0.0) {
     rmse_out[w] = INFINITY;
@@ -429,6 +475,9 @@ __global__ void k_refit_solve(const double *out_x, const uint64_t *cand, int64_t
     rmse_out[w] = INFINITY;
   } else {
     rmse_out[w] = sqrt(rss / Nd);
+    const double err = 40.0 * x[7] * rss_f * (Sdd / den);
+    err_out[w] = err;
+    atomicMin(minkey, ord_key(rss + err));
   }
 }
 
@@ -439,6 +488,10 @@ __global__ void k_refit_solve(const double *out_x, const uint64_t *cand, int64_t
 // terms that involve v are accumulated: Σv, Σv², then Σd², Σd·f_j, Σd·y with
 // d = v - mean(v), then the residual.  CACHE: v is evaluated once into
 // shared memory (N doubles); FP64 arithmetic is the cost on this part.
+// Launched twice per fit: for the fits flagged by k_refit_solve (`only`),
+// then in `near` mode for every fit whose RSS, within its error bound,
+// could be the smallest; a fit done here has err 0 (its RSS is the FP64
+// fit's), so the pick and its RMSE are those of an FP64 fit.
 constexpr int64_t kRefitCacheMax = 6144;  // samples (48 KiB)
 
 template <bool CACHE, int NF>
@@ -446,7 +499,8 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
                                                       const double *ycc, const double *pre,
                                                       const uint64_t *fixed_ids, const uint64_t *cand, int64_t n_cand,
                                                       const int64_t *n_dev, double *rmse_out, double *beta_out,
-                                                      const uint8_t *only) {
+                                                      const uint8_t *only, double *err_out,
+                                                      unsigned long long *minkey, bool near) {
   constexpr int nf = NF;
   __shared__ double sm[(kWide / 32) * 20];
   __shared__ double s_bc[kMaxP + 2];
@@ -455,10 +509,17 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   if (w >= n_cand || (n_dev && w >= *n_dev)) return;
   if (only && !only[w]) return;
   const int64_t N = F.N;
+  if (near) {
+    // a fit whose RSS, within its error bound, could be the smallest:
+    // RSS_w - err_w <= min_j (RSS_j + err_j)
+    const double r = rmse_out[w], e = err_out[w];
+    if (!(r < INFINITY) || !(e > 0.0) || ord_key(r * r * (double)N - e) > *minkey) return;
+  }
   constexpr int p = nf + 1;
   const uint64_t gid = cand[w];
   bool dup = false;
   for (int j = 0; j < nf; ++j) dup |= fixed_ids[j] == gid;
+  if (threadIdx.x == 0) err_out[w] = 0.0;  // the value written here is the FP64 fit's
   if (dup) {
     if (threadIdx.x == 0) rmse_out[w] = INFINITY;
     return;
@@ -564,7 +625,10 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
     }
   }
   block_sum_arr<1>(rss, sm);
-  if (threadIdx.x == 0) rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
+  if (threadIdx.x == 0) {
+    rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
+    if (ok && !near) atomicMin(minkey, ord_key(rss[0]));
+  }
 }
 
 __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
@@ -577,16 +641,20 @@ __global__ void k_residual(FeatTable F, RungGeom G, int64_t n_stored, const doub
 // statistics, and per candidate its column sums, RMSE, coefficients and the
 // explicit-pass flag.
 struct RefitBufs {
-  double *fc, *fcc, *ycc, *rc, *pre, *outx, *rm, *beta;
+  double *fc, *fcc, *ycc, *rc, *pre, *outx, *rm, *beta, *err;
   uint8_t *flag;
   int64_t *best;
+  unsigned long long *minkey;  // order key of the smallest RSS + err of the current fit
+  float2 *xdf;  // [kMaxP][N] pair images of {rc, fcc_0 ..}
+  int *xexp;    // [kMaxP] their scale exponents
 };
 
 static size_t rnd256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t refit_chain_bytes(int64_t N, int64_t cap) {
   return rnd256(8 * (size_t)N * kMaxP) * 2 + rnd256(8 * N) * 2 + rnd256(8 * kPreSize) + rnd256(64 * (size_t)cap) +
-         rnd256(8 * cap) + rnd256(8 * (size_t)cap * (kMaxP + 1)) + rnd256(cap) + rnd256(8);
+         rnd256(8 * cap) + rnd256(8 * (size_t)cap * (kMaxP + 1)) + rnd256(cap) + rnd256(8) + rnd256(8 * cap) +
+         rnd256(8) + rnd256(8 * (size_t)N * kMaxP) + rnd256(4 * kMaxP);
 }
 
 static RefitBufs carve(void *scratch, int64_t N, int64_t cap) {
@@ -607,12 +675,19 @@ static RefitBufs carve(void *scratch, int64_t N, int64_t cap) {
   b.beta = reinterpret_cast<double *>(take(8 * (size_t)cap * (kMaxP + 1)));
   b.flag = reinterpret_cast<uint8_t *>(take(cap));
   b.best = reinterpret_cast<int64_t *>(take(8));
+  b.err = reinterpret_cast<double *>(take(8 * cap));
+  b.minkey = reinterpret_cast<unsigned long long *>(take(8));
+  b.xdf = reinterpret_cast<float2 *>(take(8 * (size_t)N * kMaxP));
+  b.xexp = reinterpret_cast<int *>(take(4 * kMaxP));
   return b;
 }
 
 template <int NF>
 static void prep_nf(const dse_space *S, const double *y, const RefitBufs &b, cudaStream_t st) {
   k_refit_prep<NF><<<1, kPrep, 0, st>>>(y, b.fc, S->N, b.fcc, b.ycc, b.rc, b.pre);
+  const int64_t total = (int64_t)(1 + NF) * S->N;
+  k_refit_split<NF><<<(unsigned)std::min<int64_t>(256, (total + 255) / 256), 256, 0, st>>>(b.rc, b.fcc, b.pre, S->N,
+                                                                                         b.xdf, b.xexp);
 }
 
 // Fill the missing column sums, solve every fit, redo the flagged ones
@@ -621,16 +696,22 @@ template <int NF>
 static void fit_nf(const FeatTable &F, const dse_space *S, const uint64_t *fid, const uint64_t *cand, int64_t cap,
                    const int64_t *n_dev, const RefitBufs &b, cudaStream_t st) {
   const int64_t N = S->N;
-  k_refit_fill<NF><<<(unsigned)((cap * 32 + 255) / 256), 256, 0, st>>>(F, S->geom, S->n, cand, cap, n_dev, b.rc,
-                                                                        b.fcc, b.outx);
+  k_refit_fill<NF><<<(unsigned)cap, kColThreads, 0, st>>>(F, S->geom, S->n, cand, cap, n_dev, b.rc, b.fcc, b.xdf,
+                                                          b.xexp, b.outx, b.minkey);
   k_refit_solve<NF><<<(unsigned)((cap + 127) / 128), 128, 0, st>>>(b.outx, cand, cap, n_dev, fid, b.pre, N, b.rm,
-                                                                    b.beta, b.flag);
-  if (N <= kRefitCacheMax)
-    k_refit_wide<true, NF><<<(unsigned)cap, kWide, (size_t)N * sizeof(double), st>>>(
-        F, S->geom, S->n, b.fcc, b.ycc, b.pre, fid, cand, cap, n_dev, b.rm, b.beta, b.flag);
-  else
-    k_refit_wide<false, NF><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, b.fcc, b.ycc, b.pre, fid, cand, cap,
-                                                              n_dev, b.rm, b.beta, b.flag);
+                                                                    b.beta, b.flag, b.err, b.minkey);
+  auto wide = [&](const uint8_t *only, bool near) {
+    if (N <= kRefitCacheMax)
+      k_refit_wide<true, NF><<<(unsigned)cap, kWide, (size_t)N * sizeof(double), st>>>(
+          F, S->geom, S->n, b.fcc, b.ycc, b.pre, fid, cand, cap, n_dev, b.rm, b.beta, only, b.err, b.minkey, near);
+    else
+      k_refit_wide<false, NF><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, b.fcc, b.ycc, b.pre, fid, cand, cap,
+                                                                n_dev, b.rm, b.beta, only, b.err, b.minkey, near);
+  };
+  // the fits the sums cannot resolve (near-perfect ones), then every fit
+  // that could still be the best within its error bound, in FP64
+  wide(b.flag, false);
+  wide(nullptr, true);
 }
 
 // The fixed columns' statistics and residual (before the screen whose
@@ -639,7 +720,7 @@ void refit_chain_prep(dse_space *S, const double *y, const uint64_t *fid, int nf
                       cudaStream_t st) {
   const RefitBufs b = carve(scratch, S->N, cap);
   const FeatTable F = table_of(S);
-  note_launches(1 + (nf ? 1 : 0));
+  note_launches(2 + (nf ? 1 : 0));
   if (nf) k_columns<<<(unsigned)nf, 256, 0, st>>>(F, S->geom, S->n, fid, nf, b.fc);
   switch (nf) {
     case 0: prep_nf<0>(S, y, b, st); break;
@@ -650,11 +731,18 @@ void refit_chain_prep(dse_space *S, const double *y, const uint64_t *fid, int nf
 }
 
 // What a re-score needs to take the refit sums: the vectors {rc, fcc_0 ..}
-// (1 + nf of them) and the per-candidate record array.
-void refit_chain_vectors(void *scratch, int64_t N, int64_t cap, const double **vec, double **outx) {
+// (1 + nf of them), their pair images and scale exponents, and the
+// per-candidate record array.
+void refit_chain_vectors(void *scratch, int64_t N, int64_t cap, const double **vec, const float2 **vdf,
+                         const int **vexp, double **outx) {
   const RefitBufs b = carve(scratch, N, cap);
   vec[0] = b.rc;
-  for (int j = 0; j < 3; ++j) vec[1 + j] = b.fcc + (size_t)j * N;
+  vdf[0] = b.xdf;
+  for (int j = 0; j < 3; ++j) {
+    vec[1 + j] = b.fcc + (size_t)j * N;
+    vdf[1 + j] = b.xdf + (size_t)(1 + j) * N;
+  }
+  *vexp = b.xexp;
   *outx = b.outx;
 }
 
@@ -667,7 +755,7 @@ void refit_chain_fit(dse_space *S, const double *y, const uint64_t *fid, int nf,
   const RefitBufs b = carve(scratch, S->N, cap);
   const FeatTable F = table_of(S);
   if (!have_sums) cudaMemsetAsync(b.outx, 0, 64 * (size_t)cap, st);
-  note_launches(5);
+  note_launches(6);
   switch (nf) {
     case 0: fit_nf<0>(F, S, fid, cand, cap, n_dev, b, st); break;
     case 1: fit_nf<1>(F, S, fid, cand, cap, n_dev, b, st); break;

@@ -41,8 +41,8 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 
 // Centre and normalise one target in FP64 (whole block): row y of N values
 // into rows y64 / y32 of ldy (zero beyond N) and the sum of the FP32 row.
-__device__ void target_prep(const double *y, int64_t N, int32_t ldy, double *y64, float *y32, float *ysum32,
-                            int *err) {
+__device__ void target_prep(const double *y, int64_t N, int32_t ldy, double *y64, float *y32, float2 *ydf,
+                            float *ysum32, int *err) {
   __shared__ double red[32];
   auto block_sum = [&](double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -73,6 +73,7 @@ __device__ void target_prep(const double *y, int64_t N, int32_t ldy, double *y64
     float f = __double2float_rn(v);
     y64[i] = v;
     y32[i] = f;
+    if (ydf) ydf[i] = make_float2(f, __double2float_rn(__dsub_rn(v, (double)f)));
     fs += (double)f;
   }
   fs = block_sum(fs);
@@ -81,10 +82,11 @@ __device__ void target_prep(const double *y, int64_t N, int32_t ldy, double *y64
 
 // One block per target.
 __global__ void k_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,
-                          float *ysum32, int *err) {
+                          float2 *ydf, float *ysum32, int *err) {
   const int t = blockIdx.x;
   if (t >= T) return;
-  target_prep(Y + (int64_t)t * ldY, N, ldy, y64 + (int64_t)t * ldy, y32 + (int64_t)t * ldy, ysum32 + t, err);
+  target_prep(Y + (int64_t)t * ldY, N, ldy, y64 + (int64_t)t * ldy, y32 + (int64_t)t * ldy,
+              ydf ? ydf + (int64_t)t * ldy : nullptr, ysum32 + t, err);
 }
 
 // Batched screens: one block per problem, its target at Y + yoff[p] with the
@@ -93,7 +95,7 @@ __global__ void k_targets_batched(const double *Y, const int64_t *yoff, const Sc
                                   int32_t ldy, double *y64, float *y32, float *ysum32, int *err) {
   const int p = blockIdx.x;
   if (p >= n) return;
-  target_prep(Y + yoff[p], args[p].N, ldy, y64 + (int64_t)p * ldy, y32 + (int64_t)p * ldy, ysum32 + p, err);
+  target_prep(Y + yoff[p], args[p].N, ldy, y64 + (int64_t)p * ldy, y32 + (int64_t)p * ldy, nullptr, ysum32 + p, err);
 }
 
 // ------------------------------------------------------ shared epilogue
@@ -1065,11 +1067,11 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
       st[5] += y[s];
     }
     block_sum64<6>(st, sm);
-    const double sxx = st[1] - st[0] * (st[0] / (double)N);
-    int good = st[3] == 0.0 && isfinite(sxx);
-    if (good && A.fmin_std_rel64 >= 0.0)
-      good = __dsqrt_rn(fmax(sxx, 0.0) / (double)N) > A.fmin_std_rel64 * __dsqrt_rn(st[2] / (double)N);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // (FP64 work is slow on this part: one thread decides)
+      const double sxx = st[1] - st[0] * (st[0] / (double)N);
+      int good = st[3] == 0.0 && isfinite(sxx);
+      if (good && A.fmin_std_rel64 >= 0.0)
+        good = __dsqrt_rn(fmax(sxx, 0.0) / (double)N) > A.fmin_std_rel64 * __dsqrt_rn(st[2] / (double)N);
       atomicAdd(&A.stats[good ? ST_REASON0 + DSE_VALID : ST_REASON0 + DSE_R_REALISED], 1ull);
       if (good) atomicAdd(&A.stats[ST_EVALUATED], 1ull);
       if (good && sxx > 0.0) {
@@ -1216,9 +1218,9 @@ void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st, const Screen
 }
 
 void launch_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,
-                    float *ysum32, int *err, cudaStream_t st) {
+                    float2 *ydf, float *ysum32, int *err, cudaStream_t st) {
   note_launches(1);
-  k_targets<<<T, 256, 0, st>>>(Y, ldY, T, N, ldy, y64, y32, ysum32, err);
+  k_targets<<<T, 256, 0, st>>>(Y, ldY, T, N, ldy, y64, y32, ydf, ysum32, err);
 }
 
 }  // namespace dse

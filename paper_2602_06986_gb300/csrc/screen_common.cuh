@@ -39,11 +39,16 @@ template <>
 struct Num<float> {
   __device__ static float sqrt_(float x) { return sqrtf(x); }
   __device__ static float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+  // 2^-90: a shifted sum of squares below N times this is within 2^36 of
+  // the underflow threshold, where products that flushed (absolute error up
+  // to 2^-126 each) are no longer negligible against the relative model
+  __device__ static float tiny() { return 8.077935669463161e-28f; }
 };
 template <>
 struct Num<double> {
   __device__ static double sqrt_(double x) { return sqrt(x); }
   __device__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+  __device__ static double tiny() { return 1.1754943508222875e-271; }  // 2^-900
 };
 
 // Centred-norm interval and realised decision of one candidate.
@@ -80,7 +85,9 @@ __device__ __forceinline__ CandInterval<R> cand_interval(R S1, R S2, R N, R invN
   const R lo2 = Sxx - dSxx;
   o.q_lo = Num<R>::sqrt_(lo2 > R(0) ? lo2 : R(0)) * (R(1) - R(4) * u) - o.E;
   o.q_hi = Num<R>::sqrt_(Sxx + dSxx) * (R(1) + R(4) * u) + o.E;
-  bool finite = isfinite(S1) && isfinite(S2) && isfinite(o.E);
+  // non-finite sums, or a column so small that underflow could hide in it:
+  // undecided (the FP64 escalation decides)
+  bool finite = isfinite(S1) && isfinite(S2) && isfinite(o.E) && S2 > N * Num<R>::tiny();
   if (!finite) {
     o.realised = 2;
     return o;

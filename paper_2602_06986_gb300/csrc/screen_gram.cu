@@ -379,7 +379,10 @@ __device__ __forceinline__ GramCand gram_score(const gram::EpiFeat *Fa, int fu, 
   const float lo2 = Sxx - dSxx;
   const float q_lo = sqrtf(lo2 > 0.f ? lo2 : 0.f) * (1.f - 4.f * u) - E;
   const float q_hi = sqrtf(Sxx + dSxx) * (1.f + 4.f * u) + E;
-  if (!(isfinite(S1) && isfinite(S2) && isfinite(Sy) && isfinite(Z) && isfinite(E) && isfinite(q_hi))) {
+  // (a column within 2^36 of FP32 underflow, where flushed products escape
+  // the relative error model, is undecided too)
+  if (!(isfinite(S1) && isfinite(S2) && isfinite(Sy) && isfinite(Z) && isfinite(E) && isfinite(q_hi) &&
+        S2 > N * 8.077935669463161e-28f)) {
     o.realised = 2;
     o.s = 0.f;
     o.eps = 1.f;

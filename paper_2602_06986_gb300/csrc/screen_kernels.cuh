@@ -8,7 +8,7 @@ namespace dse {
 enum { KIND_MUL = 0, KIND_ADD = 1 };
 
 void launch_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,
-                    float *ysum32, int *err, cudaStream_t st);
+                    float2 *ydf, float *ysum32, int *err, cudaStream_t st);
 void launch_feature(int prec64, int nt, const ScreenArgs &A, uint64_t id0, uint64_t id1, uint64_t p0, uint64_t p1,
                     float gamma, int sms, cudaStream_t st);
 dse_status launch_pair(int prec64, int kind, int nt, const ScreenArgs &A, int block_len, int sms, cudaStream_t st);
@@ -65,10 +65,13 @@ struct SelectArgs {
   unsigned int *r_rank;     // [lists][cap] rank of each retained entry
   // optional column sums for refits that follow the screen (one target,
   // N <= 4096): the re-score of each entry also accumulates its shifted
-  // column against nx vectors; r_x [lists][cap][8] = {c, S1, S2, E_0.., 1},
-  // out_x [lists][k][8] the same in rank order (last field 0 when the entry
-  // was not re-scored)
+  // column against nx vectors (FP64 rows xv, pair images xdf with scale
+  // exponents xexp[0..nx)); r_x [lists][cap][8] = {c, S1, S2, E_0.., eps},
+  // out_x [lists][k][8] the same in rank order (last field, the sums'
+  // relative error scale, 0 when the entry was not re-scored)
   const double *xv[4];
+  const float2 *xdf[4];
+  const int *xexp;
   int32_t nx;
   double *r_x, *out_x;
   unsigned long long *stats;

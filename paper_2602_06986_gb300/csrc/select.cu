@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "dse_internal.cuh"
+#include "df32.cuh"
 #include "eval64.cuh"
 #include "screen_common.cuh"
 #include "screen_kernels.cuh"
@@ -341,38 +342,20 @@ __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const 
     const int t_begin = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
     const int nt = A.mode == DSE_MODE_AGGREGATED ? (A.T < NT ? A.T : NT) : 1;
     const double c = eval_op64(op, xa[0], xb[0]);
-    double acc[NT == 1 ? 2 + kColVec : 2 + NT];
-    if (NT == 1) {
-      // the list's target, then the refit vectors (if any)
-      const double *vec[kColVec] = {A.y64 + (int64_t)t_begin * A.ldy, S.xv[0], S.xv[1], S.xv[2], S.xv[3]};
-      double a7[2 + kColVec];
-      col_sums_warp(A.F, op, a, b, N, c, vec, 1 + S.nx, a7, lane);
+    double acc[2 + NT];
 #pragma unroll
-      for (int i = 0; i < (NT == 1 ? 2 + kColVec : 2 + NT); ++i) acc[i] = a7[i];
-    } else {
+    for (int i = 0; i < 2 + NT; ++i) acc[i] = 0.0;
+    for (int64_t s = lane; s < N; s += 32) {
+      const double v = eval_op64(op, xa[s], xb[s]) - c;
+      acc[0] += v;
+      acc[1] = fma(v, v, acc[1]);
 #pragma unroll
-      for (int i = 0; i < 2 + NT; ++i) acc[i] = 0.0;
-      for (int64_t s = lane; s < N; s += 32) {
-        const double v = eval_op64(op, xa[s], xb[s]) - c;
-        acc[0] += v;
-        acc[1] = fma(v, v, acc[1]);
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-          if (t < nt) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2 + NT; ++i) acc[i] = warp_sum64(acc[i]);
+      for (int t = 0; t < NT; ++t)
+        if (t < nt) acc[2 + t] = fma(v, A.y64[(int64_t)(t_begin + t) * A.ldy + s], acc[2 + t]);
     }
-    if (lane == 0) {
-      if (NT == 1 && S.r_x) {
-        double *x = S.r_x + r * 8;
-        x[0] = c;
-        x[1] = acc[0];
-        x[2] = acc[1];
-        for (int m = 0; m < 4; ++m) x[3 + m] = m < S.nx ? acc[3 + m] : 0.0;
-        x[7] = 1.0;
-      }
-    }
+#pragma unroll
+    for (int i = 0; i < 2 + NT; ++i) acc[i] = warp_sum64(acc[i]);
+    const double eps = (double)(N / 32 + 64) * 1.7763568394002505e-15;
     if (lane == 0 && S.r_need[r]) {
       const double mean = acc[0] / (double)N;
       const double sxx = acc[1] - acc[0] * mean;
@@ -385,9 +368,68 @@ __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const 
       }
       const double sc = A.mode == DSE_MODE_AGGREGATED ? sqrt(agg / (double)nt) : sqrt(agg);
       S.r_s64[r] = sc;
-      S.r_e64[r] = (double)(N / 32 + 64) * 1.1102230246251565e-16 * 16.0 * (sc + 1e-3);
+      S.r_e64[r] = eps * (sc + 1e-3);
       S.r_key[r] = score_key(sc);
       atomicAdd(&A.stats[ST_RESCORED], 1ull);
+    }
+  }
+}
+
+// The re-score of one-target lists (per-target mode, or aggregated with one
+// target; batched screens too): one block of kColThreads per job, the
+// column's shifted sums against the list's target and the refit vectors (if
+// any) by col_sums (FP32 pairs where they apply, else FP64); the score is
+// |sum (v - c) y| / sqrt(Sxx) of the centred unit-norm target, its bound the
+// sums' error scale times (s + 1e-3).  With S.r_x the record {c, S1, S2,
+// E.., eps} of the entry is kept for the refit.
+__global__ void __launch_bounds__(kColThreads) k_rescore1(const SelectArgs S, const ScreenArgs A0,
+                                                          const ScreenArgs *batch) {
+  __shared__ ColShared sh;
+  const unsigned nj = *S.n_jobs;
+  for (unsigned w = blockIdx.x; w < nj; w += gridDim.x) {
+    const unsigned pos = S.job[w], l = S.job_list[w];
+    const ScreenArgs &A = batch ? batch[l] : A0;
+    const int64_t N = A.N;
+    const size_t r = (size_t)l * S.B.cap + pos;
+    const uint64_t gid = S.r_id[r];
+    int op;
+    int64_t a, b;
+    if (gid < (uint64_t)A.n_stored) {
+      op = DSE_OP_PRIMARY;
+      a = (int64_t)gid;
+      b = -1;
+    } else {
+      decode_flat(A.G, gid - (uint64_t)A.n_stored, &op, &a, &b);
+    }
+    const int t = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
+    const int nx = batch ? 0 : S.nx;
+    ColVecs V;
+    V.nv = 1 + nx;
+#pragma unroll
+    for (int m = 0; m < kColVec; ++m) {
+      V.v64[m] = m == 0 ? A.y64 + (int64_t)t * A.ldy : S.xv[m - 1];
+      V.vdf[m] = m == 0 ? (A.ydf ? A.ydf + (int64_t)t * A.ldy : nullptr) : S.xdf[m - 1];
+      V.e[m] = m == 0 || m >= V.nv ? 0 : S.xexp[m - 1];
+    }
+    ColSums cs;
+    col_sums(A.F, op, a, b, N, V, cs, sh);
+    if (threadIdx.x == 0) {
+      const double eps = col_err_scale(cs, N);
+      if (S.r_x && !batch) {
+        double *x = S.r_x + r * 8;
+        x[0] = cs.c;
+        x[1] = cs.acc[0];
+        x[2] = cs.acc[1];
+        for (int m = 0; m < 4; ++m) x[3 + m] = m < nx ? cs.acc[3 + m] : 0.0;
+        x[7] = eps;
+      }
+      if (S.r_need[r]) {
+        const double sc = cs.s0;
+        S.r_s64[r] = sc;
+        S.r_e64[r] = eps * (sc + 1e-3);
+        S.r_key[r] = score_key(sc);
+        atomicAdd(&A.stats[ST_RESCORED], 1ull);
+      }
     }
   }
 }
@@ -482,13 +524,9 @@ dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cuda
   k_sel_exact<<<S.n_lists, 1024, 0, st>>>(S);
   k_sel_classify<<<g, 256, 0, st>>>(S);
   const bool one = batch || A.mode != DSE_MODE_AGGREGATED || A.T == 1;
-  if (!batch && A.N <= 4096) {
-    if (one) k_rescore_warp<1><<<sms * 8, 256, 0, st>>>(S, A);
-    else k_rescore_warp<16><<<sms * 8, 256, 0, st>>>(S, A);
-  } else {
-    if (one) k_rescore<1><<<sms * 8, kRes, 0, st>>>(S, A, batch);
-    else k_rescore<16><<<sms * 8, kRes, 0, st>>>(S, A, batch);
-  }
+  if (one) k_rescore1<<<sms * 8, kColThreads, 0, st>>>(S, A, batch);
+  else if (A.N <= 4096) k_rescore_warp<16><<<sms * 8, 256, 0, st>>>(S, A);
+  else k_rescore<16><<<sms * 8, kRes, 0, st>>>(S, A, batch);
   const dim3 gr((unsigned)std::max(1, std::min(1024, (sms * 2 + S.n_lists - 1) / S.n_lists)), S.n_lists);
   k_rank<<<gr, 256, 0, st>>>(S);
   const dim3 gw((unsigned)std::max(1, std::min(64, (sms + S.n_lists - 1) / S.n_lists)), S.n_lists);

@@ -49,6 +49,7 @@ class ScreenDesc(C.Structure):
 FLAG_TIMING = 1
 FLAG_DEDUP = 2
 FLAG_DIRECT = 4
+FLAG_TIMING_MAIN = 8
 
 
 class Stats(C.Structure):
