@@ -347,6 +347,83 @@ __device__ __forceinline__ bool push_warp(const CandBufs &B, int l, bool want, u
   return p;
 }
 
+// Warp-staged pushes: a warp collects the candidates that reach the list's
+// threshold in a shared-memory stage and writes them out with one slot
+// reservation per flush, instead of one atomic round trip per batch of 32
+// candidates (the same entries and bound counts as push_warp; the threshold
+// is the one the caller read, refreshed by it between tiles).
+template <int CAP>
+struct PushStage {
+  uint64_t id[CAP];
+  float s[CAP], e[CAP];
+};
+
+// count_bounds for the active lanes of a warp, one atomic per distinct bin
+// (entries of a flush cluster near the threshold, so bins repeat).
+__device__ __forceinline__ void count_bounds_warp(const CandBufs &B, int l, bool active, float s, float eps) {
+  const unsigned act = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
+  const int lane = threadIdx.x & 31;
+  const int bl = score_bin(s - eps), bh = score_bin(s + eps), bc = bl / kFine;
+  const unsigned gl = __match_any_sync(act, bl), gc = __match_any_sync(act, bc), gh = __match_any_sync(act, bh);
+  if (lane == __ffs(gl) - 1) atomicAdd(&B.hist[(size_t)l * kNumBins + bl], (unsigned)__popc(gl));
+  if (lane == __ffs(gc) - 1) atomicAdd(&B.hist_c[(size_t)l * kCoarse + bc], (unsigned)__popc(gc));
+  if (lane == __ffs(gh) - 1) atomicAdd(&B.hist_hi[(size_t)l * kNumBins + bh], (unsigned)__popc(gh));
+}
+
+template <int CAP>
+__device__ __forceinline__ void stage_flush(const CandBufs &B, int l, PushStage<CAP> &st, int n) {
+  __syncwarp();
+  if (n <= 0) return;
+  const unsigned lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(&B.count[l], (unsigned)n);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + (int)lane;
+    const bool act = i < n;
+    float s = 0.f, e = 0.f;
+    if (act) {
+      const unsigned pos = base + (unsigned)i;
+      s = st.s[i];
+      e = st.e[i];
+      if ((int64_t)pos < B.cap) {
+        const size_t x = (size_t)l * (size_t)B.cap + pos;
+        B.id[x] = st.id[i];
+        B.score[x] = s;
+        B.eps[x] = e;
+      }
+    }
+    count_bounds_warp(B, l, act, s, e);
+  }
+  __syncwarp();
+}
+
+// Warp-cooperative (every lane calls it); n: the stage's fill (warp-uniform),
+// returned updated; *total counts the warp's pushes.
+template <int CAP>
+__device__ __forceinline__ int stage_push(const CandBufs &B, int l, PushStage<CAP> &st, int n, int *total, float th,
+                                          bool want, uint64_t id, float s, float eps) {
+  static_assert(CAP >= 32, "a stage holds at least one warp's pushes");
+  const unsigned lane = threadIdx.x & 31;
+  const bool p = want && (s + eps >= th);
+  const unsigned m = __ballot_sync(0xffffffffu, p);
+  if (!m) return n;
+  const int c = __popc(m);
+  *total += c;
+  if (n + c > CAP) {
+    stage_flush(B, l, st, n);
+    n = 0;
+  }
+  if (p) {
+    const int pos = n + __popc(m & ((1u << lane) - 1u));
+    st.id[pos] = id;
+    st.s[pos] = s;
+    st.e[pos] = eps;
+  }
+  return n + c;
+}
+
 // Single-lane push (no warp cooperation).
 __device__ __forceinline__ bool push_one(const CandBufs &B, int l, uint64_t id, float s, float eps) {
   float th = ld_relaxed(&B.theta[l]);

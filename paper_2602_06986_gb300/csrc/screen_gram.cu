@@ -42,14 +42,17 @@
 //   warp 0      producer: two 1-D bulk copies per stage (the a- and
 //               b-images of a 32-sample chunk, each already in the canonical
 //               K-major core-matrix layout), 4-stage ring;
-//   warp 1      TMEM allocation (512 columns: two 256-column accumulators)
+//   warp 1      TMEM allocation (256 columns: two 128-column accumulators)
 //               and the MMA issuer: 2 k-steps x 3 products per chunk;
 //   warps 2-9   epilogue: warp w reads the TMEM lanes of quadrant w % 4,
 //               which hold its five a-features' rows, 32 columns at a time
 //               (every other patch: two warps per quadrant) through a private
 //               shared-memory patch, and scores the 120 candidates (5 a x 8 b
-//               x 3 slots) of each patch from a private copy of the 37
-//               features' records (loaded while the tile's MMAs run).
+//               x 3 slots) of each patch from a private copy of the 21
+//               features' records (loaded while the tile's MMAs run); the
+//               passing candidates are staged per warp and written out with
+//               one slot reservation per flush, and the warps' statistics
+//               meet in shared memory before one set of global atomics.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -68,10 +71,12 @@ namespace dse {
 namespace gram {
 
 constexpr int FA = 20;  // a-features per tile
-constexpr int FB = 64;  // b-features per tile
+constexpr int FB = 32;  // b-features per tile (about 2.6 tiles per CTA on medium, so
+                        // that a tile's MMAs run under the previous tile's epilogue)
 constexpr int FW = 5;   // a-features per epilogue warp (6 rows each)
-constexpr int M = 128, NCOL = 256;
-constexpr int NS = 3;
+constexpr int M = 128, NCOL = 4 * FB;
+constexpr int TMEM_COLS = 2 * NCOL;  // two accumulator buffers (a power of two >= 32)
+constexpr int NS = 4;
 constexpr uint32_t A_HALF = M * tc::KC * 2;     // hi or lo part of an a-image chunk
 constexpr uint32_t B_HALF = NCOL * tc::KC * 2;  // hi or lo part of a b-image chunk
 constexpr uint32_t A_IMG = 2 * A_HALF, B_IMG = 2 * B_HALF;
@@ -80,6 +85,8 @@ constexpr int EPI = 8;  // epilogue warps: two per TMEM lane quadrant
 constexpr int THREADS = (2 + EPI) * 32;
 constexpr uint32_t kWait = 1u << 22;
 constexpr int EC = 32;  // TMEM columns per epilogue patch (8 b-features)
+constexpr int PATCHES = NCOL / EC;
+constexpr int PW = PATCHES / 2;  // patches per epilogue warp (two warps per quadrant)
 
 // Row of a-feature f (0..19), type t (0..5: p, p^2, p y of x, then of 1/x):
 // epilogue warp f / 5 owns TMEM lanes 32 (f / 5) .. + 31.
@@ -88,7 +95,7 @@ __host__ __device__ inline int arow(int f, int t) { return 32 * (f / FW) + 6 * (
 __host__ __device__ inline int bcol(int g, int t) { return 4 * g + t; }
 
 // What the epilogue reads of a feature, copied once per tile into the warp's
-// own shared-memory cache (5 a-features + the 32 b-features of its patches).
+// own shared-memory cache (5 a-features + the b-features of its patches).
 struct EpiFeat {
   float4 fa;     // {mean, mean of 1/x, RU max|x|, RD max|x|}
   float2 fr;     // {RU 1/min|x|, RD 1/min|x|}
@@ -97,7 +104,7 @@ struct EpiFeat {
   float c[2], s1[2], s2[2], n1[2], n2[2], nu[2];  // GramFeat
   float sy[2], ny[2];                             // GramTgt
 };
-constexpr int NCACHE = FW + 32;
+constexpr int NCACHE = FW + 8 * PW;
 
 struct Shared {
   uint64_t full[NS], empty[NS];
@@ -107,10 +114,13 @@ struct Shared {
   int abort;
   float E[EPI][32][EC + 1];        // each epilogue warp's patch: its 32 lanes x 32 columns
   EpiFeat cache[EPI][NCACHE];      // each epilogue warp's feature records
+  PushStage<64> stage[EPI];        // each epilogue warp's pending pushes
+  unsigned st[10];                 // the epilogue warps' statistics, summed per CTA
 };
 
 constexpr size_t shared_bytes() { return (sizeof(Shared) + 1023) / 1024 * 1024; }
 constexpr size_t smem_total() { return shared_bytes() + (size_t)NS * STAGE; }
+static_assert(smem_total() <= 227 * 1024, "shared memory of one CTA");
 
 }  // namespace gram
 
@@ -486,11 +496,12 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
     }
     mbar_init(&sh.drain, 1);
     sh.abort = 0;
+    for (int k = 0; k < 10; ++k) sh.st[k] = 0;
     mbar_fence_init();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
-                 "r"(512u)
+                 "r"((uint32_t)TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -585,10 +596,11 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;         // 0 .. EPI-1
     const int q = warp & 3;          // TMEM lane quadrant = a-features 5q .. 5q+4
-    const int h = ew >> 2;           // patches h, h+2, h+4, h+6
+    const int h = ew >> 2;           // patches h, h + 2, ...
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     float(*E)[EC + 1] = sh.E[ew];
     EpiFeat *cache = sh.cache[ew];
+    PushStage<64> &stg = sh.stage[ew];
     LaneStats ls;
     ls.zero();
     const float N = (float)A.N, invN = (float)A.invN;
@@ -599,7 +611,7 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
     for (int tile = blockIdx.x; tile < GA.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
       const int2 tl = GA.tiles[tile];
       // this warp's feature records: a-features 0..4, then the b-features of
-      // its four patches (8 each), while the tile's MMAs run
+      // its patches (8 each), while the tile's MMAs run
       for (int e = lane; e < NCACHE; e += 32) {
         int64_t f;
         if (e < FW) {
@@ -634,8 +646,11 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
       const uint32_t buf = lt & 1, ub = lt >> 1;
       if (!wait_warp(&sh.acc_full[buf], ub & 1)) break;
       fence_after();
-      bool pushed_any = false;
-      for (int pcl = 0; pcl < 4; ++pcl) {
+      // pushes are staged per warp and written out once per tile (or when
+      // the stage fills); the threshold is read afresh for every batch (it
+      // rises while other warps finish their tiles)
+      int staged = 0, pushed = 0;
+      for (int pcl = 0; pcl < PW; ++pcl) {
         const int pc = 2 * pcl + h;
         float v[EC];
         tmem_ld32(tmem + lane_base + buf * NCOL + pc * EC, v);
@@ -644,6 +659,7 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
         __syncwarp();
         // 5 a-features x 8 b-features x 3 slots = 120 candidates
         for (int it = 0; it < 4; ++it) {
+          const float th = ld_relaxed(&A.B.theta[A.t0]);  // issued first: its latency hides behind the scoring
           const int idx = it * 32 + lane;
           const int fi = idx / 24, rem = idx % 24, gj = rem / 3, slot = rem % 3;
           const int64_t i = (int64_t)tl.x * FA + q * FW + fi;
@@ -686,22 +702,45 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
               }
             }
           }
-          pushed_any |= push_warp(A.B, A.t0, want, gid, s, eps);
+          staged = stage_push(A.B, A.t0, stg, staged, &pushed, th, want, gid, s, eps);
         }
         __syncwarp();
       }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
-      if (__any_sync(0xffffffffu, pushed_any)) refresh_theta(A.B, A.t0, A.k);
+      stage_flush(A.B, A.t0, stg, staged);
+      if (pushed > 0) refresh_theta(A.B, A.t0, A.k);
     }
-    flush_stats(A, ls, 1);
+    // statistics: the warps' counters meet in shared memory, then one set of
+    // global atomics per CTA (thousands of warps adding to the same few
+    // counters at once would queue at the L2)
+    {
+      const unsigned v[10] = {ls.seen, ls.r[0], ls.r[1], ls.r[2], ls.r[3], ls.r[4], ls.r[5], ls.r[DSE_VALID],
+                              ls.evaluated, ls.escalated};
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        unsigned t = v[k];
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0 && t) atomicAdd(&sh.st[k], t);
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI * 32) : "memory");
+      if (ew == 0 && lane < 10 && A.first_pass) {
+        const unsigned t = sh.st[lane];
+        const int dst = lane == 0   ? ST_ADD_SEEN
+                        : lane < 7  ? ST_REASON0 + (lane - 1)
+                        : lane == 7 ? ST_VALID_G0 + 1
+                        : lane == 8 ? ST_EVALUATED
+                                    : ST_ESCALATED;
+        if (t) atomicAdd(&A.stats[dst], (unsigned long long)t);
+      }
+    }
   }
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TMEM_COLS) : "memory");
 }
 
 // ------------------------------------------------------------------- host
