@@ -41,7 +41,7 @@
 // Warp roles (one CTA per SM, persistent over a static tile stride):
 //   warp 0      producer: two 1-D bulk copies per stage (the a- and
 //               b-images of a 32-sample chunk, each already in the canonical
-//               K-major core-matrix layout), 4-stage ring;
+//               K-major core-matrix layout), 5-stage ring;
 //   warp 1      TMEM allocation (256 columns: two 128-column accumulators)
 //               and the MMA issuer: 2 k-steps x 3 products per chunk;
 //   warps 2-9   epilogue: warp w reads the TMEM lanes of quadrant w % 4,
@@ -76,7 +76,7 @@ constexpr int FB = 32;  // b-features per tile (about 2.6 tiles per CTA on mediu
 constexpr int FW = 5;   // a-features per epilogue warp (6 rows each)
 constexpr int M = 128, NCOL = 4 * FB;
 constexpr int TMEM_COLS = 2 * NCOL;  // two accumulator buffers (a power of two >= 32)
-constexpr int NS = 4;
+constexpr int NS = 5;  // stages: the ring is bound by the copies' latency (about 2k cycles)
 constexpr uint32_t A_HALF = M * tc::KC * 2;     // hi or lo part of an a-image chunk
 constexpr uint32_t B_HALF = NCOL * tc::KC * 2;  // hi or lo part of a b-image chunk
 constexpr uint32_t A_IMG = 2 * A_HALF, B_IMG = 2 * B_HALF;
