@@ -261,38 +261,59 @@ __device__ __forceinline__ bool col_sums_pair(const FeatTable &F, int op, int64_
   // (2^-48 of |a| + |b|), which cancellation amplifies relative to v: its
   // conditioning sum takes (|a| + |b|)^2 instead of v^2
   const bool additive = op == DSE_OP_ADD || op == DSE_OP_SUB || op == DSE_OP_ABSDIFF;
-  auto value = [&](int64_t s, float *mag) -> F2 {
-    const F2 x{__fmul_rn(ah[s], fa), __fmul_rn(al[s], fa)};
-    const F2 y{__fmul_rn(bh[s], fb), __fmul_rn(bl[s], fb)};
+  auto value = [&](float xh, float xl, float yh, float yl, float *mag) -> F2 {
+    const F2 x{__fmul_rn(xh, fa), __fmul_rn(xl, fa)};
+    const F2 y{__fmul_rn(yh, fb), __fmul_rn(yl, fb)};
     const F2 v = eval_pair(op, x, y);
     *mag = additive ? __fadd_rn(fabsf(x.hi), fabsf(y.hi)) : fabsf(v.hi);
     return v;
   };
   float mag0;
-  const F2 c = value(0, &mag0);
+  const F2 c = value(ah[0], al[0], bh[0], bl[0], &mag0);
   const F2 nc = neg(c);
   Acc s1, s2, p[NV];
   float sv = 0.0f, vmax = 0.0f;
-  for (int64_t s = threadIdx.x; s < N; s += kColThreads) {
-    float mag;
-    const F2 v = value(s, &mag);
-    const F2 d = add(v, nc);
-    s1.add(d.hi, d.lo);
-    {
-      const float q = __fmul_rn(d.hi, d.hi);
-      const float qe = __fmaf_rn(__fadd_rn(d.hi, d.hi), d.lo, __fmaf_rn(d.hi, d.hi, -q));
-      s2.add(q, qe);
-    }
-    sv = __fmaf_rn(mag, mag, sv);
-    vmax = fmaxf(vmax, fabsf(v.hi));
+  // two samples per thread per step, their loads issued together (the pass
+  // is bound by load latency otherwise); each thread takes its samples in
+  // increasing order
+  constexpr int U = 2;
+  for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * kColThreads) {
+    float lh[U], ll[U], rh[U], rl[U];
+    float2 wv[U][NV];
 #pragma unroll
-    for (int m = 0; m < NV; ++m) {
-      const float2 w = V.vdf[m][s];
-      const float q = __fmul_rn(d.hi, w.x);
-      float qe = __fmaf_rn(d.hi, w.x, -q);
-      qe = __fmaf_rn(d.hi, w.y, qe);
-      qe = __fmaf_rn(d.lo, w.x, qe);
-      p[m].add(q, qe);
+    for (int k = 0; k < U; ++k) {
+      const int64_t s = s0 + (int64_t)k * kColThreads;
+      const bool in = s < N;
+      lh[k] = in ? ah[s] : 0.0f;
+      ll[k] = in ? al[s] : 0.0f;
+      rh[k] = in ? bh[s] : 0.0f;
+      rl[k] = in ? bl[s] : 0.0f;
+#pragma unroll
+      for (int m = 0; m < NV; ++m) wv[k][m] = in ? V.vdf[m][s] : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (s0 + (int64_t)k * kColThreads >= N) break;
+      float mag;
+      const F2 v = value(lh[k], ll[k], rh[k], rl[k], &mag);
+      const F2 d = add(v, nc);
+      s1.add(d.hi, d.lo);
+      {
+        const float q = __fmul_rn(d.hi, d.hi);
+        const float qe = __fmaf_rn(__fadd_rn(d.hi, d.hi), d.lo, __fmaf_rn(d.hi, d.hi, -q));
+        s2.add(q, qe);
+      }
+      sv = __fmaf_rn(mag, mag, sv);
+      vmax = fmaxf(vmax, fabsf(v.hi));
+#pragma unroll
+      for (int m = 0; m < NV; ++m) {
+        const float2 w = wv[k][m];
+        const float q = __fmul_rn(d.hi, w.x);
+        float qe = __fmaf_rn(d.hi, w.x, -q);
+        qe = __fmaf_rn(d.hi, w.y, qe);
+        qe = __fmaf_rn(d.lo, w.x, qe);
+        p[m].add(q, qe);
+      }
     }
   }
   s1.warp_reduce();

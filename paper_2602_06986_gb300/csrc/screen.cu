@@ -267,16 +267,32 @@ __device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, ui
   R o1 = 0, o2 = 0, oy[NT];
   for (int t = 0; t < NT; ++t) Sy[t] = oy[t] = 0;
   int blk = 0;
-  for (int64_t s = lane; s < Ns; s += 32) {
-    R v = unary_eval<R>(op, x[s], c);
-    S1 += v;
-    S2 = Num<R>::fma_(v, v, S2);
-    for (int t = 0; t < NT; ++t)
-      if (t < T) Sy[t] = Num<R>::fma_(v, Y[(int64_t)(t0 + t) * ldy + s], Sy[t]);
-    if (sizeof(R) == 4 && ++blk == 16) {
-      blk = 0;
-      o1 += S1; o2 += S2; S1 = 0; S2 = 0;
-      for (int t = 0; t < NT; ++t) { oy[t] += Sy[t]; Sy[t] = 0; }
+  // one target: four samples per lane per step, their loads issued
+  // together (the loop is bound by load latency otherwise); the sums take
+  // them in sample order
+  constexpr int U = NT == 1 ? 4 : 1;
+  for (int64_t s0 = lane; s0 < Ns; s0 += 32 * U) {
+    R xs[U], ys[U][NT];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t s = s0 + 32 * k;
+      xs[k] = s < Ns ? x[s] : R(0);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) ys[k][t] = (s < Ns && t < T) ? Y[(int64_t)(t0 + t) * ldy + s] : R(0);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (s0 + 32 * k >= Ns) break;
+      R v = unary_eval<R>(op, xs[k], c);
+      S1 += v;
+      S2 = Num<R>::fma_(v, v, S2);
+      for (int t = 0; t < NT; ++t)
+        if (t < T) Sy[t] = Num<R>::fma_(v, ys[k][t], Sy[t]);
+      if (sizeof(R) == 4 && ++blk == 16) {
+        blk = 0;
+        o1 += S1; o2 += S2; S1 = 0; S2 = 0;
+        for (int t = 0; t < NT; ++t) { oy[t] += Sy[t]; Sy[t] = 0; }
+      }
     }
   }
   S1 += o1;
@@ -1054,17 +1070,34 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
     decode_gid(A, gid, &op, &a, &b);
     const double c = cand_value64(A.F, A.G, A.n_stored, gid, 0, op, a, b);
     const double *y = A.y64 + (int64_t)A.t0 * A.ldy;
-    // sum (v-c), sum (v-c)^2, sum v^2, non-finite count, sum (v-c) y, sum y
+    // sum (v-c), sum (v-c)^2, sum v^2, non-finite count, sum (v-c) y, sum y;
+    // four samples per thread per step, their loads issued together, each
+    // thread taking its samples in increasing order
     double st[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int64_t s = threadIdx.x; s < N; s += kEsc) {
-      const double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
-      if (!isfinite(v)) st[3] += 1.0;
-      const double d = v - c;
-      st[0] += d;
-      st[1] = fma(d, d, st[1]);
-      st[2] = fma(v, v, st[2]);
-      st[4] = fma(d, y[s], st[4]);
-      st[5] += y[s];
+    const double *xa = A.F.v64 + a * A.F.ld, *xb = A.F.v64 + (b >= 0 ? b : a) * A.F.ld;
+    constexpr int U = 4;
+    for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * kEsc) {
+      double va[U], vb[U], yv[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int64_t s = s0 + (int64_t)k * kEsc;
+        const bool in = s < N;
+        va[k] = in ? xa[s] : 0.0;
+        vb[k] = in && b >= 0 ? xb[s] : 0.0;
+        yv[k] = in ? y[s] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (s0 + (int64_t)k * kEsc >= N) break;
+        const double v = eval_op64(op, va[k], vb[k]);
+        if (!isfinite(v)) st[3] += 1.0;
+        const double d = v - c;
+        st[0] += d;
+        st[1] = fma(d, d, st[1]);
+        st[2] = fma(v, v, st[2]);
+        st[4] = fma(d, yv[k], st[4]);
+        st[5] += yv[k];
+      }
     }
     block_sum64<6>(st, sm);
     if (threadIdx.x == 0) {  // (FP64 work is slow on this part: one thread decides)
