@@ -107,7 +107,7 @@ __global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double 
     for (int d = 0; d <= c; ++d) Gm[c][d] = warp_sum64(Gm[c][d]);
   }
   // Cholesky G = L L^T (every lane computes the same small factorisation)
-  double L[kMaxP][kMaxP] = {};
+  double L[kMaxP][kMaxP] = {}, Li[kMaxP] = {};
   bool ok = true;
   for (int c = 0; c < p; ++c) {
     double dsum = Gm[c][c];
@@ -121,10 +121,11 @@ __global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double 
       ok = false;
       break;
     }
+    Li[c] = 1.0 / L[c][c];
     for (int r = c + 1; r < p; ++r) {
       double v = Gm[r][c];
       for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
-      L[r][c] = v / L[c][c];
+      L[r][c] = v * Li[c];
     }
   }
   double beta[kMaxP + 1] = {};
@@ -133,12 +134,12 @@ __global__ void k_refit(FeatTable F, RungGeom G, int64_t n_stored, const double 
     for (int c = 0; c < p; ++c) {
       double v = g[c];
       for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
-      z[c] = v / L[c][c];
+      z[c] = v * Li[c];
     }
     for (int c = p - 1; c >= 0; --c) {
       double v = z[c];
       for (int k = c + 1; k < p; ++k) v -= L[k][c] * beta[k + 1];
-      beta[c + 1] = v / L[c][c];
+      beta[c + 1] = v * Li[c];
     }
     double b0 = my;
     for (int c = 0; c < p; ++c) b0 -= beta[c + 1] * m[c];
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(kPrep) k_refit_prep(const double *y, const dou
 #pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreNorm + c] = sqrt(acc[kMaxP * kMaxP + kMaxP + c]);
     // the fixed-only fit: Cholesky with the collinearity test on the pivots
-    double L[kMaxP][kMaxP] = {}, z[kMaxP] = {}, bf[kMaxP] = {};
+    double L[kMaxP][kMaxP] = {}, Li[kMaxP] = {}, z[kMaxP] = {}, bf[kMaxP] = {};
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < nf; ++c) {
@@ -261,14 +262,15 @@ __global__ void __launch_bounds__(kPrep) k_refit_prep(const double *y, const dou
 #pragma unroll
       for (int k = 0; k < c; ++k) dsum -= L[c][k] * L[c][k];
       const double piv = dsum > 0.0 ? sqrt(dsum) : 0.0;
-      ok = ok && dsum > 0.0 && piv > 1e-12 * sqrt(acc[kMaxP * kMaxP + kMaxP + c]);
+      ok = ok && dsum > 0.0 && dsum > 1e-24 * acc[kMaxP * kMaxP + kMaxP + c];  // piv > 1e-12 |column|
       L[c][c] = ok ? piv : 1.0;
+      Li[c] = 1.0 / L[c][c];  // one division per pivot (FP64 division is a long serial chain here)
 #pragma unroll
       for (int r = c + 1; r < nf; ++r) {
         double v = acc[r * kMaxP + c];
 #pragma unroll
         for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
-        L[r][c] = v / L[c][c];
+        L[r][c] = v * Li[c];
       }
     }
 #pragma unroll
@@ -276,14 +278,14 @@ __global__ void __launch_bounds__(kPrep) k_refit_prep(const double *y, const dou
       double v = acc[kMaxP * kMaxP + c];
 #pragma unroll
       for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
-      z[c] = v / L[c][c];
+      z[c] = v * Li[c];
     }
 #pragma unroll
     for (int c = nf - 1; c >= 0; --c) {
       double v = z[c];
 #pragma unroll
       for (int k = c + 1; k < nf; ++k) v -= L[k][c] * bf[k];
-      bf[c] = v / L[c][c];
+      bf[c] = v * Li[c];
     }
 #pragma unroll
     for (int i = 0; i < kMaxP * kMaxP; ++i) pre[kPreL + i] = L[i / kMaxP][i % kMaxP];
@@ -488,10 +490,11 @@ __global__ void k_refit_solve(const double *out_x, const uint64_t *cand, int64_t
 // terms that involve v are accumulated: Σv, Σv², then Σd², Σd·f_j, Σd·y with
 // d = v - mean(v), then the residual.  CACHE: v is evaluated once into
 // shared memory (N doubles); FP64 arithmetic is the cost on this part.
-// Launched twice per fit: for the fits flagged by k_refit_solve (`only`),
-// then in `near` mode for every fit whose RSS, within its error bound,
-// could be the smallest; a fit done here has err 0 (its RSS is the FP64
-// fit's), so the pick and its RMSE are those of an FP64 fit.
+// In `near` mode (the refit chain) a block does the fits flagged by
+// k_refit_solve (`only`) and every fit whose RSS, within its error bound,
+// could be the smallest of the unflagged ones: a fit left out has a true
+// RSS above that of the best unflagged fit, which is done here, so the pick
+// and its RMSE are those of an FP64 fit (err 0 marks a fit done here).
 constexpr int64_t kRefitCacheMax = 6144;  // samples (48 KiB)
 
 template <bool CACHE, int NF>
@@ -507,13 +510,16 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
   extern __shared__ double col[];
   const int64_t w = blockIdx.x;
   if (w >= n_cand || (n_dev && w >= *n_dev)) return;
-  if (only && !only[w]) return;
   const int64_t N = F.N;
-  if (near) {
+  const bool flagged = only && only[w];
+  if (near && !flagged) {
     // a fit whose RSS, within its error bound, could be the smallest:
-    // RSS_w - err_w <= min_j (RSS_j + err_j)
+    // RSS_w - err_w <= min_j (RSS_j + err_j) over the unflagged fits (the
+    // flagged ones are done here anyway)
     const double r = rmse_out[w], e = err_out[w];
     if (!(r < INFINITY) || !(e > 0.0) || ord_key(r * r * (double)N - e) > *minkey) return;
+  } else if (!near && only && !flagged) {
+    return;
   }
   constexpr int p = nf + 1;
   const uint64_t gid = cand[w];
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
     Gm[nf][nf] = s2[kMaxP];
     g[nf] = s2[kMaxP + 1];
     nrm[nf] = sqrt(s1[1]);
-    double L[kMaxP][kMaxP] = {};
+    double L[kMaxP][kMaxP] = {}, Li[kMaxP] = {};
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < p; ++c) {
@@ -572,12 +578,13 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
       const double piv = dsum > 0.0 ? sqrt(dsum) : 0.0;
       ok = ok && dsum > 0.0 && piv > 1e-12 * nrm[c];
       L[c][c] = ok ? piv : 1.0;
+      Li[c] = 1.0 / L[c][c];  // one division per pivot (FP64 division is a long serial chain here)
 #pragma unroll
       for (int r = c + 1; r < p; ++r) {
         double v = Gm[r][c];
 #pragma unroll
         for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
-        L[r][c] = v / L[c][c];
+        L[r][c] = v * Li[c];
       }
     }
     double beta[kMaxP + 1] = {};
@@ -588,14 +595,14 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
         double v = g[c];
 #pragma unroll
         for (int k = 0; k < c; ++k) v -= L[c][k] * z[k];
-        z[c] = v / L[c][c];
+        z[c] = v * Li[c];
       }
 #pragma unroll
       for (int c = p - 1; c >= 0; --c) {
         double v = z[c];
 #pragma unroll
         for (int k = c + 1; k < p; ++k) v -= L[k][c] * beta[k + 1];
-        beta[c + 1] = v / L[c][c];
+        beta[c + 1] = v * Li[c];
       }
       double b0 = pre[kPreMy];
 #pragma unroll
@@ -625,10 +632,7 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
     }
   }
   block_sum_arr<1>(rss, sm);
-  if (threadIdx.x == 0) {
-    rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
-    if (ok && !near) atomicMin(minkey, ord_key(rss[0]));
-  }
+  if (threadIdx.x == 0) rmse_out[w] = ok ? sqrt(rss[0] / (double)N) : INFINITY;
 }
 
 __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
@@ -708,10 +712,9 @@ static void fit_nf(const FeatTable &F, const dse_space *S, const uint64_t *fid, 
       k_refit_wide<false, NF><<<(unsigned)cap, kWide, 0, st>>>(F, S->geom, S->n, b.fcc, b.ycc, b.pre, fid, cand, cap,
                                                                 n_dev, b.rm, b.beta, only, b.err, b.minkey, near);
   };
-  // the fits the sums cannot resolve (near-perfect ones), then every fit
-  // that could still be the best within its error bound, in FP64
-  wide(b.flag, false);
-  wide(nullptr, true);
+  // in FP64: the fits the sums cannot resolve (near-perfect ones) and every
+  // fit that could still be the best within its error bound
+  wide(b.flag, true);
 }
 
 // The fixed columns' statistics and residual (before the screen whose
@@ -755,7 +758,7 @@ void refit_chain_fit(dse_space *S, const double *y, const uint64_t *fid, int nf,
   const RefitBufs b = carve(scratch, S->N, cap);
   const FeatTable F = table_of(S);
   if (!have_sums) cudaMemsetAsync(b.outx, 0, 64 * (size_t)cap, st);
-  note_launches(6);
+  note_launches(5);
   switch (nf) {
     case 0: fit_nf<0>(F, S, fid, cand, cap, n_dev, b, st); break;
     case 1: fit_nf<1>(F, S, fid, cand, cap, n_dev, b, st); break;

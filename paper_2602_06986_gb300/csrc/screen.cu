@@ -43,30 +43,42 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // into rows y64 / y32 of ldy (zero beyond N) and the sum of the FP32 row.
 __device__ void target_prep(const double *y, int64_t N, int32_t ldy, double *y64, float *y32, float2 *ydf,
                             float *ysum32, int *err) {
-  __shared__ double red[32];
-  auto block_sum = [&](double v) {
+  // warp partials, then thread 0 finishes each reduction and broadcasts what
+  // the block needs (FP64 work in every thread is slow on this part)
+  __shared__ double red[32], bc[2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  auto partial = [&](double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if (lane == 0) red[w] = v;
     __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    __syncthreads();
-    return tot;
+  };
+  auto total = [&]() {
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += red[k];
+    return t;
   };
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += y[i];
-  const double mean = block_sum(s) / (double)N;
+  partial(s);
+  if (threadIdx.x == 0) bc[0] = total() / (double)N;
+  __syncthreads();
+  const double mean = bc[0];
   double q = 0.0;
   for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
     double d = y[i] - mean;
     q = fma(d, d, q);
   }
-  const double syy = block_sum(q);
-  if (!(syy > 0.0) || !isfinite(syy)) {
+  partial(q);
+  if (threadIdx.x == 0) {
+    const double syy = total();
+    bc[1] = (syy > 0.0 && isfinite(syy)) ? 1.0 / sqrt(syy) : 0.0;
+  }
+  __syncthreads();
+  const double inv = bc[1];
+  if (!(inv > 0.0)) {
     if (threadIdx.x == 0) atomicExch(err, DSE_EINVAL);
     return;
   }
-  const double inv = 1.0 / sqrt(syy);
   double fs = 0.0;
   for (int64_t i = threadIdx.x; i < ldy; i += blockDim.x) {
     double v = i < N ? (y[i] - mean) * inv : 0.0;
@@ -76,8 +88,8 @@ __device__ void target_prep(const double *y, int64_t N, int32_t ldy, double *y64
     if (ydf) ydf[i] = make_float2(f, __double2float_rn(__dsub_rn(v, (double)f)));
     fs += (double)f;
   }
-  fs = block_sum(fs);
-  if (threadIdx.x == 0) *ysum32 = (float)fs;
+  partial(fs);
+  if (threadIdx.x == 0) *ysum32 = (float)total();
 }
 
 // One block per target.
