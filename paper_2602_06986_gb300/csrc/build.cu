@@ -352,28 +352,74 @@ static dse_status table_alloc(TableArrays &t, int64_t cap, int64_t ld, bool rule
   return DSE_OK;
 }
 
+// The features ordered by unit key (two 64-bit words, high word first), ties
+// by id (the host's stable sort of the same keys gives the same order), as
+// row ids: row f goes to position rank(f) = #{g : key_g < key_f, or equal
+// keys and g < f}; one_class: the identity.  rowid_ident gets 0..n-1.
+__global__ void k_class_rows(const uint64_t *ukey, int64_t n, int one_class, int32_t *class_rows,
+                             int32_t *rowid_ident) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  rowid_ident[f] = (int32_t)f;
+  if (one_class) {
+    class_rows[f] = (int32_t)f;
+    return;
+  }
+  const uint64_t k1 = ukey[2 * f + 1], k0 = ukey[2 * f];
+  int64_t rank = 0;
+  for (int64_t g = 0; g < n; ++g) {
+    const uint64_t g1 = ukey[2 * g + 1], g0 = ukey[2 * g];
+    rank += (g1 < k1 || (g1 == k1 && (g0 < k0 || (g0 == k0 && g < f)))) ? 1 : 0;
+  }
+  class_rows[rank] = (int32_t)f;
+}
+
+// Up to 16 device-to-device copies in one launch (blockIdx.y: the copy;
+// 4-byte words: every table array holds 4- or 8-byte elements).
+struct CopySegs {
+  uint32_t *dst[16];
+  const uint32_t *src[16];
+  uint64_t words[16];
+  int n;
+};
+
+__global__ void k_copy_segments(const CopySegs c) {
+  const int k = blockIdx.y;
+  if (k >= c.n) return;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.words[k];
+       i += (uint64_t)gridDim.x * blockDim.x)
+    c.dst[k][i] = c.src[k][i];
+}
+
 static dse_status table_copy(TableArrays &dst, const TableArrays &src, int64_t n, int64_t ld, cudaStream_t s) {
-  auto cp = [&](void *d, const void *x, size_t bytes) {
-    return cudaMemcpyAsync(d, x, bytes, cudaMemcpyDeviceToDevice, s);
-  };
-  cudaError_t e = cudaSuccess;
   if (n == 0) return DSE_OK;
-  e = cp(dst.v64, src.v64, sizeof(double) * n * ld);
-  if (!e) e = cp(dst.mean64, src.mean64, 8 * n);
-  if (!e) e = cp(dst.rmean64, src.rmean64, 8 * n);
-  if (!e) e = cp(dst.min64, src.min64, 8 * n);
-  if (!e) e = cp(dst.max64, src.max64, 8 * n);
-  if (!e) e = cp(dst.minabs64, src.minabs64, 8 * n);
-  if (!e) e = cp(dst.maxabs64, src.maxabs64, 8 * n);
-  if (!e) e = cp(dst.minabsnz64, src.minabsnz64, 8 * n);
-  if (!e) e = cp(dst.op, src.op, 4 * n);
-  if (!e) e = cp(dst.cplx, src.cplx, 4 * n);
-  if (!e) e = cp(dst.units, src.units, 4 * n * kMaxDims);
-  if (!e) e = cp(dst.ca, src.ca, 8 * n);
-  if (!e) e = cp(dst.cb, src.cb, 8 * n);
-  if (!e && src.used) e = cp(dst.used, src.used, 8 * n);
-  if (!e && src.dmask) e = cp(dst.dmask, src.dmask, 8 * n);
-  if (e) return cuda_status(e, "table copy");
+  CopySegs c{};
+  auto add = [&](void *d, const void *x, size_t bytes) {
+    if (!d || !x) return;
+    c.dst[c.n] = static_cast<uint32_t *>(d);
+    c.src[c.n] = static_cast<const uint32_t *>(x);
+    c.words[c.n] = bytes / 4;
+    ++c.n;
+  };
+  add(dst.v64, src.v64, sizeof(double) * n * ld);
+  add(dst.mean64, src.mean64, 8 * n);
+  add(dst.rmean64, src.rmean64, 8 * n);
+  add(dst.min64, src.min64, 8 * n);
+  add(dst.max64, src.max64, 8 * n);
+  add(dst.minabs64, src.minabs64, 8 * n);
+  add(dst.maxabs64, src.maxabs64, 8 * n);
+  add(dst.minabsnz64, src.minabsnz64, 8 * n);
+  add(dst.op, src.op, 4 * n);
+  add(dst.cplx, src.cplx, 4 * n);
+  add(dst.units, src.units, 4 * n * kMaxDims);
+  add(dst.ca, src.ca, 8 * n);
+  add(dst.cb, src.cb, 8 * n);
+  add(dst.used, src.used, 8 * n);
+  add(dst.dmask, src.dmask, 8 * n);
+  const uint64_t big = (uint64_t)2 * n * ld;  // the rows are the longest copy
+  note_launches(1);
+  k_copy_segments<<<dim3((unsigned)std::min<uint64_t>(1024, (big + 255) / 256), (unsigned)c.n), 256, 0, s>>>(c);
+  DSE_CUDA(cudaGetLastError());
   return DSE_OK;
 }
 
@@ -527,24 +573,39 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
         hun[f * kMaxDims + k] = (int32_t)u;
       }
     }
-    // (host-to-device copies from pageable memory are staged before the
-    // calls return, so the host vectors may go out of scope)
+    // the uploads go through the thread's pinned staging area (a copy from
+    // pageable memory would synchronise the stream first); its next users
+    // in this build write it only after a stream synchronisation, and the
+    // device reads it in stream order before anything later lands there
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t tot = r256(8 * nk) + 2 * r256(4 * nk) + r256((size_t)4 * nk * kMaxDims) + 2 * r256(8 * nk) +
+                       (rules ? 2 * r256(8 * nk) : 0);
+    char *hst = static_cast<char *>(pinned_staging(tot));
+    if (!hst) return DSE_ENOMEM;
     int64_t *keep_d = nullptr;
     DSE_TRY(dalloc(&keep_d, nk, "kept primaries"));
-    DSE_CUDA(cudaMemcpyAsync(keep_d, keep.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+    size_t off = 0;
+    auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+      if (!bytes) return cudaSuccess;
+      memcpy(hst + off, src, bytes);
+      const cudaError_t e = cudaMemcpyAsync(dst, hst + off, bytes, cudaMemcpyHostToDevice, st);
+      off += r256(bytes);
+      return e;
+    };
+    DSE_CUDA(up(keep_d, keep.data(), 8 * nk));
     note_launches(1);
     k_take_rows<<<(unsigned)nk, 128, 0, st>>>(keep_d, nk, ld, T0.v64, T0.mean64, T0.rmean64, T0.min64, T0.max64,
                                               T0.minabs64, T0.maxabs64, T0.minabsnz64, T.v64, T.mean64, T.rmean64,
                                               T.min64, T.max64, T.minabs64, T.maxabs64, T.minabsnz64);
     dfree(keep_d);
-    DSE_CUDA(cudaMemcpyAsync(T.op, hop.data(), 4 * nk, cudaMemcpyHostToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(T.cplx, hcx.data(), 4 * nk, cudaMemcpyHostToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(T.units, hun.data(), 4 * nk * kMaxDims, cudaMemcpyHostToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(T.ca, hca.data(), 8 * nk, cudaMemcpyHostToDevice, st));
-    DSE_CUDA(cudaMemcpyAsync(T.cb, hcb.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(up(T.op, hop.data(), 4 * nk));
+    DSE_CUDA(up(T.cplx, hcx.data(), 4 * nk));
+    DSE_CUDA(up(T.units, hun.data(), (size_t)4 * nk * kMaxDims));
+    DSE_CUDA(up(T.ca, hca.data(), 8 * nk));
+    DSE_CUDA(up(T.cb, hcb.data(), 8 * nk));
     if (rules) {
-      DSE_CUDA(cudaMemcpyAsync(T.used, hused.data(), 8 * nk, cudaMemcpyHostToDevice, st));
-      DSE_CUDA(cudaMemcpyAsync(T.dmask, hdmask.data(), 8 * nk, cudaMemcpyHostToDevice, st));
+      DSE_CUDA(up(T.used, hused.data(), 8 * nk));
+      DSE_CUDA(up(T.dmask, hdmask.data(), 8 * nk));
     }
     T0.release();
   }
@@ -726,10 +787,18 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   S->h_class_begin.push_back(n);
   DSE_TRY(dalloc(&S->class_rows, n, "class rows"));
   DSE_TRY(dalloc(&S->rowid_ident, n, "row ids"));
-  std::vector<int32_t> ident(n);
-  std::iota(ident.begin(), ident.end(), 0);
-  DSE_CUDA(cudaMemcpyAsync(S->class_rows, rows.data(), 4 * n, cudaMemcpyHostToDevice, st));
-  DSE_CUDA(cudaMemcpyAsync(S->rowid_ident, ident.data(), 4 * n, cudaMemcpyHostToDevice, st));
+  if (n <= 8192) {
+    // the same order computed on the device (an upload from pageable memory
+    // would synchronise the stream; the rank count is O(n^2))
+    note_launches(1);
+    k_class_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S->ukey, n, one_class ? 1 : 0, S->class_rows,
+                                                             S->rowid_ident);
+  } else {
+    std::vector<int32_t> ident(n);
+    std::iota(ident.begin(), ident.end(), 0);
+    DSE_CUDA(cudaMemcpyAsync(S->class_rows, rows.data(), 4 * n, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(S->rowid_ident, ident.data(), 4 * n, cudaMemcpyHostToDevice, st));
+  }
 
   S->geom = make_geom(S, d->max_rung);
   S->slots[d->max_rung] = S->geom.slots;

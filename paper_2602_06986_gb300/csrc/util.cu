@@ -89,7 +89,11 @@ void *pinned_staging(size_t bytes) {
   if (bytes > g_pinned.bytes) {
     size_t want = 4096;
     while (want < bytes) want <<= 1;
-    if (g_pinned.p) cudaFreeHost(g_pinned.p);
+    // an asynchronous upload from the old area may still be in flight
+    if (g_pinned.p) {
+      cudaDeviceSynchronize();
+      cudaFreeHost(g_pinned.p);
+    }
     g_pinned.p = nullptr;
     g_pinned.bytes = 0;
     if (cudaMallocHost(&g_pinned.p, want) != cudaSuccess) {
