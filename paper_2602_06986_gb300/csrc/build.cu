@@ -356,22 +356,35 @@ static dse_status table_alloc(TableArrays &t, int64_t cap, int64_t ld, bool rule
 // by id (the host's stable sort of the same keys gives the same order), as
 // row ids: row f goes to position rank(f) = #{g : key_g < key_f, or equal
 // keys and g < f}; one_class: the identity.  rowid_ident gets 0..n-1.
+// One warp per feature, lanes over the keys (staged in shared memory when
+// they fit: 16 n bytes for n <= kClassStage).
+constexpr int64_t kClassStage = 2048;
+
 __global__ void k_class_rows(const uint64_t *ukey, int64_t n, int one_class, int32_t *class_rows,
                              int32_t *rowid_ident) {
-  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ uint64_t sk[];
+  const bool staged = n <= kClassStage;
+  if (staged && !one_class) {
+    for (int64_t i = threadIdx.x; i < 2 * n; i += blockDim.x) sk[i] = ukey[i];
+    __syncthreads();
+  }
+  const uint64_t *K = staged ? sk : ukey;
+  const int lane = threadIdx.x & 31;
+  const int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (f >= n) return;
-  rowid_ident[f] = (int32_t)f;
+  if (lane == 0) rowid_ident[f] = (int32_t)f;
   if (one_class) {
-    class_rows[f] = (int32_t)f;
+    if (lane == 0) class_rows[f] = (int32_t)f;
     return;
   }
-  const uint64_t k1 = ukey[2 * f + 1], k0 = ukey[2 * f];
-  int64_t rank = 0;
-  for (int64_t g = 0; g < n; ++g) {
-    const uint64_t g1 = ukey[2 * g + 1], g0 = ukey[2 * g];
-    rank += (g1 < k1 || (g1 == k1 && (g0 < k0 || (g0 == k0 && g < f)))) ? 1 : 0;
+  const uint64_t k1 = K[2 * f + 1], k0 = K[2 * f];
+  unsigned rank = 0;
+  for (int64_t g = lane; g < n; g += 32) {
+    const uint64_t g1 = K[2 * g + 1], g0 = K[2 * g];
+    rank += (g1 < k1 || (g1 == k1 && (g0 < k0 || (g0 == k0 && g < f)))) ? 1u : 0u;
   }
-  class_rows[rank] = (int32_t)f;
+  for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+  if (lane == 0) class_rows[rank] = (int32_t)f;
 }
 
 // Up to 16 device-to-device copies in one launch (blockIdx.y: the copy;
@@ -791,8 +804,9 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
     // the same order computed on the device (an upload from pageable memory
     // would synchronise the stream; the rank count is O(n^2))
     note_launches(1);
-    k_class_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S->ukey, n, one_class ? 1 : 0, S->class_rows,
-                                                             S->rowid_ident);
+    const size_t shm = n <= kClassStage && !one_class ? (size_t)16 * n : 0;
+    k_class_rows<<<(unsigned)((n + 7) / 8), 256, shm, st>>>(S->ukey, n, one_class ? 1 : 0, S->class_rows,
+                                                           S->rowid_ident);
   } else {
     std::vector<int32_t> ident(n);
     std::iota(ident.begin(), ident.end(), 0);

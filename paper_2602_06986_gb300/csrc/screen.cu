@@ -864,32 +864,46 @@ __device__ __forceinline__ void pairlist_one(const ScreenArgs &A, int64_t ia, in
 #pragma unroll
     for (int e = 0; e < 2 + NT; ++e) acc[k][e] = tot[k][e] = R(0);
   int blk = 0;
-  for (int64_t s = lane; s < Ns; s += 32) {
-    const R a = xa[s], b = xb[s];
-    const R ac = a - mi, bc = b - mj, d = a - b;
-    R w3[3];
-    w3[0] = ac + bc;
-    w3[1] = ac - bc;
-    w3[2] = (d < R(0) ? -d : d) - cabs;
-    R y[NT];
+  // one target: four samples per lane per step, their loads issued together
+  // (the loop is bound by load latency otherwise), taken in sample order
+  constexpr int U = NT == 1 ? 4 : 1;
+  for (int64_t s0 = lane; s0 < Ns; s0 += 32 * U) {
+    R av[U], bv[U], yv[U][NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) y[t] = t < T ? Y[(int64_t)(t0 + t) * ldy + s] : R(0);
+    for (int q = 0; q < U; ++q) {
+      const int64_t s = s0 + 32 * q;
+      const bool in = s < Ns;
+      av[q] = in ? xa[s] : R(0);
+      bv[q] = in ? xb[s] : R(0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      acc[k][0] += w3[k];
-      acc[k][1] = Num<R>::fma_(w3[k], w3[k], acc[k][1]);
-#pragma unroll
-      for (int t = 0; t < NT; ++t) acc[k][2 + t] = Num<R>::fma_(w3[k], y[t], acc[k][2 + t]);
+      for (int t = 0; t < NT; ++t) yv[q][t] = (in && t < T) ? Y[(int64_t)(t0 + t) * ldy + s] : R(0);
     }
-    if (sizeof(R) == 4 && ++blk == 16) {
-      blk = 0;
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < U; ++q) {
+      if (s0 + 32 * q >= Ns) break;
+      const R a = av[q], b = bv[q];
+      const R ac = a - mi, bc = b - mj, d = a - b;
+      R w3[3];
+      w3[0] = ac + bc;
+      w3[1] = ac - bc;
+      w3[2] = (d < R(0) ? -d : d) - cabs;
 #pragma unroll
-        for (int e = 0; e < 2 + NT; ++e) {
-          tot[k][e] += acc[k][e];
-          acc[k][e] = R(0);
-        }
+      for (int k = 0; k < 3; ++k) {
+        acc[k][0] += w3[k];
+        acc[k][1] = Num<R>::fma_(w3[k], w3[k], acc[k][1]);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) acc[k][2 + t] = Num<R>::fma_(w3[k], yv[q][t], acc[k][2 + t]);
+      }
+      if (sizeof(R) == 4 && ++blk == 16) {
+        blk = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int e = 0; e < 2 + NT; ++e) {
+            tot[k][e] += acc[k][e];
+            acc[k][e] = R(0);
+          }
+      }
     }
   }
 #pragma unroll
@@ -980,7 +994,9 @@ __device__ __forceinline__ void decode_gid(const ScreenArgs &A, uint64_t gid, in
 // then one pass per group of 16 targets.
 constexpr int kEsc = 128;
 
-template <int NV>
+// Block sums of v: in every thread, or (ALL = false) in thread 0 only (the
+// FP64 adds then leave the SM's FP64 units to the other blocks).
+template <int NV, bool ALL = true>
 __device__ __forceinline__ void block_sum64(double (&v)[NV], double *sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -989,11 +1005,13 @@ __device__ __forceinline__ void block_sum64(double (&v)[NV], double *sm) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) sm[w * NV + i] = v[i];
   __syncthreads();
+  if (ALL || threadIdx.x == 0) {
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double t = 0.0;
-    for (int ww = 0; ww < kEsc / 32; ++ww) t += sm[ww * NV + i];
-    v[i] = t;
+    for (int i = 0; i < NV; ++i) {
+      double t = 0.0;
+      for (int ww = 0; ww < kEsc / 32; ++ww) t += sm[ww * NV + i];
+      v[i] = t;
+    }
   }
   __syncthreads();
 }
@@ -1111,7 +1129,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
         st[5] += yv[k];
       }
     }
-    block_sum64<6>(st, sm);
+    block_sum64<6, false>(st, sm);
     if (threadIdx.x == 0) {  // (FP64 work is slow on this part: one thread decides)
       const double sxx = st[1] - st[0] * (st[0] / (double)N);
       int good = st[3] == 0.0 && isfinite(sxx);

@@ -186,6 +186,8 @@ struct Comp32 {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Sum of v over the block, in thread 0 (the other threads keep their
+// warp's sums).
 template <int NV>
 __device__ __forceinline__ void gram_block_sum(double (&v)[NV], double *sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -196,11 +198,13 @@ __device__ __forceinline__ void gram_block_sum(double (&v)[NV], double *sm) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) sm[w * NV + i] = v[i];
   __syncthreads();
+  if (threadIdx.x == 0) {  // the totals are used by thread 0 only (FP64 adds are slow on this part)
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q * NV + i];
-    v[i] = t;
+    for (int i = 0; i < NV; ++i) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q * NV + i];
+      v[i] = t;
+    }
   }
 }
 
