@@ -540,7 +540,7 @@ def main():
                     "traffic": profiled_traffic("k_pair_gram_medium.txt"),
                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
                                       "(profiles/k_pair_gram_medium.txt)",
-                    "peak_source": tc_src + " (of measured, burst: the kernel runs ~0.1 ms inside a short step)",
+                    "peak_source": tc_src + " (of measured, burst: the kernel runs ~0.06 ms at a time inside a short step)",
                     "flops_per_launch": flops, "flops_per_pair_sample": GRAM_FLOPS_PER_PAIR_SAMPLE,
                     "pairs": pairs, "launch_ms": launch_ms, "share_of_step": mul_ms / tot_ms}
     else:

@@ -318,3 +318,28 @@ def test_residual_loop_on_device(env, wname, D, prec):
         fixed.append(bid)
         r = resid_h
     np.testing.assert_array_equal(resid, r)
+
+
+def test_timing_flags(env):
+    """DSE_FLAG_TIMING_MAIN times the product/quotient group alone (two
+    events per screen); DSE_FLAG_TIMING every group; neither changes the
+    result."""
+    torch, oracle, dse, W = env
+    w = W.medium(0)
+    sp, _ = spaces(env, w)
+    Yd = torch.from_numpy(w["Y"]).cuda()
+    base = sp.screen(Yd, w["k"])
+    ids0, sc0, _ = base.fetch(0)
+    main = sp.screen(Yd, w["k"], flags=dse.FLAG_TIMING_MAIN)
+    ids1, sc1, _ = main.fetch(0)
+    km = main.stats()["kernel_ms"]
+    assert km[1] > 0 and km[0] == 0 and km[2] == 0 and km[3] == 0
+    full = sp.screen(Yd, w["k"], flags=dse.FLAG_TIMING)
+    ids2, sc2, _ = full.fetch(0)
+    assert all(x > 0 for x in full.stats()["kernel_ms"])
+    for ids, sc in ((ids1, sc1), (ids2, sc2)):
+        np.testing.assert_array_equal(ids, ids0)
+        np.testing.assert_array_equal(sc, sc0)
+    out = sp.residual_loop(w["Y"][0], 2, w["k"], flags=dse.FLAG_TIMING_MAIN)
+    for st in out["stats"]:
+        assert st["kernel_ms"][1] > 0 and st["kernel_ms"][0] == 0
