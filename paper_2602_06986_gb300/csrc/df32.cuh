@@ -100,18 +100,18 @@ __device__ __forceinline__ F2 sqrt_(F2 x) {
   return fast_two_sum(s, c);
 }
 
-// Running sum of pair terms with renormalisation on every step (Neumaier's
-// compensated form carried in a pair).  The step is symmetric in its two
-// operands (each rounding adds a commutative pair), so a butterfly reduction
-// leaves the same bits in every lane.
+// Running sum of pair terms in Neumaier's compensated form: hi the rounded
+// sum, lo the exact two-sum errors plus the terms' low parts (no
+// renormalisation: the pair is read as (double)hi + (double)lo, and lo stays
+// within a few ulps of hi times the number of steps a thread takes).  The
+// step is symmetric in its two operands (each rounding adds a commutative
+// pair), so a butterfly reduction leaves the same bits in every lane.
 struct Acc {
   float hi = 0.0f, lo = 0.0f;
   __device__ __forceinline__ void add(float th, float tl) {
     const F2 s = two_sum(hi, th);
-    const float l = __fadd_rn(__fadd_rn(lo, tl), s.lo);
-    const F2 r = fast_two_sum(s.hi, l);
-    hi = r.hi;
-    lo = r.lo;
+    lo = __fadd_rn(__fadd_rn(lo, tl), s.lo);
+    hi = s.hi;
   }
   __device__ __forceinline__ void warp_reduce() {
     for (int o = 16; o > 0; o >>= 1) {
@@ -441,12 +441,15 @@ __device__ __forceinline__ void col_sums64(const FeatTable &F, int op, int64_t a
   __syncthreads();
 }
 
-// Relative error scale of a candidate's sums, (N/128 + 64) u with u = 2^-44
-// kappa for the pair pass and 2^-49 for FP64 (the scale of the FP64
-// re-score's bound); errors of the shifted sums are at most this times the
-// natural scale sqrt(Sxx) |x_m|.
+// Relative error scale of a candidate's sums: for the pair pass
+// (k (k/16 + 1) + 64) 2^-44 kappa with k = N/128 the steps of one thread
+// (the compensation term's own rounding grows as k^2 2^-48), for FP64
+// (k + 64) 2^-49 (the scale of the FP64 re-score's bound); errors of the
+// shifted sums are at most this times the natural scale sqrt(Sxx) |x_m|.
 __device__ __forceinline__ double col_err_scale(const ColSums &cs, int64_t N) {
-  return (double)(N / kColThreads + 64) * (cs.pair ? 5.684341886080802e-14 * cs.kappa : 1.7763568394002505e-15);
+  const double k = (double)(N / kColThreads + 1);
+  return cs.pair ? (k * (k / 16.0 + 1.0) + 64.0) * 5.684341886080802e-14 * cs.kappa
+                 : (k + 64.0) * 1.7763568394002505e-15;
 }
 
 // The column sums of one candidate (one block of kColThreads threads; the

@@ -184,6 +184,30 @@ __device__ __forceinline__ void block_sum_arr(double (&v)[NV], double *sm) {
   __syncthreads();
 }
 
+// The same over the entries `Live` marks (an entry known to be zero, such as
+// a Gram entry of an unused fixed column, costs no FP64 reduction).
+template <int NV, int THREADS, typename Live>
+__device__ __forceinline__ void block_sum_live(double (&v)[NV], double *sm, Live live) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (live(i)) v[i] = warp_sum64(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (live(i)) sm[w * NV + i] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (!live(i)) continue;
+    double t = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < THREADS / 32; ++ww) t += sm[ww * NV + i];
+    v[i] = t;
+  }
+  __syncthreads();
+}
+
 // Statistics of the fixed columns and the target, shared by every
 // candidate's fit (one block): means, centred copies, their centred Gram
 // matrix and products with the centred target, and the raw column norms
@@ -215,7 +239,7 @@ __global__ void __launch_bounds__(kPrep) k_refit_prep(const double *y, const dou
     for (int c = 0; c < nf; ++c) mv[c] += fixed_cols[(int64_t)c * N + s];
     mv[kMaxP] += y[s];
   }
-  block_sum_arr<kMaxP + 1, kPrep>(mv, sm);
+  block_sum_live<kMaxP + 1, kPrep>(mv, sm, [](int i) { return i < NF || i == kMaxP; });
   double m[kMaxP];
 #pragma unroll
   for (int c = 0; c < kMaxP; ++c) m[c] = mv[c] / (double)N;
@@ -242,7 +266,11 @@ __global__ void __launch_bounds__(kPrep) k_refit_prep(const double *y, const dou
       acc[kMaxP * kMaxP + c] = fma(xc[c], yc, acc[kMaxP * kMaxP + c]);
     }
   }
-  block_sum_arr<kMaxP * kMaxP + 3 * kMaxP, kPrep>(acc, sm);
+  // live entries: the Gram lower triangle, products with y, norms and sums
+  // of the nf used columns
+  block_sum_live<kMaxP * kMaxP + 3 * kMaxP, kPrep>(acc, sm, [](int i) {
+    return i < kMaxP * kMaxP ? (i / kMaxP < NF && i % kMaxP <= i / kMaxP) : ((i - kMaxP * kMaxP) % kMaxP < NF);
+  });
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int c = 0; c < kMaxP; ++c) pre[kPreMean + c] = m[c];
@@ -551,7 +579,7 @@ __global__ void __launch_bounds__(kWide) k_refit_wide(FeatTable F, RungGeom G, i
     s2[kMaxP] = fma(dv, dv, s2[kMaxP]);
     s2[kMaxP + 1] = fma(dv, ycc[s], s2[kMaxP + 1]);
   }
-  block_sum_arr<kMaxP + 2>(s2, sm);
+  block_sum_live<kMaxP + 2, kWide>(s2, sm, [](int i) { return i < NF || i >= kMaxP; });
   if (threadIdx.x == 0) {
     double Gm[kMaxP][kMaxP] = {}, g[kMaxP] = {}, nrm[kMaxP] = {};
 #pragma unroll
