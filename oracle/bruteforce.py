@@ -109,7 +109,7 @@ def enumerate_bruteforce(primary_units, ops, max_rung, unit_check_addsub=True, e
     pair_deny = pair_deny or set()
     op_deny = op_deny or {}
 
-    def judged(e):
+    def assessed(e):
         if e is not None and breaks_rules(e, pair_deny, op_deny):
             return RULE
         return e
@@ -121,12 +121,12 @@ def enumerate_bruteforce(primary_units, ops, max_rung, unit_check_addsub=True, e
         slots = []
         for f in newest:
             for op in unary:
-                slots.append(judged(_unary(op, f, explog_dimensionless)))
+                slots.append(assessed(_unary(op, f, explog_dimensionless)))
         for i_rel, a in enumerate(newest):
             i = begin + i_rel
             for j in range(i):
                 for op in binary:
-                    slots.append(judged(_binary(op, a, stored[j], unit_check_addsub, r)))
+                    slots.append(assessed(_binary(op, a, stored[j], unit_check_addsub, r)))
         if r == max_rung:
             return stored, slots
         begin = len(stored)

@@ -341,7 +341,7 @@ __device__ __forceinline__ bool col_sums_pair(const FeatTable &F, int op, int64_
   }
   __syncthreads();
   // the combination, the checks and the outputs in warp 0 only (FP64 work
-  // is slow on this part); the verdict reaches every thread through sh.ok
+  // is slow on this part); the decision reaches every thread through sh.ok
   if (threadIdx.x < 32) {
     auto combine = [&](int i) {
       Acc t;
