@@ -654,11 +654,15 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
 
 // Screen a prepared result (screen_impl without launch) against new targets
 // already on the device (T rows of stride ld_y): thresholds start from zero.
-static dse_status screen_enqueue_target(dse_result *R, const double *Y, int64_t ld_y) {
+// clear: zero the error flag and the thresholds first (the loop's snapshot
+// kernel leaves them zeroed for the iterations after the first).
+static dse_status screen_enqueue_target(dse_result *R, const double *Y, int64_t ld_y, bool clear = true) {
   cudaStream_t st = R->stream;
   Keep *k = reinterpret_cast<Keep *>(R->keep);
-  DSE_CUDA(cudaMemsetAsync(R->err, 0, sizeof(int), st));
-  DSE_CUDA(cudaMemsetAsync(k->A.B.theta, 0, sizeof(float) * R->n_lists, st));
+  if (clear) {
+    DSE_CUDA(cudaMemsetAsync(R->err, 0, sizeof(int), st));
+    DSE_CUDA(cudaMemsetAsync(k->A.B.theta, 0, sizeof(float) * R->n_lists, st));
+  }
   launch_targets(Y, ld_y, R->T, R->space->N, R->ldy, R->y64, R->y32, R->ydf, R->ysum32, R->err, st);
   R->launches = 1;
   R->fetched = false;
@@ -817,8 +821,8 @@ constexpr int kSmall = ST_COUNT + 5;  // per iteration: counters, overflow, buff
 // overflow flag, buffered count, list length, largest bound, error flag as
 // 64-bit words) and its list of ids, in one launch.
 __global__ void k_loop_snapshot(const unsigned long long *stats, const unsigned *overflow, const unsigned *buf_count,
-                                const int64_t *out_n, const double *max_eps, const int *err, const uint64_t *out_id,
-                                int64_t k, unsigned long long *small, uint64_t *ids) {
+                                const int64_t *out_n, const double *max_eps, int *err, const uint64_t *out_id,
+                                int64_t k, unsigned long long *small, uint64_t *ids, float *theta, int n_lists) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < ST_COUNT) small[t] = stats[t];
   if (t == 0) {
@@ -827,6 +831,10 @@ __global__ void k_loop_snapshot(const unsigned long long *stats, const unsigned 
     small[ST_COUNT + 2] = (unsigned long long)*out_n;
     small[ST_COUNT + 3] = (unsigned long long)__double_as_longlong(*max_eps);
     small[ST_COUNT + 4] = (unsigned long long)(unsigned)*err;
+    // the next iteration's screen starts from a clear error flag and zero
+    // thresholds (what its target step would otherwise reset)
+    *err = 0;
+    for (int l = 0; l < n_lists; ++l) theta[l] = 0.0f;
   }
   for (int64_t i = t; i < k; i += (int64_t)gridDim.x * blockDim.x) ids[i] = out_id[i];
 }
@@ -889,7 +897,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
     note_launches(1);
     k_loop_snapshot<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (k + 255) / 256)), 256, 0, st>>>(
         R->stats, R->overflow, R->buf_count, R->out_n, R->max_eps, R->err, R->out_id, k,
-        small + (size_t)it * kSmall, ids + (size_t)it * k);
+        small + (size_t)it * kSmall, ids + (size_t)it * k, kp->A.B.theta, R->n_lists);
     return DSE_OK;
   };
   // before iteration it's screen: the fixed columns' fit, and the vectors
@@ -919,7 +927,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   auto step = [&](int it) -> dse_status {
     const double *src = it == 0 ? y : r + (size_t)(it - 1) * N;
     prepare(it);
-    DSE_TRY(screen_enqueue_target(R, src, N));
+    DSE_TRY(screen_enqueue_target(R, src, N, it == 0));
     DSE_TRY(snapshot(it));
     fit(it);
     DSE_CUDA(cudaGetLastError());
