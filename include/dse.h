@@ -208,7 +208,7 @@ typedef struct {
 /* Evaluate the product and quotient slots sample by sample.  Without it a
    single-target FP32 screen with 16 <= N <= 2048 takes their statistics from
    Gram contractions on the tensor cores (same results: the same bounds
-   contract, the same FP64 re-score of the list). */
+   contract, the same re-score of the list). */
 #define DSE_FLAG_DIRECT 4
 /* Time only the product/quotient kernel group (kernel_ms[1]; the other
    entries 0): two events per screen instead of five, for timing that kernel
@@ -231,7 +231,9 @@ typedef struct {
   int64_t evaluated;       /* candidates whose statistics were accumulated   */
   int64_t buffered;        /* candidate-target entries that passed threshold */
   int64_t escalated;       /* FP64 decisions of the realised test            */
-  int64_t rescored;        /* candidate-target pairs re-scored in FP64       */
+  int64_t rescored;        /* candidate-target pairs re-scored (FP32-pair
+                              sums with a bound, FP64 where they do not
+                              apply)                                         */
   int32_t reruns;          /* screens repeated after a buffer overflow       */
   int32_t precision_used;  /* DSE_PREC_* actually run                        */
   double max_err_bound;    /* largest bound among returned scores            */
@@ -314,7 +316,10 @@ void dse_batch_free(dse_batch *batch);
    the smallest RMSE (ties: lower id) and writes its id, RMSE, coefficients
    (intercept first, n_fixed + 2 values, host) and the residual y - fit
    (N FP64 values; host or device).  Ids already in `fixed` are skipped.
-   All arithmetic FP64 on the device.  Synchronises. */
+   Every fit is solved from its column sums (FP32-pair arithmetic, FP64
+   where that does not apply) with a bound on its RSS error; every fit that
+   could be the best within its bound is redone in FP64, so the pick, its
+   RMSE, coefficients and residual are an FP64 fit's.  Synchronises. */
 typedef struct {
   const double *y;        /* N values, host or device                       */
   int32_t y_on_device;

@@ -53,7 +53,7 @@ struct SelectArgs {
   uint8_t *r_need;          // [lists][cap]
   unsigned int *r_count;    // [lists]
   unsigned int *overflow;   // [lists]
-  // FP64 re-score jobs
+  // re-score jobs
   uint32_t *job;            // [lists * cap] packed (list << 24 | pos) is not enough: two arrays
   uint32_t *job_list;
   unsigned int *n_jobs;

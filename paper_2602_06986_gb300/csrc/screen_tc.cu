@@ -29,7 +29,7 @@
 // the next; longer sample ranges drain each block into FP32 registers.
 //
 // Error model of the contraction (used for the reported bound, and the
-// reason reported TC scores above the 1e-5 tolerance are re-scored in FP64):
+// reason reported TC scores above the 1e-5 tolerance are re-scored):
 // the BF16x3 split drops Al Bl and the splits' residuals (BF16 rounds to
 // 8 significant bits, so each two-term split leaves at most 2^-16 of the
 // value), at most 3.01 * 2^-16 of sum |w y|; each tensor-core accumulation

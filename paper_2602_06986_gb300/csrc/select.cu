@@ -6,7 +6,8 @@
 //   lo > H          the entry is certainly in the top k;
 //   hi < L          it is certainly out (and so is every unbuffered candidate,
 //                   whose hi is below the list's threshold <= L);
-//   otherwise       it is undecided and re-scored in FP64.
+//   otherwise       it is undecided and re-scored (FP32-pair sums, FP64
+//                   where they do not apply).
 // The retained set (certain + undecided) is ordered by score (FP64 where
 // re-scored), then id, and its first k entries are the result: order by score
 // descending, then global id ascending (the SIS top-k of SISSO screening).
@@ -238,10 +239,11 @@ __global__ void k_sel_classify(const SelectArgs S) {
   }
 }
 
-// 5) FP64 re-score: one block of kRes threads per job, one pass over the
-// samples with sums shifted by the candidate's first value (so Sxx = S2 - S1^2/N
-// keeps FP64 accuracy), targets of the list (all targets in aggregated mode,
-// at most 16 there).
+// 5) re-score.  Aggregated lists of several targets: FP64, one block of kRes
+// threads per job (k_rescore_warp: one warp, for short sample ranges), one
+// pass over the samples with sums shifted by the candidate's first value (so
+// Sxx = S2 - S1^2/N keeps FP64 accuracy), at most 16 targets.  One-target
+// lists: k_rescore1 below.
 constexpr int kRes = 128;
 
 // batch != nullptr: list l is problem l of a batched screen.  NT: 1 for
