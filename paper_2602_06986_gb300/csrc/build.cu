@@ -251,18 +251,22 @@ __global__ void k_take_rows(const int64_t *keep, int64_t nk, int64_t ld, const d
   }
 }
 
-// FP32 rows and per-feature helpers: one warp per feature (row conversion
-// and the FP64 sum of squares for the norm bound are coalesced over lanes).
-__global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const double *v64, float *v32,
-                            float *v32lo, const double *mean64, const double *rmean64, const double *min64, const double *max64,
-                            const double *minabs64, const double *maxabs64, const double *minabsnz64,
-                            const int32_t *units, double exp_arg_max, float4 *fa, float2 *fr, uint32_t *flags,
-                            uint64_t *ukey, float *fnorm) {
+// FP32 rows and per-feature helpers: one block of kPrepThreads per feature
+// (row conversion and the FP64 sum of squares for the norm bound over the
+// block's threads: the conversions run on the FP64 pipe, and four warps per
+// feature keep enough of them in flight), the feature's helpers by thread 0.
+constexpr int kPrepThreads = 128;
+
+__global__ void __launch_bounds__(kPrepThreads)
+    k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const double *v64, float *v32, float *v32lo,
+                const double *mean64, const double *rmean64, const double *min64, const double *max64,
+                const double *minabs64, const double *maxabs64, const double *minabsnz64, const int32_t *units,
+                double exp_arg_max, float4 *fa, float2 *fr, uint32_t *flags, uint64_t *ukey, float *fnorm) {
+  __shared__ double red[kPrepThreads / 32];
   const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
-  for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; f < n; f += warps) {
+  for (int64_t f = blockIdx.x; f < n; f += gridDim.x) {
     double s2 = 0.0;
-    for (int64_t s = lane; s < ld; s += 32) {
+    for (int64_t s = threadIdx.x; s < ld; s += kPrepThreads) {
       const double v = s < N ? v64[f * ld + s] : 0.0;
       const float h = __double2float_rn(v);
       v32[f * ld + s] = h;
@@ -270,40 +274,47 @@ __global__ void k_fp32_prep(int64_t n, int64_t N, int64_t ld, int D, const doubl
       s2 = __fma_rn(v, v, s2);
     }
     s2 = warp_sum64(s2);
-    if (lane) continue;
-    double M = maxabs64[f], m = minabs64[f];
-    fa[f] = make_float4(__double2float_rn(mean64[f]), __double2float_rn(rmean64[f]), __double2float_ru(M),
-                        __double2float_rd(M));
-    if (m > 0.0)
-      fr[f] = make_float2(__double2float_ru(__ddiv_ru(1.0, m)), __double2float_rd(__ddiv_rd(1.0, m)));
-    else
-      fr[f] = make_float2(0.0f, 0.0f);
-    uint32_t fl = 0;
-    if (m > 0.0) fl |= F_MINABS_POS;
-    if (min64[f] > 0.0) fl |= F_MIN_POS;
-    if (min64[f] >= 0.0) fl |= F_MIN_NONNEG;
-    if (max64[f] <= 80.0) fl |= F_EXP_DOMAIN;
-    if (max64[f] <= exp_arg_max) fl |= F_EXP_MAG;
-    const double lo = 8.673617379884035e-19, hi = 1.152921504606847e18;  // 2^-60, 2^60
-    double nz = minabsnz64[f];
-    if (M <= hi && (!(nz < INFINITY) || nz >= lo)) fl |= F_FP32_SAFE;
-    uint64_t k0 = 0, k1 = 0;
-    int dimless = 1;
-    for (int d = 0; d < kMaxDims; ++d) {
-      int32_t x = d < D ? units[f * kMaxDims + d] : 0;
-      if (x) dimless = 0;
-      uint64_t bits = (uint64_t)(uint16_t)(int16_t)x;
-      if (d < 4) k0 |= bits << (16 * d);
-      else k1 |= bits << (16 * (d - 4));
+    if (lane == 0) red[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s2 = 0.0;
+      for (int w = 0; w < kPrepThreads / 32; ++w) s2 += red[w];
+      double M = maxabs64[f], m = minabs64[f];
+      fa[f] = make_float4(__double2float_rn(mean64[f]), __double2float_rn(rmean64[f]), __double2float_ru(M),
+                          __double2float_rd(M));
+      if (m > 0.0)
+        fr[f] = make_float2(__double2float_ru(__ddiv_ru(1.0, m)), __double2float_rd(__ddiv_rd(1.0, m)));
+      else
+        fr[f] = make_float2(0.0f, 0.0f);
+      uint32_t fl = 0;
+      if (m > 0.0) fl |= F_MINABS_POS;
+      if (min64[f] > 0.0) fl |= F_MIN_POS;
+      if (min64[f] >= 0.0) fl |= F_MIN_NONNEG;
+      if (max64[f] <= 80.0) fl |= F_EXP_DOMAIN;
+      if (max64[f] <= exp_arg_max) fl |= F_EXP_MAG;
+      const double lo = 8.673617379884035e-19, hi = 1.152921504606847e18;  // 2^-60, 2^60
+      double nz = minabsnz64[f];
+      if (M <= hi && (!(nz < INFINITY) || nz >= lo)) fl |= F_FP32_SAFE;
+      uint64_t k0 = 0, k1 = 0;
+      int dimless = 1;
+      for (int d = 0; d < kMaxDims; ++d) {
+        int32_t x = d < D ? units[f * kMaxDims + d] : 0;
+        if (x) dimless = 0;
+        uint64_t bits = (uint64_t)(uint16_t)(int16_t)x;
+        if (d < 4) k0 |= bits << (16 * d);
+        else k1 |= bits << (16 * (d - 4));
+      }
+      if (dimless) fl |= F_DIMLESS;
+      flags[f] = fl;
+      ukey[2 * f] = k0;
+      ukey[2 * f + 1] = k1;
+      // sum of non-negative terms: each thread's running sum of about N/128
+      // FMAs, a 5-level tree, then 4 partials: relative error below
+      // (N/128 + 10) u, inside the margin taken
+      const double margin = 1.0 + ((double)(N / 32) + 8.0) * 2.3e-16;
+      fnorm[f] = __double2float_ru(__dsqrt_ru(__dmul_ru(s2, margin)));
     }
-    if (dimless) fl |= F_DIMLESS;
-    flags[f] = fl;
-    ukey[2 * f] = k0;
-    ukey[2 * f + 1] = k1;
-    // sum of non-negative terms: each lane's running sum of about N/32 FMAs
-    // then a 5-level tree, relative error below (N/32 + 8) u
-    const double margin = 1.0 + ((double)(N / 32) + 8.0) * 2.3e-16;
-    fnorm[f] = __double2float_ru(__dsqrt_ru(__dmul_ru(s2, margin)));
+    __syncthreads();  // red is reused by the next feature
   }
 }
 
@@ -755,7 +766,7 @@ static dse_status build_impl(const dse_space_desc *d, dse_space *S) {
   DSE_TRY(dalloc(&S->fnorm, n, "helpers"));
   DSE_TRY(dalloc(&S->flags, n, "flags"));
   DSE_TRY(dalloc(&S->ukey, 2 * n, "unit keys"));
-  k_fp32_prep<<<grid_for(n * 32, 256), 256, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, S->v32lo, T.mean64, T.rmean64, T.min64,
+  k_fp32_prep<<<(unsigned)std::min<int64_t>(std::max<int64_t>(n, 1), 65535), kPrepThreads, 0, st>>>(n, N, ld, S->D, T.v64, S->v32, S->v32lo, T.mean64, T.rmean64, T.min64,
                                                      T.max64, T.minabs64, T.maxabs64, T.minabsnz64, T.units,
                                                      S->exp_arg_max, S->fa, S->fr, S->flags, S->ukey, S->fnorm);
   dfree(T.minabsnz64);
