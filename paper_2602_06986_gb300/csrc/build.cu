@@ -73,8 +73,10 @@ __global__ void __launch_bounds__(kSumThreads) k_summaries(double *v64, int64_t 
                                                            double *max64, double *minabs64, double *maxabs64,
                                                            double *minabsnz64, double fmin_std_rel, uint8_t *ok,
                                                            const unsigned long long *n_dev) {
-  __shared__ long long smi[kSumThreads / 32];
   __shared__ double smd[kSumThreads / 32];
+  // the partials of the merged reductions: per warp {sum, min|x|} after the
+  // first pass, then {min, max, max|x|, min nonzero |x|, finite, sxx, s2, rs}
+  __shared__ unsigned long long sa[kSumThreads / 32][2], sb[kSumThreads / 32][8];
   const int64_t f = f0 + blockIdx.x;
   if (f >= f1 || (n_dev && (unsigned long long)(f - f0) >= *n_dev)) return;
   const double *x = v64 + f * ld;
@@ -95,21 +97,26 @@ __global__ void __launch_bounds__(kSumThreads) k_summaries(double *v64, int64_t 
     if (a != 0ull) anz = a < anz ? a : anz;
     sum = __dadd_rn(sum, v);
   }
-  auto mn_ll = [](long long p, long long q) { return p < q ? p : q; };
-  auto mx_ll = [](long long p, long long q) { return p > q ? p : q; };
-  kmn = block_reduce_sum(kmn, smi, mn_ll);
-  kmx = block_reduce_sum(kmx, smi, mx_ll);
-  amn = (unsigned long long)block_reduce_sum((long long)amn, smi,
-                                             [](long long p, long long q) {
-                                               return (unsigned long long)p < (unsigned long long)q ? p : q;
-                                             });
-  amx = (unsigned long long)block_reduce_sum((long long)amx, smi, mx_ll);
-  anz = (unsigned long long)block_reduce_sum((long long)anz, smi,
-                                             [](long long p, long long q) {
-                                               return (unsigned long long)p < (unsigned long long)q ? p : q;
-                                             });
-  fin = __syncthreads_and(fin);
-  sum = block_reduce_sum(sum, smd, [](double p, double q) { return p + q; });
+  // merged reduction 1 (every thread needs the sum and min|x|): one barrier
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = kSumThreads / 32;
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const unsigned long long q = __shfl_xor_sync(0xffffffffu, amn, o);
+    amn = q < amn ? q : amn;
+  }
+  if (lane == 0) {
+    sa[wid][0] = (unsigned long long)__double_as_longlong(sum);
+    sa[wid][1] = amn;
+  }
+  __syncthreads();
+  sum = 0.0;
+  amn = ~0ull;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    sum += __longlong_as_double((long long)sa[w][0]);
+    amn = sa[w][1] < amn ? sa[w][1] : amn;
+  }
   const double mean = sum / (double)N;
   const double mna = __longlong_as_double((long long)amn);
   double sxx = 0.0, s2 = 0.0;
@@ -121,9 +128,47 @@ __global__ void __launch_bounds__(kSumThreads) k_summaries(double *v64, int64_t 
     s2 = __fma_rn(v, v, s2);
     if (mna > 0.0) rs += __frcp_rn(__double2float_rn(v));
   }
-  sxx = block_reduce_sum(sxx, smd, [](double p, double q) { return p + q; });
-  s2 = block_reduce_sum(s2, smd, [](double p, double q) { return p + q; });
-  rs = block_reduce_sum(rs, reinterpret_cast<float *>(smd), [](float p, float q) { return p + q; });
+  // merged reduction 2: the order statistics, the finite flag and the
+  // second-pass sums, one barrier (every thread gets them)
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long a = __shfl_xor_sync(0xffffffffu, kmn, o), b = __shfl_xor_sync(0xffffffffu, kmx, o);
+    kmn = a < kmn ? a : kmn;
+    kmx = b > kmx ? b : kmx;
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, amx, o), e = __shfl_xor_sync(0xffffffffu, anz, o);
+    amx = c > amx ? c : amx;
+    anz = e < anz ? e : anz;
+    sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+  }
+  fin = __all_sync(0xffffffffu, fin);
+  if (lane == 0) {
+    sb[wid][0] = (unsigned long long)kmn;
+    sb[wid][1] = (unsigned long long)kmx;
+    sb[wid][2] = amx;
+    sb[wid][3] = anz;
+    sb[wid][4] = (unsigned long long)fin;
+    sb[wid][5] = (unsigned long long)__double_as_longlong(sxx);
+    sb[wid][6] = (unsigned long long)__double_as_longlong(s2);
+    sb[wid][7] = (unsigned long long)__float_as_uint(rs);
+  }
+  __syncthreads();
+  sxx = 0.0;
+  s2 = 0.0;
+  rs = 0.f;
+  fin = 1;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const long long a = (long long)sb[w][0], b = (long long)sb[w][1];
+    kmn = a < kmn ? a : kmn;
+    kmx = b > kmx ? b : kmx;
+    amx = sb[w][2] > amx ? sb[w][2] : amx;
+    anz = sb[w][3] < anz ? sb[w][3] : anz;
+    fin &= (int)sb[w][4];
+    sxx += __longlong_as_double((long long)sb[w][5]);
+    s2 += __longlong_as_double((long long)sb[w][6]);
+    rs += __uint_as_float((unsigned)sb[w][7]);
+  }
   double rmean = 0.0;
   if (mna > 0.0) {
     rmean = (double)rs / (double)N;

@@ -90,3 +90,16 @@ def test_no_cpu_fallback(dse):
     with pytest.raises(dse.DseError) as e:
         dse.Space(X, None, 1 << 8, 2)
     assert e.value.status == dse.ECUDA
+
+
+def test_binding_constants_match_header(dse):
+    """Every DSE_* constant the binding mirrors has the header's value."""
+    import re
+
+    text = open(HEADER).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define DSE_(\w+) (\d+)", text)}
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"DSE_(\w+) = (\d+)", text)}
+    for name in ("FLAG_TIMING", "FLAG_DEDUP", "FLAG_DIRECT", "FLAG_TIMING_MAIN"):
+        assert getattr(dse, name) == defines[name], name
+    for name in ("PREC_FP32", "PREC_FP64"):
+        assert getattr(dse, name) == enums[name], name
