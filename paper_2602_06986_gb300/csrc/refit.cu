@@ -805,14 +805,22 @@ void refit_chain_fit(dse_space *S, const double *y, const uint64_t *fid, int nf,
 __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, int64_t *best, const double *beta,
                          double *report, const int64_t *n_dev, uint64_t *chosen) {
   if (n_dev && *n_dev < n) n = *n_dev;
-  __shared__ double bv[1024];
+  // comparisons on order-preserving integer keys of the RMSEs (the integer
+  // pipe instead of the slow FP64 one); a NaN ranks with +inf
+  const unsigned long long kinf = ord_key(INFINITY);
+  auto key = [&](double r) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(r);
+    const bool nan = (b & 0x7FF0000000000000ull) == 0x7FF0000000000000ull && (b & 0x000FFFFFFFFFFFFFull) != 0ull;
+    return nan ? kinf : ord_key(r);
+  };
+  __shared__ unsigned long long bv[1024];
   __shared__ uint64_t bid[1024];
   __shared__ int64_t bix[1024];
-  double v = INFINITY;
+  unsigned long long v = kinf;
   uint64_t id = ~0ull;
   int64_t ix = -1;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double r = rmse[i];
+    const unsigned long long r = key(rmse[i]);
     if (r < v || (r == v && cand[i] < id)) {
       v = r;
       id = cand[i];
@@ -825,7 +833,7 @@ __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, in
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
-      double r = bv[threadIdx.x + o];
+      const unsigned long long r = bv[threadIdx.x + o];
       uint64_t i2 = bid[threadIdx.x + o];
       if (r < bv[threadIdx.x] || (r == bv[threadIdx.x] && i2 < bid[threadIdx.x])) {
         bv[threadIdx.x] = r;
@@ -836,7 +844,7 @@ __global__ void k_argmin(const double *rmse, const uint64_t *cand, int64_t n, in
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const int64_t b = bv[0] < INFINITY ? bix[0] : -1;
+    const int64_t b = bv[0] < kinf ? bix[0] : -1;
     *best = b;
     if (chosen) *chosen = b >= 0 ? cand[b] : ~0ull;
     if (report) {
