@@ -84,18 +84,28 @@ __global__ void __launch_bounds__(kSumThreads) k_summaries(double *v64, int64_t 
   unsigned long long amn = ~0ull, amx = 0ull, anz = ~0ull;
   int fin = 1;
   double sum = 0.0;
-  for (int64_t s = threadIdx.x; s < N; s += kSumThreads) {
-    const double v = x[s];
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
-    fin &= a < 0x7FF0000000000000ull;
-    const long long k = ord_key(v);
-    kmn = k < kmn ? k : kmn;
-    kmx = k > kmx ? k : kmx;
-    amn = a < amn ? a : amn;
-    amx = a > amx ? a : amx;
-    if (a != 0ull) anz = a < anz ? a : anz;
-    sum = __dadd_rn(sum, v);
+  // four samples per thread per step, their loads issued together; each
+  // thread takes its samples in increasing order
+  constexpr int U = 4;
+  for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * kSumThreads) {
+    double xv[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) xv[q] = s0 + q * kSumThreads < N ? x[s0 + q * kSumThreads] : 0.0;
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (s0 + q * kSumThreads >= N) break;
+      const double v = xv[q];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+      const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+      fin &= a < 0x7FF0000000000000ull;
+      const long long k = ord_key(v);
+      kmn = k < kmn ? k : kmn;
+      kmx = k > kmx ? k : kmx;
+      amn = a < amn ? a : amn;
+      amx = a > amx ? a : amx;
+      if (a != 0ull) anz = a < anz ? a : anz;
+      sum = __dadd_rn(sum, v);
+    }
   }
   // merged reduction 1 (every thread needs the sum and min|x|): one barrier
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -121,12 +131,19 @@ __global__ void __launch_bounds__(kSumThreads) k_summaries(double *v64, int64_t 
   const double mna = __longlong_as_double((long long)amn);
   double sxx = 0.0, s2 = 0.0;
   float rs = 0.f;
-  for (int64_t s = threadIdx.x; s < N; s += kSumThreads) {
-    const double v = x[s];
-    const double d = __dsub_rn(v, mean);
-    sxx = __fma_rn(d, d, sxx);
-    s2 = __fma_rn(v, v, s2);
-    if (mna > 0.0) rs += __frcp_rn(__double2float_rn(v));
+  for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * kSumThreads) {
+    double xv[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) xv[q] = s0 + q * kSumThreads < N ? x[s0 + q * kSumThreads] : 0.0;
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (s0 + q * kSumThreads >= N) break;
+      const double v = xv[q];
+      const double d = __dsub_rn(v, mean);
+      sxx = __fma_rn(d, d, sxx);
+      s2 = __fma_rn(v, v, s2);
+      if (mna > 0.0) rs += __frcp_rn(__double2float_rn(v));
+    }
   }
   // merged reduction 2: the order statistics, the finite flag and the
   // second-pass sums, one barrier (every thread gets them)
@@ -210,7 +227,22 @@ __global__ void __launch_bounds__(kSumThreads) k_eval_rows(FeatTable F, RungGeom
   const double *xa = F.v64 + a * F.ld;
   const double *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
   double *out = rows + w * F.ld;
-  for (int64_t s = threadIdx.x; s < F.ld; s += kSumThreads) out[s] = s < F.N ? eval_op64(op, xa[s], xb[s]) : 0.0;
+  // four samples per thread per step, their loads issued together
+  constexpr int U = 4;
+  for (int64_t s0 = threadIdx.x; s0 < F.ld; s0 += U * kSumThreads) {
+    double va[U], vb[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int64_t s = s0 + q * kSumThreads;
+      va[q] = s < F.N ? xa[s] : 0.0;
+      vb[q] = s < F.N ? xb[s] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int64_t s = s0 + q * kSumThreads;
+      if (s < F.ld) out[s] = s < F.N ? eval_op64(op, va[q], vb[q]) : 0.0;
+    }
+  }
 }
 
 // Scratch summaries of one evaluated rung (per scratch row).
