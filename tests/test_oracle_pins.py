@@ -640,3 +640,144 @@ def test_dedup_near_equivalent_pair_uses_full_window(orc):
     keep = np.flatnonzero(~red)
     want = [int(ids[i]) for i in sorted(keep, key=lambda i: (-scores[i], int(ids[i])))[:3]]
     assert got == want and 2 not in got
+
+
+# ------------------------------------------------- values of every operator
+
+def _tree_values(e, X):
+    """Values of an expression tree of the brute-force enumerator, computed
+    with numpy's own routines straight from the primaries (no stored rows):
+    x**3 by numpy.power, 1/x by numpy.reciprocal, exp/log/sqrt by numpy."""
+    if not e.kids:
+        return X[e.leaf].copy()
+    k = [_tree_values(c, X) for c in e.kids]
+    op = e.op
+    if op == SQUARE:
+        return np.square(k[0])
+    if op == CUBE:
+        return np.power(k[0], 3)
+    if op == INV:
+        return np.reciprocal(k[0])
+    if op == SQRT:
+        return np.sqrt(k[0])
+    if op == EXP:
+        return np.exp(k[0])
+    if op == LOG:
+        return np.log(k[0])
+    a, b = k  # a is the higher-id operand
+    return {ADD: lambda: np.add(a, b), SUB: lambda: np.subtract(a, b), MUL: lambda: np.multiply(a, b),
+            DIV: lambda: np.divide(a, b), RDIV: lambda: np.divide(b, a),
+            ABSDIFF: lambda: np.abs(np.subtract(a, b))}[op]()
+
+
+def _expected_reason(e, X, fmax_max, explog_arg_max):
+    """Reason code of a unit-valid last-rung tree from numpy values of its
+    operands (domain, then magnitude, then finiteness; the degeneracy test is
+    off in these cases): the domain and magnitude readings restated per op."""
+    k = [_tree_values(c, X) for c in e.kids]
+    a = k[0]
+    b = k[1] if len(k) > 1 else None
+    Ma, ma = np.max(np.abs(a)), np.min(np.abs(a))
+    op = e.op
+    dom = {LOG: a.min() > 0, SQRT: a.min() >= 0, INV: ma > 0, EXP: a.max() <= 80.0,
+           DIV: b is not None and np.min(np.abs(b)) > 0, RDIV: ma > 0}.get(op, True)
+    if not dom:
+        return 3
+    if op == EXP:
+        mag = a.max() <= explog_arg_max
+    elif op == LOG:
+        mag = True
+    else:
+        Mb = np.max(np.abs(b)) if b is not None else 0.0
+        mb = np.min(np.abs(b)) if b is not None else 0.0
+        bound = {SQUARE: Ma * Ma, CUBE: (Ma * Ma) * Ma, INV: 1.0 / ma if ma > 0 else math.inf, SQRT: math.sqrt(Ma),
+                 ADD: Ma + Mb, SUB: Ma + Mb, ABSDIFF: Ma + Mb, MUL: Ma * Mb,
+                 DIV: Ma / mb if mb > 0 else math.inf, RDIV: Mb / ma if ma > 0 else math.inf}[op]
+        mag = bound <= fmax_max
+    if not mag:
+        return 4
+    return 0 if np.all(np.isfinite(_tree_values(e, X))) else 5
+
+
+ALL_OPS = (SQUARE, CUBE, INV, SQRT, EXP, LOG, ADD, SUB, MUL, DIV, RDIV, ABSDIFF)
+
+
+@pytest.mark.parametrize("seed,n0", [(21, 3), (22, 4)])
+def test_every_op_value_against_numpy_trees(orc, seed, n0):
+    """Values and reason codes of every rung-2 candidate under all twelve ops
+    against numpy evaluations of the brute-force enumerator's expression
+    trees.  Both operand orders occur (a/b and b/a, a-b of every pair in id
+    order), rung-1 features that cross zero (log x, a-b) feed the
+    domain-restricted ops of rung 2, and values of both signs meet |a-b|.
+    The tolerance covers one rounding per tree node plus the last-ulp
+    differences between numpy's and the C library's exp/log/pow."""
+    rng = np.random.default_rng(seed)
+    N = 9
+    X = rng.uniform(0.5, 2.0, size=(n0, N))
+    S = unpruned_space(orc, X, ALL_OPS, 2)
+    stored, last = enumerate_bruteforce(np.zeros((n0, 0), np.int32), ALL_OPS, 2, True, True)
+    # every stored (rung <= 1) feature is valid on this data, so the stored
+    # lists agree
+    assert [S.expr(i) for i in range(S.n_features)] == [e.text for e in stored]
+    for i, e in enumerate(stored):
+        v, why = S.candidate(i)
+        assert why == 0
+        np.testing.assert_allclose(v, _tree_values(e, X), rtol=1e-13, atol=0)
+    n_checked = {op: 0 for op in ALL_OPS}
+    for p, e in enumerate(last):
+        gid = S.n_features + p
+        assert S.expr(gid) == e.text
+        v, why = S.candidate(gid)
+        ref = _tree_values(e, X)
+        assert why == _expected_reason(e, X, 1e300, math.log(1e300)), (e.text, why)
+        if why:
+            continue
+        scale = np.abs(ref) + 1e-300
+        # a node's relative error can be amplified by a cancelling + - |a-b|
+        # above it; bound it by the magnitudes of the tree's operands
+        err = np.abs(v - ref)
+        assert np.all(err <= 1e-12 * np.maximum(scale, _operand_scale(e, X))), (e.text, np.max(err / scale))
+        n_checked[e.op] += 1
+    assert all(c > 0 for c in n_checked.values()), n_checked
+
+
+def _operand_scale(e, X):
+    """Largest |value| of any node of the tree, sample by sample."""
+    out = np.abs(_tree_values(e, X))
+    for c in e.kids:
+        out = np.maximum(out, _operand_scale(c, X))
+    return out
+
+
+def test_every_op_domain_and_magnitude_on_signed_data(orc):
+    """Rung 1 over primaries of both signs, near zero and large: every op's
+    domain and magnitude decision and every valid value against numpy.  The
+    primaries are chosen so that each of log, sqrt, x^-1, exp, a/b (divisor
+    b), b/a (divisor a) and the magnitude bounds of ^2, ^3, *, a/b, b/a and
+    + - |a-b| fails for some operand and passes for another."""
+    X = np.array([
+        [-1.5, -0.3, 0.4, 1.1, 2.0, 0.7],        # x0 signed
+        [0.6, 0.9, 1.3, 1.8, 2.4, 1.1],          # x1 positive
+        [0.0, 0.5, 0.9, 1.4, 1.2, 0.3],          # x2 has an exact zero
+        [85.0, 81.0, 90.0, 82.5, 88.0, 84.0],    # x3: exp beyond the domain limit, x3^2 > 5e3
+        [1e-4, 2e-3, 0.5, 0.8, 0.3, 0.6],        # x4: tiny values, 1/x4 large
+        [10.0, 12.0, 15.0, 11.0, 60.0, 14.0],    # x5: exp within the domain, above the magnitude limit
+    ])
+    fmax = 5e3
+    S = orc.Space(X, None, mask(*ALL_OPS), 1, fmax_max=fmax, fmin_std_rel=-1.0)
+    stored, last = enumerate_bruteforce(np.zeros((6, 0), np.int32), ALL_OPS, 1, True, True)
+    seen = set()
+    for p, e in enumerate(last):
+        gid = S.n_features + p
+        assert S.expr(gid) == e.text
+        v, why = S.candidate(gid)
+        exp_why = _expected_reason(e, X, fmax, math.log(fmax))
+        assert why == exp_why, (e.text, why, exp_why)
+        seen.add((e.op, why))
+        if why == 0:
+            ref = _tree_values(e, X)
+            np.testing.assert_allclose(v, ref, rtol=4e-16, atol=0)
+    for op in (LOG, SQRT, INV, EXP, DIV, RDIV):
+        assert (op, 3) in seen and (op, 0) in seen, op
+    for op in (SQUARE, CUBE, MUL, DIV, RDIV, INV, EXP):
+        assert (op, 4) in seen, op
