@@ -401,19 +401,22 @@ dse_status dse_l0_search(dse_space *space, const dse_l0_desc *desc, int64_t *top
                          double *top_coefs, int32_t *n_found);
 
 /* dse_ls_refit without any device allocation.  The paper has no counterpart:
-   this is an engineering variant of the same refit step for callers that may
-   not allocate device memory while they run -- code inside a CUDA stream
-   capture (cudaMalloc is not allowed there), applications that hand all
-   device memory to their own pool or run under a hard memory budget.
-   Same arguments, results and synchronisation as dse_ls_refit.  Its scratch
-   is one fixed 8 MiB area per device, held by every device that loads the
-   library until the process exits; the limits are N <= 32768 samples and
-   n_cand <= 16384 candidates, and larger requests return DSE_EOVERFLOW with
-   a message.  The first call on a device looks the area's address up
-   (cudaGetSymbolAddress): make that first call before any stream capture.
-   All calls on a device share the one area, which keeps the last call's
-   contents: calls that overlap on the GPU (other streams or threads) race,
-   so the caller must serialise them. */
+   this is an engineering variant of the same refit step for callers that
+   cannot allocate device memory while they run -- applications that hand all
+   device memory to their own pool allocator, run under a hard memory budget,
+   or have reserved the whole device for other work.  Same arguments and
+   results as dse_ls_refit; like it, the call waits for its stream and copies
+   the winner to host memory, so it must not be issued on a stream that is
+   being captured into a CUDA graph.  Its scratch is one fixed 8 MiB area per
+   device, held by every device that loads the library until the process
+   exits; the limits are N <= 32768 samples and n_cand <= 16384 candidates,
+   and larger requests return DSE_EOVERFLOW with a message (the area is left
+   as it was and later calls are unaffected).  The first call on a device
+   looks the area's address up (cudaGetSymbolAddress) and keeps it; the
+   library must not be used across a cudaDeviceReset.  All calls on a device
+   share the one area, which keeps the last call's contents: calls that
+   overlap on the GPU (other streams or threads) race, so the caller must
+   serialise them. */
 dse_status dse_ls_refit_noalloc(dse_space *space, const dse_refit_desc *desc, uint64_t *best_id,
                                 double *best_rmse, double *coefs, double *residual);
 

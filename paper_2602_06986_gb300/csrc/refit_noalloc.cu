@@ -2,12 +2,14 @@
 // dse_ls_refit with every scratch buffer carved from one fixed, file-scope
 // device array instead of cudaMalloc.
 //
-// It serves callers that must not allocate device memory while they run:
-// code between cudaStreamBeginCapture and EndCapture (an allocation there is
-// illegal in the capturing stream), applications whose device memory is
-// owned by their own pool or accounted against a hard budget, and paths that
-// run after the caller has reserved the whole device.  The price is a fixed
-// ceiling on the problem size and one shared scratch area per device.
+// It serves callers that cannot allocate device memory while they run:
+// applications whose device memory is owned by their own pool allocator or
+// accounted against a hard budget, and processes that have reserved the whole
+// device for other work before the refit runs.  The price is a fixed ceiling
+// on the problem size and one shared scratch area per device.  The call still
+// waits for its stream and reads the winner back to host memory, so it is an
+// ordinary synchronous call: it must not be issued on a stream that is being
+// captured into a CUDA graph.
 #include <string.h>
 
 #include <mutex>
@@ -45,7 +47,10 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does it).
+// device (the first call on a device does it) and kept for the life of the
+// process.  A cudaDeviceReset destroys the context the address belongs to:
+// after one, this cache is stale, so the library must not be used across a
+// device reset.
 dse_status scratch_address(void **out) {
   int dev = 0;
   DSE_CUDA(cudaGetDevice(&dev));
@@ -126,8 +131,11 @@ dse_status refit_noalloc_impl(dse_space *S, const dse_refit_desc *d, uint64_t *b
   if (e) return cuda_status(e, "no-alloc refit upload");
   refit_chain_prep(S, y, fid, nf, base + o_chain, nc, st);
   refit_chain_fit(S, y, fid, nf, cand, nc, nullptr, base + o_chain, false, res, rep, nullptr, st);
+  // the winner's report and the residual are queued on the caller's stream
+  // behind the fit; one wait for both
   double h[kCoef + 3];
   e = cudaMemcpyAsync(h, rep, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (!e && residual) e = cudaMemcpyAsync(residual, res, 8 * N, cudaMemcpyDefault, st);
   if (!e) e = cudaStreamSynchronize(st);
   if (e) return cuda_status(e, "no-alloc refit");
   long long hb, hid;
@@ -139,10 +147,6 @@ dse_status refit_noalloc_impl(dse_space *S, const dse_refit_desc *d, uint64_t *b
   }
   *best_id = (uint64_t)hid;
   *best_rmse = h[2];
-  if (residual) {
-    e = cudaMemcpy(residual, res, 8 * N, cudaMemcpyDefault);
-    if (e) return cuda_status(e, "no-alloc refit fetch");
-  }
   if (coefs)
     for (int c = 0; c < nf + 2; ++c) coefs[c] = h[3 + c];
   return DSE_OK;

@@ -125,7 +125,10 @@ __device__ __forceinline__ unsigned score_and_push(const ScreenArgs &A, bool wan
       if (t < A.T) {
         R s, e;
         cand_score<R>(ci, S1, Sy[t], invN, ysum[t], gamma, u, &s, &e);
-        R lo = s - e > R(0) ? s - e : R(0), hi = s + e < R(1) ? s + e : R(1);
+        // edges rounded outwards (see iv_lo / iv_hi)
+        R lo = Num<R>::sub_rd(s, e), hi = Num<R>::add_ru(s, e);
+        lo = lo > R(0) ? lo : R(0);
+        hi = hi < R(1) ? hi : R(1);
         a += s * s;
         alo += lo * lo;
         ahi += hi * hi;
@@ -134,7 +137,9 @@ __device__ __forceinline__ unsigned score_and_push(const ScreenArgs &A, bool wan
     R invT = R(1) / R(A.T);
     R s = Num<R>::sqrt_(a * invT);
     R lo = Num<R>::sqrt_(alo * invT), hi = Num<R>::sqrt_(ahi * invT);
-    R e = (s - lo > hi - s ? s - lo : hi - s) * (R(1) + R(8) * u);
+    // the sums of T squares and the square roots carry relative errors of
+    // at most (T + 2) u of hi, which the last term covers
+    R e = (s - lo > hi - s ? s - lo : hi - s) * (R(1) + R(8) * u) + R(A.T + 8) * u * hi;
     float sf = (float)s;
     float ef = (float)e + fabsf((float)(s - (R)sf)) + 1e-30f;
     ef = ef * (1.0f + 2.4e-7f);

@@ -39,6 +39,8 @@ template <>
 struct Num<float> {
   __device__ static float sqrt_(float x) { return sqrtf(x); }
   __device__ static float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+  __device__ static float sub_rd(float a, float b) { return __fsub_rd(a, b); }
+  __device__ static float add_ru(float a, float b) { return __fadd_ru(a, b); }
   // 2^-90: a shifted sum of squares below N times this is within 2^36 of
   // the underflow threshold, where products that flushed (absolute error up
   // to 2^-126 each) are no longer negligible against the relative model
@@ -48,6 +50,8 @@ template <>
 struct Num<double> {
   __device__ static double sqrt_(double x) { return sqrt(x); }
   __device__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+  __device__ static double sub_rd(double a, double b) { return __dsub_rd(a, b); }
+  __device__ static double add_ru(double a, double b) { return __dadd_ru(a, b); }
   __device__ static double tiny() { return 1.1754943508222875e-271; }  // 2^-900
 };
 
@@ -313,21 +317,28 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
   return v;
 }
 
+// Edges of a buffered entry's interval [s - eps, s + eps], rounded outwards
+// (toward -inf / +inf) so that the FP32 edges still enclose the exact
+// interval when eps is within a few ulp of s.  The histograms, the push test
+// and the selection all take the edges from these two functions.
+__device__ __forceinline__ float iv_lo(float s, float eps) { return __fsub_rd(s, eps); }
+__device__ __forceinline__ float iv_hi(float s, float eps) { return __fadd_ru(s, eps); }
+
 // Histogram counts of a buffered entry's lower and upper bounds.
 __device__ __forceinline__ void count_bounds(const CandBufs &B, int l, float s, float eps) {
-  const int bl = score_bin(s - eps), bh = score_bin(s + eps);
+  const int bl = score_bin(iv_lo(s, eps)), bh = score_bin(iv_hi(s, eps));
   atomicAdd(&B.hist[(size_t)l * kNumBins + bl], 1u);
   atomicAdd(&B.hist_c[(size_t)l * kCoarse + bl / kFine], 1u);
   atomicAdd(&B.hist_hi[(size_t)l * kNumBins + bh], 1u);
 }
 
-// Push (id, s, eps) into list `l` if s + eps reaches its threshold; warp-
+// Push (id, s, eps) into list `l` if its upper edge reaches the threshold; warp-
 // cooperative: every lane of the warp must call it (want = 0 to abstain).
 // Returns whether this lane pushed.
 __device__ __forceinline__ bool push_warp(const CandBufs &B, int l, bool want, uint64_t id, float s, float eps) {
   const unsigned lane = threadIdx.x & 31;
   float th = ld_relaxed(&B.theta[l]);
-  bool p = want && (s + eps >= th);
+  bool p = want && (iv_hi(s, eps) >= th);
   unsigned m = __ballot_sync(0xffffffffu, p);
   if (!m) return false;
   unsigned base = 0;
@@ -364,7 +375,7 @@ __device__ __forceinline__ void count_bounds_warp(const CandBufs &B, int l, bool
   const unsigned act = __ballot_sync(0xffffffffu, active);
   if (!active) return;
   const int lane = threadIdx.x & 31;
-  const int bl = score_bin(s - eps), bh = score_bin(s + eps), bc = bl / kFine;
+  const int bl = score_bin(iv_lo(s, eps)), bh = score_bin(iv_hi(s, eps)), bc = bl / kFine;
   const unsigned gl = __match_any_sync(act, bl), gc = __match_any_sync(act, bc), gh = __match_any_sync(act, bh);
   if (lane == __ffs(gl) - 1) atomicAdd(&B.hist[(size_t)l * kNumBins + bl], (unsigned)__popc(gl));
   if (lane == __ffs(gc) - 1) atomicAdd(&B.hist_c[(size_t)l * kCoarse + bc], (unsigned)__popc(gc));
@@ -406,7 +417,7 @@ __device__ __forceinline__ int stage_push(const CandBufs &B, int l, PushStage<CA
                                           bool want, uint64_t id, float s, float eps) {
   static_assert(CAP >= 32, "a stage holds at least one warp's pushes");
   const unsigned lane = threadIdx.x & 31;
-  const bool p = want && (s + eps >= th);
+  const bool p = want && (iv_hi(s, eps) >= th);
   const unsigned m = __ballot_sync(0xffffffffu, p);
   if (!m) return n;
   const int c = __popc(m);
@@ -427,7 +438,7 @@ __device__ __forceinline__ int stage_push(const CandBufs &B, int l, PushStage<CA
 // Single-lane push (no warp cooperation).
 __device__ __forceinline__ bool push_one(const CandBufs &B, int l, uint64_t id, float s, float eps) {
   float th = ld_relaxed(&B.theta[l]);
-  if (!(s + eps >= th)) return false;
+  if (!(iv_hi(s, eps) >= th)) return false;
   unsigned pos = atomicAdd(&B.count[l], 1u);
   if ((int64_t)pos < B.cap) {
     size_t e = (size_t)l * (size_t)B.cap + pos;

@@ -201,7 +201,7 @@ __device__ __forceinline__ uint64_t tc_targets16(const ScreenArgs &A, const TcCa
     const float v = sy[i][lane];
     float s, e;
     cand_score_num<float>(c.ci, c.S1, v, invN, ysum[t], gamma_gen, gamma_num, u, &s, &e);
-    if (s + e < theta[t]) continue;
+    if (iv_hi(s, e) < theta[t]) continue;
     if (push_one(A.B, A.t0 + t, c.gid, s, e * (1.0f + 2.4e-7f))) pushed |= 1ull << t;
   }
   return pushed;

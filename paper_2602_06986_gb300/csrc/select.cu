@@ -30,11 +30,11 @@
 namespace dse {
 
 __device__ __forceinline__ float lo_of(float s, float e) {
-  float lo = s - e;
+  const float lo = iv_lo(s, e);
   return lo > 0.f ? lo : 0.f;
 }
 __device__ __forceinline__ float hi_of(float s, float e) {
-  float hi = s + e;
+  const float hi = iv_hi(s, e);
   return hi > 0.f ? hi : 0.f;
 }
 
@@ -113,11 +113,11 @@ __global__ void k_sel_collect(const SelectArgs S) {
   const size_t base = (size_t)l * S.B.cap;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < st.n; i += (int64_t)gridDim.x * blockDim.x) {
     const float s = S.B.score[base + i], e = S.B.eps[base + i];
-    if (score_bin(s - e) == st.binL) {
+    if (score_bin(iv_lo(s, e)) == st.binL) {
       unsigned p = atomicAdd(&S.state[l].nL, 1u);
       S.colL[base + p] = lo_of(s, e);
     }
-    if (score_bin(s + e) == st.binH) {
+    if (score_bin(iv_hi(s, e)) == st.binH) {
       unsigned p = atomicAdd(&S.state[l].nH, 1u);
       S.colH[base + p] = hi_of(s, e);
     }

@@ -426,10 +426,12 @@ class Space:
 
     def ls_refit_noalloc(self, y, fixed, cand, residual=None, stream=None):
         """Same as ls_refit through dse_ls_refit_noalloc, which allocates no
-        device memory: for callers that may not allocate while they run (stream
-        capture, an external memory pool or budget).  Fixed limits: N <= 32768
-        samples, at most 16384 candidates; one shared scratch area per device,
-        so overlapping calls must be serialised by the caller."""
+        device memory: for callers that cannot allocate while they run (an
+        external memory pool or a hard budget owns the device).  It waits for
+        the stream like ls_refit, so it is not for a capturing stream.  Fixed
+        limits: N <= 32768 samples, at most 16384 candidates; one shared
+        scratch area per device, so overlapping calls must be serialised by
+        the caller."""
         if isinstance(y, np.ndarray):
             y = np.ascontiguousarray(y, dtype=np.float64)
         fixed = np.ascontiguousarray(fixed, dtype=np.uint64)

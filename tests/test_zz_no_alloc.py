@@ -1,11 +1,12 @@
 """dse_ls_refit_noalloc against dse_ls_refit, through the C ABI.
 
-The no-alloc refit exists for callers that may not allocate device memory
-while they run: code inside a CUDA stream capture, where cudaMalloc is not
-allowed, and applications whose device memory belongs to their own pool or a
-hard budget.  It must give the same pick, RMSE, coefficients and residual as
-the allocating entry point, on consecutive calls that share its fixed scratch
-area, and refuse requests beyond its stated limits.
+The no-alloc refit exists for callers that cannot allocate device memory
+while they run: applications whose device memory belongs to their own pool
+allocator or a hard budget, or that have reserved the whole device.  It must
+give the same pick, RMSE, coefficients and residual as the allocating entry
+point, on consecutive calls that share its fixed scratch area, for every
+number of fixed descriptor columns, and refuse requests beyond its stated
+limits without disturbing the calls that follow.
 
 Collected last (file name) so that a failure here comes after every other
 test has run; it also passes alone in a fresh process.
@@ -67,3 +68,35 @@ def test_noalloc_refit_rejects_oversized(setup):
         sp.ls_refit_noalloc(y, np.zeros(0, np.uint64), too_many)
     assert e.value.status == dse.EOVERFLOW
     assert "16384" in str(e.value)
+
+
+def test_noalloc_refit_two_and_three_fixed_columns(setup):
+    """The widest report and column layouts of the fixed area (n_fixed = 2
+    and 3), each called twice in a row."""
+    torch, dse, sp, y, ids = setup
+    fixed = []
+    for _ in range(4):
+        f = np.array(fixed, np.uint64)
+        ref = sp.ls_refit(y, f, ids)
+        if len(fixed) >= 2:
+            for _ in range(2):
+                _same(sp.ls_refit_noalloc(y, f, ids), ref)
+        fixed.append(ref[0])
+
+
+def test_noalloc_refit_rejects_long_samples_then_recovers(setup):
+    """A space of more samples than the area's limit is refused with
+    DSE_EOVERFLOW, and the next valid call still matches dse_ls_refit."""
+    torch, dse, sp, y, ids = setup
+    rng = np.random.default_rng(3)
+    N = 40000
+    X = rng.uniform(0.5, 2.0, size=(3, N))
+    big = dse.Space(torch.from_numpy(X).cuda(), None, (1 << 8) | (1 << 6), 1)
+    yb = rng.standard_normal(N)
+    with pytest.raises(dse.DseError) as e:
+        big.ls_refit_noalloc(yb, np.zeros(0, np.uint64), np.arange(3, dtype=np.uint64))
+    assert e.value.status == dse.EOVERFLOW
+    assert "32768" in str(e.value)
+    big.free()
+    fixed = np.zeros(0, np.uint64)
+    _same(sp.ls_refit_noalloc(y, fixed, ids), sp.ls_refit(y, fixed, ids))
