@@ -1,19 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark of the SIS screening hot path on GB300.
 
-One step = one pass of the whole path over one synthetic workload: build the
-feature space (rungs < k materialised on the device), then the residual loop
-D = 1..3 (one dse_residual_loop call, iterations chained on the device): SIS
-screen of rung 2 against the current residual (top-1000, exact top-k
-selection with FP64 re-score of the boundary band) and FP64 least-squares
-refits of the retained candidates.  Inputs are resident in HBM
-when the timed region starts; L2 is flushed (256 MiB write) between steps.
+Default workload (the largest single-GPU configuration; the one on which the
+metric's comparison with the plain FP64 GPU path is defined): N = 20000
+samples, 40 primaries of mixed distributions (uniform, lognormal, signed
+normal), units over 5 base dimensions, the full operator library, rung 2
+(19.2 M candidate ids), 16 residual targets, top-10000 per target.  One step
+= one pass of the whole hot path over it: build the feature space (rung 1
+materialised on the device, masks, summaries), then the SIS screen of every
+candidate against the 16 targets (unit check, a-priori and realised masks,
+FP32 evaluation, the BF16x3 tensor-core contraction of the numerators,
+streaming top-k, exact selection with the FP32-pair / FP64 re-score of the
+boundary).  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MiB write) between steps.
 
-Metric: SIS-screened candidate features per second (valid candidates scored),
-with evals/s (candidate x sample) and the plain FP64 GPU path on the same
-workload beside it.  Prints one JSON line (rank 0).
+Metric: SIS-screened candidate features per second (valid candidates, each
+scored on all N samples against every target), with evals/s (candidate x
+sample) and the plain FP64 GPU path on the same workload beside it.  Prints
+one JSON line (rank 0).  With N > 1 ranks (torchrun) the candidate ids are
+split into one contiguous block per rank and the per-target top-k lists are
+merged after one NCCL all-gather (strong scaling: the total work is fixed).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dse|reference]
+    python bench.py --workload medium      # N=1000 residual loop D=1..3 (separate line)
     python bench.py --workload batched     # 256-problem batched screen (separate line)
 """
 from __future__ import annotations
@@ -401,6 +410,294 @@ def bench_l0(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- headline
+
+# FP32 lane operations per (valid candidate, sample) that the tensor-core
+# multi-target kernel issues on the CUDA cores: the evaluation, sum w and
+# sum w^2, and the BF16 hi/lo split (conversion, difference, conversion);
+# the T numerators go to the tensor pipe (3 BF16 products of 2 flops each per
+# target).
+TC_ALU_OPS_PER_EVAL = 6
+
+
+def large_space(dse, w, X, stream=None):
+    return dse.Space(X, w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                     explog_dimensionless=w["explog_dimensionless"], stream=stream)
+
+
+def large_step_device(dse, w, Xd, Yd, k, precision, id_range, stream, flags, group=None):
+    """One step with device-resident inputs: space build, then the screen of
+    this rank's id block against every target.  With a process group the
+    per-target lists of all ranks are merged after one all-gather.  Returns
+    the screen's statistics."""
+    from paper_2602_06986_gb300 import shard
+
+    sp = large_space(dse, w, Xd, stream)
+    b, e = id_range(sp.n_total)
+    if group is not None:
+        lists, st = shard.sharded_screen(sp, Yd, k, group=group, precision=precision, stream=stream, flags=flags)
+        st = st or {"evaluated": 0, "kernel_ms": [0.0] * 4, "valid_by_group": [0, 0, 0], "kernel_launches": 0}
+    else:
+        r = sp.screen(Yd, k, precision=precision, id_begin=b, id_end=e, stream=stream, flags=flags)
+        st = r.stats()
+        r.free()
+    sp.free()
+    return st
+
+
+def large_step_host(dse, w, k):
+    """One step through the public API with host buffers: primaries, units
+    and the 16 targets go to the device inside the step, every list (id,
+    score, bound) comes back to host memory."""
+    X, Y = w["X"], np.ascontiguousarray(w["Y"])
+    sp = large_space(dse, w, X)
+    r = sp.screen(Y, k, precision=dse.PREC_AUTO)
+    d2h = 0
+    for t in range(r.n_lists):
+        ids, sc, eb = r.fetch(t)
+        d2h += ids.nbytes + sc.nbytes + eb.nbytes
+    st = r.stats()
+    r.free()
+    sp.free()
+    h2d = X.nbytes + w["units"].nbytes + Y.nbytes
+    return st, h2d, d2h
+
+
+def oracle_large_block(w, S, begin, n_ids):
+    """The oracle's screen of ids [begin, begin + n_ids) of the large
+    workload: (valid candidates, seconds)."""
+    t0 = time.perf_counter()
+    _, _, cnt = S.screen(w["Y"], w["k"], id_begin=begin, id_end=begin + n_ids)
+    return cnt["valid"], time.perf_counter() - t0
+
+
+def oracle_large_space(w):
+    import oracle
+
+    oracle.build()
+    return oracle.Space(w["X"], w["units"], w["op_mask"], w["max_rung"], unit_check_addsub=w["unit_check_addsub"],
+                        explog_dimensionless=w["explog_dimensionless"])
+
+
+def bench_large(args):
+    from paper_2602_06986_gb300 import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = W.large(0)
+    k = w["k"]
+    T, N = w["Y"].shape
+    config = {"workload": w["name"], "N": N, "n_primary": int(w["X"].shape[0]), "max_rung": w["max_rung"],
+              "targets": T, "k": k, "precision": "FP32 evaluation + BF16x3 tcgen05 numerators (AUTO)",
+              "l2": "flushed between steps (256 MiB write); stored FP32 rows 0.2 GB > L2",
+              "parallelism": ("one GPU" if world == 1 else
+                              f"id-range split over {world} ranks + NCCL all-gather of the top-k lists")}
+
+    if args.impl == "reference":
+        # the reference arm is the CPU FP64 oracle, timed on the host cores
+        # on bounded contiguous id blocks of the same workload
+        if rank != 0:
+            return
+        import oracle
+
+        S = oracle_large_space(w)
+        rng = np.random.Generator(np.random.PCG64(77))
+        n_ids = args.ref_ids
+        offs = rng.integers(0, S.total_candidates - n_ids, size=args.warmup + args.steps)
+        for i in range(args.warmup):
+            oracle_large_block(w, S, int(offs[i]), n_ids)
+        tot, cands = 0.0, 0
+        for i in range(args.steps):
+            c, dt = oracle_large_block(w, S, int(offs[args.warmup + i]), n_ids)
+            tot += dt
+            cands += c
+        v = cands / tot
+        sample = (f"{args.steps} contiguous blocks of {n_ids} candidate ids at seeded offsets, one per step, "
+                  f"screened against all {T} targets (the oracle's space build, 1% of the work, excluded)")
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "candidates/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "candidates/s", "cores": oracle.num_threads(),
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    group = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        group = dist.group.WORLD
+    from paper_2602_06986_gb300 import _build
+
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    _build.build()
+    from paper_2602_06986_gb300 import dse
+
+    stream = torch.cuda.current_stream().cuda_stream
+    Xd = torch.from_numpy(w["X"]).cuda()
+    Yd = torch.from_numpy(np.ascontiguousarray(w["Y"])).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    whole = lambda n: (0, 0)  # noqa: E731  (the whole space; sharding goes through the group)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        large_step_device(dse, w, Xd, Yd, k, dse.PREC_AUTO, whole, stream, dse.FLAG_TIMING_MAIN, group)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    L0 = dse.lib().dse_kernel_launches()
+    step_ms, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.cuda.nvtx.range_push("timed_step")
+        st = large_step_device(dse, w, Xd, Yd, k, dse.PREC_AUTO, whole, stream, dse.FLAG_TIMING_MAIN, group)
+        torch.cuda.nvtx.range_pop()
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    launches = dse.lib().dse_kernel_launches() - L0
+    barrier()
+    clk = clocks.stop()
+    tot_ms = sum(step_ms)
+    cands_local = sum(s["evaluated"] for s in stats)
+    if world > 1:
+        t = torch.tensor([tot_ms, float(cands_local)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        tot_ms, cands = float(tmax[0].item()), int(t[1].item())
+    else:
+        cands = cands_local
+    value = cands / (tot_ms * 1e-3)
+
+    # dominant kernel: the product/quotient group on the tensor cores
+    # (k_pair_tc, a*b, a/b, b/a), live CUDA events in the timed steps
+    mul_ms = sum(s["kernel_ms"][1] for s in stats)
+    mul_valid = sum(s["valid_by_group"][1] for s in stats)
+    mhz, clk_src = peaks()
+    alu_peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
+    ntp = 16 if T <= 16 else 32 if T <= 32 else 64
+    alu = TC_ALU_OPS_PER_EVAL * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
+    tc_peak, tc_src = measured_bf16("bf16_tflops_sustained")
+    tc_flops = 6.0 * ntp * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": f"k_pair_tc<KIND_MUL,{ntp}> (a*b, a/b, b/a; BF16x3 tcgen05 numerators)",
+                "achieved": alu, "peak": alu_peak, "unit": "T fp32-lane-ops/s",
+                "frac": alu / alu_peak if alu else None,
+                "traffic": profiled_traffic("k_pair_tc_large.txt"),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                                  "(profiles/k_pair_tc_large.txt)",
+                "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({clk_src})",
+                "ops_per_candidate_sample": TC_ALU_OPS_PER_EVAL, "valid_candidates_per_launch": mul_valid / len(stats),
+                "launch_ms": mul_ms / len(stats), "share_of_step": mul_ms / sum(step_ms),
+                "tensor": {"achieved": tc_flops, "peak": tc_peak, "unit": "TFLOP/s",
+                           "frac": tc_flops / tc_peak if tc_flops else None,
+                           "flops_per_candidate_sample": 6 * ntp, "peak_source": tc_src + " (of measured)"}}
+
+    # the kernel groups' device times from one more (untimed) step with an
+    # event at every group boundary
+    flush.zero_()
+    barrier()
+    st_all = large_step_device(dse, w, Xd, Yd, k, dse.PREC_AUTO, whole, stream, dse.FLAG_TIMING, group)
+    group_ms = st_all["kernel_ms"]
+
+    # the plain FP64 GPU path on the same workload (same step, FP64 kernels)
+    fp64_ms, fp64_c = [], 0
+    for _ in range(args.fp64_steps):
+        flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st64 = large_step_device(dse, w, Xd, Yd, k, dse.PREC_FP64, whole, stream, 0, group)
+        e1.record()
+        torch.cuda.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+        fp64_c += st64["evaluated"]
+    fp64_tot = sum(fp64_ms)
+    if world > 1:
+        t = torch.tensor([fp64_tot, float(fp64_c)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        fp64_tot, fp64_c = float(tmax[0].item()), int(t[1].item())
+    fp64 = None
+    if fp64_ms:
+        fp64_value = fp64_c / (fp64_tot * 1e-3)
+        fp64 = {"value": fp64_value, "unit": "candidates/s", "ms_per_step": fp64_tot / len(fp64_ms),
+                "steps": len(fp64_ms), "speedup_of_fp32_path": value / fp64_value}
+
+    # end to end through the public API with host buffers (rank 0's GPU; the
+    # whole workload on one device)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        e2e_ms, e2e_c = [], 0
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st_h, h2d, d2h = large_step_host(dse, w, k)
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_c += st_h["evaluated"]
+        e2e = {"value": e2e_c / (sum(e2e_ms) * 1e-3), "unit": "candidates/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": sum(e2e_ms) / len(e2e_ms),
+               "note": "host buffers through the C ABI on one GPU, copies inside the timed region"}
+    if world > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        S = oracle_large_space(w)
+        rng = np.random.Generator(np.random.PCG64(76))
+        n_ids = min(args.cpu_ids, S.total_candidates)
+        b0 = int(rng.integers(0, S.total_candidates - n_ids + 1))
+        c, dt = oracle_large_block(w, S, b0, n_ids)
+        cpu = {"value": c / dt, "unit": "candidates/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"ids [{b0}, {b0 + n_ids}) of the same workload ({n_ids} contiguous ids, {c} valid, all "
+                         f"{T} targets, top-{k}), {dt:.1f} s; rate extrapolated to the whole space"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "evals_per_s": value * N,
+        "fp64_plain": fp64,
+        "roofline": roofline,
+        "kernel_group_ms_per_step": {"stored_unary": group_ms[0], "pair_mul": group_ms[1], "pair_add": group_ms[2],
+                                     "select": group_ms[3], "source": "one untimed step with an event per group"},
+        "per_screen": {key: sum(s[key] for s in stats) / len(stats)
+                       for key in ("screened", "evaluated", "buffered", "escalated", "rescored", "reruns",
+                                   "kernel_launches")},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,15 +705,27 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dse", choices=["dse", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium",
-                    choices=["medium", "batched", "precision", "large", "tc_small", "l0"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "medium", "batched", "precision", "large_screen", "tc_small", "l0"])
+    ap.add_argument("--cpu-ids", type=int, default=1_000_000,
+                    help="contiguous candidate ids the oracle screens for the cpu_baseline of the large workload")
+    ap.add_argument("--ref-ids", type=int, default=100_000,
+                    help="candidate ids per step of the reference (oracle) arm on the large workload")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU path (0: skip)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     args = ap.parse_args()
+    if args.workload == "large":
+        return bench_large(args)
     if args.workload == "batched":
         return bench_batched(args)
-    if args.workload in ("precision", "large", "tc_small"):
-        return bench_multi_target(args, args.workload)
+    if args.workload in ("precision", "large_screen", "tc_small"):
+        return bench_multi_target(args, "large" if args.workload == "large_screen" else args.workload)
     if args.workload == "l0":
         return bench_l0(args)
+    return bench_medium(args)
+
+
+def bench_medium(args):
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

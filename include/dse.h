@@ -163,6 +163,16 @@ typedef struct {
 } dse_expr;
 
 dse_status dse_decode(const dse_space *space, uint64_t id, dse_expr *out);
+/* Unit vectors of n candidates ("Physics-Informed Constraints": the units
+   an expression carries follow from its op's exponent rule): for ids[i]
+   (host array), n_dims exponents as integers over the common denominator
+   2^max_rung into units[i * n_dims ...] (host; may be NULL when n_dims is
+   0) and unit_ok[i] = 1 when the op's unit rule holds, 0 when the candidate
+   is dimensionally invalid (its row is then 0).  Stored features are read
+   from the table, last-rung candidates computed by the screen's own device
+   rule.  DSE_ERANGE for an id outside the space.  Synchronises. */
+dse_status dse_candidate_units(dse_space *space, const uint64_t *ids, int64_t n, int64_t *units,
+                               int8_t *unit_ok);
 /* Canonical text: x<p>, sq(A), cb(A), inv(A), sqrt(A), exp(A), log(A),
    (A+B), (A-B), (A*B), (A/B), (B/A), |A-B| with A the higher-id operand. */
 dse_status dse_expr_string(const dse_space *space, uint64_t id, char *buf, int64_t len);
@@ -186,6 +196,13 @@ typedef struct {
   int32_t flags;         /* DSE_FLAG_* bits                                 */
   int32_t reserved0;
   double dedup_tau;      /* with DSE_FLAG_DEDUP: 0 < tau < 0.5 (0: 1e-10)   */
+  /* Optional DEVICE buffer of (id_end - id_begin) bytes, id_end as resolved
+     (0: the whole space), or NULL.  The screen writes, in id order, the
+     reason code (DSE_VALID or DSE_R_*) it assigned to each candidate of the
+     range: the per-candidate mask of "Physics-Informed Constraints" (units)
+     and of the domain, magnitude and realised tests, the same decisions the
+     reasons counts of dse_stats sum up.  Not a device pointer: DSE_EINVAL. */
+  int8_t *reasons;
 } dse_screen_desc;
 
 /* dse_screen_desc.flags: record CUDA events around each kernel group so that

@@ -104,6 +104,10 @@ def lib():
             L.orc_screen_dedup.argtypes = [vp, dp, C.c_int, i64, C.c_int, C.c_double, u64, u64, C.POINTER(u64),
                                            dp, C.POINTER(i64), C.POINTER(i64), dp]
             L.orc_screen_dedup.restype = C.c_int
+            L.orc_reasons.argtypes = [vp, u64, u64, C.POINTER(C.c_int8)]
+            L.orc_reasons.restype = C.c_int
+            L.orc_candidate_unit.argtypes = [vp, u64, C.POINTER(i64)]
+            L.orc_candidate_unit.restype = C.c_int
             _lib = L
     return _lib
 
@@ -205,6 +209,23 @@ class Space:
         if lib().orc_candidate(self._h, gid, _dptr(v), C.byref(why)):
             raise IndexError(gid)
         return (v if why.value == 0 else None), why.value
+
+    def reasons(self, id_begin: int = 0, id_end=None):
+        """Reason code (int8, 0 = valid) of every candidate id in [id_begin, id_end)."""
+        id_end = self.total_candidates if id_end is None else id_end
+        out = np.zeros(max(id_end - id_begin, 0), np.int8)
+        if lib().orc_reasons(self._h, id_begin, id_end, out.ctypes.data_as(C.POINTER(C.c_int8))):
+            raise IndexError((id_begin, id_end))
+        return out
+
+    def candidate_unit(self, gid: int):
+        """(unit exponents int64[n_dims] scaled by 2^max_rung, or None when
+        the op's unit rule fails)."""
+        u = np.zeros(max(self.n_dims, 1), np.int64)
+        rc = lib().orc_candidate_unit(self._h, gid, u.ctypes.data_as(C.POINTER(C.c_int64)))
+        if rc < 0:
+            raise IndexError(gid)
+        return u[: self.n_dims].copy() if rc == 1 else None
 
     def feature_info(self, f: int):
         cx = C.c_int32()

@@ -600,6 +600,43 @@ int orc_candidate(const orc_space *S, uint64_t id, double *v, int32_t *reason) {
   return 0;
 }
 
+/* Reason code of every candidate with global id in [id_begin, id_end), one
+   byte each (R8: the first failing test; stored features are valid by
+   construction).  The mask "Physics-Informed Constraints" describes, candidate
+   by candidate.  Returns 0, or -1 for a range outside the space. */
+int orc_reasons(const orc_space *S, uint64_t id_begin, uint64_t id_end, int8_t *why) {
+  const uint64_t total = orc_total_candidates(S);
+  if (id_end < id_begin || id_end > total) return -1;
+  const int r = S->P.max_rung;
+#pragma omp parallel
+  {
+    double *v = (double *)malloc((size_t)S->N * sizeof(double));
+#pragma omp for schedule(dynamic, 1024)
+    for (int64_t i = (int64_t)id_begin; i < (int64_t)id_end; ++i) {
+      if (i < S->nfeat) why[i - (int64_t)id_begin] = ORC_VALID;
+      else why[i - (int64_t)id_begin] = (int8_t)slot_reason(S, r, (uint64_t)(i - S->nfeat), v);
+    }
+    free(v);
+  }
+  return 0;
+}
+
+/* Unit vector of candidate id (R3: exponents as integers over the common
+   denominator 2^max_rung) into unit[n_dims].  Returns 1 when the op's unit
+   rule holds, 0 when it fails (unit left unspecified), -1 for an id outside
+   the space. */
+int orc_candidate_unit(const orc_space *S, uint64_t id, int64_t *unit) {
+  if (id < (uint64_t)S->nfeat) {
+    for (int k = 0; k < S->D; ++k) unit[k] = S->unit[id * S->D + k];
+    return 1;
+  }
+  const uint64_t p = id - (uint64_t)S->nfeat;
+  if (p >= rung_slots(S, S->P.max_rung)) return -1;
+  int op; int64_t a, b; int32_t cx;
+  if (decode_flat(S, S->P.max_rung, p, &op, &a, &b)) return -1;
+  return apriori(S, op, a, b, unit, &cx) == ORC_R_UNIT ? 0 : 1;
+}
+
 int orc_feature_info(const orc_space *S, int64_t f, int32_t *cplx, int64_t *unit, double *summ4) {
   if (f < 0 || f >= S->nfeat) return -1;
   *cplx = S->cplx[f];

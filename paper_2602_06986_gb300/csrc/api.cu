@@ -254,6 +254,8 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
   note_launches(1);
   k_screen_reset<<<std::max(1, std::min(sms, (int)((nl * kNumBins + 255) / 256))), 256, 0, st>>>(
       A.B.count, A.B.hist, A.B.hist_hi, A.B.hist_c, nl, A.esc_count, A.stats, S.n_jobs);
+  // per-candidate reasons: -1 until a kernel decides the candidate
+  if (A.why) DSE_CUDA(cudaMemsetAsync(A.why, 0xff, (size_t)(A.id_end - A.id_begin), st));
   // optional device timing of each kernel group
   const bool timing = (R->flags & (DSE_FLAG_TIMING | DSE_FLAG_TIMING_MAIN)) != 0;
   const bool main_only = !(R->flags & DSE_FLAG_TIMING);
@@ -330,6 +332,7 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
   E.t0 = 0;
   E.T = R->T;
   launch_escalate(E, sms, st);
+  launch_why_fixup(A, sms, st);
   DSE_TRY(launch_select(S, E, sms, st));
   DSE_TRY(mark(-1));
   DSE_CUDA(cudaGetLastError());
@@ -358,6 +361,10 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
     set_error("id range [%llu, %llu) outside [0, %llu)", (unsigned long long)id_begin,
               (unsigned long long)id_end, (unsigned long long)total);
     return DSE_ERANGE;
+  }
+  if (d->reasons && !is_device_pointer(d->reasons)) {
+    set_error("the reasons buffer must be device memory");
+    return DSE_EINVAL;
   }
   int prec = d->precision;
   ScreenPlan plan{};
@@ -575,6 +582,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   if (!e) e = cudaMemsetAsync(R->err, 0, sizeof(int), st);
   if (!e) e = cudaMemsetAsync(A.B.theta, 0, sizeof(float) * n_lists, st);
   if (e) return fail(cuda_status(e, "screen setup"));
+  A.why = d->reasons;
   if (launch) launch_targets(Ysrc, d->ld_y, (int)T, N, R->ldy, R->y64, R->y32, R->ydf, R->ysum32, R->err, st);
   R->launches = launch ? 1 : 0;
   R->flags = d->flags;

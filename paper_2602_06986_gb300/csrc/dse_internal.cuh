@@ -212,6 +212,7 @@ struct ScreenArgs {
   int32_t block_len;           // pair kernel blocking of the FP32 sums
   int32_t prob;
   uint32_t *esc_prob;          // escalation list: problem of each entry (batched only)
+  int8_t *why;                 // optional: reason code of each id of [id_begin, id_end) (device)
 };
 
 // Launch bookkeeping (process-wide count of the library's kernel launches).

@@ -267,7 +267,10 @@ __device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, ui
     }
   }
   if (reason != DSE_VALID) {
-    if (lane == 0) ls.r[reason]++;
+    if (lane == 0) {
+      ls.r[reason]++;
+      note_why(A, gid, reason);
+    }
     return;
   }
   if (sizeof(R) == 4 && !(A.F.flags[f] & F_FP32_SAFE)) {
@@ -322,7 +325,10 @@ __device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, ui
   }
   CandInterval<R> ci = cand_interval<R>(S1, S2, N, invN, sqrtN, c, ee, gamma, u, fmin);
   if (ci.realised == 0) {
-    if (lane == 0) ls.r[DSE_R_REALISED]++;
+    if (lane == 0) {
+      ls.r[DSE_R_REALISED]++;
+      note_why(A, gid, DSE_R_REALISED);
+    }
     return;
   }
   if (ci.realised == 2) {
@@ -335,6 +341,7 @@ __device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, ui
   if (lane == 0) {
     ls.r[DSE_VALID]++;
     ls.evaluated++;
+    note_why(A, gid, DSE_VALID);
   }
   unsigned pushed = score_and_push<R, NT>(A, lane == 0, gid, ci, S1, Sy, invN, gamma, u, ysum);
   refresh_pushed<NT>(A, pushed);
@@ -492,7 +499,10 @@ __device__ __forceinline__ unsigned binary_candidate(const ScreenArgs &A, LaneSt
   EvalErr<R> ee{R(0), R(0)};
   if (cand) reason = binary_apriori_W<R>(A, opc, ia, ib, fa_a, fa_b, kk, mi, mj, &ee);
   if (cand && additive) ls.seen++;
-  if (cand && reason != DSE_VALID) ls.r[reason]++;
+  if (cand && reason != DSE_VALID) {
+    ls.r[reason]++;
+    note_why(A, gid, reason);
+  }
   bool ok = cand && reason == DSE_VALID;
   if (ok && sizeof(R) == 4 && !((A.F.flags[ia] & A.F.flags[ib]) & F_FP32_SAFE)) {
     escalate(A, gid);
@@ -507,6 +517,7 @@ __device__ __forceinline__ unsigned binary_candidate(const ScreenArgs &A, LaneSt
     ci = cand_interval<R>(S1, S2, N, invN, sqrtN, cshift, ee, gamma, u, fmin);
     if (ci.realised == 0) {
       ls.r[DSE_R_REALISED]++;
+      note_why(A, gid, DSE_R_REALISED);
       ok = false;
     } else if (ci.realised == 2) {
       escalate(A, gid);
@@ -515,6 +526,7 @@ __device__ __forceinline__ unsigned binary_candidate(const ScreenArgs &A, LaneSt
     } else {
       ls.r[DSE_VALID]++;
       ls.evaluated++;
+      note_why(A, gid, DSE_VALID);
     }
   }
   return score_and_push<R, NT>(A, ok, gid, ci, S1, Sy, invN, gamma, u, ysum);
@@ -1051,6 +1063,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const Sc
     if (threadIdx.x == 0) {
       atomicAdd(&A.stats[good ? ST_REASON0 + DSE_VALID : ST_REASON0 + DSE_R_REALISED], 1ull);
       if (good) atomicAdd(&A.stats[ST_EVALUATED], 1ull);
+      if (A.why) A.why[gid - A.id_begin] = (int8_t)(good ? DSE_VALID : DSE_R_REALISED);
     }
     if (!good || !(sxx > 0.0)) continue;
     const double err = (double)(N / kEsc + 64) * 1.1102230246251565e-16 * 16.0;
@@ -1142,6 +1155,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
         good = __dsqrt_rn(fmax(sxx, 0.0) / (double)N) > A.fmin_std_rel64 * __dsqrt_rn(st[2] / (double)N);
       atomicAdd(&A.stats[good ? ST_REASON0 + DSE_VALID : ST_REASON0 + DSE_R_REALISED], 1ull);
       if (good) atomicAdd(&A.stats[ST_EVALUATED], 1ull);
+      if (A.why) A.why[gid - A.id_begin] = (int8_t)(good ? DSE_VALID : DSE_R_REALISED);
       if (good && sxx > 0.0) {
         const double err = (double)(N / kEsc + 64) * 1.1102230246251565e-16 * 16.0;
         const double dm = st[0] / (double)N;  // vbar - c
@@ -1153,6 +1167,35 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
     }
     __syncthreads();
   }
+}
+
+// Candidates no kernel visits: the additive slots of pairs whose units
+// differ (the additive kernels run over equal-unit pairs only).  Every other
+// entry of the range was written by the kernel that decided it; an entry
+// still at -1 afterwards would be a candidate no kernel looked at.
+__global__ void k_why_fixup(const ScreenArgs A) {
+  const uint64_t n = A.id_end - A.id_begin;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (A.why[i] != -1) continue;
+    const uint64_t gid = A.id_begin + i;
+    if (gid < (uint64_t)A.n_stored) continue;
+    int op;
+    int64_t a, b;
+    decode_gid(A, gid, &op, &a, &b);
+    const bool additive = op == DSE_OP_ADD || op == DSE_OP_SUB || op == DSE_OP_ABSDIFF;
+    if (additive && A.unit_check_addsub &&
+        (A.F.ukey[2 * a] != A.F.ukey[2 * b] || A.F.ukey[2 * a + 1] != A.F.ukey[2 * b + 1]))
+      A.why[i] = (int8_t)DSE_R_UNIT;
+  }
+}
+
+void launch_why_fixup(const ScreenArgs &A, int sms, cudaStream_t st) {
+  const uint64_t n = A.id_end - A.id_begin;
+  if (!A.why || n == 0) return;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > (uint64_t)sms * 8) blocks = (uint64_t)sms * 8;
+  note_launches(1);
+  k_why_fixup<<<(unsigned)blocks, 256, 0, st>>>(A);
 }
 
 // ------------------------------------------------------------ launchers

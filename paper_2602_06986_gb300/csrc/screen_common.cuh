@@ -175,6 +175,12 @@ __device__ __forceinline__ void cand_score_num(const CandInterval<R> &ci, R S1, 
   *eps_out = eps;
 }
 
+// Record the reason code a kernel assigned to candidate gid (in the first
+// target pass; a screen re-run writes the same codes again).
+__device__ __forceinline__ void note_why(const ScreenArgs &A, uint64_t gid, int reason) {
+  if (A.why && A.first_pass) A.why[gid - A.id_begin] = (int8_t)reason;
+}
+
 // ----------------------------------------------------- per-lane statistics
 
 struct LaneStats {

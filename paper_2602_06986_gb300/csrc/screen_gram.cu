@@ -682,6 +682,7 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
               const int reason = gram_apriori(A, opc, i, j, ca, cb);
               if (reason != DSE_VALID) {
                 ls.r[reason]++;
+                note_why(A, gid, reason);
               } else if (!((ca.flags & cb.flags) & F_FP32_SAFE)) {
                 escalate(A, gid);
                 ls.escalated++;
@@ -693,12 +694,14 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
                                                invN, ysum, fmin);
                 if (gc.realised == 0) {
                   ls.r[DSE_R_REALISED]++;
+                  note_why(A, gid, DSE_R_REALISED);
                 } else if (gc.realised == 2) {
                   escalate(A, gid);
                   ls.escalated++;
                 } else {
                   ls.r[DSE_VALID]++;
                   ls.evaluated++;
+                  note_why(A, gid, DSE_VALID);
                   want = true;
                   s = gc.s;
                   eps = gc.eps * (1.0f + 2.4e-7f);

@@ -13,6 +13,9 @@ void launch_feature(int prec64, int nt, const ScreenArgs &A, uint64_t id0, uint6
                     float gamma, int sms, cudaStream_t st);
 dse_status launch_pair(int prec64, int kind, int nt, const ScreenArgs &A, int block_len, int sms, cudaStream_t st);
 void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st, const ScreenArgs *batch = nullptr);
+// With A.why: the reason of the candidates no kernel visits (additive slots
+// of pairs with unequal units).
+void launch_why_fixup(const ScreenArgs &A, int sms, cudaStream_t st);
 void launch_pairlist(int prec64, int nt, const ScreenArgs &A, const int2 *pairs, int64_t n_pairs, float gamma,
                      int sms, cudaStream_t st);
 

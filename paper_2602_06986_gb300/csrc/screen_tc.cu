@@ -134,6 +134,7 @@ __device__ __forceinline__ TcCand tc_prepare(const ScreenArgs &A, LaneStats &ls,
   const int reason = binary_apriori_W<float>(A, opc, ia, ib, fa_a, fa_b, kk, mi, mj, &ee);
   if (reason != DSE_VALID) {
     ls.r[reason]++;
+    note_why(A, o.gid, reason);
     return o;
   }
   if (!((A.F.flags[ia] & A.F.flags[ib]) & F_FP32_SAFE)) {
@@ -147,6 +148,7 @@ __device__ __forceinline__ TcCand tc_prepare(const ScreenArgs &A, LaneStats &ls,
   o.ci = cand_interval<float>(S1, S2, N, invN, sqrtN, cshift, ee, gamma_gen, u, (float)A.fmin_std_rel64);
   if (o.ci.realised == 0) {
     ls.r[DSE_R_REALISED]++;
+    note_why(A, o.gid, DSE_R_REALISED);
     return o;
   }
   if (o.ci.realised == 2) {
@@ -156,6 +158,7 @@ __device__ __forceinline__ TcCand tc_prepare(const ScreenArgs &A, LaneStats &ls,
   }
   ls.r[DSE_VALID]++;
   ls.evaluated++;
+  note_why(A, o.gid, DSE_VALID);
   // The largest score the interval of target t can reach is
   // rhi = (|P_t| a2 + a0 + a1 |ysum_t|) / q_lo (the terms of cand_score_num's
   // numerator bound, split into what depends on the target and what does

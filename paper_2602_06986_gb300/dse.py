@@ -43,7 +43,7 @@ class ScreenDesc(C.Structure):
     _fields_ = [("Y", C.c_void_p), ("ld_y", C.c_int64), ("y_on_device", C.c_int32), ("n_targets", C.c_int32),
                 ("k", C.c_int64), ("mode", C.c_int32), ("precision", C.c_int32), ("id_begin", C.c_uint64),
                 ("id_end", C.c_uint64), ("stream", C.c_void_p), ("flags", C.c_int32), ("reserved0", C.c_int32),
-                ("dedup_tau", C.c_double)]
+                ("dedup_tau", C.c_double), ("reasons", C.c_void_p)]
 
 
 FLAG_TIMING = 1
@@ -96,7 +96,7 @@ class LoopResult(C.Structure):
                 ("stats", Stats * 4)]
 
 EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_counts", "dse_decode",
-           "dse_expr_string", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
+           "dse_expr_string", "dse_candidate_units", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
            "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
            "dse_residual_loop", "dse_l0_search", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error",
            "dse_version"]
@@ -119,6 +119,7 @@ def lib():
         L.dse_space_counts.argtypes = [vp, i32, C.POINTER(u64), C.POINTER(i64)]
         L.dse_decode.argtypes = [vp, u64, C.POINTER(Expr)]
         L.dse_expr_string.argtypes = [vp, u64, C.c_char_p, i64]
+        L.dse_candidate_units.argtypes = [vp, vp, i64, vp, vp]
         L.dse_sis_screen.argtypes = [vp, C.POINTER(ScreenDesc), C.POINTER(vp)]
         L.dse_result_free.argtypes = [vp]
         L.dse_result_free.restype = None
@@ -316,6 +317,7 @@ class Space:
         self._h = h
         self.n_samples = n_samples
         self.max_rung = max_rung
+        self.n_dims = units.shape[1]
         ns, nt = C.c_int64(), C.c_uint64()
         _check(lib().dse_space_size(self._h, C.byref(ns), C.byref(nt)))
         self.n_stored, self.n_total = ns.value, nt.value
@@ -347,10 +349,22 @@ class Space:
         _check(lib().dse_expr_string(self._h, gid, buf, len(buf)))
         return buf.value.decode()
 
+    def candidate_units(self, ids):
+        """(units int64 [n, n_dims] scaled by 2^max_rung, unit_ok int8 [n]) of
+        the candidate ids (dse_candidate_units)."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        n = len(ids)
+        units = np.zeros((n, max(self.n_dims, 1)), np.int64)
+        ok = np.zeros(n, np.int8)
+        _check(lib().dse_candidate_units(self._h, ids.ctypes.data, n, units.ctypes.data, ok.ctypes.data))
+        return units[:, : self.n_dims], ok
+
     def screen(self, Y, k, mode=MODE_PER_TARGET, precision=PREC_FP32, id_begin=0, id_end=0, stream=None,
-               flags=0, dedup_tau=None) -> Result:
+               flags=0, dedup_tau=None, reasons=None) -> Result:
         """SIS screen (dse_sis_screen).  With ``dedup_tau`` (0 < tau < 0.5) the
-        lists hold the top-k of the non-redundant candidates (DSE_FLAG_DEDUP)."""
+        lists hold the top-k of the non-redundant candidates (DSE_FLAG_DEDUP).
+        ``reasons``: optional torch int8 CUDA tensor of id_end - id_begin
+        entries that receives the reason code of every screened candidate."""
         if dedup_tau is not None:
             flags |= FLAG_DEDUP
         if isinstance(Y, np.ndarray):
@@ -360,8 +374,13 @@ class Space:
         T, ldy = Y.shape
         py, ydev = _ptr(Y)
         self._ykeep = Y
+        pw = None
+        if reasons is not None:
+            pw, wdev = _ptr(reasons)
+            if not wdev:
+                raise ValueError("reasons must be a CUDA tensor")
         d = ScreenDesc(py, ldy, ydev, T, k, mode, precision, id_begin, id_end, stream, flags, 0,
-                       dedup_tau if dedup_tau is not None else 0.0)
+                       dedup_tau if dedup_tau is not None else 0.0, pw)
         h = C.c_void_p()
         _check(lib().dse_sis_screen(self._h, C.byref(d), C.byref(h)))
         return Result(h, 1 if mode == MODE_AGGREGATED else T, k)

@@ -781,3 +781,37 @@ def test_every_op_domain_and_magnitude_on_signed_data(orc):
         assert (op, 3) in seen and (op, 0) in seen, op
     for op in (SQUARE, CUBE, MUL, DIV, RDIV, INV, EXP):
         assert (op, 4) in seen, op
+
+
+@pytest.mark.parametrize("n0,rung,ops,dims,seed", [
+    (4, 2, ALL_OPS, 2, 0),
+    (3, 2, (SUB, DIV, RDIV, SQRT, CUBE, INV), 3, 1),
+    (2, 3, (ADD, DIV, SQUARE, SQRT), 1, 3),
+])
+def test_candidate_units_and_reasons_against_bruteforce(orc, n0, rung, ops, dims, seed):
+    """Unit vectors of every candidate (stored and last rung) against the
+    brute-force trees' Fraction exponents times the common denominator
+    2^max_rung, and the per-candidate reason array against the value and
+    reason check of each candidate one by one."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.5, 2.0, size=(n0, 7))
+    units = rng.integers(-1, 2, size=(n0, dims)).astype(np.int32)
+    S = unpruned_space(orc, X, ops, rung, units=units, unit_check_addsub=1, explog_dimensionless=1)
+    stored, last = enumerate_bruteforce(units, ops, rung, True, True)
+    den = 2 ** rung
+    for i, e in enumerate(stored):
+        assert list(S.candidate_unit(i)) == [int(x * den) for x in e.unit]
+    why = S.reasons()
+    assert len(why) == S.total_candidates
+    assert np.all(why[: S.n_features] == 0)
+    for p, e in enumerate(last):
+        gid = S.n_features + p
+        u = S.candidate_unit(gid)
+        if e is None:
+            assert u is None and why[gid] == 1
+        else:
+            assert list(u) == [int(x * den) for x in e.unit], e.text
+            assert why[gid] == S.candidate(gid)[1]
+    # a sub-range gives the same bytes
+    a, b = S.n_features // 2, S.total_candidates - 3
+    assert np.array_equal(S.reasons(a, b), why[a:b])
