@@ -125,6 +125,21 @@ void triangle_tiles(int64_t ia, int64_t ib, int BI, int BJ, std::vector<Tile> &o
   }
 }
 
+// Order pair tiles so that the tiles resident at the same time share their
+// operand rows: groups of G consecutive i-blocks, j-block major inside a
+// group.  A wave of one CTA per SM then covers a compact block of the
+// triangle (e.g. 8 i-blocks x 19 j-blocks) whose rows stay in L2, instead of
+// one i-block against hundreds of j-blocks.
+void group_tiles(std::vector<Tile> &t, int64_t ia, int BI, int G) {
+  const int64_t span = (int64_t)BI * G;
+  std::stable_sort(t.begin(), t.end(), [&](const Tile &a, const Tile &b) {
+    const int64_t ga = (a.ibase - ia) / span, gb = (b.ibase - ia) / span;
+    if (ga != gb) return ga < gb;
+    if (a.jbase != b.jbase) return a.jbase < b.jbase;
+    return a.ibase < b.ibase;
+  });
+}
+
 // ------------------------------------------------------------- screening
 
 struct ScreenPlan {
@@ -163,8 +178,10 @@ int tc_ntp_for(int T, int N);
 size_t tc_bsplit_bytes(int ntp, int N);
 void launch_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N, int ntp, unsigned char *out,
                        cudaStream_t st);
-dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, float gamma_gen,
-                          float gamma_num, int gen_blk, int sms, cudaStream_t st);
+dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, const float *rows,
+                          int64_t nrows, float gamma_gen, float gamma_num, int gen_blk, int sms, cudaStream_t st);
+void launch_gather_rows(const float *v32, int64_t ld, const int32_t *rows, int64_t n, float *out, int sms,
+                        cudaStream_t st);
 
 // The tensor-core pass structure: each pass contracts `ntp` targets; the
 // CUDA-core kernels (stored/unary candidates, sparse additive pairs) cover the
@@ -196,12 +213,12 @@ static dse_status run_tc_passes(dse_result *R, const ScreenPlan &plan, void *scr
       if (ns > 0) {
         A.tiles = t0p;
         A.n_tiles = ns;
-        DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, plan.gamma_gen, plan.gamma_num, plan.gen_blk,
+        DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, sp->v32, sp->n, plan.gamma_gen, plan.gamma_num, plan.gen_blk,
                                sms, st));
       }
       A.tiles = t0p + ns;
       A.n_tiles = nall - ns;
-      DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
+      DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, sp->v32, sp->n, plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
                              st));
     }
     DSE_TRY(mark(2));
@@ -209,7 +226,14 @@ static dse_status run_tc_passes(dse_result *R, const ScreenPlan &plan, void *scr
       A.tiles = reinterpret_cast<const Tile *>(scr_tiles_add);
       A.n_tiles = (int32_t)plan.add_tiles.size();
       A.rowid = plan.add_by_id ? sp->rowid_ident : sp->class_rows;
-      DSE_TRY(launch_pair_tc(KIND_ADD, plan.ntp, A, plan.bsplit, plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
+      if (!plan.add_by_id && !sp->v32_class) {
+        // the rows in unit-class order, built at the first use
+        DSE_TRY(dmalloc(reinterpret_cast<void **>(&sp->v32_class), sizeof(float) * (size_t)(sp->n * sp->ld),
+                        "class-ordered rows"));
+        launch_gather_rows(sp->v32, sp->ld, sp->class_rows, sp->n, sp->v32_class, sms, st);
+      }
+      DSE_TRY(launch_pair_tc(KIND_ADD, plan.ntp, A, plan.bsplit, plan.add_by_id ? sp->v32 : sp->v32_class, sp->n,
+                             plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
                              st));
     }
   }
@@ -423,6 +447,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
       gram_tiles(sp, id_begin, id_end, plan.gram_tiles);
     } else if (any_mul) {
       triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.mul_tiles);
+      group_tiles(plan.mul_tiles, (int64_t)ia, BI, plan.use_tc ? 8 : 4);
       // A large tile list is launched in two parts: every 64th tile first, so
       // that the thresholds have risen from a spread sample of the space
       // before the bulk of the candidates is filtered.

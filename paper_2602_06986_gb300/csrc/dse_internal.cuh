@@ -257,6 +257,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
+// 2-D tensor copy (TMA) of one box at element coordinates (x, y) of the
+// tensor map into shared memory, completing on an mbarrier.  x times the
+// element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // 1-D bulk async copy global -> shared, completing on an mbarrier.
 // dst, src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -316,6 +327,7 @@ struct dse_space {
   uint64_t *used = nullptr, *dmask = nullptr, *op_deny = nullptr;  // user rules (nullptr: none)
   int32_t *rowid_ident = nullptr;   // identity row list [0, n)
   void *gram_buf = nullptr;         // product Gram images and sums (built at the first use)
+  float *v32_class = nullptr;       // v32 rows in unit-class order (tensor-core additive tiles, first use)
   // host copies for decoding
   std::vector<int32_t> h_op, h_rung, h_cplx;
   std::vector<int64_t> h_ca, h_cb;

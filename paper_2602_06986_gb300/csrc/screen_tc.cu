@@ -11,15 +11,17 @@
 // FP32.
 //
 // Warp roles (one CTA per SM, persistent over a static tile stride):
-//   warp 0        producer: 1-D bulk async copies of the tile's 24 operand
-//                 rows and the pre-split target block of each 32-sample chunk
-//                 into a 3-stage ring (mbarrier expect-tx);
+//   warp 0        producer: per 32-sample chunk, three 2-D tensor copies
+//                 (TMA, 128-byte swizzle) of the tile's 24 operand rows and a
+//                 bulk copy of the pre-split target block into a 3-stage ring
+//                 (mbarrier expect-tx);
 //   warp 1        TMEM allocation and the MMA issuer (one elected thread):
 //                 3 slots x 2 k-steps x 3 products per chunk; tcgen05.commit to
 //                 the stage's "empty" barrier and, after the last chunk of an
 //                 accumulation block, to the accumulator's "full" barrier;
-//   warps 2-9     generation: row m (a pair) x one half of each chunk's
-//                 samples: candidate values, FP32 S1/S2, BF16 hi/lo split,
+//   warps 2-9     generation: row m (a pair) x one half of each chunk's samples:
+//                 candidate values (each warp takes the reciprocals of the
+//                 rows it reads itself), FP32 S1/S2, BF16 hi/lo split,
 //                 16-byte stores into the canonical K-major layout (8x8 core
 //                 matrices, no swizzle), proxy fence, arrive;
 //   warps 10-13   epilogue: tcgen05.ld of TMEM lane quadrant (warp % 4),
@@ -36,6 +38,7 @@
 // step is modelled with a relative error of 2u on the running sum of
 // |terms|, with a safety factor of 4 (the accumulation order and rounding
 // inside an MMA are not documented, so this part is a model, not a proof).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -54,31 +57,48 @@ constexpr int M = 128;  // pairs per tile
 constexpr int BI = 16, BJ = 8, ROWS = BI + BJ;
 constexpr int NS = 3;     // stages
 constexpr int KB = 16;    // chunks per accumulation block (512 samples)
-constexpr int NGEN = 8;   // generation warps
+constexpr int NGEN = 8;   // generation warps: two per TMEM lane quadrant, one per half of a chunk
 constexpr int WARPS = 2 + NGEN + 4;
 constexpr int THREADS = WARPS * 32;
 constexpr uint32_t kWait = 1u << 22;
+// polls of the epilogue's waits, each followed by a short sleep (the
+// epilogue has a whole accumulation block of slack, so it polls gently)
+constexpr uint32_t kWaitLazy = 1u << 22;
 
-// operand rows in shared memory are RSTR floats apart (16 bytes of padding
-// per 32-sample row, so that the 8 j-rows a warp reads start in different
-// bank groups)
-constexpr int RSTR = KC + 4;
-constexpr uint32_t ROWS_BYTES = ROWS * RSTR * 4;  // 3456
+// Operand rows in shared memory: the 16 i-rows, then the 8 j-rows, 128 bytes
+// (32 samples) each, written by 2-D tensor copies (boxes of 8 rows) with the
+// 128-byte swizzle: 16-byte group q of row r sits at group q ^ (r & 7), so
+// the rows a warp reads at one sample offset lie in different banks.
+constexpr uint32_t ROWS_BYTES = ROWS * 128;  // 3072
 constexpr uint32_t A_TILE = M * KC * 2;         // 8192 per slot per hi/lo
 constexpr uint32_t A_OFF = ROWS_BYTES;
 constexpr uint32_t B_OFF = A_OFF + 6 * A_TILE;  // 52608
+// each generation warp's reciprocals of the rows it reads, for its 16
+// samples of the current chunk: its quadrant's 4 i-rows, then the 8 j-rows
+// (rows RW floats apart so that the lanes' 16-byte reads spread over banks)
+constexpr int RW = 20;
 __host__ __device__ constexpr uint32_t b_bytes(int ntp) { return 2u * (uint32_t)ntp * KC * 2; }
 __host__ __device__ constexpr uint32_t stage_bytes(int ntp) { return B_OFF + b_bytes(ntp); }
+static_assert(A_OFF % 1024 == 0 && B_OFF % 1024 == 0 && stage_bytes(16) % 1024 == 0 && stage_bytes(32) % 1024 == 0 &&
+                  stage_bytes(48) % 1024 == 0 && stage_bytes(64) % 1024 == 0,
+              "the swizzled row boxes need 1024-byte aligned stages");
+
+// Samples s .. s+3 (s a multiple of 4) and sample s of swizzled row r.
+__device__ __forceinline__ float4 row_ld4(const unsigned char *S, int r, int s) {
+  return *reinterpret_cast<const float4 *>(S + r * 128 + ((((s >> 2) ^ (r & 7))) << 4));
+}
+__device__ __forceinline__ float row_ld1(const unsigned char *S, int r, int s) {
+  return *reinterpret_cast<const float *>(S + r * 128 + ((((s >> 2) ^ (r & 7))) << 4) + ((s & 3) << 2));
+}
 
 struct Shared {
   uint64_t full_rows[NS], full_a[NS], empty[NS];
   uint64_t acc_full[2], acc_empty[2], gen_done[2], epi_free[2];
   uint64_t drain;  // last tcgen05.commit of the MMA issuer, before TMEM is freed
-  uint64_t rcp_ready[NS];  // every generation warp wrote its share of the stage's reciprocals
   uint32_t tmem_base;
   int abort;
   float hand[2][2][M][6];  // [tile parity][sample half][row][S1, S2 per slot]
-  __align__(16) float rcp[NS][ROWS * RSTR];  // reciprocals of each stage's operand rows (products/quotients)
+  __align__(16) float rcpw[NGEN][12][RW];
   float theta[4][64];        // each epilogue warp's copy of the pass's list thresholds
   float ysum[4][64];         // and of the targets' sums
   float sy[4][16][32];       // each epilogue warp's spill of 16 numerators for its rare full scores
@@ -210,14 +230,91 @@ __device__ __forceinline__ uint64_t tc_targets16(const ScreenArgs &A, const TcCa
   return pushed;
 }
 
+// Generation state of one row (pair) of a tile: the shift constants of the
+// three slots (products: the FMA constants of a*b, a/b, b/a; sums: the two
+// centring means and the |a-b| constant) and the running blocked sums.
+struct TcGen {
+  float c0, c1, c2;
+  float t1[3], t2[3];
+};
+
+// Eight samples of the three slots of one row: samples kbase + k .. +7 of
+// the stage's operand rows ri, rj (swizzled, see row_ld4) and entries k ..
+// k+7 of their reciprocals ria, rib (the warp's scratch).  Candidate values, FP32 sum w
+// and sum w^2, BF16 hi/lo splits (two values per conversion) and 16-byte
+// stores into the canonical K-major layout of the A tiles.  CHECK: entries at
+// or beyond `lim` are zero (the last, partial chunk).
+template <int KIND, bool CHECK>
+__device__ __forceinline__ void tc_gen8(TcGen &g, const unsigned char *S, int ri, int rj, const float *ria,
+                                        const float *rib, int k, int kbase, int lim, unsigned char *Aop, int m) {
+  using namespace tc;
+  float av[8], bv[8], iav[8], ibv[8];
+  *reinterpret_cast<float4 *>(av) = row_ld4(S, ri, kbase + k);
+  *reinterpret_cast<float4 *>(av + 4) = row_ld4(S, ri, kbase + k + 4);
+  *reinterpret_cast<float4 *>(bv) = row_ld4(S, rj, kbase + k);
+  *reinterpret_cast<float4 *>(bv + 4) = row_ld4(S, rj, kbase + k + 4);
+  if (KIND == KIND_MUL) {
+    *reinterpret_cast<float4 *>(iav) = *reinterpret_cast<const float4 *>(ria + k);
+    *reinterpret_cast<float4 *>(iav + 4) = *reinterpret_cast<const float4 *>(ria + k + 4);
+    *reinterpret_cast<float4 *>(ibv) = *reinterpret_cast<const float4 *>(rib + k);
+    *reinterpret_cast<float4 *>(ibv + 4) = *reinterpret_cast<const float4 *>(rib + k + 4);
+  }
+  float wv[3][8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    if (!CHECK || k + e < lim) {
+      const float a = av[e], b = bv[e];
+      if (KIND == KIND_MUL) {
+        wv[0][e] = fmaf(a, b, -g.c0);
+        wv[1][e] = fmaf(a, ibv[e], -g.c1);
+        wv[2][e] = fmaf(b, iav[e], -g.c2);
+      } else {
+        const float ac = a - g.c0, bc = b - g.c1, d = a - b;
+        wv[0][e] = ac + bc;
+        wv[1][e] = ac - bc;
+        wv[2][e] = fabsf(d) - g.c2;
+      }
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        g.t1[sl] += wv[sl][e];
+        g.t2[sl] = fmaf(wv[sl][e], wv[sl][e], g.t2[sl]);
+      }
+    } else {
+      wv[0][e] = wv[1][e] = wv[2][e] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(wv[sl][e], wv[sl][e + 1]);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(wv[sl][e] - __low2float(h), wv[sl][e + 1] - __high2float(h));
+      hi[e >> 1] = *reinterpret_cast<const uint32_t *>(&h);
+      lo[e >> 1] = *reinterpret_cast<const uint32_t *>(&l);
+    }
+    *reinterpret_cast<uint4 *>(Aop + (2 * sl) * A_TILE + core_off(m, kbase + k)) =
+        make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4 *>(Aop + (2 * sl + 1) * A_TILE + core_off(m, kbase + k)) =
+        make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
 template <int KIND, int NTP>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, const unsigned char *bsplit,
+                                                             const __grid_constant__ CUtensorMap rows_map,
                                                              float gamma_gen, float gamma_num, int gen_blk) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
   Shared &sh = *reinterpret_cast<Shared *>(smem);
   unsigned char *stages = smem + shared_bytes();
   constexpr uint32_t SB = stage_bytes(NTP);
+  // the swizzled row boxes need 1024-byte aligned stages (no static shared
+  // memory here, so the dynamic window starts aligned); refuse otherwise
+  if (smem_u32(stages) & 1023u) {
+    if (threadIdx.x == 0) atomicExch(A.err, DSE_EINVAL);
+    return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (A.N + KC - 1) / KC;
   const int nblocks = (nchunks + KB - 1) / KB;
@@ -241,7 +338,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       mbar_init(&sh.epi_free[b], 4);
     }
     mbar_init(&sh.drain, 1);
-    for (int s = 0; s < NS; ++s) mbar_init(&sh.rcp_ready[s], NGEN);
     sh.abort = 0;
     mbar_fence_init();
   }
@@ -274,21 +370,31 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
     }
     return ok;
   };
+  auto wait_warp_lazy = [&](uint64_t *bar, uint32_t parity) -> bool {
+    bool done = false;
+    for (uint32_t it = 0; it < kWaitLazy && !done; ++it) {
+      done = mbar_try_wait(bar, parity);
+      if (!done) __nanosleep(200);
+    }
+    const bool ok = __all_sync(0xffffffffu, done);
+    if (!ok && lane == 0) {
+      atomicExch(A.err, DSE_ETIMEOUT);
+      *abort_flag = 1;
+    }
+    return ok;
+  };
   auto aborted_warp = [&]() -> bool { return __any_sync(0xffffffffu, *abort_flag != 0); };
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    // whole warp: lane r < 24 copies operand row r, lane 24 the target block
+    // lane 0: three 2-D tensor copies of the chunk's operand rows (i-rows
+    // 0-7, 8-15, j-rows 0-7 at the tile's row positions; rows past the end
+    // and samples past N arrive as zeros) and one bulk copy of its target
+    // block
     int lt = 0;
     uint32_t issued = 0;  // chunks whose copies were issued
     for (int tile = blockIdx.x; tile < A.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
       const Tile tl = A.tiles[tile];
-      int id = -1;
-      if (lane < BI) {
-        if (lane < tl.ni) id = A.rowid[tl.ibase + lane];
-      } else if (lane < ROWS && lane - BI < tl.nj) {
-        id = A.rowid[tl.jbase + lane - BI];
-      }
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
         const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
@@ -297,15 +403,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
           break;
         }
         unsigned char *S = stages + (size_t)st * SB;
-        const int64_t s0 = (int64_t)c * KC;
-        int64_t cnt = A.F.ld - s0;
-        if (cnt > KC) cnt = KC;
-        const uint32_t rb = (uint32_t)cnt * 4u;
-        const unsigned bytes = __reduce_add_sync(0xffffffffu, id >= 0 ? rb : 0u) + b_bytes(NTP);
-        if (lane == 0) mbar_arrive_expect_tx(&sh.full_rows[st], bytes);
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&sh.full_rows[st], 3u * 1024u + b_bytes(NTP));
+          const int x = c * KC;
+          tma_load_2d(S, &rows_map, x, tl.ibase, &sh.full_rows[st]);
+          tma_load_2d(S + 1024, &rows_map, x, tl.ibase + 8, &sh.full_rows[st]);
+          tma_load_2d(S + 2048, &rows_map, x, tl.jbase, &sh.full_rows[st]);
+          bulk_g2s(S + B_OFF, bsplit + (size_t)c * b_bytes(NTP), b_bytes(NTP), &sh.full_rows[st]);
+        }
         __syncwarp();
-        if (id >= 0) bulk_g2s(S + lane * RSTR * 4, A.F.v32 + (int64_t)id * A.F.ld + s0, rb, &sh.full_rows[st]);
-        if (lane == ROWS) bulk_g2s(S + B_OFF, bsplit + (size_t)c * b_bytes(NTP), b_bytes(NTP), &sh.full_rows[st]);
         issued = gc + 1;
       }
       if (!ok) break;
@@ -358,6 +464,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
     }
   } else if (warp < 2 + NGEN) {
     // ---------------------------------------------------------- generation
+    // warp g = warp - 2 writes rows m = 32 (g & 3) + lane (one pair each)
+    // for samples [16 h, 16 h + 16) of every chunk, h = g >> 2 (all eight
+    // warps work on the same chunk, so each waits only for fills whose
+    // predecessors it consumed itself)
     const int gw = warp - 2;
     const int m = (gw & 3) * 32 + lane;  // row = pair
     const int half = gw >> 2;            // which 16 samples of a chunk
@@ -370,16 +480,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       const float4 fa_i = fi >= 0 ? A.F.fa[fi] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 fa_j = fj >= 0 ? A.F.fa[fj] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float mi = fa_i.x, mj = fa_j.x;
-      float c0, c1, c2;
+      TcGen g;
       if (KIND == KIND_MUL) {
-        c0 = mi * mj;
-        c1 = mi * fa_j.y;
-        c2 = mj * fa_i.y;
+        g.c0 = mi * mj;
+        g.c1 = mi * fa_j.y;
+        g.c2 = mj * fa_i.y;
       } else {
-        c0 = c1 = 0.f;
-        c2 = fabsf(mi - mj);
+        g.c0 = mi;
+        g.c1 = mj;
+        g.c2 = fabsf(mi - mj);
       }
-      float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, t1[3] = {0.f, 0.f, 0.f}, t2[3] = {0.f, 0.f, 0.f};
+      float s1[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) g.t1[k] = g.t2[k] = 0.f;
       int blk = 0;
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
@@ -389,88 +502,37 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
           break;
         }
         unsigned char *S = stages + (size_t)st * SB;
-        const float *rows = reinterpret_cast<const float *>(S);
+        const float *ria = nullptr, *rib = nullptr;
         if (KIND == KIND_MUL) {
-          // the reciprocals of the stage's 24 operand rows, computed once
-          // (each generation thread takes 3 of the 768) and shared by the
-          // 128 pairs; a bounded mbarrier wait orders them before use
-          float *rc = sh.rcp[st];
-          for (int e = gw * 32 + lane; e < ROWS * KC; e += NGEN * 32) {
-            const int r = e / KC, k = e % KC;
-            rc[r * RSTR + k] = rcp_approx(rows[r * RSTR + k]);
+          // the reciprocals this warp needs (6 per lane; the previous chunk's
+          // reads finished at the __syncwarp before its arrive)
+          float(*rw)[RW] = sh.rcpw[gw];
+#pragma unroll
+          for (int t = 0; t < 6; ++t) {
+            const int e = lane + 32 * t, r = e >> 4, k = e & 15;
+            const int src = r < 4 ? (gw & 3) * 4 + r : BI + (r - 4);
+            rw[r][k] = rcp_approx(row_ld1(S, src, half * 16 + k));
           }
           __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.rcp_ready[st]);
-          if (!wait_warp(&sh.rcp_ready[st], u & 1)) {
-            ok = false;
-            break;
-          }
+          ria = rw[ti - (gw & 3) * 4];
+          rib = rw[4 + tj];
         }
-        const float *ra = rows + ti * RSTR, *rb = rows + (BI + tj) * RSTR;
-        const float *ria = sh.rcp[st] + ti * RSTR, *rib = sh.rcp[st] + (BI + tj) * RSTR;
+        unsigned char *Aop = S + A_OFF;
+        if ((c + 1) * KC <= A.N) {
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const int k0s = half * 16 + g * 8;
-          float av[8], bv[8], iav[8], ibv[8];
-          *reinterpret_cast<float4 *>(av) = *reinterpret_cast<const float4 *>(ra + k0s);
-          *reinterpret_cast<float4 *>(av + 4) = *reinterpret_cast<const float4 *>(ra + k0s + 4);
-          *reinterpret_cast<float4 *>(bv) = *reinterpret_cast<const float4 *>(rb + k0s);
-          *reinterpret_cast<float4 *>(bv + 4) = *reinterpret_cast<const float4 *>(rb + k0s + 4);
-          if (KIND == KIND_MUL) {
-            *reinterpret_cast<float4 *>(iav) = *reinterpret_cast<const float4 *>(ria + k0s);
-            *reinterpret_cast<float4 *>(iav + 4) = *reinterpret_cast<const float4 *>(ria + k0s + 4);
-            *reinterpret_cast<float4 *>(ibv) = *reinterpret_cast<const float4 *>(rib + k0s);
-            *reinterpret_cast<float4 *>(ibv + 4) = *reinterpret_cast<const float4 *>(rib + k0s + 4);
-          }
-          float wv[3][8];
+          for (int q = 0; q < 2; ++q) tc_gen8<KIND, false>(g, S, ti, BI + tj, ria, rib, q * 8, half * 16, 0, Aop, m);
+        } else {
+          const int lim = A.N - c * KC - half * 16;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            if (c * KC + k0s + e < A.N) {
-              const float a = av[e], b = bv[e];
-              if (KIND == KIND_MUL) {
-                wv[0][e] = fmaf(a, b, -c0);
-                wv[1][e] = fmaf(a, ibv[e], -c1);
-                wv[2][e] = fmaf(b, iav[e], -c2);
-              } else {
-                const float ac = a - mi, bc = b - mj, d = a - b;
-                wv[0][e] = ac + bc;
-                wv[1][e] = ac - bc;
-                wv[2][e] = fabsf(d) - c2;
-              }
-#pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                t1[k] += wv[k][e];
-                t2[k] = fmaf(wv[k][e], wv[k][e], t2[k]);
-              }
-            } else {
-              wv[0][e] = wv[1][e] = wv[2][e] = 0.f;
-            }
-          }
-          // BF16 hi/lo splits of two values per conversion instruction
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            uint32_t hi[4], lo[4];
-#pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-              const __nv_bfloat162 h = __floats2bfloat162_rn(wv[k][e], wv[k][e + 1]);
-              const __nv_bfloat162 l =
-                  __floats2bfloat162_rn(wv[k][e] - __low2float(h), wv[k][e + 1] - __high2float(h));
-              hi[e >> 1] = *reinterpret_cast<const uint32_t *>(&h);
-              lo[e >> 1] = *reinterpret_cast<const uint32_t *>(&l);
-            }
-            *reinterpret_cast<uint4 *>(S + A_OFF + (2 * k) * A_TILE + core_off(m, k0s)) =
-                make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4 *>(S + A_OFF + (2 * k + 1) * A_TILE + core_off(m, k0s)) =
-                make_uint4(lo[0], lo[1], lo[2], lo[3]);
-          }
+          for (int q = 0; q < 2; ++q) tc_gen8<KIND, true>(g, S, ti, BI + tj, ria, rib, q * 8, half * 16, lim, Aop, m);
         }
         if (++blk == gen_blk) {
           blk = 0;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            s1[k] += t1[k];
-            s2[k] += t2[k];
-            t1[k] = t2[k] = 0.f;
+            s1[k] += g.t1[k];
+            s2[k] += g.t2[k];
+            g.t1[k] = g.t2[k] = 0.f;
           }
         }
         fence_proxy_async();
@@ -483,8 +545,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       if (lt >= 2 && !wait_warp(&sh.epi_free[p], ((lt >> 1) - 1) & 1)) break;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        sh.hand[p][half][m][2 * k] = s1[k] + t1[k];
-        sh.hand[p][half][m][2 * k + 1] = s2[k] + t2[k];
+        sh.hand[p][half][m][2 * k] = s1[k] + g.t1[k];
+        sh.hand[p][half][m][2 * k + 1] = s2[k] + g.t2[k];
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.gen_done[p]);
@@ -531,7 +593,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
             for (int t = 0; t < (NTP <= 32 ? NTP : 1); ++t) acc[k][t] = 0.f;
           for (int b = 0; b < nblocks; ++b) {
             const uint32_t gb = (uint32_t)lt * nblocks + b, buf = gb & 1, ub = gb >> 1;
-            if (!wait_warp(&sh.acc_full[buf], ub & 1)) break;
+            if (!wait_warp_lazy(&sh.acc_full[buf], ub & 1)) break;
             fence_after();
 #pragma unroll
             for (int k = 0; k < 3; ++k)
@@ -550,11 +612,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
         }
       }
       const uint32_t gb_last = (uint32_t)lt * nblocks + (nblocks - 1), buf_last = gb_last & 1;
-      if (nblocks == 1 && !wait_warp(&sh.acc_full[buf_last], (gb_last >> 1) & 1)) break;
+      if (nblocks == 1 && !wait_warp_lazy(&sh.acc_full[buf_last], (gb_last >> 1) & 1)) break;
       if (aborted_warp()) break;
       fence_after();
       const int p = lt & 1;
-      if (!wait_warp(&sh.gen_done[p], (lt >> 1) & 1)) break;
+      if (!wait_warp_lazy(&sh.gen_done[p], (lt >> 1) & 1)) break;
       // this warp's copy of the list thresholds (they only rise, so an older
       // copy is still a valid lower bound)
       for (int t = lane; t < NTP; t += 32) {
@@ -612,9 +674,45 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
 
 // --------------------------------------------------------------- launcher
 
+// Tensor map of the FP32 operand rows [nrows][ld] (N valid samples per row)
+// for the kernel's 2-D copies: boxes of 32 samples x 8 rows, 128-byte
+// swizzle, zero fill outside.  cuTensorMapEncodeTiled comes from the driver
+// through the runtime's entry-point query (the library links the runtime
+// only).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static dse_status rows_tensor_map(const float *base, int64_t nrows, int64_t N, int64_t ld, CUtensorMap *out) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      set_error("cuTensorMapEncodeTiled is not available from the driver");
+      return DSE_ECUDA;
+    }
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)(nrows > 0 ? nrows : 1)};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)tc::KC, 8u};
+  const cuuint32_t elem[2] = {1u, 1u};
+  const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box,
+                            elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DSE_ECUDA;
+  }
+  return DSE_OK;
+}
+
 template <int KIND, int NTP>
-static dse_status launch_tc_t(const ScreenArgs &A, const unsigned char *bsplit, float gamma_gen, float gamma_num,
-                              int gen_blk, int sms, cudaStream_t st) {
+static dse_status launch_tc_t(const ScreenArgs &A, const unsigned char *bsplit, const CUtensorMap &map,
+                              float gamma_gen, float gamma_num, int gen_blk, int sms, cudaStream_t st) {
   const size_t smem = tc::shared_bytes() + (size_t)tc::NS * tc::stage_bytes(NTP);
   static bool attr[64] = {false};
   int dev = 0;
@@ -628,8 +726,26 @@ static dse_status launch_tc_t(const ScreenArgs &A, const unsigned char *bsplit, 
   note_launches(1);
   ScreenArgs B = A;
   B.group = KIND == KIND_MUL ? 1 : 2;
-  k_pair_tc<KIND, NTP><<<grid, tc::THREADS, smem, st>>>(B, bsplit, gamma_gen, gamma_num, gen_blk);
+  k_pair_tc<KIND, NTP><<<grid, tc::THREADS, smem, st>>>(B, bsplit, map, gamma_gen, gamma_num, gen_blk);
   return DSE_OK;
+}
+
+// Rows in the order of a row list (the unit-class order of the additive
+// tiles): out[p] = v32[rows[p]], so that a tile's rows are consecutive for
+// the 2-D copies.
+__global__ void k_gather_rows(const float *v32, int64_t ld, const int32_t *rows, int64_t n, float *out) {
+  const int64_t total = n * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = v32[(int64_t)rows[e / ld] * ld + e % ld];
+}
+
+void launch_gather_rows(const float *v32, int64_t ld, const int32_t *rows, int64_t n, float *out, int sms,
+                        cudaStream_t st) {
+  int64_t blocks = (n * ld + 255) / 256;
+  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  if (blocks < 1) return;
+  note_launches(1);
+  k_gather_rows<<<(unsigned)blocks, 256, 0, st>>>(v32, ld, rows, n, out);
 }
 
 int tc_ntp_for(int T, int N) {
@@ -656,17 +772,19 @@ void launch_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N, int 
   k_tc_targets<<<(unsigned)blocks, 256, 0, st>>>(y32, ldy, t0, T, N, ntp, nchunks, out);
 }
 
-dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, float gamma_gen,
-                          float gamma_num, int gen_blk, int sms, cudaStream_t st) {
+dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, const float *rows,
+                          int64_t nrows, float gamma_gen, float gamma_num, int gen_blk, int sms, cudaStream_t st) {
   if (A.n_tiles <= 0) return DSE_OK;
+  CUtensorMap map;
+  DSE_TRY(rows_tensor_map(rows, nrows, A.N, A.F.ld, &map));
   if (ntp > 32 && (A.N + tc::KC - 1) / tc::KC > tc::KB) {
     set_error("target block %d needs N <= %d samples", ntp, tc::KB * tc::KC);
     return DSE_EINVAL;
   }
 #define DSE_TC_CASE(NTPV)                                                                                   \
   case NTPV:                                                                                                \
-    return kind == KIND_MUL ? launch_tc_t<KIND_MUL, NTPV>(A, bsplit, gamma_gen, gamma_num, gen_blk, sms, st) \
-                            : launch_tc_t<KIND_ADD, NTPV>(A, bsplit, gamma_gen, gamma_num, gen_blk, sms, st);
+    return kind == KIND_MUL ? launch_tc_t<KIND_MUL, NTPV>(A, bsplit, map, gamma_gen, gamma_num, gen_blk, sms, st) \
+                            : launch_tc_t<KIND_ADD, NTPV>(A, bsplit, map, gamma_gen, gamma_num, gen_blk, sms, st);
   switch (ntp) {
     DSE_TC_CASE(16)
     DSE_TC_CASE(32)
