@@ -175,11 +175,15 @@ dse_status launch_pair_gram(const ScreenArgs &A, const void *space_buf, void *sc
                             int sms, cudaStream_t st);
 
 int tc_ntp_for(int T, int N);
+int tc_gen_samples();
+int tc_gen_parts();
 size_t tc_bsplit_bytes(int ntp, int N);
 void launch_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N, int ntp, unsigned char *out,
                        cudaStream_t st);
 dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, const float *rows,
-                          int64_t nrows, float gamma_gen, float gamma_num, int gen_blk, int sms, cudaStream_t st);
+                          const float *rcp_rows, int64_t nrows, float gamma_gen, float gamma_num, int gen_blk, int sms,
+                          cudaStream_t st);
+void launch_rcp_rows(const float *v32, int64_t count, float *out, int sms, cudaStream_t st);
 void launch_gather_rows(const float *v32, int64_t ld, const int32_t *rows, int64_t n, float *out, int sms,
                         cudaStream_t st);
 
@@ -207,18 +211,24 @@ static dse_status run_tc_passes(dse_result *R, const ScreenPlan &plan, void *scr
     A.first_pass = tp == 0;
     DSE_TRY(mark(1));
     if (!plan.mul_tiles.empty()) {
+      if (!sp->rcp32) {
+        // reciprocal rows of the stored features, built at the first use
+        const int64_t cnt = sp->n * sp->ld;
+        DSE_TRY(dmalloc(reinterpret_cast<void **>(&sp->rcp32), sizeof(float) * (size_t)cnt, "reciprocal rows"));
+        launch_rcp_rows(sp->v32, cnt, sp->rcp32, sms, st);
+      }
       A.rowid = sp->rowid_ident;
       const Tile *t0p = reinterpret_cast<const Tile *>(scr_tiles_mul);
       const int32_t nall = (int32_t)plan.mul_tiles.size(), ns = plan.n_seed_tiles;
       if (ns > 0) {
         A.tiles = t0p;
         A.n_tiles = ns;
-        DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, sp->v32, sp->n, plan.gamma_gen, plan.gamma_num, plan.gen_blk,
+        DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, sp->v32, sp->rcp32, sp->n, plan.gamma_gen, plan.gamma_num, plan.gen_blk,
                                sms, st));
       }
       A.tiles = t0p + ns;
       A.n_tiles = nall - ns;
-      DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, sp->v32, sp->n, plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
+      DSE_TRY(launch_pair_tc(KIND_MUL, plan.ntp, A, plan.bsplit, sp->v32, sp->rcp32, sp->n, plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
                              st));
     }
     DSE_TRY(mark(2));
@@ -232,7 +242,7 @@ static dse_status run_tc_passes(dse_result *R, const ScreenPlan &plan, void *scr
                         "class-ordered rows"));
         launch_gather_rows(sp->v32, sp->ld, sp->class_rows, sp->n, sp->v32_class, sms, st);
       }
-      DSE_TRY(launch_pair_tc(KIND_ADD, plan.ntp, A, plan.bsplit, plan.add_by_id ? sp->v32 : sp->v32_class, sp->n,
+      DSE_TRY(launch_pair_tc(KIND_ADD, plan.ntp, A, plan.bsplit, plan.add_by_id ? sp->v32 : sp->v32_class, nullptr, sp->n,
                              plan.gamma_gen, plan.gamma_num, plan.gen_blk, sms,
                              st));
     }
@@ -492,15 +502,19 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
     plan.ntp = tc_ntp_for(d->n_targets, (int)N);
     plan.tc_passes = (d->n_targets + plan.ntp - 1) / plan.ntp;
     const int nchunks = (int)((N + 31) / 32);
-    plan.gen_blk = std::max(1, (int)lround(sqrt(nchunks / 16.0)));
-    // generation sums: 16 samples of each chunk per thread, blocks of
-    // gen_blk chunks, the two halves added at the end
-    plan.gamma_gen = (float)((16.0 * plan.gen_blk + ceil((double)nchunks / plan.gen_blk) + 6.0) * u32 * 1.05);
+    // generation sums: spp samples of each chunk per thread, blocks of
+    // gen_blk chunks, the parts' partial sums added at the end
+    const double spp = tc_gen_samples(), parts = tc_gen_parts();
+    plan.gen_blk = std::max(1, (int)lround(sqrt(nchunks / spp)));
+    plan.gamma_gen =
+        (float)((spp * plan.gen_blk + ceil((double)nchunks / plan.gen_blk) + parts + 4.0) * u32 * 1.05);
     // contraction: BF16x3 split (w = wh + wl + ew with |ew| <= 2^-16 |w|, the
     // same for y; dropping wl*yl, ew*y and w*ey leaves at most 3.01 * 2^-16
     // of sum |w y|) plus 2u per tensor-core
     // accumulation step (3 products x 2 k-steps per chunk, up to 16 chunks per
-    // TMEM block) and the register drain of the blocks, times a safety factor 4
+    // TMEM block; with 16 targets the products go to two accumulators of at
+    // most 2 x 2 steps per chunk, whose halves are added once: fewer steps)
+    // and the register drain of the blocks, times a safety factor 4
     const int nblocks = (nchunks + 15) / 16;
     const double steps = 3.0 * 2.0 * std::min(nchunks, 16);
     plan.gamma_num = (float)(4.0 * (2.0 * steps + nblocks + 2.0) * u32 + 3.02 * 1.52587890625e-5 +

@@ -11,24 +11,26 @@
 // FP32.
 //
 // Warp roles (one CTA per SM, persistent over a static tile stride):
-//   warp 0        producer: per 32-sample chunk, three 2-D tensor copies
-//                 (TMA, 128-byte swizzle) of the tile's 24 operand rows and a
-//                 bulk copy of the pre-split target block into a 3-stage ring
+//   warp 0        producer: per 32-sample chunk, 2-D tensor copies (TMA,
+//                 boxes of 8 rows, 128-byte swizzle) of the tile's 24
+//                 operand rows and of their reciprocal rows, and a bulk copy
+//                 of the pre-split target block into a 3-stage ring
 //                 (mbarrier expect-tx);
 //   warp 1        TMEM allocation and the MMA issuer (one elected thread):
 //                 3 slots x 2 k-steps x 3 products per chunk; tcgen05.commit to
 //                 the stage's "empty" barrier and, after the last chunk of an
 //                 accumulation block, to the accumulator's "full" barrier;
-//   warps 2-9     generation: row m (a pair) x one half of each chunk's samples:
-//                 candidate values (each warp takes the reciprocals of the
-//                 rows it reads itself), FP32 S1/S2, BF16 hi/lo split,
+//   warps 2-17    generation: row m (a pair) x one quarter of each chunk's samples:
+//                 candidate values (quotients from reciprocal rows copied
+//                 next to the value rows), FP32 S1/S2, BF16 hi/lo split,
 //                 16-byte stores into the canonical K-major layout (8x8 core
 //                 matrices, no swizzle), proxy fence, arrive;
-//   warps 10-13   epilogue: tcgen05.ld of TMEM lane quadrant (warp % 4),
+//   warps 18-21   epilogue: tcgen05.ld of TMEM lane quadrant (warp % 4),
 //                 block accumulation, scores, error bounds, threshold pushes.
 // Accumulators are double-buffered in TMEM by accumulation block (up to 16
 // chunks = 512 samples), so the epilogue of one block overlaps the MMAs of
-// the next; longer sample ranges drain each block into FP32 registers.
+// the next; longer sample ranges drain each block into a running FP32 sum
+// that the epilogue keeps in further TMEM columns.
 //
 // Error model of the contraction (used for the reported bound, and the
 // reason reported TC scores above the 1e-5 tolerance are re-scored):
@@ -57,7 +59,9 @@ constexpr int M = 128;  // pairs per tile
 constexpr int BI = 16, BJ = 8, ROWS = BI + BJ;
 constexpr int NS = 3;     // stages
 constexpr int KB = 16;    // chunks per accumulation block (512 samples)
-constexpr int NGEN = 8;   // generation warps: two per TMEM lane quadrant, one per half of a chunk
+constexpr int NGEN = 16;  // generation warps: four per row quadrant, one per quarter of a chunk
+constexpr int NPART = NGEN / 4;  // parts of a chunk's samples
+constexpr int SPP = 32 / NPART;  // samples per part (a multiple of 8)
 constexpr int WARPS = 2 + NGEN + 4;
 constexpr int THREADS = WARPS * 32;
 constexpr uint32_t kWait = 1u << 22;
@@ -69,26 +73,41 @@ constexpr uint32_t kWaitLazy = 1u << 22;
 // (32 samples) each, written by 2-D tensor copies (boxes of 8 rows) with the
 // 128-byte swizzle: 16-byte group q of row r sits at group q ^ (r & 7), so
 // the rows a warp reads at one sample offset lie in different banks.
-constexpr uint32_t ROWS_BYTES = ROWS * 128;  // 3072
+constexpr uint32_t ROWS_BYTES = 2 * ROWS * 128;  // 6144: the rows, then their reciprocals (products)
+constexpr int RCP_ROW = ROWS;                      // row index of the first reciprocal row
 constexpr uint32_t A_TILE = M * KC * 2;         // 8192 per slot per hi/lo
 constexpr uint32_t A_OFF = ROWS_BYTES;
-constexpr uint32_t B_OFF = A_OFF + 6 * A_TILE;  // 52608
-// each generation warp's reciprocals of the rows it reads, for its 16
-// samples of the current chunk: its quadrant's 4 i-rows, then the 8 j-rows
-// (rows RW floats apart so that the lanes' 16-byte reads spread over banks)
-constexpr int RW = 20;
+// With 16 targets a pass the A operands (candidate values, BF16 hi/lo) live
+// in tensor memory: the MMA then reads only B from shared memory, whose
+// bandwidth an N = 16 MMA with a shared-memory A would exhaust.  Wider target
+// blocks keep A in shared memory (their accumulators leave no room).
+__host__ __device__ constexpr bool tmem_a(int ntp) { return ntp == 16; }
+__host__ __device__ constexpr uint32_t b_off(int ntp) { return tmem_a(ntp) ? ROWS_BYTES : A_OFF + 6 * A_TILE; }
 __host__ __device__ constexpr uint32_t b_bytes(int ntp) { return 2u * (uint32_t)ntp * KC * 2; }
-__host__ __device__ constexpr uint32_t stage_bytes(int ntp) { return B_OFF + b_bytes(ntp); }
-static_assert(A_OFF % 1024 == 0 && B_OFF % 1024 == 0 && stage_bytes(16) % 1024 == 0 && stage_bytes(32) % 1024 == 0 &&
-                  stage_bytes(48) % 1024 == 0 && stage_bytes(64) % 1024 == 0,
+__host__ __device__ constexpr uint32_t stage_bytes(int ntp) { return b_off(ntp) + b_bytes(ntp); }
+static_assert(A_OFF % 1024 == 0 && b_off(16) % 1024 == 0 && b_off(32) % 1024 == 0 && stage_bytes(16) % 1024 == 0 &&
+                  stage_bytes(32) % 1024 == 0 && stage_bytes(48) % 1024 == 0 && stage_bytes(64) % 1024 == 0,
               "the swizzled row boxes need 1024-byte aligned stages");
+// TMEM columns: two accumulator buffers of 3 slots x acc_w columns, the
+// running sums of longer sample ranges (3 x NTP, NTP = 32; with A in TMEM
+// they are kept in shared memory), then (A in TMEM) per stage 3 slots x
+// hi/lo x KC/2 columns (two BF16 per 32-bit column).  With A in TMEM each
+// slot's accumulator is 2 NTP wide: one N = 2 NTP MMA takes wh against the
+// stacked [yh; yl] block and an N = NTP MMA adds wl yh onto the first half,
+// so the numerator is the sum of the two halves (two MMAs per K-step and
+// slot instead of three).
+__host__ __device__ constexpr int acc_w(int ntp) { return tmem_a(ntp) ? 2 * ntp : ntp; }
+__host__ __device__ constexpr int acc_cols(int ntp) {
+  return tmem_a(ntp) ? 6 * acc_w(ntp) : ntp <= 32 ? 9 * ntp : 6 * ntp;
+}
+constexpr int A_STAGE_COLS = 3 * 2 * (KC / 2);  // 96
+__host__ __device__ constexpr int tmem_cols_needed(int ntp) {
+  return acc_cols(ntp) + (tmem_a(ntp) ? NS * A_STAGE_COLS : 0);
+}
 
-// Samples s .. s+3 (s a multiple of 4) and sample s of swizzled row r.
+// Samples s .. s+3 (s a multiple of 4) of swizzled row r.
 __device__ __forceinline__ float4 row_ld4(const unsigned char *S, int r, int s) {
   return *reinterpret_cast<const float4 *>(S + r * 128 + ((((s >> 2) ^ (r & 7))) << 4));
-}
-__device__ __forceinline__ float row_ld1(const unsigned char *S, int r, int s) {
-  return *reinterpret_cast<const float *>(S + r * 128 + ((((s >> 2) ^ (r & 7))) << 4) + ((s & 3) << 2));
 }
 
 struct Shared {
@@ -97,14 +116,17 @@ struct Shared {
   uint64_t drain;  // last tcgen05.commit of the MMA issuer, before TMEM is freed
   uint32_t tmem_base;
   int abort;
-  float hand[2][2][M][6];  // [tile parity][sample half][row][S1, S2 per slot]
-  __align__(16) float rcpw[NGEN][12][RW];
+  float hand[2][NPART][M][6];  // [tile parity][sample part][row][S1, S2 per slot]
   float theta[4][64];        // each epilogue warp's copy of the pass's list thresholds
   float ysum[4][64];         // and of the targets' sums
   float sy[4][16][32];       // each epilogue warp's spill of 16 numerators for its rare full scores
 };
 
 constexpr size_t shared_bytes() { return (sizeof(Shared) + 1023) / 1024 * 1024; }
+// With A in TMEM, each row's running numerator sums (3 slots x NTP, rows 49
+// floats apart) follow the stages in shared memory.
+constexpr int RUN_W = 49;
+__host__ __device__ constexpr size_t run_bytes(int ntp) { return tmem_a(ntp) ? (size_t)M * RUN_W * 4 : 0; }
 
 }  // namespace tc
 
@@ -239,14 +261,14 @@ struct TcGen {
 };
 
 // Eight samples of the three slots of one row: samples kbase + k .. +7 of
-// the stage's operand rows ri, rj (swizzled, see row_ld4) and entries k ..
-// k+7 of their reciprocals ria, rib (the warp's scratch).  Candidate values, FP32 sum w
+// the stage's operand rows ri, rj and of their reciprocal rows (swizzled,
+// see row_ld4).  Candidate values, FP32 sum w
 // and sum w^2, BF16 hi/lo splits (two values per conversion) and 16-byte
 // stores into the canonical K-major layout of the A tiles.  CHECK: entries at
 // or beyond `lim` are zero (the last, partial chunk).
-template <int KIND, bool CHECK>
-__device__ __forceinline__ void tc_gen8(TcGen &g, const unsigned char *S, int ri, int rj, const float *ria,
-                                        const float *rib, int k, int kbase, int lim, unsigned char *Aop, int m) {
+template <int KIND, bool CHECK, bool TA>
+__device__ __forceinline__ void tc_gen8(TcGen &g, const unsigned char *S, int ri, int rj, int k, int kbase, int lim,
+                                        unsigned char *Aop, uint32_t acol, int m) {
   using namespace tc;
   float av[8], bv[8], iav[8], ibv[8];
   *reinterpret_cast<float4 *>(av) = row_ld4(S, ri, kbase + k);
@@ -254,10 +276,10 @@ __device__ __forceinline__ void tc_gen8(TcGen &g, const unsigned char *S, int ri
   *reinterpret_cast<float4 *>(bv) = row_ld4(S, rj, kbase + k);
   *reinterpret_cast<float4 *>(bv + 4) = row_ld4(S, rj, kbase + k + 4);
   if (KIND == KIND_MUL) {
-    *reinterpret_cast<float4 *>(iav) = *reinterpret_cast<const float4 *>(ria + k);
-    *reinterpret_cast<float4 *>(iav + 4) = *reinterpret_cast<const float4 *>(ria + k + 4);
-    *reinterpret_cast<float4 *>(ibv) = *reinterpret_cast<const float4 *>(rib + k);
-    *reinterpret_cast<float4 *>(ibv + 4) = *reinterpret_cast<const float4 *>(rib + k + 4);
+    *reinterpret_cast<float4 *>(iav) = row_ld4(S, RCP_ROW + ri, kbase + k);
+    *reinterpret_cast<float4 *>(iav + 4) = row_ld4(S, RCP_ROW + ri, kbase + k + 4);
+    *reinterpret_cast<float4 *>(ibv) = row_ld4(S, RCP_ROW + rj, kbase + k);
+    *reinterpret_cast<float4 *>(ibv + 4) = row_ld4(S, RCP_ROW + rj, kbase + k + 4);
   }
   float wv[3][8];
 #pragma unroll
@@ -293,22 +315,35 @@ __device__ __forceinline__ void tc_gen8(TcGen &g, const unsigned char *S, int ri
       hi[e >> 1] = *reinterpret_cast<const uint32_t *>(&h);
       lo[e >> 1] = *reinterpret_cast<const uint32_t *>(&l);
     }
-    *reinterpret_cast<uint4 *>(Aop + (2 * sl) * A_TILE + core_off(m, kbase + k)) =
-        make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4 *>(Aop + (2 * sl + 1) * A_TILE + core_off(m, kbase + k)) =
-        make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    if (TA) {
+      // this lane's row: four columns (eight samples) per component
+      const uint32_t col = acol + (uint32_t)sl * KC + (uint32_t)(kbase + k) / 2;
+      tmem_st4(col, hi);
+      tmem_st4(col + KC / 2, lo);
+    } else {
+      *reinterpret_cast<uint4 *>(Aop + (2 * sl) * A_TILE + core_off(m, kbase + k)) =
+          make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4 *>(Aop + (2 * sl + 1) * A_TILE + core_off(m, kbase + k)) =
+          make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
   }
 }
 
 template <int KIND, int NTP>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, const unsigned char *bsplit,
                                                              const __grid_constant__ CUtensorMap rows_map,
+                                                             const __grid_constant__ CUtensorMap rcp_map,
                                                              float gamma_gen, float gamma_num, int gen_blk) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
   Shared &sh = *reinterpret_cast<Shared *>(smem);
   unsigned char *stages = smem + shared_bytes();
   constexpr uint32_t SB = stage_bytes(NTP);
+  constexpr bool TA = tmem_a(NTP);
+  constexpr uint32_t B_OFF = b_off(NTP);
+  constexpr int ACOL = acc_cols(NTP);  // first A column (A in TMEM)
+  constexpr int ACW = acc_w(NTP);      // accumulator columns per slot
+  float *run_sm = reinterpret_cast<float *>(stages + (size_t)NS * SB);
   // the swizzled row boxes need 1024-byte aligned stages (no static shared
   // memory here, so the dynamic window starts aligned); refuse otherwise
   if (smem_u32(stages) & 1023u) {
@@ -318,12 +353,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (A.N + KC - 1) / KC;
   const int nblocks = (nchunks + KB - 1) / KB;
-  constexpr int TMEM_COLS = (6 * NTP <= 32)    ? 32
-                            : (6 * NTP <= 64)  ? 64
-                            : (6 * NTP <= 128) ? 128
-                            : (6 * NTP <= 256) ? 256
-                                               : 512;
-  static_assert(6 * NTP <= 512, "too many targets for the TMEM accumulators");
+  constexpr int COLS = tmem_cols_needed(NTP);
+  constexpr int TMEM_COLS = (COLS <= 32)    ? 32
+                            : (COLS <= 64)  ? 64
+                            : (COLS <= 128) ? 128
+                            : (COLS <= 256) ? 256
+                                            : 512;
+  static_assert(COLS <= 512, "too many targets for the TMEM accumulators");
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -389,7 +425,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
     // ------------------------------------------------------------ producer
     // lane 0: three 2-D tensor copies of the chunk's operand rows (i-rows
     // 0-7, 8-15, j-rows 0-7 at the tile's row positions; rows past the end
-    // and samples past N arrive as zeros) and one bulk copy of its target
+    // and samples past N arrive as zeros), three more of their reciprocal
+    // rows for the products and quotients, and one bulk copy of the target
     // block
     int lt = 0;
     uint32_t issued = 0;  // chunks whose copies were issued
@@ -404,11 +441,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
         }
         unsigned char *S = stages + (size_t)st * SB;
         if (lane == 0) {
-          mbar_arrive_expect_tx(&sh.full_rows[st], 3u * 1024u + b_bytes(NTP));
+          mbar_arrive_expect_tx(&sh.full_rows[st], (KIND == KIND_MUL ? 6u : 3u) * 1024u + b_bytes(NTP));
           const int x = c * KC;
           tma_load_2d(S, &rows_map, x, tl.ibase, &sh.full_rows[st]);
           tma_load_2d(S + 1024, &rows_map, x, tl.ibase + 8, &sh.full_rows[st]);
           tma_load_2d(S + 2048, &rows_map, x, tl.jbase, &sh.full_rows[st]);
+          if (KIND == KIND_MUL) {
+            tma_load_2d(S + 3072, &rcp_map, x, tl.ibase, &sh.full_rows[st]);
+            tma_load_2d(S + 4096, &rcp_map, x, tl.ibase + 8, &sh.full_rows[st]);
+            tma_load_2d(S + 5120, &rcp_map, x, tl.jbase, &sh.full_rows[st]);
+          }
           bulk_g2s(S + B_OFF, bsplit + (size_t)c * b_bytes(NTP), b_bytes(NTP), &sh.full_rows[st]);
         }
         __syncwarp();
@@ -440,17 +482,24 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
             fence_after();
             const uint32_t sbase = smem_u32(stages + (size_t)st * SB);
             const uint32_t bh = sbase + B_OFF, bl = bh + (uint32_t)NTP * KC * 2;
+            constexpr uint32_t IDESC2 = idesc_bf16(M, 2 * NTP);  // wh against [yh; yl]
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-              const uint32_t d = tmem + (buf * 3 + k) * NTP;
+              const uint32_t d = tmem + (buf * 3 + k) * ACW;
               const uint32_t ah = sbase + A_OFF + (2 * k) * A_TILE, al = ah + A_TILE;
+              const uint32_t tah = tmem + ACOL + st * A_STAGE_COLS + k * KC, tal = tah + KC / 2;
 #pragma unroll
               for (int kk = 0; kk < KC / 16; ++kk) {
                 const uint32_t koff = kk * 2 * LBO;
                 const uint32_t acc = (c == b * KB && kk == 0) ? 0u : 1u;
-                mma_bf16(d, smem_desc(ah + koff), smem_desc(bh + koff), IDESC, acc);
-                mma_bf16(d, smem_desc(ah + koff), smem_desc(bl + koff), IDESC, 1u);
-                mma_bf16(d, smem_desc(al + koff), smem_desc(bh + koff), IDESC, 1u);
+                if (TA) {
+                  mma_bf16_ta(d, tah + kk * 8, smem_desc(bh + koff), IDESC2, acc);
+                  mma_bf16_ta(d, tal + kk * 8, smem_desc(bh + koff), IDESC, 1u);
+                } else {
+                  mma_bf16(d, smem_desc(ah + koff), smem_desc(bh + koff), IDESC, acc);
+                  mma_bf16(d, smem_desc(ah + koff), smem_desc(bl + koff), IDESC, 1u);
+                  mma_bf16(d, smem_desc(al + koff), smem_desc(bh + koff), IDESC, 1u);
+                }
               }
             }
             mma_commit(&sh.empty[st]);
@@ -465,12 +514,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
   } else if (warp < 2 + NGEN) {
     // ---------------------------------------------------------- generation
     // warp g = warp - 2 writes rows m = 32 (g & 3) + lane (one pair each)
-    // for samples [16 h, 16 h + 16) of every chunk, h = g >> 2 (all eight
-    // warps work on the same chunk, so each waits only for fills whose
-    // predecessors it consumed itself)
+    // for samples [SPP h, SPP h + SPP) of every chunk, h = g >> 2 (all
+    // generation warps work on the same chunk, so each waits only for fills
+    // whose predecessors it consumed itself)
     const int gw = warp - 2;
-    const int m = (gw & 3) * 32 + lane;  // row = pair
-    const int half = gw >> 2;            // which 16 samples of a chunk
+    // row = pair; the warp's rows are its TMEM lane quadrant (warp % 4), the
+    // lanes its tcgen05 stores may address
+    const int m = (warp & 3) * 32 + lane;
+    const int part = gw >> 2;            // which SPP samples of a chunk
     const int ti = m >> 3, tj = m & 7;
     int lt = 0;
     for (int tile = blockIdx.x; tile < A.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
@@ -501,30 +552,19 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
           ok = false;
           break;
         }
+        // the MMAs that read this stage's A columns before have completed
+        // (their commit released the stage to the producer)
+        if (TA) fence_after();
         unsigned char *S = stages + (size_t)st * SB;
-        const float *ria = nullptr, *rib = nullptr;
-        if (KIND == KIND_MUL) {
-          // the reciprocals this warp needs (6 per lane; the previous chunk's
-          // reads finished at the __syncwarp before its arrive)
-          float(*rw)[RW] = sh.rcpw[gw];
-#pragma unroll
-          for (int t = 0; t < 6; ++t) {
-            const int e = lane + 32 * t, r = e >> 4, k = e & 15;
-            const int src = r < 4 ? (gw & 3) * 4 + r : BI + (r - 4);
-            rw[r][k] = rcp_approx(row_ld1(S, src, half * 16 + k));
-          }
-          __syncwarp();
-          ria = rw[ti - (gw & 3) * 4];
-          rib = rw[4 + tj];
-        }
         unsigned char *Aop = S + A_OFF;
+        const uint32_t acol = tmem + ((uint32_t)((warp & 3) * 32) << 16) + ACOL + st * A_STAGE_COLS;
         if ((c + 1) * KC <= A.N) {
 #pragma unroll
-          for (int q = 0; q < 2; ++q) tc_gen8<KIND, false>(g, S, ti, BI + tj, ria, rib, q * 8, half * 16, 0, Aop, m);
+          for (int q = 0; q < SPP / 8; ++q) tc_gen8<KIND, false, TA>(g, S, ti, BI + tj, q * 8, part * SPP, 0, Aop, acol, m);
         } else {
-          const int lim = A.N - c * KC - half * 16;
+          const int lim = A.N - c * KC - part * SPP;
 #pragma unroll
-          for (int q = 0; q < 2; ++q) tc_gen8<KIND, true>(g, S, ti, BI + tj, ria, rib, q * 8, half * 16, lim, Aop, m);
+          for (int q = 0; q < SPP / 8; ++q) tc_gen8<KIND, true, TA>(g, S, ti, BI + tj, q * 8, part * SPP, lim, Aop, acol, m);
         }
         if (++blk == gen_blk) {
           blk = 0;
@@ -535,18 +575,23 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
             g.t1[k] = g.t2[k] = 0.f;
           }
         }
-        fence_proxy_async();
+        if (TA) {
+          tmem_wait_st();
+          fence_before();
+        } else {
+          fence_proxy_async();
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.full_a[st]);
       }
       if (!ok) break;
-      // hand this half's S1/S2 of the row to the epilogue warps
+      // hand this part's S1/S2 of the row to the epilogue warps
       const int p = lt & 1;
       if (lt >= 2 && !wait_warp(&sh.epi_free[p], ((lt >> 1) - 1) & 1)) break;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        sh.hand[p][half][m][2 * k] = s1[k] + g.t1[k];
-        sh.hand[p][half][m][2 * k + 1] = s2[k] + g.t2[k];
+        sh.hand[p][part][m][2 * k] = s1[k] + g.t1[k];
+        sh.hand[p][part][m][2 * k + 1] = s2[k] + g.t2[k];
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.gen_done[p]);
@@ -583,32 +628,39 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
         kks[2] = fabsf(mi - mj);
       }
       // numerators: one block stays in TMEM until the end; longer sample
-      // ranges are drained block by block into registers
-      float acc[3][NTP <= 32 ? NTP : 1];
-      if (nblocks > 1) {
-        if (NTP <= 32) {
+      // ranges drain each block into a running FP32 sum kept in TMEM
+      // columns [6 NTP, 9 NTP) (added in registers, block by block)
+      if (nblocks > 1 && NTP <= 32) {
+        for (int b = 0; b < nblocks; ++b) {
+          const uint32_t gb = (uint32_t)lt * nblocks + b, buf = gb & 1, ub = gb >> 1;
+          if (!wait_warp_lazy(&sh.acc_full[buf], ub & 1)) break;
+          fence_after();
 #pragma unroll
           for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int t = 0; t < (NTP <= 32 ? NTP : 1); ++t) acc[k][t] = 0.f;
-          for (int b = 0; b < nblocks; ++b) {
-            const uint32_t gb = (uint32_t)lt * nblocks + b, buf = gb & 1, ub = gb >> 1;
-            if (!wait_warp_lazy(&sh.acc_full[buf], ub & 1)) break;
-            fence_after();
+            for (int c16 = 0; c16 < NTP; c16 += 16) {
+              float v[16], r[16];
+              tmem_ld16(tmem + lane_base + (buf * 3 + k) * ACW + c16, v);
+              if (TA) {
+                tmem_ld16(tmem + lane_base + (buf * 3 + k) * ACW + NTP + c16, r);
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
+                for (int i = 0; i < 16; ++i) v[i] = v[i] + r[i];
+                float *rs = run_sm + m * RUN_W + k * NTP + c16;
 #pragma unroll
-              for (int c16 = 0; c16 < (NTP <= 32 ? NTP : 16); c16 += 16) {
-                float v[16];
-                tmem_ld16(tmem + lane_base + (buf * 3 + k) * NTP + c16, v);
+                for (int i = 0; i < 16; ++i) rs[i] = b > 0 ? rs[i] + v[i] : v[i];
+              } else {
+                const uint32_t run = tmem + lane_base + (6 + k) * NTP + c16;
+                if (b > 0) {
+                  tmem_ld16(run, r);
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                  if (c16 + i < (NTP <= 32 ? NTP : 1)) acc[k][c16 + i] += v[i];
+                  for (int i = 0; i < 16; ++i) v[i] = r[i] + v[i];
+                }
+                tmem_st16(run, v);
               }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
-          }
+            }
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.acc_empty[buf]);
         }
       }
       const uint32_t gb_last = (uint32_t)lt * nblocks + (nblocks - 1), buf_last = gb_last & 1;
@@ -626,7 +678,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       __syncwarp();
       float st12[6];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) st12[i] = sh.hand[p][0][m][i] + sh.hand[p][1][m][i];
+      for (int i = 0; i < 6; ++i) {
+        float v = sh.hand[p][0][m][i];
+#pragma unroll
+        for (int h = 1; h < NPART; ++h) v += sh.hand[p][h][m][i];
+        st12[i] = v;
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.epi_free[p]);
       uint64_t pushed = 0;
@@ -640,10 +697,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
         for (int c16 = 0; c16 < NTP; c16 += 16) {
           float v[16];
           if (nblocks == 1) {
-            tmem_ld16(tmem + lane_base + (buf_last * 3 + k) * NTP + c16, v);  // whole warp
-          } else {
+            tmem_ld16(tmem + lane_base + (buf_last * 3 + k) * ACW + c16, v);  // whole warp
+            if (TA) {
+              float r[16];
+              tmem_ld16(tmem + lane_base + (buf_last * 3 + k) * ACW + NTP + c16, r);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = NTP <= 32 ? acc[k][(c16 + i) % (NTP <= 32 ? NTP : 1)] : 0.f;
+              for (int i = 0; i < 16; ++i) v[i] = v[i] + r[i];
+            }
+          } else if (TA) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = run_sm[m * RUN_W + k * NTP + c16 + i];
+          } else {
+            tmem_ld16(tmem + lane_base + (6 + k) * NTP + c16, v);
           }
           if (tcc.ok) pushed |= tc_targets16(A, tcc, v, c16, gamma_gen, gamma_num, sh.ysum[q], sh.theta[q], sh.sy[q]);
         }
@@ -712,8 +777,9 @@ static dse_status rows_tensor_map(const float *base, int64_t nrows, int64_t N, i
 
 template <int KIND, int NTP>
 static dse_status launch_tc_t(const ScreenArgs &A, const unsigned char *bsplit, const CUtensorMap &map,
-                              float gamma_gen, float gamma_num, int gen_blk, int sms, cudaStream_t st) {
-  const size_t smem = tc::shared_bytes() + (size_t)tc::NS * tc::stage_bytes(NTP);
+                              const CUtensorMap &rmap, float gamma_gen, float gamma_num, int gen_blk, int sms,
+                              cudaStream_t st) {
+  const size_t smem = tc::shared_bytes() + (size_t)tc::NS * tc::stage_bytes(NTP) + tc::run_bytes(NTP);
   static bool attr[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -726,8 +792,23 @@ static dse_status launch_tc_t(const ScreenArgs &A, const unsigned char *bsplit, 
   note_launches(1);
   ScreenArgs B = A;
   B.group = KIND == KIND_MUL ? 1 : 2;
-  k_pair_tc<KIND, NTP><<<grid, tc::THREADS, smem, st>>>(B, bsplit, map, gamma_gen, gamma_num, gen_blk);
+  k_pair_tc<KIND, NTP><<<grid, tc::THREADS, smem, st>>>(B, bsplit, map, rmap, gamma_gen, gamma_num, gen_blk);
   return DSE_OK;
+}
+
+// Reciprocal rows of the stored FP32 rows (the rcp.approx the error model
+// assumes), read by the product/quotient kernel next to the rows.
+__global__ void k_rcp_rows(const float *v32, int64_t count, float *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = rcp_approx(v32[e]);
+}
+
+void launch_rcp_rows(const float *v32, int64_t count, float *out, int sms, cudaStream_t st) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  if (blocks < 1) return;
+  note_launches(1);
+  k_rcp_rows<<<(unsigned)blocks, 256, 0, st>>>(v32, count, out);
 }
 
 // Rows in the order of a row list (the unit-class order of the additive
@@ -747,6 +828,11 @@ void launch_gather_rows(const float *v32, int64_t ld, const int32_t *rows, int64
   note_launches(1);
   k_gather_rows<<<(unsigned)blocks, 256, 0, st>>>(v32, ld, rows, n, out);
 }
+
+// Samples of each chunk one generation thread sums (the blocked FP32 sums
+// inner length per chunk) and the number of partial sums per row.
+int tc_gen_samples() { return tc::SPP; }
+int tc_gen_parts() { return tc::NPART; }
 
 int tc_ntp_for(int T, int N) {
   // one accumulation block keeps every target in TMEM; longer sample ranges
@@ -773,18 +859,25 @@ void launch_tc_targets(const float *y32, int32_t ldy, int t0, int T, int N, int 
 }
 
 dse_status launch_pair_tc(int kind, int ntp, const ScreenArgs &A, const unsigned char *bsplit, const float *rows,
-                          int64_t nrows, float gamma_gen, float gamma_num, int gen_blk, int sms, cudaStream_t st) {
+                          const float *rcp_rows, int64_t nrows, float gamma_gen, float gamma_num, int gen_blk, int sms,
+                          cudaStream_t st) {
   if (A.n_tiles <= 0) return DSE_OK;
-  CUtensorMap map;
+  if (kind == KIND_MUL && !rcp_rows) {
+    set_error("reciprocal rows missing");
+    return DSE_EINVAL;
+  }
+  CUtensorMap map, rmap;
   DSE_TRY(rows_tensor_map(rows, nrows, A.N, A.F.ld, &map));
+  DSE_TRY(rows_tensor_map(kind == KIND_MUL ? rcp_rows : rows, nrows, A.N, A.F.ld, &rmap));
   if (ntp > 32 && (A.N + tc::KC - 1) / tc::KC > tc::KB) {
     set_error("target block %d needs N <= %d samples", ntp, tc::KB * tc::KC);
     return DSE_EINVAL;
   }
 #define DSE_TC_CASE(NTPV)                                                                                   \
   case NTPV:                                                                                                \
-    return kind == KIND_MUL ? launch_tc_t<KIND_MUL, NTPV>(A, bsplit, map, gamma_gen, gamma_num, gen_blk, sms, st) \
-                            : launch_tc_t<KIND_ADD, NTPV>(A, bsplit, map, gamma_gen, gamma_num, gen_blk, sms, st);
+    return kind == KIND_MUL                                                                                  \
+               ? launch_tc_t<KIND_MUL, NTPV>(A, bsplit, map, rmap, gamma_gen, gamma_num, gen_blk, sms, st)         \
+               : launch_tc_t<KIND_ADD, NTPV>(A, bsplit, map, rmap, gamma_gen, gamma_num, gen_blk, sms, st);
   switch (ntp) {
     DSE_TC_CASE(16)
     DSE_TC_CASE(32)
