@@ -20,12 +20,12 @@
 //                 3 slots x 2 k-steps x 3 products per chunk; tcgen05.commit to
 //                 the stage's "empty" barrier and, after the last chunk of an
 //                 accumulation block, to the accumulator's "full" barrier;
-//   warps 2-17    generation: row m (a pair) x one quarter of each chunk's samples:
+//   warps 2-9     generation: row m (a pair) x one half of each chunk's samples:
 //                 candidate values (quotients from reciprocal rows copied
 //                 next to the value rows), FP32 S1/S2, BF16 hi/lo split,
 //                 16-byte stores into the canonical K-major layout (8x8 core
 //                 matrices, no swizzle), proxy fence, arrive;
-//   warps 18-21   epilogue: tcgen05.ld of TMEM lane quadrant (warp % 4),
+//   warps 10-13   epilogue: tcgen05.ld of TMEM lane quadrant (warp % 4),
 //                 block accumulation, scores, error bounds, threshold pushes.
 // Accumulators are double-buffered in TMEM by accumulation block (up to 16
 // chunks = 512 samples), so the epilogue of one block overlaps the MMAs of
@@ -57,9 +57,10 @@ namespace tc {
 
 constexpr int M = 128;  // pairs per tile
 constexpr int BI = 16, BJ = 8, ROWS = BI + BJ;
-constexpr int NS = 3;     // stages
+constexpr int NS = 3;     // stages of the A operands (and, with A in shared memory, of everything)
+constexpr int NR_MAX = 6;  // stages of the operand rows and target blocks with A in TMEM
 constexpr int KB = 16;    // chunks per accumulation block (512 samples)
-constexpr int NGEN = 16;  // generation warps: four per row quadrant, one per quarter of a chunk
+constexpr int NGEN = 8;   // generation warps: two per row quadrant, one per half of a chunk
 constexpr int NPART = NGEN / 4;  // parts of a chunk's samples
 constexpr int SPP = 32 / NPART;  // samples per part (a multiple of 8)
 constexpr int WARPS = 2 + NGEN + 4;
@@ -105,13 +106,31 @@ __host__ __device__ constexpr int tmem_cols_needed(int ntp) {
   return acc_cols(ntp) + (tmem_a(ntp) ? NS * A_STAGE_COLS : 0);
 }
 
-// Samples s .. s+3 (s a multiple of 4) of swizzled row r.
-__device__ __forceinline__ float4 row_ld4(const unsigned char *S, int r, int s) {
-  return *reinterpret_cast<const float4 *>(S + r * 128 + ((((s >> 2) ^ (r & 7))) << 4));
+// Byte offset of samples s .. s+3 (s a multiple of 4) of swizzled row r.
+__host__ __device__ constexpr uint32_t row_off(int r, int s) {
+  return (uint32_t)(r * 128 + ((((s >> 2) ^ (r & 7))) << 4));
+}
+
+// Offsets of the eight samples s .. s+7 a generation thread reads from each
+// of its four rows (value rows ri, rj and their reciprocals); the same in
+// every stage, so computed once.
+struct GenAddr {
+  uint32_t a[2], b[2], ia[2], ib[2];
+};
+__device__ __forceinline__ GenAddr gen_addr(int ri, int rj, int s) {
+  GenAddr g;
+  for (int h = 0; h < 2; ++h) {
+    g.a[h] = row_off(ri, s + 4 * h);
+    g.b[h] = row_off(rj, s + 4 * h);
+    g.ia[h] = row_off(RCP_ROW + ri, s + 4 * h);
+    g.ib[h] = row_off(RCP_ROW + rj, s + 4 * h);
+  }
+  return g;
 }
 
 struct Shared {
-  uint64_t full_rows[NS], full_a[NS], empty[NS];
+  uint64_t full_rows[NR_MAX], empty[NR_MAX];  // row stages: copies landed / MMAs done with them
+  uint64_t full_a[NS], empty_a[NS];           // A stages: generated / MMAs done (A in TMEM)
   uint64_t acc_full[2], acc_empty[2], gen_done[2], epi_free[2];
   uint64_t drain;  // last tcgen05.commit of the MMA issuer, before TMEM is freed
   uint32_t tmem_base;
@@ -267,19 +286,18 @@ struct TcGen {
 // stores into the canonical K-major layout of the A tiles.  CHECK: entries at
 // or beyond `lim` are zero (the last, partial chunk).
 template <int KIND, bool CHECK, bool TA>
-__device__ __forceinline__ void tc_gen8(TcGen &g, const unsigned char *S, int ri, int rj, int k, int kbase, int lim,
+__device__ __forceinline__ void tc_gen8(TcGen &g, const unsigned char *S, const tc::GenAddr &ad, int k, int kbase, int lim,
                                         unsigned char *Aop, uint32_t acol, int m) {
   using namespace tc;
   float av[8], bv[8], iav[8], ibv[8];
-  *reinterpret_cast<float4 *>(av) = row_ld4(S, ri, kbase + k);
-  *reinterpret_cast<float4 *>(av + 4) = row_ld4(S, ri, kbase + k + 4);
-  *reinterpret_cast<float4 *>(bv) = row_ld4(S, rj, kbase + k);
-  *reinterpret_cast<float4 *>(bv + 4) = row_ld4(S, rj, kbase + k + 4);
-  if (KIND == KIND_MUL) {
-    *reinterpret_cast<float4 *>(iav) = row_ld4(S, RCP_ROW + ri, kbase + k);
-    *reinterpret_cast<float4 *>(iav + 4) = row_ld4(S, RCP_ROW + ri, kbase + k + 4);
-    *reinterpret_cast<float4 *>(ibv) = row_ld4(S, RCP_ROW + rj, kbase + k);
-    *reinterpret_cast<float4 *>(ibv + 4) = row_ld4(S, RCP_ROW + rj, kbase + k + 4);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    *reinterpret_cast<float4 *>(av + 4 * h) = *reinterpret_cast<const float4 *>(S + ad.a[h]);
+    *reinterpret_cast<float4 *>(bv + 4 * h) = *reinterpret_cast<const float4 *>(S + ad.b[h]);
+    if (KIND == KIND_MUL) {
+      *reinterpret_cast<float4 *>(iav + 4 * h) = *reinterpret_cast<const float4 *>(S + ad.ia[h]);
+      *reinterpret_cast<float4 *>(ibv + 4 * h) = *reinterpret_cast<const float4 *>(S + ad.ib[h]);
+    }
   }
   float wv[3][8];
 #pragma unroll
@@ -340,10 +358,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
   unsigned char *stages = smem + shared_bytes();
   constexpr uint32_t SB = stage_bytes(NTP);
   constexpr bool TA = tmem_a(NTP);
+  // row stages: with A in TMEM they are small and outnumber the A stages, so
+  // the copies run further ahead; otherwise rows and A share the NS stages
+  constexpr int NR = TA ? NR_MAX : NS;
   constexpr uint32_t B_OFF = b_off(NTP);
   constexpr int ACOL = acc_cols(NTP);  // first A column (A in TMEM)
   constexpr int ACW = acc_w(NTP);      // accumulator columns per slot
-  float *run_sm = reinterpret_cast<float *>(stages + (size_t)NS * SB);
+  float *run_sm = reinterpret_cast<float *>(stages + (size_t)NR * SB);
   // the swizzled row boxes need 1024-byte aligned stages (no static shared
   // memory here, so the dynamic window starts aligned); refuse otherwise
   if (smem_u32(stages) & 1023u) {
@@ -362,10 +383,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
   static_assert(COLS <= 512, "too many targets for the TMEM accumulators");
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < NR; ++s) {
       mbar_init(&sh.full_rows[s], 1);
-      mbar_init(&sh.full_a[s], NGEN);
       mbar_init(&sh.empty[s], 1);
+    }
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&sh.full_a[s], NGEN);
+      mbar_init(&sh.empty_a[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.acc_full[b], 1);
@@ -434,7 +458,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       const Tile tl = A.tiles[tile];
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
-        const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
+        const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NR, u = gc / NR;
         if (u >= 1 && !wait_warp(&sh.empty[st], (u - 1) & 1)) {
           ok = false;
           break;
@@ -461,9 +485,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
     // no copy may still be landing when the CTA exits (normally these
     // phases completed long ago and the waits return at once)
     if (lane == 0)
-      for (uint32_t st = 0; st < (uint32_t)NS && st < issued; ++st) {
-        const uint32_t last = (issued - 1 - st) / NS * NS + st;  // last use of stage st
-        mbar_wait_bounded(&sh.full_rows[st], (last / NS) & 1, kWait);
+      for (uint32_t st = 0; st < (uint32_t)NR && st < issued; ++st) {
+        const uint32_t last = (issued - 1 - st) / NR * NR + st;  // last use of stage st
+        mbar_wait_bounded(&sh.full_rows[st], (last / NR) & 1, kWait);
       }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
@@ -477,8 +501,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
           fence_after();
           const int c_end = min(nchunks, (b + 1) * KB);
           for (int c = b * KB; c < c_end; ++c) {
-            const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
-            if (!wait(&sh.full_rows[st], u & 1) || !wait(&sh.full_a[st], u & 1)) break;
+            const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NR, u = gc / NR;
+            const uint32_t sa = gc % NS, ua = gc / NS;
+            if (!wait(&sh.full_rows[st], u & 1) || !wait(&sh.full_a[sa], ua & 1)) break;
             fence_after();
             const uint32_t sbase = smem_u32(stages + (size_t)st * SB);
             const uint32_t bh = sbase + B_OFF, bl = bh + (uint32_t)NTP * KC * 2;
@@ -487,7 +512,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
             for (int k = 0; k < 3; ++k) {
               const uint32_t d = tmem + (buf * 3 + k) * ACW;
               const uint32_t ah = sbase + A_OFF + (2 * k) * A_TILE, al = ah + A_TILE;
-              const uint32_t tah = tmem + ACOL + st * A_STAGE_COLS + k * KC, tal = tah + KC / 2;
+              const uint32_t tah = tmem + ACOL + sa * A_STAGE_COLS + k * KC, tal = tah + KC / 2;
 #pragma unroll
               for (int kk = 0; kk < KC / 16; ++kk) {
                 const uint32_t koff = kk * 2 * LBO;
@@ -503,6 +528,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
               }
             }
             mma_commit(&sh.empty[st]);
+            if (TA) mma_commit(&sh.empty_a[sa]);
             if (c == c_end - 1) mma_commit(&sh.acc_full[buf]);
           }
         }
@@ -522,6 +548,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
     // lanes its tcgen05 stores may address
     const int m = (warp & 3) * 32 + lane;
     const int part = gw >> 2;            // which SPP samples of a chunk
+    static_assert(SPP == 8 || SPP == 16, "one or two eight-sample steps per chunk and thread");
+    const GenAddr gad = gen_addr(m >> 3, BI + (m & 7), part * SPP);
+    const GenAddr gad2 = gen_addr(m >> 3, BI + (m & 7), part * SPP + (SPP - 8));
     const int ti = m >> 3, tj = m & 7;
     int lt = 0;
     for (int tile = blockIdx.x; tile < A.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
@@ -547,24 +576,25 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
       int blk = 0;
       bool ok = true;
       for (int c = 0; c < nchunks; ++c) {
-        const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
-        if (!wait_warp(&sh.full_rows[st], u & 1)) {
+        const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NR, u = gc / NR;
+        const uint32_t sa = gc % NS, ua = gc / NS;
+        // with A in TMEM: the MMAs that read this A stage before (chunk
+        // gc - NS, which these warps generated) have completed
+        if (!wait_warp(&sh.full_rows[st], u & 1) || (TA && ua >= 1 && !wait_warp(&sh.empty_a[sa], (ua - 1) & 1))) {
           ok = false;
           break;
         }
-        // the MMAs that read this stage's A columns before have completed
-        // (their commit released the stage to the producer)
         if (TA) fence_after();
         unsigned char *S = stages + (size_t)st * SB;
         unsigned char *Aop = S + A_OFF;
-        const uint32_t acol = tmem + ((uint32_t)((warp & 3) * 32) << 16) + ACOL + st * A_STAGE_COLS;
+        const uint32_t acol = tmem + ((uint32_t)((warp & 3) * 32) << 16) + ACOL + sa * A_STAGE_COLS;
         if ((c + 1) * KC <= A.N) {
-#pragma unroll
-          for (int q = 0; q < SPP / 8; ++q) tc_gen8<KIND, false, TA>(g, S, ti, BI + tj, q * 8, part * SPP, 0, Aop, acol, m);
+          tc_gen8<KIND, false, TA>(g, S, gad, 0, part * SPP, 0, Aop, acol, m);
+          if (SPP == 16) tc_gen8<KIND, false, TA>(g, S, gad2, 8, part * SPP, 0, Aop, acol, m);
         } else {
           const int lim = A.N - c * KC - part * SPP;
-#pragma unroll
-          for (int q = 0; q < SPP / 8; ++q) tc_gen8<KIND, true, TA>(g, S, ti, BI + tj, q * 8, part * SPP, lim, Aop, acol, m);
+          tc_gen8<KIND, true, TA>(g, S, gad, 0, part * SPP, lim, Aop, acol, m);
+          if (SPP == 16) tc_gen8<KIND, true, TA>(g, S, gad2, 8, part * SPP, lim, Aop, acol, m);
         }
         if (++blk == gen_blk) {
           blk = 0;
@@ -582,7 +612,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_pair_tc(const ScreenArgs A, 
           fence_proxy_async();
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.full_a[st]);
+        if (lane == 0) mbar_arrive(&sh.full_a[sa]);
       }
       if (!ok) break;
       // hand this part's S1/S2 of the row to the epilogue warps
@@ -779,7 +809,8 @@ template <int KIND, int NTP>
 static dse_status launch_tc_t(const ScreenArgs &A, const unsigned char *bsplit, const CUtensorMap &map,
                               const CUtensorMap &rmap, float gamma_gen, float gamma_num, int gen_blk, int sms,
                               cudaStream_t st) {
-  const size_t smem = tc::shared_bytes() + (size_t)tc::NS * tc::stage_bytes(NTP) + tc::run_bytes(NTP);
+  const size_t smem = tc::shared_bytes() + (size_t)(tc::tmem_a(NTP) ? tc::NR_MAX : tc::NS) * tc::stage_bytes(NTP) +
+                      tc::run_bytes(NTP);
   static bool attr[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
