@@ -203,6 +203,14 @@ typedef struct {
      and of the domain, magnitude and realised tests, the same decisions the
      reasons counts of dse_stats sum up.  Not a device pointer: DSE_EINVAL. */
   int8_t *reasons;
+  /* Optional DEVICE buffer of 2 x n_lists x (id_end - id_begin) floats, or
+     NULL: for each candidate of the range (id order) and each list, the
+     score s and error bound eps that the screening kernels computed for it
+     before any re-score (the FP32 or tensor-core interval, or the FP64
+     value of an escalated candidate), as (s, eps) pairs; NaN where a
+     candidate has none (excluded by a test).  For checking the error bounds
+     candidate by candidate.  Not a device pointer: DSE_EINVAL. */
+  float *intervals;
 } dse_screen_desc;
 
 /* dse_screen_desc.flags: record CUDA events around each kernel group so that

@@ -290,6 +290,8 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
       A.B.count, A.B.hist, A.B.hist_hi, A.B.hist_c, nl, A.esc_count, A.stats, S.n_jobs);
   // per-candidate reasons: -1 until a kernel decides the candidate
   if (A.why) DSE_CUDA(cudaMemsetAsync(A.why, 0xff, (size_t)(A.id_end - A.id_begin), st));
+  // intervals: NaN (all bits set) until a kernel writes one
+  if (A.ivl) DSE_CUDA(cudaMemsetAsync(A.ivl, 0xff, sizeof(float2) * (size_t)(A.id_end - A.id_begin) * nl, st));
   // optional device timing of each kernel group
   const bool timing = (R->flags & (DSE_FLAG_TIMING | DSE_FLAG_TIMING_MAIN)) != 0;
   const bool main_only = !(R->flags & DSE_FLAG_TIMING);
@@ -396,8 +398,8 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
               (unsigned long long)id_end, (unsigned long long)total);
     return DSE_ERANGE;
   }
-  if (d->reasons && !is_device_pointer(d->reasons)) {
-    set_error("the reasons buffer must be device memory");
+  if ((d->reasons && !is_device_pointer(d->reasons)) || (d->intervals && !is_device_pointer(d->intervals))) {
+    set_error("the reasons and intervals buffers must be device memory");
     return DSE_EINVAL;
   }
   int prec = d->precision;
@@ -622,6 +624,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   if (!e) e = cudaMemsetAsync(A.B.theta, 0, sizeof(float) * n_lists, st);
   if (e) return fail(cuda_status(e, "screen setup"));
   A.why = d->reasons;
+  A.ivl = reinterpret_cast<float2 *>(d->intervals);
   if (launch) launch_targets(Ysrc, d->ld_y, (int)T, N, R->ldy, R->y64, R->y32, R->ydf, R->ysum32, R->err, st);
   R->launches = launch ? 1 : 0;
   R->flags = d->flags;

@@ -213,6 +213,7 @@ struct ScreenArgs {
   int32_t prob;
   uint32_t *esc_prob;          // escalation list: problem of each entry (batched only)
   int8_t *why;                 // optional: reason code of each id of [id_begin, id_end) (device)
+  float2 *ivl;                 // optional: (s, eps) of each id of the range and list, before re-scores
 };
 
 // Launch bookkeeping (process-wide count of the library's kernel launches).

@@ -143,6 +143,7 @@ __device__ __forceinline__ unsigned score_and_push(const ScreenArgs &A, bool wan
     float sf = (float)s;
     float ef = (float)e + fabsf((float)(s - (R)sf)) + 1e-30f;
     ef = ef * (1.0f + 2.4e-7f);
+    if (want) note_ivl(A, gid, 0, sf, ef);
     if (push_warp(A.B, 0, want, gid, sf, ef)) pushed |= 1u;
     if (__any_sync(0xffffffffu, pushed)) pushed = 1u;
     return pushed;
@@ -154,6 +155,7 @@ __device__ __forceinline__ unsigned score_and_push(const ScreenArgs &A, bool wan
     float sf = (float)s;
     float ef = (float)e + fabsf((float)(s - (R)sf));
     ef = ef * (1.0f + 2.4e-7f);
+    if (w) note_ivl(A, gid, A.t0 + t, sf, ef);
     if (__any_sync(0xffffffffu, w)) {
       bool p = push_warp(A.B, A.t0 + t, w, gid, sf, ef);
       if (__any_sync(0xffffffffu, p)) pushed |= 1u << t;
@@ -1088,6 +1090,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const Sc
           } else {
             const float sf = (float)sc;
             const float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+            note_ivl(A, gid, A.t0 + t0 + t, sf, ef);
             push_one(A.B, A.t0 + t0 + t, gid, sf, ef);
           }
         }
@@ -1097,6 +1100,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const Sc
       const double sc = sqrt(agg / (double)A.T);
       const float sf = (float)sc;
       const float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+      note_ivl(A, gid, A.t0, sf, ef);
       push_one(A.B, A.t0, gid, sf, ef);
     }
   }
@@ -1162,6 +1166,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
         const double sc = fabs(st[4] - dm * st[5]) / sqrt(sxx);
         const float sf = (float)sc;
         const float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+        note_ivl(A, gid, A.t0, sf, ef);
         push_one(A.B, A.t0, gid, sf, ef);
       }
     }

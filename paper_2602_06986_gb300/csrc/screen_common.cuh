@@ -181,6 +181,11 @@ __device__ __forceinline__ void note_why(const ScreenArgs &A, uint64_t gid, int 
   if (A.why && A.first_pass) A.why[gid - A.id_begin] = (int8_t)reason;
 }
 
+// Record the score interval a kernel computed for candidate gid in list l.
+__device__ __forceinline__ void note_ivl(const ScreenArgs &A, uint64_t gid, int l, float s, float e) {
+  if (A.ivl) A.ivl[(gid - A.id_begin) * (uint64_t)A.n_lists + (uint64_t)l] = make_float2(s, e);
+}
+
 // ----------------------------------------------------- per-lane statistics
 
 struct LaneStats {

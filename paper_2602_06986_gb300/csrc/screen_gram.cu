@@ -705,6 +705,7 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
                   want = true;
                   s = gc.s;
                   eps = gc.eps * (1.0f + 2.4e-7f);
+                  note_ivl(A, gid, A.t0, s, eps);
                 }
               }
             }

@@ -244,6 +244,17 @@ __device__ __forceinline__ uint64_t tc_targets16(const ScreenArgs &A, const TcCa
   const float u = 5.9604644775390625e-8f;
   const float invN = (float)A.invN;
   const int lane = threadIdx.x & 31;
+  if (A.ivl) {
+    // every target's interval, for checking the error model
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int t = t0 + i;
+      if (t >= A.T) continue;
+      float s, e;
+      cand_score_num<float>(c.ci, c.S1, Sy[i], invN, ysum[t], gamma_gen, gamma_num, u, &s, &e);
+      note_ivl(A, c.gid, A.t0 + t, s, e * (1.0f + 2.4e-7f));
+    }
+  }
   unsigned mask = 0;
 #pragma unroll
   for (int i = 0; i < 16; ++i) {

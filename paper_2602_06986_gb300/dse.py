@@ -43,7 +43,7 @@ class ScreenDesc(C.Structure):
     _fields_ = [("Y", C.c_void_p), ("ld_y", C.c_int64), ("y_on_device", C.c_int32), ("n_targets", C.c_int32),
                 ("k", C.c_int64), ("mode", C.c_int32), ("precision", C.c_int32), ("id_begin", C.c_uint64),
                 ("id_end", C.c_uint64), ("stream", C.c_void_p), ("flags", C.c_int32), ("reserved0", C.c_int32),
-                ("dedup_tau", C.c_double), ("reasons", C.c_void_p)]
+                ("dedup_tau", C.c_double), ("reasons", C.c_void_p), ("intervals", C.c_void_p)]
 
 
 FLAG_TIMING = 1
@@ -360,11 +360,14 @@ class Space:
         return units[:, : self.n_dims], ok
 
     def screen(self, Y, k, mode=MODE_PER_TARGET, precision=PREC_FP32, id_begin=0, id_end=0, stream=None,
-               flags=0, dedup_tau=None, reasons=None) -> Result:
+               flags=0, dedup_tau=None, reasons=None, intervals=None) -> Result:
         """SIS screen (dse_sis_screen).  With ``dedup_tau`` (0 < tau < 0.5) the
         lists hold the top-k of the non-redundant candidates (DSE_FLAG_DEDUP).
         ``reasons``: optional torch int8 CUDA tensor of id_end - id_begin
-        entries that receives the reason code of every screened candidate."""
+        entries that receives the reason code of every screened candidate.
+        ``intervals``: optional torch float32 CUDA tensor of
+        (id_end - id_begin) x n_lists x 2 entries that receives each
+        candidate's pre-re-score (score, bound) per list (NaN where none)."""
         if dedup_tau is not None:
             flags |= FLAG_DEDUP
         if isinstance(Y, np.ndarray):
@@ -379,8 +382,13 @@ class Space:
             pw, wdev = _ptr(reasons)
             if not wdev:
                 raise ValueError("reasons must be a CUDA tensor")
+        pv = None
+        if intervals is not None:
+            pv, vdev = _ptr(intervals)
+            if not vdev:
+                raise ValueError("intervals must be a CUDA tensor")
         d = ScreenDesc(py, ldy, ydev, T, k, mode, precision, id_begin, id_end, stream, flags, 0,
-                       dedup_tau if dedup_tau is not None else 0.0, pw)
+                       dedup_tau if dedup_tau is not None else 0.0, pw, pv)
         h = C.c_void_p()
         _check(lib().dse_sis_screen(self._h, C.byref(d), C.byref(h)))
         return Result(h, 1 if mode == MODE_AGGREGATED else T, k)

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(dse):
 def test_struct_layouts_match_header(dse):
     # sizes implied by the header's field lists (LP64)
     assert C.sizeof(dse.SpaceDesc) == 8 * 2 + 4 * 2 + 8 + 8 + 4 * 2 + 8 + 8 + 4 * 4 + 8 * 2 + 8 + 8 * 2
-    assert C.sizeof(dse.ScreenDesc) == 8 + 8 + 4 * 2 + 8 + 4 * 2 + 8 * 2 + 8 + 4 * 2 + 8 + 8
+    assert C.sizeof(dse.ScreenDesc) == 8 + 8 + 4 * 2 + 8 + 4 * 2 + 8 * 2 + 8 + 4 * 2 + 8 + 8 + 8
     assert C.sizeof(dse.Stats) == 8 + 8 * 6 + 8 * 4 + 4 * 2 + 8 + 8 * 3 + 8 * 4 + 8 + 8 + 4 * 2
     assert C.sizeof(dse.Expr) == 4 * 2 + 8 * 2
     assert C.sizeof(dse.RefitDesc) == 8 + 4 * 2 + 8 + 8 + 8 + 4 * 2 + 8
