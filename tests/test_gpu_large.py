@@ -4,9 +4,12 @@
   * exact parity (sets, scores, counts) on id sub-ranges the oracle finishes;
   * at full size, every returned (id, score) re-scored by the oracle: within
     1e-5 relative and within the reported bound, valid, in order;
-  * completeness on a random sample of ids: any sampled candidate whose oracle
-    score beats a list's k-th returned score by more than the tie band must
-    be in that list.
+  * completeness on contiguous slices of the screened range that the oracle
+    screens exactly: any candidate of a slice whose oracle score beats a
+    list's k-th returned score by more than the tie band must be in that
+    list.  The slices are where the lists' members are densest (plus, for the
+    large workload, a seeded one), so that each list has many such
+    candidates to lose.
 """
 import numpy as np
 import pytest
@@ -38,12 +41,12 @@ def _spaces(env, w):
     return sp, orc
 
 
-def _check_full_size(res, orc, Y, lists, k, sample_ids, precision_name):
-    """Re-score every returned entry and check completeness on a sample."""
-    T = Y.shape[0]
-    samp_sc, samp_why = orc.score_ids(Y, sample_ids)
-    for l in range(lists):
-        ids, sc, eb = res.fetch(l)
+def _check_full_size(res, orc, Y, lists, k, slices, k_slice, precision_name):
+    """Re-score every returned entry; completeness on the oracle's exact
+    screens of the given id slices.  Returns the number of (slice candidate,
+    list) pairs above a list's k-th score that were checked."""
+    fetched = [res.fetch(l) for l in range(lists)]
+    for l, (ids, sc, eb) in enumerate(fetched):
         assert len(ids) == k, (precision_name, l, len(ids))
         ref, why = orc.score_ids(Y[l:l + 1], ids)
         assert np.all(why == 0)
@@ -51,11 +54,26 @@ def _check_full_size(res, orc, Y, lists, k, sample_ids, precision_name):
         assert np.all(err <= TOL * ref[:, 0] + 1e-12), (precision_name, l, np.max(err / ref[:, 0]))
         assert np.all(err <= eb + 1e-12)
         assert np.all(np.diff(sc) <= 0)
-        sk = sc[-1]
-        valid = samp_why == 0
-        beat = sample_ids[valid][samp_sc[valid, l] > sk * (1 + TOL)]
-        missing = set(int(x) for x in beat) - set(int(x) for x in ids)
-        assert not missing, (precision_name, l, sorted(missing)[:5])
+    checked = 0
+    for a, b in slices:
+        oids, osc, _ = orc.screen(Y, k_slice, id_begin=a, id_end=b)
+        for l, (ids, sc, eb) in enumerate(fetched):
+            sk = sc[-1]
+            beat = oids[l][osc[l] > sk * (1 + TOL)]
+            assert len(beat) < k_slice, "slice list too short to hold every candidate above the k-th score"
+            missing = set(int(x) for x in beat) - set(int(x) for x in ids)
+            assert not missing, (precision_name, l, (a, b), sorted(missing)[:5])
+            checked += len(beat)
+    return checked
+
+
+def _dense_slices(res, lists, begin, end, width, count):
+    """The `count` id slices of `width` (aligned to begin) holding the most
+    list members."""
+    allids = np.concatenate([res.fetch(l)[0] for l in range(lists)]).astype(np.int64) - begin
+    bins = np.bincount(allids // width)
+    top = np.argsort(-bins)[:count]
+    return [(begin + int(t) * width, min(begin + (int(t) + 1) * width, end)) for t in sorted(top)]
 
 
 def test_precision_subblock_exact(env):
@@ -90,9 +108,9 @@ def test_precision_block_full(env):
     res = sp.screen(torch.from_numpy(w["Y"]).cuda(), w["k"], id_begin=b0, id_end=b1)
     st = res.stats()
     assert st["screened"] == b1 - b0
-    rng = np.random.default_rng(1)
-    sample = rng.integers(b0, b1, size=40000).astype(np.uint64)
-    _check_full_size(res, orc, w["Y"], 64, w["k"], sample, "fp32")
+    slices = _dense_slices(res, 64, b0, b1, 1 << 20, 3)
+    checked = _check_full_size(res, orc, w["Y"], 64, w["k"], slices, 3000, "fp32")
+    assert checked >= 20 * 64, checked
 
 
 def test_large_subrange_exact(env):
@@ -112,11 +130,31 @@ def test_large_subrange_exact(env):
 
 
 def test_large_full(env):
-    """The full large workload: N=20000, 16 targets, top-10000 per target."""
+    """The full large workload: N=20000, 16 targets, top-10000 per target,
+    on the CUDA-core FP32 kernels and on the tensor-core path (the bench's
+    default), each checked against the same exact oracle slices."""
     torch, oracle, dse, W = env
     w = W.large(0, n_targets=16)
     sp, orc = _spaces(env, w)
-    res = sp.screen(torch.from_numpy(w["Y"]).cuda(), w["k"])
+    Yd = torch.from_numpy(w["Y"]).cuda()
+    results = {"fp32": sp.screen(Yd, w["k"], precision=dse.PREC_FP32),
+               "bf16x3": sp.screen(Yd, w["k"], precision=dse.PREC_AUTO)}
+    assert results["bf16x3"].stats()["precision_used"] == dse.PREC_BF16X3
     rng = np.random.default_rng(2)
-    sample = rng.integers(sp.n_stored, sp.n_total, size=6000).astype(np.uint64)
-    _check_full_size(res, orc, w["Y"], 16, w["k"], sample, "fp32")
+    a = int(rng.integers(sp.n_stored, sp.n_total - 1_000_000))
+    slices = [(a, a + 1_000_000)] + _dense_slices(results["bf16x3"], 16, 0, sp.n_total, 1 << 19, 1)
+    # one oracle screen per slice, shared by both checks
+    cache = {}
+    real_screen = orc.screen
+
+    def cached(Y, k, id_begin=0, id_end=None):
+        key = (k, id_begin, id_end)
+        if key not in cache:
+            cache[key] = real_screen(Y, k, id_begin=id_begin, id_end=id_end)
+        return cache[key]
+
+    orc.screen = cached
+    for name, res in results.items():
+        checked = _check_full_size(res, orc, w["Y"], 16, w["k"], slices, 4000, name)
+        assert checked >= 20 * 16, (name, checked)
+        res.free()
