@@ -445,6 +445,18 @@ dse_status dse_l0_search(dse_space *space, const dse_l0_desc *desc, int64_t *top
 dse_status dse_ls_refit_noalloc(dse_space *space, const dse_refit_desc *desc, uint64_t *best_id,
                                 double *best_rmse, double *coefs, double *residual);
 
+/* Failure detection without a fault.  dse_check_wait runs the bounded
+   device wait the pipelined kernels use (an mbarrier polled at most `polls`
+   times) on a barrier that completes only when `arrive` is nonzero: it
+   returns DSE_ETIMEOUT when the wait runs out, DSE_OK otherwise, and the
+   context stays usable either way.  Synchronises. */
+dse_status dse_check_wait(uint32_t polls, int32_t arrive, void *stream);
+
+/* Test hook: the device allocation after `after` more successful ones
+   fails with DSE_ENOMEM (once); a negative value switches the hook off.
+   Process-wide. */
+void dse_debug_fail_alloc(int64_t after);
+
 /* Number of kernels the library has launched in this process so far. */
 int64_t dse_kernel_launches(void);
 

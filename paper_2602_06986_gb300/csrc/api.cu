@@ -1094,6 +1094,7 @@ const char *dse_version(void) { return "dse 0.1 (sm_103a)"; }
 int64_t dse_kernel_launches(void) { return launches_so_far(); }
 
 dse_status dse_build_space(const dse_space_desc *d, dse_space **out) {
+  dse::NvtxRange nvtx_range_("dse_build_space");
   clear_error();
   if (!d || !out) {
     set_error("null argument");
@@ -1146,6 +1147,7 @@ dse_status dse_space_size(const dse_space *s, int64_t *n_stored, uint64_t *n_tot
 }
 
 dse_status dse_space_counts(dse_space *s, int32_t rung, uint64_t *slots, int64_t reasons[6]) {
+  dse::NvtxRange nvtx_range_("dse_space_counts");
   clear_error();
   if (!s || rung < 0 || rung > s->max_rung) {
     set_error("bad space or rung");
@@ -1226,6 +1228,7 @@ dse_status dse_expr_string(const dse_space *s, uint64_t id, char *buf, int64_t l
 }
 
 dse_status dse_sis_screen(dse_space *s, const dse_screen_desc *d, dse_result **out) {
+  dse::NvtxRange nvtx_range_("dse_sis_screen");
   clear_error();
   if (!s || !d || !out) {
     set_error("null argument");
@@ -1260,6 +1263,7 @@ void dse_result_free(dse_result *r) {
 
 dse_status dse_topk_fetch(dse_result *r, int32_t list, uint64_t *idx, double *score, double *err_bound, int64_t cap,
                           int64_t *n_out) {
+  dse::NvtxRange nvtx_range_("dse_topk_fetch");
   clear_error();
   if (!r || list < 0 || list >= r->n_lists || cap < 0) {
     set_error("bad result or list");
@@ -1297,6 +1301,7 @@ dse_status dse_result_stats(dse_result *r, dse_stats *out) {
 
 dse_status dse_residual_loop(dse_space *s, const dse_loop_desc *d, dse_loop_result *out, uint64_t *sis_ids,
                              double *residual) {
+  dse::NvtxRange nvtx_range_("dse_residual_loop");
   clear_error();
   if (!s || !d || !out || !d->y || d->n_iter < 1 || d->n_iter > kLoopMax || d->k < 1 || d->k > (1 << 20) ||
       d->precision < 0 || d->precision > DSE_PREC_AUTO) {
@@ -1311,6 +1316,7 @@ dse_status dse_residual_loop(dse_space *s, const dse_loop_desc *d, dse_loop_resu
 
 dse_status dse_ls_refit(dse_space *s, const dse_refit_desc *d, uint64_t *best_id, double *best_rmse, double *coefs,
                         double *residual) {
+  dse::NvtxRange nvtx_range_("dse_ls_refit");
   clear_error();
   if (!s || !d || !d->y || d->n_fixed < 0 || d->n_fixed > 3 || (d->n_fixed > 0 && !d->fixed) || !d->cand ||
       d->n_cand < 1 || !best_id || !best_rmse) {

@@ -488,6 +488,7 @@ extern "C" {
 
 dse_status dse_sis_screen_batched(const dse_batch_item *items, int32_t n_items, const dse_batch_desc *d,
                                   dse_batch **out) {
+  dse::NvtxRange nvtx_range_("dse_sis_screen_batched");
   clear_error();
   if (!items || !d || !out || n_items < 1 || d->k < 1 || d->k > (1 << 20) ||
       !(d->precision == DSE_PREC_FP32 || d->precision == DSE_PREC_FP64 || d->precision == DSE_PREC_AUTO) ||
@@ -527,6 +528,7 @@ dse_status dse_sis_screen_batched(const dse_batch_item *items, int32_t n_items, 
 }
 
 dse_status dse_batch_rescreen(dse_batch *b, const double *Y, int32_t y_on_device) {
+  dse::NvtxRange nvtx_range_("dse_batch_rescreen");
   clear_error();
   if (!b || !Y) {
     set_error("null argument");
@@ -539,6 +541,7 @@ dse_status dse_batch_rescreen(dse_batch *b, const double *Y, int32_t y_on_device
 
 dse_status dse_batch_fetch(dse_batch *b, int32_t item, uint64_t *idx, double *score, double *err_bound, int64_t cap,
                            int64_t *n_out) {
+  dse::NvtxRange nvtx_range_("dse_batch_fetch");
   clear_error();
   if (!b || item < 0 || item >= b->n || cap < 0) {
     set_error("bad batch or item");

@@ -564,6 +564,7 @@ using namespace dse;
 
 extern "C" dse_status dse_l0_search(dse_space *s, const dse_l0_desc *d, int64_t *top_pos, double *top_rmse,
                                     double *top_coefs, int32_t *n_found) {
+  dse::NvtxRange nvtx_range_("dse_l0_search");
   clear_error();
   if (!s || !d || !d->y || !d->ids || !n_found || d->dim < 1 || d->dim > 3 || d->n_ids < d->dim ||
       d->n_ids > (1 << 16) || d->n_top < 1 || d->n_top > 32) {

@@ -156,6 +156,7 @@ dse_status refit_noalloc_impl(dse_space *S, const dse_refit_desc *d, uint64_t *b
 
 extern "C" dse_status dse_ls_refit_noalloc(dse_space *s, const dse_refit_desc *d, uint64_t *best_id,
                                            double *best_rmse, double *coefs, double *residual) {
+  dse::NvtxRange nvtx_range_("dse_ls_refit_noalloc");
   dse::clear_error();
   if (!s || !d || !d->y || d->n_fixed < 0 || d->n_fixed > 3 || (d->n_fixed > 0 && !d->fixed) || !d->cand ||
       d->n_cand < 1 || !best_id || !best_rmse) {

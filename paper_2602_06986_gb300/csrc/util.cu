@@ -1,8 +1,11 @@
 // util.cu -- error state, allocation wrappers and order-preserving compaction.
+#include <atomic>
 #include <stdio.h>
 #include <string.h>
 
 #include "util.cuh"
+
+#include <nvtx3/nvToolsExt.h>
 
 namespace dse {
 
@@ -45,8 +48,29 @@ void dfree(void *p) { dfree_async(p, g_alloc_stream); }
 // driver round trip and no device-wide synchronisation.
 static bool g_pool_ready[64] = {false};
 
+// Simulated allocation failure (dse_debug_fail_alloc): the allocation after
+// g_fail_after more successful ones fails; negative: off.
+static std::atomic<int64_t> g_fail_after{-1};
+
+void debug_fail_alloc(int64_t after) { g_fail_after.store(after); }
+
+NvtxRange::NvtxRange(const char *name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+
+static bool simulated_failure() {
+  int64_t v = g_fail_after.load();
+  while (v >= 0) {
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+
 dse_status dmalloc_async(void **p, size_t bytes, cudaStream_t s, const char *what) {
   *p = nullptr;
+  if (simulated_failure()) {
+    set_error("simulated allocation failure for %s (dse_debug_fail_alloc)", what);
+    return DSE_ENOMEM;
+  }
   if (bytes == 0) bytes = 16;
   int dev = 0;
   cudaGetDevice(&dev);

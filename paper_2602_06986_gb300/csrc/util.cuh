@@ -64,6 +64,16 @@ void *pinned_staging(size_t bytes);
 // counts[c] += number of p < n with flags[p] == c, for c < 6 (device counters).
 void launch_count_reasons(const uint8_t *flags, uint64_t n, unsigned long long *counts, cudaStream_t s);
 
+// NVTX range around a public call (a no-op unless a profiler is attached),
+// so that timelines show the library's phases.
+struct NvtxRange {
+  explicit NvtxRange(const char *name);
+  ~NvtxRange();
+};
+
+// Test hook of dse_debug_fail_alloc.
+void debug_fail_alloc(int64_t after);
+
 // Process-wide count of kernels the library has launched.
 int64_t launches_so_far();
 

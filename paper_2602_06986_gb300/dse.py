@@ -98,7 +98,8 @@ class LoopResult(C.Structure):
 EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_counts", "dse_decode",
            "dse_expr_string", "dse_candidate_units", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
            "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
-           "dse_residual_loop", "dse_l0_search", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_kernel_launches", "dse_last_error",
+           "dse_residual_loop", "dse_l0_search", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_check_wait",
+           "dse_debug_fail_alloc", "dse_kernel_launches", "dse_last_error",
            "dse_version"]
 
 _lib = None
@@ -135,15 +136,29 @@ def lib():
         L.dse_l0_search.argtypes = [vp, C.POINTER(L0Desc), vp, vp, vp, C.POINTER(i32)]
         L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
         L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
+        L.dse_check_wait.argtypes = [C.c_uint32, i32, vp]
+        L.dse_debug_fail_alloc.argtypes = [i64]
+        L.dse_debug_fail_alloc.restype = None
         L.dse_last_error.restype = C.c_char_p
         L.dse_version.restype = C.c_char_p
         L.dse_kernel_launches.restype = i64
         for name in EXPORTS:
             if name not in ("dse_space_free", "dse_result_free", "dse_batch_free", "dse_last_error",
-                            "dse_version", "dse_kernel_launches"):
+                            "dse_version", "dse_kernel_launches", "dse_debug_fail_alloc"):
                 getattr(L, name).restype = i32
         _lib = L
     return _lib
+
+
+def check_wait(polls, arrive, stream=None):
+    """Status of the bounded device wait probe (dse_check_wait)."""
+    return int(lib().dse_check_wait(polls, 1 if arrive else 0, stream))
+
+
+def debug_fail_alloc(after):
+    """Make the device allocation after ``after`` more successful ones fail
+    with DSE_ENOMEM (negative: off)."""
+    lib().dse_debug_fail_alloc(after)
 
 
 def _check(status):
