@@ -231,6 +231,18 @@ def bench_batched(args):
     targets = [w["bases"][p["base"]]["y"][p["samples"]] for p in w["problems"]]
     Ycat = torch.from_numpy(np.concatenate(targets)).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # job size of the batched plan, tuned on the device (untimed)
+    from paper_2602_06986_gb300 import autotune as at
+
+    def one_batch():
+        bt0 = dse.Batch(spaces, targets, w["k"])
+        bt0.fetch(0)
+        bt0.free()
+
+    entry = at.tune("batched", max(len(t) for t in targets), 1, one_batch, reps=2)
+    dse.set_tuning(entry["config"] or None)
+    tuning = {"chosen": entry["config"] or "defaults", "in_effect": dse.get_tuning(),
+              "tried_ms": [[t["config"], round(t["seconds"] * 1e3, 2)] for t in entry["tried"]]}
     res = {}
     for mode in ("eager", "graph"):
         bt = dse.Batch(spaces, targets, w["k"], graph=(mode == "graph"))
@@ -260,7 +272,7 @@ def bench_batched(args):
             "ms_per_step": res["graph"]["ms_per_step"], "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": w["name"], "problems": len(spaces), "k": w["k"],
                                             "candidate_slots": n_total, "l2": "flushed between steps"},
-            "eager": res["eager"], "graph": res["graph"], "space_build_s_total": build_s}
+            "eager": res["eager"], "graph": res["graph"], "space_build_s_total": build_s, "tuning": tuning}
     print(json.dumps(line))
 
 
@@ -555,6 +567,25 @@ def bench_large(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
+    # the planner's tile settings for this workload class, tuned on the
+    # device (untimed; coordinate descent from the defaults, 2 runs each)
+    tuning = None
+    if not args.no_tune:
+        from paper_2602_06986_gb300 import autotune as at
+
+        sp_t = large_space(dse, w, Xd, stream)
+        entry = at.tune("screen_tc", N, T, lambda: sp_t.screen(Yd, k, precision=dse.PREC_AUTO, stream=stream).free(),
+                        reps=2)
+        sp_t.free()
+        chosen = entry["config"]
+        if world > 1:  # every rank uses rank 0's choice
+            obj = [chosen]
+            torch.distributed.broadcast_object_list(obj, src=0)
+            chosen = obj[0]
+        dse.set_tuning(chosen or None)
+        tuning = {"kernel_class": at.key("screen_tc", N, T), "chosen": chosen or "defaults",
+                  "in_effect": dse.get_tuning(),
+                  "tried_ms": [[t["config"], round(t["seconds"] * 1e3, 2)] for t in entry["tried"]]}
     for _ in range(args.warmup):
         large_step_device(dse, w, Xd, Yd, k, dse.PREC_AUTO, whole, stream, dse.FLAG_TIMING_MAIN, group)
     barrier()
@@ -694,6 +725,7 @@ def bench_large(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
+        "tuning": tuning,
     }
     print(json.dumps(line))
 
@@ -713,6 +745,7 @@ def main():
                     help="candidate ids per step of the reference (oracle) arm on the large workload")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU path (0: skip)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--no-tune", action="store_true", help="keep the planner's default tile settings")
     args = ap.parse_args()
     if args.workload == "large":
         return bench_large(args)

@@ -445,6 +445,34 @@ dse_status dse_l0_search(dse_space *space, const dse_l0_desc *desc, int64_t *top
 dse_status dse_ls_refit_noalloc(dse_space *space, const dse_refit_desc *desc, uint64_t *best_id,
                                 double *best_rmse, double *coefs, double *residual);
 
+/* Launch and tile parameters of the planner, process-wide.  An autotuner
+   (the package's autotune module) times candidate values on the device and
+   installs the fastest.  A zero field keeps the built-in default.  They
+   decide which work goes to which kernel and in what order, not what is
+   computed: the returned lists are the same apart from ties, the reported
+   bounds may differ (e.g. Gram contraction against sample by sample). */
+typedef struct {
+  int32_t tile_group;        /* consecutive 16/32-row i-blocks per group of
+                                pair tiles, 1..64 (defaults: 8 on the tensor
+                                cores, 4 on the CUDA cores)                   */
+  int32_t seed_stride;       /* every seed_stride-th product tile is launched
+                                first to raise the thresholds, 2..4096 (64)   */
+  int32_t gram_max_n;        /* largest N for the product Gram contraction,
+                                16..2048 (2048)                               */
+  int32_t tc_min_targets;    /* DSE_PREC_AUTO takes the tensor cores from this
+                                many targets, 1..4096 (8)                     */
+  int32_t batch_job_samples; /* batched screens: candidate-samples per job,
+                                1024..2^20 (16384)                           */
+  int32_t reserved[3];
+} dse_tuning;
+
+/* Installs t (NULL: every default).  DSE_EINVAL for a value outside its
+   range.  Affects screens planned afterwards. */
+dse_status dse_set_tuning(const dse_tuning *t);
+/* The values in effect (defaults filled in; tile_group 0 when the two
+   defaults differ). */
+dse_status dse_get_tuning(dse_tuning *t);
+
 /* Failure detection without a fault.  dse_check_wait runs the bounded
    device wait the pipelined kernels use (an mbarrier polled at most `polls`
    times) on a barrier that completes only when `arrive` is nonzero: it

@@ -406,7 +406,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   ScreenPlan plan{};
   // the tensor-core contraction for many targets (per-target lists only)
   if (d->mode == DSE_MODE_PER_TARGET &&
-      (prec == DSE_PREC_BF16X3 || (prec == DSE_PREC_AUTO && d->n_targets >= 8))) {
+      (prec == DSE_PREC_BF16X3 || (prec == DSE_PREC_AUTO && d->n_targets >= tuning().tc_min_targets))) {
     plan.use_tc = true;
     prec = DSE_PREC_BF16X3;
   } else if (prec == DSE_PREC_AUTO || prec == DSE_PREC_BF16X3) {
@@ -459,16 +459,18 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
       gram_tiles(sp, id_begin, id_end, plan.gram_tiles);
     } else if (any_mul) {
       triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.mul_tiles);
-      group_tiles(plan.mul_tiles, (int64_t)ia, BI, plan.use_tc ? 8 : 4);
-      // A large tile list is launched in two parts: every 64th tile first, so
-      // that the thresholds have risen from a spread sample of the space
-      // before the bulk of the candidates is filtered.
-      const size_t nt = plan.mul_tiles.size();
-      if (nt >= 64 * 64) {
+      const Tuning tn = tuning();
+      group_tiles(plan.mul_tiles, (int64_t)ia, BI, plan.use_tc ? tn.tile_group_tc : tn.tile_group_cc);
+      // A large tile list is launched in two parts: every seed_stride-th
+      // tile first (64 by default), so that the thresholds have risen from a
+      // spread sample of the space before the bulk of the candidates is
+      // filtered.
+      const size_t nt = plan.mul_tiles.size(), stride = (size_t)tn.seed_stride;
+      if (nt >= 64 * stride) {
         std::vector<Tile> seed, rest;
-        seed.reserve(nt / 64 + 1);
+        seed.reserve(nt / stride + 1);
         rest.reserve(nt);
-        for (size_t t = 0; t < nt; ++t) (t % 64 == 0 ? seed : rest).push_back(plan.mul_tiles[t]);
+        for (size_t t = 0; t < nt; ++t) (t % stride == 0 ? seed : rest).push_back(plan.mul_tiles[t]);
         plan.n_seed_tiles = (int32_t)seed.size();
         seed.insert(seed.end(), rest.begin(), rest.end());
         plan.mul_tiles.swap(seed);

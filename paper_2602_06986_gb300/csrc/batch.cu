@@ -80,9 +80,10 @@ struct dse_batch {
 
 namespace {
 
-constexpr int64_t kJobSamples = 1 << 14;  // candidate-samples (pair-samples) per job
 
-int32_t job_len(int64_t N) { return (int32_t)std::max<int64_t>(4, std::min<int64_t>(64, kJobSamples / N)); }
+int32_t job_len(int64_t N) {
+  return (int32_t)std::max<int64_t>(4, std::min<int64_t>(64, (int64_t)tuning().batch_job_samples / N));
+}
 
 // Resets, target preparation (with_targets) and every kernel of one screen of
 // the batch, enqueued on st.  reset_theta: start the thresholds from zero

@@ -216,6 +216,12 @@ struct ScreenArgs {
   float2 *ivl;                 // optional: (s, eps) of each id of the range and list, before re-scores
 };
 
+// Planner parameters in effect (dse_set_tuning, defaults filled in).
+struct Tuning {
+  int tile_group_tc, tile_group_cc, seed_stride, gram_max_n, tc_min_targets, batch_job_samples;
+};
+Tuning tuning();
+
 // Launch bookkeeping (process-wide count of the library's kernel launches).
 void note_launches(int64_t n);
 

@@ -755,7 +755,7 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
 
 // Whether a screen may take the Gram path: FP32, one target, N up to 2048
 // samples (the accumulation bound grows with the chunks per accumulator).
-bool gram_eligible(int64_t N) { return N >= 16 && N <= 2048; }
+bool gram_eligible(int64_t N) { return N >= 16 && N <= tuning().gram_max_n; }
 
 size_t gram_space_bytes(int64_t n, int64_t N) {
   const int64_t nchunks = (N + tc::KC - 1) / tc::KC;

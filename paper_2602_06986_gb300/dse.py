@@ -46,6 +46,13 @@ class ScreenDesc(C.Structure):
                 ("dedup_tau", C.c_double), ("reasons", C.c_void_p), ("intervals", C.c_void_p)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("tile_group", C.c_int32), ("seed_stride", C.c_int32), ("gram_max_n", C.c_int32),
+                ("tc_min_targets", C.c_int32), ("batch_job_samples", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+TUNING_FIELDS = ("tile_group", "seed_stride", "gram_max_n", "tc_min_targets", "batch_job_samples")
+
 FLAG_TIMING = 1
 FLAG_DEDUP = 2
 FLAG_DIRECT = 4
@@ -99,7 +106,7 @@ EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_cou
            "dse_expr_string", "dse_candidate_units", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
            "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
            "dse_residual_loop", "dse_l0_search", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_check_wait",
-           "dse_debug_fail_alloc", "dse_kernel_launches", "dse_last_error",
+           "dse_debug_fail_alloc", "dse_set_tuning", "dse_get_tuning", "dse_kernel_launches", "dse_last_error",
            "dse_version"]
 
 _lib = None
@@ -137,6 +144,8 @@ def lib():
         L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
         L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
         L.dse_check_wait.argtypes = [C.c_uint32, i32, vp]
+        L.dse_set_tuning.argtypes = [C.POINTER(Tuning)]
+        L.dse_get_tuning.argtypes = [C.POINTER(Tuning)]
         L.dse_debug_fail_alloc.argtypes = [i64]
         L.dse_debug_fail_alloc.restype = None
         L.dse_last_error.restype = C.c_char_p
@@ -148,6 +157,26 @@ def lib():
                 getattr(L, name).restype = i32
         _lib = L
     return _lib
+
+
+def set_tuning(values=None):
+    """Install planner parameters (dse_set_tuning): a dict with any of
+    TUNING_FIELDS (missing or 0: default); None restores every default."""
+    if values is None:
+        _check(lib().dse_set_tuning(None))
+        return
+    unknown = set(values) - set(TUNING_FIELDS)
+    if unknown:
+        raise ValueError(f"unknown tuning fields {sorted(unknown)}")
+    t = Tuning(*(int(values.get(f, 0)) for f in TUNING_FIELDS))
+    _check(lib().dse_set_tuning(C.byref(t)))
+
+
+def get_tuning():
+    """The planner parameters in effect (dse_get_tuning)."""
+    t = Tuning()
+    _check(lib().dse_get_tuning(C.byref(t)))
+    return {f: getattr(t, f) for f in TUNING_FIELDS}
 
 
 def check_wait(polls, arrive, stream=None):
