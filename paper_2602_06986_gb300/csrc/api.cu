@@ -160,6 +160,7 @@ struct ScreenPlan {
   unsigned char *bsplit = nullptr;
   // Gram path of the product/quotient slots (single-target FP32 screens)
   bool use_gram = false;
+  bool gram_addsub = false;      // a+b and a-b in the Gram kernel too
   std::vector<int2> gram_tiles;
   int2 *gram_tiles_dev = nullptr;
   void *gram_scr = nullptr;
@@ -444,17 +445,22 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
     uint64_t ia, ja, ib2, jb;
     pair_from_index(q0 + g.tri_o, &ia, &ja);
     pair_from_index(q1 + g.tri_o, &ib2, &jb);
-    bool any_mul = false, any_add = false;
+    bool any_mul = false, any_add = false, any_addsub = false, any_absdiff = false;
     for (int s = 0; s < g.nb; ++s) {
       int op = g.bops[s];
       if (op == DSE_OP_MUL || op == DSE_OP_DIV || op == DSE_OP_RDIV) any_mul = true;
       else {
         any_add = true;
         addpos.push_back(s);
+        (op == DSE_OP_ABSDIFF ? any_absdiff : any_addsub) = true;
       }
     }
-    plan.use_gram = any_mul && !plan.prec64 && !plan.use_tc && d->n_targets == 1 && gram_eligible(N) &&
-                    !(d->flags & DSE_FLAG_DIRECT);
+    plan.use_gram = (any_mul || any_addsub) && !plan.prec64 && !plan.use_tc && d->n_targets == 1 &&
+                    gram_eligible(N) && !(d->flags & DSE_FLAG_DIRECT);
+    // a+b and a-b come from the same contraction (the centred cross term);
+    // the additive kernels then run for |a-b| alone, or not at all
+    plan.gram_addsub = plan.use_gram && any_addsub;
+    const bool add_kernels = any_add && !(plan.gram_addsub && !any_absdiff);
     if (plan.use_gram) {
       gram_tiles(sp, id_begin, id_end, plan.gram_tiles);
     } else if (any_mul) {
@@ -476,7 +482,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
         plan.mul_tiles.swap(seed);
       }
     }
-    if (any_add) {
+    if (add_kernels) {
       const bool one_class = !(sp->unit_check_addsub && sp->D > 0) || sp->h_class_begin.size() <= 2;
       if (one_class) {
         // every pair may be added: the same id triangle as the products,
@@ -495,8 +501,9 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
         else
           class_tiles(sp->h_class_begin, sp->n, BI, BJ, 0, plan.add_tiles);
       }
-      plan.add_total = count_slots_mod(be - g.um, g.nb, addpos) - count_slots_mod(bb - g.um, g.nb, addpos);
     }
+    if (any_add)
+      plan.add_total = count_slots_mod(be - g.um, g.nb, addpos) - count_slots_mod(bb - g.um, g.nb, addpos);
   }
   // accumulation error factors
   const double u32 = 5.9604644775390625e-8, u64 = 1.1102230246251565e-16;
@@ -668,6 +675,7 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   A.err = R->err;
   for (int c = 0; c < 6; ++c) A.slot_pos[c] = -1;
   for (int s2 = 0; s2 < g.nb; ++s2) A.slot_pos[g.bops[s2] - 6] = s2;
+  A.gram_addsub = plan.gram_addsub ? 1 : 0;
 
   S.B = A.B;
   S.n_lists = n_lists;

@@ -214,6 +214,7 @@ struct ScreenArgs {
   uint32_t *esc_prob;          // escalation list: problem of each entry (batched only)
   int8_t *why;                 // optional: reason code of each id of [id_begin, id_end) (device)
   float2 *ivl;                 // optional: (s, eps) of each id of the range and list, before re-scores
+  int32_t gram_addsub;         // a+b and a-b are scored by the Gram kernel: the additive kernels take |a-b| only
 };
 
 // Planner parameters in effect (dse_set_tuning, defaults filled in).

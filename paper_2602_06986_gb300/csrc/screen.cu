@@ -496,7 +496,9 @@ __device__ __forceinline__ unsigned binary_candidate(const ScreenArgs &A, LaneSt
   const bool additive = opc == DSE_OP_ADD || opc == DSE_OP_SUB || opc == DSE_OP_ABSDIFF;
   const int pos = A.slot_pos[opc - 6];
   const uint64_t gid = (uint64_t)A.n_stored + pbase + (uint64_t)(pos < 0 ? 0 : pos);
-  const bool cand = active && pv && pos >= 0 && gid >= A.id_begin && gid < A.id_end;
+  // (a+b and a-b of every pair are the Gram kernel's when it runs)
+  const bool gram_taken = A.gram_addsub && (opc == DSE_OP_ADD || opc == DSE_OP_SUB);
+  const bool cand = active && pv && pos >= 0 && !gram_taken && gid >= A.id_begin && gid < A.id_end;
   int reason = DSE_VALID;
   EvalErr<R> ee{R(0), R(0)};
   if (cand) reason = binary_apriori_W<R>(A, opc, ia, ib, fa_a, fa_b, kk, mi, mj, &ee);

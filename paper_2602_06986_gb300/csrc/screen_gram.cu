@@ -103,6 +103,7 @@ struct EpiFeat {
   int32_t cplx;
   float c[2], s1[2], s2[2], n1[2], n2[2], nu[2];  // GramFeat
   float sy[2], ny[2];                             // GramTgt
+  uint64_t uk[2];                                 // packed unit key
 };
 constexpr int NCACHE = FW + 8 * PW;
 
@@ -343,6 +344,10 @@ struct GramCand {
   int realised;  // 1 valid, 0 degenerate, 2 undecided (escalate)
 };
 
+__device__ __forceinline__ GramCand gram_finish(float S1, float dS1, float S2, float dS2, float Sy, float dSy,
+                                                float Z, float dZ, float Vhi, float E, float N, float invN,
+                                                float ysum, float fmin);
+
 // Score interval of v = u w from the contraction entries (G11, G22, G12,
 // G21, H) and the two features' sums; family fu of the a-feature, fw of the
 // b-feature; kappa of the evaluation error.
@@ -378,17 +383,30 @@ __device__ __forceinline__ GramCand gram_score(const gram::EpiFeat *Fa, int fu, 
   const float dSy =
       (dH + 10.f * u * (fabsf(tya) + fabsf(tyb) + fabsf(H)) + 1.01f * u * (acu * Fb->n1[fw] + acw * Fa->n1[fu])) *
       1.01f;
-  // centred sum of squares and its interval
-  const float mean = S1 * invN;
-  const float Sxx = fmaf(-S1, mean, S2);
-  const float aS1 = fabsf(S1);
-  const float dSxx = (dS2 + (2.f * aS1 * dS1 + dS1 * dS1) * invN + 6.f * u * (fabsf(S2) + aS1 * fabsf(mean))) * 1.01f;
   // uncentred norm of v: Z = S2 + 2 k S1 + N k^2
   const float Z = S2 + 2.f * cucw * S1 + N * cucw * cucw;
   const float dZ = (dS2 + 2.f * fabsf(cucw) * dS1 + 10.f * u * (fabsf(S2) + 2.f * fabsf(cucw * S1) + N * cucw * cucw)) *
                    1.01f;
   const float Vhi = sqrtf(Z + dZ) * (1.f + 4.f * u);
   const float E = u * (kappa * Vhi + 1.01f * (acw * Fa->nu[fu] + acu * Fb->nu[fw])) * 1.02f;
+  return gram_finish(S1, dS1, S2, dS2, Sy, dSy, Z, dZ, Vhi, E, N, invN, ysum, fmin);
+}
+
+// The interval and realised decision from the assembled statistics of a
+// candidate and their error bounds (shared by the products and the sums):
+// S1, S2, Sy of v - k with bounds dS1, dS2, dSy, the uncentred norm
+// Z = |v|^2 with bound dZ and Vhi >= |v|, and E the bound of the
+// evaluation error vector's 2-norm.
+__device__ __forceinline__ GramCand gram_finish(float S1, float dS1, float S2, float dS2, float Sy, float dSy,
+                                                float Z, float dZ, float Vhi, float E, float N, float invN,
+                                                float ysum, float fmin) {
+  const float u = 5.9604644775390625e-8f;
+  GramCand o;
+  // centred sum of squares and its interval
+  const float mean = S1 * invN;
+  const float Sxx = fmaf(-S1, mean, S2);
+  const float aS1 = fabsf(S1);
+  const float dSxx = (dS2 + (2.f * aS1 * dS1 + dS1 * dS1) * invN + 6.f * u * (fabsf(S2) + aS1 * fabsf(mean))) * 1.01f;
   const float q = sqrtf(Sxx > 0.f ? Sxx : 0.f);
   const float lo2 = Sxx - dSxx;
   const float q_lo = sqrtf(lo2 > 0.f ? lo2 : 0.f) * (1.f - 4.f * u) - E;
@@ -462,6 +480,53 @@ __device__ __forceinline__ int gram_apriori(const ScreenArgs &A, int opc, int64_
     lo = __fmul_rd(b.fa.w, a.fr.y);
     hi = __fmul_ru(b.fa.z, a.fr.x);
   }
+  if (hi <= A.fmax32_dn) return DSE_VALID;
+  if (lo > A.fmax32_up) return DSE_R_MAGNITUDE;
+  return domain_magnitude64(opc, A.F.min64[ia], A.F.max64[ia], A.F.minabs64[ia], A.F.maxabs64[ia],
+                            A.F.minabs64[ib], A.F.maxabs64[ib], A.fmax64, 0.0);
+}
+
+// a + b and a - b of a pair (family x of both features, k = c_a +- c_b):
+//   S1 = P1 +- Q1,  S2 = P2 + Q2 +- 2 G11,  Sy = PY +- QY
+// with G11 = sum p q from the same contraction as the products (no sample is
+// evaluated).  The candidate the FP32 rows represent differs from the exact
+// one by at most u (2 |x| + |c|) per operand and sample.  The bounds grow
+// with the operands' norms, not with the (possibly cancelling) value: a
+// difference of nearly equal features gets a wide interval, or an undecided
+// realised test and the FP64 escalation.
+__device__ __forceinline__ GramCand gram_score_add(const gram::EpiFeat *Fa, const gram::EpiFeat *Fb, float sign,
+                                                   float G11, float delta, float N, float invN, float ysum,
+                                                   float fmin) {
+  const float u = 5.9604644775390625e-8f;
+  const float ca = Fa->c[0], cb = Fb->c[0], k = ca + sign * cb;
+  const float P1 = Fa->s1[0], P2 = Fa->s2[0], PY = Fa->sy[0];
+  const float Q1 = Fb->s1[0], Q2 = Fb->s2[0], QY = Fb->sy[0];
+  const float S1 = P1 + sign * Q1;
+  const float S2 = P2 + Q2 + sign * 2.f * G11;
+  const float Sy = PY + sign * QY;
+  const float dG11 = delta * Fa->n1[0] * Fb->n1[0];
+  const float dS1 = 8.f * u * (fabsf(P1) + fabsf(Q1)) * 1.01f;
+  const float dS2 = (2.f * dG11 + 8.f * u * (P2 + Q2 + 2.f * fabsf(G11))) * 1.01f;
+  const float dSy = (8.f * u * (fabsf(PY) + fabsf(QY)) + 1.01f * u * (Fa->n1[0] + Fb->n1[0])) * 1.01f;
+  const float Z = S2 + 2.f * k * S1 + N * k * k;
+  const float dZ = (dS2 + 2.f * fabsf(k) * dS1 + 10.f * u * (fabsf(S2) + 2.f * fabsf(k * S1) + N * k * k)) * 1.01f;
+  const float Vhi = sqrtf(Z + dZ) * (1.f + 4.f * u);
+  const float E = u * (2.01f * (Fa->nu[0] + Fb->nu[0]) + (fabsf(ca) + fabsf(cb)) * sqrtf(N) * (1.f + 4.f * u) +
+                       Vhi) * 1.02f;
+  return gram_finish(S1, dS1, S2, dS2, Sy, dSy, Z, dZ, Vhi, E, N, invN, ysum, fmin);
+}
+
+// A-priori tests of a + b and a - b from the cached records, in the order
+// and arithmetic of binary_apriori_W: equal units (when checked),
+// complexity, user rules, and the magnitude bound max|a| + max|b| by an FP32
+// directed-rounding interval with the exact FP64 test when it straddles the
+// limit.
+__device__ __forceinline__ int gram_apriori_add(const ScreenArgs &A, int opc, int64_t ia, int64_t ib,
+                                                const gram::EpiFeat &a, const gram::EpiFeat &b) {
+  if (A.unit_check_addsub && (a.uk[0] != b.uk[0] || a.uk[1] != b.uk[1])) return DSE_R_UNIT;
+  if (A.max_complexity > 0 && a.cplx + b.cplx + 1 > A.max_complexity) return DSE_R_COMPLEXITY;
+  if (rule_fails(A.F, opc, ia, ib)) return DSE_R_COMPLEXITY;
+  const float lo = __fadd_rd(a.fa.w, b.fa.w), hi = __fadd_ru(a.fa.z, b.fa.z);
   if (hi <= A.fmax32_dn) return DSE_VALID;
   if (lo > A.fmax32_up) return DSE_R_MAGNITUDE;
   return domain_magnitude64(opc, A.F.min64[ia], A.F.max64[ia], A.F.minabs64[ia], A.F.maxabs64[ia],
@@ -630,6 +695,8 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
           c.fr = A.F.fr[f];
           c.flags = A.F.flags[f];
           c.cplx = A.F.cplx[f];
+          c.uk[0] = A.F.ukey[2 * f];
+          c.uk[1] = A.F.ukey[2 * f + 1];
           const GramFeat g = GA.gf[f];
           const GramTgt t = GA.gt[f];
 #pragma unroll
@@ -661,25 +728,40 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
 #pragma unroll
         for (int e = 0; e < EC; ++e) E[lane][e] = v[e];
         __syncwarp();
-        // 5 a-features x 8 b-features x 3 slots = 120 candidates
-        for (int it = 0; it < 4; ++it) {
+        // 5 a-features x 8 b-features x 3 slots = 120 products and
+        // quotients (iterations 0-3), then 5 x 8 x 2 = 80 sums and
+        // differences (iterations 4-6, when this kernel takes them)
+        const int iters = A.gram_addsub ? 7 : 4;
+        for (int it = 0; it < iters; ++it) {
           const float th = ld_relaxed(&A.B.theta[A.t0]);  // issued first: its latency hides behind the scoring
-          const int idx = it * 32 + lane;
-          const int fi = idx / 24, rem = idx % 24, gj = rem / 3, slot = rem % 3;
+          const bool add = it >= 4;
+          int idx, fi, gj, opc;
+          if (!add) {
+            idx = it * 32 + lane;
+            const int rem = idx % 24, slot = rem % 3;
+            fi = idx / 24;
+            gj = rem / 3;
+            opc = slot == 0 ? DSE_OP_MUL : slot == 1 ? DSE_OP_DIV : DSE_OP_RDIV;
+          } else {
+            idx = (it - 4) * 32 + lane;
+            fi = idx >> 4;
+            gj = (idx >> 1) & 7;
+            opc = (idx & 1) ? DSE_OP_SUB : DSE_OP_ADD;
+          }
           const int64_t i = (int64_t)tl.x * FA + q * FW + fi;
           const int64_t j = (int64_t)tl.y * FB + pc * (EC / 4) + gj;
-          const int opc = slot == 0 ? DSE_OP_MUL : slot == 1 ? DSE_OP_DIV : DSE_OP_RDIV;
           bool want = false;
           uint64_t gid = 0;
           float s = 0.f, eps = 0.f;
-          const bool pair = idx < 120 && i < n && i >= o && j < i;
+          const bool pair = idx < (add ? 80 : 120) && i < n && i >= o && j < i;
           const int pos = A.slot_pos[opc - 6];
           if (pair && pos >= 0) {
             const uint64_t pbase = A.G.um + (tri((uint64_t)i) + (uint64_t)j - A.G.tri_o) * (uint64_t)A.G.nb;
             gid = (uint64_t)A.n_stored + pbase + (uint64_t)pos;
             if (gid >= A.id_begin && gid < A.id_end) {
               const EpiFeat &ca = cache[fi], &cb = cache[FW + pcl * 8 + gj];
-              const int reason = gram_apriori(A, opc, i, j, ca, cb);
+              const int reason = add ? gram_apriori_add(A, opc, i, j, ca, cb) : gram_apriori(A, opc, i, j, ca, cb);
+              if (add) ls.seen++;
               if (reason != DSE_VALID) {
                 ls.r[reason]++;
                 note_why(A, gid, reason);
@@ -687,11 +769,16 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
                 escalate(A, gid);
                 ls.escalated++;
               } else {
-                const int fu = slot == 2 ? 1 : 0, fw = slot == 1 ? 1 : 0;
-                const int ra = 6 * fi + 3 * fu, cl = 4 * gj + 2 * fw;
-                const GramCand gc = gram_score(&ca, fu, &cb, fw, E[ra][cl], E[ra + 1][cl + 1], E[ra][cl + 1],
-                                               E[ra + 1][cl], E[ra + 2][cl], slot == 0 ? 4.01f : 5.01f, GA.delta, N,
-                                               invN, ysum, fmin);
+                GramCand gc;
+                if (add) {
+                  gc = gram_score_add(&ca, &cb, opc == DSE_OP_ADD ? 1.f : -1.f, E[6 * fi][4 * gj], GA.delta, N, invN,
+                                      ysum, fmin);
+                } else {
+                  const int fu = opc == DSE_OP_RDIV ? 1 : 0, fw = opc == DSE_OP_DIV ? 1 : 0;
+                  const int ra = 6 * fi + 3 * fu, cl = 4 * gj + 2 * fw;
+                  gc = gram_score(&ca, fu, &cb, fw, E[ra][cl], E[ra + 1][cl + 1], E[ra][cl + 1], E[ra + 1][cl],
+                                  E[ra + 2][cl], opc == DSE_OP_MUL ? 4.01f : 5.01f, GA.delta, N, invN, ysum, fmin);
+                }
                 if (gc.realised == 0) {
                   ls.r[DSE_R_REALISED]++;
                   note_why(A, gid, DSE_R_REALISED);
