@@ -230,10 +230,14 @@ typedef struct {
    call synchronises the stream (it reads the list state between rounds).
    Not available in dse_residual_loop or the batched screens. */
 #define DSE_FLAG_DEDUP 2
-/* Evaluate the product and quotient slots sample by sample.  Without it a
-   single-target FP32 screen with 16 <= N <= 2048 takes their statistics from
-   Gram contractions on the tensor cores (same results: the same bounds
-   contract, the same re-score of the list). */
+/* Evaluate the binary slots sample by sample.  Without it a single-target
+   FP32 screen with 16 <= N <= 2048 takes the statistics of a*b, a/b, b/a,
+   a+b and a-b from Gram contractions on the tensor cores, and a per-target
+   screen of 2..16 targets (DSE_PREC_AUTO or DSE_PREC_BF16X3) does the same
+   for any N >= 16 (same results: the same bounds contract, the same
+   re-score of the list); |a-b| is always evaluated sample by sample.  With
+   the flag, those screens run the CUDA-core kernels (one target) or the
+   sample-by-sample tensor-core kernel (2..16 targets). */
 #define DSE_FLAG_DIRECT 4
 /* Time only the product/quotient kernel group (kernel_ms[1]; the other
    entries 0): two events per screen instead of five, for timing that kernel
@@ -274,8 +278,15 @@ typedef struct {
   int64_t redundant;       /* DSE_FLAG_DEDUP: redundant entries passed over
                               while filling the lists (all lists)           */
   int32_t dedup_rounds;    /* DSE_FLAG_DEDUP: list lengths tried (0: off)    */
-  int32_t reserved1;
+  int32_t binary_path;     /* DSE_PATH_* that scored the product/quotient
+                              slots (0: none in the range)                   */
 } dse_stats;
+
+/* dse_stats.binary_path */
+#define DSE_PATH_CUDA_CORE 1   /* sample by sample on the CUDA cores        */
+#define DSE_PATH_TENSOR 2      /* sample by sample, tensor-core numerators  */
+#define DSE_PATH_GRAM 3        /* Gram contraction, one target              */
+#define DSE_PATH_GRAM_MT 4     /* Gram contraction, 2..16 targets           */
 
 dse_status dse_result_stats(dse_result *result, dse_stats *out);
 

@@ -164,6 +164,11 @@ struct ScreenPlan {
   std::vector<int2> gram_tiles;
   int2 *gram_tiles_dev = nullptr;
   void *gram_scr = nullptr;
+  // multi-target Gram path (2..16 targets, per-target lists)
+  bool use_gmt = false;
+  std::vector<int2> gmt_tiles;
+  int2 *gmt_tiles_dev = nullptr;
+  void *gmt_scr = nullptr;
 };
 
 bool gram_eligible(int64_t N);
@@ -174,6 +179,15 @@ void gram_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::ve
 void launch_gram_arows(const ScreenArgs &A, const void *space_buf, void *scr, cudaStream_t st);
 dse_status launch_pair_gram(const ScreenArgs &A, const void *space_buf, void *scr, const int2 *tiles, int n_tiles,
                             int sms, cudaStream_t st);
+
+bool gmt_eligible(int T, int64_t N);
+size_t gmt_space_bytes(int64_t n, int64_t N);
+size_t gmt_screen_bytes(int64_t n, int64_t N);
+void gmt_build_space(const FeatTable &F, void *buf, cudaStream_t st);
+void gmt_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::vector<int2> &out);
+void launch_gmt_brows(const ScreenArgs &A, const void *space_buf, void *scr, cudaStream_t st);
+dse_status launch_pair_gmt(const ScreenArgs &A, const void *space_buf, void *scr, const int2 *tiles, int n_tiles,
+                           int sms, cudaStream_t st);
 
 int tc_ntp_for(int T, int N);
 int tc_gen_samples();
@@ -331,11 +345,20 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
         gram_build_space(table_of(sp), sp->gram_buf, st);
       }
       launch_gram_arows(A, sp->gram_buf, plan.gram_scr, st);
+    } else if (plan.use_gmt) {
+      // the operand images (timed with the stored/unary group)
+      if (!sp->gmt_buf) {
+        DSE_TRY(dmalloc(&sp->gmt_buf, gmt_space_bytes(sp->n, sp->N), "multi-target Gram images"));
+        gmt_build_space(table_of(sp), sp->gmt_buf, st);
+      }
+      launch_gmt_brows(A, sp->gmt_buf, plan.gmt_scr, st);
     }
     DSE_TRY(mark(1));
     if (plan.use_gram) {
       DSE_TRY(launch_pair_gram(A, sp->gram_buf, plan.gram_scr, plan.gram_tiles_dev, (int)plan.gram_tiles.size(), sms,
                                st));
+    } else if (plan.use_gmt) {
+      DSE_TRY(launch_pair_gmt(A, sp->gmt_buf, plan.gmt_scr, plan.gmt_tiles_dev, (int)plan.gmt_tiles.size(), sms, st));
     } else if (!plan.mul_tiles.empty()) {
       A.rowid = sp->rowid_ident;
       A.tile_counter = tile_ctr;
@@ -457,12 +480,23 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
     }
     plan.use_gram = (any_mul || any_addsub) && !plan.prec64 && !plan.use_tc && d->n_targets == 1 &&
                     gram_eligible(N) && !(d->flags & DSE_FLAG_DIRECT);
+    // 2..16 targets: the multi-target Gram contraction instead of the
+    // sample-by-sample tensor-core kernel (DSE_FLAG_DIRECT keeps the latter);
+    // the stored/unary and |a-b| candidates go to the CUDA-core kernels
+    plan.use_gmt = plan.use_tc && (any_mul || any_addsub) && gmt_eligible(d->n_targets, N) &&
+                   !(d->flags & DSE_FLAG_DIRECT);
+    if (plan.use_gmt) {
+      plan.use_tc = false;
+      BI = BJ = 16;
+    }
     // a+b and a-b come from the same contraction (the centred cross term);
     // the additive kernels then run for |a-b| alone, or not at all
-    plan.gram_addsub = plan.use_gram && any_addsub;
+    plan.gram_addsub = (plan.use_gram || plan.use_gmt) && any_addsub;
     const bool add_kernels = any_add && !(plan.gram_addsub && !any_absdiff);
     if (plan.use_gram) {
       gram_tiles(sp, id_begin, id_end, plan.gram_tiles);
+    } else if (plan.use_gmt) {
+      gmt_tiles(sp, id_begin, id_end, plan.gmt_tiles);
     } else if (any_mul) {
       triangle_tiles((int64_t)ia, (int64_t)ib2, BI, BJ, plan.mul_tiles);
       const Tuning tn = tuning();
@@ -603,8 +637,12 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   unsigned char *gram_scr = nullptr;
   sc.add(&plan.gram_tiles_dev, plan.gram_tiles.size());
   sc.add(&gram_scr, plan.use_gram ? gram_screen_bytes(sp->n, N) : 1);
+  unsigned char *gmt_scr = nullptr;
+  sc.add(&plan.gmt_tiles_dev, plan.gmt_tiles.size());
+  sc.add(&gmt_scr, plan.use_gmt ? gmt_screen_bytes(sp->n, N) : 1);
   dse_status s = sc.alloc(&R->scratch, &R->scratch_bytes);
   plan.gram_scr = gram_scr;
+  plan.gmt_scr = gmt_scr;
   if (s != DSE_OK) {
     delete R;
     return s;
@@ -628,6 +666,9 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
                         st);
   if (!e && !plan.gram_tiles.empty())
     e = cudaMemcpyAsync(plan.gram_tiles_dev, plan.gram_tiles.data(), sizeof(int2) * plan.gram_tiles.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (!e && !plan.gmt_tiles.empty())
+    e = cudaMemcpyAsync(plan.gmt_tiles_dev, plan.gmt_tiles.data(), sizeof(int2) * plan.gmt_tiles.size(),
                         cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemsetAsync(R->err, 0, sizeof(int), st);
   if (!e) e = cudaMemsetAsync(A.B.theta, 0, sizeof(float) * n_lists, st);
@@ -698,6 +739,11 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   R->host_stats = dse_stats{};
   R->host_stats.screened = (int64_t)(id_end - id_begin);
   R->host_stats.precision_used = prec;
+  R->host_stats.binary_path = plan.use_gmt                               ? DSE_PATH_GRAM_MT
+                              : plan.use_gram                            ? DSE_PATH_GRAM
+                              : plan.use_tc && !plan.mul_tiles.empty()   ? DSE_PATH_TENSOR
+                              : !plan.mul_tiles.empty()                  ? DSE_PATH_CUDA_CORE
+                                                                         : 0;
   Keep *keep = new (std::nothrow) Keep{plan, A, S, tmul, tadd, tile_ctr};
   if (!keep) return fail(DSE_ENOMEM);
   R->keep = keep;
@@ -1069,6 +1115,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
       o = dse_stats{};
       o.screened = R->host_stats.screened;
       o.precision_used = R->host_stats.precision_used;
+      o.binary_path = R->host_stats.binary_path;
       R->reruns = 0;
       stats_from_counters(R, sm, &bc, &nout, &mx, o);
     }

@@ -928,7 +928,7 @@ dse_status space_release(dse_space *S) {
   dfree(S->v64); dfree(S->v32); dfree(S->v32lo); dfree(S->mean64); dfree(S->rmean64); dfree(S->min64); dfree(S->max64);
   dfree(S->minabs64); dfree(S->maxabs64); dfree(S->fa); dfree(S->fr); dfree(S->fnorm); dfree(S->flags); dfree(S->cplx);
   dfree(S->op); dfree(S->units); dfree(S->ca); dfree(S->cb); dfree(S->ukey); dfree(S->rowid_ident);
-  dfree(S->used); dfree(S->dmask); dfree(S->op_deny); dfree(S->gram_buf); dfree(S->v32_class); dfree(S->rcp32);
+  dfree(S->used); dfree(S->dmask); dfree(S->op_deny); dfree(S->gram_buf); dfree(S->gmt_buf); dfree(S->v32_class); dfree(S->rcp32);
   dfree(S->class_rows);
   dfree(S->eq_pairs);
   delete S;

@@ -335,6 +335,7 @@ struct dse_space {
   uint64_t *used = nullptr, *dmask = nullptr, *op_deny = nullptr;  // user rules (nullptr: none)
   int32_t *rowid_ident = nullptr;   // identity row list [0, n)
   void *gram_buf = nullptr;         // product Gram images and sums (built at the first use)
+  void *gmt_buf = nullptr;          // multi-target Gram a-images and sums (built at the first use)
   float *rcp32 = nullptr;           // [n][ld] rcp.approx of v32 (tensor-core products, built at the first use)
   float *v32_class = nullptr;       // v32 rows in unit-class order (tensor-core additive tiles, first use)
   // host copies for decoding

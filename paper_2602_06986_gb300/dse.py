@@ -57,6 +57,8 @@ FLAG_TIMING = 1
 FLAG_DEDUP = 2
 FLAG_DIRECT = 4
 FLAG_TIMING_MAIN = 8
+# dse_stats.binary_path
+PATH_CUDA_CORE, PATH_TENSOR, PATH_GRAM, PATH_GRAM_MT = 1, 2, 3, 4
 
 
 class Stats(C.Structure):
@@ -64,7 +66,7 @@ class Stats(C.Structure):
                 ("buffered", C.c_int64), ("escalated", C.c_int64), ("rescored", C.c_int64),
                 ("reruns", C.c_int32), ("precision_used", C.c_int32), ("max_err_bound", C.c_double),
                 ("valid_by_group", C.c_int64 * 3), ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64),
-                ("redundant", C.c_int64), ("dedup_rounds", C.c_int32), ("reserved1", C.c_int32)]
+                ("redundant", C.c_int64), ("dedup_rounds", C.c_int32), ("binary_path", C.c_int32)]
 
 
 class Expr(C.Structure):
@@ -258,7 +260,7 @@ def _stats_dict(s) -> dict:
                 "rescored": s.rescored, "reruns": s.reruns, "precision_used": s.precision_used,
                 "max_err_bound": s.max_err_bound, "valid_by_group": list(s.valid_by_group),
             "kernel_ms": list(s.kernel_ms), "kernel_launches": s.kernel_launches,
-            "redundant": s.redundant, "dedup_rounds": s.dedup_rounds}
+            "redundant": s.redundant, "dedup_rounds": s.dedup_rounds, "binary_path": s.binary_path}
 
 
 class Batch:

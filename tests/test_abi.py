@@ -102,7 +102,8 @@ def test_binding_constants_match_header(dse):
     text = open(HEADER).read()
     defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define DSE_(\w+) (\d+)", text)}
     enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"DSE_(\w+) = (\d+)", text)}
-    for name in ("FLAG_TIMING", "FLAG_DEDUP", "FLAG_DIRECT", "FLAG_TIMING_MAIN"):
+    for name in ("FLAG_TIMING", "FLAG_DEDUP", "FLAG_DIRECT", "FLAG_TIMING_MAIN", "PATH_CUDA_CORE", "PATH_TENSOR",
+                 "PATH_GRAM", "PATH_GRAM_MT"):
         assert getattr(dse, name) == defines[name], name
     for name in ("PREC_FP32", "PREC_FP64"):
         assert getattr(dse, name) == enums[name], name

@@ -70,16 +70,39 @@ def check_intervals(env, sp, orc, Y, b, e, **kw):
     return int(valid.sum()) * T, float(np.max(err / np.maximum(eps, 1e-300)))
 
 
-def test_intervals_tensor_core_16_targets(env):
+@pytest.mark.parametrize("flags", [0, 4])
+def test_intervals_tensor_core_16_targets(env, flags):
+    """N = 20000, 16 targets: the multi-target Gram contraction (40 drained
+    accumulation blocks) and, with DSE_FLAG_DIRECT, the sample-by-sample
+    tensor-core kernel."""
     torch, oracle, dse, W = env
     w = W.large(0, n_targets=16)
     sp, orc = spaces(env, w)
     n_checked = 0
     # unary block and the first pairs; a slice deep in the pair block
     for b, e in ((sp.n_stored, sp.n_stored + 6000), (sp.n_stored + 3_456_789, sp.n_stored + 3_466_789)):
-        n, worst = check_intervals(env, sp, orc, w["Y"], b, e, precision=dse.PREC_AUTO)
+        n, worst = check_intervals(env, sp, orc, w["Y"], b, e, precision=dse.PREC_AUTO, flags=flags)
         n_checked += n
     assert n_checked > 50_000
+    sp.free()
+
+
+@pytest.mark.parametrize("T,N", [(2, 100), (7, 530), (16, 1000)])
+def test_intervals_gram_multi_target(env, T, N):
+    """The multi-target Gram contraction at a few target counts and sample
+    counts: one accumulation block (N = 100), a ragged second block of one
+    chunk (N = 530 = 16 chunks + 18 samples), two full blocks (N = 1000)."""
+    torch, oracle, dse, W = env
+    w = W.medium(3)
+    w = dict(w, X=np.ascontiguousarray(w["X"][:, :N]))
+    rng = np.random.default_rng(T * 1000 + N)
+    X = w["X"]
+    Y = np.stack([X[rng.integers(len(X))] * X[rng.integers(len(X))] / X[rng.integers(len(X))]
+                  + 0.05 * rng.standard_normal(N) for _ in range(T)])
+    sp, orc = spaces(env, w)
+    b, e = sp.n_stored, min(sp.n_total, sp.n_stored + 60_000)
+    n, worst = check_intervals(env, sp, orc, Y, b, e, precision=dse.PREC_BF16X3)
+    assert n > 10_000
     sp.free()
 
 

@@ -131,15 +131,19 @@ def test_large_subrange_exact(env):
 
 def test_large_full(env):
     """The full large workload: N=20000, 16 targets, top-10000 per target,
-    on the CUDA-core FP32 kernels and on the tensor-core path (the bench's
-    default), each checked against the same exact oracle slices."""
+    on the CUDA-core FP32 kernels, the multi-target Gram contraction (the
+    bench's default) and the sample-by-sample tensor-core kernel, each
+    checked against the same exact oracle slices."""
     torch, oracle, dse, W = env
     w = W.large(0, n_targets=16)
     sp, orc = _spaces(env, w)
     Yd = torch.from_numpy(w["Y"]).cuda()
     results = {"fp32": sp.screen(Yd, w["k"], precision=dse.PREC_FP32),
-               "bf16x3": sp.screen(Yd, w["k"], precision=dse.PREC_AUTO)}
+               "bf16x3": sp.screen(Yd, w["k"], precision=dse.PREC_AUTO),
+               "bf16x3_direct": sp.screen(Yd, w["k"], precision=dse.PREC_AUTO, flags=dse.FLAG_DIRECT)}
     assert results["bf16x3"].stats()["precision_used"] == dse.PREC_BF16X3
+    assert results["bf16x3"].stats()["binary_path"] == dse.PATH_GRAM_MT
+    assert results["bf16x3_direct"].stats()["binary_path"] == dse.PATH_TENSOR
     rng = np.random.default_rng(2)
     a = int(rng.integers(sp.n_stored, sp.n_total - 1_000_000))
     slices = [(a, a + 1_000_000)] + _dense_slices(results["bf16x3"], 16, 0, sp.n_total, 1 << 19, 1)

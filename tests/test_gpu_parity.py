@@ -132,10 +132,13 @@ def test_multi_target(env, T, mode):
     assert res.stats()["reasons"] == ocnt
 
 
-@pytest.mark.parametrize("wname,T", [("tiny", 17), ("tiny", 40), ("medium", 8), ("medium", 33)])
-def test_tensor_core_multi_target(env, wname, T):
-    """BF16x3 tcgen05 contraction (one TMEM block at N=100, drained blocks at
-    N=1000) against the oracle, per target."""
+@pytest.mark.parametrize("wname,T,flags", [("tiny", 17, 0), ("tiny", 40, 0), ("medium", 8, 4), ("medium", 33, 0),
+                                           ("tiny", 3, 0), ("tiny", 16, 0), ("medium", 8, 0), ("medium", 16, 0)])
+def test_tensor_core_multi_target(env, wname, T, flags):
+    """BF16x3 tcgen05 contractions against the oracle, per target: the
+    sample-by-sample kernel (one TMEM block at N=100, drained blocks at
+    N=1000; above 16 targets, or with DSE_FLAG_DIRECT) and the multi-target
+    Gram kernel (2..16 targets)."""
     torch, oracle, dse, W = env
     w = getattr(W, wname)(7)
     X = w["X"]
@@ -145,9 +148,10 @@ def test_tensor_core_multi_target(env, wname, T):
                   + 0.05 * rng.standard_normal(N) for _ in range(T)])
     sp, orc = spaces(env, w)
     k = 50
-    res = sp.screen(torch.from_numpy(Y).cuda(), k, precision=dse.PREC_BF16X3)
+    res = sp.screen(torch.from_numpy(Y).cuda(), k, precision=dse.PREC_BF16X3, flags=flags)
     st = res.stats()
     assert st["precision_used"] == dse.PREC_BF16X3
+    assert st["binary_path"] == (dse.PATH_GRAM_MT if T <= 16 and not flags else dse.PATH_TENSOR)
     oids, osc, ocnt = orc.screen(Y, k)
     assert st["reasons"] == ocnt
     for l in range(T):
@@ -179,6 +183,50 @@ def test_ranges_merge_to_full(env):
     sc = np.concatenate([p[1] for p in parts])
     order = np.lexsort((ids, -sc))[:50]
     assert np.array_equal(ids[order], full[0])
+
+
+def test_gram_multi_target_ranges_and_edges(env):
+    """Multi-target Gram path (4 targets): disjoint ragged id ranges (one of
+    a single binary candidate, one empty) merge to the full screen list by
+    list with the oracle's counts; k = 1 and k above the valid count."""
+    torch, oracle, dse, W = env
+    w = W.tiny(5)
+    sp, orc = spaces(env, w)
+    rng = np.random.default_rng(4)
+    N = w["X"].shape[1]
+    Y = np.stack([w["Y"][0] + 0.2 * rng.standard_normal(N) for _ in range(4)])
+    Yd = torch.from_numpy(Y).cuda()
+    full = sp.screen(Yd, 40, precision=dse.PREC_BF16X3)
+    assert full.stats()["binary_path"] == dse.PATH_GRAM_MT
+    b0 = sp.n_stored + 6 * 100  # inside the binary block of the tiny space
+    cuts = [0, 37, b0, b0 + 1, b0 + 1, 7777, 20011, sp.n_total]
+    parts = [[] for _ in range(4)]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        r = sp.screen(Yd, 40, id_begin=a, id_end=b, precision=dse.PREC_BF16X3)
+        st = r.stats()
+        assert st["screened"] == b - a
+        oi, os_, oc = orc.screen(Y, 40, id_begin=a, id_end=b)
+        assert st["reasons"] == oc, (a, b)
+        for l in range(4):
+            parts[l].append(r.fetch(l))
+            check_list(*parts[l][-1], oi[l], os_[l], orc, Y, l)
+    for l in range(4):
+        ids = np.concatenate([p[0] for p in parts[l]])
+        sc = np.concatenate([p[1] for p in parts[l]])
+        order = np.lexsort((ids, -sc))[:40]
+        assert np.array_equal(ids[order], full.fetch(l)[0]), l
+    # k = 1 and k above the number of valid candidates
+    r = sp.screen(Yd, 1, precision=dse.PREC_BF16X3)
+    oi, os_, oc = orc.screen(Y, 1)
+    for l in range(4):
+        ids, sc, eb = r.fetch(l)
+        assert abs(sc[0] - os_[l][0]) <= TOL * os_[l][0]
+    r = sp.screen(Yd, 10 ** 6, id_begin=b0, id_end=b0 + 3000, precision=dse.PREC_BF16X3)
+    oi, os_, oc = orc.screen(Y, 10 ** 6, id_begin=b0, id_end=b0 + 3000)
+    for l in range(4):
+        ids, sc, eb = r.fetch(l)
+        assert len(ids) == oc["valid"] == len(oi[l])
+        check_list(ids, sc, eb, oi[l], os_[l], orc, Y, l)
 
 
 def test_edge_cases(env):

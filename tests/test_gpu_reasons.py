@@ -99,19 +99,23 @@ def test_reasons_medium_fp64(env):
     sp.free()
 
 
-def test_reasons_tensor_core_targets(env):
-    """Sixteen targets on the tensor-core path: the large workload's signed
-    and lognormal primaries (domain masks fire), a 2e5-id slice of its pair
-    block, and the precision primaries at rung 2."""
+@pytest.mark.parametrize("flags", [0, 4])
+def test_reasons_tensor_core_targets(env, flags):
+    """Sixteen targets on the multi-target Gram path (and, with
+    DSE_FLAG_DIRECT, the sample-by-sample tensor-core kernel): the large
+    workload's signed and lognormal primaries (domain masks fire), a 2e5-id
+    slice of its pair block, and the precision primaries at rung 2."""
     torch, oracle, dse, W = env
+    path = dse.PATH_TENSOR if flags else dse.PATH_GRAM_MT
     w = W.large(0, n_targets=16)
     sp, orc = spaces(env, w)
     # the unary block (sqrt and log of signed features fail their domain)
     # with the first pairs, then a slice deep in the pair block
     for b, e in ((sp.n_stored, sp.n_stored + 40_000), (sp.n_stored + 1_234_567, sp.n_stored + 1_434_567)):
         ref = orc.reasons(b, e)
-        got, st = gpu_reasons(env, sp, w["Y"], 100, id_begin=b, id_end=e, precision=dse.PREC_AUTO)
+        got, st = gpu_reasons(env, sp, w["Y"], 100, id_begin=b, id_end=e, precision=dse.PREC_AUTO, flags=flags)
         assert st["precision_used"] == dse.PREC_BF16X3
+        assert st["binary_path"] == path
         check_equal(got, ref, st)
         assert np.sum(ref == 1) > 0 and np.sum(ref == 0) > 0
         if b == sp.n_stored:
@@ -119,9 +123,29 @@ def test_reasons_tensor_core_targets(env):
     sp.free()
     w = dict(W.precision(0, n_targets=16), max_rung=2)
     sp, orc = spaces(env, w)
-    got, st = gpu_reasons(env, sp, w["Y"], 100, precision=dse.PREC_AUTO)
+    got, st = gpu_reasons(env, sp, w["Y"], 100, precision=dse.PREC_AUTO, flags=flags)
+    assert st["binary_path"] == path
     check_equal(got, orc.reasons(), st)
     sp.free()
+
+
+@pytest.mark.parametrize("T", [2, 9])
+def test_reasons_gram_multi_target_units(env, T):
+    """The multi-target Gram path on the tiny workload, whose + and - are
+    unit-checked (the kernel's own unit test of the sum and difference
+    slots) and whose primaries are few enough for every candidate."""
+    torch, oracle, dse, W = env
+    for seed in (0, 1):
+        w = W.tiny(seed)
+        rng = np.random.default_rng(seed + 10 * T)
+        Y = np.stack([w["Y"][0] + 0.3 * rng.standard_normal(w["X"].shape[1]) for _ in range(T)])
+        sp, orc = spaces(env, w)
+        got, st = gpu_reasons(env, sp, Y, 30, precision=dse.PREC_BF16X3)
+        assert st["binary_path"] == dse.PATH_GRAM_MT
+        ref = orc.reasons()
+        check_equal(got, ref, st)
+        assert np.sum(ref == 0) > 0
+        sp.free()
 
 
 @pytest.mark.parametrize("seed", [0, 1])

@@ -75,24 +75,27 @@ def test_single_target_settings(env, settings):
     sp.free()
 
 
-@pytest.mark.parametrize("settings", [{"tile_group": 2, "seed_stride": 32}, {"tc_min_targets": 32}])
-def test_multi_target_settings(env, settings):
-    """16 targets: the tensor-core path under other tile settings, and the
-    CUDA-core path (tc_min_targets above 16) against it."""
+@pytest.mark.parametrize("settings,flags", [({"tile_group": 2, "seed_stride": 32}, 4), ({"tc_min_targets": 32}, 0)])
+def test_multi_target_settings(env, settings, flags):
+    """16 targets: the sample-by-sample tensor-core kernel (DSE_FLAG_DIRECT)
+    under other tile settings; the CUDA-core path (tc_min_targets above 16)
+    against the default multi-target Gram screen."""
     torch, oracle, dse, W = env
     w = W.large(0, n_targets=16)
     sp = _space(env, w)
     b, e = sp.n_stored + 1_000_000, sp.n_stored + 1_600_000
     dse.set_tuning(None)
-    ref = _lists(env, sp, w["Y"], 200, id_begin=b, id_end=e, precision=dse.PREC_AUTO)
+    ref = _lists(env, sp, w["Y"], 200, id_begin=b, id_end=e, precision=dse.PREC_AUTO, flags=flags)
     assert ref[1]["precision_used"] == dse.PREC_BF16X3
+    assert ref[1]["binary_path"] == (dse.PATH_TENSOR if flags else dse.PATH_GRAM_MT)
     dse.set_tuning(settings)
     try:
-        got = _lists(env, sp, w["Y"], 200, id_begin=b, id_end=e, precision=dse.PREC_AUTO)
+        got = _lists(env, sp, w["Y"], 200, id_begin=b, id_end=e, precision=dse.PREC_AUTO, flags=flags)
     finally:
         dse.set_tuning(None)
     if "tc_min_targets" in settings:
         assert got[1]["precision_used"] == dse.PREC_FP32
+        assert got[1]["binary_path"] == dse.PATH_CUDA_CORE
     _same(ref, got)
     sp.free()
 
