@@ -8,10 +8,11 @@ normal), units over 5 base dimensions, the full operator library, rung 2
 (19.2 M candidate ids), 16 residual targets, top-10000 per target.  One step
 = one pass of the whole hot path over it: build the feature space (rung 1
 materialised on the device, masks, summaries), then the SIS screen of every
-candidate against the 16 targets (unit check, a-priori and realised masks,
-FP32 evaluation, the BF16x3 tensor-core contraction of the numerators,
-streaming top-k, exact selection with the FP32-pair / FP64 re-score of the
-boundary).  Inputs are resident in HBM when the timed region starts; L2 is
+candidate against the 16 targets (unit check, a-priori and realised masks;
+a*b, a/b, b/a, a+b, a-b from the multi-target Gram contraction on the
+tensor cores, BF16x3 with FP32 bounds; stored, unary and |a-b| candidates
+evaluated in FP32 on the CUDA cores; streaming top-k, exact selection with
+the FP32-pair / FP64 re-score of the boundary).  Inputs are resident in HBM when the timed region starts; L2 is
 flushed (256 MiB write) between steps.
 
 Metric: SIS-screened candidate features per second (valid candidates, each
@@ -24,6 +25,8 @@ merged after one NCCL all-gather (strong scaling: the total work is fixed).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dse|reference]
     python bench.py --workload medium      # N=1000 residual loop D=1..3 (separate line)
     python bench.py --workload batched     # 256-problem batched screen (separate line)
+    python bench.py --workload gmt_small   # the default workload's first 4096 samples,
+                                           # screen only (a small case for profiling)
 """
 from __future__ import annotations
 
@@ -293,7 +296,11 @@ def bench_multi_target(args, which):
     w = W.precision(0, n_targets=64) if which in ("precision", "tc_small") else W.large(0, n_targets=16)
     if which == "tc_small":  # the precision primaries at rung 2: a small case of the same kernels
         w = dict(w, max_rung=2, name="precision_primaries_rung2_T64_top1000")
-    sp = dse.Space(torch.from_numpy(w["X"]).cuda(), w["units"], w["op_mask"], w["max_rung"],
+    if which == "gmt_small":  # the large workload's first 4096 samples: a small case of its kernels
+        w = dict(w, X=np.ascontiguousarray(w["X"][:, :4096]), Y=np.ascontiguousarray(w["Y"][:, :4096]),
+                 name="large_first4096_samples_rung2_T16_top10000")
+    Xd = torch.from_numpy(w["X"]).cuda()
+    sp = dse.Space(Xd, w["units"], w["op_mask"], w["max_rung"],
                    unit_check_addsub=w["unit_check_addsub"], explog_dimensionless=w["explog_dimensionless"])
     Yd = torch.from_numpy(w["Y"]).cuda()
     T, N = w["Y"].shape
@@ -339,17 +346,22 @@ def bench_multi_target(args, which):
     mhz, _ = peaks()
     alu_peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
     alu = 6.0 * N * tc_valid / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    roofline = {"bound": "tensor", "kernel": "k_pair_tc (BF16x3 tcgen05)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                "traffic": None, "peak_source": peak_src, "flops_per_candidate_sample": 6 * T,
+                "launch_ms_total_per_step": tc_ms / args.steps,
+                "alu_lane_ops_tps": alu, "alu_frac": alu / alu_peak if alu else None}
+    if stats[0]["binary_path"] == dse.PATH_GRAM_MT:
+        roofline = gmt_roofline(dse, w, Xd, None, sum(s["kernel_ms"][1] for s in stats) / len(stats),
+                                tot / args.steps, peak, peak_src)
+        roofline["traffic"] = None
     line = {"metric": f"{which}: SIS-screened candidate features/sec (multi-target, tensor cores)",
             "value": cands / (tot * 1e-3), "unit": "candidates/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "dtype": "f32+bf16x3",
             "data": "synthetic", "config": {"workload": w["name"], "targets": T, "N": N, "k": w["k"],
                                             "screened_ids": stats[0]["screened"], "l2": "flushed between steps"},
             "evals_per_s": cands * N / (tot * 1e-3), "precision_used": stats[0]["precision_used"],
-            "roofline": {"bound": "tensor", "kernel": "k_pair_tc (BF16x3 tcgen05)", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
-                         "traffic": None, "peak_source": peak_src, "flops_per_candidate_sample": 6 * T,
-                         "launch_ms_total_per_step": tc_ms / args.steps,
-                         "alu_lane_ops_tps": alu, "alu_frac": alu / alu_peak if alu else None},
+            "binary_path": stats[0]["binary_path"], "roofline": roofline,
             "per_screen": {k2: sum(s[k2] for s in stats) / len(stats)
                            for k2 in ("evaluated", "buffered", "escalated", "rescored", "reruns")},
             "kernel_group_ms_per_step": [sum(s["kernel_ms"][g] for s in stats) / len(stats) for g in range(4)],
@@ -491,6 +503,68 @@ def oracle_large_space(w):
                         explog_dimensionless=w["explog_dimensionless"])
 
 
+def binary_pairs(sp, max_rung):
+    """Pairs (i, j), j < i, of the binary block of the last rung: i among the
+    features of rung max_rung - 1 (ids from o), j any stored feature."""
+    n = sp.n_stored
+    o = sum(sp.counts(r)[1]["valid"] for r in range(max_rung - 1))
+    return n * (n - 1) // 2 - o * (o - 1) // 2
+
+
+# contraction entries per ordered pair and sample of the multi-target Gram
+# kernel at T targets: H (q y_t of x and of 1/x) and G (p q, p q^2, p^2 q,
+# p^2 q^2 of both families); 2 flops each, 3 BF16 products each (BF16x3)
+def gmt_flops_per_ordered_pair_sample(T):
+    return (2 * T + 8) * 2 * 3
+
+
+def gmt_roofline(dse, w, Xd, stream, launch_ms, step_ms, tc_peak, tc_src):
+    """Roofline of k_pair_gmt: algorithmic flops = the contraction entries
+    the method needs for every ordered pair of the binary block (both orders:
+    a/b and b/a) x N samples; time = the kernel's CUDA events in the timed
+    steps."""
+    T, N = w["Y"].shape
+    sp = large_space(dse, w, Xd, stream)
+    pairs = binary_pairs(sp, w["max_rung"])
+    sp.free()
+    fl = gmt_flops_per_ordered_pair_sample(T)
+    flops = 2.0 * pairs * N * fl
+    achieved = flops / (launch_ms * 1e-3) / 1e12 if launch_ms > 0 else None
+    return {"bound": "tensor",
+            "kernel": "k_pair_gmt (multi-target Gram contraction, BF16x3 tcgen05: a/b, b/a, a*b, a+b, a-b)",
+            "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+            "frac": achieved / tc_peak if achieved else None,
+            "traffic": profiled_traffic("k_pair_gmt_large.txt"),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                              "(profiles/k_pair_gmt_large.txt)",
+            "peak_source": tc_src + " (of measured, sustained: the kernel runs inside a long step)",
+            "flops_per_ordered_pair_sample": fl, "ordered_pairs": 2 * pairs, "flops_per_launch": flops,
+            "launch_ms": launch_ms, "share_of_step": launch_ms / step_ms}
+
+
+def tc_roofline(T, N, mul_ms, mul_valid, step_ms, stats, tc_peak, tc_src):
+    """Roofline of k_pair_tc (sample-by-sample generation on the FP32 pipes,
+    numerators on the tensor cores): the FP32 ALU bound, with the tensor
+    fraction beside it."""
+    mhz, clk_src = peaks()
+    alu_peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
+    ntp = 16 if T <= 16 else 32 if T <= 32 else 64
+    alu = TC_ALU_OPS_PER_EVAL * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
+    tc_flops = 6.0 * ntp * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
+    return {"bound": "alu", "kernel": f"k_pair_tc<KIND_MUL,{ntp}> (a*b, a/b, b/a; BF16x3 tcgen05 numerators)",
+            "achieved": alu, "peak": alu_peak, "unit": "T fp32-lane-ops/s",
+            "frac": alu / alu_peak if alu else None,
+            "traffic": profiled_traffic("k_pair_tc_large.txt"),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                              "(profiles/k_pair_tc_large.txt)",
+            "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({clk_src})",
+            "ops_per_candidate_sample": TC_ALU_OPS_PER_EVAL, "valid_candidates_per_launch": mul_valid / len(stats),
+            "launch_ms": mul_ms / len(stats), "share_of_step": mul_ms / sum(step_ms),
+            "tensor": {"achieved": tc_flops, "peak": tc_peak, "unit": "TFLOP/s",
+                       "frac": tc_flops / tc_peak if tc_flops else None,
+                       "flops_per_candidate_sample": 6 * ntp, "peak_source": tc_src + " (of measured)"}}
+
+
 def bench_large(args):
     from paper_2602_06986_gb300 import workloads as W
 
@@ -501,7 +575,8 @@ def bench_large(args):
     k = w["k"]
     T, N = w["Y"].shape
     config = {"workload": w["name"], "N": N, "n_primary": int(w["X"].shape[0]), "max_rung": w["max_rung"],
-              "targets": T, "k": k, "precision": "FP32 evaluation + BF16x3 tcgen05 numerators (AUTO)",
+              "targets": T, "k": k, "precision": "AUTO: binary slots from BF16x3 tcgen05 Gram contractions (FP32 bounds), "
+                                                 "stored/unary and |a-b| on FP32 CUDA cores",
               "l2": "flushed between steps (256 MiB write); stored FP32 rows 0.2 GB > L2",
               "parallelism": ("one GPU" if world == 1 else
                               f"id-range split over {world} ranks + NCCL all-gather of the top-k lists")}
@@ -574,7 +649,10 @@ def bench_large(args):
         from paper_2602_06986_gb300 import autotune as at
 
         sp_t = large_space(dse, w, Xd, stream)
-        entry = at.tune("screen_tc", N, T, lambda: sp_t.screen(Yd, k, precision=dse.PREC_AUTO, stream=stream).free(),
+        r_t = sp_t.screen(Yd, k, precision=dse.PREC_AUTO, stream=stream)
+        kclass = "screen_gmt" if r_t.stats()["binary_path"] == dse.PATH_GRAM_MT else "screen_tc"
+        r_t.free()
+        entry = at.tune(kclass, N, T, lambda: sp_t.screen(Yd, k, precision=dse.PREC_AUTO, stream=stream).free(),
                         reps=2)
         sp_t.free()
         chosen = entry["config"]
@@ -583,7 +661,7 @@ def bench_large(args):
             torch.distributed.broadcast_object_list(obj, src=0)
             chosen = obj[0]
         dse.set_tuning(chosen or None)
-        tuning = {"kernel_class": at.key("screen_tc", N, T), "chosen": chosen or "defaults",
+        tuning = {"kernel_class": at.key(kclass, N, T), "chosen": chosen or "defaults",
                   "in_effect": dse.get_tuning(),
                   "tried_ms": [[t["config"], round(t["seconds"] * 1e3, 2)] for t in entry["tried"]]}
     for _ in range(args.warmup):
@@ -621,29 +699,15 @@ def bench_large(args):
         cands = cands_local
     value = cands / (tot_ms * 1e-3)
 
-    # dominant kernel: the product/quotient group on the tensor cores
-    # (k_pair_tc, a*b, a/b, b/a), live CUDA events in the timed steps
+    # dominant kernel: the binary slots' group on the tensor cores, live
+    # CUDA events in the timed steps
     mul_ms = sum(s["kernel_ms"][1] for s in stats)
     mul_valid = sum(s["valid_by_group"][1] for s in stats)
-    mhz, clk_src = peaks()
-    alu_peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
-    ntp = 16 if T <= 16 else 32 if T <= 32 else 64
-    alu = TC_ALU_OPS_PER_EVAL * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
     tc_peak, tc_src = measured_bf16("bf16_tflops_sustained")
-    tc_flops = 6.0 * ntp * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
-    roofline = {"bound": "alu", "kernel": f"k_pair_tc<KIND_MUL,{ntp}> (a*b, a/b, b/a; BF16x3 tcgen05 numerators)",
-                "achieved": alu, "peak": alu_peak, "unit": "T fp32-lane-ops/s",
-                "frac": alu / alu_peak if alu else None,
-                "traffic": profiled_traffic("k_pair_tc_large.txt"),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
-                                  "(profiles/k_pair_tc_large.txt)",
-                "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({clk_src})",
-                "ops_per_candidate_sample": TC_ALU_OPS_PER_EVAL, "valid_candidates_per_launch": mul_valid / len(stats),
-                "launch_ms": mul_ms / len(stats), "share_of_step": mul_ms / sum(step_ms),
-                "tensor": {"achieved": tc_flops, "peak": tc_peak, "unit": "TFLOP/s",
-                           "frac": tc_flops / tc_peak if tc_flops else None,
-                           "flops_per_candidate_sample": 6 * ntp, "peak_source": tc_src + " (of measured)"}}
-
+    if stats[0].get("binary_path") == dse.PATH_GRAM_MT:
+        roofline = gmt_roofline(dse, w, Xd, stream, mul_ms / len(stats), sum(step_ms) / len(stats), tc_peak, tc_src)
+    else:
+        roofline = tc_roofline(T, N, mul_ms, mul_valid, step_ms, stats, tc_peak, tc_src)
     # the kernel groups' device times from one more (untimed) step with an
     # event at every group boundary
     flush.zero_()
@@ -738,7 +802,7 @@ def main():
     ap.add_argument("--impl", default="dse", choices=["dse", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "medium", "batched", "precision", "large_screen", "tc_small", "l0"])
+                    choices=["large", "medium", "batched", "precision", "large_screen", "tc_small", "gmt_small", "l0"])
     ap.add_argument("--cpu-ids", type=int, default=1_000_000,
                     help="contiguous candidate ids the oracle screens for the cpu_baseline of the large workload")
     ap.add_argument("--ref-ids", type=int, default=100_000,
@@ -751,7 +815,7 @@ def main():
         return bench_large(args)
     if args.workload == "batched":
         return bench_batched(args)
-    if args.workload in ("precision", "large_screen", "tc_small"):
+    if args.workload in ("precision", "large_screen", "tc_small", "gmt_small"):
         return bench_multi_target(args, "large" if args.workload == "large_screen" else args.workload)
     if args.workload == "l0":
         return bench_l0(args)

@@ -27,6 +27,9 @@ import statistics
 CANDIDATES = {
     # tensor-core multi-target screen (product/quotient tiles)
     "screen_tc": {"tile_group": [2, 4, 8, 16], "seed_stride": [32, 64, 128]},
+    # multi-target Gram screen: whether 2..16 targets take it (8) or the
+    # CUDA-core kernels (17)
+    "screen_gmt": {"tc_min_targets": [8, 17]},
     # CUDA-core screens (one target, or sample by sample)
     "screen_cc": {"tile_group": [1, 2, 4, 8]},
     # one target with 16 <= N <= 2048: Gram contraction (2048) or direct (16)
