@@ -474,7 +474,11 @@ typedef struct {
                                 many targets, 1..4096 (8)                     */
   int32_t batch_job_samples; /* batched screens: candidate-samples per job,
                                 1024..2^20 (16384)                           */
-  int32_t reserved[3];
+  int32_t gmt_group;         /* multi-target Gram tiles: a-blocks (128
+                                features each) per group of the tile order
+                                (the b-blocks are swept once per group),
+                                1..4096 (2)                                  */
+  int32_t reserved[2];
 } dse_tuning;
 
 /* Installs t (NULL: every default).  DSE_EINVAL for a value outside its

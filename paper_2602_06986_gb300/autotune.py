@@ -5,7 +5,8 @@ screen is cut and ordered, not what is computed (dse_set_tuning): the number
 of i-blocks per group of pair tiles (which tiles run side by side and share
 operand rows in L2), the stride of the seed tiles launched first, the largest
 N for the product Gram contraction, the number of targets from which the
-tensor cores are used, and the work per job of a batched screen.  This module
+tensor cores are used, the work per job of a batched screen, and the
+a-blocks per group of the multi-target Gram kernel's tile order.  This module
 times candidate values on the device for a workload class and keeps the
 fastest in a JSON cache keyed by (kernel, N bucket, T bucket); ``apply``
 installs the cached choice before a screen of that class.
@@ -27,9 +28,9 @@ import statistics
 CANDIDATES = {
     # tensor-core multi-target screen (product/quotient tiles)
     "screen_tc": {"tile_group": [2, 4, 8, 16], "seed_stride": [32, 64, 128]},
-    # multi-target Gram screen: whether 2..16 targets take it (8) or the
-    # CUDA-core kernels (17)
-    "screen_gmt": {"tc_min_targets": [8, 17]},
+    # multi-target Gram screen: a-blocks per group of its tile order, and
+    # whether 2..16 targets take it (8) or the CUDA-core kernels (17)
+    "screen_gmt": {"gmt_group": [1, 5, 4096], "tc_min_targets": [8, 17]},
     # CUDA-core screens (one target, or sample by sample)
     "screen_cc": {"tile_group": [1, 2, 4, 8]},
     # one target with 16 <= N <= 2048: Gram contraction (2048) or direct (16)

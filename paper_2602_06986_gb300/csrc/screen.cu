@@ -231,6 +231,43 @@ __device__ __forceinline__ EvalErr<R> unary_err(const FeatTable &F, int op, int6
 // One candidate of the stored/unary group (whole warp, lanes over samples):
 // index w < nid is stored id id0 + w, otherwise unary flat index
 // p0 + (w - nid) of rung k.
+// Candidate w of the stored/unary group (stored ids [id0, id0 + nid), then
+// unary flat indices from p0): its id, op and operand, and its a-priori
+// reason (unit: exp/log need a dimensionless operand; complexity; rules;
+// domain; magnitude).
+__device__ __forceinline__ int feature_setup(const ScreenArgs &A, uint64_t w, uint64_t id0, uint64_t nid,
+                                             uint64_t p0, uint64_t *gid_out, int *op_out, int64_t *f_out) {
+  int op;
+  int64_t f;
+  uint64_t gid;
+  int reason = DSE_VALID;
+  if (w < nid) {
+    gid = id0 + w;
+    f = (int64_t)gid;
+    op = DSE_OP_PRIMARY;
+  } else {
+    uint64_t p = p0 + (w - nid);
+    gid = (uint64_t)A.n_stored + p;
+    int64_t b;
+    decode_flat(A.G, p, &op, &f, &b);
+    if ((op == DSE_OP_EXP || op == DSE_OP_LOG) && A.explog_dimensionless && !(A.F.flags[f] & F_DIMLESS))
+      reason = DSE_R_UNIT;
+    else if (A.max_complexity > 0 && A.F.cplx[f] + 1 > A.max_complexity)
+      reason = DSE_R_COMPLEXITY;
+    else if (rule_fails(A.F, op, f, -1))
+      reason = DSE_R_COMPLEXITY;
+    else {
+      double ea = (op == DSE_OP_EXP && (A.F.flags[f] & F_EXP_MAG)) ? INFINITY : -INFINITY;
+      reason = domain_magnitude64(op, A.F.min64[f], A.F.max64[f], A.F.minabs64[f], A.F.maxabs64[f], 0.0, 0.0,
+                                  A.fmax64, ea);
+    }
+  }
+  *gid_out = gid;
+  *op_out = op;
+  *f_out = f;
+  return reason;
+}
+
 template <typename R, int NT>
 __device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, uint64_t id0, uint64_t nid,
                                              uint64_t p0, R gamma, const R *ysum, LaneStats &ls) {
@@ -245,29 +282,7 @@ __device__ __forceinline__ void feature_cand(const ScreenArgs &A, uint64_t w, ui
   int op;
   int64_t f;
   uint64_t gid;
-  int reason = DSE_VALID;
-  if (w < nid) {
-    gid = id0 + w;
-    f = (int64_t)gid;
-    op = DSE_OP_PRIMARY;
-  } else {
-    uint64_t p = p0 + (w - nid);
-    gid = (uint64_t)A.n_stored + p;
-    int64_t b;
-    decode_flat(A.G, p, &op, &f, &b);
-    // unit (exp/log need a dimensionless operand), complexity, domain, magnitude
-    if ((op == DSE_OP_EXP || op == DSE_OP_LOG) && A.explog_dimensionless && !(A.F.flags[f] & F_DIMLESS))
-      reason = DSE_R_UNIT;
-    else if (A.max_complexity > 0 && A.F.cplx[f] + 1 > A.max_complexity)
-      reason = DSE_R_COMPLEXITY;
-    else if (rule_fails(A.F, op, f, -1))
-      reason = DSE_R_COMPLEXITY;
-    else {
-      double ea = (op == DSE_OP_EXP && (A.F.flags[f] & F_EXP_MAG)) ? INFINITY : -INFINITY;
-      reason = domain_magnitude64(op, A.F.min64[f], A.F.max64[f], A.F.minabs64[f], A.F.maxabs64[f], 0.0, 0.0,
-                                  A.fmax64, ea);
-    }
-  }
+  const int reason = feature_setup(A, w, id0, nid, p0, &gid, &op, &f);
   if (reason != DSE_VALID) {
     if (lane == 0) {
       ls.r[reason]++;
@@ -367,6 +382,185 @@ __global__ void __launch_bounds__(256) k_feature(const ScreenArgs A, uint64_t id
   ls.zero();
   for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ncand; w += warps)
     feature_cand<R, NT>(A, w, id0, nid, p0, (R)gamma_lane, ysum, ls);
+  flush_stats(A, ls);
+}
+
+// Stored and unary candidates against 16 targets in FP32.  One warp per
+// candidate would read all 16 target rows from L2 for every candidate; here
+// a warp scores CW candidates at once and the block's 8 warps move through
+// the samples together: each 256-sample chunk of the targets is staged once
+// per block in shared memory, sample-major ([s][16], read with 16-byte
+// loads), double-buffered (the next chunk is loaded into registers while the
+// current one is used).  Each lane takes samples lane, lane + 32, ... in
+// order with the same blocking as k_feature, so the sums, bounds and
+// decisions are those of k_feature<float, 16>.
+constexpr int kF16Chunk = 256, kF16CW = 4;
+
+template <int CW>
+__global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64_t id0, uint64_t id1, uint64_t p0,
+                                                      uint64_t p1, float gamma_lane) {
+  constexpr int NT = 16, KS = kF16Chunk, WARPS = 8;
+  __shared__ __align__(16) float ys[2][KS][NT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t nid = id1 - id0, ncand = nid + (p1 - p0);
+  const uint64_t per_tile = (uint64_t)WARPS * CW;
+  const uint64_t n_tiles = (ncand + per_tile - 1) / per_tile;
+  const float u = 5.9604644775390625e-8f;
+  const int64_t Ns = A.N;
+  const int T = A.T, t0 = A.t0;
+  const int64_t ldy = A.ldy;
+  const float N = (float)Ns, invN = (float)A.invN, sqrtN = sqrtf(N);
+  const float fmin = (float)A.fmin_std_rel64, gamma = gamma_lane;
+  float ysum[NT];
+  load_ysum<float, NT>(A, ysum);
+  LaneStats ls;
+  ls.zero();
+  const int nchunk = (int)((Ns + KS - 1) / KS);
+  // staging: thread i takes sample i of a chunk, all 16 targets
+  auto load_chunk = [&](int ch, float (&r)[NT]) {
+    const int64_t s = (int64_t)ch * KS + threadIdx.x;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) r[t] = (s < Ns && t < T) ? A.y32[(int64_t)(t0 + t) * ldy + s] : 0.f;
+  };
+  auto store_chunk = [&](int buf, const float (&r)[NT]) {
+    float4 *d = reinterpret_cast<float4 *>(&ys[buf][threadIdx.x][0]);
+#pragma unroll
+    for (int q = 0; q < NT / 4; ++q) d[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  };
+  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    uint64_t gid[CW];
+    int op[CW];
+    const float *x[CW];
+    float c[CW];
+    bool act[CW];
+    EvalErr<float> ee[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+      const uint64_t w = tile * per_tile + (uint64_t)warp * CW + k;
+      act[k] = false;
+      gid[k] = 0;
+      op[k] = DSE_OP_PRIMARY;
+      x[k] = A.F.v32;
+      c[k] = 0.f;
+      ee[k] = EvalErr<float>{0.f, 0.f};
+      if (w >= ncand) continue;
+      int64_t f;
+      const int reason = feature_setup(A, w, id0, nid, p0, &gid[k], &op[k], &f);
+      if (reason != DSE_VALID) {
+        if (lane == 0) {
+          ls.r[reason]++;
+          note_why(A, gid[k], reason);
+        }
+      } else if (!(A.F.flags[f] & F_FP32_SAFE)) {
+        if (lane == 0) {
+          escalate(A, gid[k]);
+          ls.escalated++;
+        }
+      } else {
+        act[k] = true;
+        x[k] = A.F.v32 + f * A.F.ld;
+        c[k] = unary_eval<float>(op[k], x[k][0], 0.f);
+        ee[k] = unary_err<float>(A.F, op[k], f, c[k], sqrtN);
+      }
+    }
+    float S1[CW], S2[CW], o1[CW], o2[CW], Sy[CW][NT], oy[CW][NT];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+      S1[k] = S2[k] = o1[k] = o2[k] = 0.f;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) Sy[k][t] = oy[k][t] = 0.f;
+    }
+    int blk = 0;
+    {
+      float r[NT];
+      load_chunk(0, r);
+      __syncthreads();  // (the previous tile's last chunk is no longer read)
+      store_chunk(0, r);
+      __syncthreads();
+    }
+    for (int ch = 0; ch < nchunk; ++ch) {
+      float r[NT];
+      if (ch + 1 < nchunk) load_chunk(ch + 1, r);
+      const int buf = ch & 1;
+#pragma unroll 1
+      for (int j = 0; j < KS / 32; ++j) {
+        const int64_t s = (int64_t)ch * KS + lane + 32 * j;
+        if (s >= Ns) break;
+        float xv[CW];
+#pragma unroll
+        for (int k = 0; k < CW; ++k) xv[k] = act[k] ? x[k][s] : 0.f;
+        float yv[NT];
+        const float4 *yp = reinterpret_cast<const float4 *>(&ys[buf][lane + 32 * j][0]);
+#pragma unroll
+        for (int q = 0; q < NT / 4; ++q) {
+          const float4 y4 = yp[q];
+          yv[4 * q] = y4.x, yv[4 * q + 1] = y4.y, yv[4 * q + 2] = y4.z, yv[4 * q + 3] = y4.w;
+        }
+#pragma unroll
+        for (int k = 0; k < CW; ++k) {
+          if (!act[k]) continue;
+          const float v = unary_eval<float>(op[k], xv[k], c[k]);
+          S1[k] += v;
+          S2[k] = fmaf(v, v, S2[k]);
+#pragma unroll
+          for (int t = 0; t < NT; ++t)
+            if (t < T) Sy[k][t] = fmaf(v, yv[t], Sy[k][t]);
+        }
+        if (++blk == 16) {
+          blk = 0;
+#pragma unroll
+          for (int k = 0; k < CW; ++k) {
+            o1[k] += S1[k];
+            o2[k] += S2[k];
+            S1[k] = 0.f;
+            S2[k] = 0.f;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+              oy[k][t] += Sy[k][t];
+              Sy[k][t] = 0.f;
+            }
+          }
+        }
+      }
+      if (ch + 1 < nchunk) store_chunk(buf ^ 1, r);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+      if (!act[k]) continue;  // (warp-uniform)
+      float s1 = S1[k] + o1[k], s2 = S2[k] + o2[k], sy[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) sy[t] = Sy[k][t] + oy[k][t];
+      for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) sy[t] += __shfl_xor_sync(0xffffffffu, sy[t], o);
+      }
+      const CandInterval<float> ci = cand_interval<float>(s1, s2, N, invN, sqrtN, c[k], ee[k], gamma, u, fmin);
+      if (ci.realised == 0) {
+        if (lane == 0) {
+          ls.r[DSE_R_REALISED]++;
+          note_why(A, gid[k], DSE_R_REALISED);
+        }
+        continue;
+      }
+      if (ci.realised == 2) {
+        if (lane == 0) {
+          escalate(A, gid[k]);
+          ls.escalated++;
+        }
+        continue;
+      }
+      if (lane == 0) {
+        ls.r[DSE_VALID]++;
+        ls.evaluated++;
+        note_why(A, gid[k], DSE_VALID);
+      }
+      const unsigned pushed = score_and_push<float, NT>(A, lane == 0, gid[k], ci, s1, sy, invN, gamma, u, ysum);
+      refresh_pushed<NT>(A, pushed);
+    }
+  }
   flush_stats(A, ls);
 }
 
@@ -1218,6 +1412,13 @@ void launch_feature_t(const ScreenArgs &A, uint64_t id0, uint64_t id1, uint64_t 
   note_launches(1);
   ScreenArgs B = A;
   B.group = 0;
+  if (sizeof(R) == 4 && NT == 16) {
+    // 32 candidates per block, one block per SM at a time
+    uint64_t tiles = (ncand + 8 * kF16CW - 1) / (8 * kF16CW);
+    if (tiles > (uint64_t)sms) tiles = (uint64_t)sms;
+    k_feature16<kF16CW><<<(unsigned)tiles, 256, 0, st>>>(B, id0, id1, p0, p1, gamma);
+    return;
+  }
   k_feature<R, NT><<<(unsigned)blocks, 256, 0, st>>>(B, id0, id1, p0, p1, gamma);
 }
 

@@ -163,139 +163,150 @@ __global__ void __launch_bounds__(128) k_gmt_space(FeatTable F, int nchunks, uns
   acc.finish(sm, groups, c, ok, real ? gf + f : &tmp);
 }
 
-// Compensated FP32 pair (s, c) of another lane added into (s, c).
-__device__ __forceinline__ void comp_merge(Comp32 &a, float s, float c) {
-  a.add(s);
-  a.c += c;
+// The b-images are written a row group at a time: 8 rows x 32 samples of
+// one chunk part are 512 contiguous bytes, one 16-byte piece per lane (lane
+// = 8 k-group + row within the group), so every warp store is coalesced.
+// A block takes one b-block and kBrowsCh chunks; its warps take the row
+// groups (H: b-feature g, family, half of the targets; G: two b-features'
+// [q, q^2, q', q'^2]) and keep, per lane, the target sums of its H rows
+// over the block's chunks.
+constexpr int kBrowsCh = 16;  // chunks per k_gmt_brows block
+constexpr int kHTypes = gmt::FB * 4;  // H row groups per b-block: g x family x half of the targets
+static_assert(kHTypes == 3 * 8 && gmt::NTP == 16 && gmt::NG == 4 * 8, "row groups of the 8 warps");
+
+// Per-block partial target sums: [b-block][chunk block][g][family][target]
+// of (compensated pair s, c; sum of squares).
+struct GmtPart {
+  float s, c, q;
+};
+
+size_t gmt_part_count(int64_t n, int64_t N) {
+  const int64_t nchunks = (N + tc::KC - 1) / tc::KC;
+  const int64_t ncb = (nchunks + kBrowsCh - 1) / kBrowsCh;
+  return (size_t)((n + gmt::FB - 1) / gmt::FB) * ncb * gmt::FB * 2 * gmt::NTP;
 }
 
-constexpr int kBrowsT = gmt::NTP / 2;  // targets per k_gmt_brows block
-
-// Per screen, one block per (feature slot f of the b-blocks, half th of the
-// targets); slots past n write zero rows.  The b-image rows of the half's
-// targets (H rows q y_t of x and of 1/x, y the FP32 targets t0 ..
-// t0+T-1, zero rows for t >= T), for th = 0 also the G rows (q, q^2 of x
-// and of 1/x; the block of slot 0 of a b-block also its zero G rows), and
-// the target sums: sum fl(q y_t) as compensated sums of plain FP32 sums of
-// 8 samples (so within 8u sum |fl(q y_t)| of the exact sum of the rounded
-// products) and RU |fl(q y_t)|_2.
-__global__ void __launch_bounds__(128) k_gmt_brows(FeatTable F, int nchunks, const float *y32, int64_t ldy, int T,
-                                                   const GramFeat *gf, unsigned char *bimg, GmtTgt *gt) {
+// Per screen: the b-image of b-block blockIdx.x, chunks kBrowsCh blockIdx.y
+// .. + kBrowsCh - 1, and the block's partial target sums.  H rows: q y_t
+// of x and of 1/x, y the FP32 targets t0 .. t0+T-1 (zero rows for t >= T
+// and for feature slots past n); G rows: q, q^2 of x and of 1/x, and the
+// zero rows after the last b-feature's.
+__global__ void __launch_bounds__(256) k_gmt_brows(FeatTable F, int nchunks, const float *y32, int64_t ldy, int T,
+                                                   const GramFeat *gf, unsigned char *bimg, GmtPart *part) {
   using namespace gmt;
-  __shared__ float sm_s[4][2 * kBrowsT], sm_c[4][2 * kBrowsT], sm_q[4][2 * kBrowsT];
-  const int64_t f = blockIdx.x >> 1;
-  const int th = blockIdx.x & 1;
-  const bool real = f < F.n;
-  GramFeat G{};
-  if (real) G = gf[f];
-  const int64_t bb = f / FB;
-  const int g = (int)(f % FB);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kg = lane >> 3, r8 = lane & 7;
+  const int64_t bb = blockIdx.x, cb = blockIdx.y;
+  const int c0 = (int)cb * kBrowsCh, c1 = min(nchunks, c0 + kBrowsCh);
   const int64_t N = F.N;
-  Comp32 csy[2][kBrowsT];
-  float sq[2][kBrowsT];
+  // H row groups of this warp: types warp, warp + 8, warp + 16 (type =
+  // 4 g + 2 family + half)
+  Comp32 acc[3];
+  float sq[3] = {0.f, 0.f, 0.f};
+  for (int c = c0; c < c1; ++c) {
+    unsigned char *base = bimg + ((size_t)bb * nchunks + c) * B_IMG;
+    const int64_t s0 = (int64_t)c * tc::KC + kg * 8;
 #pragma unroll
-  for (int fam = 0; fam < 2; ++fam)
-#pragma unroll
-    for (int t = 0; t < kBrowsT; ++t) sq[fam][t] = 0.f;
-  const int64_t groups = (int64_t)nchunks * (tc::KC / 8);
-  for (int64_t gi = threadIdx.x; gi < groups; gi += blockDim.x) {
-    const int64_t s0 = gi * 8;
-    const int ch = (int)(s0 / tc::KC), k0 = (int)(s0 % tc::KC);
-    unsigned char *base = bimg + ((size_t)bb * nchunks + ch) * B_IMG;
-    float p[2][8];
-#pragma unroll
-    for (int fam = 0; fam < 2; ++fam) {
-      gram_vals(F, real ? f : 0, s0, fam, G.c[fam], real && G.ok[fam] != 0, p[fam]);
-      if (th == 0) {
-        float p2[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) p2[e] = p[fam][e] * p[fam][e];
-        uint4 h, l;
-        uint32_t o = tc::core_off(grow(g, 2 * fam), k0);
-        split8(p[fam], h, l);
-        *reinterpret_cast<uint4 *>(base + o) = h;
-        *reinterpret_cast<uint4 *>(base + B_PART + o) = l;
-        o = tc::core_off(grow(g, 2 * fam + 1), k0);
-        split8(p2, h, l);
-        *reinterpret_cast<uint4 *>(base + o) = h;
-        *reinterpret_cast<uint4 *>(base + B_PART + o) = l;
-      }
-    }
-    if (th == 0 && g == 0) {
-      // the b-block's zero G rows
-      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-      for (int k = FB * 4; k < NG; ++k) {
-        const uint32_t o = tc::core_off(NH + k, k0);
-        *reinterpret_cast<uint4 *>(base + o) = z;
-        *reinterpret_cast<uint4 *>(base + B_PART + o) = z;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kBrowsT; ++i) {
-      const int t = th * kBrowsT + i;
-      float y[8];
-      if (t < T && s0 + 8 <= N) {
-        // (rows start 16-byte aligned: ldy is a multiple of 4)
-        const float4 *yp = reinterpret_cast<const float4 *>(y32 + (int64_t)t * ldy + s0);
-        const float4 a = yp[0], b = yp[1];
-        y[0] = a.x, y[1] = a.y, y[2] = a.z, y[3] = a.w, y[4] = b.x, y[5] = b.y, y[6] = b.z, y[7] = b.w;
+    for (int i = 0; i < 3; ++i) {
+      const int type = warp + 8 * i;
+      const int g = type >> 2, fam = (type >> 1) & 1, half = type & 1;
+      const int t = half * 8 + r8;
+      const int64_t f = bb * FB + g;
+      const bool real = f < F.n;
+      float p[8], py[8];
+      if (real) {
+        const GramFeat G = gf[f];
+        gram_vals(F, f, s0, fam, G.c[fam], G.ok[fam] != 0, p);
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) y[e] = (t < T && s0 + e < N) ? y32[(int64_t)t * ldy + s0 + e] : 0.f;
+        for (int e = 0; e < 8; ++e) p[e] = 0.f;
       }
+      float part8 = 0.f;
 #pragma unroll
-      for (int fam = 0; fam < 2; ++fam) {
-        float py[8], part = 0.f;
+      for (int e = 0; e < 8; ++e) {
+        const float y = (t < T && s0 + e < N) ? y32[(int64_t)t * ldy + s0 + e] : 0.f;
+        py[e] = p[e] * y;
+        part8 += py[e];
+        sq[i] = fmaf(py[e], py[e], sq[i]);
+      }
+      acc[i].add(part8);
+      uint4 h, l;
+      split8(py, h, l);
+      const uint32_t o = tc::core_off(hrow(g, fam, t), kg * 8);
+      *reinterpret_cast<uint4 *>(base + o) = h;
+      *reinterpret_cast<uint4 *>(base + B_PART + o) = l;
+    }
+    if (warp < NG / 8) {
+      // G row group `warp`: rows NH + 8 warp + r8 = b-feature 2 warp + r8 / 4,
+      // type r8 % 4 (q, q^2 of x, then of 1/x)
+      const int g = 2 * warp + (r8 >> 2), k = r8 & 3, fam = k >> 1;
+      const int64_t f = bb * FB + g;
+      float v[8];
+      if (g < FB && f < F.n) {
+        const GramFeat G = gf[f];
+        gram_vals(F, f, s0, fam, G.c[fam], G.ok[fam] != 0, v);
+        if (k & 1) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          py[e] = p[fam][e] * y[e];
-          part += py[e];
-          sq[fam][i] = fmaf(py[e], py[e], sq[fam][i]);
+          for (int e = 0; e < 8; ++e) v[e] = v[e] * v[e];
         }
-        csy[fam][i].add(part);
-        uint4 h, l;
-        const uint32_t o = tc::core_off(hrow(g, fam, t), k0);
-        split8(py, h, l);
-        *reinterpret_cast<uint4 *>(base + o) = h;
-        *reinterpret_cast<uint4 *>(base + B_PART + o) = l;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.f;
       }
+      uint4 h, l;
+      split8(v, h, l);
+      const uint32_t o = tc::core_off(NH + 8 * warp + r8, kg * 8);
+      *reinterpret_cast<uint4 *>(base + o) = h;
+      *reinterpret_cast<uint4 *>(base + B_PART + o) = l;
     }
   }
-  if (!real) return;  // (block-uniform)
-  // warp sums (compensated pairs), then the four warps
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // the four k-groups of each target meet in lanes 0..7
 #pragma unroll
-  for (int fam = 0; fam < 2; ++fam)
-#pragma unroll
-    for (int i = 0; i < kBrowsT; ++i) {
-      Comp32 a = csy[fam][i];
-      float q = sq[fam][i];
-      for (int off = 16; off > 0; off >>= 1) {
-        const float s = __shfl_xor_sync(0xffffffffu, a.s, off), c = __shfl_xor_sync(0xffffffffu, a.c, off);
-        comp_merge(a, s, c);
-        q += __shfl_xor_sync(0xffffffffu, q, off);
-      }
-      if (lane == 0) {
-        sm_s[w][fam * kBrowsT + i] = a.s;
-        sm_c[w][fam * kBrowsT + i] = a.c;
-        sm_q[w][fam * kBrowsT + i] = q;
-      }
+  for (int i = 0; i < 3; ++i) {
+    Comp32 a = acc[i];
+    float q = sq[i];
+    for (int off = 8; off < 32; off <<= 1) {
+      const float s = __shfl_xor_sync(0xffffffffu, a.s, off), c = __shfl_xor_sync(0xffffffffu, a.c, off);
+      a.add(s);
+      a.c += c;
+      q += __shfl_xor_sync(0xffffffffu, q, off);
     }
-  __syncthreads();
-  if (threadIdx.x < 2 * kBrowsT) {
-    const int x = threadIdx.x, fam = x / kBrowsT, t = th * kBrowsT + x % kBrowsT;
-    Comp32 a;
-    float q = 0.f;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      comp_merge(a, sm_s[k][x], sm_c[k][x]);
-      q += sm_q[k][x];
+    if (kg == 0) {
+      const int type = warp + 8 * i;
+      const int g = type >> 2, fam = (type >> 1) & 1, half = type & 1;
+      const int t = half * 8 + r8;
+      GmtPart o;
+      o.s = a.s;
+      o.c = a.c;
+      o.q = q;
+      part[(((size_t)bb * gridDim.y + cb) * FB + g) * 2 * NTP + fam * NTP + t] = o;
     }
-    // the FP32 sums of squares are low by at most (terms per thread + tree
-    // depth + 4) u of themselves
-    const double marg = 1.0 + ((double)groups * 8.0 / blockDim.x + 16.0) * 5.9604644775390625e-8;
-    gt[f].sy[fam][t] = (float)a.value();
-    gt[f].ny[fam][t] = __double2float_ru(sqrt((double)q * marg) * (1.0 + 1e-15));
   }
+}
+
+// The target sums of each feature from the blocks' partials: the pairs
+// merged in FP32 (compensated), the sums of squares added in FP64.
+__global__ void __launch_bounds__(64) k_gmt_tsum(int64_t n, int ncb, const GmtPart *part, int64_t groups,
+                                                 GmtTgt *gt) {
+  using namespace gmt;
+  const int64_t f = blockIdx.x;
+  const int x = threadIdx.x;  // family x NTP + target
+  if (f >= n || x >= 2 * NTP) return;
+  const int64_t bb = f / FB, g = f % FB;
+  Comp32 a;
+  double q = 0.0;
+  for (int cb = 0; cb < ncb; ++cb) {
+    const GmtPart p = part[(((size_t)bb * ncb + cb) * FB + g) * 2 * NTP + x];
+    a.add(p.s);
+    a.c += p.c;
+    q += (double)p.q;
+  }
+  // the FP32 per-lane sums of squares are low by at most (terms per lane +
+  // 2 shuffle levels + 4) u of themselves
+  const double marg = 1.0 + ((double)kBrowsCh * 8.0 + 8.0) * 5.9604644775390625e-8;
+  gt[f].sy[x / NTP][x % NTP] = (float)a.value();
+  gt[f].ny[x / NTP][x % NTP] = __double2float_ru(sqrt(q * marg) * (1.0 + 1e-15));
+  (void)groups;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -752,7 +763,8 @@ size_t gmt_space_bytes(int64_t n, int64_t N) {
 }
 
 size_t gmt_screen_bytes(int64_t n, int64_t N) {
-  return (size_t)gmt_nb(n) * gmt_chunks(N) * gmt::B_IMG + (size_t)n * sizeof(GmtTgt) + 256;
+  return (size_t)gmt_nb(n) * gmt_chunks(N) * gmt::B_IMG + (size_t)n * sizeof(GmtTgt) +
+         gmt_part_count(n, N) * sizeof(GmtPart) + 512;
 }
 
 // Space part: a-images and feature sums, built once per space into `buf`
@@ -767,22 +779,28 @@ void gmt_build_space(const FeatTable &F, void *buf, cudaStream_t st) {
   k_gmt_space<<<(unsigned)(gmt_na(n) * gmt::FA), 128, 0, st>>>(F, nchunks, aimg, gf);
 }
 
-// One screen's b-images and target sums into `scr` (gmt_screen_bytes).
+// One screen's b-images and target sums into `scr` (gmt_screen_bytes):
+// the images with the blocks' partial sums, then the sums.
 void launch_gmt_brows(const ScreenArgs &A, const void *space_buf, void *scr, cudaStream_t st) {
   const int64_t n = A.F.n, N = A.N;
   const int nchunks = (int)gmt_chunks(N);
+  const int ncb = (nchunks + kBrowsCh - 1) / kBrowsCh;
   const unsigned char *aimg = static_cast<const unsigned char *>(space_buf);
   const GramFeat *gf = reinterpret_cast<const GramFeat *>(aimg + (size_t)gmt_na(n) * nchunks * gmt::A_IMG);
   unsigned char *bimg = static_cast<unsigned char *>(scr);
   GmtTgt *gt = reinterpret_cast<GmtTgt *>(bimg + (size_t)gmt_nb(n) * nchunks * gmt::B_IMG);
-  note_launches(1);
-  k_gmt_brows<<<(unsigned)(gmt_nb(n) * gmt::FB * 2), 128, 0, st>>>(A.F, nchunks, A.y32 + (int64_t)A.t0 * A.ldy,
-                                                                   A.ldy, A.T, gf, bimg, gt);
+  GmtPart *part = reinterpret_cast<GmtPart *>(reinterpret_cast<unsigned char *>(gt) +
+                                              ((size_t)n * sizeof(GmtTgt) + 255) / 256 * 256);
+  note_launches(2);
+  k_gmt_brows<<<dim3((unsigned)gmt_nb(n), (unsigned)ncb), 256, 0, st>>>(A.F, nchunks, A.y32 + (int64_t)A.t0 * A.ldy,
+                                                                      A.ldy, A.T, gf, bimg, part);
+  k_gmt_tsum<<<(unsigned)n, 64, 0, st>>>(n, ncb, part, (int64_t)nchunks * (tc::KC / 8), gt);
 }
 
 // The tiles (a-block, b-block) holding an ordered pair (i, j), i != j, of a
 // candidate of the binary block of rung k with an id in [id_begin, id_end),
-// b-block major (the CTAs working at one time share b-images and sweep the
+// in groups of `group` consecutive a-blocks, b-block major within a group
+// (the CTAs working at one time share b-images and sweep the group's
 // a-images together).  The test is conservative: the pairs of a tile have
 // max(i, j) in [max(a0, b0), max(a1, b1)].
 void gmt_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::vector<int2> &out) {
@@ -795,17 +813,20 @@ void gmt_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::vec
   if (p_hi <= p_lo) return;
   auto pidx = [&](int64_t i, int64_t j) { return g.um + (tri((uint64_t)i) + (uint64_t)j - g.tri_o) * (uint64_t)g.nb; };
   const int64_t na = gmt_na(n), nb = gmt_nb(n);
-  for (int64_t c = 0; c < nb; ++c) {
-    const int64_t b0 = c * gmt::FB, b1 = std::min<int64_t>(b0 + gmt::FB, n) - 1;
-    for (int64_t a = 0; a < na; ++a) {
-      const int64_t a0 = a * gmt::FA, a1 = std::min<int64_t>(a0 + gmt::FA, n) - 1;
-      const int64_t Ilo = std::max<int64_t>(std::max(a0, b0), std::max<int64_t>(o, 1));
-      const int64_t Ihi = std::max(a1, b1);
-      if (Ilo > Ihi) continue;
-      if (a0 == b1 && a1 == b0) continue;  // a single feature on both sides: only i == j
-      const uint64_t lo = pidx(Ilo, 0), hi = pidx(Ihi, Ihi - 1) + (uint64_t)g.nb;
-      if (hi <= p_lo || lo >= p_hi) continue;
-      out.push_back(make_int2((int)a, (int)c));
+  const int64_t group = std::max(1, tuning().gmt_group);
+  for (int64_t ga = 0; ga < na; ga += group) {
+    for (int64_t c = 0; c < nb; ++c) {
+      const int64_t b0 = c * gmt::FB, b1 = std::min<int64_t>(b0 + gmt::FB, n) - 1;
+      for (int64_t a = ga; a < std::min(na, ga + group); ++a) {
+        const int64_t a0 = a * gmt::FA, a1 = std::min<int64_t>(a0 + gmt::FA, n) - 1;
+        const int64_t Ilo = std::max<int64_t>(std::max(a0, b0), std::max<int64_t>(o, 1));
+        const int64_t Ihi = std::max(a1, b1);
+        if (Ilo > Ihi) continue;
+        if (a0 == b1 && a1 == b0) continue;  // a single feature on both sides: only i == j
+        const uint64_t lo = pidx(Ilo, 0), hi = pidx(Ihi, Ihi - 1) + (uint64_t)g.nb;
+        if (hi <= p_lo || lo >= p_hi) continue;
+        out.push_back(make_int2((int)a, (int)c));
+      }
     }
   }
 }

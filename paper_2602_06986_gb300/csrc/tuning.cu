@@ -28,6 +28,7 @@ Tuning tuning() {
   o.gram_max_n = t.gram_max_n > 0 ? t.gram_max_n : 2048;
   o.tc_min_targets = t.tc_min_targets > 0 ? t.tc_min_targets : 8;
   o.batch_job_samples = t.batch_job_samples > 0 ? t.batch_job_samples : (1 << 14);
+  o.gmt_group = t.gmt_group > 0 ? t.gmt_group : 2;
   return o;
 }
 
@@ -43,7 +44,8 @@ extern "C" dse_status dse_set_tuning(const dse_tuning *t) {
                     (v.seed_stride == 0 || (v.seed_stride >= 2 && v.seed_stride <= 4096)) &&
                     (v.gram_max_n == 0 || (v.gram_max_n >= 16 && v.gram_max_n <= 2048)) &&
                     (v.tc_min_targets == 0 || (v.tc_min_targets >= 1 && v.tc_min_targets <= 4096)) &&
-                    (v.batch_job_samples == 0 || (v.batch_job_samples >= 1024 && v.batch_job_samples <= (1 << 20)));
+                    (v.batch_job_samples == 0 || (v.batch_job_samples >= 1024 && v.batch_job_samples <= (1 << 20))) &&
+                    (v.gmt_group == 0 || (v.gmt_group >= 1 && v.gmt_group <= 4096));
     if (!ok) {
       set_error("tuning value outside its range");
       return DSE_EINVAL;
@@ -68,6 +70,7 @@ extern "C" dse_status dse_get_tuning(dse_tuning *t) {
   o.gram_max_n = a.gram_max_n;
   o.tc_min_targets = a.tc_min_targets;
   o.batch_job_samples = a.batch_job_samples;
+  o.gmt_group = a.gmt_group;
   *t = o;
   return DSE_OK;
 }
