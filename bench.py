@@ -120,6 +120,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+_PROBED = {}
+
+
+def probed_peaks(dse):
+    """The library's issue-rate probe (dse_measure_peaks), run once per
+    process: FP32 FMA, MUFU and FP64 FMA lane operations per second."""
+    if not _PROBED:
+        _PROBED.update(dse.measure_peaks())
+    return dict(_PROBED)
+
+
+def alu_peak(dse):
+    """FP32 ALU roofline denominator in T lane-ops/s (an FMA is one lane
+    operation) and its source."""
+    p = probed_peaks(dse)
+    return p["fp32_fma_per_s"] / 1e12, "FP32 FMA issue rate measured on this GPU (dse_measure_peaks)"
+
+
 def measured_bf16(key):
     """A bf16 tensor peak (TFLOP/s) from MEASURED_PEAKS.json, else the
     recipe's fallback."""
@@ -343,14 +361,13 @@ def bench_multi_target(args, which):
             peak = float(json.load(f)["bf16_tflops_sustained"])
     except Exception:
         peak, peak_src = 1700.0, "fallback sustained bf16"
-    mhz, _ = peaks()
-    alu_peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
+    alu_pk, _ = alu_peak(dse)
     alu = 6.0 * N * tc_valid / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
     roofline = {"bound": "tensor", "kernel": "k_pair_tc (BF16x3 tcgen05)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
                 "traffic": None, "peak_source": peak_src, "flops_per_candidate_sample": 6 * T,
                 "launch_ms_total_per_step": tc_ms / args.steps,
-                "alu_lane_ops_tps": alu, "alu_frac": alu / alu_peak if alu else None}
+                "alu_lane_ops_tps": alu, "alu_frac": alu / alu_pk if alu else None}
     if stats[0]["binary_path"] == dse.PATH_GRAM_MT:
         roofline = gmt_roofline(dse, w, Xd, None, sum(s["kernel_ms"][1] for s in stats) / len(stats),
                                 tot / args.steps, peak, peak_src)
@@ -542,22 +559,21 @@ def gmt_roofline(dse, w, Xd, stream, launch_ms, step_ms, tc_peak, tc_src):
             "launch_ms": launch_ms, "share_of_step": launch_ms / step_ms}
 
 
-def tc_roofline(T, N, mul_ms, mul_valid, step_ms, stats, tc_peak, tc_src):
+def tc_roofline(dse, T, N, mul_ms, mul_valid, step_ms, stats, tc_peak, tc_src):
     """Roofline of k_pair_tc (sample-by-sample generation on the FP32 pipes,
     numerators on the tensor cores): the FP32 ALU bound, with the tensor
     fraction beside it."""
-    mhz, clk_src = peaks()
-    alu_peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12
+    alu_pk, alu_src = alu_peak(dse)
     ntp = 16 if T <= 16 else 32 if T <= 32 else 64
     alu = TC_ALU_OPS_PER_EVAL * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
     tc_flops = 6.0 * ntp * N * mul_valid / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
     return {"bound": "alu", "kernel": f"k_pair_tc<KIND_MUL,{ntp}> (a*b, a/b, b/a; BF16x3 tcgen05 numerators)",
-            "achieved": alu, "peak": alu_peak, "unit": "T fp32-lane-ops/s",
-            "frac": alu / alu_peak if alu else None,
+            "achieved": alu, "peak": alu_pk, "unit": "T fp32-lane-ops/s",
+            "frac": alu / alu_pk if alu else None,
             "traffic": profiled_traffic("k_pair_tc_large.txt"),
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
                               "(profiles/k_pair_tc_large.txt)",
-            "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({clk_src})",
+            "peak_source": alu_src,
             "ops_per_candidate_sample": TC_ALU_OPS_PER_EVAL, "valid_candidates_per_launch": mul_valid / len(stats),
             "launch_ms": mul_ms / len(stats), "share_of_step": mul_ms / sum(step_ms),
             "tensor": {"achieved": tc_flops, "peak": tc_peak, "unit": "TFLOP/s",
@@ -707,7 +723,7 @@ def bench_large(args):
     if stats[0].get("binary_path") == dse.PATH_GRAM_MT:
         roofline = gmt_roofline(dse, w, Xd, stream, mul_ms / len(stats), sum(step_ms) / len(stats), tc_peak, tc_src)
     else:
-        roofline = tc_roofline(T, N, mul_ms, mul_valid, step_ms, stats, tc_peak, tc_src)
+        roofline = tc_roofline(dse, T, N, mul_ms, mul_valid, step_ms, stats, tc_peak, tc_src)
     # the kernel groups' device times from one more (untimed) step with an
     # event at every group boundary
     flush.zero_()
@@ -738,8 +754,15 @@ def bench_large(args):
     fp64 = None
     if fp64_ms:
         fp64_value = fp64_c / (fp64_tot * 1e-3)
+        # FP64 lane operations of the plain path: evaluation, sum w, sum w^2
+        # and one FMA per target, per valid candidate and sample
+        fp64_rate = fp64_c * N * (3 + T) / (fp64_tot * 1e-3)  # all ranks' candidates over the slowest rank's time
+        pk = probed_peaks(dse)["fp64_fma_per_s"]
         fp64 = {"value": fp64_value, "unit": "candidates/s", "ms_per_step": fp64_tot / len(fp64_ms),
-                "steps": len(fp64_ms), "speedup_of_fp32_path": value / fp64_value}
+                "steps": len(fp64_ms), "speedup_of_fp32_path": value / fp64_value,
+                "fp64_lane_ops_per_s": fp64_rate, "fp64_peak_lane_ops_per_s": pk * world,
+                "fp64_frac": fp64_rate / (pk * world) if pk else None,
+                "fp64_peak_source": "FP64 FMA issue rate measured on this GPU (dse_measure_peaks)"}
 
     # end to end through the public API with host buffers (rank 0's GPU; the
     # whole workload on one device)
@@ -790,6 +813,10 @@ def bench_large(args):
         "gpu_launches": launches,
         "clocks": clk,
         "tuning": tuning,
+        "measured_peaks": {"fp32_fma_per_s": probed_peaks(dse)["fp32_fma_per_s"],
+                           "sfu_per_s": probed_peaks(dse)["sfu_per_s"],
+                           "fp64_fma_per_s": probed_peaks(dse)["fp64_fma_per_s"],
+                           "source": "dse_measure_peaks on this GPU (lane operations per second)"},
     }
     print(json.dumps(line))
 
@@ -950,12 +977,12 @@ def bench_medium(args):
                     "flops_per_launch": flops, "flops_per_pair_sample": GRAM_FLOPS_PER_PAIR_SAMPLE,
                     "pairs": pairs, "launch_ms": launch_ms, "share_of_step": mul_ms / tot_ms}
     else:
-        peak = SM_COUNT * FP32_LANES * mhz * 1e6 / 1e12  # T lane-ops/s
+        peak, alu_src = alu_peak(dse)  # T lane-ops/s
         achieved = mul_valid * N * OPS_PER_EVAL / (mul_ms * 1e-3) / 1e12 if mul_ms > 0 else None
         roofline = {"bound": "alu", "kernel": "k_pair<float,MUL,1,2,2> (a*b, a/b, b/a slots)",
                     "achieved": achieved, "peak": peak, "unit": "T fp32-lane-ops/s",
                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                    "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz ({peak_src})",
+                    "peak_source": alu_src,
                     "ops_per_eval": OPS_PER_EVAL, "launch_ms": launch_ms, "share_of_step": mul_ms / tot_ms}
 
     # the plain FP64 GPU path on the same workload (same step, FP64 kernels)

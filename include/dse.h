@@ -495,6 +495,14 @@ dse_status dse_get_tuning(dse_tuning *t);
    context stays usable either way.  Synchronises. */
 dse_status dse_check_wait(uint32_t polls, int32_t arrive, void *stream);
 
+/* Issue rates of the pipes the CUDA-core kernels are bound by, measured on
+   the current device: FP32 fused multiply-adds, special-function (MUFU
+   ex2) operations and FP64 fused multiply-adds per second over the whole
+   device (lane operations; register-resident independent chains in 64
+   warps per SM, best of three timed rounds after a warm-up round).  The
+   denominators of the ALU rooflines.  Synchronises. */
+dse_status dse_measure_peaks(double *fp32_fma_per_s, double *sfu_per_s, double *fp64_fma_per_s, void *stream);
+
 /* Test hook: the device allocation after `after` more successful ones
    fails with DSE_ENOMEM (once); a negative value switches the hook off.
    Process-wide. */

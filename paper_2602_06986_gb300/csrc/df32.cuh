@@ -402,6 +402,9 @@ __device__ __forceinline__ bool col_sums_pair(const FeatTable &F, int op, int64_
 
 // The FP64 pass (whole block, results in warp 0): the same sums with c the
 // FP64 value at sample 0.
+// (NVB: the largest number of vectors the caller passes, known at compile
+// time; the vectors past V.nv are skipped either way)
+template <int NVB = kColVec>
 __device__ __forceinline__ void col_sums64(const FeatTable &F, int op, int64_t a, int64_t b, int64_t N,
                                            const ColVecs &V, ColSums &out, ColShared &sh) {
   const double *xa = F.v64 + a * F.ld, *xb = F.v64 + (b >= 0 ? b : a) * F.ld;
@@ -414,7 +417,7 @@ __device__ __forceinline__ void col_sums64(const FeatTable &F, int op, int64_t a
     acc[0] += v;
     acc[1] = fma(v, v, acc[1]);
 #pragma unroll
-    for (int m = 0; m < kColVec; ++m)
+    for (int m = 0; m < NVB; ++m)
       if (m < V.nv) acc[2 + m] = fma(v, V.v64[m][s], acc[2 + m]);
   }
   const int w = threadIdx.x >> 5;
@@ -470,6 +473,14 @@ __device__ __forceinline__ void col_sums(const FeatTable &F, int op, int64_t a, 
     default: break;
   }
   if (!done) col_sums64(F, op, a, b, N, V, out, sh);
+}
+
+// The same for callers whose candidates are summed against one vector only
+// (V.nv == 1): the same arithmetic, without the code (and registers) of the
+// wider passes.
+__device__ __forceinline__ void col_sums1(const FeatTable &F, int op, int64_t a, int64_t b, int64_t N,
+                                          const ColVecs &V, ColSums &out, ColShared &sh) {
+  if (!df::col_sums_pair<1>(F, op, a, b, N, V, out, sh)) col_sums64<1>(F, op, a, b, N, V, out, sh);
 }
 
 }  // namespace dse

@@ -82,6 +82,7 @@ constexpr int THREADS = (2 + EPI) * 32;
 constexpr int BPW = FB / 2;        // b-features per epilogue warp
 constexpr int RUN = BPW * (HC + 8);  // running sums per epilogue thread (120)
 constexpr uint32_t kWait = 1u << 22;
+constexpr int kStage = 128;        // pending pushes per epilogue warp
 
 static_assert(N1 % 16 == 0 && N1 <= 256 && NG % 16 == 0, "MMA shapes (M = 128)");
 static_assert(FB * 4 <= NG, "G rows");
@@ -94,6 +95,13 @@ struct Shared {
   int abort;
   float theta[EPI][NTP];  // each epilogue warp's copy of the list thresholds
   float ysum[NTP];
+  float py[EPI][NTP][32];  // each epilogue warp's a-features' target sums (target-major)
+  // each epilogue warp's pending pushes (list, id, score, bound), written
+  // out a b-feature at a time
+  uint64_t pid[EPI][kStage];
+  float ps[EPI][kStage], pe[EPI][kStage];
+  uint8_t pl[EPI][kStage];
+  int pn[EPI];
 };
 
 constexpr size_t shared_bytes() { return (sizeof(Shared) + 1023) / 1024 * 1024; }
@@ -345,28 +353,87 @@ __device__ __forceinline__ gram::EpiFeat gmt_rec(const ScreenArgs &A, const Gram
   return c;
 }
 
+// A warp's pending pushes.  A lane stages a push with a shared-memory
+// atomic (no global round trip in the scoring loop; a full stage falls back
+// to a direct push); the whole warp writes the stage out: entries still at
+// or above their list's current threshold, one global slot reservation per
+// distinct list (the lanes holding one list's entries take consecutive
+// slots), then the bound histograms.  Returns the lists written to.
+struct GmtStage {
+  uint64_t *id;
+  float *s, *e;
+  uint8_t *l;
+  int *n;
+};
+
+__device__ __forceinline__ bool gmt_stage(const GmtStage &P, const CandBufs &B, int t0, int l, uint64_t id, float s,
+                                          float e) {
+  const int pos = atomicAdd(P.n, 1);
+  if (pos < gmt::kStage) {
+    P.id[pos] = id;
+    P.s[pos] = s;
+    P.e[pos] = e;
+    P.l[pos] = (uint8_t)l;
+    return true;
+  }
+  return push_one(B, t0 + l, id, s, e);
+}
+
+__device__ __forceinline__ uint32_t gmt_flush(const GmtStage &P, const CandBufs &B, int t0) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  const int n = min(*P.n, gmt::kStage);
+  uint32_t lists = 0;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    int l = -1;
+    uint64_t id = 0;
+    float s = 0.f, e = 0.f;
+    if (i < n) {
+      l = P.l[i];
+      id = P.id[i];
+      s = P.s[i];
+      e = P.e[i];
+      if (!(iv_hi(s, e) >= ld_relaxed(&B.theta[t0 + l]))) l = -1;  // below a threshold raised meanwhile
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, l);
+    const int leader = __ffs(grp) - 1;
+    unsigned base = 0;
+    if (l >= 0 && lane == leader) base = atomicAdd(&B.count[t0 + l], (unsigned)__popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (l >= 0) {
+      const unsigned pos = base + (unsigned)__popc(grp & ((1u << lane) - 1u));
+      if ((int64_t)pos < B.cap) {
+        const size_t x = (size_t)(t0 + l) * (size_t)B.cap + pos;
+        B.id[x] = id;
+        B.score[x] = s;
+        B.eps[x] = e;
+      }
+      count_bounds(B, t0 + l, s, e);
+      lists |= 1u << l;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) *P.n = 0;
+  __syncwarp();
+  return __reduce_or_sync(0xffffffffu, lists);
+}
+
 // Common bookkeeping of one candidate once its interval part is known:
 // realised decision, escalation, then every target's score, interval note
-// and threshold push.  sy(t, &Sy, &dSy) gives target t's sum and bound.
-// Returns the lists pushed to.
+// and threshold push.  sy(t, &Sy, &dSy) gives target t's sum and bound;
+// sy_bound bounds every |Sy| (a non-finite bound leaves the candidate to the
+// FP64 escalation).  Returns the lists pushed to.
 template <class SyFn>
 __device__ __forceinline__ uint32_t gmt_targets(const ScreenArgs &A, LaneStats &ls, uint64_t gid, const GramVar &v,
-                                                float invN, const float *ysum, const float *theta, SyFn sy) {
+                                                float invN, const float *ysum, const float *theta, float sy_bound,
+                                                const GmtStage &P, SyFn sy) {
   if (v.realised == 0) {
     ls.r[DSE_R_REALISED]++;
     note_why(A, gid, DSE_R_REALISED);
     return 0;
   }
-  bool fin = v.realised == 1;
-  if (fin) {
-#pragma unroll
-    for (int t = 0; t < gmt::NTP; ++t) {
-      float S, d;
-      sy(t, &S, &d);
-      fin = fin && (t >= A.T || isfinite(S));
-    }
-  }
-  if (!fin) {
+  if (v.realised != 1 || !(sy_bound < 1e30f)) {
     escalate(A, gid);
     ls.escalated++;
     return 0;
@@ -375,15 +442,29 @@ __device__ __forceinline__ uint32_t gmt_targets(const ScreenArgs &A, LaneStats &
   ls.evaluated++;
   note_why(A, gid, DSE_VALID);
   uint32_t pushed = 0;
+  const float u = 5.9604644775390625e-8f;
 #pragma unroll
   for (int t = 0; t < gmt::NTP; ++t) {
     if (t >= A.T) break;
     float S, d, s, eps;
     sy(t, &S, &d);
+    if (!A.ivl && v.q_lo > 0.f) {
+      // cheap rejection: the pushed interval's upper edge is at most
+      // 2 rhi (1 + 24u) + 4e-12 with rhi = (|P| + dP) / q_lo (gram_num's
+      // numerator bound); most candidate-target pairs are far below the
+      // list's threshold, and this test needs no division
+      const float ys = ysum[t];
+      const float P = fmaf(-v.S1, ys * invN, S);
+      const float aP = fabsf(P), ays = fabsf(ys), aS1 = fabsf(v.S1);
+      const float dP = (d + ays * invN * v.dS1 + 6.f * u * (fabsf(S) + aS1 * ays * invN) + v.E * (1.f + 2.f * u) +
+                        2.f * u * v.q_hi + u * aP) *
+                       1.01f;
+      if ((aP + dP) * 2.0002f + 1e-10f * v.q_lo < theta[t] * v.q_lo) continue;
+    }
     gram_num(v, S, d, invN, ysum[t], &s, &eps);
     eps *= 1.0f + 2.4e-7f;
     note_ivl(A, gid, A.t0 + t, s, eps);
-    if (iv_hi(s, eps) >= theta[t] && push_one(A.B, A.t0 + t, gid, s, eps)) pushed |= 1u << t;
+    if (iv_hi(s, eps) >= theta[t] && gmt_stage(P, A.B, A.t0, t, gid, s, eps)) pushed |= 1u << t;
   }
   return pushed;
 }
@@ -398,7 +479,8 @@ __device__ __forceinline__ uint32_t gmt_product(const ScreenArgs &A, const GmtAr
                                                 int64_t ia, int64_t ib, int64_t i, int64_t j,
                                                 const gram::EpiFeat &Fi, const gram::EpiFeat &Fj,
                                                 const float (&run)[gmt::RUN], float G11, float G12, float G21,
-                                                float G22, const float *ysum, const float *theta) {
+                                                float G22, const float *ysum, const float *theta,
+                                                const float (*py)[32], const GmtStage &P) {
   const int pos = A.slot_pos[opc - 6];
   if (pos < 0) return 0;
   const uint64_t pbase = A.G.um + (tri((uint64_t)ia) + (uint64_t)ib - A.G.tri_o) * (uint64_t)A.G.nb;
@@ -442,23 +524,27 @@ __device__ __forceinline__ uint32_t gmt_product(const ScreenArgs &A, const GmtAr
   const float kappa = FW == 0 ? 4.01f : 5.01f;
   const float E = u * (kappa * Vhi + 1.01f * (acw * Fi.nu[0] + acu * Fj.nu[FW])) * 1.02f;
   const GramVar v = gram_var(S1, dS1, S2, dS2, Z, dZ, Vhi, E, N, invN, (float)A.fmin_std_rel64);
-  const GmtTgt *ti = GA.gt + i, *tj = GA.gt + j;
+  const GmtTgt *tj = GA.gt + j;
+  const int lane = threadIdx.x & 31;
   auto sy = [&](int t, float *S, float *d) {
-    const float PY = __ldg(&ti->sy[0][t]), QY = __ldg(&tj->sy[FW][t]), nyw = __ldg(&tj->ny[FW][t]);
+    const float PY = py[t][lane], QY = __ldg(&tj->sy[FW][t]), nyw = __ldg(&tj->ny[FW][t]);
     const float tya = cu * QY, tyb = cw * PY, h = run[HOFF + t];
     *S = tya + tyb + h;
     *d = (delta * fminf(n1u * nyw, ge.h) + 10.f * u * (fabsf(tya) + fabsf(tyb) + fabsf(h)) +
           9.1f * u * (acu * n1w + acw * n1u)) *
          1.01f;
   };
-  return gmt_targets(A, ls, gid, v, invN, ysum, theta, sy);
+  // |QY| <= |q|, |PY| <= |p| and |H| <= sqrt(G22) for a unit target
+  const float bound = (acu * n1w + acw * n1u + ge.h) * 1.01f;
+  return gmt_targets(A, ls, gid, v, invN, ysum, theta, bound, P, sy);
 }
 
 // a + b (sign 1) or a - b (sign -1) of the pair (i, j), i > j: family x of
 // both features, shift k = c_i +- c_j; needs G11 of the x family.
 __device__ __forceinline__ uint32_t gmt_addsub(const ScreenArgs &A, const GmtArgs &GA, LaneStats &ls, int opc,
                                                int64_t i, int64_t j, const gram::EpiFeat &Fi, const gram::EpiFeat &Fj,
-                                               float G11, float G22, const float *ysum, const float *theta) {
+                                               float G11, float G22, const float *ysum, const float *theta,
+                                               const float (*py)[32], const GmtStage &P) {
   const int pos = A.slot_pos[opc - 6];
   if (pos < 0) return 0;
   const uint64_t pbase = A.G.um + (tri((uint64_t)i) + (uint64_t)j - A.G.tri_o) * (uint64_t)A.G.nb;
@@ -493,14 +579,15 @@ __device__ __forceinline__ uint32_t gmt_addsub(const ScreenArgs &A, const GmtArg
   const float E = u * (2.01f * (Fi.nu[0] + Fj.nu[0]) + (fabsf(ca) + fabsf(cb)) * sqrtf(N) * (1.f + 4.f * u) + Vhi) *
                   1.02f;
   const GramVar v = gram_var(S1, dS1, S2, dS2, Z, dZ, Vhi, E, N, invN, (float)A.fmin_std_rel64);
-  const GmtTgt *ti = GA.gt + i, *tj = GA.gt + j;
+  const GmtTgt *tj = GA.gt + j;
   const float n1s = Fi.n1[0] + Fj.n1[0];
+  const int lane = threadIdx.x & 31;
   auto sy = [&](int t, float *S, float *d) {
-    const float PY = __ldg(&ti->sy[0][t]), QY = __ldg(&tj->sy[0][t]);
+    const float PY = py[t][lane], QY = __ldg(&tj->sy[0][t]);
     *S = PY + sign * QY;
     *d = (8.f * u * (fabsf(PY) + fabsf(QY)) + 9.1f * u * n1s) * 1.01f;
   };
-  return gmt_targets(A, ls, gid, v, invN, ysum, theta, sy);
+  return gmt_targets(A, ls, gid, v, invN, ysum, theta, n1s * 1.01f, P, sy);
 }
 
 // Drain one accumulator set into the running sums: this warp's half HH of
@@ -528,7 +615,8 @@ __device__ __forceinline__ void gmt_drain(uint32_t t, float (&run)[gmt::RUN], bo
 template <int G>
 __device__ __forceinline__ uint32_t gmt_pair(const ScreenArgs &A, const GmtArgs &GA, LaneStats &ls, int64_t i,
                                              int64_t j, const gram::EpiFeat &Fi, const float (&run)[gmt::RUN],
-                                             const float *ysum, const float *theta) {
+                                             const float *ysum, const float *theta, const float (*py)[32],
+                                             const GmtStage &P) {
   const int64_t n = A.F.n;
   if (i >= n || j >= n || j == i) return 0;
   const bool igt = i > j;
@@ -538,13 +626,13 @@ __device__ __forceinline__ uint32_t gmt_pair(const ScreenArgs &A, const GmtArgs 
   constexpr int H0 = 32 * G, G0 = 96 + 4 * G, G1 = 108 + 4 * G;
   uint32_t pushed = gmt_product<1, H0 + gmt::NTP>(A, GA, ls, igt ? DSE_OP_DIV : DSE_OP_RDIV, hi, lo, i, j, Fi, Fj,
                                                    run, run[G0 + 2], run[G0 + 3], run[G1 + 2], run[G1 + 3], ysum,
-                                                   theta);
+                                                   theta, py, P);
   if (igt) {
     pushed |= gmt_product<0, H0>(A, GA, ls, DSE_OP_MUL, i, j, i, j, Fi, Fj, run, run[G0], run[G0 + 1], run[G1],
-                                 run[G1 + 1], ysum, theta);
+                                 run[G1 + 1], ysum, theta, py, P);
     if (A.gram_addsub) {
-      pushed |= gmt_addsub(A, GA, ls, DSE_OP_ADD, i, j, Fi, Fj, run[G0], run[G1 + 1], ysum, theta);
-      pushed |= gmt_addsub(A, GA, ls, DSE_OP_SUB, i, j, Fi, Fj, run[G0], run[G1 + 1], ysum, theta);
+      pushed |= gmt_addsub(A, GA, ls, DSE_OP_ADD, i, j, Fi, Fj, run[G0], run[G1 + 1], ysum, theta, py, P);
+      pushed |= gmt_addsub(A, GA, ls, DSE_OP_SUB, i, j, Fi, Fj, run[G0], run[G1 + 1], ysum, theta, py, P);
     }
   }
   return pushed;
@@ -560,6 +648,10 @@ __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs 
   LaneStats ls;
   ls.zero();
   float *theta = sh.theta[ew];
+  int pend = 0;  // lane t: this warp's pushes to list t since it last raised its threshold
+  const GmtStage P{sh.pid[ew], sh.ps[ew], sh.pe[ew], sh.pl[ew], &sh.pn[ew]};
+  if (lane == 0) sh.pn[ew] = 0;
+  __syncwarp();
   int lt = 0;
   for (int tile = blockIdx.x; tile < GA.n_tiles && !aborted_warp(); tile += gridDim.x, ++lt) {
     const int2 tl = GA.tiles[tile];
@@ -587,22 +679,47 @@ __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs 
     const bool own = i < A.F.n;
     gram::EpiFeat Fi;
     if (own) Fi = gmt_rec(A, GA.gf, i);
-    // after each b-feature the lists this warp pushed to get their
-    // thresholds raised and re-read (every warp of the first wave of tiles
-    // scores with thresholds still at zero: without this, that wave alone
-    // could fill the candidate buffers)
+    // this lane's a-feature target sums (x family), target-major in shared
+    // memory: read once per tile, not once per candidate and target
+    float(*py)[32] = sh.py[ew];
+    {
+      const float4 *src = reinterpret_cast<const float4 *>(&GA.gt[own ? i : 0].sy[0][0]);
+#pragma unroll
+      for (int q4 = 0; q4 < NTP / 4; ++q4) {
+        const float4 v4 = own ? src[q4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        py[4 * q4][lane] = v4.x;
+        py[4 * q4 + 1][lane] = v4.y;
+        py[4 * q4 + 2][lane] = v4.z;
+        py[4 * q4 + 3][lane] = v4.w;
+      }
+      __syncwarp();
+    }
+    // after each b-feature the warp writes its staged pushes out, and the
+    // lists it has pushed at least 16 entries to since it last raised them
+    // get their thresholds raised and re-read (every warp of the first wave
+    // of tiles scores with thresholds still at zero: without this, that
+    // wave alone could fill the candidate buffers; later, pushes are rare
+    // and a threshold scan per push would cost more than the scoring).
+    // Lane t counts list t's pushes (staged or direct).
     auto raise = [&](uint32_t pushed) {
-      pushed = __reduce_or_sync(0xffffffffu, pushed);
+#pragma unroll
+      for (int t = 0; t < NTP; ++t) {
+        const int c = __popc(__ballot_sync(0xffffffffu, (pushed >> t) & 1u));
+        if (lane == t) pend += c;
+      }
+      gmt_flush(P, A.B, A.t0);
+      const uint32_t due = __ballot_sync(0xffffffffu, lane < NTP && pend >= 16);
+      if (lane < NTP && pend >= 16) pend = 0;
       for (int t = 0; t < NTP; ++t)
-        if (pushed & (1u << t)) refresh_theta(A.B, A.t0 + t, A.k);
-      if (pushed) {
+        if (due & (1u << t)) refresh_theta(A.B, A.t0 + t, A.k);
+      if (due) {
         for (int t = lane; t < NTP; t += 32) theta[t] = t < A.T ? ld_relaxed(&A.B.theta[A.t0 + t]) : 0.f;
         __syncwarp();
       }
     };
-    raise(own ? gmt_pair<0>(A, GA, ls, i, j0, Fi, run, sh.ysum, theta) : 0u);
-    raise(own ? gmt_pair<1>(A, GA, ls, i, j0 + 1, Fi, run, sh.ysum, theta) : 0u);
-    raise(own ? gmt_pair<2>(A, GA, ls, i, j0 + 2, Fi, run, sh.ysum, theta) : 0u);
+    raise(own ? gmt_pair<0>(A, GA, ls, i, j0, Fi, run, sh.ysum, theta, py, P) : 0u);
+    raise(own ? gmt_pair<1>(A, GA, ls, i, j0 + 1, Fi, run, sh.ysum, theta, py, P) : 0u);
+    raise(own ? gmt_pair<2>(A, GA, ls, i, j0 + 2, Fi, run, sh.ysum, theta, py, P) : 0u);
   }
   flush_stats(A, ls);
 }

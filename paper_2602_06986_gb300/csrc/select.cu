@@ -384,7 +384,10 @@ __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const 
 // |sum (v - c) y| / sqrt(Sxx) of the centred unit-norm target, its bound the
 // sums' error scale times (s + 1e-3).  With S.r_x the record {c, S1, S2,
 // E.., eps} of the entry is kept for the refit.
-__global__ void __launch_bounds__(kColThreads) k_rescore1(const SelectArgs S, const ScreenArgs A0,
+// ONE: every job is summed against its target alone (no refit vectors, a
+// single screen): the one-vector column sums.
+template <bool ONE>
+__global__ void __launch_bounds__(kColThreads, ONE ? 6 : 1) k_rescore1(const SelectArgs S, const ScreenArgs A0,
                                                           const ScreenArgs *batch) {
   __shared__ ColShared sh;
   const unsigned nj = *S.n_jobs;
@@ -414,7 +417,10 @@ __global__ void __launch_bounds__(kColThreads) k_rescore1(const SelectArgs S, co
       V.e[m] = m == 0 || m >= V.nv ? 0 : S.xexp[m - 1];
     }
     ColSums cs;
-    col_sums(A.F, op, a, b, N, V, cs, sh);
+    if (ONE)
+      col_sums1(A.F, op, a, b, N, V, cs, sh);
+    else
+      col_sums(A.F, op, a, b, N, V, cs, sh);
     if (threadIdx.x == 0) {
       const double eps = col_err_scale(cs, N);
       if (S.r_x && !batch) {
@@ -526,7 +532,10 @@ dse_status launch_select(const SelectArgs &S, const ScreenArgs &A, int sms, cuda
   k_sel_exact<<<S.n_lists, 1024, 0, st>>>(S);
   k_sel_classify<<<g, 256, 0, st>>>(S);
   const bool one = batch || A.mode != DSE_MODE_AGGREGATED || A.T == 1;
-  if (one) k_rescore1<<<sms * 8, kColThreads, 0, st>>>(S, A, batch);
+  if (one && !batch && S.nx == 0)
+    k_rescore1<true><<<sms * 16, kColThreads, 0, st>>>(S, A, batch);
+  else if (one)
+    k_rescore1<false><<<sms * 8, kColThreads, 0, st>>>(S, A, batch);
   else if (A.N <= 4096) k_rescore_warp<16><<<sms * 8, 256, 0, st>>>(S, A);
   else k_rescore<16><<<sms * 8, kRes, 0, st>>>(S, A, batch);
   const dim3 gr((unsigned)std::max(1, std::min(1024, (sms * 2 + S.n_lists - 1) / S.n_lists)), S.n_lists);

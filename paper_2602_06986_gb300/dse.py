@@ -109,6 +109,7 @@ EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_cou
            "dse_expr_string", "dse_candidate_units", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
            "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
            "dse_residual_loop", "dse_l0_search", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_check_wait",
+           "dse_measure_peaks",
            "dse_debug_fail_alloc", "dse_set_tuning", "dse_get_tuning", "dse_kernel_launches", "dse_last_error",
            "dse_version"]
 
@@ -147,6 +148,7 @@ def lib():
         L.dse_ls_refit.argtypes = [vp, C.POINTER(RefitDesc), C.POINTER(u64), C.POINTER(C.c_double), vp, vp]
         L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
         L.dse_check_wait.argtypes = [C.c_uint32, i32, vp]
+        L.dse_measure_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.dse_set_tuning.argtypes = [C.POINTER(Tuning)]
         L.dse_get_tuning.argtypes = [C.POINTER(Tuning)]
         L.dse_debug_fail_alloc.argtypes = [i64]
@@ -185,6 +187,14 @@ def get_tuning():
 def check_wait(polls, arrive, stream=None):
     """Status of the bounded device wait probe (dse_check_wait)."""
     return int(lib().dse_check_wait(polls, 1 if arrive else 0, stream))
+
+
+def measure_peaks(stream=None) -> dict:
+    """Issue rates of the FP32 FMA, MUFU and FP64 FMA pipes on the current
+    device, lane operations per second (dse_measure_peaks)."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().dse_measure_peaks(C.byref(a), C.byref(b), C.byref(c), stream))
+    return {"fp32_fma_per_s": a.value, "sfu_per_s": b.value, "fp64_fma_per_s": c.value}
 
 
 def debug_fail_alloc(after):

@@ -90,8 +90,11 @@ def test_no_cpu_fallback(dse):
     with pytest.raises(dse.DseError) as e:
         dse.Space(X, None, 1 << 8, 2)
     assert e.value.status == dse.ECUDA
-    # the wait probe needs the device too
+    # the wait probe and the peak probe need the device too
     assert dse.check_wait(10, arrive=True) == dse.ECUDA
+    with pytest.raises(dse.DseError) as e:
+        dse.measure_peaks()
+    assert e.value.status == dse.ECUDA
     assert dse.check_wait(0, arrive=True) == dse.EINVAL
 
 
