@@ -383,7 +383,16 @@ dse_status dse_ls_refit(dse_space *space, const dse_refit_desc *desc, uint64_t *
    the end (and re-runs an iteration on the host-driven path if its
    candidate buffer overflowed).  Synchronises.  Errors: DSE_EINVAL when an
    iteration finds no full-rank fit, DSE_EOVERFLOW on a persistent overflow,
-   the codes of dse_sis_screen otherwise. */
+   the codes of dse_sis_screen otherwise.
+
+   Resume: with n_fixed > 0 the descriptors d_1..d_n_fixed are taken as
+   chosen (a checkpoint of an earlier call), the fit with all of them and
+   its residual r_n_fixed are recomputed on the device (the same refit
+   kernels, so the same bits as the iteration that chose d_n_fixed), and the
+   loop continues with D = n_fixed + 1..n_iter.  out gets the fixed ids in
+   chosen[0..n_fixed), the recomputed fit's RMSE and coefficients in entry
+   n_fixed - 1, NaN RMSEs and zero statistics for the earlier entries (the
+   checkpoint holds them), and sis_ids rows only for the iterations run. */
 typedef struct {
   const double *y;        /* N values, host or device                       */
   int32_t y_on_device;
@@ -393,6 +402,9 @@ typedef struct {
   int32_t flags;          /* DSE_FLAG_TIMING / _TIMING_MAIN: kernel_ms of
                              each screen                                     */
   void *stream;           /* cudaStream_t                                   */
+  int32_t n_fixed;        /* 0..n_iter-1 descriptors already chosen         */
+  int32_t reserved0;
+  const uint64_t *fixed;  /* host, n_fixed distinct candidate ids           */
 } dse_loop_desc;
 
 typedef struct {

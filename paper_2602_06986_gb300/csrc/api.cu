@@ -949,6 +949,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
                                      double *residual) {
   cudaStream_t st = (cudaStream_t)d->stream;
   const int D = d->n_iter;
+  const int it0 = d->n_fixed;  // first iteration run (resume after it0 chosen descriptors)
   const int64_t N = sp->N, k = d->k;
   dse_screen_desc sd{};
   sd.ld_y = N;
@@ -987,6 +988,10 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   sc.add(&ids, (size_t)D * k);
   sc.add(&rscr, refit_chain_bytes(N, k));
   sc.add(&rx, fused ? (size_t)R->n_lists * kp->plan.cap * 8 : 1);
+  uint64_t *cand1 = nullptr;
+  int64_t *n1 = nullptr;
+  sc.add(&cand1, 1);
+  sc.add(&n1, 1);
   size_t bytes = 0;
   DSE_TRY(sc.alloc(&own.scratch, &bytes));
   const double *y = d->y;
@@ -998,6 +1003,24 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   DSE_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * D * N, st));
   DSE_CUDA(cudaMemsetAsync(small, 0, sizeof(unsigned long long) * D * kSmall, st));
   DSE_CUDA(cudaMemsetAsync(ids, 0xFF, sizeof(uint64_t) * D * k, st));
+  if (it0 > 0) {
+    // resume: the chosen descriptors, and the fit with all of them (the
+    // last one as the only candidate of iteration it0 - 1's refit) for the
+    // residual r_it0 the next screen takes
+    uint64_t *h = static_cast<uint64_t *>(pinned_staging(sizeof(uint64_t) * (kLoopMax + 1) + sizeof(int64_t)));
+    if (!h) return DSE_ENOMEM;
+    for (int i = 0; i < it0; ++i) h[i] = d->fixed[i];
+    int64_t one = 1;
+    memcpy(h + kLoopMax, &one, sizeof(int64_t));
+    DSE_CUDA(cudaMemcpyAsync(fid, h, sizeof(uint64_t) * it0, cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(cand1, h + it0 - 1, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaMemcpyAsync(n1, h + kLoopMax, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    DSE_CUDA(cudaStreamSynchronize(st));  // (the staging area is reused)
+    refit_chain_prep(sp, y, fid, it0 - 1, rscr, 1, st);
+    refit_chain_fit(sp, y, fid, it0 - 1, cand1, 1, n1, rscr, false, r + (size_t)(it0 - 1) * N,
+                    rep + (size_t)(it0 - 1) * kReport, fid + it0 - 1, st);
+    DSE_CUDA(cudaGetLastError());
+  }
 
   auto snapshot = [&](int it) -> dse_status {
     note_launches(1);
@@ -1033,7 +1056,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   auto step = [&](int it) -> dse_status {
     const double *src = it == 0 ? y : r + (size_t)(it - 1) * N;
     prepare(it);
-    DSE_TRY(screen_enqueue_target(R, src, N, it == 0));
+    DSE_TRY(screen_enqueue_target(R, src, N, it == it0));
     DSE_TRY(snapshot(it));
     fit(it);
     DSE_CUDA(cudaGetLastError());
@@ -1056,14 +1079,14 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
   size_t tmark[kLoopMax + 1];  // each iteration's range of timing events
   for (int it = 0; it < D; ++it) {
     tmark[it] = R->timing.size();
-    DSE_TRY(step(it));
+    if (it >= it0) DSE_TRY(step(it));
   }
   tmark[D] = R->timing.size();
   unsigned long long *hs = nullptr;
   double *hr = nullptr;
   DSE_TRY(read_back(&hs, &hr));
   int first_bad = D;
-  for (int it = 0; it < D && first_bad == D; ++it) {
+  for (int it = it0; it < D && first_bad == D; ++it) {
     const unsigned long long *sm = hs + (size_t)it * kSmall;
     if ((unsigned)sm[ST_COUNT] != 0u) first_bad = it;  // buffer overflow
   }
@@ -1084,6 +1107,11 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
     DSE_TRY(read_back(&hs, &hr));
   }
   for (int it = 0; it < D; ++it) {
+    if (it < it0 - 1) {  // chosen in the call being resumed
+      out->chosen[it] = d->fixed[it];
+      out->rmse[it] = NAN;
+      continue;
+    }
     const unsigned long long *sm = hs + (size_t)it * kSmall;
     const int herr = (int)(unsigned)sm[ST_COUNT + 4];
     if (herr) {
@@ -1106,6 +1134,7 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
     out->chosen[it] = (uint64_t)bid;
     out->rmse[it] = rr[2];
     for (int c = 0; c < 5; ++c) out->coefs[it][c] = c < it + 2 ? rr[3 + c] : 0.0;
+    if (it < it0) continue;  // the resumed fit: no screen of its own
     if (it < first_bad) {
       const unsigned bc = (unsigned)sm[ST_COUNT + 1];
       const int64_t nout = (int64_t)sm[ST_COUNT + 2];
@@ -1361,9 +1390,18 @@ dse_status dse_residual_loop(dse_space *s, const dse_loop_desc *d, dse_loop_resu
   dse::NvtxRange nvtx_range_("dse_residual_loop");
   clear_error();
   if (!s || !d || !out || !d->y || d->n_iter < 1 || d->n_iter > kLoopMax || d->k < 1 || d->k > (1 << 20) ||
-      d->precision < 0 || d->precision > DSE_PREC_AUTO) {
+      d->precision < 0 || d->precision > DSE_PREC_AUTO || d->n_fixed < 0 || d->n_fixed >= d->n_iter ||
+      (d->n_fixed > 0 && !d->fixed)) {
     set_error("invalid loop descriptor");
     return DSE_EINVAL;
+  }
+  for (int i = 0; i < d->n_fixed; ++i) {
+    bool dup = false;
+    for (int j = 0; j < i; ++j) dup = dup || d->fixed[j] == d->fixed[i];
+    if (dup || d->fixed[i] >= (uint64_t)s->n + s->geom.slots) {
+      set_error("fixed descriptor %d is out of range or repeated", i);
+      return DSE_EINVAL;
+    }
   }
   *out = dse_loop_result{};
   DSE_TRY(check_device());

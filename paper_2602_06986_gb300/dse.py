@@ -93,7 +93,8 @@ BATCH_GRAPH = 1
 
 class LoopDesc(C.Structure):
     _fields_ = [("y", C.c_void_p), ("y_on_device", C.c_int32), ("n_iter", C.c_int32), ("k", C.c_int64),
-                ("precision", C.c_int32), ("flags", C.c_int32), ("stream", C.c_void_p)]
+                ("precision", C.c_int32), ("flags", C.c_int32), ("stream", C.c_void_p), ("n_fixed", C.c_int32),
+                ("reserved0", C.c_int32), ("fixed", C.c_void_p)]
 
 
 class L0Desc(C.Structure):
@@ -450,15 +451,18 @@ class Space:
         _check(lib().dse_sis_screen(self._h, C.byref(d), C.byref(h)))
         return Result(h, 1 if mode == MODE_AGGREGATED else T, k)
 
-    def residual_loop(self, y, n_iter, k, precision=PREC_FP32, sis_ids=None, residual=None, stream=None, flags=0):
+    def residual_loop(self, y, n_iter, k, precision=PREC_FP32, sis_ids=None, residual=None, stream=None, flags=0,
+                      fixed=()):
         """The residual loop on the device (dse_residual_loop): returns a dict
         with the chosen ids, RMSEs, coefficients and per-iteration screen
         statistics.  ``sis_ids`` / ``residual``: optional output buffers
-        (numpy or torch CUDA) of n_iter*k ids and N values."""
+        (numpy or torch CUDA) of n_iter*k ids and N values.  ``fixed``:
+        descriptors already chosen (resume after len(fixed) iterations)."""
         if isinstance(y, np.ndarray):
             y = np.ascontiguousarray(y, dtype=np.float64)
         py, ydev = _ptr(y)
-        d = LoopDesc(py, ydev, n_iter, k, precision, flags, stream)
+        fx = np.ascontiguousarray(np.asarray(fixed, dtype=np.uint64))
+        d = LoopDesc(py, ydev, n_iter, k, precision, flags, stream, len(fx), 0, fx.ctypes.data if len(fx) else None)
         out = LoopResult()
         pi, _ = _ptr(sis_ids)
         pr, _ = _ptr(residual)

@@ -47,7 +47,7 @@ def test_struct_layouts_match_header(dse):
     assert C.sizeof(dse.RefitDesc) == 8 + 4 * 2 + 8 + 8 + 8 + 4 * 2 + 8
     assert C.sizeof(dse.BatchItem) == 8 + 8 + 4 * 2
     assert C.sizeof(dse.BatchDesc) == 8 + 4 * 2 + 8
-    assert C.sizeof(dse.LoopDesc) == 8 + 4 * 2 + 8 + 4 * 2 + 8
+    assert C.sizeof(dse.LoopDesc) == 8 + 4 * 2 + 8 + 4 * 2 + 8 + 4 * 2 + 8
     assert C.sizeof(dse.L0Desc) == 8 + 4 * 2 + 8 + 8 + 4 * 2 + 8
     assert C.sizeof(dse.LoopResult) == 8 * 4 + 8 * 4 + 8 * 20 + 4 * C.sizeof(dse.Stats)
 
