@@ -72,6 +72,8 @@ typedef int32_t dse_status;
 #define DSE_ERANGE (-4)    /* id or id range outside the candidate space */
 #define DSE_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
 #define DSE_EOVERFLOW (-6) /* space, unit exponent or buffer beyond limits */
+#define DSE_EBOUNDS (-7)   /* bounds-checked build only: an index check
+                              failed (the access was skipped)              */
 
 enum {
   DSE_OP_SQUARE = 0, DSE_OP_CUBE = 1, DSE_OP_INV = 2, DSE_OP_SQRT = 3, DSE_OP_EXP = 4,
@@ -514,6 +516,17 @@ dse_status dse_check_wait(uint32_t polls, int32_t arrive, void *stream);
    warps per SM, best of three timed rounds after a warm-up round).  The
    denominators of the ALU rooflines.  Synchronises. */
 dse_status dse_measure_peaks(double *fp32_fma_per_s, double *sfu_per_s, double *fp64_fma_per_s, void *stream);
+
+/* Bounds-checked builds (compiled with DSE_CHECK_BOUNDS, libdse_checked.so;
+   the substitute for a memory checker where none can run): the screening
+   kernels check their gathered and computed indices (feature rows and
+   samples, tile coordinates against the operand images, candidate ids
+   against the screened range, list positions) and, on a violation, skip
+   the access and store DSE_EBOUNDS in the screen's error word, which the
+   screen then returns.  dse_bounds_probe runs one such check on the device
+   (index against limit) and returns DSE_EBOUNDS when it fails, DSE_OK when
+   it holds; in a normal build it returns DSE_EINVAL (no checks compiled). */
+dse_status dse_bounds_probe(int64_t index, int64_t limit, void *stream);
 
 /* Test hook: the device allocation after `after` more successful ones
    fails with DSE_ENOMEM (once); a negative value switches the hook off.

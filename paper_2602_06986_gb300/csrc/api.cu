@@ -821,7 +821,9 @@ static dse_status finish(dse_result *R) {
     const unsigned long long *hs = reinterpret_cast<const unsigned long long *>(h + o_stats);
     const int herr = *reinterpret_cast<const int *>(h + o_err);
     if (herr) {
-      set_error(herr == DSE_ETIMEOUT ? "a bounded device wait timed out" : "invalid target (zero variance or not finite)");
+      set_error(herr == DSE_ETIMEOUT   ? "a bounded device wait timed out"
+                : herr == DSE_EBOUNDS ? "an index check of the bounds-checked build failed"
+                                      : "invalid target (zero variance or not finite)");
       return herr;
     }
     if (hs[ST_ESC_OVERFLOW]) {
@@ -1115,8 +1117,9 @@ static dse_status residual_loop_impl(dse_space *sp, const dse_loop_desc *d, dse_
     const unsigned long long *sm = hs + (size_t)it * kSmall;
     const int herr = (int)(unsigned)sm[ST_COUNT + 4];
     if (herr) {
-      set_error(herr == DSE_ETIMEOUT ? "a bounded device wait timed out"
-                                     : "invalid target or residual (zero variance or not finite)");
+      set_error(herr == DSE_ETIMEOUT   ? "a bounded device wait timed out"
+                : herr == DSE_EBOUNDS ? "an index check of the bounds-checked build failed"
+                                      : "invalid target or residual (zero variance or not finite)");
       return herr;
     }
     if (sm[ST_ESC_OVERFLOW]) {

@@ -169,8 +169,9 @@ dse_status finish(dse_batch *b) {
     DSE_CUDA(cudaMemcpyAsync(bc.data(), b->B.count, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, st));
     DSE_CUDA(cudaStreamSynchronize(st));
     if (herr) {
-      set_error(herr == DSE_ETIMEOUT ? "a bounded device wait timed out"
-                                     : "invalid target (zero variance or not finite)");
+      set_error(herr == DSE_ETIMEOUT   ? "a bounded device wait timed out"
+                : herr == DSE_EBOUNDS ? "an index check of the bounds-checked build failed"
+                                      : "invalid target (zero variance or not finite)");
       return herr;
     }
     for (int p = 0; p < n; ++p)

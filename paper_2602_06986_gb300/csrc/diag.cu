@@ -21,7 +21,44 @@ __global__ void k_wait_probe(uint32_t polls, int arrive, int *status) {
   *status = mbar_wait_bounded(&bar, 0, polls) ? DSE_OK : DSE_ETIMEOUT;
 }
 
+// One bounds check of the checked build on the device: status gets
+// DSE_EBOUNDS when index is outside [0, limit), DSE_OK otherwise.
+__global__ void k_bounds_probe(int64_t index, int64_t limit, int *status) {
+  if (threadIdx.x != 0) return;
+  *status = DSE_OK;
+  if (DSE_IN_BOUNDS(index, limit, status)) {
+  }
+}
+
 }  // namespace dse
+
+extern "C" dse_status dse_bounds_probe(int64_t index, int64_t limit, void *stream) {
+  using namespace dse;
+  clear_error();
+#ifndef DSE_CHECK_BOUNDS
+  (void)index;
+  (void)limit;
+  (void)stream;
+  set_error("not a bounds-checked build (compile with DSE_CHECK_BOUNDS)");
+  return DSE_EINVAL;
+#else
+  DSE_TRY(check_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  AllocStream as(st);
+  int *d = nullptr;
+  DSE_TRY(dmalloc(reinterpret_cast<void **>(&d), sizeof(int), "bounds probe status"));
+  int h = DSE_ECUDA;
+  note_launches(1);
+  k_bounds_probe<<<1, 32, 0, st>>>(index, limit, d);
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(d);
+  if (e) return cuda_status(e, "bounds probe");
+  if (h == DSE_EBOUNDS) set_error("index %lld outside [0, %lld)", (long long)index, (long long)limit);
+  return h;
+#endif
+}
 
 extern "C" dse_status dse_check_wait(uint32_t polls, int32_t arrive, void *stream) {
   using namespace dse;

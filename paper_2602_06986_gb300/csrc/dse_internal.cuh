@@ -226,6 +226,23 @@ Tuning tuning();
 // Launch bookkeeping (process-wide count of the library's kernel launches).
 void note_launches(int64_t n);
 
+// ---------------------------------------------------- bounds-checked build
+// DSE_IN_BOUNDS(i, n, err): with DSE_CHECK_BOUNDS, whether 0 <= i < n; on a
+// violation DSE_EBOUNDS goes to the error word *err (when not null) and the
+// caller skips the access.  Always true otherwise (no code).
+#ifdef DSE_CHECK_BOUNDS
+__device__ __forceinline__ bool dse_in_bounds(int64_t i, int64_t n, int *err) {
+  if (i >= 0 && i < n) return true;
+  if (err) atomicExch(err, DSE_EBOUNDS);
+  return false;
+}
+#define DSE_IN_BOUNDS(i, n, err) ::dse::dse_in_bounds((int64_t)(i), (int64_t)(n), (err))
+#else
+#define DSE_IN_BOUNDS(i, n, err) true
+#endif
+// the operands a (and b >= 0) of a decoded candidate are rows of F
+#define DSE_OPERANDS_OK(F, a, b, err) (DSE_IN_BOUNDS((a), (F).n, (err)) && ((b) < 0 || DSE_IN_BOUNDS((b), (F).n, (err))))
+
 // ----------------------------------------------------------- PTX helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

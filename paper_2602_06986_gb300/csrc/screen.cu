@@ -250,6 +250,7 @@ __device__ __forceinline__ int feature_setup(const ScreenArgs &A, uint64_t w, ui
     gid = (uint64_t)A.n_stored + p;
     int64_t b;
     decode_flat(A.G, p, &op, &f, &b);
+    if (!DSE_IN_BOUNDS(f, A.F.n, A.err)) f = 0;  // (the error stands; the candidate is scored on row 0)
     if ((op == DSE_OP_EXP || op == DSE_OP_LOG) && A.explog_dimensionless && !(A.F.flags[f] & F_DIMLESS))
       reason = DSE_R_UNIT;
     else if (A.max_complexity > 0 && A.F.cplx[f] + 1 > A.max_complexity)
@@ -1242,6 +1243,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const Sc
     int op;
     int64_t a, b;
     decode_gid(A, gid, &op, &a, &b);
+    if (!DSE_OPERANDS_OK(A.F, a, b, A0.err)) continue;
     const double c = cand_value64(A.F, A.G, A.n_stored, gid, 0, op, a, b);
     // sum (v-c), sum (v-c)^2, sum v^2, number of non-finite values
     double st[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1316,6 +1318,7 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
     int op;
     int64_t a, b;
     decode_gid(A, gid, &op, &a, &b);
+    if (!DSE_OPERANDS_OK(A.F, a, b, A0.err)) continue;
     const double c = cand_value64(A.F, A.G, A.n_stored, gid, 0, op, a, b);
     const double *y = A.y64 + (int64_t)A.t0 * A.ldy;
     // sum (v-c), sum (v-c)^2, sum v^2, non-finite count, sum (v-c) y, sum y;

@@ -178,12 +178,14 @@ __device__ __forceinline__ void cand_score_num(const CandInterval<R> &ci, R S1, 
 // Record the reason code a kernel assigned to candidate gid (in the first
 // target pass; a screen re-run writes the same codes again).
 __device__ __forceinline__ void note_why(const ScreenArgs &A, uint64_t gid, int reason) {
-  if (A.why && A.first_pass) A.why[gid - A.id_begin] = (int8_t)reason;
+  if (A.why && A.first_pass && DSE_IN_BOUNDS(gid - A.id_begin, A.id_end - A.id_begin, A.err))
+    A.why[gid - A.id_begin] = (int8_t)reason;
 }
 
 // Record the score interval a kernel computed for candidate gid in list l.
 __device__ __forceinline__ void note_ivl(const ScreenArgs &A, uint64_t gid, int l, float s, float e) {
-  if (A.ivl) A.ivl[(gid - A.id_begin) * (uint64_t)A.n_lists + (uint64_t)l] = make_float2(s, e);
+  if (A.ivl && DSE_IN_BOUNDS(gid - A.id_begin, A.id_end - A.id_begin, A.err) && DSE_IN_BOUNDS(l, A.n_lists, A.err))
+    A.ivl[(gid - A.id_begin) * (uint64_t)A.n_lists + (uint64_t)l] = make_float2(s, e);
 }
 
 // ----------------------------------------------------- per-lane statistics

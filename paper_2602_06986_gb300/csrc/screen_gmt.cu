@@ -327,6 +327,7 @@ struct GmtArgs {
   int n_tiles;
   int nchunks, nblocks;
   float delta;
+  int na, nb;  // a-blocks and b-blocks of the images
 };
 
 // The epilogue record of feature f (a-priori fields and sums).
@@ -781,7 +782,8 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
       int lt = 0;
       uint32_t issued = 0;
       for (int tile = blockIdx.x; tile < GA.n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
-        const int2 tl = GA.tiles[tile];
+        int2 tl = GA.tiles[tile];
+        if (!(DSE_IN_BOUNDS(tl.x, GA.na, A.err) && DSE_IN_BOUNDS(tl.y, GA.nb, A.err))) tl = make_int2(0, 0);
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
           const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
@@ -980,7 +982,8 @@ dse_status launch_pair_gmt(const ScreenArgs &A, const void *space_buf, void *scr
     DSE_CUDA(cudaFuncSetAttribute(k_pair_gmt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmt::smem_total()));
     attr[dev & 63] = true;
   }
-  GmtArgs GA{aimg, bimg, gf, gt, tiles, n_tiles, nchunks, (nchunks + gmt::DB - 1) / gmt::DB, gmt_delta(N)};
+  GmtArgs GA{aimg, bimg, gf, gt, tiles, n_tiles, nchunks, (nchunks + gmt::DB - 1) / gmt::DB, gmt_delta(N),
+             (int)gmt_na(n), (int)gmt_nb(n)};
   ScreenArgs B = A;
   B.group = 1;
   const int grid = sms < n_tiles ? sms : n_tiles;

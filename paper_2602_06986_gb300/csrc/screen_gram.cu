@@ -228,6 +228,7 @@ struct GramArgs {
   int n_tiles;
   int nchunks;
   float delta;
+  int na, nb;  // a-blocks and b-blocks of the images
 };
 
 __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs A, const GramArgs GA) {
@@ -287,7 +288,8 @@ __global__ void __launch_bounds__(gram::THREADS, 1) k_pair_gram(const ScreenArgs
       int lt = 0;
       uint32_t issued = 0;
       for (int tile = blockIdx.x; tile < GA.n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
-        const int2 tl = GA.tiles[tile];
+        int2 tl = GA.tiles[tile];
+        if (!(DSE_IN_BOUNDS(tl.x, GA.na, A.err) && DSE_IN_BOUNDS(tl.y, GA.nb, A.err))) tl = make_int2(0, 0);
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
           const uint32_t gc = (uint32_t)lt * nchunks + c, st = gc % NS, u = gc / NS;
@@ -623,7 +625,7 @@ dse_status launch_pair_gram(const ScreenArgs &A, const void *space_buf, void *sc
     DSE_CUDA(cudaFuncSetAttribute(k_pair_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram::smem_total()));
     attr[dev & 63] = true;
   }
-  GramArgs GA{aimg, bimg, gf, gt, tiles, n_tiles, nchunks, gram_delta(N)};
+  GramArgs GA{aimg, bimg, gf, gt, tiles, n_tiles, nchunks, gram_delta(N), (int)na, (int)nb};
   ScreenArgs B = A;
   B.group = 1;
   const int grid = sms < n_tiles ? sms : n_tiles;

@@ -406,6 +406,7 @@ __global__ void __launch_bounds__(kColThreads, ONE ? 6 : 1) k_rescore1(const Sel
     } else {
       decode_flat(A.G, gid - (uint64_t)A.n_stored, &op, &a, &b);
     }
+    if (!DSE_OPERANDS_OK(A.F, a, b, A0.err)) continue;
     const int t = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
     const int nx = batch ? 0 : S.nx;
     ColVecs V;

@@ -14,9 +14,10 @@ import os
 import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libdse.so")
+# DSE_LIB_VARIANT=checked loads the bounds-checked build (DSE_CHECK_BOUNDS)
+LIB_PATH = os.path.join(PKG, "libdse_checked.so" if os.environ.get("DSE_LIB_VARIANT") == "checked" else "libdse.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ERANGE, ETIMEOUT, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ERANGE, ETIMEOUT, EOVERFLOW, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 SQUARE, CUBE, INV, SQRT, EXP, LOG, ADD, SUB, MUL, DIV, RDIV, ABSDIFF = range(12)
 PRIMARY = 15
 MODE_PER_TARGET, MODE_AGGREGATED = 0, 1
@@ -110,7 +111,7 @@ EXPORTS = ["dse_build_space", "dse_space_free", "dse_space_size", "dse_space_cou
            "dse_expr_string", "dse_candidate_units", "dse_sis_screen", "dse_result_free", "dse_topk_fetch", "dse_result_stats",
            "dse_sis_screen_batched", "dse_batch_rescreen", "dse_batch_fetch", "dse_batch_stats", "dse_batch_free",
            "dse_residual_loop", "dse_l0_search", "dse_ls_refit", "dse_ls_refit_noalloc", "dse_check_wait",
-           "dse_measure_peaks",
+           "dse_measure_peaks", "dse_bounds_probe",
            "dse_debug_fail_alloc", "dse_set_tuning", "dse_get_tuning", "dse_kernel_launches", "dse_last_error",
            "dse_version"]
 
@@ -150,6 +151,7 @@ def lib():
         L.dse_ls_refit_noalloc.argtypes = L.dse_ls_refit.argtypes
         L.dse_check_wait.argtypes = [C.c_uint32, i32, vp]
         L.dse_measure_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+        L.dse_bounds_probe.argtypes = [i64, i64, vp]
         L.dse_set_tuning.argtypes = [C.POINTER(Tuning)]
         L.dse_get_tuning.argtypes = [C.POINTER(Tuning)]
         L.dse_debug_fail_alloc.argtypes = [i64]
@@ -196,6 +198,12 @@ def measure_peaks(stream=None) -> dict:
     a, b, c = C.c_double(), C.c_double(), C.c_double()
     _check(lib().dse_measure_peaks(C.byref(a), C.byref(b), C.byref(c), stream))
     return {"fp32_fma_per_s": a.value, "sfu_per_s": b.value, "fp64_fma_per_s": c.value}
+
+
+def bounds_probe(index, limit, stream=None):
+    """Status of one device-side index check (dse_bounds_probe): EBOUNDS
+    outside [0, limit), OK inside; EINVAL in a build without the checks."""
+    return int(lib().dse_bounds_probe(index, limit, stream))
 
 
 def debug_fail_alloc(after):
