@@ -1212,7 +1212,7 @@ constexpr int kEsc = 128;
 
 // Block sums of v: in every thread, or (ALL = false) in thread 0 only (the
 // FP64 adds then leave the SM's FP64 units to the other blocks).
-template <int NV, bool ALL = true>
+template <int NV, bool ALL = true, int THREADS = kEsc>
 __device__ __forceinline__ void block_sum64(double (&v)[NV], double *sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -1225,7 +1225,7 @@ __device__ __forceinline__ void block_sum64(double (&v)[NV], double *sm) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       double t = 0.0;
-      for (int ww = 0; ww < kEsc / 32; ++ww) t += sm[ww * NV + i];
+      for (int ww = 0; ww < THREADS / 32; ++ww) t += sm[ww * NV + i];
       v[i] = t;
     }
   }
@@ -1298,6 +1298,128 @@ __global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const Sc
       const double sc = sqrt(agg / (double)A.T);
       const float sf = (float)sc;
       const float ef = (float)(err * (sc + 1e-3)) + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+      note_ivl(A, gid, A.t0, sf, ef);
+      push_one(A.B, A.t0, gid, sf, ef);
+    }
+  }
+}
+
+// Many targets, 8192 <= N <= 40960 (single screens): the FP64 pass of
+// k_escalate also keeps w_s = fl32(v_s - c) in
+// shared memory, and the numerators come from it in FP32 (blocks of 16
+// samples per thread, then warp shuffles and the warps in FP64), without a
+// second FP64 evaluation of every sample.  Numerator error for target t,
+// with e_s = fl32(w_s - fl32(vbar - c)) and the FP32 target y32 (within u of
+// the FP64 one per sample), by Cauchy-Schwarz (|y| = 1):
+//   u (2 |v - c| + 2 |vbar - c| sqrt(N)) + (u + gamma) |e|,
+//   gamma = (16 + m / 16 + 8) u, m = N / kEscS terms per thread,
+// |e| <= sqrt(Sxx) + 2u of the above; the score's bound is that / sqrt(Sxx)
+// plus the FP64 part's.  Columns outside [2^-60, 2^60] take k_escalate.
+constexpr int64_t kEscStashMax = 40960;  // samples kept in shared memory (160 KB)
+constexpr int kEscS = 512;                // threads per candidate (FP64 latency wants many warps)
+
+__global__ void __launch_bounds__(kEscS, 2) k_escalate_stash(const ScreenArgs A) {
+  extern __shared__ float wsm[];
+  __shared__ double sm[(kEscS / 32) * 16];
+  const unsigned n = min(*A.esc_count, (unsigned)A.esc_cap);
+  const int64_t N = A.N;
+  const float u = 5.9604644775390625e-8f;
+  for (unsigned w = blockIdx.x; w < n; w += gridDim.x) {
+    const uint64_t gid = A.esc_id[w];
+    int op;
+    int64_t a, b;
+    decode_gid(A, gid, &op, &a, &b);
+    if (!DSE_OPERANDS_OK(A.F, a, b, A.err)) continue;
+    const double c = cand_value64(A.F, A.G, A.n_stored, gid, 0, op, a, b);
+    double st[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t s = threadIdx.x; s < N; s += kEscS) {
+      const double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
+      if (!isfinite(v)) st[3] += 1.0;
+      const double d = v - c;
+      st[0] += d;
+      st[1] = fma(d, d, st[1]);
+      st[2] = fma(v, v, st[2]);
+      wsm[s] = (float)d;
+    }
+    block_sum64<4, true, kEscS>(st, sm);
+    const double sxx = st[1] - st[0] * (st[0] / (double)N);
+    int good = st[3] == 0.0 && isfinite(sxx);
+    if (good && A.fmin_std_rel64 >= 0.0)
+      good = __dsqrt_rn(fmax(sxx, 0.0) / (double)N) > A.fmin_std_rel64 * __dsqrt_rn(st[2] / (double)N);
+    if (threadIdx.x == 0) {
+      atomicAdd(&A.stats[good ? ST_REASON0 + DSE_VALID : ST_REASON0 + DSE_R_REALISED], 1ull);
+      if (good) atomicAdd(&A.stats[ST_EVALUATED], 1ull);
+      if (A.why && DSE_IN_BOUNDS(gid - A.id_begin, A.id_end - A.id_begin, A.err))
+        A.why[gid - A.id_begin] = (int8_t)(good ? DSE_VALID : DSE_R_REALISED);
+    }
+    if (!good || !(sxx > 0.0)) continue;
+    const double err = (double)(N / kEscS + 64) * 1.1102230246251565e-16 * 16.0;
+    const double dm = st[0] / (double)N;  // vbar - c
+    const double q = sqrt(sxx), nvc = sqrt(st[1]), dmn = fabs(dm) * sqrt((double)N);
+    const bool fp32 = q > 8.67e-19 && nvc < 1.15e18 && dmn < 1.15e18;  // 2^-60 .. 2^60
+    const float dm32 = (float)dm;
+    const double m = (double)((N + kEscS - 1) / kEscS);
+    const double gamma = (16.0 + m / 16.0 + 8.0) * (double)u;
+    const double esx = q + 2.0 * (double)u * (2.0 * nvc + 2.0 * dmn);
+    const double dnum = ((double)u * (2.0 * nvc + 2.0 * dmn) + ((double)u + gamma) * esx) * 1.01;
+    double agg = 0.0;
+    constexpr int TG = 8;  // targets per pass over the kept values
+    for (int t0 = 0; t0 < A.T; t0 += TG) {
+      double sy[TG];
+#pragma unroll
+      for (int t = 0; t < TG; ++t) sy[t] = 0.0;
+      if (fp32) {
+        float acc[TG], blk[TG];
+#pragma unroll
+        for (int t = 0; t < TG; ++t) acc[t] = blk[t] = 0.f;
+        int nb = 0;
+        for (int64_t s = threadIdx.x; s < N; s += kEscS) {
+          const float e = wsm[s] - dm32;
+#pragma unroll
+          for (int t = 0; t < TG; ++t)
+            if (t0 + t < A.T) blk[t] = fmaf(e, A.y32[(int64_t)(A.t0 + t0 + t) * A.ldy + s], blk[t]);
+          if (++nb == 16) {
+            nb = 0;
+#pragma unroll
+            for (int t = 0; t < TG; ++t) {
+              acc[t] += blk[t];
+              blk[t] = 0.f;
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < TG; ++t) sy[t] = (double)(acc[t] + blk[t]);
+      } else {
+        for (int64_t s = threadIdx.x; s < N; s += kEscS) {
+          const double d = (cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b) - c) - dm;
+#pragma unroll
+          for (int t = 0; t < TG; ++t)
+            if (t0 + t < A.T) sy[t] = fma(d, A.y64[(int64_t)(A.t0 + t0 + t) * A.ldy + s], sy[t]);
+        }
+      }
+      block_sum64<TG, true, kEscS>(sy, sm);
+      if (threadIdx.x == 0) {
+        for (int t = 0; t < TG && t0 + t < A.T; ++t) {
+          const double sc = fabs(sy[t]) / q;
+          // (the FP32 numerators add dnum / q; the FP64 ones the err term)
+          const double eb = err * (sc + 1e-3) + (fp32 ? dnum / q * 1.01 : 0.0);
+          if (A.mode == DSE_MODE_AGGREGATED) {
+            agg += sc * sc;
+          } else {
+            const float sf = (float)(sc < 1.0 ? sc : 1.0);
+            const float ef = (float)eb + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
+            note_ivl(A, gid, A.t0 + t0 + t, sf, ef);
+            push_one(A.B, A.t0 + t0 + t, gid, sf, ef);
+          }
+        }
+      }
+    }
+    if (A.mode == DSE_MODE_AGGREGATED && threadIdx.x == 0) {
+      // sqrt(mean sc^2) moves by at most the largest target's bound
+      const double sc = sqrt(agg / (double)A.T);
+      const float sf = (float)sc;
+      const double eb = err * (sc + 1e-3) + (fp32 ? dnum / q * 1.01 : 0.0);
+      const float ef = (float)eb + fabsf((float)(sc - (double)sf)) * 1.0001f + 1e-30f;
       note_ivl(A, gid, A.t0, sf, ef);
       push_one(A.B, A.t0, gid, sf, ef);
     }
@@ -1533,10 +1655,23 @@ void launch_pairlist_batched(int prec64, const ScreenArgs *args, const int2 *pai
 
 void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st, const ScreenArgs *batch) {
   note_launches(1);
-  if (batch || A.T == 1)
+  if (batch || A.T == 1) {
     k_escalate1<<<sms * 8, kEsc, 0, st>>>(A, batch);
-  else
+  } else if (A.N >= 8192 && A.N <= kEscStashMax) {
+    // (below 8192 samples the 128-thread blocks of k_escalate keep more
+    // candidates in flight and win)
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr[dev & 63]) {
+      cudaFuncSetAttribute(k_escalate_stash, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kEscStashMax * sizeof(float)));
+      attr[dev & 63] = true;
+    }
+    k_escalate_stash<<<sms * 2, kEscS, (size_t)A.N * sizeof(float), st>>>(A);
+  } else {
     k_escalate<<<sms * 8, kEsc, 0, st>>>(A, batch);
+  }
 }
 
 void launch_targets(const double *Y, int64_t ldY, int T, int64_t N, int32_t ldy, double *y64, float *y32,
