@@ -358,7 +358,8 @@ static dse_status run_screen(dse_result *R, const ScreenPlan &plan, void *scr_ti
       DSE_TRY(launch_pair_gram(A, sp->gram_buf, plan.gram_scr, plan.gram_tiles_dev, (int)plan.gram_tiles.size(), sms,
                                st));
     } else if (plan.use_gmt) {
-      DSE_TRY(launch_pair_gmt(A, sp->gmt_buf, plan.gmt_scr, plan.gmt_tiles_dev, (int)plan.gmt_tiles.size(), sms, st));
+      DSE_TRY(launch_pair_gmt(A, sp->gmt_buf, plan.gmt_scr, plan.gmt_tiles_dev, (int)plan.gmt_tiles.size(), sms,
+                              st));
     } else if (!plan.mul_tiles.empty()) {
       A.rowid = sp->rowid_ident;
       A.tile_counter = tile_ctr;

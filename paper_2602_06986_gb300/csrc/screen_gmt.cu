@@ -33,10 +33,10 @@
 //               hi/lo), 3-stage ring;
 //   warp 1      TMEM allocation (512 columns: two sets of 256) and the MMA
 //               issuer: 2 k-steps x 3 products x 2 MMAs per chunk;
-//   warps 2-9   epilogue: warp w reads TMEM lane quadrant w % 4 (its 32
-//               a-features) and half (w - 2) / 4 of the b-features (3
+//   warps 2-13  epilogue: warp w reads TMEM lane quadrant w % 4 (its 32
+//               a-features) and third (w - 2) / 4 of the b-features (2
 //               each); after the tile's last block it scores its a-feature
-//               against its 3 b-features, every slot and target, with the
+//               against its 2 b-features, every slot and target, with the
 //               a-priori tests, intervals, realised test, escalation and
 //               threshold pushes of the single-target Gram epilogue.
 // The a-images and the per-feature sums are built once per space, the
@@ -77,12 +77,13 @@ constexpr uint32_t STAGE = A_IMG + B_IMG;     // 60 KB
 constexpr uint32_t G_OFF = (NH / 8) * tc::SBO;  // byte offset of the G rows in a B part
 constexpr int NS = 3;
 constexpr int DB = 16;             // chunks per accumulation block
-constexpr int EPI = 8;             // epilogue warps: two per TMEM lane quadrant
+constexpr int EPI = 12;            // epilogue warps: three per TMEM lane quadrant
 constexpr int THREADS = (2 + EPI) * 32;
-constexpr int BPW = FB / 2;        // b-features per epilogue warp
-constexpr int RUN = BPW * (HC + 8);  // running sums per epilogue thread (120)
+constexpr int BPW = FB / 3;        // b-features per epilogue warp
+constexpr int RUN = BPW * (HC + 8);  // running sums per epilogue thread (80)
+constexpr int RG0 = BPW * HC, RG1 = RG0 + 4 * BPW;  // offsets of the G0 and G1 sums in them
 constexpr uint32_t kWait = 1u << 22;
-constexpr int kStage = 128;        // pending pushes per epilogue warp
+constexpr int kStage = 64;         // pending pushes per epilogue warp
 
 static_assert(N1 % 16 == 0 && N1 <= 256 && NG % 16 == 0, "MMA shapes (M = 128)");
 static_assert(FB * 4 <= NG, "G rows");
@@ -410,8 +411,20 @@ __device__ __forceinline__ uint32_t gmt_flush(const GmtStage &P, const CandBufs 
         B.score[x] = s;
         B.eps[x] = e;
       }
-      count_bounds(B, t0 + l, s, e);
       lists |= 1u << l;
+    }
+    // the bound histograms, one atomic per distinct (list, bin) of the batch
+    // (entries near a threshold share bins)
+    const bool act = l >= 0;
+    const unsigned am = __ballot_sync(0xffffffffu, act);
+    if (act) {
+      const int bl = score_bin(iv_lo(s, e)), bh = score_bin(iv_hi(s, e)), bc = bl / kFine;
+      const unsigned gl = __match_any_sync(am, l * kNumBins + bl), gc = __match_any_sync(am, l * kCoarse + bc),
+                     gh = __match_any_sync(am, l * kNumBins + bh);
+      const size_t lb = (size_t)(t0 + l);
+      if (lane == __ffs(gl) - 1) atomicAdd(&B.hist[lb * kNumBins + bl], (unsigned)__popc(gl));
+      if (lane == __ffs(gc) - 1) atomicAdd(&B.hist_c[lb * kCoarse + bc], (unsigned)__popc(gc));
+      if (lane == __ffs(gh) - 1) atomicAdd(&B.hist_hi[lb * kNumBins + bh], (unsigned)__popc(gh));
     }
   }
   __syncwarp();
@@ -605,10 +618,10 @@ __device__ __forceinline__ void gmt_drain(uint32_t t, float (&run)[gmt::RUN], bo
   }
   tc::tmem_ld32(t + NH, v);
 #pragma unroll
-  for (int k = 0; k < 4 * BPW; ++k) run[96 + k] = first ? v[4 * BPW * HH + k] : run[96 + k] + v[4 * BPW * HH + k];
+  for (int k = 0; k < 4 * BPW; ++k) run[RG0 + k] = first ? v[4 * BPW * HH + k] : run[RG0 + k] + v[4 * BPW * HH + k];
   tc::tmem_ld32(t + N1, v);
 #pragma unroll
-  for (int k = 0; k < 4 * BPW; ++k) run[108 + k] = first ? v[4 * BPW * HH + k] : run[108 + k] + v[4 * BPW * HH + k];
+  for (int k = 0; k < 4 * BPW; ++k) run[RG1 + k] = first ? v[4 * BPW * HH + k] : run[RG1 + k] + v[4 * BPW * HH + k];
 }
 
 // The candidates of the ordered pair (i, j), j the G-th b-feature of this
@@ -624,7 +637,7 @@ __device__ __forceinline__ uint32_t gmt_pair(const ScreenArgs &A, const GmtArgs 
   const int64_t hi = igt ? i : j, lo = igt ? j : i;
   if (hi < A.G.o) return 0;
   const gram::EpiFeat Fj = gmt_rec(A, GA.gf, j);
-  constexpr int H0 = 32 * G, G0 = 96 + 4 * G, G1 = 108 + 4 * G;
+  constexpr int H0 = gmt::HC * G, G0 = gmt::RG0 + 4 * G, G1 = gmt::RG1 + 4 * G;
   uint32_t pushed = gmt_product<1, H0 + gmt::NTP>(A, GA, ls, igt ? DSE_OP_DIV : DSE_OP_RDIV, hi, lo, i, j, Fi, Fj,
                                                    run, run[G0 + 2], run[G0 + 3], run[G1 + 2], run[G1 + 3], ysum,
                                                    theta, py, P);
@@ -720,7 +733,7 @@ __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs 
     };
     raise(own ? gmt_pair<0>(A, GA, ls, i, j0, Fi, run, sh.ysum, theta, py, P) : 0u);
     raise(own ? gmt_pair<1>(A, GA, ls, i, j0 + 1, Fi, run, sh.ysum, theta, py, P) : 0u);
-    raise(own ? gmt_pair<2>(A, GA, ls, i, j0 + 2, Fi, run, sh.ysum, theta, py, P) : 0u);
+    static_assert(BPW == 2, "b-features per epilogue warp");
   }
   flush_stats(A, ls);
 }
@@ -858,8 +871,10 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
     const int q = warp & 3;   // TMEM lane quadrant = a-features 32 q .. 32 q + 31
     if ((ew >> 2) == 0)
       gmt_epilogue<0>(A, GA, sh, tmem, q, ew, wait_warp, aborted_warp);
-    else
+    else if ((ew >> 2) == 1)
       gmt_epilogue<1>(A, GA, sh, tmem, q, ew, wait_warp, aborted_warp);
+    else
+      gmt_epilogue<2>(A, GA, sh, tmem, q, ew, wait_warp, aborted_warp);
   }
   fence_before();
   __syncthreads();
@@ -986,6 +1001,10 @@ dse_status launch_pair_gmt(const ScreenArgs &A, const void *space_buf, void *scr
              (int)gmt_na(n), (int)gmt_nb(n)};
   ScreenArgs B = A;
   B.group = 1;
+  // (a spread sample of tiles launched first does not help here: a streaming
+  // top-k over candidates in arbitrary order buffers about k (1 + ln(n / k))
+  // entries per list whatever the start, and the sample's thresholds rise
+  // no faster)
   const int grid = sms < n_tiles ? sms : n_tiles;
   k_pair_gmt<<<grid, gmt::THREADS, gmt::smem_total(), st>>>(B, GA);
   return DSE_OK;
