@@ -288,12 +288,67 @@ def bench_batched(args):
                      "reruns": max(s["reruns"] for s in st), "kernel_launches": st[0]["kernel_launches"]}
         bt.free()
     n_total = sum(sp.n_total for sp in spaces)
+    # roofline over the whole batched screen (every kernel group; the batch
+    # has no per-group events): 4 FP32 lane operations per valid
+    # candidate-sample against the measured FP32 FMA rate
+    bt = dse.Batch(spaces, targets, w["k"])
+    bt.fetch(0)
+    st = [bt.stats(i) for i in range(len(spaces))]
+    bt.free()
+    lane_ops = sum(s["evaluated"] * len(t) for s, t in zip(st, targets)) * OPS_PER_EVAL
+    pk, pk_src = alu_peak(dse)
+    ach = lane_ops / (res["graph"]["ms_per_step"] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "the whole batched screen (k_feature_batched, k_pair<float,..,BATCH>, "
+                                          "k_pairlist_batched, selection)",
+                "achieved": ach, "peak": pk, "unit": "T fp32-lane-ops/s", "frac": ach / pk, "traffic": None,
+                "peak_source": pk_src, "ops_per_candidate_sample": OPS_PER_EVAL,
+                "note": "time of the whole step: a lower bound of the dominant kernel's fraction"}
+    # the plain FP64 GPU path on the same problems (one eager batch)
+    ms64 = []
+    for _ in range(2):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b64 = dse.Batch(spaces, targets, w["k"], precision=dse.PREC_FP64)
+        b64.fetch(0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64.append(e0.elapsed_time(e1))
+        c64 = sum(b64.stats(i)["evaluated"] for i in range(len(spaces)))
+        b64.free()
+    fp64 = {"value": c64 / (min(ms64) * 1e-3), "unit": "candidates/s", "ms_per_step": min(ms64),
+            "speedup_of_fp32_path": res["graph"]["value"] / (c64 / (min(ms64) * 1e-3)),
+            "note": "plan, screen and fetch of every problem in FP64 (best of 2)"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        # the oracle's full screens of the first problems (about 15 s of CPU
+        # work), rate per valid candidate
+        c_sum, t_sum, n_done = 0, 0.0, 0
+        for p, t in zip(w["problems"], targets):
+            b = w["bases"][p["base"]]
+            S = oracle.Space(np.ascontiguousarray(b["X"][:, p["samples"]]), b["units"], w["op_mask"], w["max_rung"],
+                             **kw)
+            t0 = time.perf_counter()
+            _, _, cnt = S.screen(t[None, :], w["k"])
+            t_sum += time.perf_counter() - t0
+            c_sum += cnt["valid"]
+            n_done += 1
+            if t_sum > 15.0:
+                break
+        cpu = {"value": c_sum / t_sum, "unit": "candidates/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"full screens of the first {n_done} of {len(spaces)} problems ({c_sum} valid candidates, "
+                         f"{t_sum:.1f} s)"}
     line = {"metric": "batched SIS-screened candidate features/sec", "value": res["graph"]["value"],
             "unit": "candidates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["graph"]["ms_per_step"], "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": w["name"], "problems": len(spaces), "k": w["k"],
                                             "candidate_slots": n_total, "l2": "flushed between steps"},
-            "eager": res["eager"], "graph": res["graph"], "space_build_s_total": build_s, "tuning": tuning}
+            "eager": res["eager"], "graph": res["graph"], "roofline": roofline, "fp64_plain": fp64,
+            "cpu_baseline": cpu, "space_build_s_total": build_s, "tuning": tuning}
     print(json.dumps(line))
 
 
