@@ -389,22 +389,33 @@ __global__ void __launch_bounds__(256) k_feature(const ScreenArgs A, uint64_t id
 // Stored and unary candidates against 16 targets in FP32.  One warp per
 // candidate would read all 16 target rows from L2 for every candidate; here
 // a warp scores CW candidates at once and the block's 8 warps move through
-// the samples together: each 256-sample chunk of the targets is staged once
-// per block in shared memory, sample-major ([s][16], read with 16-byte
-// loads), double-buffered (the next chunk is loaded into registers while the
-// current one is used).  Each lane takes samples lane, lane + 32, ... in
-// order with the same blocking as k_feature, so the sums, bounds and
-// decisions are those of k_feature<float, 16>.
+// the samples together: each 256-sample chunk of the targets (sample-major,
+// [s][16], read with 16-byte loads) and of the block's 32 operand rows is
+// staged in shared memory by asynchronous copies (cp.async, zero-filled past
+// N), double-buffered, so the scoring loop reads shared memory only.  Each
+// lane takes samples lane, lane + 32, ... in order with the same blocking as
+// k_feature, so the sums, bounds and decisions are those of
+// k_feature<float, 16>.
 constexpr int kF16Chunk = 256, kF16CW = 4;
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
 
 template <int CW>
 __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64_t id0, uint64_t id1, uint64_t p0,
                                                       uint64_t p1, float gamma_lane) {
-  constexpr int NT = 16, KS = kF16Chunk, WARPS = 8;
-  __shared__ __align__(16) float ys[2][KS][NT];
+  constexpr int NT = 16, KS = kF16Chunk, WARPS = 8, NC = WARPS * CW;
+  extern __shared__ __align__(16) float f16sm[];
+  float(*ys)[KS][NT] = reinterpret_cast<float(*)[KS][NT]>(f16sm);                  // [2][KS][NT]
+  float(*xs)[NC][KS] = reinterpret_cast<float(*)[NC][KS]>(f16sm + 2 * KS * NT);     // [2][NC][KS]
+  __shared__ const float *rows[NC];
+  __shared__ int ract[NC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t nid = id1 - id0, ncand = nid + (p1 - p0);
-  const uint64_t per_tile = (uint64_t)WARPS * CW;
+  const uint64_t per_tile = (uint64_t)NC;
   const uint64_t n_tiles = (ncand + per_tile - 1) / per_tile;
   const float u = 5.9604644775390625e-8f;
   const int64_t Ns = A.N;
@@ -417,21 +428,25 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
   LaneStats ls;
   ls.zero();
   const int nchunk = (int)((Ns + KS - 1) / KS);
-  // staging: thread i takes sample i of a chunk, all 16 targets
-  auto load_chunk = [&](int ch, float (&r)[NT]) {
+  // thread i stages sample i of a chunk: the 16 targets and the 32 rows
+  auto stage = [&](int ch, int buf) {
     const int64_t s = (int64_t)ch * KS + threadIdx.x;
+    const bool in = s < Ns;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) r[t] = (s < Ns && t < T) ? A.y32[(int64_t)(t0 + t) * ldy + s] : 0.f;
-  };
-  auto store_chunk = [&](int buf, const float (&r)[NT]) {
-    float4 *d = reinterpret_cast<float4 *>(&ys[buf][threadIdx.x][0]);
-#pragma unroll
-    for (int q = 0; q < NT / 4; ++q) d[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    for (int t = 0; t < NT; ++t) {
+      const bool v = in && t < T;
+      cp_async4(&ys[buf][threadIdx.x][t], A.y32 + (v ? (int64_t)(t0 + t) * ldy + s : 0), v);
+    }
+#pragma unroll 8
+    for (int k = 0; k < NC; ++k) {
+      const bool v = in && ract[k];
+      cp_async4(&xs[buf][k][threadIdx.x], rows[k] + (v ? s : 0), v);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
   for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     uint64_t gid[CW];
     int op[CW];
-    const float *x[CW];
     float c[CW];
     bool act[CW];
     EvalErr<float> ee[CW];
@@ -441,27 +456,32 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
       act[k] = false;
       gid[k] = 0;
       op[k] = DSE_OP_PRIMARY;
-      x[k] = A.F.v32;
       c[k] = 0.f;
       ee[k] = EvalErr<float>{0.f, 0.f};
-      if (w >= ncand) continue;
-      int64_t f;
-      const int reason = feature_setup(A, w, id0, nid, p0, &gid[k], &op[k], &f);
-      if (reason != DSE_VALID) {
-        if (lane == 0) {
-          ls.r[reason]++;
-          note_why(A, gid[k], reason);
+      const float *xr = A.F.v32;
+      if (w < ncand) {
+        int64_t f;
+        const int reason = feature_setup(A, w, id0, nid, p0, &gid[k], &op[k], &f);
+        if (reason != DSE_VALID) {
+          if (lane == 0) {
+            ls.r[reason]++;
+            note_why(A, gid[k], reason);
+          }
+        } else if (!(A.F.flags[f] & F_FP32_SAFE)) {
+          if (lane == 0) {
+            escalate(A, gid[k]);
+            ls.escalated++;
+          }
+        } else {
+          act[k] = true;
+          xr = A.F.v32 + f * A.F.ld;
+          c[k] = unary_eval<float>(op[k], xr[0], 0.f);
+          ee[k] = unary_err<float>(A.F, op[k], f, c[k], sqrtN);
         }
-      } else if (!(A.F.flags[f] & F_FP32_SAFE)) {
-        if (lane == 0) {
-          escalate(A, gid[k]);
-          ls.escalated++;
-        }
-      } else {
-        act[k] = true;
-        x[k] = A.F.v32 + f * A.F.ld;
-        c[k] = unary_eval<float>(op[k], x[k][0], 0.f);
-        ee[k] = unary_err<float>(A.F, op[k], f, c[k], sqrtN);
+      }
+      if (lane == 0) {
+        rows[warp * CW + k] = xr;
+        ract[warp * CW + k] = act[k] ? 1 : 0;
       }
     }
     float S1[CW], S2[CW], o1[CW], o2[CW], Sy[CW][NT], oy[CW][NT];
@@ -472,24 +492,24 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
       for (int t = 0; t < NT; ++t) Sy[k][t] = oy[k][t] = 0.f;
     }
     int blk = 0;
-    {
-      float r[NT];
-      load_chunk(0, r);
-      __syncthreads();  // (the previous tile's last chunk is no longer read)
-      store_chunk(0, r);
-      __syncthreads();
-    }
+    __syncthreads();  // (rows of this tile; the previous tile's last chunk is no longer read)
+    stage(0, 0);
     for (int ch = 0; ch < nchunk; ++ch) {
-      float r[NT];
-      if (ch + 1 < nchunk) load_chunk(ch + 1, r);
       const int buf = ch & 1;
+      if (ch + 1 < nchunk) {
+        stage(ch + 1, buf ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      __syncthreads();
 #pragma unroll 1
       for (int j = 0; j < KS / 32; ++j) {
         const int64_t s = (int64_t)ch * KS + lane + 32 * j;
         if (s >= Ns) break;
         float xv[CW];
 #pragma unroll
-        for (int k = 0; k < CW; ++k) xv[k] = act[k] ? x[k][s] : 0.f;
+        for (int k = 0; k < CW; ++k) xv[k] = xs[buf][warp * CW + k][lane + 32 * j];
         float yv[NT];
         const float4 *yp = reinterpret_cast<const float4 *>(&ys[buf][lane + 32 * j][0]);
 #pragma unroll
@@ -523,8 +543,7 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
           }
         }
       }
-      if (ch + 1 < nchunk) store_chunk(buf ^ 1, r);
-      __syncthreads();
+      __syncthreads();  // (the buffer is staged again two chunks later)
     }
 #pragma unroll
     for (int k = 0; k < CW; ++k) {
@@ -564,6 +583,8 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
   }
   flush_stats(A, ls);
 }
+
+constexpr size_t kF16Smem = (size_t)2 * kF16Chunk * 16 * sizeof(float) + (size_t)2 * 8 * kF16CW * kF16Chunk * sizeof(float);
 
 // Batched screens: warps take jobs (runs of one problem's stored/unary
 // candidates, the whole group of every problem) from a shared counter.
@@ -1541,7 +1562,14 @@ void launch_feature_t(const ScreenArgs &A, uint64_t id0, uint64_t id1, uint64_t 
     // 32 candidates per block, one block per SM at a time
     uint64_t tiles = (ncand + 8 * kF16CW - 1) / (8 * kF16CW);
     if (tiles > (uint64_t)sms) tiles = (uint64_t)sms;
-    k_feature16<kF16CW><<<(unsigned)tiles, 256, 0, st>>>(B, id0, id1, p0, p1, gamma);
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr[dev & 63]) {
+      cudaFuncSetAttribute(k_feature16<kF16CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF16Smem);
+      attr[dev & 63] = true;
+    }
+    k_feature16<kF16CW><<<(unsigned)tiles, 256, kF16Smem, st>>>(B, id0, id1, p0, p1, gamma);
     return;
   }
   k_feature<R, NT><<<(unsigned)blocks, 256, 0, st>>>(B, id0, id1, p0, p1, gamma);

@@ -451,14 +451,16 @@ __device__ __forceinline__ uint64_t retained_key(const SelectArgs &S, size_t r) 
 
 // 6) order of the retained set (score descending, id ascending) by counting:
 // the rank of an entry is the number of entries ordered before it (ids are
-// unique within a list, so the ranks are a permutation).  Work items are
-// (8 entries, a tile of kRankTile keys); a block stages the tile's keys in
-// shared memory and each warp counts for one entry, lanes over the tile;
-// partial counts meet in r_rank by atomic adds.  Spread over all blocks, so
-// a list of a thousand entries costs a few microseconds instead of a
-// single-block sort.
-constexpr int kRankTile = 2048, kRankGroup = 8;
+// unique within a list, so the ranks are a permutation).  A block stages a
+// tile's keys in shared memory and its warps count for their entries, lanes
+// over the tile; partial counts meet in r_rank by atomic adds.  Spread over
+// all blocks, so a list of a thousand entries costs a few microseconds
+// instead of a single-block sort.
+constexpr int kRankTile = 2048, kRankPer = 8, kRankGroup = 8 * kRankPer;
 
+// Work items are (64 entries, a tile of kRankTile keys): each warp holds 8
+// entries' keys in registers and its lanes run over the tile, so that every
+// key read from shared memory serves 8 comparisons.
 __global__ void __launch_bounds__(256) k_rank(const SelectArgs S) {
   __shared__ uint64_t tk[kRankTile], ti[kRankTile];
   const int l = blockIdx.y;
@@ -480,14 +482,25 @@ __global__ void __launch_bounds__(256) k_rank(const SelectArgs S) {
       __syncthreads();
       loaded = t;
     }
-    for (int e = 0; e < kRankGroup / 8; ++e) {
-      const int64_t i = g * kRankGroup + warp * (kRankGroup / 8) + e;
-      if (i >= rn) break;
-      const uint64_t ki = retained_key(S, base + i), ii = S.r_id[base + i];
-      unsigned c = 0;
-      for (int j = lane; j < nt; j += 32) c += before(tk[j], ti[j], ki, ii) ? 1u : 0u;
-      c = __reduce_add_sync(0xffffffffu, c);
-      if (lane == 0 && c) atomicAdd(&S.r_rank[base + i], c);
+    const int64_t i0 = g * kRankGroup + (int64_t)warp * kRankPer;
+    uint64_t ki[kRankPer], ii[kRankPer];
+    unsigned c[kRankPer];
+#pragma unroll
+    for (int e = 0; e < kRankPer; ++e) {
+      const int64_t i = i0 + e;
+      ki[e] = i < rn ? retained_key(S, base + i) : 0ull;
+      ii[e] = i < rn ? S.r_id[base + i] : 0ull;
+      c[e] = 0;
+    }
+    for (int j = lane; j < nt; j += 32) {
+      const uint64_t kj = tk[j], ij = ti[j];
+#pragma unroll
+      for (int e = 0; e < kRankPer; ++e) c[e] += before(kj, ij, ki[e], ii[e]) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < kRankPer; ++e) {
+      const unsigned v = __reduce_add_sync(0xffffffffu, c[e]);
+      if (lane == 0 && v && i0 + e < rn) atomicAdd(&S.r_rank[base + i0 + e], v);
     }
   }
 }
