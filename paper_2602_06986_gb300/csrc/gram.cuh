@@ -53,6 +53,16 @@ struct GramTgt {
 // family's rows are unusable).
 __device__ __forceinline__ void gram_vals(const FeatTable &F, int64_t f, int64_t s0, int fam, float c, bool ok,
                                           float (&p)[8]) {
+  if (ok && s0 + 8 <= F.N) {
+    // a whole group: two 16-byte loads (rows are 16-byte aligned: ld is a
+    // multiple of 4, s0 of 8)
+    const float4 *src = reinterpret_cast<const float4 *>(F.v32 + f * F.ld + s0);
+    const float4 a = src[0], b = src[1];
+    const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) p[e] = (fam == 0 ? x[e] : __frcp_rn(x[e])) - c;
+    return;
+  }
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int64_t s = s0 + e;

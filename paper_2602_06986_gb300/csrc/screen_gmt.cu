@@ -230,11 +230,20 @@ __global__ void __launch_bounds__(256) k_gmt_brows(FeatTable F, int nchunks, con
 #pragma unroll
         for (int e = 0; e < 8; ++e) p[e] = 0.f;
       }
+      float y[8];
+      if (t < T && s0 + 8 <= N) {
+        // (target rows are 16-byte aligned: ldy is a multiple of 4)
+        const float4 *src = reinterpret_cast<const float4 *>(y32 + (int64_t)t * ldy + s0);
+        const float4 a = src[0], b = src[1];
+        y[0] = a.x, y[1] = a.y, y[2] = a.z, y[3] = a.w, y[4] = b.x, y[5] = b.y, y[6] = b.z, y[7] = b.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) y[e] = (t < T && s0 + e < N) ? y32[(int64_t)t * ldy + s0 + e] : 0.f;
+      }
       float part8 = 0.f;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const float y = (t < T && s0 + e < N) ? y32[(int64_t)t * ldy + s0 + e] : 0.f;
-        py[e] = p[e] * y;
+        py[e] = p[e] * y[e];
         part8 += py[e];
         sq[i] = fmaf(py[e], py[e], sq[i]);
       }
