@@ -224,6 +224,71 @@ __device__ __forceinline__ F2 eval_pair(int op, F2 x, F2 y) {
   }
 }
 
+// The value of op on scaled pair operands (x = a 2^-sa, y = b 2^-sb from
+// their FP32 high and low rows).
+__device__ __forceinline__ F2 pair_value(int op, float xh, float xl, float yh, float yl, float fa, float fb) {
+  const F2 x{__fmul_rn(xh, fa), __fmul_rn(xl, fa)};
+  const F2 y{__fmul_rn(yh, fb), __fmul_rn(yl, fb)};
+  return eval_pair(op, x, y);
+}
+
+// One thread's samples (threadIdx.x, + kColThreads, ...) of the pair pass for
+// operator OP: the shifted sums, the conditioning sum and the largest value.
+// A sum or difference carries the operands' representation error (2^-48 of
+// |a| + |b|), which cancellation amplifies relative to v: its conditioning
+// sum takes (|a| + |b|)^2 instead of v^2.
+template <int NV, int OP>
+__device__ __forceinline__ void pair_pass(const float *ah, const float *al, const float *bh, const float *bl,
+                                          float fa, float fb, F2 nc, int64_t N, const ColVecs &V, Acc &s1, Acc &s2,
+                                          Acc (&p)[NV], float &sv, float &vmax) {
+  constexpr bool additive = OP == DSE_OP_ADD || OP == DSE_OP_SUB || OP == DSE_OP_ABSDIFF;
+  // two samples per thread per step, their loads issued together (the pass
+  // is bound by load latency otherwise); each thread takes its samples in
+  // increasing order
+  constexpr int U = 2;
+  for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * kColThreads) {
+    float lh[U], ll[U], rh[U], rl[U];
+    float2 wv[U][NV];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t s = s0 + (int64_t)k * kColThreads;
+      const bool in = s < N;
+      lh[k] = in ? ah[s] : 0.0f;
+      ll[k] = in ? al[s] : 0.0f;
+      rh[k] = in ? bh[s] : 0.0f;
+      rl[k] = in ? bl[s] : 0.0f;
+#pragma unroll
+      for (int m = 0; m < NV; ++m) wv[k][m] = in ? V.vdf[m][s] : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (s0 + (int64_t)k * kColThreads >= N) break;
+      const F2 x{__fmul_rn(lh[k], fa), __fmul_rn(ll[k], fa)};
+      const F2 y{__fmul_rn(rh[k], fb), __fmul_rn(rl[k], fb)};
+      const F2 v = eval_pair(OP, x, y);
+      const float mag = additive ? __fadd_rn(fabsf(x.hi), fabsf(y.hi)) : fabsf(v.hi);
+      const F2 d = add(v, nc);
+      s1.add(d.hi, d.lo);
+      {
+        const float q = __fmul_rn(d.hi, d.hi);
+        const float qe = __fmaf_rn(__fadd_rn(d.hi, d.hi), d.lo, __fmaf_rn(d.hi, d.hi, -q));
+        s2.add(q, qe);
+      }
+      sv = __fmaf_rn(mag, mag, sv);
+      vmax = fmaxf(vmax, fabsf(v.hi));
+#pragma unroll
+      for (int m = 0; m < NV; ++m) {
+        const float2 w = wv[k][m];
+        const float q = __fmul_rn(d.hi, w.x);
+        float qe = __fmaf_rn(d.hi, w.x, -q);
+        qe = __fmaf_rn(d.hi, w.y, qe);
+        qe = __fmaf_rn(d.lo, w.x, qe);
+        p[m].add(q, qe);
+      }
+    }
+  }
+}
+
 // The pair pass (whole block, results in warp 0); false when it does not
 // apply or its result fails the range / conditioning checks (every thread
 // returns the same).
@@ -260,61 +325,26 @@ __device__ __forceinline__ bool col_sums_pair(const FeatTable &F, int op, int64_
   // a sum or difference carries the operands' representation error
   // (2^-48 of |a| + |b|), which cancellation amplifies relative to v: its
   // conditioning sum takes (|a| + |b|)^2 instead of v^2
-  const bool additive = op == DSE_OP_ADD || op == DSE_OP_SUB || op == DSE_OP_ABSDIFF;
-  auto value = [&](float xh, float xl, float yh, float yl, float *mag) -> F2 {
-    const F2 x{__fmul_rn(xh, fa), __fmul_rn(xl, fa)};
-    const F2 y{__fmul_rn(yh, fb), __fmul_rn(yl, fb)};
-    const F2 v = eval_pair(op, x, y);
-    *mag = additive ? __fadd_rn(fabsf(x.hi), fabsf(y.hi)) : fabsf(v.hi);
-    return v;
-  };
-  float mag0;
-  const F2 c = value(ah[0], al[0], bh[0], bl[0], &mag0);
-  const F2 nc = neg(c);
+  // (the pass over the samples is instantiated per operator, so that the
+  // operator's arithmetic is not a branch inside the loop)
+  const F2 c = pair_value(op, ah[0], al[0], bh[0], bl[0], fa, fb);
   Acc s1, s2, p[NV];
   float sv = 0.0f, vmax = 0.0f;
-  // two samples per thread per step, their loads issued together (the pass
-  // is bound by load latency otherwise); each thread takes its samples in
-  // increasing order
-  constexpr int U = 2;
-  for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * kColThreads) {
-    float lh[U], ll[U], rh[U], rl[U];
-    float2 wv[U][NV];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const int64_t s = s0 + (int64_t)k * kColThreads;
-      const bool in = s < N;
-      lh[k] = in ? ah[s] : 0.0f;
-      ll[k] = in ? al[s] : 0.0f;
-      rh[k] = in ? bh[s] : 0.0f;
-      rl[k] = in ? bl[s] : 0.0f;
-#pragma unroll
-      for (int m = 0; m < NV; ++m) wv[k][m] = in ? V.vdf[m][s] : make_float2(0.0f, 0.0f);
-    }
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      if (s0 + (int64_t)k * kColThreads >= N) break;
-      float mag;
-      const F2 v = value(lh[k], ll[k], rh[k], rl[k], &mag);
-      const F2 d = add(v, nc);
-      s1.add(d.hi, d.lo);
-      {
-        const float q = __fmul_rn(d.hi, d.hi);
-        const float qe = __fmaf_rn(__fadd_rn(d.hi, d.hi), d.lo, __fmaf_rn(d.hi, d.hi, -q));
-        s2.add(q, qe);
-      }
-      sv = __fmaf_rn(mag, mag, sv);
-      vmax = fmaxf(vmax, fabsf(v.hi));
-#pragma unroll
-      for (int m = 0; m < NV; ++m) {
-        const float2 w = wv[k][m];
-        const float q = __fmul_rn(d.hi, w.x);
-        float qe = __fmaf_rn(d.hi, w.x, -q);
-        qe = __fmaf_rn(d.hi, w.y, qe);
-        qe = __fmaf_rn(d.lo, w.x, qe);
-        p[m].add(q, qe);
-      }
-    }
+  switch (op) {
+#define DSE_PAIR_CASE(OPC) \
+  case OPC: pair_pass<NV, OPC>(ah, al, bh, bl, fa, fb, neg(c), N, V, s1, s2, p, sv, vmax); break;
+    DSE_PAIR_CASE(DSE_OP_SQUARE)
+    DSE_PAIR_CASE(DSE_OP_CUBE)
+    DSE_PAIR_CASE(DSE_OP_INV)
+    DSE_PAIR_CASE(DSE_OP_SQRT)
+    DSE_PAIR_CASE(DSE_OP_ADD)
+    DSE_PAIR_CASE(DSE_OP_SUB)
+    DSE_PAIR_CASE(DSE_OP_MUL)
+    DSE_PAIR_CASE(DSE_OP_DIV)
+    DSE_PAIR_CASE(DSE_OP_RDIV)
+    DSE_PAIR_CASE(DSE_OP_ABSDIFF)
+#undef DSE_PAIR_CASE
+    default: pair_pass<NV, DSE_OP_PRIMARY>(ah, al, bh, bl, fa, fb, neg(c), N, V, s1, s2, p, sv, vmax); break;
   }
   s1.warp_reduce();
   s2.warp_reduce();
