@@ -1253,6 +1253,81 @@ __device__ __forceinline__ void block_sum64(double (&v)[NV], double *sm) {
   __syncthreads();
 }
 
+// The FP64 passes of the escalation kernels, instantiated per operator (the
+// operator is then not a branch inside the sample loop).
+template <int OP>
+__device__ __forceinline__ bool esc_binary() {
+  return OP == DSE_OP_ADD || OP == DSE_OP_SUB || OP == DSE_OP_MUL || OP == DSE_OP_DIV || OP == DSE_OP_RDIV ||
+         OP == DSE_OP_ABSDIFF;
+}
+
+// k_escalate_stash: sum (v-c), sum (v-c)^2, sum v^2, non-finite count, and
+// fl32(v - c) of every sample into w (THREADS threads over the samples).
+template <int OP, int THREADS>
+__device__ __forceinline__ void esc_pass_stash(const double *xa, const double *xb, int64_t N, double c,
+                                               double (&st)[4], float *w) {
+  for (int64_t s = threadIdx.x; s < N; s += THREADS) {
+    const double v = eval_op64(OP, xa[s], esc_binary<OP>() ? xb[s] : 0.0);
+    if (!isfinite(v)) st[3] += 1.0;
+    const double d = v - c;
+    st[0] += d;
+    st[1] = fma(d, d, st[1]);
+    st[2] = fma(v, v, st[2]);
+    w[s] = (float)d;
+  }
+}
+
+// k_escalate1: sum (v-c), sum (v-c)^2, sum v^2, non-finite count, sum (v-c)
+// y, sum y; four samples per thread per step, their loads issued together,
+// each thread taking its samples in increasing order.
+template <int OP, int THREADS>
+__device__ __forceinline__ void esc_pass1(const double *xa, const double *xb, const double *y, int64_t N, double c,
+                                          double (&st)[6]) {
+  constexpr int U = 4;
+  for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * THREADS) {
+    double va[U], vb[U], yv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t s = s0 + (int64_t)k * THREADS;
+      const bool in = s < N;
+      va[k] = in ? xa[s] : 0.0;
+      vb[k] = in && esc_binary<OP>() ? xb[s] : 0.0;
+      yv[k] = in ? y[s] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (s0 + (int64_t)k * THREADS >= N) break;
+      const double v = eval_op64(OP, va[k], vb[k]);
+      if (!isfinite(v)) st[3] += 1.0;
+      const double d = v - c;
+      st[0] += d;
+      st[1] = fma(d, d, st[1]);
+      st[2] = fma(v, v, st[2]);
+      st[4] = fma(d, yv[k], st[4]);
+      st[5] += yv[k];
+    }
+  }
+}
+
+// switch over the operator codes, CALL(OPC) for each (the primary /
+// identity code as the default)
+#define DSE_OP_SWITCH(op, CALL)  \
+  switch (op) {                  \
+    case DSE_OP_SQUARE: CALL(DSE_OP_SQUARE); break; \
+    case DSE_OP_CUBE: CALL(DSE_OP_CUBE); break;     \
+    case DSE_OP_INV: CALL(DSE_OP_INV); break;       \
+    case DSE_OP_SQRT: CALL(DSE_OP_SQRT); break;     \
+    case DSE_OP_EXP: CALL(DSE_OP_EXP); break;       \
+    case DSE_OP_LOG: CALL(DSE_OP_LOG); break;       \
+    case DSE_OP_ADD: CALL(DSE_OP_ADD); break;       \
+    case DSE_OP_SUB: CALL(DSE_OP_SUB); break;       \
+    case DSE_OP_MUL: CALL(DSE_OP_MUL); break;       \
+    case DSE_OP_DIV: CALL(DSE_OP_DIV); break;       \
+    case DSE_OP_RDIV: CALL(DSE_OP_RDIV); break;     \
+    case DSE_OP_ABSDIFF: CALL(DSE_OP_ABSDIFF); break; \
+    default: CALL(DSE_OP_PRIMARY); break;           \
+  }
+
 // batch != nullptr: entries of a batched screen, each with its problem.
 __global__ void __launch_bounds__(kEsc) k_escalate(const ScreenArgs A0, const ScreenArgs *batch) {
   __shared__ double sm[(kEsc / 32) * 16];
@@ -1353,15 +1428,10 @@ __global__ void __launch_bounds__(kEscS, 2) k_escalate_stash(const ScreenArgs A)
     if (!DSE_OPERANDS_OK(A.F, a, b, A.err)) continue;
     const double c = cand_value64(A.F, A.G, A.n_stored, gid, 0, op, a, b);
     double st[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t s = threadIdx.x; s < N; s += kEscS) {
-      const double v = cand_value64(A.F, A.G, A.n_stored, gid, s, op, a, b);
-      if (!isfinite(v)) st[3] += 1.0;
-      const double d = v - c;
-      st[0] += d;
-      st[1] = fma(d, d, st[1]);
-      st[2] = fma(v, v, st[2]);
-      wsm[s] = (float)d;
-    }
+    const double *xa = A.F.v64 + a * A.F.ld, *xb = A.F.v64 + (b >= 0 ? b : a) * A.F.ld;
+#define DSE_ESC_STASH(OPC) esc_pass_stash<OPC, kEscS>(xa, xb, N, c, st, wsm)
+    DSE_OP_SWITCH(op, DSE_ESC_STASH)
+#undef DSE_ESC_STASH
     block_sum64<4, true, kEscS>(st, sm);
     const double sxx = st[1] - st[0] * (st[0] / (double)N);
     int good = st[3] == 0.0 && isfinite(sxx);
@@ -1469,30 +1539,9 @@ __global__ void __launch_bounds__(kEsc) k_escalate1(const ScreenArgs A0, const S
     // thread taking its samples in increasing order
     double st[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const double *xa = A.F.v64 + a * A.F.ld, *xb = A.F.v64 + (b >= 0 ? b : a) * A.F.ld;
-    constexpr int U = 4;
-    for (int64_t s0 = threadIdx.x; s0 < N; s0 += U * kEsc) {
-      double va[U], vb[U], yv[U];
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int64_t s = s0 + (int64_t)k * kEsc;
-        const bool in = s < N;
-        va[k] = in ? xa[s] : 0.0;
-        vb[k] = in && b >= 0 ? xb[s] : 0.0;
-        yv[k] = in ? y[s] : 0.0;
-      }
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        if (s0 + (int64_t)k * kEsc >= N) break;
-        const double v = eval_op64(op, va[k], vb[k]);
-        if (!isfinite(v)) st[3] += 1.0;
-        const double d = v - c;
-        st[0] += d;
-        st[1] = fma(d, d, st[1]);
-        st[2] = fma(v, v, st[2]);
-        st[4] = fma(d, yv[k], st[4]);
-        st[5] += yv[k];
-      }
-    }
+#define DSE_ESC1(OPC) esc_pass1<OPC, kEsc>(xa, xb, y, N, c, st)
+    DSE_OP_SWITCH(op, DSE_ESC1)
+#undef DSE_ESC1
     block_sum64<6, false>(st, sm);
     if (threadIdx.x == 0) {  // (FP64 work is slow on this part: one thread decides)
       const double sxx = st[1] - st[0] * (st[0] / (double)N);
