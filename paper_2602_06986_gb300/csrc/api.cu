@@ -275,7 +275,7 @@ uint64_t count_slots_mod(uint64_t x, int nb, const std::vector<int> &posset) {
 }
 
 // Zero a screen's buffer counts, bound histograms, escalation count,
-// statistics and re-score job count.
+// statistics and re-score job counts (n_jobs[0..2)).
 __global__ void k_screen_reset(unsigned *count, unsigned *hist, unsigned *hist_hi, unsigned *hist_c, int nl,
                                unsigned *esc_count, unsigned long long *stats, unsigned *n_jobs) {
   const int64_t nh = (int64_t)nl * kNumBins, nc = (int64_t)nl * kCoarse;
@@ -287,7 +287,8 @@ __global__ void k_screen_reset(unsigned *count, unsigned *hist, unsigned *hist_h
     if (e < ST_COUNT) stats[e] = 0ull;
     if (e == 0) {
       *esc_count = 0u;
-      *n_jobs = 0u;
+      n_jobs[0] = 0u;
+      n_jobs[1] = 0u;
     }
   }
 }
@@ -623,7 +624,9 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   sc.add(&R->overflow, (size_t)n_lists);
   sc.add(&S.job, (size_t)n_lists * cap);
   sc.add(&S.job_list, (size_t)n_lists * cap);
-  sc.add(&S.n_jobs, 1);
+  sc.add(&S.job32, (size_t)n_lists * cap);
+  sc.add(&S.job32_list, (size_t)n_lists * cap);
+  sc.add(&S.n_jobs, 2);
   sc.add(&R->out_id, (size_t)n_lists * d->k);
   sc.add(&R->out_score, (size_t)n_lists * d->k);
   sc.add(&R->out_eps, (size_t)n_lists * d->k);

@@ -56,10 +56,14 @@ struct SelectArgs {
   uint8_t *r_need;          // [lists][cap]
   unsigned int *r_count;    // [lists]
   unsigned int *overflow;   // [lists]
-  // re-score jobs
+  // re-score jobs: the pair / FP64 re-score's (count n_jobs[0]) and, with
+  // rescore32, the FP32 re-score's (job32, job32_list, count n_jobs[1])
   uint32_t *job;            // [lists * cap] packed (list << 24 | pos) is not enough: two arrays
   uint32_t *job_list;
-  unsigned int *n_jobs;
+  unsigned int *n_jobs;     // [2]
+  uint32_t *job32 = nullptr;       // [lists * cap]
+  uint32_t *job32_list = nullptr;  // [lists * cap]
+  int32_t rescore32 = 0;    // set by launch_select where the FP32 re-score applies
   // outputs
   uint64_t *out_id;
   double *out_score, *out_eps;

@@ -51,6 +51,30 @@ def check_list(ids, sc, eb, oids, osc, orc, Y, t):
     ge._check_topk(ids, sc, eb, oids, osc, orc, Y, t, tol=TOL)
 
 
+def assert_same_topk(ids_m, sc_m, eb_m, ids_f, sc_f, eb_f):
+    """Two top-k lists of one screen taken different ways (merged range
+    screens and the full screen) agree up to ties inside the scores' bounds:
+    a candidate's reported score may come from the FP32 or the FP32-pair
+    re-score depending on how it was classified in its own screen, so
+    members whose scores lie within the bounds of the k-th score are
+    interchangeable; every member clear of that band is in both lists, and
+    common members' scores agree within their bounds."""
+    assert len(ids_m) == len(ids_f)
+    if len(ids_f) == 0:
+        return
+    band = 2.0 * (float(np.max(eb_m)) + float(np.max(eb_f))) + 1e-12
+    kth = max(float(sc_m[-1]), float(sc_f[-1]))
+    sm, sf = set(int(i) for i in ids_m), set(int(i) for i in ids_f)
+    assert {int(i) for i, s in zip(ids_m, sc_m) if s > kth + band} <= sf
+    assert {int(i) for i, s in zip(ids_f, sc_f) if s > kth + band} <= sm
+    fm = {int(i): (s, e) for i, s, e in zip(ids_m, sc_m, eb_m)}
+    for i, s, e in zip(ids_f, sc_f, eb_f):
+        if int(i) in fm:
+            s2, e2 = fm[int(i)]
+            assert abs(s - s2) <= e + e2 + 1e-12, (int(i), s, s2)
+    assert len(sm & sf) >= len(ids_f) - sum(1 for s in sc_f if s <= kth + band)
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_tiny_parity(env, seed):
     torch, oracle, dse, W = env
@@ -181,8 +205,9 @@ def test_ranges_merge_to_full(env):
         assert st["reasons"] == oc
     ids = np.concatenate([p[0] for p in parts])
     sc = np.concatenate([p[1] for p in parts])
+    eb = np.concatenate([p[2] for p in parts])
     order = np.lexsort((ids, -sc))[:50]
-    assert np.array_equal(ids[order], full[0])
+    assert_same_topk(ids[order], sc[order], eb[order], *full)
 
 
 def test_gram_multi_target_ranges_and_edges(env):
@@ -213,8 +238,9 @@ def test_gram_multi_target_ranges_and_edges(env):
     for l in range(4):
         ids = np.concatenate([p[0] for p in parts[l]])
         sc = np.concatenate([p[1] for p in parts[l]])
+        eb = np.concatenate([p[2] for p in parts[l]])
         order = np.lexsort((ids, -sc))[:40]
-        assert np.array_equal(ids[order], full.fetch(l)[0]), l
+        assert_same_topk(ids[order], sc[order], eb[order], *full.fetch(l))
     # k = 1 and k above the number of valid candidates
     r = sp.screen(Yd, 1, precision=dse.PREC_BF16X3)
     oi, os_, oc = orc.screen(Y, 1)
@@ -358,7 +384,11 @@ def test_residual_loop_on_device(env, wname, D, prec):
     for d in range(D):
         res = sp.screen(r, k, precision=p)
         hids, hsc, heb = res.fetch(0)
-        np.testing.assert_array_equal(hids, ids[d][:len(hids)])
+        # the loop takes every retained score from the pair sums it needs for
+        # the refit, a single screen from the FP32 re-score where that is
+        # within the tolerance: the same set, in an order that may differ
+        # inside the scores' bounds
+        np.testing.assert_array_equal(np.sort(hids), np.sort(ids[d][:len(hids)]))
         bid, rmse, coefs, resid_h = sp.ls_refit(y, np.array(fixed, np.uint64), hids)
         assert bid == out["chosen"][d]
         assert rmse == out["rmse"][d]
