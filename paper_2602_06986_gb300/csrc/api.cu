@@ -612,6 +612,8 @@ static dse_status screen_impl(dse_space *sp, const dse_screen_desc *d, dse_resul
   const int64_t esc_cap = 1 << 20;
   sc.add(&A.esc_id, (size_t)esc_cap);
   sc.add(&A.esc_count, 1);
+  sc.add(&A.esc2_id, (size_t)esc_cap);
+  sc.add(&A.esc2_count, 1);
   sc.add(&R->stats, ST_COUNT);
   sc.add(&R->err, 1);
   sc.add(&S.r_id, (size_t)n_lists * cap);

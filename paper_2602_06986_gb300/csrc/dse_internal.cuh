@@ -215,6 +215,10 @@ struct ScreenArgs {
   int8_t *why;                 // optional: reason code of each id of [id_begin, id_end) (device)
   float2 *ivl;                 // optional: (s, eps) of each id of the range and list, before re-scores
   int32_t gram_addsub;         // a+b and a-b are scored by the Gram kernel: the additive kernels take |a-b| only
+  // the entries of the escalation list that its FP32 stage left undecided
+  // (single screens; nullptr: no FP32 stage)
+  uint64_t *esc2_id = nullptr;
+  unsigned int *esc2_count = nullptr;
 };
 
 // Planner parameters in effect (dse_set_tuning, defaults filled in).

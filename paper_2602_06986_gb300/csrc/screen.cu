@@ -1517,6 +1517,68 @@ __global__ void __launch_bounds__(kEscS, 2) k_escalate_stash(const ScreenArgs A)
   }
 }
 
+// FP32 stage of the escalation (single screens, at most 16 targets): one
+// warp per escalated binary candidate evaluates it again in FP32 with the
+// tight accumulation of r32_sums (16-sample FP32 blocks into FP32 pairs,
+// gamma = kGamma32 u instead of the screening kernel's wider bound: the Gram
+// contractions escalate candidates whose BF16x3 interval of the centred sum
+// of squares reaches zero, most of which are far from degenerate) and
+// decides the realised test on the screen's interval.  Decided candidates
+// take their reason code, statistics and every target's score and push here,
+// exactly as in the FP32 screen; the others (near-constant columns such as
+// x * (1/x), other operators, operands outside the FP32-safe range) go to
+// the undecided list that the FP64 kernels then take.
+__global__ void __launch_bounds__(256) k_escalate32(const ScreenArgs A) {
+  const int lane = threadIdx.x & 31;
+  const unsigned n = min(*A.esc_count, (unsigned)A.esc_cap);
+  const unsigned warps = (gridDim.x * blockDim.x) >> 5;
+  const float u = 5.9604644775390625e-8f;
+  const float Nf = (float)A.N, invN = (float)A.invN, sqrtN = sqrtf(Nf);
+  const float gamma = kGamma32 * u * 1.05f, fmin = (float)A.fmin_std_rel64;
+  float ysum[16];
+  load_ysum<float, 16>(A, ysum);
+  LaneStats ls;
+  ls.zero();
+  for (unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += warps) {
+    const uint64_t gid = A.esc_id[w];
+    int op;
+    int64_t a, b;
+    decode_gid(A, gid, &op, &a, &b);
+    R32Setup c;
+    const bool ok = gid >= (uint64_t)A.n_stored && r32_setup(A, op, a, b, c);
+    float Sm[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) Sm[k] = 0.f;
+    if (ok) r32_sums<16, 1>(A, op, a, b, A.y32 + (int64_t)A.t0 * A.ldy, A.T, c, Sm);
+    CandInterval<float> ci{};
+    int decided = 0;  // 1 valid, 2 degenerate
+    if (ok) {
+      ci = cand_interval<float>(Sm[0], Sm[1], Nf, invN, sqrtN, c.cshift, c.ee, gamma, u, fmin);
+      decided = ci.realised == 1 ? 1 : ci.realised == 0 ? 2 : 0;
+    }
+    if (lane == 0) {
+      if (decided == 1) {
+        ls.r[DSE_VALID]++;
+        ls.evaluated++;
+        note_why(A, gid, DSE_VALID);
+      } else if (decided == 2) {
+        ls.r[DSE_R_REALISED]++;
+        note_why(A, gid, DSE_R_REALISED);
+      } else {
+        const unsigned pos = atomicAdd(A.esc2_count, 1u);
+        A.esc2_id[pos] = gid;
+      }
+    }
+    float Sy[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) Sy[t] = Sm[2 + t];
+    const unsigned pushed =
+        score_and_push<float, 16>(A, lane == 0 && decided == 1, gid, ci, Sm[0], Sy, invN, gamma, u, ysum);
+    refresh_pushed<16>(A, pushed);
+  }
+  flush_stats(A, ls);
+}
+
 // The same decision and score for screens with one target (every problem of
 // a batched screen too), in one pass over the samples: the centred numerator
 // follows from the shifted sums, sum (v - vbar) y = sum (v - c) y -
@@ -1730,7 +1792,17 @@ void launch_pairlist_batched(int prec64, const ScreenArgs *args, const int2 *pai
   else k_pairlist_batched<float><<<blocks, 256, 0, st>>>(args, pairs, jobs, n_jobs, counter);
 }
 
-void launch_escalate(const ScreenArgs &A, int sms, cudaStream_t st, const ScreenArgs *batch) {
+void launch_escalate(const ScreenArgs &A0, int sms, cudaStream_t st, const ScreenArgs *batch) {
+  ScreenArgs A = A0;
+  if (!batch && A.esc2_id && A.esc2_count && A.T <= 16 && A.F.v32 && A.y32 && A.ysum32 && A.u > 1e-10f) {
+    // (FP32 screens) the FP32 stage first; the FP64 kernels below take what
+    // it left undecided
+    cudaMemsetAsync(A.esc2_count, 0, sizeof(unsigned), st);
+    note_launches(1);
+    k_escalate32<<<sms * 4, 256, 0, st>>>(A0);
+    A.esc_id = A.esc2_id;
+    A.esc_count = A.esc2_count;
+  }
   note_launches(1);
   if (batch || A.T == 1) {
     k_escalate1<<<sms * 8, kEsc, 0, st>>>(A, batch);

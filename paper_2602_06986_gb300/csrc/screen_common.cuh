@@ -322,6 +322,181 @@ __device__ __forceinline__ int binary_apriori_W(const ScreenArgs &A, int opc, in
   return reason;
 }
 
+// ------------------------------------------- FP32 re-evaluation (one warp)
+//
+// The selection's FP32 re-score and the FP32 stage of the escalation
+// evaluate a binary candidate again, one warp per candidate, in the screen's
+// own FP32 evaluation forms (so binary_apriori_W's evaluation-error
+// coefficients apply): float4 groups lane, lane + 32, ... of the operand rows
+// and the targets; every 16 of a lane's samples form one FP32 summation block
+// whose totals are added into FP32 pairs (hi, lo); the lane totals meet in
+// FP64 and are rounded to FP32 once.  The accumulation error is then at most
+// 16 u (the blocks) plus 2 u (the pairs' residual, the final rounding) of the
+// sums of absolute terms: gamma takes kGamma32 = 24 units of u.
+constexpr float kGamma32 = 24.0f;
+
+// (hi, lo) += x, Knuth's two-sum with the error term gathered in lo
+__device__ __forceinline__ void pair_acc(float &hi, float &lo, float x) {
+  const float t = __fadd_rn(hi, x);
+  const float z = __fsub_rn(t, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(x, z)));
+  hi = t;
+}
+
+// The screen's FP32 evaluation forms of the binary operators (shift kk for
+// the products, quotients and |a-b|; centring means mi, mj for a+b, a-b).
+template <int OP>
+__device__ __forceinline__ float r32_value(float a, float b, float kk, float mi, float mj) {
+  if (OP == DSE_OP_MUL) return __fmaf_rn(a, b, -kk);
+  if (OP == DSE_OP_DIV) return __fmaf_rn(a, rcp_approx(b), -kk);
+  if (OP == DSE_OP_RDIV) return __fmaf_rn(b, rcp_approx(a), -kk);
+  if (OP == DSE_OP_ADD) return __fadd_rn(__fsub_rn(a, mi), __fsub_rn(b, mj));
+  if (OP == DSE_OP_SUB) return __fsub_rn(__fsub_rn(a, mi), __fsub_rn(b, mj));
+  return __fsub_rn(fabsf(__fsub_rn(a, b)), kk);  // |a-b|
+}
+
+// the unshifted value (for the shift estimate)
+__device__ __forceinline__ float r32_plain(int op, float a, float b) {
+  switch (op) {
+    case DSE_OP_MUL: return __fmul_rn(a, b);
+    case DSE_OP_DIV: return __fmul_rn(a, rcp_approx(b));
+    case DSE_OP_RDIV: return __fmul_rn(b, rcp_approx(a));
+    default: return fabsf(__fsub_rn(a, b));
+  }
+}
+
+// the samples of a row's last float4 group past N read as zero
+__device__ __forceinline__ void r32_zero_tail(float4 &v, int64_t i, int64_t n4, int rem) {
+  if (rem == 0 || i != n4 - 1) return;
+  if (rem == 1) v.y = 0.f;
+  if (rem <= 2) v.z = 0.f;
+  v.w = 0.f;
+}
+
+// One lane's samples: s[0] = sum w, s[1] = sum w^2, s[2 + t] = sum w y_t for
+// the nt (<= NT) target rows y + t ldy; U float4 groups per step.
+template <int OP, int NT, int U>
+__device__ __forceinline__ void r32_pass(const float *ra, const float *rb, const float *y, int64_t ldy, int nt,
+                                         int64_t N, float kk, float mi, float mj, float (&hi)[2 + NT],
+                                         float (&lo)[2 + NT]) {
+  static_assert(U == 1 || U == 2 || U == 4, "16-sample blocks");
+  constexpr int STEPS = 4 / U;
+  const int lane = threadIdx.x & 31;
+  const int64_t n4 = (N + 3) >> 2;
+  const int rem = (int)(N & 3);
+  const float4 *xa = reinterpret_cast<const float4 *>(ra), *xb = reinterpret_cast<const float4 *>(rb);
+  float acc[2 + NT];
+#pragma unroll
+  for (int k = 0; k < 2 + NT; ++k) acc[k] = 0.f;
+  int nb = 0;
+  for (int64_t i0 = lane; i0 < n4; i0 += 32 * U) {
+    float4 av[U], bv[U], yv[U][NT];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int64_t i = i0 + 32 * q;
+      const bool in = i < n4;
+      av[q] = in ? __ldg(xa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      bv[q] = in ? __ldg(xb + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        yv[q][t] = in && t < nt ? __ldg(reinterpret_cast<const float4 *>(y + (int64_t)t * ldy) + i)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        r32_zero_tail(yv[q][t], i, n4, rem);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int64_t s = (i0 + 32 * q) * 4;
+      const float ae[4] = {av[q].x, av[q].y, av[q].z, av[q].w};
+      const float be[4] = {bv[q].x, bv[q].y, bv[q].z, bv[q].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float w = r32_value<OP>(ae[e], be[e], kk, mi, mj);
+        w = s + e < N ? w : 0.f;  // padding and groups past the row: no term
+        acc[0] = __fadd_rn(acc[0], w);
+        acc[1] = __fmaf_rn(w, w, acc[1]);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const float yy = e == 0 ? yv[q][t].x : e == 1 ? yv[q][t].y : e == 2 ? yv[q][t].z : yv[q][t].w;
+          acc[2 + t] = __fmaf_rn(w, yy, acc[2 + t]);
+        }
+      }
+    }
+    if (++nb == STEPS) {
+      nb = 0;
+#pragma unroll
+      for (int k = 0; k < 2 + NT; ++k) {
+        pair_acc(hi[k], lo[k], acc[k]);
+        acc[k] = 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2 + NT; ++k) pair_acc(hi[k], lo[k], acc[k]);
+}
+
+// An FP32 re-evaluation's constants.
+struct R32Setup {
+  float kk, mi, mj, cshift;
+  EvalErr<float> ee;
+};
+
+// Whole warp.  False when the re-evaluation does not apply: an operator
+// outside the six binary ones, operands outside the FP32-safe range, or an
+// a-priori test that is not valid.  Else the shift kk of a*b, a/b, b/a and
+// |a-b| (the mean of the first, up to 32, values, so that the shifted sum of
+// squares stays close to the centred one), the centring means of a+b and
+// a-b, the shift of the sums and the evaluation-error coefficients.
+__device__ __forceinline__ bool r32_setup(const ScreenArgs &A, int op, int64_t a, int64_t b, R32Setup &o) {
+  const bool binop = op == DSE_OP_MUL || op == DSE_OP_DIV || op == DSE_OP_RDIV || op == DSE_OP_ADD ||
+                     op == DSE_OP_SUB || op == DSE_OP_ABSDIFF;
+  if (!binop || b < 0 || !DSE_OPERANDS_OK(A.F, a, b, A.err)) return false;
+  if (!((A.F.flags[a] & A.F.flags[b]) & F_FP32_SAFE)) return false;
+  const int lane = threadIdx.x & 31;
+  const int64_t N = A.N;
+  const float4 fa_a = A.F.fa[a], fa_b = A.F.fa[b];
+  o.mi = fa_a.x;
+  o.mj = fa_b.x;
+  o.kk = 0.f;
+  if (op != DSE_OP_ADD && op != DSE_OP_SUB) {
+    float v0 = lane < N ? r32_plain(op, A.F.v32[a * A.F.ld + lane], A.F.v32[b * A.F.ld + lane]) : 0.f;
+    for (int k = 16; k > 0; k >>= 1) v0 += __shfl_xor_sync(0xffffffffu, v0, k);
+    o.kk = v0 / (float)(N < 32 ? N : 32);
+    if (!isfinite(o.kk)) o.kk = 0.f;
+  }
+  o.cshift = op == DSE_OP_ADD ? o.mi + o.mj : op == DSE_OP_SUB ? o.mi - o.mj : o.kk;
+  return binary_apriori_W<float>(A, op, a, b, fa_a, fa_b, o.kk, o.mi, o.mj, &o.ee) == DSE_VALID;
+}
+
+// The warp's sums (every lane gets them), rounded to FP32 once.
+template <int OP, int NT, int U>
+__device__ __forceinline__ void r32_sums_op(const ScreenArgs &A, int64_t a, int64_t b, const float *y, int nt,
+                                            const R32Setup &c, float (&S)[2 + NT]) {
+  float hi[2 + NT], lo[2 + NT];
+#pragma unroll
+  for (int k = 0; k < 2 + NT; ++k) hi[k] = lo[k] = 0.f;
+  r32_pass<OP, NT, U>(A.F.v32 + a * A.F.ld, A.F.v32 + b * A.F.ld, y, A.ldy, nt, A.N, c.kk, c.mi, c.mj, hi, lo);
+#pragma unroll
+  for (int k = 0; k < 2 + NT; ++k) {
+    double d = (double)hi[k] + (double)lo[k];
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    S[k] = (float)d;
+  }
+}
+
+template <int NT, int U>
+__device__ __forceinline__ void r32_sums(const ScreenArgs &A, int op, int64_t a, int64_t b, const float *y, int nt,
+                                         const R32Setup &c, float (&S)[2 + NT]) {
+  switch (op) {
+    case DSE_OP_MUL: r32_sums_op<DSE_OP_MUL, NT, U>(A, a, b, y, nt, c, S); break;
+    case DSE_OP_DIV: r32_sums_op<DSE_OP_DIV, NT, U>(A, a, b, y, nt, c, S); break;
+    case DSE_OP_RDIV: r32_sums_op<DSE_OP_RDIV, NT, U>(A, a, b, y, nt, c, S); break;
+    case DSE_OP_ADD: r32_sums_op<DSE_OP_ADD, NT, U>(A, a, b, y, nt, c, S); break;
+    case DSE_OP_SUB: r32_sums_op<DSE_OP_SUB, NT, U>(A, a, b, y, nt, c, S); break;
+    default: r32_sums_op<DSE_OP_ABSDIFF, NT, U>(A, a, b, y, nt, c, S); break;
+  }
+}
+
 // ------------------------------------------------------ threshold filter
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {

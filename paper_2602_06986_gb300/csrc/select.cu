@@ -385,96 +385,22 @@ __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const 
 // 5a) FP32 re-score of entries that are certainly in the top k but whose
 // screening bound is wider than the reporting tolerance (products,
 // quotients, sums and differences from the Gram and tensor-core
-// contractions).  One warp per entry evaluates the candidate again in FP32,
-// in the screen's own evaluation forms (so the screen's evaluation-error
-// coefficients apply), sums blocks of 16 samples per lane in FP32 and adds
-// the block totals into FP32 pairs; the lane totals meet in FP64 and are
-// rounded to FP32 once.  The accumulation error is then at most 16 u (the
-// blocks) plus 2 u (the pairs' residual, the final rounding) of the sums of
-// absolute terms; gamma takes 24 u.  The interval comes from the screen's
-// bound (realised test already decided).  The entry is taken when its bound
-// is within the reporting tolerance; its reported score is the FP32 score
-// clamped to the screening interval, which holds the FP64 score, so the
-// clamp moves it towards that score (the bound stays valid) and keeps every
-// certain entry above H, the list's (k+1)-th upper bound.  Entries it cannot
-// take (other operators, operands outside the FP32-safe range, a wider
-// bound) join the pair re-score's jobs.
-constexpr float kGamma32 = 24.0f;
-
-// (hi, lo) += x, Knuth's two-sum with the error term gathered in lo
-__device__ __forceinline__ void pair_acc(float &hi, float &lo, float x) {
-  const float t = __fadd_rn(hi, x);
-  const float z = __fsub_rn(t, hi);
-  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(x, z)));
-  hi = t;
-}
-
-// The screen's FP32 evaluation forms of the binary operators (shift kk for
-// the products, quotients and |a-b|; centring means mi, mj for a+b, a-b).
-template <int OP>
-__device__ __forceinline__ float r32_value(float a, float b, float kk, float mi, float mj) {
-  if (OP == DSE_OP_MUL) return __fmaf_rn(a, b, -kk);
-  if (OP == DSE_OP_DIV) return __fmaf_rn(a, rcp_approx(b), -kk);
-  if (OP == DSE_OP_RDIV) return __fmaf_rn(b, rcp_approx(a), -kk);
-  if (OP == DSE_OP_ADD) return __fadd_rn(__fsub_rn(a, mi), __fsub_rn(b, mj));
-  if (OP == DSE_OP_SUB) return __fsub_rn(__fsub_rn(a, mi), __fsub_rn(b, mj));
-  return __fsub_rn(fabsf(__fsub_rn(a, b)), kk);  // |a-b|
-}
-
-// One lane's samples of the FP32 re-score: float4 groups lane, lane + 32,
-// ...; four groups (16 samples) per step form one summation block.
-template <int OP>
-__device__ __forceinline__ void r32_pass(const float4 *xa, const float4 *xb, const float4 *y, int64_t N, float kk,
-                                         float mi, float mj, float (&hi)[3], float (&lo)[3]) {
-  constexpr int U = 4;
-  const int lane = threadIdx.x & 31;
-  const int64_t n4 = (N + 3) >> 2;
-  for (int64_t i0 = lane; i0 < n4; i0 += 32 * U) {
-    float4 av[U], bv[U], yv[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int64_t i = i0 + 32 * q;
-      const bool in = i < n4;
-      av[q] = in ? __ldg(xa + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-      bv[q] = in ? __ldg(xb + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-      yv[q] = in ? __ldg(y + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    float acc[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int64_t s = (i0 + 32 * q) * 4;
-      const float ae[4] = {av[q].x, av[q].y, av[q].z, av[q].w};
-      const float be[4] = {bv[q].x, bv[q].y, bv[q].z, bv[q].w};
-      const float ye[4] = {yv[q].x, yv[q].y, yv[q].z, yv[q].w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        float w = r32_value<OP>(ae[e], be[e], kk, mi, mj);
-        w = s + e < N ? w : 0.f;  // padding and groups past the row: no term
-        acc[0] = __fadd_rn(acc[0], w);
-        acc[1] = __fmaf_rn(w, w, acc[1]);
-        acc[2] = __fmaf_rn(w, s + e < N ? ye[e] : 0.f, acc[2]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) pair_acc(hi[k], lo[k], acc[k]);
-  }
-}
-
-template <int OP>
-__device__ __forceinline__ float r32_shift(float a, float b) {
-  if (OP == DSE_OP_MUL) return __fmul_rn(a, b);
-  if (OP == DSE_OP_DIV) return __fmul_rn(a, rcp_approx(b));
-  if (OP == DSE_OP_RDIV) return __fmul_rn(b, rcp_approx(a));
-  return fabsf(__fsub_rn(a, b));
-}
-
-__global__ void __launch_bounds__(256) k_rescore32(const SelectArgs S, const ScreenArgs A) {
+// contractions): one warp per entry re-evaluates the candidate in FP32
+// (r32_setup / r32_sums: the screen's evaluation forms, 16-sample FP32
+// blocks added into FP32 pairs, gamma = kGamma32 u) and takes the interval
+// from the screen's bound (realised test already decided).  The entry is
+// taken when its bound is within the reporting tolerance; its reported
+// score is the FP32 score clamped to the screening interval, which holds the
+// FP64 score, so the clamp moves it towards that score (the bound stays
+// valid) and keeps every certain entry above H, the list's (k+1)-th upper
+// bound.  Entries it cannot take (other operators, operands outside the
+// FP32-safe range, a wider bound) join the pair re-score's jobs.
+__global__ void __launch_bounds__(256, 3) k_rescore32(const SelectArgs S, const ScreenArgs A) {
   const int lane = threadIdx.x & 31;
   const unsigned nj = S.n_jobs[1];
   const unsigned warps = (gridDim.x * blockDim.x) >> 5;
   const float u = 5.9604644775390625e-8f;
-  const int64_t N = A.N;
-  const float Nf = (float)N, invN = (float)A.invN, sqrtN = sqrtf(Nf);
+  const float Nf = (float)A.N, invN = (float)A.invN, sqrtN = sqrtf(Nf);
   const float gamma = kGamma32 * u * 1.05f;
   for (unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nj; w += warps) {
     const unsigned pos = S.job32[w], l = S.job32_list[w];
@@ -483,66 +409,19 @@ __global__ void __launch_bounds__(256) k_rescore32(const SelectArgs S, const Scr
     int op = DSE_OP_PRIMARY;
     int64_t a = (int64_t)gid, b = -1;
     if (gid >= (uint64_t)A.n_stored) decode_flat(A.G, gid - (uint64_t)A.n_stored, &op, &a, &b);
-    bool ok = gid >= (uint64_t)A.n_stored && b >= 0 &&
-              (op == DSE_OP_MUL || op == DSE_OP_DIV || op == DSE_OP_RDIV || op == DSE_OP_ADD ||
-               op == DSE_OP_SUB || op == DSE_OP_ABSDIFF) &&
-              DSE_OPERANDS_OK(A.F, a, b, A.err);
-    ok = ok && ((A.F.flags[a] & A.F.flags[b]) & F_FP32_SAFE);
     const int t = A.mode == DSE_MODE_AGGREGATED ? 0 : (int)l;
-    float S1 = 0.f, S2 = 0.f, Sy = 0.f, cshift = 0.f;
-    EvalErr<float> ee{0.f, 0.f};
-    if (ok) {
-      const float4 fa_a = A.F.fa[a], fa_b = A.F.fa[b];
-      const float mi = fa_a.x, mj = fa_b.x;
-      const float *ra = A.F.v32 + a * A.F.ld, *rb = A.F.v32 + b * A.F.ld;
-      // shift of the products, quotients and |a-b|: the mean of the first
-      // (up to) 32 values, so that S2 stays close to the centred sum
-      float kk = 0.f;
-      if (op != DSE_OP_ADD && op != DSE_OP_SUB) {
-        float v0 = 0.f;
-        if (lane < N) {
-          const float x0 = ra[lane], y0 = rb[lane];
-          v0 = op == DSE_OP_MUL ? r32_shift<DSE_OP_MUL>(x0, y0)
-               : op == DSE_OP_DIV ? r32_shift<DSE_OP_DIV>(x0, y0)
-               : op == DSE_OP_RDIV ? r32_shift<DSE_OP_RDIV>(x0, y0)
-                                   : r32_shift<DSE_OP_ABSDIFF>(x0, y0);
-        }
-        for (int o = 16; o > 0; o >>= 1) v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        kk = v0 / (float)(N < 32 ? N : 32);
-        if (!isfinite(kk)) kk = 0.f;
-      }
-      ok = binary_apriori_W<float>(A, op, a, b, fa_a, fa_b, kk, mi, mj, &ee) == DSE_VALID;
-      cshift = op == DSE_OP_ADD ? mi + mj : op == DSE_OP_SUB ? mi - mj : kk;
-      if (ok) {
-        const float4 *xa = reinterpret_cast<const float4 *>(ra), *xb = reinterpret_cast<const float4 *>(rb);
-        const float4 *yr = reinterpret_cast<const float4 *>(A.y32 + (int64_t)t * A.ldy);
-        float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
-        switch (op) {
-          case DSE_OP_MUL: r32_pass<DSE_OP_MUL>(xa, xb, yr, N, kk, mi, mj, hi, lo); break;
-          case DSE_OP_DIV: r32_pass<DSE_OP_DIV>(xa, xb, yr, N, kk, mi, mj, hi, lo); break;
-          case DSE_OP_RDIV: r32_pass<DSE_OP_RDIV>(xa, xb, yr, N, kk, mi, mj, hi, lo); break;
-          case DSE_OP_ADD: r32_pass<DSE_OP_ADD>(xa, xb, yr, N, kk, mi, mj, hi, lo); break;
-          case DSE_OP_SUB: r32_pass<DSE_OP_SUB>(xa, xb, yr, N, kk, mi, mj, hi, lo); break;
-          default: r32_pass<DSE_OP_ABSDIFF>(xa, xb, yr, N, kk, mi, mj, hi, lo); break;
-        }
-        double d[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          d[k] = (double)hi[k] + (double)lo[k];
-          for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_xor_sync(0xffffffffu, d[k], o);
-        }
-        S1 = (float)d[0];
-        S2 = (float)d[1];
-        Sy = (float)d[2];
-      }
-    }
+    R32Setup c;
+    const bool ok = gid >= (uint64_t)A.n_stored && r32_setup(A, op, a, b, c);
+    float Sm[3] = {0.f, 0.f, 0.f};
+    if (ok) r32_sums<1, 4>(A, op, a, b, A.y32 + (int64_t)t * A.ldy, 1, c, Sm);
     if (lane == 0) {
       bool take = false;
       float s = 0.f, e = 1.f;
       if (ok) {
-        const CandInterval<float> ci = cand_interval<float>(S1, S2, Nf, invN, sqrtN, cshift, ee, gamma, u, -1.0f);
+        const CandInterval<float> ci = cand_interval<float>(Sm[0], Sm[1], Nf, invN, sqrtN, c.cshift, c.ee, gamma, u,
+                                                            -1.0f);
         if (ci.realised == 1) {
-          cand_score<float>(ci, S1, Sy, invN, A.ysum32[t], gamma, u, &s, &e);
+          cand_score<float>(ci, Sm[0], Sm[2], invN, A.ysum32[t], gamma, u, &s, &e);
           take = s > 0.f && e <= 0.99f * kTol * s;
         }
       }
