@@ -1519,7 +1519,7 @@ __global__ void __launch_bounds__(kEscS, 2) k_escalate_stash(const ScreenArgs A)
 
 // FP32 stage of the escalation (single screens, at most 16 targets): one
 // warp per escalated binary candidate evaluates it again in FP32 with the
-// tight accumulation of r32_sums (16-sample FP32 blocks into FP32 pairs,
+// tight accumulation of r32_sums (8-sample FP32 blocks into FP32 pairs,
 // gamma = kGamma32 u instead of the screening kernel's wider bound: the Gram
 // contractions escalate candidates whose BF16x3 interval of the centred sum
 // of squares reaches zero, most of which are far from degenerate) and
@@ -1534,7 +1534,7 @@ __global__ void __launch_bounds__(256) k_escalate32(const ScreenArgs A) {
   const unsigned warps = (gridDim.x * blockDim.x) >> 5;
   const float u = 5.9604644775390625e-8f;
   const float Nf = (float)A.N, invN = (float)A.invN, sqrtN = sqrtf(Nf);
-  const float gamma = kGamma32 * u * 1.05f, fmin = (float)A.fmin_std_rel64;
+  const float gamma = kGamma32 * u, fmin = (float)A.fmin_std_rel64;
   float ysum[16];
   load_ysum<float, 16>(A, ysum);
   LaneStats ls;

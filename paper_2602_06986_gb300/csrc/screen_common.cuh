@@ -328,12 +328,15 @@ __device__ __forceinline__ int binary_apriori_W(const ScreenArgs &A, int opc, in
 // evaluate a binary candidate again, one warp per candidate, in the screen's
 // own FP32 evaluation forms (so binary_apriori_W's evaluation-error
 // coefficients apply): float4 groups lane, lane + 32, ... of the operand rows
-// and the targets; every 16 of a lane's samples form one FP32 summation block
-// whose totals are added into FP32 pairs (hi, lo); the lane totals meet in
-// FP64 and are rounded to FP32 once.  The accumulation error is then at most
-// 16 u (the blocks) plus 2 u (the pairs' residual, the final rounding) of the
-// sums of absolute terms: gamma takes kGamma32 = 24 units of u.
-constexpr float kGamma32 = 24.0f;
+// and the targets; every kR32Block of a lane's samples form one FP32
+// summation block whose totals are added into FP32 pairs (hi, lo); the lane
+// totals meet in FP64 and are rounded to FP32 once.  The accumulation error
+// on the sum of absolute terms is then at most (kR32Block - 1) u (the
+// blocks), u (the pairs' residual, which gathers rounding errors of size u^2)
+// and u (the final rounding), plus 2^-48 for the FP64 lane tree: gamma takes
+// (kR32Block + 2) u with 5% to spare.
+constexpr int kR32Block = 8;  // samples per summation block (two float4 groups)
+constexpr float kGamma32 = (float)(kR32Block + 2) * 1.05f;  // units of u
 
 // (hi, lo) += x, Knuth's two-sum with the error term gathered in lo
 __device__ __forceinline__ void pair_acc(float &hi, float &lo, float x) {
@@ -379,8 +382,9 @@ template <int OP, int NT, int U>
 __device__ __forceinline__ void r32_pass(const float *ra, const float *rb, const float *y, int64_t ldy, int nt,
                                          int64_t N, float kk, float mi, float mj, float (&hi)[2 + NT],
                                          float (&lo)[2 + NT]) {
-  static_assert(U == 1 || U == 2 || U == 4, "16-sample blocks");
-  constexpr int STEPS = 4 / U;
+  constexpr int BQ = kR32Block / 4;  // float4 groups per block
+  static_assert(kR32Block % 4 == 0 && (U % BQ == 0 || BQ % U == 0), "blocks of whole groups and steps");
+  constexpr int STEPS = BQ > U ? BQ / U : 1;  // steps per block (blocks of several steps)
   const int lane = threadIdx.x & 31;
   const int64_t n4 = (N + 3) >> 2;
   const int rem = (int)(N & 3);
@@ -421,8 +425,15 @@ __device__ __forceinline__ void r32_pass(const float *ra, const float *rb, const
           acc[2 + t] = __fmaf_rn(w, yy, acc[2 + t]);
         }
       }
+      if (BQ <= U && (q + 1) % BQ == 0) {  // a block ends inside the step
+#pragma unroll
+        for (int k = 0; k < 2 + NT; ++k) {
+          pair_acc(hi[k], lo[k], acc[k]);
+          acc[k] = 0.f;
+        }
+      }
     }
-    if (++nb == STEPS) {
+    if (BQ > U && ++nb == STEPS) {
       nb = 0;
 #pragma unroll
       for (int k = 0; k < 2 + NT; ++k) {

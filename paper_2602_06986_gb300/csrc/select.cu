@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(256) k_rescore_warp(const SelectArgs S, const 
 // screening bound is wider than the reporting tolerance (products,
 // quotients, sums and differences from the Gram and tensor-core
 // contractions): one warp per entry re-evaluates the candidate in FP32
-// (r32_setup / r32_sums: the screen's evaluation forms, 16-sample FP32
+// (r32_setup / r32_sums: the screen's evaluation forms, 8-sample FP32
 // blocks added into FP32 pairs, gamma = kGamma32 u) and takes the interval
 // from the screen's bound (realised test already decided).  The entry is
 // taken when its bound is within the reporting tolerance; its reported
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256, 3) k_rescore32(const SelectArgs S, const 
   const unsigned warps = (gridDim.x * blockDim.x) >> 5;
   const float u = 5.9604644775390625e-8f;
   const float Nf = (float)A.N, invN = (float)A.invN, sqrtN = sqrtf(Nf);
-  const float gamma = kGamma32 * u * 1.05f;
+  const float gamma = kGamma32 * u;
   for (unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nj; w += warps) {
     const unsigned pos = S.job32[w], l = S.job32_list[w];
     const size_t r = (size_t)l * S.B.cap + pos;
