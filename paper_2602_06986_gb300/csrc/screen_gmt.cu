@@ -466,7 +466,9 @@ __device__ __forceinline__ uint32_t gmt_targets(const ScreenArgs &A, LaneStats &
   note_why(A, gid, DSE_VALID);
   uint32_t pushed = 0;
   const float u = 5.9604644775390625e-8f;
-#pragma unroll
+  // (a loop, not 16 unrolled copies: the epilogue's code stays small enough
+  // for the instruction cache)
+#pragma unroll 1
   for (int t = 0; t < gmt::NTP; ++t) {
     if (t >= A.T) break;
     float S, d, s, eps;
@@ -549,9 +551,14 @@ __device__ __forceinline__ uint32_t gmt_product(const ScreenArgs &A, const GmtAr
   const GramVar v = gram_var(S1, dS1, S2, dS2, Z, dZ, Vhi, E, N, invN, (float)A.fmin_std_rel64);
   const GmtTgt *tj = GA.gt + j;
   const int lane = threadIdx.x & 31;
+  // the slot's H entries, copied out of the running sums with compile-time
+  // indices (the target loop indexes this copy, so run[] stays in registers)
+  float hv[gmt::NTP];
+#pragma unroll
+  for (int t = 0; t < gmt::NTP; ++t) hv[t] = run[HOFF + t];
   auto sy = [&](int t, float *S, float *d) {
     const float PY = py[t][lane], QY = __ldg(&tj->sy[FW][t]), nyw = __ldg(&tj->ny[FW][t]);
-    const float tya = cu * QY, tyb = cw * PY, h = run[HOFF + t];
+    const float tya = cu * QY, tyb = cw * PY, h = hv[t];
     *S = tya + tyb + h;
     *d = (delta * fminf(n1u * nyw, ge.h) + 10.f * u * (fabsf(tya) + fabsf(tyb) + fabsf(h)) +
           9.1f * u * (acu * n1w + acw * n1u)) *
@@ -661,10 +668,12 @@ __device__ __forceinline__ uint32_t gmt_pair(const ScreenArgs &A, const GmtArgs 
   return pushed;
 }
 
-// Epilogue of half HH (b-features 3 HH .. 3 HH + 2 of every tile).
-template <int HH, class WaitWarp, class Aborted>
+// Epilogue of warp part hh (b-features BPW hh .. BPW hh + BPW - 1 of every
+// tile); one instance for every part (only the drain's TMEM columns depend
+// on hh), so that the code stays small.
+template <class WaitWarp, class Aborted>
 __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs &GA, gmt::Shared &sh, uint32_t tmem,
-                                             int q, int ew, WaitWarp wait_warp, Aborted aborted_warp) {
+                                             int q, int ew, int hh, WaitWarp wait_warp, Aborted aborted_warp) {
   using namespace gmt;
   const int lane = threadIdx.x & 31;
   const uint32_t lane_base = (uint32_t)(q * 32) << 16;
@@ -687,7 +696,13 @@ __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs 
         break;
       }
       tc::fence_after();
-      gmt_drain<HH>(tmem + lane_base + set * SET, run, b == 0);
+      const uint32_t ta = tmem + lane_base + set * SET;
+      if (hh == 0)
+        gmt_drain<0>(ta, run, b == 0);
+      else if (hh == 1)
+        gmt_drain<1>(ta, run, b == 0);
+      else
+        gmt_drain<2>(ta, run, b == 0);
       tc::fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&sh.acc_empty[set]);
@@ -698,7 +713,7 @@ __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs 
     for (int t = lane; t < NTP; t += 32) theta[t] = t < A.T ? ld_relaxed(&A.B.theta[A.t0 + t]) : 0.f;
     __syncwarp();
     const int64_t i = (int64_t)tl.x * FA + q * 32 + lane;
-    const int64_t j0 = (int64_t)tl.y * FB + BPW * HH;
+    const int64_t j0 = (int64_t)tl.y * FB + BPW * hh;
     const bool own = i < A.F.n;
     gram::EpiFeat Fi;
     if (own) Fi = gmt_rec(A, GA.gf, i);
@@ -878,12 +893,7 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;  // 0 .. EPI-1
     const int q = warp & 3;   // TMEM lane quadrant = a-features 32 q .. 32 q + 31
-    if ((ew >> 2) == 0)
-      gmt_epilogue<0>(A, GA, sh, tmem, q, ew, wait_warp, aborted_warp);
-    else if ((ew >> 2) == 1)
-      gmt_epilogue<1>(A, GA, sh, tmem, q, ew, wait_warp, aborted_warp);
-    else
-      gmt_epilogue<2>(A, GA, sh, tmem, q, ew, wait_warp, aborted_warp);
+    gmt_epilogue(A, GA, sh, tmem, q, ew, ew >> 2, wait_warp, aborted_warp);
   }
   fence_before();
   __syncthreads();
