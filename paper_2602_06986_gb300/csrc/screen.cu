@@ -390,13 +390,17 @@ __global__ void __launch_bounds__(256) k_feature(const ScreenArgs A, uint64_t id
 // candidate would read all 16 target rows from L2 for every candidate; here
 // a warp scores CW candidates at once and the block's 8 warps move through
 // the samples together: each 256-sample chunk of the targets (sample-major,
-// [s][16], read with 16-byte loads) and of the block's 32 operand rows is
+// [s][8], read with 16-byte loads) and of the block's 32 operand rows is
 // staged in shared memory by asynchronous copies (cp.async, zero-filled past
-// N), double-buffered, so the scoring loop reads shared memory only.  Each
-// lane takes samples lane, lane + 32, ... in order with the same blocking as
+// N), double-buffered, so the scoring loop reads shared memory only.  The
+// samples are taken twice, for targets 0..7 (with S1 and S2) and 8..15, so
+// that the running sums of one half fit in registers at two blocks per SM
+// (one pass over all 16 needed 233 registers: one block, 8 warps per SM);
+// the reduced sums of the first half wait in shared memory.  Each lane takes
+// samples lane, lane + 32, ... in order with the same blocking as
 // k_feature, so the sums, bounds and decisions are those of
 // k_feature<float, 16>.
-constexpr int kF16Chunk = 256, kF16CW = 4;
+constexpr int kF16Chunk = 256, kF16CW = 4, kF16Half = 8;
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
@@ -405,14 +409,15 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid
 }
 
 template <int CW>
-__global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64_t id0, uint64_t id1, uint64_t p0,
+__global__ void __launch_bounds__(256, 2) k_feature16(const ScreenArgs A, uint64_t id0, uint64_t id1, uint64_t p0,
                                                       uint64_t p1, float gamma_lane) {
-  constexpr int NT = 16, KS = kF16Chunk, WARPS = 8, NC = WARPS * CW;
+  constexpr int NT = 16, TH = kF16Half, KS = kF16Chunk, WARPS = 8, NC = WARPS * CW;
   extern __shared__ __align__(16) float f16sm[];
-  float(*ys)[KS][NT] = reinterpret_cast<float(*)[KS][NT]>(f16sm);                  // [2][KS][NT]
-  float(*xs)[NC][KS] = reinterpret_cast<float(*)[NC][KS]>(f16sm + 2 * KS * NT);     // [2][NC][KS]
+  float(*ys)[KS][TH] = reinterpret_cast<float(*)[KS][TH]>(f16sm);                  // [2][KS][TH]
+  float(*xs)[NC][KS] = reinterpret_cast<float(*)[NC][KS]>(f16sm + 2 * KS * TH);     // [2][NC][KS]
   __shared__ const float *rows[NC];
   __shared__ int ract[NC];
+  __shared__ float sres[NC][2 + NT];  // reduced S1, S2, Sy of the first half
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t nid = id1 - id0, ncand = nid + (p1 - p0);
   const uint64_t per_tile = (uint64_t)NC;
@@ -428,14 +433,14 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
   LaneStats ls;
   ls.zero();
   const int nchunk = (int)((Ns + KS - 1) / KS);
-  // thread i stages sample i of a chunk: the 16 targets and the 32 rows
-  auto stage = [&](int ch, int buf) {
+  // thread i stages sample i of a chunk: the half's 8 targets and the 32 rows
+  auto stage = [&](int ch, int buf, int th0) {
     const int64_t s = (int64_t)ch * KS + threadIdx.x;
     const bool in = s < Ns;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const bool v = in && t < T;
-      cp_async4(&ys[buf][threadIdx.x][t], A.y32 + (v ? (int64_t)(t0 + t) * ldy + s : 0), v);
+    for (int t = 0; t < TH; ++t) {
+      const bool v = in && th0 + t < T;
+      cp_async4(&ys[buf][threadIdx.x][t], A.y32 + (v ? (int64_t)(t0 + th0 + t) * ldy + s : 0), v);
     }
 #pragma unroll 8
     for (int k = 0; k < NC; ++k) {
@@ -484,79 +489,105 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
         ract[warp * CW + k] = act[k] ? 1 : 0;
       }
     }
-    float S1[CW], S2[CW], o1[CW], o2[CW], Sy[CW][NT], oy[CW][NT];
+    for (int half = 0; half < 2; ++half) {
+      const int th0 = half * TH;
+      const bool first = half == 0;
+      float S1[CW], S2[CW], o1[CW], o2[CW], Sy[CW][TH], oy[CW][TH];
 #pragma unroll
-    for (int k = 0; k < CW; ++k) {
-      S1[k] = S2[k] = o1[k] = o2[k] = 0.f;
+      for (int k = 0; k < CW; ++k) {
+        S1[k] = S2[k] = o1[k] = o2[k] = 0.f;
 #pragma unroll
-      for (int t = 0; t < NT; ++t) Sy[k][t] = oy[k][t] = 0.f;
-    }
-    int blk = 0;
-    __syncthreads();  // (rows of this tile; the previous tile's last chunk is no longer read)
-    stage(0, 0);
-    for (int ch = 0; ch < nchunk; ++ch) {
-      const int buf = ch & 1;
-      if (ch + 1 < nchunk) {
-        stage(ch + 1, buf ^ 1);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-      } else {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        for (int t = 0; t < TH; ++t) Sy[k][t] = oy[k][t] = 0.f;
       }
-      __syncthreads();
+      int blk = 0;
+      __syncthreads();  // (rows of this tile; the previous pass's last chunk is no longer read)
+      stage(0, 0, th0);
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int buf = ch & 1;
+        if (ch + 1 < nchunk) {
+          stage(ch + 1, buf ^ 1, th0);
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
 #pragma unroll 1
-      for (int j = 0; j < KS / 32; ++j) {
-        const int64_t s = (int64_t)ch * KS + lane + 32 * j;
-        if (s >= Ns) break;
-        float xv[CW];
+        for (int j = 0; j < KS / 32; ++j) {
+          const int64_t s = (int64_t)ch * KS + lane + 32 * j;
+          if (s >= Ns) break;
+          float xv[CW];
 #pragma unroll
-        for (int k = 0; k < CW; ++k) xv[k] = xs[buf][warp * CW + k][lane + 32 * j];
-        float yv[NT];
-        const float4 *yp = reinterpret_cast<const float4 *>(&ys[buf][lane + 32 * j][0]);
+          for (int k = 0; k < CW; ++k) xv[k] = xs[buf][warp * CW + k][lane + 32 * j];
+          float yv[TH];
+          const float4 *yp = reinterpret_cast<const float4 *>(&ys[buf][lane + 32 * j][0]);
 #pragma unroll
-        for (int q = 0; q < NT / 4; ++q) {
-          const float4 y4 = yp[q];
-          yv[4 * q] = y4.x, yv[4 * q + 1] = y4.y, yv[4 * q + 2] = y4.z, yv[4 * q + 3] = y4.w;
-        }
-#pragma unroll
-        for (int k = 0; k < CW; ++k) {
-          if (!act[k]) continue;
-          const float v = unary_eval<float>(op[k], xv[k], c[k]);
-          S1[k] += v;
-          S2[k] = fmaf(v, v, S2[k]);
-#pragma unroll
-          for (int t = 0; t < NT; ++t)
-            if (t < T) Sy[k][t] = fmaf(v, yv[t], Sy[k][t]);
-        }
-        if (++blk == 16) {
-          blk = 0;
+          for (int q = 0; q < TH / 4; ++q) {
+            const float4 y4 = yp[q];
+            yv[4 * q] = y4.x, yv[4 * q + 1] = y4.y, yv[4 * q + 2] = y4.z, yv[4 * q + 3] = y4.w;
+          }
 #pragma unroll
           for (int k = 0; k < CW; ++k) {
-            o1[k] += S1[k];
-            o2[k] += S2[k];
-            S1[k] = 0.f;
-            S2[k] = 0.f;
+            if (!act[k]) continue;
+            const float v = unary_eval<float>(op[k], xv[k], c[k]);
+            if (first) {
+              S1[k] += v;
+              S2[k] = fmaf(v, v, S2[k]);
+            }
 #pragma unroll
-            for (int t = 0; t < NT; ++t) {
-              oy[k][t] += Sy[k][t];
-              Sy[k][t] = 0.f;
+            for (int t = 0; t < TH; ++t)
+              if (th0 + t < T) Sy[k][t] = fmaf(v, yv[t], Sy[k][t]);
+          }
+          if (++blk == 16) {
+            blk = 0;
+#pragma unroll
+            for (int k = 0; k < CW; ++k) {
+              o1[k] += S1[k];
+              o2[k] += S2[k];
+              S1[k] = 0.f;
+              S2[k] = 0.f;
+#pragma unroll
+              for (int t = 0; t < TH; ++t) {
+                oy[k][t] += Sy[k][t];
+                Sy[k][t] = 0.f;
+              }
             }
           }
         }
+        __syncthreads();  // (the buffer is staged again two chunks later)
       }
-      __syncthreads();  // (the buffer is staged again two chunks later)
-    }
+      // the half's sums, reduced over the warp, wait in shared memory
 #pragma unroll
+      for (int k = 0; k < CW; ++k) {
+        if (!act[k]) continue;  // (warp-uniform)
+        float s1 = S1[k] + o1[k], s2 = S2[k] + o2[k], sy[TH];
+#pragma unroll
+        for (int t = 0; t < TH; ++t) sy[t] = Sy[k][t] + oy[k][t];
+        for (int o = 16; o > 0; o >>= 1) {
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+#pragma unroll
+          for (int t = 0; t < TH; ++t) sy[t] += __shfl_xor_sync(0xffffffffu, sy[t], o);
+        }
+        if (lane == 0) {
+          float *r = sres[warp * CW + k];
+          if (first) {
+            r[0] = s1;
+            r[1] = s2;
+          }
+#pragma unroll
+          for (int t = 0; t < TH; ++t) r[2 + th0 + t] = sy[t];
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll 1
     for (int k = 0; k < CW; ++k) {
       if (!act[k]) continue;  // (warp-uniform)
-      float s1 = S1[k] + o1[k], s2 = S2[k] + o2[k], sy[NT];
+      const float *r = sres[warp * CW + k];
+      const float s1 = r[0], s2 = r[1];
+      float sy[NT];
 #pragma unroll
-      for (int t = 0; t < NT; ++t) sy[t] = Sy[k][t] + oy[k][t];
-      for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) sy[t] += __shfl_xor_sync(0xffffffffu, sy[t], o);
-      }
+      for (int t = 0; t < NT; ++t) sy[t] = r[2 + t];
       const CandInterval<float> ci = cand_interval<float>(s1, s2, N, invN, sqrtN, c[k], ee[k], gamma, u, fmin);
       if (ci.realised == 0) {
         if (lane == 0) {
@@ -584,7 +615,8 @@ __global__ void __launch_bounds__(256, 1) k_feature16(const ScreenArgs A, uint64
   flush_stats(A, ls);
 }
 
-constexpr size_t kF16Smem = (size_t)2 * kF16Chunk * 16 * sizeof(float) + (size_t)2 * 8 * kF16CW * kF16Chunk * sizeof(float);
+constexpr size_t kF16Smem =
+    (size_t)2 * kF16Chunk * kF16Half * sizeof(float) + (size_t)2 * 8 * kF16CW * kF16Chunk * sizeof(float);
 
 // Batched screens: warps take jobs (runs of one problem's stored/unary
 // candidates, the whole group of every problem) from a shared counter.
@@ -1670,9 +1702,9 @@ void launch_feature_t(const ScreenArgs &A, uint64_t id0, uint64_t id1, uint64_t 
   ScreenArgs B = A;
   B.group = 0;
   if (sizeof(R) == 4 && NT == 16) {
-    // 32 candidates per block, one block per SM at a time
+    // 32 candidates per block, two blocks per SM at a time
     uint64_t tiles = (ncand + 8 * kF16CW - 1) / (8 * kF16CW);
-    if (tiles > (uint64_t)sms) tiles = (uint64_t)sms;
+    if (tiles > (uint64_t)sms * 2) tiles = (uint64_t)sms * 2;
     static bool attr[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
