@@ -175,13 +175,17 @@ __global__ void __launch_bounds__(128) k_gmt_space(FeatTable F, int nchunks, uns
 // The b-images are written a row group at a time: 8 rows x 32 samples of
 // one chunk part are 512 contiguous bytes, one 16-byte piece per lane (lane
 // = 8 k-group + row within the group), so every warp store is coalesced.
-// A block takes one b-block and kBrowsCh chunks; its warps take the row
-// groups (H: b-feature g, family, half of the targets; G: two b-features'
-// [q, q^2, q', q'^2]) and keep, per lane, the target sums of its H rows
-// over the block's chunks.
+// A block takes one b-block and kBrowsCh chunks.  Per chunk the block first
+// puts the centred values of its 6 b-features (both families) and the 16
+// targets' values in shared memory, each computed or loaded once (the 8
+// target lanes of a row group need the same values), then its warps take
+// the row groups (H: b-feature g, family, half of the targets; G: two
+// b-features' [q, q^2, q', q'^2]) and keep, per lane, the target sums of its
+// H rows over the block's chunks.
 constexpr int kBrowsCh = 16;  // chunks per k_gmt_brows block
 constexpr int kHTypes = gmt::FB * 4;  // H row groups per b-block: g x family x half of the targets
 static_assert(kHTypes == 3 * 8 && gmt::NTP == 16 && gmt::NG == 4 * 8, "row groups of the 8 warps");
+static_assert(tc::KC == 32, "one chunk = 32 samples = 4 k-groups of 8");
 
 // Per-block partial target sums: [b-block][chunk block][g][family][target]
 // of (compensated pair s, c; sum of squares).
@@ -203,43 +207,66 @@ size_t gmt_part_count(int64_t n, int64_t N) {
 __global__ void __launch_bounds__(256) k_gmt_brows(FeatTable F, int nchunks, const float *y32, int64_t ldy, int T,
                                                    const GramFeat *gf, unsigned char *bimg, GmtPart *part) {
   using namespace gmt;
+  constexpr int KC = tc::KC;
+  // double-buffered per-chunk values: [g][family][sample], [target][sample]
+  // (rows padded to 36 floats: the 8 target rows a quarter-warp reads with
+  // 16-byte loads fall in distinct banks)
+  __shared__ __align__(16) float pv[2][FB][2][KC + 4];
+  __shared__ __align__(16) float yv[2][NTP][KC + 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int kg = lane >> 3, r8 = lane & 7;
   const int64_t bb = blockIdx.x, cb = blockIdx.y;
   const int c0 = (int)cb * kBrowsCh, c1 = min(nchunks, c0 + kBrowsCh);
   const int64_t N = F.N;
+  // the values thread x computes for every chunk: (g, family, sample) of
+  // x < 2 FB KC = 384, then (target, sample) of x - 2 FB KC < NTP KC = 512
+  // (x = threadIdx.x + 256 h, h = 0..3)
+  static_assert(2 * FB * KC + NTP * KC <= 4 * 256, "four values per thread");
+  auto fill = [&](int c, int buf) {
+    const int64_t sb = (int64_t)c * KC;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int x = threadIdx.x + 256 * h;
+      if (x < 2 * FB * KC) {
+        const int g = x / (2 * KC), fam = (x / KC) & 1, e = x % KC;
+        const int64_t f = bb * FB + g, sidx = sb + e;
+        float v = 0.f;
+        if (f < F.n) {
+          const GramFeat G = gf[f];
+          if (G.ok[fam] && sidx < N) {
+            const float xv = F.v32[f * F.ld + sidx];
+            v = (fam == 0 ? xv : __frcp_rn(xv)) - G.c[fam];
+          }
+        }
+        pv[buf][g][fam][e] = v;
+      } else if (x < 2 * FB * KC + NTP * KC) {
+        const int t = (x - 2 * FB * KC) / KC, e = (x - 2 * FB * KC) % KC;
+        const int64_t sidx = sb + e;
+        yv[buf][t][e] = (t < T && sidx < N) ? y32[(int64_t)t * ldy + sidx] : 0.f;
+      }
+    }
+  };
   // H row groups of this warp: types warp, warp + 8, warp + 16 (type =
   // 4 g + 2 family + half)
   Comp32 acc[3];
   float sq[3] = {0.f, 0.f, 0.f};
+  if (c0 < c1) fill(c0, 0);
   for (int c = c0; c < c1; ++c) {
+    const int buf = (c - c0) & 1;
+    __syncthreads();  // this chunk's values are in; the other buffer is free
+    if (c + 1 < c1) fill(c + 1, buf ^ 1);
     unsigned char *base = bimg + ((size_t)bb * nchunks + c) * B_IMG;
-    const int64_t s0 = (int64_t)c * tc::KC + kg * 8;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int type = warp + 8 * i;
       const int g = type >> 2, fam = (type >> 1) & 1, half = type & 1;
       const int t = half * 8 + r8;
-      const int64_t f = bb * FB + g;
-      const bool real = f < F.n;
-      float p[8], py[8];
-      if (real) {
-        const GramFeat G = gf[f];
-        gram_vals(F, f, s0, fam, G.c[fam], G.ok[fam] != 0, p);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) p[e] = 0.f;
-      }
-      float y[8];
-      if (t < T && s0 + 8 <= N) {
-        // (target rows are 16-byte aligned: ldy is a multiple of 4)
-        const float4 *src = reinterpret_cast<const float4 *>(y32 + (int64_t)t * ldy + s0);
-        const float4 a = src[0], b = src[1];
-        y[0] = a.x, y[1] = a.y, y[2] = a.z, y[3] = a.w, y[4] = b.x, y[5] = b.y, y[6] = b.z, y[7] = b.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) y[e] = (t < T && s0 + e < N) ? y32[(int64_t)t * ldy + s0 + e] : 0.f;
-      }
+      const float4 *pp = reinterpret_cast<const float4 *>(&pv[buf][g][fam][kg * 8]);
+      const float4 *yp = reinterpret_cast<const float4 *>(&yv[buf][t][kg * 8]);
+      const float4 pa = pp[0], pb = pp[1], ya = yp[0], yb = yp[1];
+      const float p[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+      const float y[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+      float py[8];
       float part8 = 0.f;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -258,11 +285,11 @@ __global__ void __launch_bounds__(256) k_gmt_brows(FeatTable F, int nchunks, con
       // G row group `warp`: rows NH + 8 warp + r8 = b-feature 2 warp + r8 / 4,
       // type r8 % 4 (q, q^2 of x, then of 1/x)
       const int g = 2 * warp + (r8 >> 2), k = r8 & 3, fam = k >> 1;
-      const int64_t f = bb * FB + g;
       float v[8];
-      if (g < FB && f < F.n) {
-        const GramFeat G = gf[f];
-        gram_vals(F, f, s0, fam, G.c[fam], G.ok[fam] != 0, v);
+      if (g < FB) {
+        const float4 *pp = reinterpret_cast<const float4 *>(&pv[buf][g][fam][kg * 8]);
+        const float4 pa = pp[0], pb = pp[1];
+        v[0] = pa.x, v[1] = pa.y, v[2] = pa.z, v[3] = pa.w, v[4] = pb.x, v[5] = pb.y, v[6] = pb.z, v[7] = pb.w;
         if (k & 1) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) v[e] = v[e] * v[e];
