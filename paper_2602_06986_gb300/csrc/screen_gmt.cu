@@ -741,7 +741,7 @@ __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs 
     __syncwarp();
     const int64_t i = (int64_t)tl.x * FA + q * 32 + lane;
     const int64_t j0 = (int64_t)tl.y * FB + BPW * hh;
-    const bool own = i < A.F.n;
+    const bool own = tl.x >= 0 && i < A.F.n;  // (tl.x < 0: the empty partner of a pair)
     gram::EpiFeat Fi;
     if (own) Fi = gmt_rec(A, GA.gf, i);
     // this lane's a-feature target sums (x family), target-major in shared
@@ -789,19 +789,28 @@ __device__ __forceinline__ void gmt_epilogue(const ScreenArgs &A, const GmtArgs 
   flush_stats(A, ls);
 }
 
+// CL = 2: the two CTAs of a cluster take the two tiles of a pair (the same
+// b-block, two a-blocks): each copies its own a-image chunk and one half
+// (BF16 hi or lo part) of the shared b-image chunk, multicast into both
+// CTAs' stages, so the b-side is read from L2 once per pair; a stage is
+// refilled once both CTAs' MMAs have released it (each MMA commit arrives on
+// the empty barriers of both CTAs).  CL = 1: one CTA per tile.
+template <int CL>
 __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A, const GmtArgs GA) {
   using namespace gmt;
   using namespace tc;
+  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
   extern __shared__ __align__(1024) unsigned char smem[];
   Shared &sh = *reinterpret_cast<Shared *>(smem);
   unsigned char *stages = smem + shared_bytes();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = GA.nchunks, nblocks = GA.nblocks;
+  const uint32_t crank = CL == 2 ? cluster_ctarank() : 0u;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(&sh.full[s], 1);
-      mbar_init(&sh.empty[s], 1);
+      mbar_init(&sh.empty[s], CL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.acc_full[b], 1);
@@ -821,6 +830,8 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
   fence_before();
   __syncthreads();
   fence_after();
+  // (the peer's barriers are initialised before any copy or commit reaches them)
+  if (CL == 2) cluster_sync_all();
   const uint32_t tmem = sh.tmem_base;
 
   volatile int *abort_flag = &sh.abort;
@@ -847,6 +858,7 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
       uint32_t issued = 0;
       for (int tile = blockIdx.x; tile < GA.n_tiles && !*abort_flag; tile += gridDim.x, ++lt) {
         int2 tl = GA.tiles[tile];
+        if (tl.x < 0) tl.x = 0;  // the empty partner of a pair: any a-block, nothing is scored
         if (!(DSE_IN_BOUNDS(tl.x, GA.na, A.err) && DSE_IN_BOUNDS(tl.y, GA.nb, A.err))) tl = make_int2(0, 0);
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
@@ -858,7 +870,11 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
           unsigned char *S = stages + (size_t)st * STAGE;
           mbar_arrive_expect_tx(&sh.full[st], STAGE);
           bulk_g2s(S, GA.aimg + ((size_t)tl.x * nchunks + c) * A_IMG, A_IMG, &sh.full[st]);
-          bulk_g2s(S + A_IMG, GA.bimg + ((size_t)tl.y * nchunks + c) * B_IMG, B_IMG, &sh.full[st]);
+          const unsigned char *bsrc = GA.bimg + ((size_t)tl.y * nchunks + c) * B_IMG;
+          if (CL == 2)
+            bulk_g2s_mc(S + A_IMG + crank * B_PART, bsrc + crank * B_PART, B_PART, &sh.full[st], (uint16_t)3);
+          else
+            bulk_g2s(S + A_IMG, bsrc, B_IMG, &sh.full[st]);
           issued = gc + 1;
         }
         if (!ok) break;
@@ -906,7 +922,10 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
               mma_bf16(d, smem_desc(pl + koff), smem_desc(bh + koff), IDESC1, 1u);
               mma_bf16(d + N1, smem_desc(p2l + koff), smem_desc(bh + G_OFF + koff), IDESC2, 1u);
             }
-            mma_commit(&sh.empty[st]);
+            if (CL == 2)
+              mma_commit_mc(&sh.empty[st], (uint16_t)3);
+            else
+              mma_commit(&sh.empty[st]);
           }
           if (!ok) break;
           mma_commit(&sh.acc_full[set]);
@@ -927,6 +946,8 @@ __global__ void __launch_bounds__(gmt::THREADS, 1) k_pair_gmt(const ScreenArgs A
   fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TMEM_COLS) : "memory");
+  // neither CTA leaves while the other's copies or commits may still reach it
+  if (CL == 2) cluster_sync_all();
 }
 
 // ------------------------------------------------------------------- host
@@ -993,10 +1014,15 @@ void gmt_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::vec
   if (p_hi <= p_lo) return;
   auto pidx = [&](int64_t i, int64_t j) { return g.um + (tri((uint64_t)i) + (uint64_t)j - g.tri_o) * (uint64_t)g.nb; };
   const int64_t na = gmt_na(n), nb = gmt_nb(n);
-  const int64_t group = std::max(1, tuning().gmt_group);
+  // (an even group: the tiles of a b-block within a group pair up for the
+  // two CTAs of a cluster)
+  int64_t group = std::max(1, tuning().gmt_group);
+  group += group & 1;
+  std::vector<int> as;
   for (int64_t ga = 0; ga < na; ga += group) {
     for (int64_t c = 0; c < nb; ++c) {
       const int64_t b0 = c * gmt::FB, b1 = std::min<int64_t>(b0 + gmt::FB, n) - 1;
+      as.clear();
       for (int64_t a = ga; a < std::min(na, ga + group); ++a) {
         const int64_t a0 = a * gmt::FA, a1 = std::min<int64_t>(a0 + gmt::FA, n) - 1;
         const int64_t Ilo = std::max<int64_t>(std::max(a0, b0), std::max<int64_t>(o, 1));
@@ -1005,8 +1031,10 @@ void gmt_tiles(const dse_space *sp, uint64_t id_begin, uint64_t id_end, std::vec
         if (a0 == b1 && a1 == b0) continue;  // a single feature on both sides: only i == j
         const uint64_t lo = pidx(Ilo, 0), hi = pidx(Ihi, Ihi - 1) + (uint64_t)g.nb;
         if (hi <= p_lo || lo >= p_hi) continue;
-        out.push_back(make_int2((int)a, (int)c));
+        as.push_back((int)a);
       }
+      if (as.size() & 1) as.push_back(-1);  // an empty partner: the pair's second tile scores nothing
+      for (int a : as) out.push_back(make_int2(a, (int)c));
     }
   }
 }
@@ -1036,12 +1064,31 @@ dse_status launch_pair_gmt(const ScreenArgs &A, const void *space_buf, void *scr
   const unsigned char *bimg = static_cast<const unsigned char *>(scr);
   const GmtTgt *gt = reinterpret_cast<const GmtTgt *>(bimg + (size_t)gmt_nb(n) * nchunks * gmt::B_IMG);
   note_launches(1);
-  static bool attr[64] = {false};
+  // pairs of CTAs per cluster where the device co-schedules them (the count
+  // of clusters that fit at once, per device)
+  static int clusters[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (!attr[dev & 63]) {
-    DSE_CUDA(cudaFuncSetAttribute(k_pair_gmt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmt::smem_total()));
-    attr[dev & 63] = true;
+  if (clusters[dev & 63] == 0) {
+    DSE_CUDA(cudaFuncSetAttribute(k_pair_gmt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmt::smem_total()));
+    DSE_CUDA(cudaFuncSetAttribute(k_pair_gmt<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gmt::smem_total()));
+    cudaLaunchConfig_t q = {};
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = 2;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.gridDim = dim3((unsigned)(sms - sms % 2));
+    q.blockDim = dim3(gmt::THREADS);
+    q.dynamicSmemBytes = gmt::smem_total();
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_pair_gmt<2>, &q) != cudaSuccess || nc < 1) {
+      cudaGetLastError();
+      nc = -1;  // no clusters: one CTA per tile
+    }
+    clusters[dev & 63] = nc;
   }
   GmtArgs GA{aimg, bimg, gf, gt, tiles, n_tiles, nchunks, (nchunks + gmt::DB - 1) / gmt::DB, gmt_delta(N),
              (int)gmt_na(n), (int)gmt_nb(n)};
@@ -1051,8 +1098,30 @@ dse_status launch_pair_gmt(const ScreenArgs &A, const void *space_buf, void *scr
   // top-k over candidates in arbitrary order buffers about k (1 + ln(n / k))
   // entries per list whatever the start, and the sample's thresholds rise
   // no faster)
+  const int nc = clusters[dev & 63];
+  if (nc > 0 && n_tiles % 2 == 0) {
+    // the tile list holds pairs (2p, 2p + 1) of one b-block; CTA x of the
+    // grid takes tiles x, x + grid, ..., so both CTAs of a cluster take the
+    // two tiles of the same pairs
+    int grid = 2 * nc;
+    if (grid > n_tiles) grid = n_tiles;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(gmt::THREADS);
+    cfg.dynamicSmemBytes = gmt::smem_total();
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    DSE_CUDA(cudaLaunchKernelEx(&cfg, k_pair_gmt<2>, B, GA));
+    return DSE_OK;
+  }
   const int grid = sms < n_tiles ? sms : n_tiles;
-  k_pair_gmt<<<grid, gmt::THREADS, gmt::smem_total(), st>>>(B, GA);
+  k_pair_gmt<1><<<grid, gmt::THREADS, gmt::smem_total(), st>>>(B, GA);
   return DSE_OK;
 }
 
