@@ -492,7 +492,11 @@ typedef struct {
                                 features each) per group of the tile order
                                 (the b-blocks are swept once per group),
                                 1..4096 (2)                                  */
-  int32_t reserved[2];
+  int32_t gmt_cluster;       /* multi-target Gram kernel: CTAs per thread-
+                                block cluster sharing each b-image chunk by
+                                multicast, 1 or 2 (2; one CTA per tile also
+                                where the device cannot co-schedule pairs)   */
+  int32_t reserved[1];
 } dse_tuning;
 
 /* Installs t (NULL: every default).  DSE_EINVAL for a value outside its

@@ -30,7 +30,7 @@ CANDIDATES = {
     "screen_tc": {"tile_group": [2, 4, 8, 16], "seed_stride": [32, 64, 128]},
     # multi-target Gram screen: a-blocks per group of its tile order, and
     # whether 2..16 targets take it (8) or the CUDA-core kernels (17)
-    "screen_gmt": {"gmt_group": [1, 5, 4096], "tc_min_targets": [8, 17]},
+    "screen_gmt": {"gmt_group": [1, 5, 4096], "gmt_cluster": [1], "tc_min_targets": [8, 17]},
     # CUDA-core screens (one target, or sample by sample)
     "screen_cc": {"tile_group": [1, 2, 4, 8]},
     # one target with 16 <= N <= 2048: Gram contraction (2048) or direct (16)

@@ -223,7 +223,8 @@ struct ScreenArgs {
 
 // Planner parameters in effect (dse_set_tuning, defaults filled in).
 struct Tuning {
-  int tile_group_tc, tile_group_cc, seed_stride, gram_max_n, tc_min_targets, batch_job_samples, gmt_group;
+  int tile_group_tc, tile_group_cc, seed_stride, gram_max_n, tc_min_targets, batch_job_samples, gmt_group,
+      gmt_cluster;
 };
 Tuning tuning();
 

@@ -1099,7 +1099,7 @@ dse_status launch_pair_gmt(const ScreenArgs &A, const void *space_buf, void *scr
   // entries per list whatever the start, and the sample's thresholds rise
   // no faster)
   const int nc = clusters[dev & 63];
-  if (nc > 0 && n_tiles % 2 == 0) {
+  if (tuning().gmt_cluster == 2 && nc > 0 && n_tiles % 2 == 0) {
     // the tile list holds pairs (2p, 2p + 1) of one b-block; CTA x of the
     // grid takes tiles x, x + grid, ..., so both CTAs of a cluster take the
     // two tiles of the same pairs

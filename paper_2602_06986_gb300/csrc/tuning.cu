@@ -29,6 +29,7 @@ Tuning tuning() {
   o.tc_min_targets = t.tc_min_targets > 0 ? t.tc_min_targets : 8;
   o.batch_job_samples = t.batch_job_samples > 0 ? t.batch_job_samples : (1 << 14);
   o.gmt_group = t.gmt_group > 0 ? t.gmt_group : 2;
+  o.gmt_cluster = t.gmt_cluster > 0 ? t.gmt_cluster : 2;
   return o;
 }
 
@@ -45,7 +46,8 @@ extern "C" dse_status dse_set_tuning(const dse_tuning *t) {
                     (v.gram_max_n == 0 || (v.gram_max_n >= 16 && v.gram_max_n <= 2048)) &&
                     (v.tc_min_targets == 0 || (v.tc_min_targets >= 1 && v.tc_min_targets <= 4096)) &&
                     (v.batch_job_samples == 0 || (v.batch_job_samples >= 1024 && v.batch_job_samples <= (1 << 20))) &&
-                    (v.gmt_group == 0 || (v.gmt_group >= 1 && v.gmt_group <= 4096));
+                    (v.gmt_group == 0 || (v.gmt_group >= 1 && v.gmt_group <= 4096)) &&
+                    (v.gmt_cluster == 0 || v.gmt_cluster == 1 || v.gmt_cluster == 2);
     if (!ok) {
       set_error("tuning value outside its range");
       return DSE_EINVAL;
@@ -71,6 +73,7 @@ extern "C" dse_status dse_get_tuning(dse_tuning *t) {
   o.tc_min_targets = a.tc_min_targets;
   o.batch_job_samples = a.batch_job_samples;
   o.gmt_group = a.gmt_group;
+  o.gmt_cluster = a.gmt_cluster;
   *t = o;
   return DSE_OK;
 }

@@ -50,10 +50,11 @@ class ScreenDesc(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("tile_group", C.c_int32), ("seed_stride", C.c_int32), ("gram_max_n", C.c_int32),
                 ("tc_min_targets", C.c_int32), ("batch_job_samples", C.c_int32), ("gmt_group", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("gmt_cluster", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
-TUNING_FIELDS = ("tile_group", "seed_stride", "gram_max_n", "tc_min_targets", "batch_job_samples", "gmt_group")
+TUNING_FIELDS = ("tile_group", "seed_stride", "gram_max_n", "tc_min_targets", "batch_job_samples", "gmt_group",
+                 "gmt_cluster")
 
 FLAG_TIMING = 1
 FLAG_DEDUP = 2

@@ -86,3 +86,26 @@ def test_json_round_trip_and_apply(tmp_path):
     assert got == {"gram_max_n": 16} and f.installed == {"gram_max_n": 16}
     assert at.apply(back, "screen_single", 100, 1, install=f.install) is None and f.installed == {}
     assert at.load(str(tmp_path / "missing.json")) == {}
+
+
+def test_tuning_fields_and_ranges_host():
+    """dse_set_tuning / dse_get_tuning on the host (no GPU needed): every
+    candidate value the tuner may install is accepted, values outside a
+    field's range are rejected, and None restores the defaults."""
+    from paper_2602_06986_gb300 import dse
+
+    try:
+        for cls, params in at.CANDIDATES.items():
+            for field, values in params.items():
+                assert field in dse.TUNING_FIELDS, (cls, field)
+                for v in values:
+                    dse.set_tuning({field: v})
+                    assert dse.get_tuning()[field] == v, (cls, field, v)
+        for bad in ({"gmt_cluster": 3}, {"gmt_group": 5000}, {"gram_max_n": 8}):
+            with pytest.raises(dse.DseError):
+                dse.set_tuning(bad)
+        dse.set_tuning(None)
+        t = dse.get_tuning()
+        assert t["gmt_cluster"] == 2 and t["gmt_group"] == 2
+    finally:
+        dse.set_tuning(None)

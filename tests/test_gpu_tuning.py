@@ -76,12 +76,13 @@ def test_single_target_settings(env, settings):
 
 
 @pytest.mark.parametrize("settings,flags", [({"tile_group": 2, "seed_stride": 32}, 4), ({"tc_min_targets": 32}, 0),
-                                            ({"gmt_group": 2}, 0)])
+                                            ({"gmt_group": 5}, 0), ({"gmt_cluster": 1}, 0)])
 def test_multi_target_settings(env, settings, flags):
     """16 targets: the sample-by-sample tensor-core kernel (DSE_FLAG_DIRECT)
-    under other tile settings; the CUDA-core path (tc_min_targets above 16)
-    and another tile order of the multi-target Gram kernel against the
-    default multi-target Gram screen."""
+    under other tile settings; the CUDA-core path (tc_min_targets above 16),
+    another tile order of the multi-target Gram kernel and that kernel with
+    one CTA per tile (no clusters) against the default multi-target Gram
+    screen."""
     torch, oracle, dse, W = env
     w = W.large(0, n_targets=16)
     sp = _space(env, w)
