@@ -1826,9 +1826,11 @@ void launch_pairlist_batched(int prec64, const ScreenArgs *args, const int2 *pai
 
 void launch_escalate(const ScreenArgs &A0, int sms, cudaStream_t st, const ScreenArgs *batch) {
   ScreenArgs A = A0;
-  if (!batch && A.esc2_id && A.esc2_count && A.T <= 16 && A.F.v32 && A.y32 && A.ysum32 && A.u > 1e-10f) {
+  if (!batch && A.esc2_id && A.esc2_count && A.T <= 16 && A.N >= 4096 && A.F.v32 && A.y32 && A.ysum32 &&
+      A.u > 1e-10f) {
     // (FP32 screens) the FP32 stage first; the FP64 kernels below take what
-    // it left undecided
+    // it left undecided (below 4096 samples the FP64 pass of a few hundred
+    // candidates costs less than the stage's extra launches)
     cudaMemsetAsync(A.esc2_count, 0, sizeof(unsigned), st);
     note_launches(1);
     k_escalate32<<<sms * 4, 256, 0, st>>>(A0);
