@@ -1022,7 +1022,7 @@ def bench_medium(args):
         flops = GRAM_FLOPS_PER_PAIR_SAMPLE * pairs * N
         peak, tc_src = measured_bf16("bf16_tflops")
         achieved = flops / (launch_ms * 1e-3) / 1e12 if launch_ms > 0 else None
-        roofline = {"bound": "tensor", "kernel": "k_pair_gram (BF16x3 tcgen05 Gram contraction: a*b, a/b, b/a)",
+        roofline = {"bound": "tensor", "kernel": "k_pair_gram (BF16x3 tcgen05 Gram contraction: a*b, a/b, b/a, a+b, a-b)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": (achieved / peak) if achieved else None,
                     "traffic": profiled_traffic("k_pair_gram_medium.txt"),
