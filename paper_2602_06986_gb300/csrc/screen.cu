@@ -1831,11 +1831,14 @@ void launch_escalate(const ScreenArgs &A0, int sms, cudaStream_t st, const Scree
     // (FP32 screens) the FP32 stage first; the FP64 kernels below take what
     // it left undecided (below 4096 samples the FP64 pass of a few hundred
     // candidates costs less than the stage's extra launches)
-    cudaMemsetAsync(A.esc2_count, 0, sizeof(unsigned), st);
-    note_launches(1);
-    k_escalate32<<<sms * 4, 256, 0, st>>>(A0);
-    A.esc_id = A.esc2_id;
-    A.esc_count = A.esc2_count;
+    if (cudaMemsetAsync(A.esc2_count, 0, sizeof(unsigned), st) == cudaSuccess) {
+      note_launches(1);
+      k_escalate32<<<sms * 4, 256, 0, st>>>(A0);
+      A.esc_id = A.esc2_id;
+      A.esc_count = A.esc2_count;
+    } else {
+      cudaGetLastError();  // (the FP64 kernels then take the whole list)
+    }
   }
   note_launches(1);
   if (batch || A.T == 1) {
