@@ -1560,7 +1560,7 @@ __global__ void __launch_bounds__(kEscS, 2) k_escalate_stash(const ScreenArgs A)
 // exactly as in the FP32 screen; the others (near-constant columns such as
 // x * (1/x), other operators, operands outside the FP32-safe range) go to
 // the undecided list that the FP64 kernels then take.
-__global__ void __launch_bounds__(256) k_escalate32(const ScreenArgs A) {
+__global__ void __launch_bounds__(256, 2) k_escalate32(const ScreenArgs A) {
   const int lane = threadIdx.x & 31;
   const unsigned n = min(*A.esc_count, (unsigned)A.esc_cap);
   const unsigned warps = (gridDim.x * blockDim.x) >> 5;
@@ -1578,15 +1578,27 @@ __global__ void __launch_bounds__(256) k_escalate32(const ScreenArgs A) {
     decode_gid(A, gid, &op, &a, &b);
     R32Setup c;
     const bool ok = gid >= (uint64_t)A.n_stored && r32_setup(A, op, a, b, c);
-    float Sm[18];
+    // two passes over the samples, targets 0..7 with the realised decision,
+    // then (valid candidates only) targets 8..15: half the running sums, so
+    // that two blocks fit on an SM; the sums are those of one pass over all
+    float Sm[18], Sh[10];
 #pragma unroll
     for (int k = 0; k < 18; ++k) Sm[k] = 0.f;
-    if (ok) r32_sums<16, 1>(A, op, a, b, A.y32 + (int64_t)A.t0 * A.ldy, A.T, c, Sm);
+    if (ok) {
+      r32_sums<8, 1>(A, op, a, b, A.y32 + (int64_t)A.t0 * A.ldy, A.T < 8 ? A.T : 8, c, Sh);
+#pragma unroll
+      for (int k = 0; k < 10; ++k) Sm[k] = Sh[k];
+    }
     CandInterval<float> ci{};
     int decided = 0;  // 1 valid, 2 degenerate
     if (ok) {
       ci = cand_interval<float>(Sm[0], Sm[1], Nf, invN, sqrtN, c.cshift, c.ee, gamma, u, fmin);
       decided = ci.realised == 1 ? 1 : ci.realised == 0 ? 2 : 0;
+    }
+    if (decided == 1 && A.T > 8) {
+      r32_sums<8, 1>(A, op, a, b, A.y32 + (int64_t)(A.t0 + 8) * A.ldy, A.T - 8, c, Sh);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) Sm[10 + k] = Sh[2 + k];
     }
     if (lane == 0) {
       if (decided == 1) {
