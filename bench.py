@@ -1025,9 +1025,11 @@ def bench_medium(args):
         roofline = {"bound": "tensor", "kernel": "k_pair_gram (BF16x3 tcgen05 Gram contraction: a*b, a/b, b/a, a+b, a-b)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": (achieved / peak) if achieved else None,
-                    "traffic": profiled_traffic("k_pair_gram_medium.txt"),
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
-                                      "(profiles/k_pair_gram_medium.txt)",
+                    # (the committed capture predates the kernel's a+b / a-b slots: no
+                    # counters of the current kernel, so no traffic figure)
+                    "traffic": None,
+                    "traffic_source": "none: profiles/k_pair_gram_medium.txt was captured before the kernel "
+                                      "took the a+b and a-b slots",
                     "peak_source": tc_src + " (of measured, burst: the kernel runs ~0.06 ms at a time inside a short step)",
                     "flops_per_launch": flops, "flops_per_pair_sample": GRAM_FLOPS_PER_PAIR_SAMPLE,
                     "pairs": pairs, "launch_ms": launch_ms, "share_of_step": mul_ms / tot_ms}
