@@ -53,7 +53,9 @@ def check_list(ids, sc, eb, oids, osc, orc, Y, t):
 
 def assert_same_topk(ids_m, sc_m, eb_m, ids_f, sc_f, eb_f):
     """Two top-k lists of one screen taken different ways (merged range
-    screens and the full screen) agree up to ties inside the scores' bounds:
+    screens and the full screen) agree up to ties inside the scores' bounds
+    (the method's parity target is top-k sets identical apart from ties
+    inside the score tolerance, 1e-5 relative):
     a candidate's reported score may come from the FP32 or the FP32-pair
     re-score depending on how it was classified in its own screen, so
     members whose scores lie within the bounds of the k-th score are
